@@ -1,0 +1,860 @@
+"""AIRG oracle: setup and solve, step by step in the paper's order.
+
+TEST INFRASTRUCTURE ONLY -- imported by tests, the smoke check and the CPU
+baseline of the benchmark; never by the product library.
+
+Every function names the passage of arXiv 2508.17517 it restates.  Where the
+paper leaves a choice open, the reading taken is stated in the docstring (the
+same readings are listed in the design notes of the repository).
+
+Functions pinned by tests against closed forms, brute force or library
+routines: exact dot, SpMV, problem builder + sweep, strength, PMISR, DDC,
+extract, GMRES polynomial coefficients, fixed-sparsity inverse, restrictor,
+one-point prolongator, RAP + drop/lump, harmonic Ritz / Newton application,
+V-cycle, FGMRES, dense adjoint.
+Parity unpinned (internal choices with no closed form in the paper): the
+value of the R drop tolerance, the PMISR measure direction, the one-point
+weight, and the Loe-Morgan added-root thresholds.
+"""
+import ctypes
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import lib
+
+# Purposes of the counter-based random streams (stream key = (seed, level, purpose)).
+PURPOSE_COEF = 1      # random rhs for the smoother polynomial coefficients (Sec. 2.2)
+PURPOSE_PMISR = 2     # Luby weights of PMISR (Sec. 2.1)
+PURPOSE_COARSE = 3    # random rhs for the coarse-grid polynomial (Sec. 2.3)
+PURPOSE_TRUNC = 4     # second random rhs of the truncation test (Sec. 2.4)
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# --------------------------------------------------------------------------
+# Sparse matrix container
+# --------------------------------------------------------------------------
+@dataclass
+class CSR:
+    n_rows: int
+    n_cols: int
+    rowptr: np.ndarray   # int64, n_rows + 1
+    col: np.ndarray      # int64, ascending within a row
+    val: np.ndarray      # float64
+
+    @property
+    def nnz(self):
+        return int(self.rowptr[-1])
+
+    def row_ids(self):
+        return np.repeat(np.arange(self.n_rows, dtype=np.int64), np.diff(self.rowptr))
+
+    def to_dense(self):
+        D = np.zeros((self.n_rows, self.n_cols))
+        D[self.row_ids(), self.col] = self.val
+        return D
+
+
+def csr_from_entries(n_rows, n_cols, rows, cols, vals):
+    """CSR from entries already sorted by (row, col) with no duplicates."""
+    rowptr = np.zeros(n_rows + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n_rows), out=rowptr[1:])
+    return CSR(n_rows, n_cols, rowptr, np.ascontiguousarray(cols, dtype=np.int64),
+               np.ascontiguousarray(vals, dtype=np.float64))
+
+
+def csr_select(A, keep):
+    rows = A.row_ids()[keep]
+    return csr_from_entries(A.n_rows, A.n_cols, rows, A.col[keep], A.val[keep])
+
+
+# --------------------------------------------------------------------------
+# Random streams and the correctly rounded dot product
+# --------------------------------------------------------------------------
+def rng_uniform(seed, level, purpose, n):
+    out = np.empty(n, dtype=np.float64)
+    L = lib()
+    L.orc_rng_uniform(L.orc_rng_key(seed, level, purpose), n, _p(out))
+    return out
+
+
+def rng_u32(seed, level, purpose, n):
+    out = np.empty(n, dtype=np.uint32)
+    L = lib()
+    L.orc_rng_u32(L.orc_rng_key(seed, level, purpose), n, _p(out))
+    return out
+
+
+def xdot(x, y):
+    """<x, y> rounded once from the exact sum of exact products."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    return float(lib().orc_dot_exact(x.size, _p(x), _p(y)))
+
+
+def xnorm(x):
+    return math.sqrt(xdot(x, x))
+
+
+def spmv(A, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(A.n_rows, dtype=np.float64)
+    lib().orc_spmv(A.n_rows, _p(A.rowptr), _p(A.col), _p(A.val), _p(x), _p(y))
+    return y
+
+
+def spgemm(A, B):
+    """C = A B, each entry summed in ascending order of A's column index."""
+    L = lib()
+    crp, cci, cv = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    rc = L.orc_spgemm(A.n_rows, _p(A.rowptr), _p(A.col), _p(A.val), B.n_cols,
+                      _p(B.rowptr), _p(B.col), _p(B.val),
+                      ctypes.byref(crp), ctypes.byref(cci), ctypes.byref(cv))
+    if rc != 0:
+        raise MemoryError("oracle spgemm")
+    rowptr = np.ctypeslib.as_array(ctypes.cast(crp, ctypes.POINTER(ctypes.c_int64)),
+                                   (A.n_rows + 1,)).copy()
+    nnz = int(rowptr[-1])
+    if nnz:
+        col = np.ctypeslib.as_array(ctypes.cast(cci, ctypes.POINTER(ctypes.c_int64)), (nnz,)).copy()
+        val = np.ctypeslib.as_array(ctypes.cast(cv, ctypes.POINTER(ctypes.c_double)), (nnz,)).copy()
+    else:
+        col = np.zeros(0, np.int64)
+        val = np.zeros(0, np.float64)
+    for p in (crp, cci, cv):
+        L.orc_free(p)
+    return CSR(A.n_rows, B.n_cols, rowptr, col, val)
+
+
+# --------------------------------------------------------------------------
+# Problem: Eq. 1-2, discretised by first-order upwind differences (Sec. 3)
+# --------------------------------------------------------------------------
+@dataclass
+class Advection2D:
+    nx: int
+    ny: int
+    vx: float
+    vy: float
+    h: float
+    A: CSR
+    inflow: np.ndarray     # sorted node indices on the inflow boundary
+    diag: float
+
+
+def advection_2d(nx, ny, vx, vy, h=None):
+    """Upwind finite differences for v.grad(u) = s on an nx-by-ny node grid.
+
+    Reading of Eq. 1-2 and Sec. 3: nodes x_i = i*h, y_j = j*h, index
+    i + nx*j; the equation is multiplied by h so that the stencil does not
+    change with refinement: interior row d*u_ij - |vx| u_(upwind x) -
+    |vy| u_(upwind y) = h*s_ij with d = |vx| + |vy|; nodes on the inflow
+    boundary (v.n < 0) keep their unknowns (the boundary is not eliminated)
+    with the row d*u = d*g.  Zero velocity components store no entry.
+    """
+    if h is None:
+        h = 1.0 / (nx - 1)
+    n = nx * ny
+    ax, ay = abs(vx), abs(vy)
+    d = ax + ay
+    idx = np.arange(n, dtype=np.int64)
+    i = idx % nx
+    j = idx // nx
+    inflow = np.zeros(n, dtype=bool)
+    if vx > 0:
+        inflow |= i == 0
+    elif vx < 0:
+        inflow |= i == nx - 1
+    if vy > 0:
+        inflow |= j == 0
+    elif vy < 0:
+        inflow |= j == ny - 1
+    rows, cols, vals = [idx], [idx], [np.full(n, d)]
+    interior = ~inflow
+    if vx != 0:
+        up = idx - 1 if vx > 0 else idx + 1
+        rows.append(idx[interior]); cols.append(up[interior]); vals.append(np.full(interior.sum(), -ax))
+    if vy != 0:
+        up = idx - nx if vy > 0 else idx + nx
+        rows.append(idx[interior]); cols.append(up[interior]); vals.append(np.full(interior.sum(), -ay))
+    r = np.concatenate(rows); c = np.concatenate(cols); v = np.concatenate(vals)
+    order = np.lexsort((c, r))
+    A = csr_from_entries(n, n, r[order], c[order], v[order])
+    return Advection2D(nx, ny, vx, vy, h, A, np.nonzero(inflow)[0].astype(np.int64), d)
+
+
+def assemble_rhs(prob, g, s):
+    """b = B g + h s: d*g on inflow nodes (g in increasing node order), h*s elsewhere."""
+    n = prob.A.n_rows
+    b = prob.h * np.asarray(s, dtype=np.float64).reshape(n)
+    b[prob.inflow] = prob.diag * np.asarray(g, dtype=np.float64)
+    return b
+
+
+def sweep_order(prob):
+    ii = np.arange(prob.nx) if prob.vx >= 0 else np.arange(prob.nx)[::-1]
+    jj = np.arange(prob.ny) if prob.vy >= 0 else np.arange(prob.ny)[::-1]
+    return (ii[None, :] + prob.nx * jj[:, None]).reshape(-1).astype(np.int64)
+
+
+def sweep_solve(A, b, order):
+    """Exact discrete solution by substitution in upwind order (Sec. 1.1)."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    u = np.empty(A.n_rows)
+    rc = lib().orc_sweep(A.n_rows, _p(A.rowptr), _p(A.col), _p(A.val), _p(order), _p(b), _p(u))
+    if rc != 0:
+        raise ValueError("matrix is not triangular in the given order (%d)" % rc)
+    return u
+
+
+# --------------------------------------------------------------------------
+# Options (defaults = the command line of Sec. 3)
+# --------------------------------------------------------------------------
+@dataclass
+class Options:
+    strong_threshold: float = 0.99
+    ddc_fraction: float = 0.01
+    ddc_its: int = 2
+    poly_order: int = 6              # degree p: p SpMVs per application, p+1 coefficients
+    coarse_poly_order: int = 100     # m_c: Arnoldi steps for the coarse polynomial
+    trunc_rtol: float = 1e-1         # alpha_trunc; <= 0 disables truncation
+    trunc_start_level: int = 0
+    max_levels: int = 64
+    coarse_min_rows: int = 1
+    a_drop: float = 1e-6
+    a_lump: bool = True
+    r_drop: float = 1e-2             # parity unpinned: the paper gives no value
+    seed: int = 2508175
+    breakdown_tol: float = 1e-8      # rank reading of Sec. 2.3: h_{j+1,j} <= tol * ||H(:,j)||
+    addroot_log10: float = 4.0       # Loe-Morgan extra-root threshold (unpinned)
+    addroot_per: float = 14.0
+
+
+# --------------------------------------------------------------------------
+# CF splitting: PMISR DDC (Sec. 2.1)
+# --------------------------------------------------------------------------
+def strength(A, theta):
+    """Per-entry strong flags; reading: |a_ij| >= theta * max_{k!=i} |a_ik|."""
+    s = np.empty(A.nnz, dtype=np.int8)
+    lib().orc_strength(A.n_rows, _p(A.rowptr), _p(A.col), _p(A.val), float(theta), _p(s))
+    return s.astype(bool)
+
+
+def symmetrized_graph(A, strong):
+    """Adjacency of S + S^T without self loops, as (rowptr, col) sorted."""
+    n = A.n_rows
+    r = A.row_ids()[strong]
+    c = A.col[strong]
+    key = np.unique(np.concatenate([r * n + c, c * n + r]))
+    gr = key // n
+    gc = key % n
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(gr, minlength=n), out=rowptr[1:])
+    return rowptr, gc
+
+
+def pmisr(n, g_rowptr, g_col, weights):
+    """Luby-type independent set in S + S^T whose members become F points.
+
+    Reading: each point has the key (degree in S + S^T, 32-bit random weight,
+    index), compared lexicographically.  A round makes F every undecided point
+    whose key beats the keys of all its undecided neighbours, then makes C
+    every undecided neighbour of a new F point.  Rounds repeat until nothing is
+    undecided (no loop cap, Sec. 2.1).
+    """
+    deg = np.diff(g_rowptr)
+    order = np.lexsort((np.arange(n), weights.astype(np.int64), deg))
+    rank = np.empty(n, dtype=np.int64)
+    rank[order] = np.arange(n)
+    src = np.repeat(np.arange(n, dtype=np.int64), deg)
+    dst = g_col
+    UND, F, C = 0, 1, 2
+    state = np.zeros(n, dtype=np.int8)
+    rounds = 0
+    while (state == UND).any():
+        rounds += 1
+        und = state == UND
+        loses = np.zeros(n, dtype=bool)
+        e = und[src] & und[dst] & (rank[dst] > rank[src])
+        loses[src[e]] = True
+        new_f = und & ~loses
+        state[new_f] = F
+        e2 = new_f[src] & (state[dst] == UND)
+        state[dst[e2]] = C
+    return state == F, rounds
+
+
+def ddc_ratio(A, is_f):
+    r = np.empty(A.n_rows)
+    f8 = is_f.astype(np.int8)
+    lib().orc_ddc_ratio(A.n_rows, _p(A.rowptr), _p(A.col), _p(A.val), _p(f8), _p(r))
+    return r
+
+
+def ddc_pass(A, is_f, fraction, nbins=1000):
+    """One diagonal-dominance clean-up pass (Sec. 2.1).
+
+    Reading of the binning described in Sec. 2.1: ratios of the F rows are
+    placed in `nbins` equal bins over [0, max ratio] (bin = min(nbins-1,
+    floor((r / r_max) * nbins))); the target is k = ceil(fraction * n_F); the
+    bin boundary B whose count of F points at or above it is closest to k is
+    chosen (ties: the higher boundary), and those points become C.
+    """
+    n_f = int(is_f.sum())
+    if n_f == 0:
+        return is_f, 0
+    ratio = ddc_ratio(A, is_f)
+    rf = ratio[is_f]
+    rmax = float(rf.max())
+    if not (rmax > 0.0):
+        return is_f, 0
+    if math.isinf(rmax):
+        raise ValueError("zero diagonal in an F row")
+    k = math.ceil(fraction * float(n_f))
+    t = (rf / rmax) * float(nbins)
+    bins = np.minimum(nbins - 1, np.floor(t).astype(np.int64))
+    cnt = np.bincount(bins, minlength=nbins)
+    above = np.zeros(nbins + 1, dtype=np.int64)
+    above[:nbins] = np.cumsum(cnt[::-1])[::-1]
+    best_b, best_d = nbins, abs(0 - k)
+    for b in range(nbins - 1, -1, -1):
+        dist = abs(int(above[b]) - k)
+        if dist < best_d:
+            best_b, best_d = b, dist
+    fidx = np.nonzero(is_f)[0]
+    conv = fidx[bins >= best_b]
+    out = is_f.copy()
+    out[conv] = False
+    return out, conv.size
+
+
+def cf_split(A, opts, level):
+    strong = strength(A, opts.strong_threshold)
+    g_rowptr, g_col = symmetrized_graph(A, strong)
+    w = rng_u32(opts.seed, level, PURPOSE_PMISR, A.n_rows)
+    is_f, rounds = pmisr(A.n_rows, g_rowptr, g_col, w)
+    converted = []
+    for _ in range(opts.ddc_its):
+        is_f, nconv = ddc_pass(A, is_f, opts.ddc_fraction)
+        converted.append(nconv)
+    return strong, is_f, rounds, converted
+
+
+# --------------------------------------------------------------------------
+# Block extraction (Eq. 3)
+# --------------------------------------------------------------------------
+def local_index(mask):
+    idx = np.full(mask.size, -1, dtype=np.int64)
+    idx[mask] = np.arange(int(mask.sum()), dtype=np.int64)
+    return idx
+
+
+def extract(A, row_mask, col_mask):
+    """A[rows, cols] with rows/cols renumbered in increasing original index."""
+    rid = A.row_ids()
+    keep = row_mask[rid] & col_mask[A.col]
+    rmap = local_index(row_mask)
+    cmap = local_index(col_mask)
+    return csr_from_entries(int(row_mask.sum()), int(col_mask.sum()),
+                            rmap[rid[keep]], cmap[A.col[keep]], A.val[keep])
+
+
+# --------------------------------------------------------------------------
+# GMRES polynomials (Sec. 2.2, Eq. 4)
+# --------------------------------------------------------------------------
+def arnoldi(A, b, m, breakdown_tol):
+    """m steps of modified Gram-Schmidt Arnoldi from b (x0 = 0).
+
+    Dots are correctly rounded, norms are sqrt of those, updates are
+    w - (h * v) with the product rounded first, and normalisation divides.
+    Breakdown reading: stop after step j when h_{j+1,j} <= tol * ||H(:,j)||,
+    the column norm summed in order.
+    Returns (H[(k+1) x k], k, broke, beta).
+    """
+    beta = xnorm(b)
+    V = [b / beta]
+    H = np.zeros((m + 1, m))
+    k = m
+    broke = False
+    for j in range(m):
+        w = spmv(A, V[j])
+        for i in range(j + 1):
+            hij = xdot(w, V[i])
+            H[i, j] = hij
+            w = w - hij * V[i]
+        hn = xnorm(w)
+        H[j + 1, j] = hn
+        s = 0.0
+        for i in range(j + 2):
+            s = s + float(H[i, j]) * float(H[i, j])
+        if hn <= breakdown_tol * math.sqrt(s):
+            k = j + 1
+            broke = True
+            break
+        if j + 1 < m:
+            V.append(w / hn)
+    return H[:k + 1, :k].copy(), k, broke, beta
+
+
+def givens_lsq(H, beta):
+    """y = argmin || beta e1 - H y || for the (k+1) x k Hessenberg H (Givens QR)."""
+    k = H.shape[1]
+    R = [[float(H[i, j]) for j in range(k)] for i in range(k + 1)]
+    g = [0.0] * (k + 1)
+    g[0] = float(beta)
+    cs, sn = [0.0] * k, [0.0] * k
+    for j in range(k):
+        for i in range(j):
+            t1 = cs[i] * R[i][j] + sn[i] * R[i + 1][j]
+            t2 = -sn[i] * R[i][j] + cs[i] * R[i + 1][j]
+            R[i][j] = t1
+            R[i + 1][j] = t2
+        a, bb = R[j][j], R[j + 1][j]
+        r = math.sqrt(a * a + bb * bb)
+        cs[j] = a / r
+        sn[j] = bb / r
+        R[j][j] = r
+        R[j + 1][j] = 0.0
+        g[j + 1] = -sn[j] * g[j]
+        g[j] = cs[j] * g[j]
+    y = [0.0] * k
+    for j in range(k - 1, -1, -1):
+        s = g[j]
+        for i in range(j + 1, k):
+            s = s - R[j][i] * y[i]
+        y[j] = s / R[j][j]
+    return y
+
+
+def power_coefficients(H, beta, y):
+    """alpha with x = sum_j y_j v_j = (alpha_0 + alpha_1 A + ...) b  (Eq. 4).
+
+    Each Arnoldi vector is a polynomial in A applied to b: c_1 = 1/beta and
+    c_{j+1}(z) = (z c_j(z) - sum_{i<=j} h_ij c_i(z)) / h_{j+1,j}.
+    """
+    k = len(y)
+    c = [[0.0] * k for _ in range(k)]
+    c[0][0] = 1.0 / float(beta)
+    for j in range(k - 1):
+        hn = float(H[j + 1, j])
+        for t in range(j + 2):
+            num = c[j][t - 1] if t >= 1 else 0.0
+            for i in range(j + 1):
+                num = num - float(H[i, j]) * c[i][t]
+            c[j + 1][t] = num / hn
+    alpha = [0.0] * k
+    for t in range(k):
+        s = 0.0
+        for j in range(k):
+            s = s + y[j] * c[j][t]
+        alpha[t] = s
+    return alpha
+
+
+def gmres_poly_coeffs(A_ff, opts, level):
+    """Coefficients of the degree-p GMRES polynomial q(A_ff) ~ A_ff^-1 (Eq. 4).
+
+    Reading of "order p": degree p, p+1 coefficients, p+1 Arnoldi steps from a
+    uniform [0,1) random rhs.  On breakdown the degree drops and the higher
+    coefficients are zero.
+    """
+    p = opts.poly_order
+    b = rng_uniform(opts.seed, level, PURPOSE_COEF, A_ff.n_rows)
+    H, k, broke, beta = arnoldi(A_ff, b, p + 1, opts.breakdown_tol)
+    y = givens_lsq(H, beta)
+    alpha = power_coefficients(H, beta, y)
+    return np.array(alpha + [0.0] * (p + 1 - k)), k, broke
+
+
+def horner_apply(A, alpha, t):
+    """q(A) t with q(z) = sum alpha_k z^k: w = alpha_p t; w = alpha_k t + A w."""
+    p = len(alpha) - 1
+    w = float(alpha[p]) * t
+    for k in range(p - 1, -1, -1):
+        w = float(alpha[k]) * t + spmv(A, w)
+    return w
+
+
+def fixed_sparsity_inverse(A_ff, alpha):
+    """Eq. 5: alpha_0 I + alpha_1 A_ff + sum_{k>=2} alpha_k T_k on pattern(A_ff).
+
+    Reading: T_1 = A_ff, T_k = mask(A_ff T_{k-1}) (each power restricted to
+    the sparsity of A_ff); entries accumulate as (i==j ? alpha_0 : 0) then
+    + alpha_k * T_k for k = 1..p in turn.  Every row must store its diagonal.
+    """
+    n = A_ff.n_rows
+    diag = A_ff.col == A_ff.row_ids()
+    if int(diag.sum()) != n:
+        raise ValueError("A_ff row without a stored diagonal")
+    acc = np.where(diag, float(alpha[0]), 0.0)
+    T = A_ff.val.copy()
+    for k in range(1, len(alpha)):
+        if k >= 2:
+            Tn = np.empty_like(T)
+            lib().orc_fixed_sparsity_power(n, _p(A_ff.rowptr), _p(A_ff.col), _p(A_ff.val),
+                                           _p(T), _p(Tn))
+            T = Tn
+        acc = acc + float(alpha[k]) * T
+    return CSR(n, n, A_ff.rowptr.copy(), A_ff.col.copy(), acc)
+
+
+def restrictor_block(A_cf, Ainv, r_drop):
+    """Z = -A_cf Ahat_ff^-1 (Eq. 3-4 context), then the relative drop on R."""
+    P = spgemm(A_cf, Ainv)
+    Z = CSR(P.n_rows, P.n_cols, P.rowptr, P.col, -P.val)
+    keep = np.empty(Z.nnz, dtype=np.int8)
+    lib().orc_drop_rows(Z.n_rows, _p(Z.rowptr), _p(Z.val), float(r_drop), _p(keep))
+    return csr_select(Z, keep.astype(bool))
+
+
+def one_point(A, strong, is_f):
+    c_index = local_index(~is_f)
+    f8 = is_f.astype(np.int8)
+    s8 = strong.astype(np.int8)
+    w = np.empty(A.n_rows, dtype=np.int64)
+    lib().orc_one_point(A.n_rows, _p(A.rowptr), _p(A.col), _p(A.val), _p(s8), _p(f8),
+                        _p(c_index), _p(w))
+    return w[is_f].copy()
+
+
+def coarse_matrix(A, is_f, Z, W, a_drop, lump):
+    """A_coarse = R (A P), R = [Z I], P = [W; I] (Eq. 3), then drop + lump.
+
+    R and P are written in the fine numbering; AP is formed first and every
+    entry of both products is summed in ascending inner index.
+    """
+    n = A.n_rows
+    f_ids = np.nonzero(is_f)[0]
+    c_ids = np.nonzero(~is_f)[0]
+    n_c = c_ids.size
+    c_index = local_index(~is_f)
+    # P: one entry per row (weight 1) for C rows and F rows with a C neighbour
+    prow = np.concatenate([c_ids, f_ids[W >= 0]])
+    pcol = np.concatenate([c_index[c_ids], W[W >= 0]])
+    o = np.argsort(prow, kind="stable")
+    P = csr_from_entries(n, n_c, prow[o], pcol[o], np.ones(prow.size))
+    # R: Z row c in fine columns plus the identity at the C point itself
+    zr = Z.row_ids()
+    rrow = np.concatenate([zr, np.arange(n_c, dtype=np.int64)])
+    rcol = np.concatenate([f_ids[Z.col], c_ids])
+    rval = np.concatenate([Z.val, np.ones(n_c)])
+    o = np.lexsort((rcol, rrow))
+    R = csr_from_entries(n_c, n, rrow[o], rcol[o], rval[o])
+    AP = spgemm(A, P)
+    Ac = spgemm(R, AP)
+    keep = np.empty(Ac.nnz, dtype=np.int8)
+    vout = np.empty(Ac.nnz)
+    rc = lib().orc_drop_lump(Ac.n_rows, _p(Ac.rowptr), _p(Ac.col), _p(Ac.val), float(a_drop),
+                             1 if lump else 0, _p(keep), _p(vout))
+    if rc != 0:
+        raise ValueError("coarse row without a diagonal")
+    Ac = CSR(Ac.n_rows, Ac.n_cols, Ac.rowptr, Ac.col, vout)
+    return csr_select(Ac, keep.astype(bool))
+
+
+# --------------------------------------------------------------------------
+# Coarse-grid solver: GMRES polynomial in Newton form with harmonic Ritz
+# roots (Sec. 2.3) and the truncation test (Sec. 2.4)
+# --------------------------------------------------------------------------
+def harmonic_ritz(H, k, broke):
+    """Roots of the GMRES residual polynomial: eig(H_k + h^2 H_k^-T e_k e_k^T).
+
+    After a breakdown the Krylov space is invariant and the roots are the
+    eigenvalues of H_k itself.
+    """
+    Hk = np.array(H[:k, :k], dtype=np.float64)
+    if not broke:
+        h = float(H[k, k - 1])
+        ek = np.zeros(k)
+        ek[-1] = 1.0
+        f = np.linalg.solve(Hk.T, ek)
+        Hk[:, -1] += (h * h) * f
+    return np.linalg.eigvals(Hk)
+
+
+def _log_dist(a, b):
+    d = abs(a - b)
+    return -math.inf if d == 0.0 else math.log(d)
+
+
+def order_roots(theta, opts):
+    """Leja order (conjugates kept adjacent) + Loe-Morgan extra copies.
+
+    Reading (unpinned constants): pof_k = prod_{i!=k} |1 - theta_k/theta_i|
+    in log form; a root with log10(pof_k) > addroot_log10 gets
+    ceil((log10 pof_k - addroot_log10) / addroot_per) extra copies, appended
+    after the Leja-ordered distinct roots.  Returns a list of (re, im) with
+    im > 0 standing for the conjugate pair and im == 0 for a real root.
+    """
+    theta = np.asarray(theta, dtype=np.complex128)
+    reps = [complex(t) for t in theta if t.imag >= 0.0]
+    allr = [complex(t) for t in theta]
+    # Leja order of the representatives
+    chosen, rest = [], list(reps)
+    if rest:
+        i0 = max(range(len(rest)), key=lambda i: abs(rest[i]))
+        chosen.append(rest.pop(i0))
+    while rest:
+        pts = []
+        for c in chosen:
+            pts.append(c)
+            if c.imag > 0:
+                pts.append(c.conjugate())
+        best, bi = -math.inf, 0
+        for i, z in enumerate(rest):
+            s = sum(_log_dist(z, q) for q in pts)
+            if s > best:
+                best, bi = s, i
+        chosen.append(rest.pop(bi))
+    extra = []
+    for z in chosen:
+        lp = 0.0
+        for q in allr:
+            if q == z:
+                continue
+            d = abs(1.0 - z / q)
+            lp += -math.inf if d == 0.0 else math.log10(d)
+        if z.imag > 0:
+            pass  # the conjugate of z is among allr and was counted above
+        if lp > opts.addroot_log10:
+            extra += [z] * int(math.ceil((lp - opts.addroot_log10) / opts.addroot_per))
+    return [(z.real, z.imag if z.imag > 0 else 0.0) for z in chosen + extra]
+
+
+def coarse_polynomial(A, opts, level, m):
+    b1 = rng_uniform(opts.seed, level, PURPOSE_COARSE, A.n_rows)
+    H, k, broke, beta = arnoldi(A, b1, m, opts.breakdown_tol)
+    theta = harmonic_ritz(H, k, broke)
+    return order_roots(theta, opts), H, k, broke
+
+
+def newton_apply(A, roots, b):
+    """x = q(A) b with q(z) = (1 - prod(1 - z/theta_i)) / z (Sec. 2.3).
+
+    Real root theta: x += r/theta, r -= A r / theta.  Pair a +- ib:
+    w = A r, t = 2a r - w, x += t/|theta|^2, r -= A t / |theta|^2.  The last
+    root skips its residual update.
+    """
+    x = np.zeros_like(b)
+    r = b.copy()
+    nr = len(roots)
+    for idx, (a, bi) in enumerate(roots):
+        last = idx == nr - 1
+        if bi == 0.0:
+            x = x + r / a
+            if not last:
+                r = r - spmv(A, r) / a
+        else:
+            mod2 = a * a + bi * bi
+            w = spmv(A, r)
+            t = (2.0 * a) * r - w
+            x = x + t / mod2
+            if not last:
+                r = r - spmv(A, t) / mod2
+    return x
+
+
+def truncation_residual(A, roots, opts, level):
+    """||b2 - A q(A) b2|| / ||b2|| for a fresh random b2 (Sec. 2.4)."""
+    b2 = rng_uniform(opts.seed, level, PURPOSE_TRUNC, A.n_rows)
+    x = newton_apply(A, roots, b2)
+    r = b2 - spmv(A, x)
+    return xnorm(r) / xnorm(b2)
+
+
+# --------------------------------------------------------------------------
+# Hierarchy
+# --------------------------------------------------------------------------
+@dataclass
+class Level:
+    n: int
+    A: CSR
+    strong: np.ndarray
+    is_f: np.ndarray
+    A_ff: CSR
+    A_fc: CSR
+    Z: CSR
+    W: np.ndarray
+    alpha: np.ndarray
+    alpha_k: int
+    pmisr_rounds: int
+    ddc_converted: list
+    trunc_rel: float = float("nan")
+
+
+@dataclass
+class Hierarchy:
+    levels: list = field(default_factory=list)
+    A_coarse: CSR = None
+    roots: list = None
+    coarse_k: int = 0
+    coarse_trunc_rel: float = float("nan")
+    truncated: bool = False
+    opts: Options = None
+
+
+def setup(A, opts=None):
+    """AIRG setup, level by level, in the order of Sec. 2 (Sec. 2.4: the
+    truncation test comes before the CF splitting on each level)."""
+    opts = opts or Options()
+    Hh = Hierarchy(opts=opts)
+    level = 0
+    while True:
+        n = A.n_rows
+        last = level >= opts.max_levels - 1 or n <= opts.coarse_min_rows
+        m_c = min(opts.coarse_poly_order, n)
+        trunc_rel = float("nan")
+        if not last and opts.trunc_rtol > 0.0 and level >= opts.trunc_start_level:
+            roots, H, k, broke = coarse_polynomial(A, opts, level, m_c)
+            trunc_rel = truncation_residual(A, roots, opts, level)
+            if trunc_rel <= opts.trunc_rtol:
+                Hh.A_coarse, Hh.roots, Hh.coarse_k = A, roots, k
+                Hh.coarse_trunc_rel, Hh.truncated = trunc_rel, True
+                return Hh
+        if not last:
+            strong, is_f, rounds, conv = cf_split(A, opts, level)
+            n_f = int(is_f.sum())
+            if n_f == 0 or n_f == n:
+                last = True
+        if last:
+            roots, H, k, broke = coarse_polynomial(A, opts, level, m_c)
+            Hh.A_coarse, Hh.roots, Hh.coarse_k = A, roots, k
+            Hh.coarse_trunc_rel = trunc_rel
+            return Hh
+        A_ff = extract(A, is_f, is_f)
+        A_fc = extract(A, is_f, ~is_f)
+        A_cf = extract(A, ~is_f, is_f)
+        alpha, k, broke = gmres_poly_coeffs(A_ff, opts, level)
+        Ainv = fixed_sparsity_inverse(A_ff, alpha)
+        Z = restrictor_block(A_cf, Ainv, opts.r_drop)
+        W = one_point(A, strong, is_f)
+        Ac = coarse_matrix(A, is_f, Z, W, opts.a_drop, opts.a_lump)
+        Hh.levels.append(Level(n, A, strong, is_f, A_ff, A_fc, Z, W, alpha, k, rounds, conv,
+                               trunc_rel))
+        A = Ac
+        level += 1
+
+
+# --------------------------------------------------------------------------
+# Solve: V-cycle with up F-point smoothing only (Eq. 6), outer FGMRES
+# --------------------------------------------------------------------------
+def vcycle(Hh, r, level=0):
+    """e = M^-1 r with zero initial guess: restrict, coarse-correct,
+    prolongate with W, then one F-point smooth e_f += q(A_ff)(r_f - A_fc e_c -
+    A_ff e_f) (Eq. 6)."""
+    if level == len(Hh.levels):
+        return newton_apply(Hh.A_coarse, Hh.roots, r)
+    L = Hh.levels[level]
+    rf = r[L.is_f]
+    rc = r[~L.is_f] + spmv(L.Z, rf)
+    ec = vcycle(Hh, rc, level + 1)
+    ef = np.where(L.W >= 0, ec[np.maximum(L.W, 0)], 0.0)
+    t = rf - spmv(L.A_fc, ec) - spmv(L.A_ff, ef)
+    ef = ef + horner_apply(L.A_ff, L.alpha, t)
+    e = np.empty(L.n)
+    e[L.is_f] = ef
+    e[~L.is_f] = ec
+    return e
+
+
+@dataclass
+class SolveInfo:
+    iterations: int
+    rel_residual: float
+    converged: bool
+    history: list
+
+
+def fgmres(A, b, precond, x0=None, rtol=1e-10, atol=1e-50, restart=30, maxit=200):
+    """Right-preconditioned (flexible) GMRES with modified Gram-Schmidt.
+
+    Converged when the true ||b - A x||_2 <= max(rtol ||b||_2, atol), the
+    unpreconditioned norm of Sec. 3 (the paper wraps the V-cycle in
+    Richardson instead; the outer Krylov method is GMRES here).
+    """
+    n = A.n_rows
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    bn = float(np.linalg.norm(b))
+    tol = max(rtol * bn, atol)
+    its = 0
+    hist = []
+    r = b - spmv(A, x)
+    rn = float(np.linalg.norm(r))
+    hist.append(rn / bn if bn > 0 else 0.0)
+    while rn > tol and its < maxit:
+        V = [r / rn]
+        Zs = []
+        H = np.zeros((restart + 1, restart))
+        g = np.zeros(restart + 1)
+        g[0] = rn
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        j_done = 0
+        for j in range(restart):
+            z = precond(V[j])
+            Zs.append(z)
+            w = spmv(A, z)
+            for i in range(j + 1):
+                H[i, j] = float(np.dot(w, V[i]))
+                w = w - H[i, j] * V[i]
+            hn = float(np.linalg.norm(w))
+            H[j + 1, j] = hn
+            for i in range(j):
+                t1 = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t1
+            den = math.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            j_done = j + 1
+            hist.append(abs(g[j + 1]) / bn)
+            if abs(g[j + 1]) <= tol or its >= maxit or H[j, j] == 0.0:
+                break
+            if hn == 0.0:
+                break
+            V.append(w / hn)
+        y = np.linalg.solve(np.triu(H[:j_done, :j_done]), g[:j_done])
+        for i in range(j_done):
+            x = x + y[i] * Zs[i]
+        r = b - spmv(A, x)
+        rn = float(np.linalg.norm(r))
+    return x, SolveInfo(its, rn / bn if bn > 0 else 0.0, rn <= tol, hist)
+
+
+def solve(Hh, A, b, rtol=1e-10, atol=1e-50, restart=30, maxit=200, x0=None):
+    return fgmres(A, b, lambda v: vcycle(Hh, v), x0=x0, rtol=rtol, atol=atol,
+                  restart=restart, maxit=maxit)
+
+
+# --------------------------------------------------------------------------
+# Complexities (Sec. 3)
+# --------------------------------------------------------------------------
+def complexities(Hh):
+    """Storage complexity: nnz of the matrices kept for the solve over
+    nnz(A_top).  Cycle complexity: flops of one V-cycle over the flops of one
+    top-level SpMV (2 flops per stored entry)."""
+    top = Hh.levels[0].A.nnz if Hh.levels else Hh.A_coarse.nnz
+    store = 0
+    flops = 0
+    for L in Hh.levels:
+        p = len(L.alpha) - 1
+        store += L.A_ff.nnz + L.A_fc.nnz + L.Z.nnz
+        flops += 2 * L.Z.nnz + 2 * L.A_fc.nnz + 2 * L.A_ff.nnz * (p + 1)
+    nr = len(Hh.roots)
+    store += Hh.A_coarse.nnz
+    flops += 2 * Hh.A_coarse.nnz * max(nr - 1, 0)
+    return {"storage": store / top, "cycle": flops / (2.0 * top),
+            "levels": len(Hh.levels) + 1}
+
+
+# --------------------------------------------------------------------------
+# Dense adjoint (for small grids): lambda = A^-T rhs by LU with pivoting
+# --------------------------------------------------------------------------
+def dense_adjoint(A, rhs):
+    return np.linalg.solve(A.to_dense().T, rhs)

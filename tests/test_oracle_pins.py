@@ -1,0 +1,468 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Each test checks one oracle step against a closed form, a brute-force or
+library computation, an invariant the paper states, or a published value, so
+that a dropped term, a wrong sign or index or a transposed operand fails.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import airg as O
+from oracle import lib
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _grid(nx, ny, theta):
+    return O.advection_2d(nx, ny, math.cos(theta), math.sin(theta))
+
+
+# ---------------------------------------------------------------- RNG ----
+def test_splitmix64_published_outputs():
+    vals = [int(l) for l in open(os.path.join(GOLDEN, "splitmix64_1234567.txt"))
+            if l.strip() and not l.startswith("#")]
+    out = np.empty(len(vals))
+    lib().orc_rng_uniform(1234567, len(vals), O._p(out))
+    assert [int(v * 2.0 ** 53) for v in out] == [v >> 11 for v in vals]
+    u32 = np.empty(len(vals), dtype=np.uint32)
+    lib().orc_rng_u32(1234567, len(vals), O._p(u32))
+    assert [int(v) for v in u32] == [v >> 32 for v in vals]
+
+
+def test_rng_streams_distinct_and_uniform():
+    a = O.rng_uniform(7, 0, O.PURPOSE_COEF, 20000)
+    b = O.rng_uniform(7, 1, O.PURPOSE_COEF, 20000)
+    c = O.rng_uniform(7, 0, O.PURPOSE_TRUNC, 20000)
+    assert not np.array_equal(a, b) and not np.array_equal(a, c)
+    assert a.min() >= 0.0 and a.max() < 1.0
+    assert abs(a.mean() - 0.5) < 0.01
+
+
+# ------------------------------------------------------ exact dot product --
+def _exact_dot(x, y):
+    return float(sum((Fraction(float(a)) * Fraction(float(b)) for a, b in zip(x, y)),
+                     Fraction(0)))
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_exact_dot_matches_fractions(case):
+    rng = np.random.default_rng(case)
+    n = [1, 2, 7, 64, 257, 1000, 33, 500][case]
+    x = rng.standard_normal(n) * np.exp2(rng.integers(-60, 60, n))
+    y = rng.standard_normal(n) * np.exp2(rng.integers(-60, 60, n))
+    if case == 6:  # heavy cancellation: sum of products is tiny
+        y = np.concatenate([y[: n // 2], -y[: n // 2] * x[: n // 2] / x[n // 2: 2 * (n // 2)], [1e-30]])
+        x = np.concatenate([x[: 2 * (n // 2)], [1e-30]])
+    assert O.xdot(x, y) == _exact_dot(x, y)
+
+
+def test_exact_dot_subnormal_and_ties():
+    x = np.array([2.0 ** -1074, 2.0 ** -1000, 1.0, 2.0 ** -53])
+    y = np.array([1.0, 2.0 ** -60, 1.0, 1.0])
+    assert O.xdot(x, y) == _exact_dot(x, y)
+    # 1 + 2^-53 is a tie and rounds to even (1.0); adding 2^-1074 breaks the tie upward
+    assert O.xdot(np.array([1.0, 2.0 ** -53]), np.array([1.0, 1.0])) == 1.0
+    assert O.xdot(np.array([1.0, 2.0 ** -53, 2.0 ** -1074]), np.ones(3)) == 1.0 + 2.0 ** -52
+    assert O.xdot(np.zeros(3), np.ones(3)) == 0.0
+
+
+# ------------------------------------------------------- SpMV / SpGEMM ----
+def test_spmv_and_spgemm_against_dense():
+    rng = np.random.default_rng(3)
+    D = rng.standard_normal((30, 20)) * (rng.random((30, 20)) < 0.2)
+    E = rng.standard_normal((20, 25)) * (rng.random((20, 25)) < 0.3)
+
+    def csr(M):
+        r, c = np.nonzero(M)
+        return O.csr_from_entries(M.shape[0], M.shape[1], r, c, M[r, c])
+
+    A, B = csr(D), csr(E)
+    x = rng.standard_normal(20)
+    assert np.allclose(O.spmv(A, x), D @ x, rtol=1e-14, atol=1e-14)
+    C = O.spgemm(A, B)
+    assert np.allclose(C.to_dense(), D @ E, rtol=1e-13, atol=1e-14)
+    # pattern of C is the symbolic product pattern
+    assert set(zip(C.row_ids(), C.col)) == set(zip(*np.nonzero((D != 0).astype(int) @ (E != 0).astype(int))))
+    # integer-valued operands: products and sums are exact
+    Di = np.round(D * 4); Ei = np.round(E * 4)
+    assert np.array_equal(O.spgemm(csr(Di), csr(Ei)).to_dense(), Di @ Ei)
+
+
+# --------------------------------------------- problem builder and sweep ----
+@pytest.mark.parametrize("theta", [3 * math.pi / 8, math.pi / 4, 0.3, 2.0, 3.5, 5.0])
+def test_builder_exact_for_linear_solution(theta):
+    """Upwind differences are exact for u = a x + b y + c: with s = v.grad(u)
+    and g = u on the inflow edges, the discrete solution is u at the nodes."""
+    nx, ny = 17, 11
+    P = _grid(nx, ny, theta)
+    a, bb, c = 0.7, -1.3, 0.25
+    idx = np.arange(nx * ny)
+    X = (idx % nx) * P.h
+    Y = (idx // nx) * P.h
+    u = a * X + bb * Y + c
+    s = np.full(nx * ny, P.vx * a + P.vy * bb)
+    rhs = O.assemble_rhs(P, u[P.inflow], s)
+    sol = O.sweep_solve(P.A, rhs, O.sweep_order(P))
+    assert np.max(np.abs(sol - u)) < 1e-12
+    # and the dense solve agrees
+    assert np.max(np.abs(np.linalg.solve(P.A.to_dense(), rhs) - u)) < 1e-11
+
+
+def test_builder_structure_c1():
+    P = _grid(64, 64, 3 * math.pi / 8)
+    A = P.A
+    assert A.n_rows == 4096 and P.inflow.size == 127        # 2N-1 inflow nodes
+    D = A.to_dense()
+    assert np.allclose(D, np.tril(D))                        # lower triangular (Sec. 1.1)
+    assert np.all(np.diag(D) == abs(P.vx) + abs(P.vy))
+    interior = np.setdiff1d(np.arange(4096), P.inflow)
+    assert np.allclose(D[interior].sum(1), 0.0, atol=1e-15)  # consistent: constants in kernel
+    assert A.nnz == 4096 + 2 * interior.size
+
+
+def test_constant_inflow_gives_constant_solution():
+    """Eq. 1-2 with constant g and zero source: u = g everywhere."""
+    P = _grid(64, 64, 3 * math.pi / 8)
+    b = O.assemble_rhs(P, np.full(P.inflow.size, 1.0), np.zeros(4096))
+    u = O.sweep_solve(P.A, b, O.sweep_order(P))
+    assert np.array_equal(u, np.ones(4096))
+
+
+# ---------------------------------------------------------------- CF split --
+def test_strength_hand_cases():
+    P = _grid(8, 8, 3 * math.pi / 8)     # |vy| = 0.924 > |vx| = 0.383: only y-upwind strong
+    s = O.strength(P.A, 0.99)
+    rid = P.A.row_ids()
+    strong_cols = P.A.col[s] - rid[s]
+    assert np.all(strong_cols == -8)
+    assert s.sum() == 8 * 8 - 15                                  # one per interior row
+    P2 = _grid(8, 8, math.pi / 4)        # equal magnitudes: both neighbours strong
+    s2 = O.strength(P2.A, 0.99)
+    assert s2.sum() == 2 * (64 - 15)
+    assert not np.any(s2[P2.A.col == rid])                       # diagonal never strong
+
+
+def _path_graph(n):
+    r = np.concatenate([np.arange(n - 1), np.arange(1, n)])
+    c = np.concatenate([np.arange(1, n), np.arange(n - 1)])
+    o = np.lexsort((c, r))
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=n), out=rowptr[1:])
+    return rowptr, c[o].astype(np.int64)
+
+
+def test_pmisr_hand_example_path():
+    # path 0-1-2-3-4-5; degrees 1,2,2,2,2,1; weights decide among equal degrees
+    rowptr, col = _path_graph(6)
+    w = np.array([0, 10, 50, 20, 40, 0], dtype=np.uint32)
+    is_f, rounds = O.pmisr(6, rowptr, col, w)
+    # round 1: node 2 (deg 2, w 50) beats 1 and 3; node 4 (w 40) beats 3 and 5 -> F;
+    # neighbours 1, 3, 5 -> C; node 0's only neighbour 1 is C -> round 2 makes 0 F.
+    assert list(np.nonzero(is_f)[0]) == [0, 2, 4]
+    assert rounds == 2
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_pmisr_independent_and_maximal(seed):
+    P = _grid(40, 30, 0.2 + seed)
+    s = O.strength(P.A, 0.5)
+    rp, gc = O.symmetrized_graph(P.A, s)
+    is_f, _ = O.pmisr(P.A.n_rows, rp, gc, O.rng_u32(seed, 0, O.PURPOSE_PMISR, P.A.n_rows))
+    src = np.repeat(np.arange(P.A.n_rows), np.diff(rp))
+    assert not np.any(is_f[src] & is_f[gc])                  # F independent in S+S^T
+    has_f_nb = np.zeros(P.A.n_rows, bool)
+    has_f_nb[src[is_f[gc]]] = True
+    assert np.all(has_f_nb[~is_f])                           # every C has an F neighbour
+    # no large off-diagonal in A_ff: F-F entries are all weak
+    rid = P.A.row_ids()
+    ff = is_f[rid] & is_f[P.A.col] & (rid != P.A.col)
+    assert not np.any(s[ff])
+
+
+def test_symmetrized_graph_is_s_plus_st():
+    P = _grid(9, 7, 0.9)
+    s = O.strength(P.A, 0.6)
+    rp, gc = O.symmetrized_graph(P.A, s)
+    n = P.A.n_rows
+    S = np.zeros((n, n), bool)
+    S[P.A.row_ids()[s], P.A.col[s]] = True
+    G = np.zeros((n, n), bool)
+    G[np.repeat(np.arange(n), np.diff(rp)), gc] = True
+    assert np.array_equal(G, S | S.T)
+
+
+def test_ddc_converts_closest_to_target():
+    # 100 F points with distinct ratios 0.01*i (diagonal 1, one F neighbour)
+    n = 200
+    rows, cols, vals = [], [], []
+    for i in range(100):
+        rows += [i, i]; cols += [i, 100 + i]; vals += [1.0, 0.0]
+    for i in range(100, 200):
+        rows += [i]; cols += [i]; vals += [1.0]
+    A = O.csr_from_entries(n, n, np.array(rows), np.array(cols), np.array(vals))
+    # give F row i the coupling 0.01*(i+1) to F point (i+1)%100 instead
+    rows, cols, vals = [], [], []
+    for i in range(100):
+        j = (i + 1) % 100
+        e = sorted([(i, 1.0), (j, -0.01 * (i + 1))])
+        for c, v in e:
+            rows.append(i); cols.append(c); vals.append(v)
+    for i in range(100, 200):
+        rows.append(i); cols.append(i); vals.append(1.0)
+    A = O.csr_from_entries(n, n, np.array(rows), np.array(cols), np.array(vals))
+    is_f = np.zeros(n, bool); is_f[:100] = True
+    out, nconv = O.ddc_pass(A, is_f, 0.05)
+    assert nconv == 5                                   # ceil(0.05 * 100)
+    assert set(np.nonzero(is_f & ~out)[0]) == {95, 96, 97, 98, 99}  # least dominant
+    # worst case of Sec. 2.1: all ratios equal -> the closest boundary converts none
+    rows, cols, vals = [], [], []
+    for i in range(100):
+        j = (i + 1) % 100
+        for c, v in sorted([(i, 1.0), (j, -0.5)]):
+            rows.append(i); cols.append(c); vals.append(v)
+    A2 = O.csr_from_entries(100, 100, np.array(rows), np.array(cols), np.array(vals))
+    out2, n2 = O.ddc_pass(A2, np.ones(100, bool), 0.01)
+    assert n2 == 0 and out2.all()
+
+
+def test_ddc_ratio_definition():
+    P = _grid(6, 6, 0.7)
+    is_f = np.zeros(36, bool); is_f[::2] = True
+    r = O.ddc_ratio(P.A, is_f)
+    D = P.A.to_dense()
+    for i in range(36):
+        if is_f[i]:
+            off = sum(abs(D[i, j]) for j in range(36) if j != i and is_f[j])
+            assert r[i] == pytest.approx(off / abs(D[i, i]), rel=1e-15)
+        else:
+            assert r[i] == -1.0
+
+
+def test_extract_blocks_reassemble():
+    P = _grid(12, 9, 1.1)
+    rng = np.random.default_rng(5)
+    is_f = rng.random(P.A.n_rows) < 0.5
+    D = P.A.to_dense()
+    f, c = np.nonzero(is_f)[0], np.nonzero(~is_f)[0]
+    assert np.array_equal(O.extract(P.A, is_f, is_f).to_dense(), D[np.ix_(f, f)])
+    assert np.array_equal(O.extract(P.A, is_f, ~is_f).to_dense(), D[np.ix_(f, c)])
+    assert np.array_equal(O.extract(P.A, ~is_f, is_f).to_dense(), D[np.ix_(c, f)])
+    assert np.array_equal(O.extract(P.A, ~is_f, ~is_f).to_dense(), D[np.ix_(c, c)])
+
+
+# ------------------------------------------------------ GMRES polynomials --
+def _diag_dominant(n, seed):
+    rng = np.random.default_rng(seed)
+    D = np.diag(2.0 + rng.random(n))
+    mask = rng.random((n, n)) < 0.15
+    D = D + np.where(mask & ~np.eye(n, dtype=bool), rng.uniform(-0.3, 0.3, (n, n)), 0.0)
+    r, c = np.nonzero(D)
+    return O.csr_from_entries(n, n, r, c, D[r, c]), D
+
+
+@pytest.mark.parametrize("p", [1, 2, 4, 6])
+def test_gmres_coeffs_equal_bruteforce_least_squares(p):
+    """alpha minimises ||b - A q(A) b|| over degree-p polynomials (Eq. 4)."""
+    A, D = _diag_dominant(40, p)
+    opts = O.Options(poly_order=p)
+    alpha, k, broke = O.gmres_poly_coeffs(A, opts, 3)
+    assert k == p + 1 and not broke
+    b = O.rng_uniform(opts.seed, 3, O.PURPOSE_COEF, 40)
+    K = np.stack([np.linalg.matrix_power(D, j) @ b for j in range(p + 1)], axis=1)
+    abf = np.linalg.lstsq(D @ K, b, rcond=None)[0]
+    assert np.allclose(alpha, abf, rtol=1e-8, atol=1e-10)
+    assert np.allclose(K @ alpha, K @ abf, rtol=1e-11, atol=1e-12)
+    # Horner application equals the dense polynomial
+    t = np.random.default_rng(9).standard_normal(40)
+    qd = sum(alpha[j] * np.linalg.matrix_power(D, j) for j in range(p + 1))
+    assert np.allclose(O.horner_apply(A, alpha, t), qd @ t, rtol=1e-13, atol=1e-13)
+
+
+def test_gmres_coeffs_scaled_identity_breakdown():
+    n, d = 30, 2.5
+    A = O.csr_from_entries(n, n, np.arange(n), np.arange(n), np.full(n, d))
+    alpha, k, broke = O.gmres_poly_coeffs(A, O.Options(poly_order=6), 0)
+    assert broke and k == 1
+    assert alpha[0] == pytest.approx(1.0 / d, rel=1e-15) and np.all(alpha[1:] == 0.0)
+
+
+def test_fixed_sparsity_inverse_dense_check():
+    A, D = _diag_dominant(25, 11)
+    alpha = np.array([0.9, -0.4, 0.15, -0.05])
+    Ah = O.fixed_sparsity_inverse(A, alpha)
+    M = D != 0
+    T = D.copy()
+    acc = alpha[0] * np.eye(25) + alpha[1] * D
+    for k in range(2, 4):
+        T = np.where(M, D @ T, 0.0)
+        acc = acc + alpha[k] * T
+    assert np.allclose(Ah.to_dense(), np.where(M, acc, 0.0), rtol=1e-13, atol=1e-15)
+    # a diagonal A_ff is closed under powers: the assembled inverse equals q(A)
+    Dg = O.csr_from_entries(5, 5, np.arange(5), np.arange(5), np.arange(1.0, 6.0))
+    Ahd = O.fixed_sparsity_inverse(Dg, alpha)
+    x = np.arange(1.0, 6.0)
+    assert np.allclose(Ahd.val, alpha[0] + alpha[1] * x + alpha[2] * x ** 2 + alpha[3] * x ** 3)
+
+
+def test_restrictor_block_dense_check():
+    A, D = _diag_dominant(30, 4)
+    f = np.arange(30) % 3 != 0
+    Aff = O.extract(A, f, f); Acf = O.extract(A, ~f, f)
+    alpha = np.array([0.5, -0.1, 0.02])
+    Ah = O.fixed_sparsity_inverse(Aff, alpha)
+    Z = O.restrictor_block(Acf, Ah, 0.05)
+    Zd = -(Acf.to_dense() @ Ah.to_dense())
+    m = np.abs(Zd).max(1, keepdims=True)
+    keep = (Zd != 0) & (np.abs(Zd) >= 0.05 * m)
+    assert np.array_equal(Z.to_dense() != 0, keep)
+    assert np.allclose(Z.to_dense(), np.where(keep, Zd, 0.0), rtol=1e-13, atol=1e-15)
+
+
+def test_one_point_prolongator():
+    P = _grid(10, 10, 3 * math.pi / 8)
+    s = O.strength(P.A, 0.99)
+    rp, gc = O.symmetrized_graph(P.A, s)
+    is_f, _ = O.pmisr(100, rp, gc, O.rng_u32(1, 0, O.PURPOSE_PMISR, 100))
+    W = O.one_point(P.A, s, is_f)
+    c_ids = np.nonzero(~is_f)[0]
+    D = P.A.to_dense()
+    for fi, i in enumerate(np.nonzero(is_f)[0]):
+        cands = [j for j in np.nonzero(D[i])[0] if j != i and not is_f[j]]
+        if not cands:
+            assert W[fi] == -1
+            continue
+        strongc = [j for j in cands if s[P.A.rowptr[i] + list(P.A.col[P.A.rowptr[i]:P.A.rowptr[i + 1]]).index(j)]]
+        pool = strongc or cands
+        best = max(pool, key=lambda j: (abs(D[i, j]), -j))
+        assert c_ids[W[fi]] == best
+    # P = [W; I] with weight 1 preserves constants on rows that have a C neighbour
+
+
+def test_coarse_matrix_is_rap_and_lumping_keeps_row_sums():
+    P = _grid(14, 14, 1.0)
+    opts = O.Options(poly_order=3)
+    strong, is_f, _, _ = O.cf_split(P.A, opts, 0)
+    Aff = O.extract(P.A, is_f, is_f); Acf = O.extract(P.A, ~is_f, is_f)
+    alpha, _, _ = O.gmres_poly_coeffs(Aff, opts, 0)
+    Z = O.restrictor_block(Acf, O.fixed_sparsity_inverse(Aff, alpha), opts.r_drop)
+    W = O.one_point(P.A, strong, is_f)
+    n, nf = P.A.n_rows, int(is_f.sum())
+    f, c = np.nonzero(is_f)[0], np.nonzero(~is_f)[0]
+    R = np.zeros((n - nf, n)); R[:, f] = Z.to_dense(); R[np.arange(n - nf), c] = 1.0
+    Pd = np.zeros((n, n - nf)); Pd[c, np.arange(n - nf)] = 1.0
+    Pd[f[W >= 0], W[W >= 0]] = 1.0
+    RAP = R @ P.A.to_dense() @ Pd
+    Ac0 = O.coarse_matrix(P.A, is_f, Z, W, 0.0, True)         # no dropping
+    assert np.allclose(Ac0.to_dense(), RAP, rtol=1e-12, atol=1e-14)
+    Ac = O.coarse_matrix(P.A, is_f, Z, W, 0.3, True)          # heavy drop with lumping
+    assert Ac.nnz < Ac0.nnz
+    assert np.allclose(Ac.to_dense().sum(1), RAP.sum(1), rtol=1e-12, atol=1e-13)
+    Acn = O.coarse_matrix(P.A, is_f, Z, W, 0.3, False)        # without lumping: diag unchanged
+    assert np.array_equal(np.diag(Acn.to_dense()), np.diag(Ac0.to_dense()))
+
+
+# ------------------------------------------------ coarse Newton polynomial --
+def test_newton_polynomial_full_krylov_is_exact_inverse():
+    A, D = _diag_dominant(24, 8)
+    opts = O.Options()
+    roots, H, k, broke = O.coarse_polynomial(A, opts, 0, 24)
+    b = np.random.default_rng(2).standard_normal(24)
+    x = O.newton_apply(A, roots, b)
+    assert np.linalg.norm(b - D @ x) / np.linalg.norm(b) < 1e-10
+    # harmonic Ritz values of the full Krylov space are the eigenvalues of A
+    # (checked on a small matrix with a separated spectrum, where Arnoldi
+    # keeps its basis orthogonal)
+    n = 8
+    Dm = np.diag(np.arange(1.0, n + 1)) + 0.05 * np.tril(np.ones((n, n)), -1)
+    r, c = np.nonzero(Dm)
+    Am = O.csr_from_entries(n, n, r, c, Dm[r, c])
+    _, Hm, km, brm = O.coarse_polynomial(Am, opts, 0, n)
+    th = np.sort_complex(O.harmonic_ritz(Hm, km, brm))
+    assert km == n
+    assert np.allclose(th, np.arange(1.0, n + 1), atol=1e-6)
+
+
+def test_newton_form_equals_power_form():
+    A, D = _diag_dominant(50, 13)
+    opts = O.Options()
+    b1 = O.rng_uniform(opts.seed, 0, O.PURPOSE_COARSE, 50)
+    H, k, broke, beta = O.arnoldi(A, b1, 5, 1e-8)
+    roots = O.order_roots(O.harmonic_ritz(H, k, broke), opts)
+    alpha = O.power_coefficients(H, beta, O.givens_lsq(H, beta))
+    v = np.random.default_rng(0).standard_normal(50)
+    assert np.allclose(O.newton_apply(A, roots, v), O.horner_apply(A, alpha, v), rtol=1e-9, atol=1e-10)
+    # residual polynomial prod(1 - z/theta) is 1 at z = 0 and q(A) b1 is the GMRES iterate
+    x = O.newton_apply(A, roots, b1)
+    K = np.stack([np.linalg.matrix_power(D, j) @ b1 for j in range(5)], 1)
+    ybf = np.linalg.lstsq(D @ K, b1, rcond=None)[0]
+    assert np.allclose(x, K @ ybf, rtol=1e-8)
+
+
+# ------------------------------------------------------------- V-cycle ----
+def test_grid_aligned_direction_is_exact_solver():
+    """v = (1, 0): uncoupled 1D chains; A_ff diagonal, ideal R, exact
+    F-smoothing: the V-cycle is an exact inverse (Sec. 2 and 3.4)."""
+    P = O.advection_2d(32, 24, 1.0, 0.0)
+    opts = O.Options(trunc_rtol=0.0, coarse_min_rows=40)
+    H = O.setup(P.A, opts)
+    assert len(H.levels) >= 2
+    for L in H.levels:
+        assert np.all(L.A_ff.col == L.A_ff.row_ids())          # diagonal A_ff
+    r = np.random.default_rng(1).standard_normal(P.A.n_rows)
+    e = O.vcycle(H, r)
+    assert np.linalg.norm(r - P.A.to_dense() @ e) / np.linalg.norm(r) < 1e-12
+    b = O.assemble_rhs(P, np.random.default_rng(2).random(P.inflow.size), np.zeros(P.A.n_rows))
+    x, info = O.solve(H, P.A, b)
+    assert info.iterations <= 2 and info.converged
+
+
+def test_c1_constant_solution_and_convergence():
+    P = _grid(64, 64, 3 * math.pi / 8)
+    b = O.assemble_rhs(P, np.ones(P.inflow.size), np.zeros(4096))
+    H = O.setup(P.A, O.Options(poly_order=4, trunc_start_level=2))
+    assert len(H.levels) >= 3
+    x, info = O.solve(H, P.A, b, rtol=1e-10)
+    assert info.converged
+    assert np.linalg.norm(b - P.A.to_dense() @ x) <= 1e-10 * np.linalg.norm(b)
+    assert np.linalg.norm(x - 1.0) / np.linalg.norm(np.ones(4096)) < 1e-9
+    assert info.iterations <= 12
+
+
+def test_solution_matches_sweep_random_inflow_and_source():
+    P = _grid(48, 40, 0.9)
+    rng = np.random.default_rng(4)
+    b = O.assemble_rhs(P, rng.random(P.inflow.size), rng.standard_normal(P.A.n_rows))
+    H = O.setup(P.A, O.Options(trunc_start_level=1))
+    x, info = O.solve(H, P.A, b, rtol=1e-12)
+    u = O.sweep_solve(P.A, b, O.sweep_order(P))
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) < 1e-9
+
+
+def test_truncation_reduces_levels():
+    P = _grid(64, 64, math.pi / 4)
+    full = O.setup(P.A, O.Options(trunc_rtol=0.0, coarse_min_rows=8))
+    trunc = O.setup(P.A, O.Options(trunc_rtol=0.1, coarse_poly_order=30, trunc_start_level=1))
+    assert trunc.truncated and len(trunc.levels) < len(full.levels)
+    assert trunc.coarse_trunc_rel <= 0.1
+    for L in trunc.levels[1:]:
+        assert L.trunc_rel > 0.1                     # levels kept had failed the test
+
+
+def test_complexities_in_paper_range():
+    """Sanity band (not parity): pi/4, order 6 smoother (Sec. 3)."""
+    P = _grid(128, 128, math.pi / 4)
+    H = O.setup(P.A, O.Options(trunc_rtol=0.0, coarse_min_rows=16))
+    cx = O.complexities(H)
+    assert 10 < cx["cycle"] < 60
+    assert 2 < cx["storage"] < 20
+
+
+def test_dense_adjoint():
+    P = _grid(12, 12, 0.5)
+    rhs = np.random.default_rng(0).standard_normal(144)
+    lam = O.dense_adjoint(P.A, rhs)
+    assert np.allclose(P.A.to_dense().T @ lam, rhs, atol=1e-12)
