@@ -1,0 +1,236 @@
+/*
+ * airg.h -- C ABI of the GB300 (sm_103a) AIRG solver.
+ *
+ * AIRG is the reduction multigrid of Dargaville, Smedley-Stevenson, Smith &
+ * Pain, "Solving advection equations with reduction multigrids on GPUs"
+ * (arXiv 2508.17517): approximate ideal restriction built from GMRES
+ * polynomials (Sec. 2.2, Eq. 4-5), one-point prolongation and up F-point
+ * smoothing only (Sec. 2, Eq. 6), a PMISR DDC coarse/fine splitting
+ * (Sec. 2.1), a high-order GMRES polynomial in Newton form as the coarse-grid
+ * solver (Sec. 2.3) on a hierarchy truncated automatically by that
+ * polynomial's quality (Sec. 2.4).  Setup and solve run on the GPU; the
+ * outer iteration is flexible GMRES in FP64.
+ *
+ * Conventions (every entry point):
+ *  - Return an airg_status; never abort, never trap on the device.  The text
+ *    of the last error on the calling thread is airg_last_error().
+ *  - "device" pointers are CUDA global-memory addresses on the current
+ *    device; "host" pointers are ordinary CPU memory.  Each pointer argument
+ *    says which it takes.  Pointers are borrowed for the duration of the call
+ *    only, unless stated otherwise.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    stream-ordered on it and return after the work they launched has
+ *    finished, unless stated otherwise.
+ *  - Index types: row pointers int64, column indices int32; n < 2^31 and
+ *    nnz < 2^31 (AIRG_ERR_ARG otherwise).  Columns strictly ascending per row.
+ */
+#ifndef AIRG_H
+#define AIRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AIRG_OK = 0,
+    AIRG_ERR_ARG = 1,            /* invalid argument or malformed matrix        */
+    AIRG_ERR_CUDA = 2,           /* a CUDA runtime call failed                  */
+    AIRG_ERR_OOM = 3,            /* device or host allocation failed            */
+    AIRG_ERR_BREAKDOWN = 4,      /* zero diagonal / singular polynomial step    */
+    AIRG_ERR_NOT_CONVERGED = 5,  /* maxit reached; x and info are still valid   */
+    AIRG_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up          */
+    AIRG_ERR_STATE = 7           /* handle not in a state that allows the call  */
+} airg_status;
+
+enum { AIRG_FP64 = 0, AIRG_MIXED_FP32 = 1 };
+
+/* Compressed sparse row matrix (n_rows x n_cols).  Caller-owned, read-only. */
+typedef struct {
+    int64_t n_rows, n_cols, nnz;
+    const int64_t* rowptr;   /* n_rows + 1 entries                          */
+    const int32_t* col;      /* nnz entries, ascending within each row      */
+    const double* val;       /* nnz entries                                 */
+    int on_device;           /* 1: the three arrays are device pointers     */
+} airg_csr;
+
+/* Solver options.  airg_options_default() fills the values of the command
+ * line in Sec. 3 of the paper (strong threshold 0.99, DDC fraction 0.01 with
+ * 2 passes, smoother polynomial order 6, coarse polynomial order 100,
+ * truncation tolerance 0.1, A drop 1e-6 with lumping). */
+typedef struct {
+    double strong_threshold;   /* PMISR strength threshold                   */
+    double ddc_fraction;       /* share of F points converted per DDC pass    */
+    int ddc_its;               /* DDC passes                                  */
+    int poly_order;            /* smoother GMRES polynomial degree p          */
+    int coarse_poly_order;     /* Arnoldi steps m_c of the coarse polynomial  */
+    double trunc_rtol;         /* truncation tolerance alpha_trunc; <=0: off  */
+    int trunc_start_level;     /* first level tested for truncation           */
+    int max_levels;            /* hard cap on levels (coarsest included)      */
+    int coarse_min_rows;       /* a level this small is the coarsest          */
+    double a_drop;             /* relative drop tolerance on A_coarse         */
+    int a_lump;                /* 1: add dropped A_coarse entries to diagonal */
+    double r_drop;             /* relative drop tolerance on R                */
+    uint64_t seed;             /* seed of all random streams of the setup     */
+    double breakdown_tol;      /* Arnoldi rank threshold on h_{j+1,j}         */
+    double addroot_log10;      /* extra-root threshold on log10(pof)          */
+    double addroot_per;        /* decades of pof per extra root               */
+    int precision;             /* AIRG_FP64 or AIRG_MIXED_FP32 (V-cycle)      */
+    int gmres_restart;         /* outer FGMRES restart length                 */
+} airg_options;
+
+typedef struct airg_handle_s airg_handle;
+
+typedef struct {
+    int iterations;            /* outer FGMRES iterations (= V-cycles)        */
+    double rel_residual;       /* true ||b - A x||_2 / ||b||_2 at exit        */
+    int converged;             /* 1 if rel_residual test met                  */
+    double solve_ms;           /* wall time of the call                       */
+} airg_solve_info;
+
+typedef struct {
+    int levels;                /* number of levels, coarsest included         */
+    int truncated;             /* 1 if the hierarchy was truncated (Sec. 2.4) */
+    int coarse_roots;          /* Newton roots of the coarse solver           */
+    double cycle_complexity;   /* V-cycle flops / top SpMV flops (Sec. 3)     */
+    double storage_complexity; /* solve-time nnz / nnz(A_top) (Sec. 3)        */
+    double setup_ms;           /* wall time of airg_setup                     */
+    int64_t n[64];             /* unknowns per level                          */
+    int64_t n_f[64];           /* F points per level (0 on the coarsest)      */
+    int64_t nnz_a[64];         /* nnz of the level operator A_l               */
+    int64_t bytes_per_vcycle;  /* algorithmic bytes of one V-cycle            */
+} airg_hierarchy_info;
+
+/* Fills `opt` with the defaults above.  AIRG_ERR_ARG if opt is NULL. */
+airg_status airg_options_default(airg_options* opt);
+
+/*
+ * Upwind finite-difference operator of v.grad(u) = s on an nx-by-ny node grid
+ * with spacing h (Eq. 1-2, Sec. 3).  Nodes (i, j) have index i + nx*j.  Each
+ * equation is multiplied by h (the non-dimensionalisation of Sec. 3):
+ * interior rows d*u_ij - |vx| u_(upwind x) - |vy| u_(upwind y) = h s_ij with
+ * d = |vx| + |vy|; inflow nodes (v.n < 0) keep their unknowns with the row
+ * d*u = d*g (boundary DOFs not eliminated).  Zero velocity components store
+ * no entry.  All pointers are DEVICE pointers, caller-allocated:
+ *   rowptr: n+1, col: 3n, val: 3n, inflow: nx+ny (sorted node indices).
+ * *nnz_out and *n_inflow_out (HOST pointers) receive the counts.
+ */
+airg_status airg_problem_advection2d(int64_t nx, int64_t ny, double vx, double vy, double h,
+                                     int64_t* rowptr, int32_t* col, double* val,
+                                     int64_t* inflow, int64_t* nnz_out,
+                                     int64_t* n_inflow_out, void* stream);
+
+/*
+ * Right-hand sides b = B g + h s for the operator above (Eq. 1-2):
+ * b = d*g on inflow nodes (g ordered as `inflow`), h*s elsewhere.  nrhs
+ * systems stored one after the other (b: nrhs*n, g: nrhs*n_inflow,
+ * s: nrhs*n, s may be NULL for zero source).  DEVICE pointers.
+ */
+airg_status airg_assemble_rhs_advection2d(int64_t nx, int64_t ny, double vx, double vy,
+                                          double h, int nrhs, const int64_t* inflow,
+                                          int64_t n_inflow, const double* g, const double* s,
+                                          double* b, void* stream);
+
+/*
+ * AIRG setup (Sec. 2): the level loop of truncation test (Sec. 2.4), CF
+ * splitting (Sec. 2.1), block extraction, GMRES polynomial coefficients
+ * (Eq. 4), fixed-sparsity inverse (Eq. 5), restrictor with drop, one-point
+ * prolongator, RAP with drop and lumping, then the coarse-grid Newton
+ * polynomial (Sec. 2.3), all on the GPU.  A is copied; the handle owns every
+ * device buffer it allocates.  Setup values are reproducible: sums run in a
+ * fixed order and dot products are correctly rounded.
+ * Errors: AIRG_ERR_ARG (bad sizes, unsorted columns, missing diagonal),
+ * AIRG_ERR_OOM, AIRG_ERR_CUDA, AIRG_ERR_BREAKDOWN.
+ */
+airg_status airg_setup(const airg_csr* A, const airg_options* opt, void* stream,
+                       airg_handle** out);
+
+/*
+ * Solve A x = b with FGMRES(restart) right-preconditioned by one AIRG V-cycle
+ * per iteration (Eq. 6: restriction, coarse Newton polynomial, one-point
+ * prolongation, one up F-point smooth with the matrix-free GMRES
+ * polynomial).  Converged when ||b - A x||_2 <= max(rtol ||b||_2, atol), the
+ * unpreconditioned norm of Sec. 3.  b and x hold nrhs vectors of length n,
+ * one after the other; x is the initial guess on entry and the solution on
+ * exit.  on_device = 1: b and x are DEVICE pointers; 0: HOST pointers (the
+ * copies in and out are part of the call).  info (HOST, may be NULL)
+ * receives the worst iteration count / residual over the right-hand sides.
+ * AIRG_ERR_NOT_CONVERGED still returns x and info.
+ */
+airg_status airg_solve(airg_handle* h, int nrhs, const double* b, double* x, int on_device,
+                       double rtol, double atol, int maxit, airg_solve_info* info,
+                       void* stream);
+
+/*
+ * Adjoint solve A^T lambda = rhs (the reversed-flow operator) with its own
+ * AIRG hierarchy, built on the first call from the transpose of A and kept in
+ * the handle.  Arguments as for airg_solve.
+ */
+airg_status airg_solve_adjoint(airg_handle* h, int nrhs, const double* rhs, double* lambda,
+                               int on_device, double rtol, double atol, int maxit,
+                               airg_solve_info* info, void* stream);
+
+/* Levels, sizes and the complexities of Sec. 3.  info is a HOST pointer. */
+airg_status airg_setup_info(const airg_handle* h, airg_hierarchy_info* info);
+
+/*
+ * Export one setup product of level `level` in the level's own numbering
+ * (points in increasing index, F/C-local indices in increasing index), for
+ * checking against an independent implementation.  `what`:
+ *   0 A_l (the level operator)   1 A_ff   2 A_fc   3 Z (restrictor block, after drop)
+ * Two-call protocol with HOST buffers: pass NULL arrays to get *n_rows,
+ * *n_cols, *nnz; then pass arrays of those sizes.  `what` = 0 on the coarsest
+ * level returns the coarse operator.
+ */
+airg_status airg_export_matrix(const airg_handle* h, int level, int what, int64_t* n_rows,
+                               int64_t* n_cols, int64_t* nnz, int64_t* rowptr, int32_t* col,
+                               double* val);
+
+/*
+ * Export per-level vectors (HOST buffers, two-call protocol as above):
+ *   what 0: CF marker, int8, n entries (1 = F, 0 = C)
+ *   what 1: one-point prolongator W, int32 per F point (C-local index, -1 none)
+ *   what 2: smoother coefficients alpha_0..alpha_p, double
+ *   what 3: coarse Newton roots, double pairs (re, im), im > 0 for a
+ *           conjugate pair, im == 0 for a real root (coarsest level only)
+ *   what 4: per-level scalars, double: [pmisr_rounds, ddc_converted_pass1,
+ *           ddc_converted_pass2.., trunc_rel, alpha_k]
+ * *count receives the number of elements.
+ */
+airg_status airg_export_vector(const airg_handle* h, int level, int what, int64_t* count,
+                               void* out);
+
+/* Releases every device and host buffer of the handle.  NULL is a no-op. */
+void airg_free(airg_handle* h);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* airg_last_error(void);
+
+/*
+ * Building blocks exposed for testing (same contracts as their use inside
+ * the setup):
+ *  airg_dot_exact: <x, y> correctly rounded from the exact sum of exact
+ *    products; x, y DEVICE (length n), result to *out (HOST).
+ *  airg_rng_uniform: uniform [0,1) counter stream (SplitMix64, Steele, Lea &
+ *    Flood 2014) of (seed, level, purpose) into out (DEVICE, length n).
+ *  airg_host_gmres_coeffs: power-basis coefficients alpha (length k, HOST) of
+ *    the GMRES polynomial from an Arnoldi Hessenberg H ((k+1) x k, row-major,
+ *    HOST) and beta = ||b|| (Eq. 4), by Givens least squares; CPU only.
+ *  airg_host_eigvals: eigenvalues (wr, wi; HOST, length n) of a real upper
+ *    Hessenberg matrix (row-major n x n, HOST) by the Francis double-shift QR
+ *    iteration; CPU only.  AIRG_ERR_BREAKDOWN if it does not converge.
+ */
+airg_status airg_dot_exact(int64_t n, const double* x, const double* y, double* out,
+                           void* stream);
+airg_status airg_rng_uniform(uint64_t seed, int64_t level, int64_t purpose, int64_t n,
+                             double* out, void* stream);
+airg_status airg_host_gmres_coeffs(int k, const double* H, double beta, double* alpha);
+airg_status airg_host_eigvals(int n, const double* H, double* wr, double* wi);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AIRG_H */

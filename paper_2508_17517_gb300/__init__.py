@@ -1,0 +1,284 @@
+"""GB300 (sm_103a) AIRG: reduction multigrid with GMRES polynomials for advection.
+
+Python binding of the C ABI declared in ``include/airg.h``: argument
+marshalling only.  Every step of setup and solve runs in the CUDA library
+``_lib/libairg.so`` (built by ``paper_2508_17517_gb300._build.build()``); if
+that library is missing, the binding raises -- there is no CPU fallback.
+Tensors are torch CUDA tensors; the current torch stream is passed to every
+call.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB, build  # noqa: F401
+
+AIRG_OK = 0
+AIRG_ERR_NOT_CONVERGED = 5
+AIRG_FP64 = 0
+AIRG_MIXED_FP32 = 1
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_BREAKDOWN",
+                5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_STATE"}
+
+# symbols declared in include/airg.h
+EXPORTS = ["airg_options_default", "airg_problem_advection2d", "airg_assemble_rhs_advection2d",
+           "airg_setup", "airg_solve", "airg_solve_adjoint", "airg_setup_info",
+           "airg_export_matrix", "airg_export_vector", "airg_free", "airg_last_error",
+           "airg_dot_exact", "airg_rng_uniform", "airg_host_gmres_coeffs", "airg_host_eigvals"]
+
+
+class airg_options(ctypes.Structure):
+    _fields_ = [("strong_threshold", ctypes.c_double), ("ddc_fraction", ctypes.c_double),
+                ("ddc_its", ctypes.c_int), ("poly_order", ctypes.c_int),
+                ("coarse_poly_order", ctypes.c_int), ("trunc_rtol", ctypes.c_double),
+                ("trunc_start_level", ctypes.c_int), ("max_levels", ctypes.c_int),
+                ("coarse_min_rows", ctypes.c_int), ("a_drop", ctypes.c_double),
+                ("a_lump", ctypes.c_int), ("r_drop", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("breakdown_tol", ctypes.c_double), ("addroot_log10", ctypes.c_double),
+                ("addroot_per", ctypes.c_double), ("precision", ctypes.c_int),
+                ("gmres_restart", ctypes.c_int)]
+
+
+class airg_csr(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("on_device", ctypes.c_int)]
+
+
+class airg_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("converged", ctypes.c_int), ("solve_ms", ctypes.c_double)]
+
+
+class airg_hierarchy_info(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("truncated", ctypes.c_int),
+                ("coarse_roots", ctypes.c_int), ("cycle_complexity", ctypes.c_double),
+                ("storage_complexity", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("n", ctypes.c_int64 * 64), ("n_f", ctypes.c_int64 * 64),
+                ("nnz_a", ctypes.c_int64 * 64), ("bytes_per_vcycle", ctypes.c_int64)]
+
+
+class AirgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError("AIRG CUDA library not built (%s); run "
+                               "paper_2508_17517_gb300._build.build()" % LIB)
+        L = ctypes.CDLL(LIB)
+        vp, i64, f64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        sig = {
+            "airg_options_default": [ctypes.POINTER(airg_options)],
+            "airg_problem_advection2d": [i64, i64, f64, f64, f64, vp, vp, vp, vp,
+                                         ctypes.POINTER(i64), ctypes.POINTER(i64), vp],
+            "airg_assemble_rhs_advection2d": [i64, i64, f64, f64, f64, ci, vp, i64, vp, vp, vp, vp],
+            "airg_setup": [ctypes.POINTER(airg_csr), ctypes.POINTER(airg_options), vp,
+                           ctypes.POINTER(vp)],
+            "airg_solve": [vp, ci, vp, vp, ci, f64, f64, ci, ctypes.POINTER(airg_solve_info), vp],
+            "airg_solve_adjoint": [vp, ci, vp, vp, ci, f64, f64, ci,
+                                   ctypes.POINTER(airg_solve_info), vp],
+            "airg_setup_info": [vp, ctypes.POINTER(airg_hierarchy_info)],
+            "airg_export_matrix": [vp, ci, ci, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                   ctypes.POINTER(i64), vp, vp, vp],
+            "airg_export_vector": [vp, ci, ci, ctypes.POINTER(i64), vp],
+            "airg_dot_exact": [i64, vp, vp, ctypes.POINTER(f64), vp],
+            "airg_rng_uniform": [ctypes.c_uint64, i64, i64, i64, vp, vp],
+            "airg_host_gmres_coeffs": [ci, vp, f64, vp],
+            "airg_host_eigvals": [ci, vp, vp, vp],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.airg_free.argtypes = [vp]
+        L.airg_free.restype = None
+        L.airg_last_error.argtypes = []
+        L.airg_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status, allow=()):
+    if status != AIRG_OK and status not in allow:
+        raise AirgError(status, airg_last_error())
+    return status
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def airg_last_error():
+    return lib().airg_last_error().decode()
+
+
+def airg_options_default(**overrides):
+    o = airg_options()
+    _check(lib().airg_options_default(ctypes.byref(o)))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def airg_problem_advection2d(nx, ny, vx, vy, h=None, stream=None):
+    """Device CSR (rowptr int64, col int32, val f64) and inflow node list."""
+    import torch
+    h = 1.0 / (nx - 1) if h is None else h
+    n = nx * ny
+    dev = torch.device("cuda")
+    rowptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(3 * n, dtype=torch.int32, device=dev)
+    val = torch.empty(3 * n, dtype=torch.float64, device=dev)
+    inflow = torch.empty(nx + ny, dtype=torch.int64, device=dev)
+    nnz, nin = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().airg_problem_advection2d(nx, ny, float(vx), float(vy), float(h), _ptr(rowptr),
+                                          _ptr(col), _ptr(val), _ptr(inflow), ctypes.byref(nnz),
+                                          ctypes.byref(nin), _stream(stream)))
+    return {"rowptr": rowptr, "col": col[: nnz.value], "val": val[: nnz.value],
+            "inflow": inflow[: nin.value], "n": n, "nx": nx, "ny": ny, "vx": vx, "vy": vy, "h": h}
+
+
+def airg_assemble_rhs_advection2d(prob, g, s=None, stream=None):
+    import torch
+    nrhs = g.shape[0] if g.dim() == 2 else 1
+    b = torch.empty(nrhs * prob["n"], dtype=torch.float64, device="cuda")
+    g = g.contiguous()
+    sp = _ptr(s.contiguous()) if s is not None else ctypes.c_void_p(0)
+    _check(lib().airg_assemble_rhs_advection2d(prob["nx"], prob["ny"], float(prob["vx"]),
+                                               float(prob["vy"]), float(prob["h"]), nrhs,
+                                               _ptr(prob["inflow"]), prob["inflow"].numel(),
+                                               _ptr(g), sp, _ptr(b), _stream(stream)))
+    return b.view(nrhs, prob["n"]) if nrhs > 1 else b
+
+
+class Handle:
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            airg_free(self)
+
+
+def airg_setup(rowptr, col, val, opts=None, stream=None):
+    """rowptr/col/val: torch tensors (CUDA or CPU) of a square CSR matrix."""
+    on_dev = int(rowptr.is_cuda)
+    A = airg_csr(rowptr.numel() - 1, rowptr.numel() - 1, col.numel(), rowptr.data_ptr(),
+                 col.data_ptr(), val.data_ptr(), on_dev)
+    out = ctypes.c_void_p()
+    o = opts if opts is not None else airg_options_default()
+    _check(lib().airg_setup(ctypes.byref(A), ctypes.byref(o), _stream(stream), ctypes.byref(out)))
+    return Handle(out)
+
+
+def _solve(fn, handle, b, x, rtol, atol, maxit, stream, allow_nc):
+    import torch
+    on_dev = int(b.is_cuda)
+    nrhs = b.shape[0] if b.dim() == 2 else 1
+    if x is None:
+        x = torch.zeros_like(b)
+    info = airg_solve_info()
+    st = fn(handle.ptr, nrhs, _ptr(b), _ptr(x), on_dev, float(rtol), float(atol), int(maxit),
+            ctypes.byref(info), _stream(stream))
+    _check(st, allow=(AIRG_ERR_NOT_CONVERGED,) if allow_nc else ())
+    return x, info
+
+
+def airg_solve(handle, b, x=None, rtol=1e-10, atol=1e-50, maxit=200, stream=None, allow_nc=False):
+    """x (in/out, same device as b) and airg_solve_info."""
+    return _solve(lib().airg_solve, handle, b, x, rtol, atol, maxit, stream, allow_nc)
+
+
+def airg_solve_adjoint(handle, rhs, lam=None, rtol=1e-10, atol=1e-50, maxit=200, stream=None,
+                       allow_nc=False):
+    return _solve(lib().airg_solve_adjoint, handle, rhs, lam, rtol, atol, maxit, stream, allow_nc)
+
+
+def airg_setup_info(handle):
+    info = airg_hierarchy_info()
+    _check(lib().airg_setup_info(handle.ptr, ctypes.byref(info)))
+    L = info.levels
+    return {"levels": L, "truncated": bool(info.truncated), "coarse_roots": info.coarse_roots,
+            "cycle_complexity": info.cycle_complexity,
+            "storage_complexity": info.storage_complexity, "setup_ms": info.setup_ms,
+            "n": list(info.n[:L]), "n_f": list(info.n_f[:L]), "nnz_a": list(info.nnz_a[:L]),
+            "bytes_per_vcycle": info.bytes_per_vcycle}
+
+
+def airg_export_matrix(handle, level, what):
+    """(n_rows, n_cols, rowptr, col, val) as numpy arrays, level numbering."""
+    nr, nc, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    L = lib()
+    _check(L.airg_export_matrix(handle.ptr, level, what, ctypes.byref(nr), ctypes.byref(nc),
+                                ctypes.byref(nnz), None, None, None))
+    rp = np.empty(nr.value + 1, np.int64)
+    ci = np.empty(max(nnz.value, 1), np.int32)
+    v = np.empty(max(nnz.value, 1), np.float64)
+    _check(L.airg_export_matrix(handle.ptr, level, what, ctypes.byref(nr), ctypes.byref(nc),
+                                ctypes.byref(nnz), rp.ctypes.data, ci.ctypes.data, v.ctypes.data))
+    return nr.value, nc.value, rp, ci[: nnz.value], v[: nnz.value]
+
+
+_VEC_DTYPES = {0: np.int8, 1: np.int32, 2: np.float64, 3: np.float64, 4: np.float64}
+
+
+def airg_export_vector(handle, level, what):
+    cnt = ctypes.c_int64()
+    L = lib()
+    _check(L.airg_export_vector(handle.ptr, level, what, ctypes.byref(cnt), None))
+    out = np.empty(max(cnt.value, 1), _VEC_DTYPES[what])
+    _check(L.airg_export_vector(handle.ptr, level, what, ctypes.byref(cnt), out.ctypes.data))
+    return out[: cnt.value]
+
+
+def airg_free(handle):
+    if handle.ptr:
+        lib().airg_free(handle.ptr)
+        handle.ptr = None
+
+
+def airg_dot_exact(x, y, stream=None):
+    out = ctypes.c_double()
+    _check(lib().airg_dot_exact(x.numel(), _ptr(x), _ptr(y), ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def airg_rng_uniform(seed, level, purpose, n, stream=None):
+    import torch
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    _check(lib().airg_rng_uniform(seed, level, purpose, n, _ptr(out), _stream(stream)))
+    return out
+
+
+def airg_host_gmres_coeffs(H, beta):
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    k = H.shape[1]
+    alpha = np.empty(k)
+    _check(lib().airg_host_gmres_coeffs(k, H.ctypes.data, float(beta), alpha.ctypes.data))
+    return alpha
+
+
+def airg_host_eigvals(H):
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    n = H.shape[0]
+    wr, wi = np.empty(n), np.empty(n)
+    _check(lib().airg_host_eigvals(n, H.ctypes.data, wr.ctypes.data, wi.ctypes.data))
+    return wr + 1j * wi

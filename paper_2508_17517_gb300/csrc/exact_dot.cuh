@@ -1,0 +1,163 @@
+// Correctly rounded dot product on the GPU.
+//
+// <x, y> is defined as the exact sum of the exact products x_i * y_i,
+// rounded once to the nearest double (ties to even).  That value does not
+// depend on the order of summation, so it is the same however the grid is
+// shaped and equals any other correct implementation bit for bit; the setup
+// uses it for every Arnoldi inner product and norm (Sec. 2.2-2.4) so that
+// the polynomial coefficients, and from them every sparsity decision of the
+// hierarchy, are reproducible.
+//
+// A finite double is m * 2^e with an integer m < 2^53 and e >= -1074, so the
+// product of two is an integer below 2^106 (two 64-bit halves from
+// __umul64hi / mul) times 2^(ex+ey), ex+ey >= -2148.  The accumulator is a
+// signed fixed-point integer with least significant bit 2^-2148 stored as
+// 140 digits of 32 bits, each digit held in a 64-bit word so that many
+// deposits can wait for one carry pass: a product touches at most 5 digits.
+// Warps deposit into shared-memory accumulators with 64-bit atomics
+// (two's-complement wrap-around makes signed addition exact), blocks add
+// theirs into a global accumulator, and one thread propagates carries and
+// rounds.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace airg {
+
+constexpr int XD_DIGITS = 140;   // 140 * 32 = 4480 bits >= 2148 + 2046 + 2
+constexpr int XD_BIAS = 2148;    // digit-bit position of 2^0
+constexpr int XD_WARPS = 8;      // warps (shared accumulators) per block
+constexpr int XD_THREADS = XD_WARPS * 32;
+
+__device__ __forceinline__ bool xd_split(double x, unsigned long long& m, int& e, int& neg)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    neg = int(b >> 63);
+    int ex = int((b >> 52) & 0x7ffULL);
+    unsigned long long fr = b & ((1ULL << 52) - 1ULL);
+    if (ex == 0) { m = fr; e = -1074; }
+    else { m = fr | (1ULL << 52); e = ex - 1075; }
+    return m != 0ULL;
+}
+
+// Adds +-(hi:lo) * 2^(pos) to the digits (pos >= 0 in accumulator bits).
+__device__ __forceinline__ void xd_deposit(unsigned long long* acc, unsigned long long hi,
+                                           unsigned long long lo, int pos, int neg)
+{
+    int d = pos >> 5;
+    int sh = pos & 31;
+    // 160-bit value (w2:w1:w0 as 64-bit words) = (hi:lo) << sh
+    unsigned long long w0 = lo << sh;
+    unsigned long long w1 = sh ? ((hi << sh) | (lo >> (64 - sh))) : hi;
+    unsigned long long w2 = sh ? (hi >> (64 - sh)) : 0ULL;
+    unsigned long long piece[5] = {w0 & 0xffffffffULL, w0 >> 32, w1 & 0xffffffffULL, w1 >> 32,
+                                   w2 & 0xffffffffULL};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        if (piece[k]) atomicAdd(acc + d + k, neg ? (0ULL - piece[k]) : piece[k]);
+    }
+}
+
+__device__ __forceinline__ void xd_add_product(unsigned long long* acc, double x, double y,
+                                               int* bad)
+{
+    unsigned long long mx, my;
+    int ex, ey, nx, ny;
+    bool zx = !xd_split(x, mx, ex, nx);
+    bool zy = !xd_split(y, my, ey, ny);
+    if (!isfinite(x) || !isfinite(y)) { *bad = 1; return; }
+    if (zx || zy) return;
+    unsigned long long lo = mx * my;
+    unsigned long long hi = __umul64hi(mx, my);
+    xd_deposit(acc, hi, lo, ex + ey + XD_BIAS, nx ^ ny);
+}
+
+// Block: XD_THREADS threads.  gacc: XD_DIGITS words, zero on entry of the
+// first block (cleared by the caller).  bad: set when an input is inf/nan.
+__global__ void __launch_bounds__(XD_THREADS)
+k_xdot_accumulate(long long n, const double* __restrict__ x, const double* __restrict__ y,
+                  unsigned long long* __restrict__ gacc, int* bad)
+{
+    __shared__ unsigned long long sacc[XD_WARPS][XD_DIGITS];
+    for (int t = threadIdx.x; t < XD_WARPS * XD_DIGITS; t += blockDim.x)
+        (&sacc[0][0])[t] = 0ULL;
+    __syncthreads();
+    unsigned long long* mine = sacc[threadIdx.x >> 5];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        xd_add_product(mine, x[i], y[i], bad);
+    __syncthreads();
+    for (int t = threadIdx.x; t < XD_DIGITS; t += blockDim.x) {
+        unsigned long long s = 0ULL;
+#pragma unroll
+        for (int w = 0; w < XD_WARPS; ++w) s += sacc[w][t];
+        if (s) atomicAdd(gacc + t, s);
+    }
+}
+
+// One thread: carry propagation and round-to-nearest-even of the global
+// accumulator.  Writes the double to *out, optionally its square root to
+// *out_sqrt, and clears the accumulator for the next use.
+__device__ inline double xd_round(unsigned long long* g)
+{
+    long long* d = reinterpret_cast<long long*>(g);
+    long long carry = 0;
+    for (int i = 0; i < XD_DIGITS - 1; ++i) {
+        long long v = d[i] + carry;
+        long long lo = v & 0xffffffffLL;
+        d[i] = lo;
+        carry = (v - lo) >> 32;   // v - lo is a multiple of 2^32
+    }
+    d[XD_DIGITS - 1] += carry;
+    int neg = 0;
+    if (d[XD_DIGITS - 1] < 0) {
+        neg = 1;
+        carry = 0;
+        for (int i = 0; i < XD_DIGITS; ++i) d[i] = -d[i];
+        for (int i = 0; i < XD_DIGITS - 1; ++i) {
+            long long v = d[i] + carry;
+            long long lo = v & 0xffffffffLL;
+            d[i] = lo;
+            carry = (v - lo) >> 32;
+        }
+        d[XD_DIGITS - 1] += carry;
+    }
+    int top = -1;
+    for (int i = XD_DIGITS - 1; i >= 0; --i)
+        if (d[i] != 0) { top = i; break; }
+    double r = 0.0;
+    if (top >= 0) {
+        int hb = 63 - __clzll(d[top]);
+        int P = top * 32 + hb;                 // most significant bit
+        int lsb = P - 52;                      // last bit kept
+        if (lsb < XD_BIAS - 1074) lsb = XD_BIAS - 1074;
+        unsigned long long M = 0ULL;
+        for (int b = P; b >= lsb; --b) M = (M << 1) | (unsigned long long)((d[b >> 5] >> (b & 31)) & 1);
+        int rb = (lsb - 1 >= 0) ? int((d[(lsb - 1) >> 5] >> ((lsb - 1) & 31)) & 1) : 0;
+        int sticky = 0;
+        int lim = lsb - 1;                     // bits [0, lim) are sticky bits
+        for (int w = 0; w < (lim >> 5) && !sticky; ++w) sticky = d[w] != 0;
+        if (!sticky && lim > 0 && (lim & 31)) {
+            long long mask = (1LL << (lim & 31)) - 1;
+            sticky = (d[lim >> 5] & mask) != 0;
+        }
+        if (rb && (sticky || (M & 1ULL))) M += 1ULL;
+        r = scalbn((double)M, lsb - XD_BIAS);
+    }
+    for (int i = 0; i < XD_DIGITS; ++i) d[i] = 0;
+    return neg ? -r : r;
+}
+
+__global__ void k_xdot_finalize(unsigned long long* gacc, const int* bad, double* out,
+                                double* out_sqrt)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double r = xd_round(gacc);
+    if (*bad) r = __longlong_as_double(0x7ff8000000000000LL);
+    if (out) *out = r;
+    if (out_sqrt) *out_sqrt = __dsqrt_rn(r);
+}
+
+}  // namespace airg

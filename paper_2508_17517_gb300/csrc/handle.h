@@ -1,0 +1,69 @@
+// The AIRG hierarchy object behind airg_handle: setup products in each
+// level's own numbering (kept for export and checking) and the solve-phase
+// operators in the nested F/C layout (see solve.cu).
+#pragma once
+
+#include <cmath>
+#include <memory>
+#include <vector>
+
+#include "dev_util.cuh"
+#include "hostmath.h"
+
+namespace airg {
+
+// Setup products of one non-coarsest level, in the level's numbering.
+struct SetupLevel {
+    int n = 0, n_f = 0, n_c = 0;
+    DevCSR A;                 // level operator A_l
+    DBuf<int8_t> strong;      // per stored entry of A_l
+    DBuf<int8_t> is_f;        // per row: 1 = F point
+    DBuf<int> f_index, c_index;   // F-/C-local index of each row, -1 otherwise
+    DBuf<int> f_ids, c_ids;       // row of each F / C point
+    DevCSR A_ff, A_fc, Z;     // blocks of Eq. 3; Z = -A_cf Ahat_ff^-1 after drop
+    DevCSR M;                 // rows of A P at the F points = A_fc + A_ff W
+    DBuf<int> W;              // one-point prolongator: C-local index or -1
+    std::vector<double> alpha;    // p+1 smoother coefficients (zero-padded)
+    int alpha_k = 0;              // Krylov dimension reached (p+1 unless breakdown)
+    int pmisr_rounds = 0;
+    std::vector<int> ddc_converted;
+    double trunc_rel = NAN;
+};
+
+struct CoarseLevel {
+    DevCSR A;
+    std::vector<Root> roots;
+    int k = 0;
+    double trunc_rel = NAN;
+    bool truncated = false;
+};
+
+struct SolveData;   // solve.cu
+
+struct Hierarchy {
+    airg_options opt{};
+    std::vector<std::unique_ptr<SetupLevel>> levels;
+    CoarseLevel coarse;
+    double setup_ms = 0.0;
+    std::unique_ptr<SolveData> solve;
+    Hierarchy();
+    ~Hierarchy();
+};
+
+// setup.cu
+std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& opt,
+                                           cudaStream_t st);
+void dot_exact_device(long long n, const double* x, const double* y, double* out,
+                      double* out_sqrt, cudaStream_t st);
+void rng_uniform_device(uint64_t seed, long long level, long long purpose, long long n,
+                        double* out, cudaStream_t st);
+void csr_transpose(const DevCSR& A, DevCSR& T, cudaStream_t st);
+void validate_csr(const DevCSR& A, bool square, cudaStream_t st);
+
+// solve.cu
+void build_solve_data(Hierarchy& H, cudaStream_t st);
+void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_device,
+                  double rtol, double atol, int maxit, airg_solve_info* info, cudaStream_t st);
+void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info);
+
+}  // namespace airg

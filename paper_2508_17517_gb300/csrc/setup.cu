@@ -1,0 +1,1252 @@
+// AIRG setup on the GPU (Sec. 2 of arXiv 2508.17517), level by level:
+//   truncation test (Sec. 2.4) -> strength + S+S^T -> PMISR -> DDC (Sec. 2.1)
+//   -> block extraction (Eq. 3) -> GMRES polynomial coefficients (Eq. 4)
+//   -> fixed-sparsity inverse (Eq. 5) -> Z = -A_cf Ahat^-1 with R drop
+//   -> one-point W -> A_coarse = R A P with drop + lumping
+// and finally the coarse-grid Newton polynomial (Sec. 2.3).
+//
+// Reproducibility: every value that feeds a discrete decision (strength,
+// DDC bins, drops, one-point choice, truncation) is computed with a fixed
+// operation order: row sums run left to right in column order from +0.0
+// with explicitly rounded products (__dmul_rn/__dadd_rn, no FMA), sparse
+// products accumulate each entry in ascending inner index, and dot products
+// are correctly rounded (exact_dot.cuh).  The results are therefore the
+// bits of the sequential definitions, whatever the launch shape.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "dev_util.cuh"
+#include "exact_dot.cuh"
+#include "handle.h"
+#include "hostmath.h"
+
+namespace airg {
+
+namespace {
+
+constexpr int TB = 256;
+enum { PURPOSE_COEF = 1, PURPOSE_PMISR = 2, PURPOSE_COARSE = 3, PURPOSE_TRUNC = 4 };
+
+// ------------------------------------------------------------- prefix sum --
+constexpr int SCAN_B = 1024;
+
+__global__ void k_scan_block(const int* in, int* out, int* sums, int n)
+{
+    __shared__ int wsum[32];
+    int i = blockIdx.x * SCAN_B + threadIdx.x;
+    int v = i < n ? in[i] : 0;
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        wsum[lane] = s;
+    }
+    __syncthreads();
+    int incl = x + (w > 0 ? wsum[w - 1] : 0);
+    if (i < n) out[i] = incl - v;
+    if (threadIdx.x == SCAN_B - 1) sums[blockIdx.x] = incl;
+}
+
+// single block: exclusive scan of the block sums, in chunks
+__global__ void k_scan_sums(int* sums, int nb, int* total)
+{
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < nb; base += SCAN_B) {
+        int i = base + threadIdx.x;
+        int v = i < nb ? sums[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int s = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;
+        }
+        __syncthreads();
+        int incl = x + (w > 0 ? wsum[w - 1] : 0);
+        int c = carry;
+        if (i < nb) sums[i] = c + incl - v;
+        __syncthreads();
+        if (threadIdx.x == SCAN_B - 1) carry = c + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int* out, const int* sums, int n, const int* total)
+{
+    int i = blockIdx.x * SCAN_B + threadIdx.x;
+    if (i < n) out[i] += sums[blockIdx.x];
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = *total;
+}
+
+}  // namespace
+
+void exclusive_scan_async(const int* in, int* out, int n, cudaStream_t st)
+{
+    int nb = std::max(1, (n + SCAN_B - 1) / SCAN_B);
+    DBuf<int> sums(size_t(nb) + 1);
+    k_scan_block<<<nb, SCAN_B, 0, st>>>(in, out, sums.p, n);
+    k_scan_sums<<<1, SCAN_B, 0, st>>>(sums.p, nb, sums.p + nb);
+    k_scan_add<<<nb, SCAN_B, 0, st>>>(out, sums.p, n, sums.p + nb);
+    CK_LAUNCH();
+    CK(cudaStreamSynchronize(st));   // sums is released on return
+}
+
+int exclusive_scan(const int* in, int* out, int n, cudaStream_t st)
+{
+    exclusive_scan_async(in, out, n, st);
+    return read1(out + n, st);
+}
+
+namespace {
+
+// ---------------------------------------------------------- random streams --
+__device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z)
+{
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+constexpr unsigned long long SM64_GAMMA = 0x9e3779b97f4a7c15ULL;
+
+inline unsigned long long host_mix(unsigned long long z)
+{
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+inline unsigned long long stream_key(unsigned long long seed, long long level, long long purpose)
+{
+    unsigned long long tag = ((unsigned long long)level << 8) | (unsigned long long)purpose;
+    return host_mix(seed + SM64_GAMMA * (tag + 1ULL));
+}
+
+__global__ void k_rng_uniform(unsigned long long key, long long n, double* out)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long z = sm64_mix(key + SM64_GAMMA * (unsigned long long)(i + 1));
+    out[i] = (double)(z >> 11) * 0x1.0p-53;
+}
+
+__global__ void k_rng_u32(unsigned long long key, long long n, unsigned* out)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned long long z = sm64_mix(key + SM64_GAMMA * (unsigned long long)(i + 1));
+    out[i] = (unsigned)(z >> 32);
+}
+
+// ------------------------------------------------------------- validation --
+__global__ void k_validate(int n_rows, int n_cols, const int* rp, const int* ci, int square,
+                           int* flags)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_rows) return;
+    int prev = -1;
+    bool diag = false;
+    if (rp[i + 1] < rp[i]) flags[0] = 1;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        int j = ci[k];
+        if (j <= prev || j < 0 || j >= n_cols) flags[0] = 1;
+        prev = j;
+        if (j == i) diag = true;
+    }
+    if (square && !diag) flags[1] = 1;
+}
+
+// ------------------------------------------------------- strength / graph --
+__global__ void k_strength(int n, const int* rp, const int* ci, const double* v, double theta,
+                           int8_t* s)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double m = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+        if (ci[k] != i && fabs(v[k]) > m) m = fabs(v[k]);
+    double thr = __dmul_rn(theta, m);
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+        s[k] = (int8_t)(ci[k] != i && m > 0.0 && fabs(v[k]) >= thr);
+}
+
+__global__ void k_count_strong_t(int n, const int* rp, const int* ci, const int8_t* s, int* cnt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+        if (s[k]) atomicAdd(cnt + ci[k], 1);
+}
+
+__global__ void k_fill_strong_t(int n, const int* rp, const int* ci, const int8_t* s,
+                                const int* rpt, int* cursor, int* ct)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+        if (s[k]) {
+            int j = ci[k];
+            ct[rpt[j] + atomicAdd(cursor + j, 1)] = i;
+        }
+}
+
+// insertion sort of each row's column list (rows are short)
+__global__ void k_sort_rows(int n, const int* rp, int* c)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int a = rp[i] + 1; a < rp[i + 1]; ++a) {
+        int key = c[a], b = a - 1;
+        while (b >= rp[i] && c[b] > key) { c[b + 1] = c[b]; --b; }
+        c[b + 1] = key;
+    }
+}
+
+// sort each row's (col, val) pairs by column
+__global__ void k_sort_rows_kv(int n, const int* rp, int* c, double* v)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int a = rp[i] + 1; a < rp[i + 1]; ++a) {
+        int key = c[a];
+        double val = v[a];
+        int b = a - 1;
+        while (b >= rp[i] && c[b] > key) { c[b + 1] = c[b]; v[b + 1] = v[b]; --b; }
+        c[b + 1] = key;
+        v[b + 1] = val;
+    }
+}
+
+// row i of S + S^T: merge of the strong columns of row i and the sorted
+// row i of S^T, without duplicates
+__global__ void k_union(int n, const int* rp, const int* ci, const int8_t* s, const int* rpt,
+                        const int* ct, const int* rpg, int* cg, int* cnt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int a = rp[i], ae = rp[i + 1], b = rpt[i], be = rpt[i + 1];
+    int c = 0, o = rpg ? rpg[i] : 0;
+    while (true) {
+        while (a < ae && !s[a]) ++a;
+        if (a >= ae && b >= be) break;
+        int ja = a < ae ? ci[a] : 0x7fffffff;
+        int jb = b < be ? ct[b] : 0x7fffffff;
+        int j = ja < jb ? ja : jb;
+        if (ja == j) ++a;
+        if (jb == j) ++b;
+        if (cg) cg[o + c] = j;
+        ++c;
+    }
+    if (cnt) cnt[i] = c;
+}
+
+// ------------------------------------------------------------------ PMISR --
+__device__ __forceinline__ bool key_beats(int dj, unsigned wj, int j, int di, unsigned wi, int i)
+{
+    if (dj != di) return dj > di;
+    if (wj != wi) return wj > wi;
+    return j > i;
+}
+
+__global__ void k_pmisr_select(int n, const int* rpg, const int* cg, const unsigned* w,
+                               const int8_t* state, int8_t* newf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (state[i] != 0) { newf[i] = 0; return; }
+    int di = rpg[i + 1] - rpg[i];
+    int8_t sel = 1;
+    for (int k = rpg[i]; k < rpg[i + 1]; ++k) {
+        int j = cg[k];
+        if (state[j] == 0 && key_beats(rpg[j + 1] - rpg[j], w[j], j, di, w[i], i)) { sel = 0; break; }
+    }
+    newf[i] = sel;
+}
+
+__global__ void k_pmisr_update(int n, const int* rpg, const int* cg, int8_t* state,
+                               const int8_t* newf, int* undecided)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || state[i] != 0) return;
+    if (newf[i]) { state[i] = 1; return; }
+    for (int k = rpg[i]; k < rpg[i + 1]; ++k)
+        if (newf[cg[k]]) { state[i] = 2; return; }
+    atomicAdd(undecided, 1);
+}
+
+__global__ void k_state_to_f(int n, const int8_t* state, int8_t* is_f)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) is_f[i] = state[i] == 1;
+}
+
+// -------------------------------------------------------------------- DDC --
+__global__ void k_ddc_ratio(int n, const int* rp, const int* ci, const double* v,
+                            const int8_t* is_f, double* ratio, unsigned long long* rmax_bits)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (!is_f[i]) { ratio[i] = -1.0; return; }
+    double s = 0.0, d = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        int j = ci[k];
+        if (j == i) d = fabs(v[k]);
+        else if (is_f[j]) s = __dadd_rn(s, fabs(v[k]));
+    }
+    double r = d > 0.0 ? __ddiv_rn(s, d) : __longlong_as_double(0x7ff0000000000000LL);
+    ratio[i] = r;
+    atomicMax(rmax_bits, (unsigned long long)__double_as_longlong(r));   // r >= 0
+}
+
+__global__ void k_ddc_bin(int n, const int8_t* is_f, const double* ratio, double rmax, int nbins,
+                          int* bins, int* hist)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !is_f[i]) return;
+    double t = __dmul_rn(__ddiv_rn(ratio[i], rmax), (double)nbins);
+    int b = (int)floor(t);
+    if (b > nbins - 1) b = nbins - 1;
+    bins[i] = b;
+    atomicAdd(hist + b, 1);
+}
+
+__global__ void k_ddc_convert(int n, int8_t* is_f, const int* bins, int B)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && is_f[i] && bins[i] >= B) is_f[i] = 0;
+}
+
+// ----------------------------------------------------------- local indices --
+__global__ void k_flag_eq(int n, const int8_t* is_f, int want, int* flag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flag[i] = (is_f[i] == want);
+}
+
+__global__ void k_local_index(int n, const int8_t* is_f, int want, const int* excl, int* idx,
+                              int* ids)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (is_f[i] == want) { idx[i] = excl[i]; ids[excl[i]] = i; }
+    else idx[i] = -1;
+}
+
+// --------------------------------------------------------------- extract --
+// rows: list of source rows (nullptr = identity); colmap: new column of each
+// source column or -1 to drop (nullptr = keep all, same index)
+__global__ void k_sub_count(int nr, const int* rows, const int* rp, const int* ci,
+                            const int* colmap, int* cnt)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    int i = rows ? rows[r] : r;
+    int c = 0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+        if (!colmap || colmap[ci[k]] >= 0) ++c;
+    cnt[r] = c;
+}
+
+__global__ void k_sub_fill(int nr, const int* rows, const int* rp, const int* ci, const double* v,
+                           const int* colmap, const int* orp, int* oci, double* ov)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nr) return;
+    int i = rows ? rows[r] : r;
+    int o = orp[r];
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        int j = colmap ? colmap[ci[k]] : ci[k];
+        if (j >= 0) { oci[o] = j; ov[o] = v[k]; ++o; }
+    }
+}
+
+// -------------------------------------------------------- Arnoldi pieces --
+__global__ void k_spmv_det(int n, const int* rp, const int* ci, const double* v,
+                           const double* x, double* y)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) s = __dadd_rn(s, __dmul_rn(v[k], x[ci[k]]));
+    y[i] = s;
+}
+
+__global__ void k_axpy_dev(long long n, double* w, const double* vi, const double* h)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double hh = *h;
+    w[i] = __dsub_rn(w[i], __dmul_rn(hh, vi[i]));
+}
+
+__global__ void k_div_dev(long long n, double* out, const double* w, const double* h)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = __ddiv_rn(w[i], *h);
+}
+
+__global__ void k_sub(long long n, const double* a, const double* b, double* out)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __dsub_rn(a[i], b[i]);
+}
+
+__global__ void k_newton_real_x(long long n, double* x, const double* r, double a)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = __dadd_rn(x[i], __ddiv_rn(r[i], a));
+}
+
+__global__ void k_newton_r(long long n, double* r, const double* w, double a)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = __dsub_rn(r[i], __ddiv_rn(w[i], a));
+}
+
+__global__ void k_newton_pair(long long n, double* x, const double* r, const double* w,
+                              double* t, double a2, double mod2)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double tt = __dsub_rn(__dmul_rn(a2, r[i]), w[i]);
+    t[i] = tt;
+    x[i] = __dadd_rn(x[i], __ddiv_rn(tt, mod2));
+}
+
+// --------------------------------------------------- fixed-sparsity powers --
+__global__ void k_fsp_init(int n, const int* rp, const int* ci, double a0, double* acc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) acc[k] = ci[k] == i ? a0 : 0.0;
+}
+
+__device__ __forceinline__ int find_col(const int* ci, int lo, int hi, int j)
+{
+    while (lo < hi) {
+        int mid = lo + ((hi - lo) >> 1);
+        if (ci[mid] < j) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_fsp_power(int n, const int* rp, const int* ci, const double* a,
+                            const double* tprev, double* tout)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int q = rp[i]; q < rp[i + 1]; ++q) {
+        int j = ci[q];
+        double s = 0.0;
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
+            int l = ci[p];
+            int r = find_col(ci, rp[l], rp[l + 1], j);
+            if (r < rp[l + 1] && ci[r] == j) s = __dadd_rn(s, __dmul_rn(a[p], tprev[r]));
+        }
+        tout[q] = s;
+    }
+}
+
+__global__ void k_fsp_acc(int nnz, double* acc, const double* T, double ak)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nnz) acc[k] = __dadd_rn(acc[k], __dmul_rn(ak, T[k]));
+}
+
+__global__ void k_scale(int nnz, double* v, double s)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nnz) v[k] = v[k] * s;
+}
+
+// -------------------------------------------------------------- SpGEMM ----
+// C = A B.  Each row of C is built by one thread in a private open-addressing
+// table: contributions arrive in ascending order of A's column (the inner
+// index), so every entry is the left-to-right sum of the definition.
+__global__ void k_gemm_bound(int m, const int* arp, const int* aci, const int* brp, int* tsize)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    long long b = 0;
+    for (int p = arp[i]; p < arp[i + 1]; ++p) b += brp[aci[p] + 1] - brp[aci[p]];
+    int sz = 0;
+    if (b > 0) {
+        sz = 1;
+        while (sz < 2 * b) sz <<= 1;
+    }
+    tsize[i] = sz;
+}
+
+__device__ __forceinline__ unsigned hash_col(int j) { return (unsigned)j * 2654435761u; }
+
+__global__ void k_gemm_hash(int m, const int* arp, const int* aci, const double* av,
+                            const int* brp, const int* bci, const double* bv, const int* toff,
+                            int* keys, double* vals, int* cnt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int base = toff[i], size = toff[i + 1] - base;
+    int c = 0;
+    if (size > 0) {
+        unsigned mask = (unsigned)size - 1u;
+        for (int p = arp[i]; p < arp[i + 1]; ++p) {
+            int l = aci[p];
+            double a = av[p];
+            for (int q = brp[l]; q < brp[l + 1]; ++q) {
+                int j = bci[q];
+                double prod = __dmul_rn(a, bv[q]);
+                unsigned h = hash_col(j) & mask;
+                while (true) {
+                    int key = keys[base + h];
+                    if (key == j) { vals[base + h] = __dadd_rn(vals[base + h], prod); break; }
+                    if (key == -1) {
+                        keys[base + h] = j;
+                        vals[base + h] = __dadd_rn(0.0, prod);
+                        ++c;
+                        break;
+                    }
+                    h = (h + 1u) & mask;
+                }
+            }
+        }
+    }
+    cnt[i] = c;
+}
+
+__global__ void k_gemm_emit(int m, const int* toff, const int* keys, const double* vals,
+                            const int* crp, int* cci, double* cv)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int o = crp[i], s = crp[i];
+    for (int t = toff[i]; t < toff[i + 1]; ++t) {
+        int j = keys[t];
+        if (j < 0) continue;
+        double v = vals[t];
+        int b = o - 1;
+        while (b >= s && cci[b] > j) { cci[b + 1] = cci[b]; cv[b + 1] = cv[b]; --b; }
+        cci[b + 1] = j;
+        cv[b + 1] = v;
+        ++o;
+    }
+}
+
+// ------------------------------------------------------------ drop rules --
+__global__ void k_drop_rows(int n, const int* rp, const double* v, double tol, int8_t* keep,
+                            int* cnt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double m = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+        if (fabs(v[k]) > m) m = fabs(v[k]);
+    double thr = __dmul_rn(tol, m);
+    int c = 0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        int8_t kp = (int8_t)(v[k] != 0.0 && fabs(v[k]) >= thr);
+        keep[k] = kp;
+        c += kp;
+    }
+    cnt[i] = c;
+}
+
+__global__ void k_drop_lump(int n, const int* rp, const int* ci, const double* v, double tol,
+                            int lump, int8_t* keep, double* vout, int* cnt, int* bad)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double m = 0.0;
+    int dpos = -1;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        if (ci[k] == i) dpos = k;
+        else if (fabs(v[k]) > m) m = fabs(v[k]);
+    }
+    if (dpos < 0) { *bad = 1; cnt[i] = 0; return; }
+    double thr = __dmul_rn(tol, m);
+    double d = v[dpos];
+    int c = 0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        vout[k] = v[k];
+        if (k == dpos) { keep[k] = 1; ++c; continue; }
+        if (v[k] == 0.0 || fabs(v[k]) < thr) {
+            keep[k] = 0;
+            if (lump) d = __dadd_rn(d, v[k]);
+        } else {
+            keep[k] = 1;
+            ++c;
+        }
+    }
+    vout[dpos] = d;
+    cnt[i] = c;
+}
+
+__global__ void k_compact(int n, const int* rp, const int* ci, const double* v,
+                          const int8_t* keep, const int* nrp, int* nci, double* nv)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int o = nrp[i];
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+        if (keep[k]) { nci[o] = ci[k]; nv[o] = v[k]; ++o; }
+}
+
+// --------------------------------------------------------- one-point W ----
+__global__ void k_one_point(int n, const int* rp, const int* ci, const double* v,
+                            const int8_t* strong, const int8_t* is_f, const int* c_index,
+                            const int* f_index, int* W)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !is_f[i]) return;
+    int best = -1;
+    for (int pass = 0; pass < 2 && best < 0; ++pass) {
+        double bestv = -1.0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            int j = ci[k];
+            if (j == i || is_f[j]) continue;
+            if (pass == 0 && !strong[k]) continue;
+            double a = fabs(v[k]);
+            if (a > bestv) { bestv = a; best = j; }
+        }
+    }
+    W[f_index[i]] = best >= 0 ? c_index[best] : -1;
+}
+
+// P = [W; I] in the fine numbering: one entry (weight 1) per row
+__global__ void k_p_count(int n, const int8_t* is_f, const int* f_index, const int* W, int* cnt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cnt[i] = is_f[i] ? (W[f_index[i]] >= 0) : 1;
+}
+
+__global__ void k_p_fill(int n, const int8_t* is_f, const int* f_index, const int* c_index,
+                         const int* W, const int* prp, int* pci, double* pv)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || prp[i + 1] == prp[i]) return;
+    pci[prp[i]] = is_f[i] ? W[f_index[i]] : c_index[i];
+    pv[prp[i]] = 1.0;
+}
+
+// R = [Z I] in the fine numbering: row c holds Z's row (F columns mapped to
+// their fine index) and a 1 at the C point itself, columns ascending
+__global__ void k_r_rowptr(int nc, const int* zrp, int* rrp)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c <= nc) rrp[c] = zrp[c] + c;
+}
+
+__global__ void k_r_fill(int nc, const int* zrp, const int* zci, const double* zv,
+                         const int* f_ids, const int* c_ids, const int* rrp, int* rci, double* rv)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    int o = rrp[c], self = c_ids[c];
+    bool done = false;
+    for (int k = zrp[c]; k < zrp[c + 1]; ++k) {
+        int col = f_ids[zci[k]];
+        if (!done && self < col) { rci[o] = self; rv[o] = 1.0; ++o; done = true; }
+        rci[o] = col;
+        rv[o] = zv[k];
+        ++o;
+    }
+    if (!done) { rci[o] = self; rv[o] = 1.0; }
+}
+
+// ------------------------------------------------------------- transpose --
+__global__ void k_count_cols(int n, const int* rp, const int* ci, int* cnt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) atomicAdd(cnt + ci[k], 1);
+}
+
+__global__ void k_fill_transpose(int n, const int* rp, const int* ci, const double* v,
+                                 const int* trp, int* cursor, int* tci, double* tv)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        int j = ci[k];
+        int pos = trp[j] + atomicAdd(cursor + j, 1);
+        tci[pos] = i;
+        tv[pos] = v[k];
+    }
+}
+
+// =========================================================================
+// host-side building blocks
+// =========================================================================
+struct Ctx {
+    cudaStream_t st;
+    DBuf<unsigned long long> xacc;   // exact-dot accumulator
+    DBuf<int> xbad;
+    explicit Ctx(cudaStream_t s) : st(s)
+    {
+        xacc.alloc(XD_DIGITS);
+        xbad.alloc(1);
+        CK(cudaMemsetAsync(xacc.p, 0, xacc.bytes(), st));
+        CK(cudaMemsetAsync(xbad.p, 0, xbad.bytes(), st));
+    }
+};
+
+int num_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return sms;
+}
+
+void xdot(Ctx& c, long long n, const double* x, const double* y, double* out, double* out_sqrt)
+{
+    int grid = (int)std::min<long long>(std::max<long long>(1, (n + XD_THREADS - 1) / XD_THREADS),
+                                        2LL * num_sms());
+    k_xdot_accumulate<<<grid, XD_THREADS, 0, c.st>>>(n, x, y, c.xacc.p, c.xbad.p);
+    k_xdot_finalize<<<1, 32, 0, c.st>>>(c.xacc.p, c.xbad.p, out, out_sqrt);
+    CK_LAUNCH();
+}
+
+// Builds CSR from per-row counts already in rp[0..n-1]; returns nnz.
+int counts_to_rowptr(DBuf<int>& rp, int n, cudaStream_t st) { return exclusive_scan(rp.p, rp.p, n, st); }
+
+void submatrix(const DevCSR& A, const int* rows, int nr, const int* colmap, int ncols, DevCSR& out,
+               cudaStream_t st)
+{
+    out.n_rows = nr;
+    out.n_cols = ncols;
+    out.rp.alloc(size_t(nr) + 1);
+    if (nr) k_sub_count<<<grid_for(nr, TB), TB, 0, st>>>(nr, rows, A.rp.p, A.ci.p, colmap, out.rp.p);
+    CK_LAUNCH();
+    out.nnz = counts_to_rowptr(out.rp, nr, st);
+    out.ci.alloc(out.nnz);
+    out.v.alloc(out.nnz);
+    if (nr) k_sub_fill<<<grid_for(nr, TB), TB, 0, st>>>(nr, rows, A.rp.p, A.ci.p, A.v.p, colmap,
+                                                          out.rp.p, out.ci.p, out.v.p);
+    CK_LAUNCH();
+}
+
+void spgemm(const DevCSR& A, const DevCSR& B, DevCSR& C, cudaStream_t st)
+{
+    int m = A.n_rows;
+    C.n_rows = m;
+    C.n_cols = B.n_cols;
+    C.rp.alloc(size_t(m) + 1);
+    DBuf<int> toff(size_t(m) + 1);
+    if (m) k_gemm_bound<<<grid_for(m, TB), TB, 0, st>>>(m, A.rp.p, A.ci.p, B.rp.p, toff.p);
+    CK_LAUNCH();
+    int tsz = exclusive_scan(toff.p, toff.p, m, st);
+    DBuf<int> keys(std::max(tsz, 1));
+    DBuf<double> vals(std::max(tsz, 1));
+    CK(cudaMemsetAsync(keys.p, 0xff, keys.bytes(), st));
+    if (m) k_gemm_hash<<<grid_for(m, TB), TB, 0, st>>>(m, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p,
+                                                         B.v.p, toff.p, keys.p, vals.p, C.rp.p);
+    CK_LAUNCH();
+    C.nnz = counts_to_rowptr(C.rp, m, st);
+    C.ci.alloc(C.nnz);
+    C.v.alloc(C.nnz);
+    if (m) k_gemm_emit<<<grid_for(m, TB), TB, 0, st>>>(m, toff.p, keys.p, vals.p, C.rp.p, C.ci.p,
+                                                         C.v.p);
+    CK_LAUNCH();
+    CK(cudaStreamSynchronize(st));
+}
+
+void compact(const DevCSR& A, const int8_t* keep, DBuf<int>& cnt, DevCSR& out, cudaStream_t st)
+{
+    int n = A.n_rows;
+    out.n_rows = n;
+    out.n_cols = A.n_cols;
+    out.rp = std::move(cnt);
+    out.nnz = counts_to_rowptr(out.rp, n, st);
+    out.ci.alloc(out.nnz);
+    out.v.alloc(out.nnz);
+    if (n) k_compact<<<grid_for(n, TB), TB, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, keep, out.rp.p,
+                                                       out.ci.p, out.v.p);
+    CK_LAUNCH();
+}
+
+// Local indices of the rows with is_f == want: idx (n), ids (count); returns count
+int local_index(const DBuf<int8_t>& is_f, int n, int want, DBuf<int>& idx, DBuf<int>& ids,
+                cudaStream_t st)
+{
+    DBuf<int> ex(size_t(n) + 1);
+    if (n) k_flag_eq<<<grid_for(n, TB), TB, 0, st>>>(n, is_f.p, want, ex.p);
+    CK_LAUNCH();
+    int cnt = exclusive_scan(ex.p, ex.p, n, st);
+    idx.alloc(n);
+    ids.alloc(std::max(cnt, 1));
+    if (n) k_local_index<<<grid_for(n, TB), TB, 0, st>>>(n, is_f.p, want, ex.p, idx.p, ids.p);
+    CK_LAUNCH();
+    return cnt;
+}
+
+// ---------------------------------------------------------------- Arnoldi --
+struct ArnoldiOut {
+    std::vector<double> H;   // (k+1) x k row-major
+    int k = 0;
+    bool broke = false;
+    double beta = 0.0;
+};
+
+// m steps of MGS Arnoldi from b (device, length n); dots correctly rounded.
+ArnoldiOut arnoldi(Ctx& c, const DevCSR& A, const double* b, int m, double tol)
+{
+    cudaStream_t st = c.st;
+    long long n = A.n_rows;
+    DBuf<double> V(size_t(m + 1) * n), w(n), Hd(size_t(m + 1) * m + 1);
+    CK(cudaMemsetAsync(Hd.p, 0, Hd.bytes(), st));
+    double* beta_d = Hd.p + size_t(m + 1) * m;
+    xdot(c, n, b, b, nullptr, beta_d);
+    int g = grid_for(n, TB);
+    k_div_dev<<<g, TB, 0, st>>>(n, V.p, b, beta_d);
+    CK_LAUNCH();
+    std::vector<double> Hh(size_t(m + 1) * m, 0.0);
+    ArnoldiOut out;
+    out.k = m;
+    std::vector<double> col(m + 1);
+    for (int j = 0; j < m; ++j) {
+        k_spmv_det<<<grid_for(n, TB), TB, 0, st>>>(int(n), A.rp.p, A.ci.p, A.v.p, V.p + size_t(j) * n, w.p);
+        CK_LAUNCH();
+        for (int i = 0; i <= j; ++i) {
+            double* hij = Hd.p + size_t(i) * m + j;
+            xdot(c, n, w.p, V.p + size_t(i) * n, hij, nullptr);
+            k_axpy_dev<<<g, TB, 0, st>>>(n, w.p, V.p + size_t(i) * n, hij);
+            CK_LAUNCH();
+        }
+        double* hn = Hd.p + size_t(j + 1) * m + j;
+        xdot(c, n, w.p, w.p, nullptr, hn);
+        // read column j (rows 0..j+1)
+        for (int i = 0; i <= j + 1; ++i)
+            CK(cudaMemcpyAsync(&col[i], Hd.p + size_t(i) * m + j, sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int i = 0; i <= j + 1; ++i) Hh[size_t(i) * m + j] = col[i];
+        double s = 0.0;
+        for (int i = 0; i <= j + 1; ++i) s = s + col[i] * col[i];
+        if (col[j + 1] <= tol * std::sqrt(s)) {
+            out.k = j + 1;
+            out.broke = true;
+            break;
+        }
+        if (j + 1 < m) {
+            k_div_dev<<<g, TB, 0, st>>>(n, V.p + size_t(j + 1) * n, w.p, hn);
+            CK_LAUNCH();
+        }
+    }
+    out.beta = read1(beta_d, st);
+    int k = out.k;
+    out.H.assign(size_t(k + 1) * k, 0.0);
+    for (int i = 0; i <= k; ++i)
+        for (int j = 0; j < k; ++j) out.H[size_t(i) * k + j] = Hh[size_t(i) * m + j];
+    return out;
+}
+
+std::vector<double> gmres_poly_coeffs(Ctx& c, const DevCSR& Aff, const airg_options& o, int level,
+                                      int& kout)
+{
+    int p = o.poly_order;
+    long long n = Aff.n_rows;
+    DBuf<double> b(n);
+    k_rng_uniform<<<grid_for(n, TB), TB, 0, c.st>>>(stream_key(o.seed, level, PURPOSE_COEF), n, b.p);
+    CK_LAUNCH();
+    ArnoldiOut ar = arnoldi(c, Aff, b.p, p + 1, o.breakdown_tol);
+    std::vector<double> y = givens_lsq(ar.H, ar.k, ar.beta);
+    std::vector<double> alpha = power_coefficients(ar.H, ar.k, ar.beta, y);
+    alpha.resize(size_t(p) + 1, 0.0);
+    kout = ar.k;
+    return alpha;
+}
+
+void fixed_sparsity_inverse(const DevCSR& Aff, const std::vector<double>& alpha, DevCSR& out,
+                            cudaStream_t st)
+{
+    int n = Aff.n_rows, nnz = Aff.nnz;
+    out.alloc(n, n, nnz);
+    CK(cudaMemcpyAsync(out.rp.p, Aff.rp.p, (n + 1) * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(out.ci.p, Aff.ci.p, nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    if (!n) return;
+    k_fsp_init<<<grid_for(n, TB), TB, 0, st>>>(n, Aff.rp.p, Aff.ci.p, alpha[0], out.v.p);
+    DBuf<double> T(nnz), Tn(nnz);
+    CK(cudaMemcpyAsync(T.p, Aff.v.p, nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (size_t k = 1; k < alpha.size(); ++k) {
+        if (k >= 2) {
+            k_fsp_power<<<grid_for(n, TB), TB, 0, st>>>(n, Aff.rp.p, Aff.ci.p, Aff.v.p, T.p, Tn.p);
+            std::swap(T.p, Tn.p);
+        }
+        k_fsp_acc<<<grid_for(nnz, TB), TB, 0, st>>>(nnz, out.v.p, T.p, alpha[k]);
+        CK_LAUNCH();
+    }
+    CK(cudaStreamSynchronize(st));
+}
+
+// Newton application x = q(A) b (Sec. 2.3), deterministic kernels.
+void newton_apply(Ctx& c, const DevCSR& A, const std::vector<Root>& roots, const double* b,
+                  double* x)
+{
+    cudaStream_t st = c.st;
+    long long n = A.n_rows;
+    DBuf<double> r(n), w(n), t(n);
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+    CK(cudaMemcpyAsync(r.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int g = grid_for(n, TB);
+    for (size_t idx = 0; idx < roots.size(); ++idx) {
+        bool last = idx + 1 == roots.size();
+        double a = roots[idx].re, bi = roots[idx].im;
+        if (bi == 0.0) {
+            k_newton_real_x<<<g, TB, 0, st>>>(n, x, r.p, a);
+            if (!last) {
+                k_spmv_det<<<g, TB, 0, st>>>(int(n), A.rp.p, A.ci.p, A.v.p, r.p, w.p);
+                k_newton_r<<<g, TB, 0, st>>>(n, r.p, w.p, a);
+            }
+        } else {
+            double mod2 = a * a + bi * bi;
+            k_spmv_det<<<g, TB, 0, st>>>(int(n), A.rp.p, A.ci.p, A.v.p, r.p, w.p);
+            k_newton_pair<<<g, TB, 0, st>>>(n, x, r.p, w.p, t.p, 2.0 * a, mod2);
+            if (!last) {
+                k_spmv_det<<<g, TB, 0, st>>>(int(n), A.rp.p, A.ci.p, A.v.p, t.p, w.p);
+                k_newton_r<<<g, TB, 0, st>>>(n, r.p, w.p, mod2);
+            }
+        }
+        CK_LAUNCH();
+    }
+    CK(cudaStreamSynchronize(st));
+}
+
+std::vector<Root> coarse_polynomial(Ctx& c, const DevCSR& A, const airg_options& o, int level,
+                                    int m, int& kout)
+{
+    long long n = A.n_rows;
+    DBuf<double> b(n);
+    k_rng_uniform<<<grid_for(n, TB), TB, 0, c.st>>>(stream_key(o.seed, level, PURPOSE_COARSE), n, b.p);
+    CK_LAUNCH();
+    ArnoldiOut ar = arnoldi(c, A, b.p, m, o.breakdown_tol);
+    std::vector<double> wr, wi;
+    if (!harmonic_ritz(ar.H, ar.k, ar.broke, wr, wi))
+        fail(AIRG_ERR_BREAKDOWN, "harmonic Ritz eigenvalue iteration did not converge");
+    kout = ar.k;
+    return order_roots(wr, wi, o.addroot_log10, o.addroot_per);
+}
+
+double truncation_residual(Ctx& c, const DevCSR& A, const std::vector<Root>& roots,
+                           const airg_options& o, int level)
+{
+    cudaStream_t st = c.st;
+    long long n = A.n_rows;
+    DBuf<double> b2(n), x(n), y(n), r(n), nrm(2);
+    k_rng_uniform<<<grid_for(n, TB), TB, 0, st>>>(stream_key(o.seed, level, PURPOSE_TRUNC), n, b2.p);
+    CK_LAUNCH();
+    newton_apply(c, A, roots, b2.p, x.p);
+    k_spmv_det<<<grid_for(n, TB), TB, 0, st>>>(int(n), A.rp.p, A.ci.p, A.v.p, x.p, y.p);
+    k_sub<<<grid_for(n, TB), TB, 0, st>>>(n, b2.p, y.p, r.p);
+    CK_LAUNCH();
+    xdot(c, n, r.p, r.p, nullptr, nrm.p);
+    xdot(c, n, b2.p, b2.p, nullptr, nrm.p + 1);
+    double h[2];
+    d2h(h, nrm.p, 2, st);
+    return h[0] / h[1];
+}
+
+// ------------------------------------------------------------- CF split --
+void cf_split(Ctx& c, SetupLevel& L, const airg_options& o, int level)
+{
+    cudaStream_t st = c.st;
+    const DevCSR& A = L.A;
+    int n = A.n_rows;
+    int g = grid_for(n, TB);
+    L.strong.alloc(std::max(A.nnz, 1));
+    k_strength<<<g, TB, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, o.strong_threshold, L.strong.p);
+    // S^T
+    DBuf<int> rpt(size_t(n) + 1), cursor(n);
+    CK(cudaMemsetAsync(rpt.p, 0, rpt.bytes(), st));
+    CK(cudaMemsetAsync(cursor.p, 0, cursor.bytes(), st));
+    k_count_strong_t<<<g, TB, 0, st>>>(n, A.rp.p, A.ci.p, L.strong.p, rpt.p);
+    CK_LAUNCH();
+    int nst = exclusive_scan(rpt.p, rpt.p, n, st);
+    DBuf<int> ct(std::max(nst, 1));
+    k_fill_strong_t<<<g, TB, 0, st>>>(n, A.rp.p, A.ci.p, L.strong.p, rpt.p, cursor.p, ct.p);
+    k_sort_rows<<<g, TB, 0, st>>>(n, rpt.p, ct.p);
+    CK_LAUNCH();
+    // G = S + S^T
+    DBuf<int> rpg(size_t(n) + 1);
+    k_union<<<g, TB, 0, st>>>(n, A.rp.p, A.ci.p, L.strong.p, rpt.p, ct.p, nullptr, nullptr, rpg.p);
+    CK_LAUNCH();
+    int ng = exclusive_scan(rpg.p, rpg.p, n, st);
+    DBuf<int> cg(std::max(ng, 1));
+    k_union<<<g, TB, 0, st>>>(n, A.rp.p, A.ci.p, L.strong.p, rpt.p, ct.p, rpg.p, cg.p, nullptr);
+    CK_LAUNCH();
+    // PMISR rounds
+    DBuf<unsigned> w(n);
+    DBuf<int8_t> state(n), newf(n);
+    DBuf<int> und(1);
+    k_rng_u32<<<g, TB, 0, st>>>(stream_key(o.seed, level, PURPOSE_PMISR), n, w.p);
+    CK(cudaMemsetAsync(state.p, 0, state.bytes(), st));
+    int rounds = 0;
+    while (true) {
+        ++rounds;
+        CK(cudaMemsetAsync(und.p, 0, sizeof(int), st));
+        k_pmisr_select<<<g, TB, 0, st>>>(n, rpg.p, cg.p, w.p, state.p, newf.p);
+        k_pmisr_update<<<g, TB, 0, st>>>(n, rpg.p, cg.p, state.p, newf.p, und.p);
+        CK_LAUNCH();
+        if (read1(und.p, st) == 0) break;
+        if (rounds > n + 1) fail(AIRG_ERR_STATE, "PMISR made no progress");
+    }
+    L.pmisr_rounds = rounds;
+    L.is_f.alloc(n);
+    k_state_to_f<<<g, TB, 0, st>>>(n, state.p, L.is_f.p);
+    CK_LAUNCH();
+    // DDC passes (Sec. 2.1): 1000 equal bins over [0, max ratio]
+    const int nbins = 1000;
+    DBuf<double> ratio(n);
+    DBuf<int> bins(n), hist(nbins), cnt(size_t(n) + 1);
+    DBuf<unsigned long long> rmax(1);
+    L.ddc_converted.clear();
+    for (int it = 0; it < o.ddc_its; ++it) {
+        k_flag_eq<<<g, TB, 0, st>>>(n, L.is_f.p, 1, cnt.p);
+        CK_LAUNCH();
+        int n_f = exclusive_scan(cnt.p, cnt.p, n, st);
+        if (n_f == 0) { L.ddc_converted.push_back(0); continue; }
+        CK(cudaMemsetAsync(rmax.p, 0, sizeof(unsigned long long), st));
+        k_ddc_ratio<<<g, TB, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, L.is_f.p, ratio.p, rmax.p);
+        CK_LAUNCH();
+        unsigned long long rb = read1(rmax.p, st);
+        double rm;
+        std::memcpy(&rm, &rb, sizeof rm);
+        if (!(rm > 0.0)) { L.ddc_converted.push_back(0); continue; }
+        if (std::isinf(rm)) fail(AIRG_ERR_BREAKDOWN, "zero diagonal in an F row");
+        long long k = (long long)std::ceil(o.ddc_fraction * double(n_f));
+        CK(cudaMemsetAsync(hist.p, 0, hist.bytes(), st));
+        k_ddc_bin<<<g, TB, 0, st>>>(n, L.is_f.p, ratio.p, rm, nbins, bins.p, hist.p);
+        CK_LAUNCH();
+        std::vector<int> hh(nbins);
+        d2h(hh.data(), hist.p, nbins, st);
+        // boundary B whose count at or above it is closest to k (ties: higher B)
+        long long above = 0;
+        int best_b = nbins;
+        long long best_d = k;   // |0 - k|
+        std::vector<long long> ab(nbins + 1, 0);
+        for (int b = nbins - 1; b >= 0; --b) { above += hh[b]; ab[b] = above; }
+        for (int b = nbins - 1; b >= 0; --b) {
+            long long d = std::llabs(ab[b] - k);
+            if (d < best_d) { best_d = d; best_b = b; }
+        }
+        L.ddc_converted.push_back(int(best_b < nbins ? ab[best_b] : 0));
+        if (best_b < nbins) {
+            k_ddc_convert<<<g, TB, 0, st>>>(n, L.is_f.p, bins.p, best_b);
+            CK_LAUNCH();
+        }
+    }
+}
+
+}  // namespace
+
+// ===========================================================================
+void dot_exact_device(long long n, const double* x, const double* y, double* out,
+                      double* out_sqrt, cudaStream_t st)
+{
+    Ctx c(st);
+    xdot(c, n, x, y, out, out_sqrt);
+    CK(cudaStreamSynchronize(st));
+}
+
+void rng_uniform_device(uint64_t seed, long long level, long long purpose, long long n,
+                        double* out, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_rng_uniform<<<grid_for(n, TB), TB, 0, st>>>(stream_key(seed, level, purpose), n, out);
+    CK_LAUNCH();
+    CK(cudaStreamSynchronize(st));
+}
+
+void validate_csr(const DevCSR& A, bool square, cudaStream_t st)
+{
+    DBuf<int> flags(2);
+    CK(cudaMemsetAsync(flags.p, 0, flags.bytes(), st));
+    if (A.n_rows)
+        k_validate<<<grid_for(A.n_rows, TB), TB, 0, st>>>(A.n_rows, A.n_cols, A.rp.p, A.ci.p,
+                                                            square ? 1 : 0, flags.p);
+    CK_LAUNCH();
+    int f[2];
+    d2h(f, flags.p, 2, st);
+    if (f[0]) fail(AIRG_ERR_ARG, "CSR columns out of range or not strictly ascending");
+    if (f[1]) fail(AIRG_ERR_ARG, "a row has no stored diagonal");
+}
+
+void csr_transpose(const DevCSR& A, DevCSR& T, cudaStream_t st)
+{
+    int n = A.n_rows, m = A.n_cols;
+    T.n_rows = m;
+    T.n_cols = n;
+    T.nnz = A.nnz;
+    T.rp.alloc(size_t(m) + 1);
+    DBuf<int> cursor(std::max(m, 1));
+    CK(cudaMemsetAsync(T.rp.p, 0, T.rp.bytes(), st));
+    CK(cudaMemsetAsync(cursor.p, 0, cursor.bytes(), st));
+    if (n) k_count_cols<<<grid_for(n, TB), TB, 0, st>>>(n, A.rp.p, A.ci.p, T.rp.p);
+    CK_LAUNCH();
+    exclusive_scan(T.rp.p, T.rp.p, m, st);
+    T.ci.alloc(A.nnz);
+    T.v.alloc(A.nnz);
+    if (n) k_fill_transpose<<<grid_for(n, TB), TB, 0, st>>>(n, A.rp.p, A.ci.p, A.v.p, T.rp.p,
+                                                              cursor.p, T.ci.p, T.v.p);
+    if (m) k_sort_rows_kv<<<grid_for(m, TB), TB, 0, st>>>(m, T.rp.p, T.ci.p, T.v.p);
+    CK_LAUNCH();
+    CK(cudaStreamSynchronize(st));
+}
+
+std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, cudaStream_t st)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    auto H = std::make_unique<Hierarchy>();
+    H->opt = o;
+    Ctx c(st);
+    DevCSR A = std::move(A0);
+    int level = 0;
+    while (true) {
+        int n = A.n_rows;
+        bool last = level >= o.max_levels - 1 || n <= o.coarse_min_rows;
+        int m_c = std::min(o.coarse_poly_order, n);
+        double trunc_rel = NAN;
+        if (!last && o.trunc_rtol > 0.0 && level >= o.trunc_start_level) {
+            int k = 0;
+            std::vector<Root> roots = coarse_polynomial(c, A, o, level, m_c, k);
+            trunc_rel = truncation_residual(c, A, roots, o, level);
+            if (trunc_rel <= o.trunc_rtol) {
+                H->coarse.A = std::move(A);
+                H->coarse.roots = std::move(roots);
+                H->coarse.k = k;
+                H->coarse.trunc_rel = trunc_rel;
+                H->coarse.truncated = true;
+                break;
+            }
+        }
+        auto L = std::make_unique<SetupLevel>();
+        L->n = n;
+        L->A = std::move(A);
+        if (!last) {
+            cf_split(c, *L, o, level);
+            L->n_f = local_index(L->is_f, n, 1, L->f_index, L->f_ids, st);
+            L->n_c = n - L->n_f;
+            if (L->n_f == 0 || L->n_f == n) last = true;
+        }
+        if (last) {
+            int k = 0;
+            H->coarse.roots = coarse_polynomial(c, L->A, o, level, m_c, k);
+            H->coarse.k = k;
+            H->coarse.trunc_rel = trunc_rel;
+            H->coarse.A = std::move(L->A);
+            break;
+        }
+        L->trunc_rel = trunc_rel;
+        local_index(L->is_f, n, 0, L->c_index, L->c_ids, st);
+        const DevCSR& Al = L->A;
+        // blocks of Eq. 3
+        submatrix(Al, L->f_ids.p, L->n_f, L->f_index.p, L->n_f, L->A_ff, st);
+        submatrix(Al, L->f_ids.p, L->n_f, L->c_index.p, L->n_c, L->A_fc, st);
+        DevCSR A_cf;
+        submatrix(Al, L->c_ids.p, L->n_c, L->f_index.p, L->n_f, A_cf, st);
+        // GMRES polynomial (Eq. 4) and fixed-sparsity inverse (Eq. 5)
+        L->alpha = gmres_poly_coeffs(c, L->A_ff, o, level, L->alpha_k);
+        DevCSR Ainv;
+        fixed_sparsity_inverse(L->A_ff, L->alpha, Ainv, st);
+        // Z = -A_cf Ahat^-1, then the relative drop on R
+        DevCSR Zfull;
+        spgemm(A_cf, Ainv, Zfull, st);
+        if (Zfull.nnz) k_scale<<<grid_for(Zfull.nnz, TB), TB, 0, st>>>(Zfull.nnz, Zfull.v.p, -1.0);
+        {
+            DBuf<int8_t> keep(std::max(Zfull.nnz, 1));
+            DBuf<int> cnt(size_t(L->n_c) + 1);
+            if (L->n_c) k_drop_rows<<<grid_for(L->n_c, TB), TB, 0, st>>>(L->n_c, Zfull.rp.p, Zfull.v.p,
+                                                                         o.r_drop, keep.p, cnt.p);
+            CK_LAUNCH();
+            compact(Zfull, keep.p, cnt, L->Z, st);
+        }
+        // one-point prolongator
+        L->W.alloc(std::max(L->n_f, 1));
+        k_one_point<<<grid_for(n, TB), TB, 0, st>>>(n, Al.rp.p, Al.ci.p, Al.v.p, L->strong.p,
+                                                    L->is_f.p, L->c_index.p, L->f_index.p, L->W.p);
+        CK_LAUNCH();
+        // P = [W; I] and R = [Z I] in the fine numbering
+        DevCSR P, R, AP, Ac;
+        P.n_rows = n;
+        P.n_cols = L->n_c;
+        P.rp.alloc(size_t(n) + 1);
+        k_p_count<<<grid_for(n, TB), TB, 0, st>>>(n, L->is_f.p, L->f_index.p, L->W.p, P.rp.p);
+        CK_LAUNCH();
+        P.nnz = counts_to_rowptr(P.rp, n, st);
+        P.ci.alloc(P.nnz);
+        P.v.alloc(P.nnz);
+        k_p_fill<<<grid_for(n, TB), TB, 0, st>>>(n, L->is_f.p, L->f_index.p, L->c_index.p, L->W.p,
+                                                 P.rp.p, P.ci.p, P.v.p);
+        CK_LAUNCH();
+        R.n_rows = L->n_c;
+        R.n_cols = n;
+        R.nnz = L->Z.nnz + L->n_c;
+        R.rp.alloc(size_t(L->n_c) + 1);
+        R.ci.alloc(R.nnz);
+        R.v.alloc(R.nnz);
+        k_r_rowptr<<<grid_for(L->n_c + 1, TB), TB, 0, st>>>(L->n_c, L->Z.rp.p, R.rp.p);
+        k_r_fill<<<grid_for(L->n_c, TB), TB, 0, st>>>(L->n_c, L->Z.rp.p, L->Z.ci.p, L->Z.v.p,
+                                                      L->f_ids.p, L->c_ids.p, R.rp.p, R.ci.p, R.v.p);
+        CK_LAUNCH();
+        // A_coarse = R (A P), then drop + lump
+        spgemm(Al, P, AP, st);
+        spgemm(R, AP, Ac, st);
+        // rows of AP at the F points: A_fc + A_ff W (the solve's residual operator)
+        submatrix(AP, L->f_ids.p, L->n_f, nullptr, L->n_c, L->M, st);
+        {
+            int nc = Ac.n_rows;
+            DBuf<int8_t> keep(std::max(Ac.nnz, 1));
+            DBuf<double> vout(std::max(Ac.nnz, 1));
+            DBuf<int> cnt(size_t(nc) + 1), bad(1);
+            CK(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+            if (nc) k_drop_lump<<<grid_for(nc, TB), TB, 0, st>>>(nc, Ac.rp.p, Ac.ci.p, Ac.v.p, o.a_drop,
+                                                                o.a_lump, keep.p, vout.p, cnt.p, bad.p);
+            CK_LAUNCH();
+            if (read1(bad.p, st)) fail(AIRG_ERR_BREAKDOWN, "coarse row without a diagonal");
+            std::swap(Ac.v.p, vout.p);
+            DevCSR Acd;
+            compact(Ac, keep.p, cnt, Acd, st);
+            A = std::move(Acd);
+        }
+        CK(cudaStreamSynchronize(st));
+        H->levels.push_back(std::move(L));
+        ++level;
+    }
+    build_solve_data(*H, st);
+    CK(cudaStreamSynchronize(st));
+    H->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return H;
+}
+
+}  // namespace airg

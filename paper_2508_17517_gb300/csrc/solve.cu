@@ -1,0 +1,789 @@
+// AIRG solve phase on the GPU: one V-cycle with up F-point smoothing only
+// (Sec. 2, Eq. 6) as the right preconditioner of FP64 flexible GMRES.
+//
+// Layout ("nested F/C order").  Level l's unknowns are stored as
+// [F points of level l | unknowns of level l+1], recursively, so the whole
+// hierarchy lives in one vector of the top-level length: level l occupies the
+// suffix starting at off_l = n_F,0 + ... + n_F,l-1 and its C points are
+// exactly level l+1's block.  Restriction r_{l+1} = r_c + Z r_f (Eq. 3)
+// therefore updates the C block in place, the coarse-grid correction e_c is
+// already where the prolongation reads it, and no gather or scatter runs
+// between levels.  The outer FGMRES works on the top operator permuted into
+// the same order; b and x are permuted once on entry and exit.
+//
+// Operators are SELL-32 (slices of 32 rows, column-major inside a slice,
+// padded to the slice's longest row) so that a warp reads 32 consecutive
+// rows with coalesced loads.  The F-point residual uses M = A_fc + A_ff W
+// (the F rows of A P, formed in the setup), so t = r_f - M e_c is one SpMV
+// instead of a prolongation followed by two (Eq. 6 with e_f = W e_c).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "dev_util.cuh"
+#include "handle.h"
+
+namespace airg {
+
+namespace {
+constexpr int TB = 256;
+}
+
+template <class T>
+struct Sell {
+    int n_rows = 0, n_cols = 0, n_slices = 0;
+    long long nnz = 0, padded = 0;
+    DBuf<int> sptr;   // n_slices + 1 element offsets
+    DBuf<int> col;
+    DBuf<T> val;
+};
+
+template <class T>
+struct SellView {
+    int n_rows;
+    const int* __restrict__ sptr;
+    const int* __restrict__ col;
+    const T* __restrict__ val;
+};
+
+template <class T>
+SellView<T> view(const Sell<T>& s) { return SellView<T>{s.n_rows, s.sptr.p, s.col.p, s.val.p}; }
+
+template <class T>
+struct SolveLevelT {
+    Sell<T> Z, M, Aff;
+};
+
+struct SolveLevel {
+    int off = 0, n_f = 0, n_c = 0;
+    DBuf<int> W;                 // nested-relative C position, -1 none
+    std::vector<double> alpha;
+    SolveLevelT<double> d;
+    SolveLevelT<float> f;
+};
+
+struct SolveData {
+    int n0 = 0, nlev = 0, off_c = 0, n_coarse = 0;
+    DBuf<int> pos0;              // natural index -> nested position (top level)
+    Sell<double> Atop;
+    std::vector<std::unique_ptr<SolveLevel>> lv;
+    Sell<double> Ac;
+    Sell<float> Ac32;
+    std::vector<Root> roots;
+    int max_nf = 0;
+    // V-cycle work (FP64 and FP32 copies)
+    DBuf<double> rwork, t, wa, wb, cx, cr0, cr1, ct;
+    DBuf<float> rwork32, e32, t32, wa32, wb32, cx32, cr032, cr132, ct32, vin32;
+    // outer FGMRES
+    int restart = 0;
+    DBuf<double> V, Zs, w, bp, xp, r, part;
+    DBuf<double> hdev;
+    HBuf<double> hhost;
+    long long bytes_vcycle = 0;
+};
+
+Hierarchy::Hierarchy() = default;
+Hierarchy::~Hierarchy() = default;
+
+namespace {
+
+// ----------------------------------------------------------- SELL build --
+__global__ void k_sell_width(int nrows, int nslices, const int* rp, const int* src_row, int* width)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslices) return;
+    int w = 0;
+    for (int l = 0; l < 32; ++l) {
+        int r = s * 32 + l;
+        if (r >= nrows) break;
+        int i = src_row ? src_row[r] : r;
+        w = max(w, rp[i + 1] - rp[i]);
+    }
+    width[s] = w * 32;
+}
+
+template <class T>
+__global__ void k_sell_fill(int nrows, int nslices, const int* rp, const int* ci, const double* v,
+                            const int* src_row, const int* cmap, const int* sptr, int* col, T* val)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nslices * 32) return;
+    int s = r >> 5, lane = r & 31;
+    int w = (sptr[s + 1] - sptr[s]) >> 5;
+    int base = sptr[s] + lane;
+    if (r >= nrows) {
+        for (int k = 0; k < w; ++k) { col[base + k * 32] = 0; val[base + k * 32] = T(0); }
+        return;
+    }
+    int i = src_row ? src_row[r] : r;
+    int b = rp[i], len = rp[i + 1] - rp[i];
+    int lastc = 0;
+    for (int k = 0; k < w; ++k) {
+        if (k < len) {
+            int c = ci[b + k];
+            lastc = cmap ? cmap[c] : c;
+            col[base + k * 32] = lastc;
+            val[base + k * 32] = T(v[b + k]);
+        } else {
+            col[base + k * 32] = lastc;
+            val[base + k * 32] = T(0);
+        }
+    }
+}
+
+template <class T>
+void build_sell(const DevCSR& A, const int* src_row, const int* cmap, int n_cols, Sell<T>& S,
+                cudaStream_t st)
+{
+    S.n_rows = A.n_rows;
+    S.n_cols = n_cols;
+    S.nnz = A.nnz;
+    S.n_slices = (A.n_rows + 31) / 32;
+    S.sptr.alloc(size_t(S.n_slices) + 1);
+    if (S.n_slices)
+        k_sell_width<<<grid_for(S.n_slices, TB), TB, 0, st>>>(A.n_rows, S.n_slices, A.rp.p, src_row,
+                                                                S.sptr.p);
+    CK_LAUNCH();
+    S.padded = exclusive_scan(S.sptr.p, S.sptr.p, S.n_slices, st);
+    S.col.alloc(std::max<long long>(S.padded, 1));
+    S.val.alloc(std::max<long long>(S.padded, 1));
+    if (S.n_slices)
+        k_sell_fill<T><<<grid_for((long long)S.n_slices * 32, TB), TB, 0, st>>>(
+            A.n_rows, S.n_slices, A.rp.p, A.ci.p, A.v.p, src_row, cmap, S.sptr.p, S.col.p, S.val.p);
+    CK_LAUNCH();
+}
+
+template <class T>
+void sell_to_f32(const Sell<double>& S, Sell<T>& out, cudaStream_t st);
+
+__global__ void k_d2f(long long n, const double* a, float* b)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+__global__ void k_f2d(long long n, const float* a, double* b)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
+void copy_sell_f32(const Sell<double>& S, Sell<float>& out, cudaStream_t st)
+{
+    out.n_rows = S.n_rows;
+    out.n_cols = S.n_cols;
+    out.n_slices = S.n_slices;
+    out.nnz = S.nnz;
+    out.padded = S.padded;
+    out.sptr.alloc(S.sptr.n);
+    out.col.alloc(S.col.n);
+    out.val.alloc(S.val.n);
+    CK(cudaMemcpyAsync(out.sptr.p, S.sptr.p, S.sptr.bytes(), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(out.col.p, S.col.p, S.col.bytes(), cudaMemcpyDeviceToDevice, st));
+    if (S.val.n) k_d2f<<<grid_for(S.val.n, TB), TB, 0, st>>>((long long)S.val.n, S.val.p, out.val.p);
+    CK_LAUNCH();
+}
+
+// ------------------------------------------------------- nested ordering --
+__global__ void k_pos_coarse(int n, int off, int* pos)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) pos[i] = off + i;
+}
+
+__global__ void k_pos_level(int n, const int8_t* is_f, const int* f_index, const int* c_index,
+                            int off, const int* pos_next, int* pos)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    pos[i] = is_f[i] ? off + f_index[i] : pos_next[c_index[i]];
+}
+
+__global__ void k_rel(int n, const int* pos, int off, int* rel, int* inv)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = pos[i] - off;
+    rel[i] = r;
+    if (inv) inv[r] = i;
+}
+
+__global__ void k_map_w(int nf, const int* W, const int* rel, int* out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nf) out[i] = W[i] >= 0 ? rel[W[i]] : -1;
+}
+
+// ------------------------------------------------------- V-cycle kernels --
+template <class T>
+__device__ __forceinline__ T sell_row(const SellView<T>& S, int r, const T* __restrict__ x)
+{
+    int s = r >> 5;
+    int base = S.sptr[s] + (r & 31);
+    int w = (S.sptr[s + 1] - S.sptr[s]) >> 5;
+    T acc = T(0);
+    for (int k = 0; k < w; ++k) {
+        int idx = base + k * 32;
+        acc = fma(S.val[idx], x[S.col[idx]], acc);
+    }
+    return acc;
+}
+
+// y = S x
+template <class T>
+__global__ void k_spmv(SellView<T> S, const T* __restrict__ x, T* __restrict__ y)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < S.n_rows) y[r] = sell_row(S, r, x);
+}
+
+// restriction (Eq. 3): dst_c[k] = src_c[k] + (Z src_f)[k]
+template <class T>
+__global__ void k_restrict(SellView<T> Z, const T* __restrict__ src_f, const T* __restrict__ src_c,
+                           T* __restrict__ dst_c)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < Z.n_rows) dst_c[r] = src_c[r] + sell_row(Z, r, src_f);
+}
+
+// F-point residual (Eq. 6): t = r_f - M e_c, and the first Horner term w = a_p t
+template <class T>
+__global__ void k_fresid(SellView<T> M, const T* __restrict__ rf, const T* __restrict__ ec,
+                         T* __restrict__ t, T* __restrict__ w, T ap)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M.n_rows) return;
+    T tt = rf[r] - sell_row(M, r, ec);
+    t[r] = tt;
+    w[r] = ap * tt;
+}
+
+// Horner term: wout = a_k t + A_ff win
+template <class T>
+__global__ void k_horner(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
+                         T* __restrict__ wout, T ak)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < A.n_rows) wout[r] = fma(ak, t[r], sell_row(A, r, win));
+}
+
+// last Horner term and the correction: e_f = W e_c + (a_0 t + A_ff win)
+template <class T>
+__global__ void k_horner_last(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
+                              const T* __restrict__ ec, const int* __restrict__ W,
+                              T* __restrict__ ef, T a0)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= A.n_rows) return;
+    int wc = W[r];
+    T p = wc >= 0 ? ec[wc] : T(0);
+    ef[r] = p + fma(a0, t[r], sell_row(A, r, win));
+}
+
+// degree-0 smoother: e_f = W e_c + a_0 t
+template <class T>
+__global__ void k_smooth0(int n, const T* __restrict__ t, const T* __restrict__ ec,
+                          const int* __restrict__ W, T* __restrict__ ef, T a0)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int wc = W[r];
+    ef[r] = (wc >= 0 ? ec[wc] : T(0)) + a0 * t[r];
+}
+
+// Newton steps of the coarse polynomial (Sec. 2.3)
+template <class T>
+__global__ void k_newton_real(SellView<T> A, const T* __restrict__ rin, T* __restrict__ rout,
+                              T* __restrict__ x, T inv_theta, int first, int last)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= A.n_rows) return;
+    T ri = rin[r];
+    T xv = first ? T(0) : x[r];
+    x[r] = fma(ri, inv_theta, xv);
+    if (!last) rout[r] = ri - sell_row(A, r, rin) * inv_theta;
+}
+
+template <class T>
+__global__ void k_newton_pair1(SellView<T> A, const T* __restrict__ rin, T* __restrict__ t,
+                               T* __restrict__ x, T two_a, T inv_mod2, int first)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= A.n_rows) return;
+    T tt = two_a * rin[r] - sell_row(A, r, rin);
+    t[r] = tt;
+    T xv = first ? T(0) : x[r];
+    x[r] = fma(tt, inv_mod2, xv);
+}
+
+template <class T>
+__global__ void k_newton_pair2(SellView<T> A, const T* __restrict__ rin, const T* __restrict__ t,
+                               T* __restrict__ rout, T inv_mod2)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= A.n_rows) return;
+    rout[r] = rin[r] - sell_row(A, r, t) * inv_mod2;
+}
+
+// ---------------------------------------------------------- Krylov kernels --
+constexpr int RB = 256;          // reduction block
+constexpr int RGRID = 304;       // partial sums per reduction (2 x SMs)
+
+// part[b*m + i] = partial of <w, V_i> for i < m
+__global__ void k_multidot(long long n, int m, const double* __restrict__ V, long long ldv,
+                           const double* __restrict__ w, double* __restrict__ part)
+{
+    __shared__ double red[RB / 32][32];
+    for (int i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (long long r = (long long)blockIdx.x * RB + threadIdx.x; r < n; r += (long long)gridDim.x * RB)
+            s = fma(V[i * ldv + r], w[r], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][i & 31] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < RB / 32; ++q) t += red[q][i & 31];
+            part[(long long)blockIdx.x * m + i] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// out[i] = sum_b part[b*m + i], fixed order
+__global__ void k_sum_parts(int nb, int m, const double* part, double* out)
+{
+    int i = threadIdx.x;
+    if (i >= m) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(long long)b * m + i];
+    out[i] = s;
+}
+
+// w -= sum_i h_i V_i
+__global__ void k_multiaxpy(long long n, int m, const double* __restrict__ V, long long ldv,
+                            const double* __restrict__ h, double* __restrict__ w)
+{
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double s = w[r];
+    for (int i = 0; i < m; ++i) s = fma(-h[i], V[i * ldv + r], s);
+    w[r] = s;
+}
+
+// x += sum_i y_i Z_i   (y on device)
+__global__ void k_multiaxpy_plus(long long n, int m, const double* __restrict__ Zs, long long ldz,
+                                 const double* __restrict__ y, double* __restrict__ x)
+{
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double s = x[r];
+    for (int i = 0; i < m; ++i) s = fma(y[i], Zs[i * ldz + r], s);
+    x[r] = s;
+}
+
+__global__ void k_scale_into(long long n, const double* __restrict__ w, double inv, double* __restrict__ v)
+{
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) v[r] = w[r] * inv;
+}
+
+// r = b - y
+__global__ void k_sub2(long long n, const double* b, const double* y, double* r)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) r[i] = b[i] - y[i];
+}
+
+// nested <-> natural permutation
+__global__ void k_to_nested(long long n, const int* pos, const double* a, double* b)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[pos[i]] = a[i];
+}
+__global__ void k_from_nested(long long n, const int* pos, const double* a, double* b)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[pos[i]];
+}
+
+// ------------------------------------------------------------ V-cycle ----
+template <class T>
+struct VWork {
+    T* rwork; T* t; T* wa; T* wb; T* cx; T* cr0; T* cr1; T* ct;
+};
+
+template <class T>
+const SolveLevelT<T>& ops(const SolveLevel& L);
+template <>
+const SolveLevelT<double>& ops<double>(const SolveLevel& L) { return L.d; }
+template <>
+const SolveLevelT<float>& ops<float>(const SolveLevel& L) { return L.f; }
+
+template <class T>
+const Sell<T>& coarse_op(const SolveData& S);
+template <>
+const Sell<double>& coarse_op<double>(const SolveData& S) { return S.Ac; }
+template <>
+const Sell<float>& coarse_op<float>(const SolveData& S) { return S.Ac32; }
+
+// e = M^-1 v in the nested order.  v is only read; e is written everywhere.
+template <class T>
+void vcycle(const SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
+{
+    const int L = S.nlev;
+    // restriction, top to bottom (level 0 reads v, deeper levels the work vector)
+    for (int l = 0; l < L; ++l) {
+        const SolveLevel& lv = *S.lv[l];
+        const T* src = l == 0 ? v : wk.rwork;
+        const Sell<T>& Z = ops<T>(lv).Z;
+        if (lv.n_c)
+            k_restrict<T><<<grid_for(lv.n_c, TB), TB, 0, st>>>(view(Z), src + lv.off,
+                                                               src + lv.off + lv.n_f,
+                                                               wk.rwork + lv.off + lv.n_f);
+    }
+    // coarse-grid polynomial
+    {
+        const T* rc = (L == 0 ? v : wk.rwork) + S.off_c;
+        T* x = e + S.off_c;
+        const Sell<T>& A = coarse_op<T>(S);
+        SellView<T> Av = view(A);
+        int g = grid_for(S.n_coarse, TB);
+        const T* rin = rc;
+        T* bufs[2] = {wk.cr0, wk.cr1};
+        int nb = 0;
+        size_t nr = S.roots.size();
+        for (size_t i = 0; i < nr; ++i) {
+            bool last = i + 1 == nr;
+            const Root& q = S.roots[i];
+            T* rout = bufs[nb];
+            if (q.im == 0.0) {
+                k_newton_real<T><<<g, TB, 0, st>>>(Av, rin, rout, x, T(1.0 / q.re), i == 0, last);
+            } else {
+                double mod2 = q.re * q.re + q.im * q.im;
+                k_newton_pair1<T><<<g, TB, 0, st>>>(Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0);
+                if (!last) k_newton_pair2<T><<<g, TB, 0, st>>>(Av, rin, wk.ct, rout, T(1.0 / mod2));
+            }
+            if (!last) { rin = rout; nb ^= 1; }
+        }
+        if (nr == 0) CK(cudaMemsetAsync(x, 0, sizeof(T) * S.n_coarse, st));
+    }
+    // up: prolongation + F-point smoothing, bottom to top
+    for (int l = L - 1; l >= 0; --l) {
+        const SolveLevel& lv = *S.lv[l];
+        const T* src = l == 0 ? v : wk.rwork;
+        const SolveLevelT<T>& o = ops<T>(lv);
+        const T* rf = src + lv.off;
+        const T* ec = e + lv.off + lv.n_f;
+        T* ef = e + lv.off;
+        int nf = lv.n_f;
+        int g = grid_for(nf, TB);
+        int p = int(lv.alpha.size()) - 1;
+        k_fresid<T><<<g, TB, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa, T(lv.alpha[p]));
+        if (p == 0) {
+            k_smooth0<T><<<g, TB, 0, st>>>(nf, wk.t, ec, lv.W.p, ef, T(lv.alpha[0]));
+            continue;
+        }
+        T* win = wk.wa;
+        T* wout = wk.wb;
+        for (int k = p - 1; k >= 1; --k) {
+            k_horner<T><<<g, TB, 0, st>>>(view(o.Aff), wk.t, win, wout, T(lv.alpha[k]));
+            std::swap(win, wout);
+        }
+        k_horner_last<T><<<g, TB, 0, st>>>(view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0]));
+    }
+    CK_LAUNCH();
+}
+
+long long sell_bytes(long long nnz, int n_rows, int vbytes)
+{
+    // values + column indices + one read of the input gathered + one write
+    return nnz * (vbytes + 4) + 2LL * n_rows * vbytes;
+}
+
+}  // namespace
+
+// ===========================================================================
+void build_solve_data(Hierarchy& H, cudaStream_t st)
+{
+    auto S = std::make_unique<SolveData>();
+    const int L = int(H.levels.size());
+    S->nlev = L;
+    S->n0 = L ? H.levels[0]->n : H.coarse.A.n_rows;
+    // offsets
+    std::vector<int> off(L + 1, 0);
+    for (int l = 0; l < L; ++l) off[l + 1] = off[l] + H.levels[l]->n_f;
+    S->off_c = off[L];
+    S->n_coarse = H.coarse.A.n_rows;
+    // nested positions, coarsest upward
+    std::vector<DBuf<int>> pos(L + 1);
+    pos[L].alloc(std::max(S->n_coarse, 1));
+    if (S->n_coarse) k_pos_coarse<<<grid_for(S->n_coarse, TB), TB, 0, st>>>(S->n_coarse, off[L], pos[L].p);
+    for (int l = L - 1; l >= 0; --l) {
+        SetupLevel& lv = *H.levels[l];
+        pos[l].alloc(lv.n);
+        k_pos_level<<<grid_for(lv.n, TB), TB, 0, st>>>(lv.n, lv.is_f.p, lv.f_index.p, lv.c_index.p,
+                                                       off[l], pos[l + 1].p, pos[l].p);
+    }
+    CK_LAUNCH();
+    // level operators
+    long long bytes = 0;
+    for (int l = 0; l < L; ++l) {
+        SetupLevel& lv = *H.levels[l];
+        auto sl = std::make_unique<SolveLevel>();
+        sl->off = off[l];
+        sl->n_f = lv.n_f;
+        sl->n_c = lv.n_c;
+        sl->alpha = lv.alpha;
+        // relative C positions: rel[c] = pos_{l+1}[c] - off_{l+1}; inv: row of Z'
+        DBuf<int> rel(std::max(lv.n_c, 1)), inv(std::max(lv.n_c, 1));
+        if (lv.n_c)
+            k_rel<<<grid_for(lv.n_c, TB), TB, 0, st>>>(lv.n_c, pos[l + 1].p, off[l + 1], rel.p, inv.p);
+        build_sell<double>(lv.A_ff, nullptr, nullptr, lv.n_f, sl->d.Aff, st);
+        build_sell<double>(lv.M, nullptr, rel.p, lv.n_c, sl->d.M, st);
+        build_sell<double>(lv.Z, inv.p, nullptr, lv.n_f, sl->d.Z, st);
+        sl->W.alloc(std::max(lv.n_f, 1));
+        if (lv.n_f) k_map_w<<<grid_for(lv.n_f, TB), TB, 0, st>>>(lv.n_f, lv.W.p, rel.p, sl->W.p);
+        CK_LAUNCH();
+        if (H.opt.precision == AIRG_MIXED_FP32) {
+            copy_sell_f32(sl->d.Aff, sl->f.Aff, st);
+            copy_sell_f32(sl->d.M, sl->f.M, st);
+            copy_sell_f32(sl->d.Z, sl->f.Z, st);
+        }
+        int vb = H.opt.precision == AIRG_MIXED_FP32 ? 4 : 8;
+        int p = int(lv.alpha.size()) - 1;
+        bytes += sell_bytes(lv.Z.nnz, lv.n_c, vb) + sell_bytes(lv.M.nnz, lv.n_f, vb) + 4LL * lv.n_f +
+                 p * sell_bytes(lv.A_ff.nnz, lv.n_f, vb) + 2LL * lv.n_f * vb;
+        S->max_nf = std::max(S->max_nf, lv.n_f);
+        CK(cudaStreamSynchronize(st));
+        S->lv.push_back(std::move(sl));
+    }
+    build_sell<double>(H.coarse.A, nullptr, nullptr, S->n_coarse, S->Ac, st);
+    if (H.opt.precision == AIRG_MIXED_FP32) copy_sell_f32(S->Ac, S->Ac32, st);
+    S->roots = H.coarse.roots;
+    {
+        int vb = H.opt.precision == AIRG_MIXED_FP32 ? 4 : 8;
+        long long nsp = 0;
+        for (size_t i = 0; i < S->roots.size(); ++i) {
+            bool last = i + 1 == S->roots.size();
+            nsp += S->roots[i].im == 0.0 ? (last ? 0 : 1) : (last ? 1 : 2);
+        }
+        bytes += nsp * sell_bytes(H.coarse.A.nnz, S->n_coarse, vb);
+    }
+    S->bytes_vcycle = bytes;
+    // top operator in the nested order: row pos0[i] <- natural row i
+    const DevCSR& A0 = L ? H.levels[0]->A : H.coarse.A;
+    S->pos0 = std::move(pos[0]);
+    {
+        DBuf<int> inv0(std::max(S->n0, 1));
+        DBuf<int> dummy(std::max(S->n0, 1));
+        if (S->n0) k_rel<<<grid_for(S->n0, TB), TB, 0, st>>>(S->n0, S->pos0.p, 0, dummy.p, inv0.p);
+        CK_LAUNCH();
+        build_sell<double>(A0, inv0.p, S->pos0.p, S->n0, S->Atop, st);
+        CK(cudaStreamSynchronize(st));
+    }
+    // work vectors
+    size_t n0 = std::max(S->n0, 1), nf = std::max(S->max_nf, 1), nc = std::max(S->n_coarse, 1);
+    S->rwork.alloc(n0);
+    S->t.alloc(nf); S->wa.alloc(nf); S->wb.alloc(nf);
+    S->cr0.alloc(nc); S->cr1.alloc(nc); S->ct.alloc(nc);
+    if (H.opt.precision == AIRG_MIXED_FP32) {
+        S->rwork32.alloc(n0); S->e32.alloc(n0); S->vin32.alloc(n0);
+        S->t32.alloc(nf); S->wa32.alloc(nf); S->wb32.alloc(nf);
+        S->cr032.alloc(nc); S->cr132.alloc(nc); S->ct32.alloc(nc);
+    }
+    S->restart = std::max(1, H.opt.gmres_restart);
+    int m = S->restart;
+    S->V.alloc(size_t(m + 1) * n0);
+    S->Zs.alloc(size_t(m) * n0);
+    S->w.alloc(n0); S->bp.alloc(n0); S->xp.alloc(n0); S->r.alloc(n0);
+    S->part.alloc(size_t(RGRID) * (m + 2));
+    S->hdev.alloc(size_t(3 * (m + 2)));
+    S->hhost.alloc(size_t(3 * (m + 2)));
+    H.solve = std::move(S);
+}
+
+namespace {
+
+double dev_norm(SolveData& S, const double* x, long long n, cudaStream_t st)
+{
+    k_multidot<<<RGRID, RB, 0, st>>>(n, 1, x, n, x, S.part.p);
+    k_sum_parts<<<1, 32, 0, st>>>(RGRID, 1, S.part.p, S.hdev.p);
+    CK_LAUNCH();
+    double v = read1(S.hdev.p, st);
+    return std::sqrt(v);
+}
+
+void precond(Hierarchy& H, const double* v, double* z, cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    long long n = S.n0;
+    if (H.opt.precision == AIRG_MIXED_FP32) {
+        k_d2f<<<grid_for(n, TB), TB, 0, st>>>(n, v, S.vin32.p);
+        VWork<float> wk{S.rwork32.p, S.t32.p, S.wa32.p, S.wb32.p, nullptr, S.cr032.p, S.cr132.p, S.ct32.p};
+        vcycle<float>(S, S.vin32.p, S.e32.p, wk, st);
+        k_f2d<<<grid_for(n, TB), TB, 0, st>>>(n, S.e32.p, z);
+        CK_LAUNCH();
+    } else {
+        VWork<double> wk{S.rwork.p, S.t.p, S.wa.p, S.wb.p, nullptr, S.cr0.p, S.cr1.p, S.ct.p};
+        vcycle<double>(S, v, z, wk, st);
+    }
+}
+
+// FGMRES(m) on the nested system; bp/xp hold b and x in nested order.
+void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& info,
+            cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    long long n = S.n0;
+    int m = S.restart;
+    int g = grid_for(n, TB);
+    SellView<double> A = view(S.Atop);
+    double bn = dev_norm(S, S.bp.p, n, st);
+    double tol = std::max(rtol * bn, atol);
+    int its = 0;
+    auto residual = [&]() {
+        k_spmv<double><<<g, TB, 0, st>>>(A, S.xp.p, S.w.p);
+        k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p);
+        CK_LAUNCH();
+        return dev_norm(S, S.r.p, n, st);
+    };
+    double rn = residual();
+    std::vector<double> Hm(size_t(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+    double* hh = S.hhost.p;
+    while (rn > tol && its < maxit) {
+        k_scale_into<<<g, TB, 0, st>>>(n, S.r.p, 1.0 / rn, S.V.p);
+        std::fill(gv.begin(), gv.end(), 0.0);
+        gv[0] = rn;
+        int jdone = 0;
+        for (int j = 0; j < m; ++j) {
+            double* vj = S.V.p + size_t(j) * n;
+            double* zj = S.Zs.p + size_t(j) * n;
+            precond(H, vj, zj, st);
+            k_spmv<double><<<g, TB, 0, st>>>(A, zj, S.w.p);
+            // classical Gram-Schmidt, twice
+            for (int pass = 0; pass < 2; ++pass) {
+                k_multidot<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, S.w.p, S.part.p);
+                k_sum_parts<<<1, 32, 0, st>>>(RGRID, j + 1, S.part.p, S.hdev.p + pass * (m + 2));
+                k_multiaxpy<<<g, TB, 0, st>>>(n, j + 1, S.V.p, n, S.hdev.p + pass * (m + 2), S.w.p);
+            }
+            k_multidot<<<RGRID, RB, 0, st>>>(n, 1, S.w.p, n, S.w.p, S.part.p);
+            k_sum_parts<<<1, 32, 0, st>>>(RGRID, 1, S.part.p, S.hdev.p + 2 * (m + 2));
+            CK_LAUNCH();
+            CK(cudaMemcpyAsync(hh, S.hdev.p, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            for (int i = 0; i <= j; ++i) Hm[size_t(i) * m + j] = hh[i] + hh[(m + 2) + i];
+            double hn = std::sqrt(std::max(hh[2 * (m + 2)], 0.0));
+            Hm[size_t(j + 1) * m + j] = hn;
+            for (int i = 0; i < j; ++i) {
+                double a = Hm[size_t(i) * m + j], b = Hm[size_t(i + 1) * m + j];
+                Hm[size_t(i) * m + j] = cs[i] * a + sn[i] * b;
+                Hm[size_t(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+            }
+            double a = Hm[size_t(j) * m + j], b = Hm[size_t(j + 1) * m + j];
+            double den = std::hypot(a, b);
+            cs[j] = den > 0 ? a / den : 1.0;
+            sn[j] = den > 0 ? b / den : 0.0;
+            Hm[size_t(j) * m + j] = den;
+            Hm[size_t(j + 1) * m + j] = 0.0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            ++its;
+            jdone = j + 1;
+            if (std::fabs(gv[j + 1]) <= tol || its >= maxit || den == 0.0 || hn == 0.0) break;
+            k_scale_into<<<g, TB, 0, st>>>(n, S.w.p, 1.0 / hn, S.V.p + size_t(j + 1) * n);
+        }
+        for (int j = jdone - 1; j >= 0; --j) {
+            double s = gv[j];
+            for (int i = j + 1; i < jdone; ++i) s -= Hm[size_t(j) * m + i] * y[i];
+            y[j] = s / Hm[size_t(j) * m + j];
+        }
+        h2d(S.hdev.p, y.data(), jdone, st);
+        k_multiaxpy_plus<<<g, TB, 0, st>>>(n, jdone, S.Zs.p, n, S.hdev.p, S.xp.p);
+        CK_LAUNCH();
+        rn = residual();
+    }
+    info.iterations = std::max(info.iterations, its);
+    double rel = bn > 0 ? rn / bn : 0.0;
+    info.rel_residual = std::max(info.rel_residual, rel);
+    info.converged = info.converged && (rn <= tol);
+}
+
+}  // namespace
+
+void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_device, double rtol,
+                  double atol, int maxit, airg_solve_info* info_out, cudaStream_t st)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    SolveData& S = *H.solve;
+    long long n = S.n0;
+    airg_solve_info info{};
+    info.converged = 1;
+    DBuf<double> bd, xd;
+    const double* bdev = b;
+    double* xdev = x;
+    if (!on_device) {
+        bd.alloc(size_t(n) * nrhs);
+        xd.alloc(size_t(n) * nrhs);
+        h2d(bd.p, b, size_t(n) * nrhs, st);
+        h2d(xd.p, x, size_t(n) * nrhs, st);
+        bdev = bd.p;
+        xdev = xd.p;
+    }
+    int g = grid_for(n, TB);
+    for (int q = 0; q < nrhs; ++q) {
+        k_to_nested<<<g, TB, 0, st>>>(n, S.pos0.p, bdev + size_t(q) * n, S.bp.p);
+        k_to_nested<<<g, TB, 0, st>>>(n, S.pos0.p, xdev + size_t(q) * n, S.xp.p);
+        CK_LAUNCH();
+        fgmres(H, rtol, atol, maxit, info, st);
+        k_from_nested<<<g, TB, 0, st>>>(n, S.pos0.p, S.xp.p, xdev + size_t(q) * n);
+        CK_LAUNCH();
+    }
+    if (!on_device) {
+        CK(cudaMemcpyAsync(x, xd.p, sizeof(double) * n * nrhs, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    info.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info_out) *info_out = info;
+    if (!info.converged) fail(AIRG_ERR_NOT_CONVERGED, "FGMRES did not reach the tolerance within maxit");
+}
+
+void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info)
+{
+    std::memset(info, 0, sizeof *info);
+    int L = int(H.levels.size());
+    info->levels = L + 1;
+    info->truncated = H.coarse.truncated ? 1 : 0;
+    info->coarse_roots = int(H.coarse.roots.size());
+    info->setup_ms = H.setup_ms;
+    long long top = L ? H.levels[0]->A.nnz : H.coarse.A.nnz;
+    long long store = top, flops = 0;
+    for (int l = 0; l < L && l < 63; ++l) {
+        const SetupLevel& lv = *H.levels[l];
+        info->n[l] = lv.n;
+        info->n_f[l] = lv.n_f;
+        info->nnz_a[l] = lv.A.nnz;
+        int p = int(lv.alpha.size()) - 1;
+        // kept for the solve: A_ff, A_fc, R = [Z I], P = [W; I] (Sec. 3)
+        long long np = lv.n_c;
+        for (int i = 0; i < 1; ++i) (void)i;
+        store += lv.A_ff.nnz + lv.A_fc.nnz + (lv.Z.nnz + lv.n_c) + (lv.n_f + np);
+        flops += 2LL * lv.Z.nnz + 2LL * lv.A_fc.nnz + 2LL * lv.A_ff.nnz * (p + 1);
+    }
+    if (L < 64) {
+        info->n[L] = H.coarse.A.n_rows;
+        info->nnz_a[L] = H.coarse.A.nnz;
+    }
+    store += H.coarse.A.nnz;
+    long long nsp = 0;
+    for (size_t i = 0; i < H.coarse.roots.size(); ++i) {
+        bool last = i + 1 == H.coarse.roots.size();
+        nsp += H.coarse.roots[i].im == 0.0 ? (last ? 0 : 1) : (last ? 1 : 2);
+    }
+    flops += 2LL * H.coarse.A.nnz * nsp;
+    info->storage_complexity = top ? double(store) / double(top) : 0.0;
+    info->cycle_complexity = top ? double(flops) / (2.0 * double(top)) : 0.0;
+    info->bytes_per_vcycle = H.solve ? H.solve->bytes_vcycle : 0;
+}
+
+}  // namespace airg

@@ -1,0 +1,91 @@
+"""Seeded synthetic workloads shared by the oracle tests, the GPU tests and
+the benchmark.  Holds no arithmetic of the method: only the draws of the
+velocity angle, inflow values, sources and targets, with the shapes and
+distributions of the paper's structured-grid experiments (Sec. 3): a square
+[0,1]^2 node grid, constant velocity direction, inflow data on the two inflow
+edges.  Seeds are 2508175 + workload number.
+
+Options carry the solver settings of each workload (paper defaults, Sec. 3,
+unless the workload overrides them).
+"""
+import math
+
+import numpy as np
+
+BASE_SEED = 2508175
+
+
+def _n_inflow(nx, ny, theta):
+    vx, vy = math.cos(theta), math.sin(theta)
+    return (ny if vx != 0 else 0) + (nx if vy != 0 else 0) - (1 if vx != 0 and vy != 0 else 0)
+
+
+def workload(name, n=None):
+    """Returns dict(nx, ny, theta, g (n_rhs x n_inflow), s (n_rhs x n or None),
+    opts (dict), rtol, n_rhs, desc)."""
+    if name == "c1":
+        # 64x64, theta = 3 pi/8, g = 1, s = 0, order-4 smoother; exact answer u = 1
+        nx = ny = n or 64
+        th = 3 * math.pi / 8
+        g = np.ones((1, _n_inflow(nx, ny, th)))
+        return dict(nx=nx, ny=ny, theta=th, g=g, s=None, n_rhs=1, rtol=1e-10,
+                    opts=dict(poly_order=4, trunc_start_level=2),
+                    desc="%dx%d theta=3pi/8 g=1 s=0 p=4" % (nx, ny))
+    if name == "c2":
+        # 1024x1024, theta ~ U[pi/12, 5pi/12], g ~ U[0.5, 2] per inflow node,
+        # truncation with a coarse polynomial of order 30 at tolerance 1e-2
+        nx = ny = n or 1024
+        rng = np.random.default_rng(BASE_SEED + 2)
+        th = float(rng.uniform(math.pi / 12, 5 * math.pi / 12))
+        g = rng.uniform(0.5, 2.0, (1, _n_inflow(nx, ny, th)))
+        return dict(nx=nx, ny=ny, theta=th, g=g, s=None, n_rhs=1, rtol=1e-10,
+                    opts=dict(coarse_poly_order=30, trunc_rtol=1e-2),
+                    desc="%dx%d theta~U[pi/12,5pi/12] g~U[0.5,2] m_c=30 trunc=1e-2" % (nx, ny))
+    if name == "c3":
+        # 4096x4096, seeded theta, g ~ U[0,1] per inflow node; FP32 V-cycle
+        nx = ny = n or 4096
+        rng = np.random.default_rng(BASE_SEED + 3)
+        th = float(rng.uniform(math.pi / 12, 5 * math.pi / 12))
+        g = rng.uniform(0.0, 1.0, (1, _n_inflow(nx, ny, th)))
+        return dict(nx=nx, ny=ny, theta=th, g=g, s=None, n_rhs=1, rtol=1e-10,
+                    opts=dict(coarse_poly_order=30, trunc_rtol=1e-2, precision=1),
+                    desc="%dx%d theta seeded g~U[0,1] FP32 V-cycle" % (nx, ny))
+    if name == "c4a":
+        # 2048x2048, one operator, 64 right-hand sides: g ~ U[0,1], s ~ N(0,1)
+        nx = ny = n or 2048
+        rng = np.random.default_rng(BASE_SEED + 4)
+        th = float(rng.uniform(math.pi / 12, 5 * math.pi / 12))
+        k = 64
+        g = rng.uniform(0.0, 1.0, (k, _n_inflow(nx, ny, th)))
+        s = rng.standard_normal((k, nx * ny))
+        return dict(nx=nx, ny=ny, theta=th, g=g, s=s, n_rhs=k, rtol=1e-8,
+                    opts=dict(coarse_poly_order=30, trunc_rtol=1e-2),
+                    desc="%dx%d 64 rhs g~U[0,1] s~N(0,1)" % (nx, ny))
+    if name == "c5":
+        # 1024x1024 adjoint workload: g ~ U[0,1], s ~ N(0,1), target u_t ~ N(1, 0.1^2)
+        nx = ny = n or 1024
+        rng = np.random.default_rng(BASE_SEED + 5)
+        th = float(rng.uniform(math.pi / 12, 5 * math.pi / 12))
+        g = rng.uniform(0.0, 1.0, (1, _n_inflow(nx, ny, th)))
+        s = rng.standard_normal((1, nx * ny)).astype(np.float32).astype(np.float64)
+        ut = rng.normal(1.0, 0.1, nx * ny)
+        dirs_g = rng.standard_normal((32, g.shape[1]))
+        dirs_s = rng.standard_normal((32, nx * ny))
+        return dict(nx=nx, ny=ny, theta=th, g=g, s=s, ut=ut, dirs_g=dirs_g, dirs_s=dirs_s,
+                    n_rhs=1, rtol=1e-10, opts=dict(coarse_poly_order=30, trunc_rtol=1e-2),
+                    desc="%dx%d adjoint L=sum(u-u_t)^2" % (nx, ny))
+    if name == "grid":
+        # generic seeded grid of given size for parity cases
+        nx, ny = n if isinstance(n, tuple) else (n, n)
+        rng = np.random.default_rng(BASE_SEED + 100 + nx + 7 * ny)
+        th = float(rng.uniform(math.pi / 12, 5 * math.pi / 12))
+        g = rng.uniform(0.0, 1.0, (1, _n_inflow(nx, ny, th)))
+        s = rng.standard_normal((1, nx * ny))
+        return dict(nx=nx, ny=ny, theta=th, g=g, s=s, n_rhs=1, rtol=1e-10,
+                    opts=dict(coarse_poly_order=30, trunc_rtol=1e-2),
+                    desc="%dx%d seeded" % (nx, ny))
+    raise KeyError(name)
+
+
+def velocity(theta):
+    return math.cos(theta), math.sin(theta)

@@ -1,0 +1,89 @@
+"""CPU-only checks of the CUDA library: it loads, exports every entry point
+declared in include/airg.h, and its host-side FP64 steps agree with the
+oracle (no GPU calls)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2508_17517_gb300 as G
+from oracle import airg as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    G.build()
+    return G.lib()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "airg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(airg_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_declares_binding_names():
+    assert _declared() == sorted(G.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_options_default_are_paper_values(L):
+    o = G.airg_options_default()
+    assert (o.strong_threshold, o.ddc_fraction, o.ddc_its, o.poly_order) == (0.99, 0.01, 2, 6)
+    assert (o.coarse_poly_order, o.trunc_rtol, o.a_drop, o.a_lump) == (100, 0.1, 1e-6, 1)
+    d = O.Options()
+    assert (o.r_drop, o.seed, o.breakdown_tol) == (d.r_drop, d.seed, d.breakdown_tol)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_host_gmres_coeffs_bitwise_equal_to_oracle(L, seed):
+    """The host least-squares + recurrence performs the same IEEE operations
+    as the oracle, so the coefficients agree bit for bit."""
+    rng = np.random.default_rng(seed)
+    k = [1, 2, 3, 5, 7, 7][seed]
+    if seed < 4:
+        H = np.triu(rng.standard_normal((k + 1, k)), -1)
+        H[np.arange(1, k + 1), np.arange(k)] = np.abs(H[np.arange(1, k + 1), np.arange(k)]) + 0.1
+        beta = float(rng.random() + 0.5)
+    else:
+        A, _ = _dd(40, seed)
+        b = O.rng_uniform(seed, 0, O.PURPOSE_COEF, 40)
+        H, k2, broke, beta = O.arnoldi(A, b, k, 1e-8)
+        assert k2 == k
+    y = O.givens_lsq(H, beta)
+    ref = np.array(O.power_coefficients(H, beta, y))
+    got = G.airg_host_gmres_coeffs(H, beta)
+    assert np.array_equal(got, ref)
+
+
+def _dd(n, seed):
+    rng = np.random.default_rng(seed)
+    D = np.diag(2.0 + rng.random(n))
+    D = D + np.where((rng.random((n, n)) < 0.15) & ~np.eye(n, dtype=bool), rng.uniform(-0.3, 0.3, (n, n)), 0)
+    r, c = np.nonzero(D)
+    return O.csr_from_entries(n, n, r, c, D[r, c]), D
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 6, 17, 40, 100])
+def test_host_eigvals_match_lapack(L, n):
+    rng = np.random.default_rng(n)
+    H = np.triu(rng.standard_normal((n, n)), -1)
+    got = np.sort_complex(G.airg_host_eigvals(H))
+    ref = np.sort_complex(np.linalg.eigvals(H))
+    assert np.allclose(got, ref, rtol=1e-8, atol=1e-9 * max(1.0, np.abs(ref).max()))
+
+
+def test_host_eigvals_of_arnoldi_hessenberg(L):
+    A, D = _dd(60, 3)
+    b = O.rng_uniform(1, 0, O.PURPOSE_COARSE, 60)
+    H, k, broke, beta = O.arnoldi(A, b, 20, 1e-8)
+    got = np.sort_complex(G.airg_host_eigvals(H[:k, :k]))
+    ref = np.sort_complex(np.linalg.eigvals(H[:k, :k]))
+    assert np.allclose(got, ref, rtol=1e-9, atol=1e-10)

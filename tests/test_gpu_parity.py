@@ -1,0 +1,199 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Setup products must match bit for bit: CF splitting, every sparsity pattern
+and, by construction (fixed operation order, correctly rounded dots), every
+value.  The coarse-grid roots come from two different eigenvalue solvers and
+are compared with a tolerance.  Solutions must agree with the oracle to
+1e-9 relative L2 at rtol 1e-10, with the true residual at or below rtol.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2508_17517_gb300 as G  # noqa: E402
+from oracle import airg as O  # noqa: E402
+from synthetic import velocity, workload  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    G.build()
+    G.lib()
+
+
+def _oopts(d):
+    return O.Options(**{k: v for k, v in d.items() if k != "precision"})
+
+
+def _csr_equal(M, exp, what, exact_values=True):
+    nr, nc, rp, ci, v = exp
+    assert (nr, nc) == (M.n_rows, M.n_cols), what
+    assert np.array_equal(rp, M.rowptr), what + " rowptr"
+    assert np.array_equal(ci.astype(np.int64), M.col), what + " pattern"
+    if exact_values:
+        bad = np.nonzero(v != M.val)[0]
+        assert bad.size == 0, "%s values differ at %d entries, max rel %.3e" % (
+            what, bad.size, np.max(np.abs(v[bad] - M.val[bad]) / np.maximum(np.abs(M.val[bad]), 1e-300)))
+
+
+class Case:
+    def __init__(self, w, opts_over=None):
+        self.w = w
+        o = dict(w["opts"])
+        o.update(opts_over or {})
+        self.o = o
+        vx, vy = velocity(w["theta"])
+        self.po = O.advection_2d(w["nx"], w["ny"], vx, vy)
+        self.pg = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
+        self.Ho = O.setup(self.po.A, _oopts(o))
+        self.h = G.airg_setup(self.pg["rowptr"], self.pg["col"], self.pg["val"],
+                              G.airg_options_default(**o))
+
+
+def _check_setup(c):
+    Ho, h = c.Ho, c.h
+    info = G.airg_setup_info(h)
+    assert info["levels"] == len(Ho.levels) + 1
+    assert info["truncated"] == Ho.truncated
+    for l, L in enumerate(Ho.levels):
+        cf = G.airg_export_vector(h, l, 0).astype(bool)
+        assert np.array_equal(cf, L.is_f), "CF split level %d" % l
+        _csr_equal(L.A, G.airg_export_matrix(h, l, 0), "A_%d" % l)
+        _csr_equal(L.A_ff, G.airg_export_matrix(h, l, 1), "A_ff level %d" % l)
+        _csr_equal(L.A_fc, G.airg_export_matrix(h, l, 2), "A_fc level %d" % l)
+        _csr_equal(L.Z, G.airg_export_matrix(h, l, 3), "Z level %d" % l)
+        assert np.array_equal(G.airg_export_vector(h, l, 1), L.W), "W level %d" % l
+        assert np.array_equal(G.airg_export_vector(h, l, 2), L.alpha), "alpha level %d" % l
+        sc = G.airg_export_vector(h, l, 4)
+        assert int(sc[0]) == L.pmisr_rounds
+        assert [int(x) for x in sc[1:-2]] == list(L.ddc_converted)
+    _csr_equal(Ho.A_coarse, G.airg_export_matrix(h, len(Ho.levels), 0), "A_coarse")
+    r = G.airg_export_vector(h, len(Ho.levels), 3).reshape(-1, 2)
+    ro = np.array(Ho.roots)
+    assert r.shape == ro.shape
+    zg = np.sort_complex(r[:, 0] + 1j * r[:, 1])
+    zo = np.sort_complex(ro[:, 0] + 1j * ro[:, 1])
+    assert np.allclose(zg, zo, rtol=1e-6, atol=1e-8 * np.abs(zo).max())
+
+
+def _check_solve(c, rtol=None, host=False):
+    w = c.w
+    rtol = rtol or w["rtol"]
+    s = w["s"][0] if w["s"] is not None else np.zeros(c.po.A.n_rows)
+    bo = O.assemble_rhs(c.po, w["g"][0], s)
+    gt = torch.tensor(w["g"][0], device="cuda")
+    st = torch.tensor(s, device="cuda")
+    bg = G.airg_assemble_rhs_advection2d(c.pg, gt, st)
+    assert np.array_equal(bg.cpu().numpy(), bo)
+    xo, io = O.solve(c.Ho, c.po.A, bo, rtol=rtol)
+    if host:
+        bh = torch.tensor(bo)
+        xg, ig = G.airg_solve(c.h, bh, rtol=rtol)
+        xg = xg.numpy()
+    else:
+        xg, ig = G.airg_solve(c.h, bg, rtol=rtol)
+        xg = xg.cpu().numpy()
+    res = np.linalg.norm(bo - O.spmv(c.po.A, xg)) / np.linalg.norm(bo)
+    assert ig.converged and res <= rtol * (1 + 1e-6)
+    rel = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    assert rel <= 1e-9, "GPU vs oracle rel L2 %.3e" % rel
+    u = O.sweep_solve(c.po.A, bo, O.sweep_order(c.po))
+    assert np.linalg.norm(xg - u) / np.linalg.norm(u) <= 1e-9
+    return xg, ig, io
+
+
+# ------------------------------------------------------------ primitives --
+def test_exact_dot_bitwise():
+    rng = np.random.default_rng(0)
+    for n in [1, 7, 1000, 100003, 3_000_001]:
+        x = rng.standard_normal(n) * np.exp2(rng.integers(-40, 40, n))
+        y = rng.standard_normal(n)
+        got = G.airg_dot_exact(torch.tensor(x, device="cuda"), torch.tensor(y, device="cuda"))
+        assert got == O.xdot(x, y)
+    assert G.airg_dot_exact(torch.zeros(5, device="cuda", dtype=torch.float64),
+                            torch.ones(5, device="cuda", dtype=torch.float64)) == 0.0
+
+
+def test_rng_bitwise():
+    for lev, pur, n in [(0, 1, 10), (3, 2, 100001), (7, 4, 1)]:
+        g = G.airg_rng_uniform(2508175, lev, pur, n).cpu().numpy()
+        assert np.array_equal(g, O.rng_uniform(2508175, lev, pur, n))
+
+
+@pytest.mark.parametrize("theta", [3 * math.pi / 8, 0.0, math.pi / 2 + 0.3, 3.7, 5.5])
+def test_builder_bitwise(theta):
+    vx, vy = velocity(theta)
+    po = O.advection_2d(37, 23, vx, vy)
+    pg = G.airg_problem_advection2d(37, 23, vx, vy)
+    assert np.array_equal(pg["rowptr"].cpu().numpy(), po.A.rowptr)
+    assert np.array_equal(pg["col"].cpu().numpy().astype(np.int64), po.A.col)
+    assert np.array_equal(pg["val"].cpu().numpy(), po.A.val)
+    assert np.array_equal(pg["inflow"].cpu().numpy(), po.inflow)
+
+
+# ----------------------------------------------------------- full paths --
+def test_c1_setup_and_solve():
+    c = Case(workload("c1"))
+    _check_setup(c)
+    xg, ig, io = _check_solve(c)
+    assert np.max(np.abs(xg - 1.0)) < 1e-8          # Eq. 1-2: u = g = 1
+    assert abs(ig.iterations - io.iterations) <= 1
+
+
+@pytest.mark.parametrize("shape", [(203, 157), (96, 331)])
+def test_ragged_grids(shape):
+    c = Case(workload("grid", shape))
+    _check_setup(c)
+    _check_solve(c)
+
+
+def test_host_buffer_path():
+    c = Case(workload("grid", (120, 90)))
+    _check_solve(c, host=True)
+
+
+def test_grid_aligned_exact():
+    w = workload("grid", (48, 40))
+    w["theta"] = 0.0
+    w["g"] = np.random.default_rng(1).random((1, 40))
+    c = Case(w, dict(trunc_rtol=0.0, coarse_min_rows=40))
+    _check_setup(c)
+    xg, ig, io = _check_solve(c)
+    assert ig.iterations <= 2
+
+
+def test_pure_polynomial_and_level0_truncation():
+    w = workload("grid", (40, 40))
+    c = Case(w, dict(max_levels=1, coarse_poly_order=100))
+    _check_setup(c)
+    _check_solve(c)
+    c2 = Case(w, dict(trunc_rtol=0.5, coarse_poly_order=100))
+    _check_setup(c2)
+    assert c2.Ho.truncated
+
+
+def test_tiny_grid():
+    c = Case(workload("grid", (2, 3)))
+    _check_setup(c)
+    _check_solve(c)
+
+
+def test_mixed_precision_fp32_vcycle():
+    w = workload("grid", (256, 200))
+    c = Case(w, dict(precision=1))
+    _check_setup(c)
+    _check_solve(c)
+
+
+def test_c2_full_size():
+    """The 1024x1024 workload of the benchmark, complete comparison."""
+    c = Case(workload("c2"))
+    _check_setup(c)
+    _check_solve(c)
