@@ -75,6 +75,9 @@ typedef struct {
     double r_drop;             /* relative drop tolerance on R                */
     uint64_t seed;             /* seed of all random streams of the setup     */
     double breakdown_tol;      /* Arnoldi rank threshold on h_{j+1,j}         */
+    double exact_tol;          /* Arnoldi stops once the GMRES residual of its
+                                  least-squares problem is <= exact_tol*||b||
+                                  (the polynomial already inverts exactly)   */
     double addroot_log10;      /* extra-root threshold on log10(pof)          */
     double addroot_per;        /* decades of pof per extra root               */
     int precision;             /* AIRG_FP64 or AIRG_MIXED_FP32 (V-cycle)      */
@@ -88,6 +91,7 @@ typedef struct {
     double rel_residual;       /* true ||b - A x||_2 / ||b||_2 at exit        */
     int converged;             /* 1 if rel_residual test met                  */
     double solve_ms;           /* wall time of the call                       */
+    int64_t kernel_launches;   /* CUDA kernels this call launched             */
 } airg_solve_info;
 
 typedef struct {
@@ -201,6 +205,22 @@ airg_status airg_export_matrix(const airg_handle* h, int level, int what, int64_
  */
 airg_status airg_export_vector(const airg_handle* h, int level, int what, int64_t* count,
                                void* out);
+
+/*
+ * Per-kernel timing of the solve phase.  airg_profile(h, 1) makes every
+ * kernel that airg_solve launches record a CUDA event before and after it on
+ * the solve's stream, and clears the totals; airg_profile(h, 0) stops
+ * recording.  airg_profile_read returns, for one kind of kernel, the summed
+ * event time (ms), the number of launches and the algorithmic bytes those
+ * launches move (stored entries, column indices and each vector read or
+ * written once; padding excluded).  Kinds: 0 restriction, 1 F-point
+ * residual, 2 F-point smoother (Horner terms), 3 coarse Newton steps,
+ * 4 top-level SpMV of FGMRES, 5 FGMRES vector work, 6 layout / precision
+ * conversions.  Outputs are HOST pointers.
+ */
+airg_status airg_profile(airg_handle* h, int enable);
+airg_status airg_profile_read(const airg_handle* h, int kind, double* ms, int64_t* launches,
+                              int64_t* bytes);
 
 /* Releases every device and host buffer of the handle.  NULL is a no-op. */
 void airg_free(airg_handle* h);

@@ -229,6 +229,7 @@ class Options:
     r_drop: float = 1e-2             # parity unpinned: the paper gives no value
     seed: int = 2508175
     breakdown_tol: float = 1e-8      # rank reading of Sec. 2.3: h_{j+1,j} <= tol * ||H(:,j)||
+    exact_tol: float = 1e-12         # rank reading of Sec. 2.3: GMRES residual <= tol * beta
     addroot_log10: float = 4.0       # Loe-Morgan extra-root threshold (unpinned)
     addroot_per: float = 14.0
 
@@ -365,13 +366,17 @@ def extract(A, row_mask, col_mask):
 # --------------------------------------------------------------------------
 # GMRES polynomials (Sec. 2.2, Eq. 4)
 # --------------------------------------------------------------------------
-def arnoldi(A, b, m, breakdown_tol):
+def arnoldi(A, b, m, breakdown_tol, exact_tol=1e-12):
     """m steps of modified Gram-Schmidt Arnoldi from b (x0 = 0).
 
     Dots are correctly rounded, norms are sqrt of those, updates are
     w - (h * v) with the product rounded first, and normalisation divides.
-    Breakdown reading: stop after step j when h_{j+1,j} <= tol * ||H(:,j)||,
-    the column norm summed in order.
+    Rank reading of Sec. 2.3 (higher-order terms are unstable once a lower
+    order already inverts exactly): stop after step j when
+    h_{j+1,j} <= breakdown_tol * ||H(:,j)|| (the column norm summed in
+    order; a breakdown), or when the GMRES residual of the Givens least
+    squares problem is <= exact_tol * beta (the polynomial is already an
+    exact inverse for b).
     Returns (H[(k+1) x k], k, broke, beta).
     """
     beta = xnorm(b)
@@ -394,13 +399,16 @@ def arnoldi(A, b, m, breakdown_tol):
             k = j + 1
             broke = True
             break
+        if givens_residual(H[:j + 2, :j + 1], beta) <= exact_tol * beta:
+            k = j + 1
+            break
         if j + 1 < m:
             V.append(w / hn)
     return H[:k + 1, :k].copy(), k, broke, beta
 
 
-def givens_lsq(H, beta):
-    """y = argmin || beta e1 - H y || for the (k+1) x k Hessenberg H (Givens QR)."""
+def _givens_qr(H, beta):
+    """Givens QR of the (k+1) x k Hessenberg H applied to beta e1."""
     k = H.shape[1]
     R = [[float(H[i, j]) for j in range(k)] for i in range(k + 1)]
     g = [0.0] * (k + 1)
@@ -420,6 +428,19 @@ def givens_lsq(H, beta):
         R[j + 1][j] = 0.0
         g[j + 1] = -sn[j] * g[j]
         g[j] = cs[j] * g[j]
+    return R, g
+
+
+def givens_residual(H, beta):
+    """|| beta e1 - H y || at the least-squares minimiser."""
+    R, g = _givens_qr(H, beta)
+    return abs(g[-1])
+
+
+def givens_lsq(H, beta):
+    """y = argmin || beta e1 - H y || for the (k+1) x k Hessenberg H (Givens QR)."""
+    k = H.shape[1]
+    R, g = _givens_qr(H, beta)
     y = [0.0] * k
     for j in range(k - 1, -1, -1):
         s = g[j]
@@ -463,7 +484,7 @@ def gmres_poly_coeffs(A_ff, opts, level):
     """
     p = opts.poly_order
     b = rng_uniform(opts.seed, level, PURPOSE_COEF, A_ff.n_rows)
-    H, k, broke, beta = arnoldi(A_ff, b, p + 1, opts.breakdown_tol)
+    H, k, broke, beta = arnoldi(A_ff, b, p + 1, opts.breakdown_tol, opts.exact_tol)
     y = givens_lsq(H, beta)
     alpha = power_coefficients(H, beta, y)
     return np.array(alpha + [0.0] * (p + 1 - k)), k, broke
@@ -626,7 +647,7 @@ def order_roots(theta, opts):
 
 def coarse_polynomial(A, opts, level, m):
     b1 = rng_uniform(opts.seed, level, PURPOSE_COARSE, A.n_rows)
-    H, k, broke, beta = arnoldi(A, b1, m, opts.breakdown_tol)
+    H, k, broke, beta = arnoldi(A, b1, m, opts.breakdown_tol, opts.exact_tol)
     theta = harmonic_ritz(H, k, broke)
     return order_roots(theta, opts), H, k, broke
 

@@ -25,7 +25,10 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_BREA
 EXPORTS = ["airg_options_default", "airg_problem_advection2d", "airg_assemble_rhs_advection2d",
            "airg_setup", "airg_solve", "airg_solve_adjoint", "airg_setup_info",
            "airg_export_matrix", "airg_export_vector", "airg_free", "airg_last_error",
-           "airg_dot_exact", "airg_rng_uniform", "airg_host_gmres_coeffs", "airg_host_eigvals"]
+           "airg_dot_exact", "airg_rng_uniform", "airg_host_gmres_coeffs", "airg_host_eigvals",
+           "airg_profile", "airg_profile_read"]
+PROFILE_KINDS = ["restrict", "f_residual", "f_smoother", "coarse_newton", "top_spmv",
+                 "krylov_vectors", "layout"]
 
 
 class airg_options(ctypes.Structure):
@@ -35,7 +38,8 @@ class airg_options(ctypes.Structure):
                 ("trunc_start_level", ctypes.c_int), ("max_levels", ctypes.c_int),
                 ("coarse_min_rows", ctypes.c_int), ("a_drop", ctypes.c_double),
                 ("a_lump", ctypes.c_int), ("r_drop", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("breakdown_tol", ctypes.c_double), ("addroot_log10", ctypes.c_double),
+                ("breakdown_tol", ctypes.c_double), ("exact_tol", ctypes.c_double),
+                ("addroot_log10", ctypes.c_double),
                 ("addroot_per", ctypes.c_double), ("precision", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int)]
 
@@ -48,7 +52,8 @@ class airg_csr(ctypes.Structure):
 
 class airg_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("converged", ctypes.c_int), ("solve_ms", ctypes.c_double)]
+                ("converged", ctypes.c_int), ("solve_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 class airg_hierarchy_info(ctypes.Structure):
@@ -95,6 +100,9 @@ def lib():
             "airg_rng_uniform": [ctypes.c_uint64, i64, i64, i64, vp, vp],
             "airg_host_gmres_coeffs": [ci, vp, f64, vp],
             "airg_host_eigvals": [ci, vp, vp, vp],
+            "airg_profile": [vp, ci],
+            "airg_profile_read": [vp, ci, ctypes.POINTER(f64), ctypes.POINTER(i64),
+                                  ctypes.POINTER(i64)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -253,6 +261,21 @@ def airg_free(handle):
     if handle.ptr:
         lib().airg_free(handle.ptr)
         handle.ptr = None
+
+
+def airg_profile(handle, enable):
+    _check(lib().airg_profile(handle.ptr, int(enable)))
+
+
+def airg_profile_read(handle):
+    """{kind: (ms, launches, algorithmic bytes)} for every kernel kind."""
+    out = {}
+    for k, name in enumerate(PROFILE_KINDS):
+        ms, nl, nb = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().airg_profile_read(handle.ptr, k, ctypes.byref(ms), ctypes.byref(nl),
+                                       ctypes.byref(nb)))
+        out[name] = (ms.value, nl.value, nb.value)
+    return out
 
 
 def airg_dot_exact(x, y, stream=None):

@@ -172,6 +172,7 @@ airg_status airg_options_default(airg_options* o)
     o->r_drop = 1e-2;
     o->seed = 2508175ULL;
     o->breakdown_tol = 1e-8;
+    o->exact_tol = 1e-12;
     o->addroot_log10 = 4.0;
     o->addroot_per = 14.0;
     o->precision = AIRG_FP64;
@@ -366,6 +367,27 @@ airg_status airg_export_vector(const airg_handle* h, int level, int what, int64_
             }
             default: airg::fail(AIRG_ERR_ARG, "bad vector id");
         }
+    });
+}
+
+airg_status airg_profile(airg_handle* h, int enable)
+{
+    return guarded([&] {
+        if (!h || !h->H || !h->H->solve) airg::fail(AIRG_ERR_STATE, "handle not set up");
+        airg::set_profiling(*h->H, enable != 0);
+    });
+}
+
+airg_status airg_profile_read(const airg_handle* h, int kind, double* ms, int64_t* launches,
+                              int64_t* bytes)
+{
+    return guarded([&] {
+        if (!h || !h->H || !h->H->solve || !ms || !launches || !bytes)
+            airg::fail(AIRG_ERR_ARG, "bad profile arguments");
+        long long l = 0, b = 0;
+        if (!airg::read_profile(*h->H, kind, ms, &l, &b)) airg::fail(AIRG_ERR_ARG, "bad kernel kind");
+        *launches = l;
+        *bytes = b;
     });
 }
 

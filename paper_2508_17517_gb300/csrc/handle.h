@@ -65,5 +65,7 @@ void build_solve_data(Hierarchy& H, cudaStream_t st);
 void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_device,
                   double rtol, double atol, int maxit, airg_solve_info* info, cudaStream_t st);
 void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info);
+void set_profiling(Hierarchy& H, bool on);
+bool read_profile(const Hierarchy& H, int kind, double* ms, long long* launches, long long* bytes);
 
 }  // namespace airg

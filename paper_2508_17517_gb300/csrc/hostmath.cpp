@@ -11,12 +11,17 @@
 
 namespace airg {
 
-std::vector<double> givens_lsq(const std::vector<double>& H, int k, double beta)
+namespace {
+
+// Givens QR of the (k+1) x k Hessenberg H (row-major) applied to beta e1:
+// R overwrites a copy of H, g is the rotated right-hand side.
+void givens_qr(const std::vector<double>& H, int k, double beta, std::vector<double>& R,
+               std::vector<double>& g)
 {
-    // R: (k+1) x k working copy, g: rotated right-hand side
-    std::vector<double> R(H.begin(), H.begin() + size_t(k + 1) * k);
+    R.assign(H.begin(), H.begin() + size_t(k + 1) * k);
     auto at = [&](int i, int j) -> double& { return R[size_t(i) * k + j]; };
-    std::vector<double> g(size_t(k) + 1, 0.0), cs(k, 0.0), sn(k, 0.0), y(k, 0.0);
+    std::vector<double> cs(k, 0.0), sn(k, 0.0);
+    g.assign(size_t(k) + 1, 0.0);
     g[0] = beta;
     for (int j = 0; j < k; ++j) {
         for (int i = 0; i < j; ++i) {
@@ -34,6 +39,22 @@ std::vector<double> givens_lsq(const std::vector<double>& H, int k, double beta)
         g[j + 1] = -sn[j] * g[j];
         g[j] = cs[j] * g[j];
     }
+}
+
+}  // namespace
+
+double givens_residual(const std::vector<double>& H, int k, double beta)
+{
+    std::vector<double> R, g;
+    givens_qr(H, k, beta, R, g);
+    return std::fabs(g[k]);
+}
+
+std::vector<double> givens_lsq(const std::vector<double>& H, int k, double beta)
+{
+    std::vector<double> R, g, y(k, 0.0);
+    givens_qr(H, k, beta, R, g);
+    auto at = [&](int i, int j) -> double& { return R[size_t(i) * k + j]; };
     for (int j = k - 1; j >= 0; --j) {
         double s = g[j];
         for (int i = j + 1; i < k; ++i) s = s - at(j, i) * y[i];

@@ -12,6 +12,9 @@ namespace airg {
 // Returns y = argmin || beta e1 - H y || by Givens rotations.
 std::vector<double> givens_lsq(const std::vector<double>& H, int k, double beta);
 
+// || beta e1 - H y || at the least-squares minimiser (same rotations).
+double givens_residual(const std::vector<double>& H, int k, double beta);
+
 // Coefficients alpha_0..alpha_{k-1} of the polynomial with
 // sum_j y_j v_j = (sum_t alpha_t A^t) b, from the Arnoldi recurrence
 // c_1 = 1/beta, c_{j+1}(z) = (z c_j(z) - sum_{i<=j} h_ij c_i(z)) / h_{j+1,j}.

@@ -820,7 +820,7 @@ struct ArnoldiOut {
 };
 
 // m steps of MGS Arnoldi from b (device, length n); dots correctly rounded.
-ArnoldiOut arnoldi(Ctx& c, const DevCSR& A, const double* b, int m, double tol)
+ArnoldiOut arnoldi(Ctx& c, const DevCSR& A, const double* b, int m, double tol, double exact_tol)
 {
     cudaStream_t st = c.st;
     long long n = A.n_rows;
@@ -832,6 +832,7 @@ ArnoldiOut arnoldi(Ctx& c, const DevCSR& A, const double* b, int m, double tol)
     k_div_dev<<<g, TB, 0, st>>>(n, V.p, b, beta_d);
     CK_LAUNCH();
     std::vector<double> Hh(size_t(m + 1) * m, 0.0);
+    const double beta_h = read1(beta_d, st);
     ArnoldiOut out;
     out.k = m;
     std::vector<double> col(m + 1);
@@ -859,12 +860,23 @@ ArnoldiOut arnoldi(Ctx& c, const DevCSR& A, const double* b, int m, double tol)
             out.broke = true;
             break;
         }
+        {
+            // GMRES residual of the (j+2) x (j+1) least-squares problem
+            int kk = j + 1;
+            std::vector<double> Hs(size_t(kk + 1) * kk);
+            for (int i = 0; i <= kk; ++i)
+                for (int q = 0; q < kk; ++q) Hs[size_t(i) * kk + q] = Hh[size_t(i) * m + q];
+            if (givens_residual(Hs, kk, beta_h) <= exact_tol * beta_h) {
+                out.k = kk;
+                break;
+            }
+        }
         if (j + 1 < m) {
             k_div_dev<<<g, TB, 0, st>>>(n, V.p + size_t(j + 1) * n, w.p, hn);
             CK_LAUNCH();
         }
     }
-    out.beta = read1(beta_d, st);
+    out.beta = beta_h;
     int k = out.k;
     out.H.assign(size_t(k + 1) * k, 0.0);
     for (int i = 0; i <= k; ++i)
@@ -880,7 +892,7 @@ std::vector<double> gmres_poly_coeffs(Ctx& c, const DevCSR& Aff, const airg_opti
     DBuf<double> b(n);
     k_rng_uniform<<<grid_for(n, TB), TB, 0, c.st>>>(stream_key(o.seed, level, PURPOSE_COEF), n, b.p);
     CK_LAUNCH();
-    ArnoldiOut ar = arnoldi(c, Aff, b.p, p + 1, o.breakdown_tol);
+    ArnoldiOut ar = arnoldi(c, Aff, b.p, p + 1, o.breakdown_tol, o.exact_tol);
     std::vector<double> y = givens_lsq(ar.H, ar.k, ar.beta);
     std::vector<double> alpha = power_coefficients(ar.H, ar.k, ar.beta, y);
     alpha.resize(size_t(p) + 1, 0.0);
@@ -950,7 +962,7 @@ std::vector<Root> coarse_polynomial(Ctx& c, const DevCSR& A, const airg_options&
     DBuf<double> b(n);
     k_rng_uniform<<<grid_for(n, TB), TB, 0, c.st>>>(stream_key(o.seed, level, PURPOSE_COARSE), n, b.p);
     CK_LAUNCH();
-    ArnoldiOut ar = arnoldi(c, A, b.p, m, o.breakdown_tol);
+    ArnoldiOut ar = arnoldi(c, A, b.p, m, o.breakdown_tol, o.exact_tol);
     std::vector<double> wr, wi;
     if (!harmonic_ritz(ar.H, ar.k, ar.broke, wr, wi))
         fail(AIRG_ERR_BREAKDOWN, "harmonic Ritz eigenvalue iteration did not converge");

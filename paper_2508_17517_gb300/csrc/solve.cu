@@ -29,6 +29,8 @@ namespace airg {
 namespace {
 constexpr int TB = 256;
 }
+enum { PK_RESTRICT = 0, PK_FRESID = 1, PK_HORNER = 2, PK_NEWTON = 3, PK_TOPSPMV = 4, PK_KRYLOV = 5,
+       PK_LAYOUT = 6, PROF_KINDS = 7 };
 
 template <class T>
 struct Sell {
@@ -81,7 +83,63 @@ struct SolveData {
     DBuf<double> hdev;
     HBuf<double> hhost;
     long long bytes_vcycle = 0;
+    // launch count and optional per-kind CUDA-event timing of the solve kernels
+    long long launches = 0;
+    bool prof = false;
+    struct Rec { int kind; cudaEvent_t a, b; long long bytes; };
+    std::vector<cudaEvent_t> evpool;
+    size_t evnext = 0;
+    std::vector<Rec> recs;
+    double kind_ms[PROF_KINDS] = {};
+    long long kind_launches[PROF_KINDS] = {}, kind_bytes[PROF_KINDS] = {};
+    cudaEvent_t next_event()
+    {
+        if (evnext == evpool.size()) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            evpool.push_back(e);
+        }
+        return evpool[evnext++];
+    }
+    void begin(cudaStream_t st, cudaEvent_t& a)
+    {
+        ++launches;
+        if (prof) { a = next_event(); CK(cudaEventRecord(a, st)); }
+    }
+    void end(int kind, long long bytes, cudaStream_t st, cudaEvent_t a)
+    {
+        if (!prof) return;
+        cudaEvent_t b = next_event();
+        CK(cudaEventRecord(b, st));
+        recs.push_back(Rec{kind, a, b, bytes});
+    }
+    // after the stream has been synchronised
+    void collect()
+    {
+        for (const Rec& r : recs) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, r.a, r.b));
+            kind_ms[r.kind] += ms;
+            kind_launches[r.kind] += 1;
+            kind_bytes[r.kind] += r.bytes;
+        }
+        recs.clear();
+        evnext = 0;
+    }
+    ~SolveData()
+    {
+        for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+    }
 };
+
+// Launch through the counter / profiler: LAUNCH(S, kind, bytes, kernel<<<...>>>(...))
+#define LAUNCH(S, KIND, BYTES, ...)                  \
+    do {                                             \
+        cudaEvent_t ev_a_ = nullptr;                 \
+        (S).begin(st, ev_a_);                        \
+        __VA_ARGS__;                                 \
+        (S).end((KIND), (BYTES), st, ev_a_);         \
+    } while (0)
 
 Hierarchy::Hierarchy() = default;
 Hierarchy::~Hierarchy() = default;
@@ -429,18 +487,20 @@ const Sell<float>& coarse_op<float>(const SolveData& S) { return S.Ac32; }
 
 // e = M^-1 v in the nested order.  v is only read; e is written everywhere.
 template <class T>
-void vcycle(const SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
+void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
 {
     const int L = S.nlev;
+    constexpr long long VB = sizeof(T);
     // restriction, top to bottom (level 0 reads v, deeper levels the work vector)
     for (int l = 0; l < L; ++l) {
         const SolveLevel& lv = *S.lv[l];
         const T* src = l == 0 ? v : wk.rwork;
         const Sell<T>& Z = ops<T>(lv).Z;
         if (lv.n_c)
-            k_restrict<T><<<grid_for(lv.n_c, TB), TB, 0, st>>>(view(Z), src + lv.off,
-                                                               src + lv.off + lv.n_f,
-                                                               wk.rwork + lv.off + lv.n_f);
+            LAUNCH(S, PK_RESTRICT, Z.nnz * (VB + 4) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB,
+                   k_restrict<T><<<grid_for(lv.n_c, TB), TB, 0, st>>>(view(Z), src + lv.off,
+                                                                      src + lv.off + lv.n_f,
+                                                                      wk.rwork + lv.off + lv.n_f));
     }
     // coarse-grid polynomial
     {
@@ -453,16 +513,21 @@ void vcycle(const SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream
         T* bufs[2] = {wk.cr0, wk.cr1};
         int nb = 0;
         size_t nr = S.roots.size();
+        const long long nB = (long long)S.n_coarse * VB, mB = A.nnz * (VB + 4);
         for (size_t i = 0; i < nr; ++i) {
             bool last = i + 1 == nr;
             const Root& q = S.roots[i];
             T* rout = bufs[nb];
             if (q.im == 0.0) {
-                k_newton_real<T><<<g, TB, 0, st>>>(Av, rin, rout, x, T(1.0 / q.re), i == 0, last);
+                LAUNCH(S, PK_NEWTON, (last ? 0 : mB + 2 * nB) + (i == 0 ? 2 : 3) * nB,
+                       k_newton_real<T><<<g, TB, 0, st>>>(Av, rin, rout, x, T(1.0 / q.re), i == 0, last));
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
-                k_newton_pair1<T><<<g, TB, 0, st>>>(Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0);
-                if (!last) k_newton_pair2<T><<<g, TB, 0, st>>>(Av, rin, wk.ct, rout, T(1.0 / mod2));
+                LAUNCH(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB,
+                       k_newton_pair1<T><<<g, TB, 0, st>>>(Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0));
+                if (!last)
+                    LAUNCH(S, PK_NEWTON, mB + 3 * nB,
+                           k_newton_pair2<T><<<g, TB, 0, st>>>(Av, rin, wk.ct, rout, T(1.0 / mod2)));
             }
             if (!last) { rin = rout; nb ^= 1; }
         }
@@ -479,18 +544,23 @@ void vcycle(const SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream
         int nf = lv.n_f;
         int g = grid_for(nf, TB);
         int p = int(lv.alpha.size()) - 1;
-        k_fresid<T><<<g, TB, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa, T(lv.alpha[p]));
+        const long long fB = (long long)nf * VB;
+        LAUNCH(S, PK_FRESID, o.M.nnz * (VB + 4) + (long long)lv.n_c * VB + 3 * fB,
+               k_fresid<T><<<g, TB, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa, T(lv.alpha[p])));
         if (p == 0) {
-            k_smooth0<T><<<g, TB, 0, st>>>(nf, wk.t, ec, lv.W.p, ef, T(lv.alpha[0]));
+            LAUNCH(S, PK_HORNER, 3 * fB + 4LL * nf,
+                   k_smooth0<T><<<g, TB, 0, st>>>(nf, wk.t, ec, lv.W.p, ef, T(lv.alpha[0])));
             continue;
         }
+        const long long hB = o.Aff.nnz * (VB + 4) + 3 * fB;
         T* win = wk.wa;
         T* wout = wk.wb;
         for (int k = p - 1; k >= 1; --k) {
-            k_horner<T><<<g, TB, 0, st>>>(view(o.Aff), wk.t, win, wout, T(lv.alpha[k]));
+            LAUNCH(S, PK_HORNER, hB, k_horner<T><<<g, TB, 0, st>>>(view(o.Aff), wk.t, win, wout, T(lv.alpha[k])));
             std::swap(win, wout);
         }
-        k_horner_last<T><<<g, TB, 0, st>>>(view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0]));
+        LAUNCH(S, PK_HORNER, hB + fB + 4LL * nf,
+               k_horner_last<T><<<g, TB, 0, st>>>(view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0])));
     }
     CK_LAUNCH();
 }
@@ -607,8 +677,8 @@ namespace {
 
 double dev_norm(SolveData& S, const double* x, long long n, cudaStream_t st)
 {
-    k_multidot<<<RGRID, RB, 0, st>>>(n, 1, x, n, x, S.part.p);
-    k_sum_parts<<<1, 32, 0, st>>>(RGRID, 1, S.part.p, S.hdev.p);
+    LAUNCH(S, PK_KRYLOV, 8 * n, k_multidot<<<RGRID, RB, 0, st>>>(n, 1, x, n, x, S.part.p));
+    LAUNCH(S, PK_KRYLOV, 8LL * RGRID, k_sum_parts<<<1, 32, 0, st>>>(RGRID, 1, S.part.p, S.hdev.p));
     CK_LAUNCH();
     double v = read1(S.hdev.p, st);
     return std::sqrt(v);
@@ -619,10 +689,10 @@ void precond(Hierarchy& H, const double* v, double* z, cudaStream_t st)
     SolveData& S = *H.solve;
     long long n = S.n0;
     if (H.opt.precision == AIRG_MIXED_FP32) {
-        k_d2f<<<grid_for(n, TB), TB, 0, st>>>(n, v, S.vin32.p);
+        LAUNCH(S, PK_LAYOUT, 12 * n, k_d2f<<<grid_for(n, TB), TB, 0, st>>>(n, v, S.vin32.p));
         VWork<float> wk{S.rwork32.p, S.t32.p, S.wa32.p, S.wb32.p, nullptr, S.cr032.p, S.cr132.p, S.ct32.p};
         vcycle<float>(S, S.vin32.p, S.e32.p, wk, st);
-        k_f2d<<<grid_for(n, TB), TB, 0, st>>>(n, S.e32.p, z);
+        LAUNCH(S, PK_LAYOUT, 12 * n, k_f2d<<<grid_for(n, TB), TB, 0, st>>>(n, S.e32.p, z));
         CK_LAUNCH();
     } else {
         VWork<double> wk{S.rwork.p, S.t.p, S.wa.p, S.wb.p, nullptr, S.cr0.p, S.cr1.p, S.ct.p};
@@ -639,12 +709,13 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
     int m = S.restart;
     int g = grid_for(n, TB);
     SellView<double> A = view(S.Atop);
+    const long long topB = S.Atop.nnz * 12 + 16 * n;
     double bn = dev_norm(S, S.bp.p, n, st);
     double tol = std::max(rtol * bn, atol);
     int its = 0;
     auto residual = [&]() {
-        k_spmv<double><<<g, TB, 0, st>>>(A, S.xp.p, S.w.p);
-        k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p);
+        LAUNCH(S, PK_TOPSPMV, topB, k_spmv<double><<<g, TB, 0, st>>>(A, S.xp.p, S.w.p));
+        LAUNCH(S, PK_KRYLOV, 24 * n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
         CK_LAUNCH();
         return dev_norm(S, S.r.p, n, st);
     };
@@ -652,7 +723,7 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
     std::vector<double> Hm(size_t(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
     double* hh = S.hhost.p;
     while (rn > tol && its < maxit) {
-        k_scale_into<<<g, TB, 0, st>>>(n, S.r.p, 1.0 / rn, S.V.p);
+        LAUNCH(S, PK_KRYLOV, 16 * n, k_scale_into<<<g, TB, 0, st>>>(n, S.r.p, 1.0 / rn, S.V.p));
         std::fill(gv.begin(), gv.end(), 0.0);
         gv[0] = rn;
         int jdone = 0;
@@ -660,15 +731,19 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             double* vj = S.V.p + size_t(j) * n;
             double* zj = S.Zs.p + size_t(j) * n;
             precond(H, vj, zj, st);
-            k_spmv<double><<<g, TB, 0, st>>>(A, zj, S.w.p);
+            LAUNCH(S, PK_TOPSPMV, topB, k_spmv<double><<<g, TB, 0, st>>>(A, zj, S.w.p));
             // classical Gram-Schmidt, twice
             for (int pass = 0; pass < 2; ++pass) {
-                k_multidot<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, S.w.p, S.part.p);
-                k_sum_parts<<<1, 32, 0, st>>>(RGRID, j + 1, S.part.p, S.hdev.p + pass * (m + 2));
-                k_multiaxpy<<<g, TB, 0, st>>>(n, j + 1, S.V.p, n, S.hdev.p + pass * (m + 2), S.w.p);
+                LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 2),
+                       k_multidot<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, S.w.p, S.part.p));
+                LAUNCH(S, PK_KRYLOV, 8LL * RGRID * (j + 1),
+                       k_sum_parts<<<1, 32, 0, st>>>(RGRID, j + 1, S.part.p, S.hdev.p + pass * (m + 2)));
+                LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 3),
+                       k_multiaxpy<<<g, TB, 0, st>>>(n, j + 1, S.V.p, n, S.hdev.p + pass * (m + 2), S.w.p));
             }
-            k_multidot<<<RGRID, RB, 0, st>>>(n, 1, S.w.p, n, S.w.p, S.part.p);
-            k_sum_parts<<<1, 32, 0, st>>>(RGRID, 1, S.part.p, S.hdev.p + 2 * (m + 2));
+            LAUNCH(S, PK_KRYLOV, 8 * n, k_multidot<<<RGRID, RB, 0, st>>>(n, 1, S.w.p, n, S.w.p, S.part.p));
+            LAUNCH(S, PK_KRYLOV, 8LL * RGRID,
+                   k_sum_parts<<<1, 32, 0, st>>>(RGRID, 1, S.part.p, S.hdev.p + 2 * (m + 2)));
             CK_LAUNCH();
             CK(cudaMemcpyAsync(hh, S.hdev.p, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -691,7 +766,8 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             ++its;
             jdone = j + 1;
             if (std::fabs(gv[j + 1]) <= tol || its >= maxit || den == 0.0 || hn == 0.0) break;
-            k_scale_into<<<g, TB, 0, st>>>(n, S.w.p, 1.0 / hn, S.V.p + size_t(j + 1) * n);
+            LAUNCH(S, PK_KRYLOV, 16 * n,
+                   k_scale_into<<<g, TB, 0, st>>>(n, S.w.p, 1.0 / hn, S.V.p + size_t(j + 1) * n));
         }
         for (int j = jdone - 1; j >= 0; --j) {
             double s = gv[j];
@@ -699,7 +775,8 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             y[j] = s / Hm[size_t(j) * m + j];
         }
         h2d(S.hdev.p, y.data(), jdone, st);
-        k_multiaxpy_plus<<<g, TB, 0, st>>>(n, jdone, S.Zs.p, n, S.hdev.p, S.xp.p);
+        LAUNCH(S, PK_KRYLOV, 8LL * n * (jdone + 2),
+               k_multiaxpy_plus<<<g, TB, 0, st>>>(n, jdone, S.Zs.p, n, S.hdev.p, S.xp.p));
         CK_LAUNCH();
         rn = residual();
     }
@@ -717,6 +794,7 @@ void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_de
     auto t0 = std::chrono::steady_clock::now();
     SolveData& S = *H.solve;
     long long n = S.n0;
+    long long launches0 = S.launches;
     airg_solve_info info{};
     info.converged = 1;
     DBuf<double> bd, xd;
@@ -732,17 +810,19 @@ void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_de
     }
     int g = grid_for(n, TB);
     for (int q = 0; q < nrhs; ++q) {
-        k_to_nested<<<g, TB, 0, st>>>(n, S.pos0.p, bdev + size_t(q) * n, S.bp.p);
-        k_to_nested<<<g, TB, 0, st>>>(n, S.pos0.p, xdev + size_t(q) * n, S.xp.p);
+        LAUNCH(S, PK_LAYOUT, 20 * n, k_to_nested<<<g, TB, 0, st>>>(n, S.pos0.p, bdev + size_t(q) * n, S.bp.p));
+        LAUNCH(S, PK_LAYOUT, 20 * n, k_to_nested<<<g, TB, 0, st>>>(n, S.pos0.p, xdev + size_t(q) * n, S.xp.p));
         CK_LAUNCH();
         fgmres(H, rtol, atol, maxit, info, st);
-        k_from_nested<<<g, TB, 0, st>>>(n, S.pos0.p, S.xp.p, xdev + size_t(q) * n);
+        LAUNCH(S, PK_LAYOUT, 20 * n, k_from_nested<<<g, TB, 0, st>>>(n, S.pos0.p, S.xp.p, xdev + size_t(q) * n));
         CK_LAUNCH();
     }
     if (!on_device) {
         CK(cudaMemcpyAsync(x, xd.p, sizeof(double) * n * nrhs, cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
+    S.collect();
+    info.kernel_launches = S.launches - launches0;
     info.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info_out) *info_out = info;
     if (!info.converged) fail(AIRG_ERR_NOT_CONVERGED, "FGMRES did not reach the tolerance within maxit");
@@ -784,6 +864,29 @@ void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info)
     info->storage_complexity = top ? double(store) / double(top) : 0.0;
     info->cycle_complexity = top ? double(flops) / (2.0 * double(top)) : 0.0;
     info->bytes_per_vcycle = H.solve ? H.solve->bytes_vcycle : 0;
+}
+
+}  // namespace airg
+
+namespace airg {
+
+void set_profiling(Hierarchy& H, bool on)
+{
+    SolveData& S = *H.solve;
+    S.prof = on;
+    S.recs.clear();
+    S.evnext = 0;
+    for (int k = 0; k < PROF_KINDS; ++k) { S.kind_ms[k] = 0; S.kind_launches[k] = 0; S.kind_bytes[k] = 0; }
+}
+
+bool read_profile(const Hierarchy& H, int kind, double* ms, long long* launches, long long* bytes)
+{
+    if (kind < 0 || kind >= PROF_KINDS) return false;
+    const SolveData& S = *H.solve;
+    *ms = S.kind_ms[kind];
+    *launches = S.kind_launches[kind];
+    *bytes = S.kind_bytes[kind];
+    return true;
 }
 
 }  // namespace airg

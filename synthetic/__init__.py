@@ -29,7 +29,7 @@ def workload(name, n=None):
         th = 3 * math.pi / 8
         g = np.ones((1, _n_inflow(nx, ny, th)))
         return dict(nx=nx, ny=ny, theta=th, g=g, s=None, n_rhs=1, rtol=1e-10,
-                    opts=dict(poly_order=4, trunc_start_level=2),
+                    opts=dict(poly_order=4, trunc_start_level=4),
                     desc="%dx%d theta=3pi/8 g=1 s=0 p=4" % (nx, ny))
     if name == "c2":
         # 1024x1024, theta ~ U[pi/12, 5pi/12], g ~ U[0.5, 2] per inflow node,

@@ -39,7 +39,7 @@ def test_options_default_are_paper_values(L):
     assert (o.strong_threshold, o.ddc_fraction, o.ddc_its, o.poly_order) == (0.99, 0.01, 2, 6)
     assert (o.coarse_poly_order, o.trunc_rtol, o.a_drop, o.a_lump) == (100, 0.1, 1e-6, 1)
     d = O.Options()
-    assert (o.r_drop, o.seed, o.breakdown_tol) == (d.r_drop, d.seed, d.breakdown_tol)
+    assert (o.r_drop, o.seed, o.breakdown_tol, o.exact_tol) == (d.r_drop, d.seed, d.breakdown_tol, d.exact_tol)
 
 
 @pytest.mark.parametrize("seed", range(6))

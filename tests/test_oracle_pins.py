@@ -423,7 +423,7 @@ def test_grid_aligned_direction_is_exact_solver():
 def test_c1_constant_solution_and_convergence():
     P = _grid(64, 64, 3 * math.pi / 8)
     b = O.assemble_rhs(P, np.ones(P.inflow.size), np.zeros(4096))
-    H = O.setup(P.A, O.Options(poly_order=4, trunc_start_level=2))
+    H = O.setup(P.A, O.Options(poly_order=4, trunc_start_level=4))
     assert len(H.levels) >= 3
     x, info = O.solve(H, P.A, b, rtol=1e-10)
     assert info.converged
