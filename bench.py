@@ -1,0 +1,308 @@
+#!/usr/bin/env python3
+"""Benchmark of the AIRG solve phase: DOFs solved per second to rtol 1e-10.
+
+A step is one complete solve (FP64 FGMRES preconditioned by AIRG V-cycles,
+Sec. 2-3 of arXiv 2508.17517) of the 1024x1024 upwind advection workload
+(seeded direction and inflow, coarse polynomial order 30, truncation
+tolerance 1e-2) from x0 = 0, with the hierarchy set up once beforehand (the
+paper times the second solve).  `value` = DOFs solved per second over all
+ranks, timed on the device with CUDA events around each solve, L2 flushed
+between steps.  `e2e` repeats the solves through the C ABI with host
+buffers, copies included.  The roofline entry comes from a second pass of
+the same steps with per-kernel CUDA events (airg_profile).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1]
+  python bench.py --impl reference ...   (the CPU oracle as the reference arm)
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOFs solved/s to rtol 1e-10 (mixed vs FP64 on GPU); V-cycle HBM GB/s vs peak"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value, world, device=None):
+    """Max of a float over the ranks of the default process group."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------- clock sampling --
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- workloads --
+def problem_and_rhs(w, G, torch):
+    from synthetic import velocity
+    vx, vy = velocity(w["theta"])
+    prob = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
+    g = torch.tensor(w["g"][0], device="cuda")
+    s = torch.tensor(w["s"][0], device="cuda") if w["s"] is not None else None
+    b = G.airg_assemble_rhs_advection2d(prob, g, s)
+    return prob, b
+
+
+def cpu_oracle_solve(w, steps, warmup):
+    """Times the oracle's solve (after an untimed oracle setup) of the same
+    workload; returns (DOFs/s, per-step seconds)."""
+    from oracle import airg as O
+    from synthetic import velocity
+    vx, vy = velocity(w["theta"])
+    po = O.advection_2d(w["nx"], w["ny"], vx, vy)
+    opts = O.Options(**{k: v for k, v in w["opts"].items() if k != "precision"})
+    Ho = O.setup(po.A, opts)
+    s = w["s"][0] if w["s"] is not None else [0.0] * po.A.n_rows
+    bo = O.assemble_rhs(po, w["g"][0], s)
+    for _ in range(warmup):
+        O.solve(Ho, po.A, bo, rtol=w["rtol"])
+    ts = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        O.solve(Ho, po.A, bo, rtol=w["rtol"])
+        ts.append(time.perf_counter() - t0)
+    n = po.A.n_rows
+    return n * len(ts) / sum(ts), ts
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from synthetic import workload
+    w = workload(args.workload)
+    n = w["nx"] * w["ny"]
+    t0 = time.time()
+    value, ts = cpu_oracle_solve(w, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(ts) / len(ts), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "n": n, "nrhs": 1, "rtol": w["rtol"]},
+        "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d full oracle solves of the workload (single-threaded C "
+                                   "kernels + numpy, FP64), setup untimed" % args.steps},
+        "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.time() - t0,
+    }
+    print(json.dumps(line))
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2508_17517_gb300 as G
+    from synthetic import workload
+    G.lib()
+    w = workload(args.workload)
+    n = w["nx"] * w["ny"]
+    prob, b = problem_and_rhs(w, G, torch)
+    opts = G.airg_options_default(**w["opts"])
+    h = G.airg_setup(prob["rowptr"], prob["col"], prob["val"], opts)
+    sinfo = G.airg_setup_info(h)
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        x.zero_()
+        G.airg_solve(h, b, x, rtol=w["rtol"])
+    # ---- timed region: device time of each solve (CUDA events on the solve stream)
+    clk = Clocks(local_rank)
+    barrier()
+    clk.start()
+    total_ms, its, launches = 0.0, [], 0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        x.zero_()
+        ev0.record(stream)
+        _, info = G.airg_solve(h, b, x, rtol=w["rtol"])
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        its.append(info.iterations)
+        launches += info.kernel_launches
+        assert info.converged and info.rel_residual <= w["rtol"]
+    barrier()
+    wall_s = time.perf_counter() - t_wall0
+    clocks = clk.stop()
+    t_max = max_over_ranks(total_ms, world, dev)
+    value = world * n * args.steps / (t_max / 1e3)
+    # ---- end-to-end through the C ABI with host buffers (copies in the call)
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    barrier()
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        xh.zero_()
+        t0 = time.perf_counter()
+        G.airg_solve(h, bh, xh, rtol=w["rtol"])
+        e2e_s += time.perf_counter() - t0
+    e2e_max = max_over_ranks(e2e_s, world, dev)
+    e2e = {"value": world * n * args.steps / e2e_max, "unit": "DOF/s",
+           "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n}
+    # ---- per-kernel event timing over a second pass of the same steps
+    G.airg_profile(h, True)
+    for _ in range(args.steps):
+        flush.zero_()
+        x.zero_()
+        G.airg_solve(h, b, x, rtol=w["rtol"])
+    prof = G.airg_profile_read(h)
+    G.airg_profile(h, False)
+    peak, peak_kind = measured_peaks()
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    ms, nl, nb = kinds[dom]
+    achieved = nb / (ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "launches": nl, "avg_launch_us": 1e3 * ms / nl,
+                "algorithmic_bytes_per_launch": nb / nl,
+                "kernel_share": {k: v[0] / sum(q[0] for q in kinds.values()) for k, v in kinds.items()}}
+    vc_bytes = sinfo["bytes_per_vcycle"]
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cv, ts = cpu_oracle_solve(w, 1, 0)
+        cpu = {"value": cv, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+               "sample": "1 full oracle solve of the same workload (setup untimed), %.1f s" % ts[0]}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if w["opts"].get("precision") == 1 else "f64",
+            "data": "synthetic",
+            "config": {"workload": w["desc"], "n": n, "nrhs": 1, "rtol": w["rtol"],
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "levels": sinfo["levels"], "iterations_per_solve": statistics.median(its),
+                       "setup_ms": sinfo["setup_ms"], "cycle_complexity": sinfo["cycle_complexity"],
+                       "storage_complexity": sinfo["storage_complexity"],
+                       "vcycle_algorithmic_bytes": vc_bytes,
+                       "l2": "flushed (256 MiB write) between timed steps"},
+            "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": launches, "wall_s_timed": wall_s,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -98,6 +98,7 @@ typedef struct {
     int levels;                /* number of levels, coarsest included         */
     int truncated;             /* 1 if the hierarchy was truncated (Sec. 2.4) */
     int coarse_roots;          /* Newton roots of the coarse solver           */
+    int coarse_krylov;         /* Arnoldi steps taken for those roots         */
     double cycle_complexity;   /* V-cycle flops / top SpMV flops (Sec. 3)     */
     double storage_complexity; /* solve-time nnz / nnz(A_top) (Sec. 3)        */
     double setup_ms;           /* wall time of airg_setup                     */

@@ -58,7 +58,8 @@ class airg_solve_info(ctypes.Structure):
 
 class airg_hierarchy_info(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("truncated", ctypes.c_int),
-                ("coarse_roots", ctypes.c_int), ("cycle_complexity", ctypes.c_double),
+                ("coarse_roots", ctypes.c_int), ("coarse_krylov", ctypes.c_int),
+                ("cycle_complexity", ctypes.c_double),
                 ("storage_complexity", ctypes.c_double), ("setup_ms", ctypes.c_double),
                 ("n", ctypes.c_int64 * 64), ("n_f", ctypes.c_int64 * 64),
                 ("nnz_a", ctypes.c_int64 * 64), ("bytes_per_vcycle", ctypes.c_int64)]
@@ -225,6 +226,7 @@ def airg_setup_info(handle):
     _check(lib().airg_setup_info(handle.ptr, ctypes.byref(info)))
     L = info.levels
     return {"levels": L, "truncated": bool(info.truncated), "coarse_roots": info.coarse_roots,
+            "coarse_krylov": info.coarse_krylov,
             "cycle_complexity": info.cycle_complexity,
             "storage_complexity": info.storage_complexity, "setup_ms": info.setup_ms,
             "n": list(info.n[:L]), "n_f": list(info.n_f[:L]), "nnz_a": list(info.nnz_a[:L]),

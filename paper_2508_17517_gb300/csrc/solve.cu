@@ -835,6 +835,7 @@ void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info)
     info->levels = L + 1;
     info->truncated = H.coarse.truncated ? 1 : 0;
     info->coarse_roots = int(H.coarse.roots.size());
+    info->coarse_krylov = H.coarse.k;
     info->setup_ms = H.setup_ms;
     long long top = L ? H.levels[0]->A.nnz : H.coarse.A.nnz;
     long long store = top, flops = 0;
@@ -845,9 +846,7 @@ void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info)
         info->nnz_a[l] = lv.A.nnz;
         int p = int(lv.alpha.size()) - 1;
         // kept for the solve: A_ff, A_fc, R = [Z I], P = [W; I] (Sec. 3)
-        long long np = lv.n_c;
-        for (int i = 0; i < 1; ++i) (void)i;
-        store += lv.A_ff.nnz + lv.A_fc.nnz + (lv.Z.nnz + lv.n_c) + (lv.n_f + np);
+        store += lv.A_ff.nnz + lv.A_fc.nnz + (lv.Z.nnz + lv.n_c) + (lv.n_f + lv.n_c);
         flops += 2LL * lv.Z.nnz + 2LL * lv.A_fc.nnz + 2LL * lv.A_ff.nnz * (p + 1);
     }
     if (L < 64) {
