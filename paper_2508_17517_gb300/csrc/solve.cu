@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "dev_util.cuh"
@@ -32,25 +33,44 @@ constexpr int TB = 256;
 enum { PK_RESTRICT = 0, PK_FRESID = 1, PK_HORNER = 2, PK_NEWTON = 3, PK_TOPSPMV = 4, PK_KRYLOV = 5,
        PK_LAYOUT = 6, PROF_KINDS = 7 };
 
+// A solve-phase operator in SELL-32: slices of 32 consecutive rows, entries
+// column-major inside a slice (entry k of the slice's 32 rows are adjacent),
+// each slice padded to its longest row (padding: value 0, column repeated).
+// Lane l of a warp always owns row 32s+l, so at a given entry index the 32
+// lanes read adjacent values and columns, and -- rows of these operators
+// having similar stencils -- gather nearby entries of x.  k = number of
+// warps sharing a slice: for long rows the entries of a slice are split
+// among k warps of a block (entry indices interleaved) whose partial sums
+// meet in shared memory.
 template <class T>
 struct Sell {
-    int n_rows = 0, n_cols = 0, n_slices = 0;
+    int n_rows = 0, n_cols = 0, n_slices = 0, k = 1;
     long long nnz = 0, padded = 0;
-    DBuf<int> sptr;   // n_slices + 1 element offsets
+    DBuf<int> sptr;
     DBuf<int> col;
     DBuf<T> val;
 };
 
 template <class T>
 struct SellView {
-    int n_rows;
+    int n_rows, n_slices;
     const int* __restrict__ sptr;
     const int* __restrict__ col;
     const T* __restrict__ val;
 };
 
 template <class T>
-SellView<T> view(const Sell<T>& s) { return SellView<T>{s.n_rows, s.sptr.p, s.col.p, s.val.p}; }
+SellView<T> view(const Sell<T>& s) { return SellView<T>{s.n_rows, s.n_slices, s.sptr.p, s.col.p, s.val.p}; }
+
+// warps per slice from the mean row length (about 4-20 entries per lane)
+inline int choose_parts(long long nnz, int n_rows)
+{
+    double avg = n_rows ? double(nnz) / n_rows : 0.0;
+    if (avg <= 12.0) return 1;
+    if (avg <= 32.0) return 2;
+    if (avg <= 80.0) return 4;
+    return 8;
+}
 
 template <class T>
 struct SolveLevelT {
@@ -73,6 +93,11 @@ struct SolveData {
     Sell<double> Ac;
     Sell<float> Ac32;
     std::vector<Root> roots;
+    // persistent coarse polynomial: CSR copies, roots on the device, barrier
+    DBuf<double> roots_dev;
+    DBuf<unsigned> bar;          // [count, generation, error flag]
+    DBuf<unsigned> ticket;       // last-block ticket of the dot kernels
+    int newton_grid[2] = {0, 0}; // per precision (0: FP64, 1: FP32); 0 = not usable
     int max_nf = 0;
     // V-cycle work (FP64 and FP32 copies)
     DBuf<double> rwork, t, wa, wb, cx, cr0, cr1, ct;
@@ -126,9 +151,19 @@ struct SolveData {
         recs.clear();
         evnext = 0;
     }
+    // private stream (capturable, unlike the legacy default stream) and the
+    // V-cycle graphs, one per (input, output) pair = FGMRES basis slot
+    cudaStream_t sst = nullptr;
+    cudaEvent_t ev_in = nullptr;
+    bool use_graphs = true;
+    struct GEntry { const void* v; void* z; cudaGraphExec_t exec; long long kernels; };
+    std::vector<GEntry> graphs;
     ~SolveData()
     {
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+        for (GEntry& g : graphs) cudaGraphExecDestroy(g.exec);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (sst) cudaStreamDestroy(sst);
     }
 };
 
@@ -197,6 +232,7 @@ void build_sell(const DevCSR& A, const int* src_row, const int* cmap, int n_cols
     S.n_rows = A.n_rows;
     S.n_cols = n_cols;
     S.nnz = A.nnz;
+    S.k = choose_parts(A.nnz, A.n_rows);
     S.n_slices = (A.n_rows + 31) / 32;
     S.sptr.alloc(size_t(S.n_slices) + 1);
     if (S.n_slices)
@@ -231,6 +267,7 @@ void copy_sell_f32(const Sell<double>& S, Sell<float>& out, cudaStream_t st)
     out.n_rows = S.n_rows;
     out.n_cols = S.n_cols;
     out.n_slices = S.n_slices;
+    out.k = S.k;
     out.nnz = S.nnz;
     out.padded = S.padded;
     out.sptr.alloc(S.sptr.n);
@@ -273,69 +310,141 @@ __global__ void k_map_w(int nf, const int* W, const int* rel, int* out)
 }
 
 // ------------------------------------------------------- V-cycle kernels --
+// Row r of S times x.  K == 1: SELL-32, one thread per row.  K > 1: CSR,
+// K consecutive lanes share a row (strided over its entries, so a group's
+// loads are contiguous) and reduce with shuffles; the sum is valid in the
+// group's first lane.  Every lane of a warp reaches the shuffles.
+// Sum of val[idx] * x[col[idx]] over idx = first, first + stride, ... < end.
+// Loads of four (then two) entries are issued before their gathers so that
+// each lane keeps several memory requests in flight (the gathers depend on
+// the column loads; without this every entry costs a full round trip).
+template <class T>
+__device__ __forceinline__ T strided_dot(const int* __restrict__ col, const T* __restrict__ val,
+                                         const T* __restrict__ x, int idx, int end, int stride)
+{
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    for (; idx + 3 * stride < end; idx += 4 * stride) {
+        int c0 = __ldg(col + idx), c1 = __ldg(col + idx + stride);
+        int c2 = __ldg(col + idx + 2 * stride), c3 = __ldg(col + idx + 3 * stride);
+        T v0 = __ldg(val + idx), v1 = __ldg(val + idx + stride);
+        T v2 = __ldg(val + idx + 2 * stride), v3 = __ldg(val + idx + 3 * stride);
+        a0 = fma(v0, x[c0], a0);
+        a1 = fma(v1, x[c1], a1);
+        a2 = fma(v2, x[c2], a2);
+        a3 = fma(v3, x[c3], a3);
+    }
+    if (idx + stride < end) {
+        int c0 = __ldg(col + idx), c1 = __ldg(col + idx + stride);
+        T v0 = __ldg(val + idx), v1 = __ldg(val + idx + stride);
+        a0 = fma(v0, x[c0], a0);
+        a1 = fma(v1, x[c1], a1);
+        idx += 2 * stride;
+    }
+    if (idx < end) a2 = fma(__ldg(val + idx), x[__ldg(col + idx)], a2);
+    return (a0 + a1) + (a2 + a3);
+}
+
 template <class T>
 __device__ __forceinline__ T sell_row(const SellView<T>& S, int r, const T* __restrict__ x)
 {
     int s = r >> 5;
     int base = S.sptr[s] + (r & 31);
     int w = (S.sptr[s + 1] - S.sptr[s]) >> 5;
+    return strided_dot(S.col, S.val, x, base, base + 32 * w, 32);
+}
+
+// Row (32*slice + lane) of S times x, computed by the P warps of the block
+// that share the slice (part = this warp's index among them).  Every thread
+// of the block must call it (it synchronises the block when P > 1).  The
+// sum is valid in the part-0 warp.
+template <class T, int P>
+__device__ __forceinline__ T row_dot(const SellView<T>& S, int slice, int lane, int part,
+                                     const T* __restrict__ x)
+{
     T acc = T(0);
-    for (int k = 0; k < w; ++k) {
-        int idx = base + k * 32;
-        acc = fma(S.val[idx], x[S.col[idx]], acc);
+    if (slice < S.n_slices) {
+        int b = S.sptr[slice], w = (S.sptr[slice + 1] - b) >> 5;
+        acc = strided_dot(S.col, S.val, x, b + lane + 32 * part, b + lane + 32 * w, 32 * P);
+    }
+    if (P > 1) {
+        __shared__ T red[8][32];
+        const int warp = threadIdx.x >> 5;
+        red[warp][lane] = acc;
+        __syncthreads();
+        if (part == 0) {
+#pragma unroll
+            for (int q = 1; q < P; ++q) acc += red[warp + q][lane];
+        }
+        __syncthreads();
     }
     return acc;
 }
 
+// Thread -> (slice, part, row) for 256-thread blocks: 8/P slices per block.
+#define ROW_IDS(P, NROWS)                                                   \
+    const int lane = threadIdx.x & 31;                                      \
+    const int part = (threadIdx.x >> 5) % (P);                              \
+    const int slice = blockIdx.x * (8 / (P)) + (threadIdx.x >> 5) / (P);    \
+    const int r = slice * 32 + lane;                                        \
+    const bool lead = part == 0 && r < (NROWS)
+#define ROW_DOT(P, S, X) row_dot<T, P>((S), slice, lane, part, (X))
+
 // y = S x
-template <class T>
+template <class T, int K>
 __global__ void k_spmv(SellView<T> S, const T* __restrict__ x, T* __restrict__ y)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < S.n_rows) y[r] = sell_row(S, r, x);
+    ROW_IDS(K, S.n_rows);
+    T d = ROW_DOT(K, S, x);
+    if (lead) y[r] = d;
 }
 
 // restriction (Eq. 3): dst_c[k] = src_c[k] + (Z src_f)[k]
-template <class T>
+template <class T, int K>
 __global__ void k_restrict(SellView<T> Z, const T* __restrict__ src_f, const T* __restrict__ src_c,
                            T* __restrict__ dst_c)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < Z.n_rows) dst_c[r] = src_c[r] + sell_row(Z, r, src_f);
+    ROW_IDS(K, Z.n_rows);
+    T d = ROW_DOT(K, Z, src_f);
+    if (lead) dst_c[r] = src_c[r] + d;
 }
 
 // F-point residual (Eq. 6): t = r_f - M e_c, and the first Horner term w = a_p t
-template <class T>
+template <class T, int K>
 __global__ void k_fresid(SellView<T> M, const T* __restrict__ rf, const T* __restrict__ ec,
                          T* __restrict__ t, T* __restrict__ w, T ap)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= M.n_rows) return;
-    T tt = rf[r] - sell_row(M, r, ec);
-    t[r] = tt;
-    w[r] = ap * tt;
+    ROW_IDS(K, M.n_rows);
+    T d = ROW_DOT(K, M, ec);
+    if (lead) {
+        T tt = rf[r] - d;
+        t[r] = tt;
+        w[r] = ap * tt;
+    }
 }
 
 // Horner term: wout = a_k t + A_ff win
-template <class T>
+template <class T, int K>
 __global__ void k_horner(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
                          T* __restrict__ wout, T ak)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < A.n_rows) wout[r] = fma(ak, t[r], sell_row(A, r, win));
+    ROW_IDS(K, A.n_rows);
+    T d = ROW_DOT(K, A, win);
+    if (lead) wout[r] = fma(ak, t[r], d);
 }
 
 // last Horner term and the correction: e_f = W e_c + (a_0 t + A_ff win)
-template <class T>
+template <class T, int K>
 __global__ void k_horner_last(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
                               const T* __restrict__ ec, const int* __restrict__ W,
                               T* __restrict__ ef, T a0)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= A.n_rows) return;
-    int wc = W[r];
-    T p = wc >= 0 ? ec[wc] : T(0);
-    ef[r] = p + fma(a0, t[r], sell_row(A, r, win));
+    ROW_IDS(K, A.n_rows);
+    T d = ROW_DOT(K, A, win);
+    if (lead) {
+        int wc = W[r];
+        T p = wc >= 0 ? ec[wc] : T(0);
+        ef[r] = p + fma(a0, t[r], d);
+    }
 }
 
 // degree-0 smoother: e_f = W e_c + a_0 t
@@ -350,48 +459,173 @@ __global__ void k_smooth0(int n, const T* __restrict__ t, const T* __restrict__ 
 }
 
 // Newton steps of the coarse polynomial (Sec. 2.3)
-template <class T>
+template <class T, int K>
 __global__ void k_newton_real(SellView<T> A, const T* __restrict__ rin, T* __restrict__ rout,
                               T* __restrict__ x, T inv_theta, int first, int last)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= A.n_rows) return;
-    T ri = rin[r];
-    T xv = first ? T(0) : x[r];
-    x[r] = fma(ri, inv_theta, xv);
-    if (!last) rout[r] = ri - sell_row(A, r, rin) * inv_theta;
+    ROW_IDS(K, A.n_rows);
+    T d = last ? T(0) : ROW_DOT(K, A, rin);
+    if (lead) {
+        T ri = rin[r];
+        T xv = first ? T(0) : x[r];
+        x[r] = fma(ri, inv_theta, xv);
+        if (!last) rout[r] = ri - d * inv_theta;
+    }
 }
 
-template <class T>
+template <class T, int K>
 __global__ void k_newton_pair1(SellView<T> A, const T* __restrict__ rin, T* __restrict__ t,
                                T* __restrict__ x, T two_a, T inv_mod2, int first)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= A.n_rows) return;
-    T tt = two_a * rin[r] - sell_row(A, r, rin);
-    t[r] = tt;
-    T xv = first ? T(0) : x[r];
-    x[r] = fma(tt, inv_mod2, xv);
+    ROW_IDS(K, A.n_rows);
+    T d = ROW_DOT(K, A, rin);
+    if (lead) {
+        T tt = two_a * rin[r] - d;
+        t[r] = tt;
+        T xv = first ? T(0) : x[r];
+        x[r] = fma(tt, inv_mod2, xv);
+    }
 }
 
-template <class T>
+template <class T, int K>
 __global__ void k_newton_pair2(SellView<T> A, const T* __restrict__ rin, const T* __restrict__ t,
                                T* __restrict__ rout, T inv_mod2)
 {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= A.n_rows) return;
-    rout[r] = rin[r] - sell_row(A, r, t) * inv_mod2;
+    ROW_IDS(K, A.n_rows);
+    T d = ROW_DOT(K, A, t);
+    if (lead) rout[r] = rin[r] - d * inv_mod2;
+}
+
+// blocks of 256 threads for n rows with P warps per 32-row slice
+inline int gk(long long n, int P) { return grid_for((n + 31) / 32, 8 / P); }
+
+// Runs the statement with the compile-time constant KK = kv (warps per slice).
+#define WITH_K(kv, ...)                                                         \
+    do {                                                                        \
+        switch (kv) {                                                           \
+            case 1: { constexpr int KK = 1; __VA_ARGS__; } break;               \
+            case 2: { constexpr int KK = 2; __VA_ARGS__; } break;               \
+            case 4: { constexpr int KK = 4; __VA_ARGS__; } break;               \
+            case 8: { constexpr int KK = 8; __VA_ARGS__; } break;               \
+            default: fail(AIRG_ERR_STATE, "bad warps-per-slice");               \
+        }                                                                       \
+    } while (0)
+
+// ------------------------------------------ persistent coarse polynomial --
+// Grid-wide barrier for a cooperative launch.  Thread 0 of each block
+// arrives on a counter; the last arrival resets it and advances the
+// generation the others wait on.  The wait is bounded: after
+// BARRIER_SPIN_LIMIT polls it records an error flag (AIRG_ERR_TIMEOUT on the
+// host) and lets the block continue, so a launch that is not co-resident
+// ends instead of hanging.
+constexpr long long BARRIER_SPIN_LIMIT = 20000000;   // ~1 s of 50 ns polls
+
+__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, int* err)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = gen;
+        unsigned g = *vgen;
+        __threadfence();
+        unsigned arrived = atomicAdd(count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == g) {
+                if (++spins > BARRIER_SPIN_LIMIT) { atomicExch(err, 1); break; }
+                __nanosleep(50);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// x = q(A) b with the Newton roots of Sec. 2.3 (real: x += r/th, r -= A r/th;
+// pair a+-ib: t = 2a r - A r, x += t/|th|^2, r -= A t/|th|^2), all steps in one
+// cooperative launch: one SpMV per phase, grid barrier between phases.
+// Blocks loop over groups of 8/P slices (same SELL-32 x P mapping as the
+// other kernels).  roots[2i], roots[2i+1] = (re, im), im == 0 for real.
+template <class T, int P>
+__global__ void __launch_bounds__(256)
+k_newton_persistent(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
+                    T* __restrict__ r0, T* __restrict__ r1, T* __restrict__ t,
+                    const double* __restrict__ roots, int nroots, unsigned* bar_count,
+                    unsigned* bar_gen, int* err)
+{
+    const int lane = threadIdx.x & 31;
+    const int part = (threadIdx.x >> 5) % P;
+    const int sl = (threadIdx.x >> 5) / P;
+    const int spb = 8 / P;
+    const int ngroups = (A.n_slices + spb - 1) / spb;
+    const int n = A.n_rows;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const T* rin = b;
+    T* rbuf[2] = {r0, r1};
+    int nb = 0;
+    for (int i = 0; i < nroots; ++i) {
+        const bool last = i == nroots - 1;
+        const T xz = T(0);
+        const double re = roots[2 * i], im = roots[2 * i + 1];
+        T* rout = rbuf[nb];
+        if (im == 0.0) {
+            const T inv = T(1.0 / re);
+            if (last) {
+                for (int q = gt; q < n; q += nt) x[q] = fma(rin[q], inv, i == 0 ? xz : x[q]);
+            } else {
+                for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+                    const int slice = g * spb + sl, row = slice * 32 + lane;
+                    T d = row_dot<T, P>(A, slice, lane, part, rin);
+                    if (part == 0 && row < n) {
+                        T ri = rin[row];
+                        x[row] = fma(ri, inv, i == 0 ? xz : x[row]);
+                        rout[row] = ri - d * inv;
+                    }
+                }
+            }
+        } else {
+            const T two_a = T(2.0 * re), inv2 = T(1.0 / (re * re + im * im));
+            for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+                const int slice = g * spb + sl, row = slice * 32 + lane;
+                T d = row_dot<T, P>(A, slice, lane, part, rin);
+                if (part == 0 && row < n) {
+                    T tt = two_a * rin[row] - d;
+                    t[row] = tt;
+                    x[row] = fma(tt, inv2, i == 0 ? xz : x[row]);
+                }
+            }
+            if (!last) {
+                grid_barrier(bar_count, bar_gen, err);
+                for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
+                    const int slice = g * spb + sl, row = slice * 32 + lane;
+                    T d = row_dot<T, P>(A, slice, lane, part, t);
+                    if (part == 0 && row < n) rout[row] = rin[row] - d * inv2;
+                }
+            }
+        }
+        if (!last) {
+            grid_barrier(bar_count, bar_gen, err);
+            rin = rout;
+            nb ^= 1;
+        }
+    }
 }
 
 // ---------------------------------------------------------- Krylov kernels --
 constexpr int RB = 256;          // reduction block
 constexpr int RGRID = 304;       // partial sums per reduction (2 x SMs)
 
-// part[b*m + i] = partial of <w, V_i> for i < m
+// out[i] = <w, V_i> for i < m.  Blocks write partial sums; the last block to
+// finish (atomic ticket) adds them in a fixed order and resets the ticket.
 __global__ void k_multidot(long long n, int m, const double* __restrict__ V, long long ldv,
-                           const double* __restrict__ w, double* __restrict__ part)
+                           const double* __restrict__ w, double* __restrict__ part,
+                           double* __restrict__ out, unsigned* ticket)
 {
     __shared__ double red[RB / 32][32];
+    __shared__ bool last_block;
     for (int i = 0; i < m; ++i) {
         double s = 0.0;
         for (long long r = (long long)blockIdx.x * RB + threadIdx.x; r < n; r += (long long)gridDim.x * RB)
@@ -406,6 +640,26 @@ __global__ void k_multidot(long long n, int m, const double* __restrict__ V, lon
         }
         __syncthreads();
     }
+    __threadfence();
+    if (threadIdx.x == 0) last_block = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last_block) return;
+    __threadfence();
+    const int nb = gridDim.x;
+    for (int i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int q = threadIdx.x; q < nb; q += RB) s += part[(long long)q * m + i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][0] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < RB / 32; ++q) t += red[q][0];
+            out[i] = t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // out[i] = sum_b part[b*m + i], fixed order
@@ -485,6 +739,21 @@ const Sell<double>& coarse_op<double>(const SolveData& S) { return S.Ac; }
 template <>
 const Sell<float>& coarse_op<float>(const SolveData& S) { return S.Ac32; }
 
+// grid of the persistent coarse kernel (0 if no block can be resident)
+template <class T>
+int newton_persistent_grid(const Sell<T>& A)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (A.n_rows < 1) return 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    WITH_K(A.k, CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton_persistent<T, KK>, 256, 0)));
+    if (per_sm < 1) return 0;
+    int spb = 8 / A.k;
+    int groups = (A.n_slices + spb - 1) / spb;
+    return std::min(groups, per_sm * sms);
+}
+
 // e = M^-1 v in the nested order.  v is only read; e is written everywhere.
 template <class T>
 void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
@@ -498,9 +767,9 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         const Sell<T>& Z = ops<T>(lv).Z;
         if (lv.n_c)
             LAUNCH(S, PK_RESTRICT, Z.nnz * (VB + 4) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB,
-                   k_restrict<T><<<grid_for(lv.n_c, TB), TB, 0, st>>>(view(Z), src + lv.off,
-                                                                      src + lv.off + lv.n_f,
-                                                                      wk.rwork + lv.off + lv.n_f));
+                   WITH_K(Z.k, k_restrict<T, KK><<<gk(lv.n_c, KK), TB, 0, st>>>(
+                                   view(Z), src + lv.off, src + lv.off + lv.n_f,
+                                   wk.rwork + lv.off + lv.n_f)));
     }
     // coarse-grid polynomial
     {
@@ -508,31 +777,60 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         T* x = e + S.off_c;
         const Sell<T>& A = coarse_op<T>(S);
         SellView<T> Av = view(A);
-        int g = grid_for(S.n_coarse, TB);
+        const int nco = S.n_coarse;
         const T* rin = rc;
         T* bufs[2] = {wk.cr0, wk.cr1};
         int nb = 0;
         size_t nr = S.roots.size();
         const long long nB = (long long)S.n_coarse * VB, mB = A.nnz * (VB + 4);
+        const int pidx = sizeof(T) == 8 ? 0 : 1;
+        if (S.newton_grid[pidx] > 0 && nr > 0) {
+            // all Newton steps in one cooperative launch
+            long long bytes = 0;
+            for (size_t i = 0; i < nr; ++i) {
+                bool last = i + 1 == nr;
+                bytes += S.roots[i].im == 0.0 ? (last ? 3 * nB : mB + 4 * nB) : (last ? mB + 4 * nB : 2 * mB + 8 * nB);
+            }
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(S.newton_grid[pidx]);
+            cfg.blockDim = dim3(256);
+            cfg.dynamicSmemBytes = 0;
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nroots = int(nr);
+            LAUNCH(S, PK_NEWTON, bytes,
+                   WITH_K(A.k, CK(cudaLaunchKernelEx(&cfg, k_newton_persistent<T, KK>, Av, rc, x, wk.cr0,
+                                                     wk.cr1, wk.ct, (const double*)S.roots_dev.p, nroots,
+                                                     S.bar.p, S.bar.p + 1, (int*)(S.bar.p + 2)))));
+            goto coarse_done;
+        }
         for (size_t i = 0; i < nr; ++i) {
             bool last = i + 1 == nr;
             const Root& q = S.roots[i];
             T* rout = bufs[nb];
             if (q.im == 0.0) {
                 LAUNCH(S, PK_NEWTON, (last ? 0 : mB + 2 * nB) + (i == 0 ? 2 : 3) * nB,
-                       k_newton_real<T><<<g, TB, 0, st>>>(Av, rin, rout, x, T(1.0 / q.re), i == 0, last));
+                       WITH_K(A.k, k_newton_real<T, KK><<<gk(nco, KK), TB, 0, st>>>(
+                                       Av, rin, rout, x, T(1.0 / q.re), i == 0, last)));
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
                 LAUNCH(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB,
-                       k_newton_pair1<T><<<g, TB, 0, st>>>(Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0));
+                       WITH_K(A.k, k_newton_pair1<T, KK><<<gk(nco, KK), TB, 0, st>>>(
+                                       Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
                 if (!last)
                     LAUNCH(S, PK_NEWTON, mB + 3 * nB,
-                           k_newton_pair2<T><<<g, TB, 0, st>>>(Av, rin, wk.ct, rout, T(1.0 / mod2)));
+                           WITH_K(A.k, k_newton_pair2<T, KK><<<gk(nco, KK), TB, 0, st>>>(
+                                           Av, rin, wk.ct, rout, T(1.0 / mod2))));
             }
             if (!last) { rin = rout; nb ^= 1; }
         }
         if (nr == 0) CK(cudaMemsetAsync(x, 0, sizeof(T) * S.n_coarse, st));
     }
+coarse_done:
     // up: prolongation + F-point smoothing, bottom to top
     for (int l = L - 1; l >= 0; --l) {
         const SolveLevel& lv = *S.lv[l];
@@ -546,7 +844,8 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         int p = int(lv.alpha.size()) - 1;
         const long long fB = (long long)nf * VB;
         LAUNCH(S, PK_FRESID, o.M.nnz * (VB + 4) + (long long)lv.n_c * VB + 3 * fB,
-               k_fresid<T><<<g, TB, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa, T(lv.alpha[p])));
+               WITH_K(o.M.k, k_fresid<T, KK><<<gk(nf, KK), TB, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
+                                                                       T(lv.alpha[p]))));
         if (p == 0) {
             LAUNCH(S, PK_HORNER, 3 * fB + 4LL * nf,
                    k_smooth0<T><<<g, TB, 0, st>>>(nf, wk.t, ec, lv.W.p, ef, T(lv.alpha[0])));
@@ -556,11 +855,14 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         T* win = wk.wa;
         T* wout = wk.wb;
         for (int k = p - 1; k >= 1; --k) {
-            LAUNCH(S, PK_HORNER, hB, k_horner<T><<<g, TB, 0, st>>>(view(o.Aff), wk.t, win, wout, T(lv.alpha[k])));
+            LAUNCH(S, PK_HORNER, hB,
+                   WITH_K(o.Aff.k, k_horner<T, KK><<<gk(nf, KK), TB, 0, st>>>(view(o.Aff), wk.t, win, wout,
+                                                                             T(lv.alpha[k]))));
             std::swap(win, wout);
         }
         LAUNCH(S, PK_HORNER, hB + fB + 4LL * nf,
-               k_horner_last<T><<<g, TB, 0, st>>>(view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0])));
+               WITH_K(o.Aff.k, k_horner_last<T, KK><<<gk(nf, KK), TB, 0, st>>>(view(o.Aff), wk.t, win, ec,
+                                                                                lv.W.p, ef, T(lv.alpha[0]))));
     }
     CK_LAUNCH();
 }
@@ -632,6 +934,20 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
     if (H.opt.precision == AIRG_MIXED_FP32) copy_sell_f32(S->Ac, S->Ac32, st);
     S->roots = H.coarse.roots;
     {
+        std::vector<double> rr;
+        for (const Root& q : S->roots) { rr.push_back(q.re); rr.push_back(q.im); }
+        S->roots_dev.alloc(std::max<size_t>(rr.size(), 2));
+        h2d(S->roots_dev.p, rr.data(), rr.size(), st);
+        S->bar.alloc(4);
+        CK(cudaMemsetAsync(S->bar.p, 0, S->bar.bytes(), st));
+        const char* np = getenv("AIRG_NO_PERSISTENT");
+        bool allow = !(np && np[0] == '1');
+        if (allow && H.opt.precision != AIRG_MIXED_FP32) S->newton_grid[0] = newton_persistent_grid<double>(S->Ac);
+        if (allow && H.opt.precision == AIRG_MIXED_FP32) S->newton_grid[1] = newton_persistent_grid<float>(S->Ac32);
+    }
+    S->ticket.alloc(1);
+    CK(cudaMemsetAsync(S->ticket.p, 0, sizeof(unsigned), st));
+    {
         int vb = H.opt.precision == AIRG_MIXED_FP32 ? 4 : 8;
         long long nsp = 0;
         for (size_t i = 0; i < S->roots.size(); ++i) {
@@ -670,6 +986,10 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
     S->part.alloc(size_t(RGRID) * (m + 2));
     S->hdev.alloc(size_t(3 * (m + 2)));
     S->hhost.alloc(size_t(3 * (m + 2)));
+    CK(cudaStreamCreateWithFlags(&S->sst, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming));
+    const char* ng = getenv("AIRG_NO_GRAPHS");
+    S->use_graphs = !(ng && ng[0] == '1');
     H.solve = std::move(S);
 }
 
@@ -677,14 +997,14 @@ namespace {
 
 double dev_norm(SolveData& S, const double* x, long long n, cudaStream_t st)
 {
-    LAUNCH(S, PK_KRYLOV, 8 * n, k_multidot<<<RGRID, RB, 0, st>>>(n, 1, x, n, x, S.part.p));
-    LAUNCH(S, PK_KRYLOV, 8LL * RGRID, k_sum_parts<<<1, 32, 0, st>>>(RGRID, 1, S.part.p, S.hdev.p));
+    LAUNCH(S, PK_KRYLOV, 8 * n,
+           k_multidot<<<RGRID, RB, 0, st>>>(n, 1, x, n, x, S.part.p, S.hdev.p, S.ticket.p));
     CK_LAUNCH();
     double v = read1(S.hdev.p, st);
     return std::sqrt(v);
 }
 
-void precond(Hierarchy& H, const double* v, double* z, cudaStream_t st)
+void precond_launch(Hierarchy& H, const double* v, double* z, cudaStream_t st)
 {
     SolveData& S = *H.solve;
     long long n = S.n0;
@@ -698,6 +1018,44 @@ void precond(Hierarchy& H, const double* v, double* z, cudaStream_t st)
         VWork<double> wk{S.rwork.p, S.t.p, S.wa.p, S.wb.p, nullptr, S.cr0.p, S.cr1.p, S.ct.p};
         vcycle<double>(S, v, z, wk, st);
     }
+}
+
+// z = M^-1 v: replays the captured V-cycle graph of this (v, z) pair, or
+// launches the kernels directly while profiling.
+void precond(Hierarchy& H, const double* v, double* z, cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    if (S.prof || !S.use_graphs) {
+        precond_launch(H, v, z, st);
+        return;
+    }
+    SolveData::GEntry* ge = nullptr;
+    for (auto& g : S.graphs)
+        if (g.v == v && g.z == z) { ge = &g; break; }
+    if (!ge) {
+        long long before = S.launches;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        try {
+            precond_launch(H, v, z, st);
+        } catch (...) {
+            cudaGraph_t g0;
+            cudaStreamEndCapture(st, &g0);
+            if (g0) cudaGraphDestroy(g0);
+            throw;
+        }
+        cudaGraph_t graph;
+        CK(cudaStreamEndCapture(st, &graph));
+        cudaGraphExec_t exec;
+        cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+        long long nk = S.launches - before;
+        S.launches = before;
+        S.graphs.push_back(SolveData::GEntry{v, z, exec, nk});
+        ge = &S.graphs.back();
+    }
+    CK(cudaGraphLaunch(ge->exec, st));
+    S.launches += ge->kernels;
 }
 
 // FGMRES(m) on the nested system; bp/xp hold b and x in nested order.
@@ -714,7 +1072,8 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
     double tol = std::max(rtol * bn, atol);
     int its = 0;
     auto residual = [&]() {
-        LAUNCH(S, PK_TOPSPMV, topB, k_spmv<double><<<g, TB, 0, st>>>(A, S.xp.p, S.w.p));
+        LAUNCH(S, PK_TOPSPMV, topB,
+               WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), TB, 0, st>>>(A, S.xp.p, S.w.p)));
         LAUNCH(S, PK_KRYLOV, 24 * n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
         CK_LAUNCH();
         return dev_norm(S, S.r.p, n, st);
@@ -731,19 +1090,19 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             double* vj = S.V.p + size_t(j) * n;
             double* zj = S.Zs.p + size_t(j) * n;
             precond(H, vj, zj, st);
-            LAUNCH(S, PK_TOPSPMV, topB, k_spmv<double><<<g, TB, 0, st>>>(A, zj, S.w.p));
+            LAUNCH(S, PK_TOPSPMV, topB,
+                   WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), TB, 0, st>>>(A, zj, S.w.p)));
             // classical Gram-Schmidt, twice
             for (int pass = 0; pass < 2; ++pass) {
                 LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 2),
-                       k_multidot<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, S.w.p, S.part.p));
-                LAUNCH(S, PK_KRYLOV, 8LL * RGRID * (j + 1),
-                       k_sum_parts<<<1, 32, 0, st>>>(RGRID, j + 1, S.part.p, S.hdev.p + pass * (m + 2)));
+                       k_multidot<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, S.w.p, S.part.p,
+                                                        S.hdev.p + pass * (m + 2), S.ticket.p));
                 LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 3),
                        k_multiaxpy<<<g, TB, 0, st>>>(n, j + 1, S.V.p, n, S.hdev.p + pass * (m + 2), S.w.p));
             }
-            LAUNCH(S, PK_KRYLOV, 8 * n, k_multidot<<<RGRID, RB, 0, st>>>(n, 1, S.w.p, n, S.w.p, S.part.p));
-            LAUNCH(S, PK_KRYLOV, 8LL * RGRID,
-                   k_sum_parts<<<1, 32, 0, st>>>(RGRID, 1, S.part.p, S.hdev.p + 2 * (m + 2)));
+            LAUNCH(S, PK_KRYLOV, 8 * n,
+                   k_multidot<<<RGRID, RB, 0, st>>>(n, 1, S.w.p, n, S.w.p, S.part.p,
+                                                    S.hdev.p + 2 * (m + 2), S.ticket.p));
             CK_LAUNCH();
             CK(cudaMemcpyAsync(hh, S.hdev.p, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -789,10 +1148,14 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
 }  // namespace
 
 void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_device, double rtol,
-                  double atol, int maxit, airg_solve_info* info_out, cudaStream_t st)
+                  double atol, int maxit, airg_solve_info* info_out, cudaStream_t caller)
 {
     auto t0 = std::chrono::steady_clock::now();
     SolveData& S = *H.solve;
+    // order after the caller's stream, then work on the private stream
+    CK(cudaEventRecord(S.ev_in, caller));
+    CK(cudaStreamWaitEvent(S.sst, S.ev_in, 0));
+    cudaStream_t st = S.sst;
     long long n = S.n0;
     long long launches0 = S.launches;
     airg_solve_info info{};
@@ -822,6 +1185,15 @@ void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_de
     }
     CK(cudaStreamSynchronize(st));
     S.collect();
+    {
+        unsigned err = 0;
+        d2h(&err, S.bar.p + 2, 1, st);
+        if (err) {
+            CK(cudaMemsetAsync(S.bar.p, 0, S.bar.bytes(), st));
+            CK(cudaStreamSynchronize(st));
+            fail(AIRG_ERR_TIMEOUT, "a grid barrier of the coarse-grid kernel gave up waiting");
+        }
+    }
     info.kernel_launches = S.launches - launches0;
     info.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info_out) *info_out = info;

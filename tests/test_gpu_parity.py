@@ -203,3 +203,12 @@ def test_c2_full_size():
     c = Case(workload("c2"))
     _check_setup(c)
     _check_solve(c)
+
+
+@pytest.mark.parametrize("env", ["AIRG_NO_GRAPHS", "AIRG_NO_PERSISTENT"])
+def test_fallback_launch_paths(env, monkeypatch):
+    """Direct kernel launches (no CUDA graph) and the per-root coarse kernels
+    (no persistent launch) give the same parity."""
+    monkeypatch.setenv(env, "1")
+    c = Case(workload("grid", (160, 120)))
+    _check_solve(c)
