@@ -250,6 +250,28 @@ airg_status airg_rng_uniform(uint64_t seed, int64_t level, int64_t purpose, int6
 airg_status airg_host_gmres_coeffs(int k, const double* H, double beta, double* alpha);
 airg_status airg_host_eigvals(int n, const double* H, double* wr, double* wi);
 
+/*
+ * airg_dot_exact_noalloc: the same correctly rounded <x, y> as
+ * airg_dot_exact, for callers that cannot allocate device memory (code
+ * running during CUDA graph capture, inside a framework whose pool owns every
+ * allocation, or on a latency-critical path where cudaMalloc's implicit
+ * synchronisation is not allowed).  The paper has no counterpart: it is a
+ * service of this library.
+ *  - Allocates nothing: its scratch is a file-scope __device__ array of
+ *    141 x 8 bytes (accumulator + inf/nan flag) that every GPU loading the
+ *    library keeps until the process exits.
+ *  - x, y: DEVICE pointers, length n; out: DEVICE pointer to one double.
+ *    Asynchronous: the result is in *out when `stream` reaches that point.
+ *  - n must be <= 2^31 - 1 (the accumulator's carry headroom);
+ *    AIRG_ERR_ARG beyond that, before any GPU work.
+ *  - The first call on a device looks up the scratch array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls on a device share the scratch: each call clears it first, and
+ *    calls that overlap on the GPU (different streams, no ordering) race.
+ */
+airg_status airg_dot_exact_noalloc(int64_t n, const double* x, const double* y, double* out,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ EXPORTS = ["airg_options_default", "airg_problem_advection2d", "airg_assemble_rh
            "airg_setup", "airg_solve", "airg_solve_adjoint", "airg_setup_info",
            "airg_export_matrix", "airg_export_vector", "airg_free", "airg_last_error",
            "airg_dot_exact", "airg_rng_uniform", "airg_host_gmres_coeffs", "airg_host_eigvals",
-           "airg_profile", "airg_profile_read"]
+           "airg_profile", "airg_profile_read", "airg_dot_exact_noalloc"]
 PROFILE_KINDS = ["restrict", "f_residual", "f_smoother", "coarse_newton", "top_spmv",
                  "krylov_vectors", "layout"]
 
@@ -102,6 +102,7 @@ def lib():
             "airg_host_gmres_coeffs": [ci, vp, f64, vp],
             "airg_host_eigvals": [ci, vp, vp, vp],
             "airg_profile": [vp, ci],
+            "airg_dot_exact_noalloc": [i64, vp, vp, vp, vp],
             "airg_profile_read": [vp, ci, ctypes.POINTER(f64), ctypes.POINTER(i64),
                                   ctypes.POINTER(i64)],
         }
@@ -284,6 +285,13 @@ def airg_dot_exact(x, y, stream=None):
     out = ctypes.c_double()
     _check(lib().airg_dot_exact(x.numel(), _ptr(x), _ptr(y), ctypes.byref(out), _stream(stream)))
     return out.value
+
+
+def airg_dot_exact_noalloc(x, y, out, stream=None, n=None):
+    """Correctly rounded <x, y> into the device tensor `out` (one double),
+    without any device allocation; asynchronous on the stream."""
+    n = x.numel() if n is None else n
+    _check(lib().airg_dot_exact_noalloc(n, _ptr(x), _ptr(y), _ptr(out), _stream(stream)))
 
 
 def airg_rng_uniform(seed, level, purpose, n, stream=None):

@@ -152,6 +152,11 @@ const airg::Hierarchy* level_owner(const airg_handle* h)
 
 }  // namespace
 
+namespace airg {
+// lets entry points outside this file report through airg_last_error()
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace airg
+
 extern "C" {
 
 airg_status airg_options_default(airg_options* o)

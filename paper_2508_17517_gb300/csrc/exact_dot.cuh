@@ -76,7 +76,7 @@ __device__ __forceinline__ void xd_add_product(unsigned long long* acc, double x
 
 // Block: XD_THREADS threads.  gacc: XD_DIGITS words, zero on entry of the
 // first block (cleared by the caller).  bad: set when an input is inf/nan.
-__global__ void __launch_bounds__(XD_THREADS)
+static __global__ void __launch_bounds__(XD_THREADS)
 k_xdot_accumulate(long long n, const double* __restrict__ x, const double* __restrict__ y,
                   unsigned long long* __restrict__ gacc, int* bad)
 {
@@ -100,7 +100,7 @@ k_xdot_accumulate(long long n, const double* __restrict__ x, const double* __res
 // One thread: carry propagation and round-to-nearest-even of the global
 // accumulator.  Writes the double to *out, optionally its square root to
 // *out_sqrt, and clears the accumulator for the next use.
-__device__ inline double xd_round(unsigned long long* g)
+static __device__ inline double xd_round(unsigned long long* g)
 {
     long long* d = reinterpret_cast<long long*>(g);
     long long carry = 0;
@@ -150,7 +150,7 @@ __device__ inline double xd_round(unsigned long long* g)
     return neg ? -r : r;
 }
 
-__global__ void k_xdot_finalize(unsigned long long* gacc, const int* bad, double* out,
+static __global__ void k_xdot_finalize(unsigned long long* gacc, const int* bad, double* out,
                                 double* out_sqrt)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
