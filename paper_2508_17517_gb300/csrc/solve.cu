@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <string>
 
 #include "dev_util.cuh"
 #include "handle.h"
@@ -62,15 +63,27 @@ struct SellView {
 template <class T>
 SellView<T> view(const Sell<T>& s) { return SellView<T>{s.n_rows, s.n_slices, s.sptr.p, s.col.p, s.val.p}; }
 
-// warps per slice from the mean row length (about 4-20 entries per lane)
+// Warps per slice from the mean row length: the smallest power of two that
+// leaves at most `per_lane` entries per lane (default 12), capped at
+// `max_parts` (default 8).  Both can be overridden for tuning with
+// AIRG_PER_LANE / AIRG_MAX_PARTS.
 inline int choose_parts(long long nnz, int n_rows)
 {
+    static int max_parts = 0, per_lane = 0;
+    if (!max_parts) {
+        const char* e = getenv("AIRG_MAX_PARTS");
+        max_parts = e ? std::max(1, std::min(32, atoi(e))) : 8;
+        const char* q = getenv("AIRG_PER_LANE");
+        per_lane = q ? std::max(1, atoi(q)) : 12;
+    }
     double avg = n_rows ? double(nnz) / n_rows : 0.0;
-    if (avg <= 12.0) return 1;
-    if (avg <= 32.0) return 2;
-    if (avg <= 80.0) return 4;
-    return 8;
+    int p = 1;
+    while (p < max_parts && avg > double(per_lane) * p) p *= 2;
+    return p;
 }
+
+// warps per block for P warps per slice (blocks of at least 8 warps)
+__host__ __device__ constexpr int wpb_for(int P) { return P > 8 ? P : 8; }
 
 template <class T>
 struct SolveLevelT {
@@ -98,6 +111,7 @@ struct SolveData {
     DBuf<unsigned> bar;          // [count, generation, error flag]
     DBuf<unsigned> ticket;       // last-block ticket of the dot kernels
     int newton_grid[2] = {0, 0}; // per precision (0: FP64, 1: FP32); 0 = not usable
+    int smooth_grid[2] = {0, 0}; // co-resident blocks of the persistent smoother
     int max_nf = 0;
     // V-cycle work (FP64 and FP32 copies)
     DBuf<double> rwork, t, wa, wb, cx, cr0, cr1, ct;
@@ -115,6 +129,7 @@ struct SolveData {
     std::vector<cudaEvent_t> evpool;
     size_t evnext = 0;
     std::vector<Rec> recs;
+    std::vector<cudaGraphExec_t> prof_execs;   // profiled V-cycle graphs awaiting collect()
     double kind_ms[PROF_KINDS] = {};
     long long kind_launches[PROF_KINDS] = {}, kind_bytes[PROF_KINDS] = {};
     cudaEvent_t next_event()
@@ -126,16 +141,25 @@ struct SolveData {
         }
         return evpool[evnext++];
     }
+    // inside a stream capture an event record becomes a timing node of the
+    // graph only with cudaEventRecordExternal
+    static void record(cudaEvent_t e, cudaStream_t st)
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(st, &cs));
+        if (cs == cudaStreamCaptureStatusActive) CK(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal));
+        else CK(cudaEventRecord(e, st));
+    }
     void begin(cudaStream_t st, cudaEvent_t& a)
     {
         ++launches;
-        if (prof) { a = next_event(); CK(cudaEventRecord(a, st)); }
+        if (prof) { a = next_event(); record(a, st); }
     }
     void end(int kind, long long bytes, cudaStream_t st, cudaEvent_t a)
     {
         if (!prof) return;
         cudaEvent_t b = next_event();
-        CK(cudaEventRecord(b, st));
+        record(b, st);
         recs.push_back(Rec{kind, a, b, bytes});
     }
     // after the stream has been synchronised
@@ -150,6 +174,8 @@ struct SolveData {
         }
         recs.clear();
         evnext = 0;
+        for (cudaGraphExec_t e : prof_execs) cudaGraphExecDestroy(e);
+        prof_execs.clear();
     }
     // private stream (capturable, unlike the legacy default stream) and the
     // V-cycle graphs, one per (input, output) pair = FGMRES basis slot
@@ -162,6 +188,7 @@ struct SolveData {
     {
         for (cudaEvent_t e : evpool) cudaEventDestroy(e);
         for (GEntry& g : graphs) cudaGraphExecDestroy(g.exec);
+        for (cudaGraphExec_t e : prof_execs) cudaGraphExecDestroy(e);
         if (ev_in) cudaEventDestroy(ev_in);
         if (sst) cudaStreamDestroy(sst);
     }
@@ -367,7 +394,7 @@ __device__ __forceinline__ T row_dot(const SellView<T>& S, int slice, int lane, 
         acc = strided_dot(S.col, S.val, x, b + lane + 32 * part, b + lane + 32 * w, 32 * P);
     }
     if (P > 1) {
-        __shared__ T red[8][32];
+        __shared__ T red[32][32];
         const int warp = threadIdx.x >> 5;
         red[warp][lane] = acc;
         __syncthreads();
@@ -380,11 +407,12 @@ __device__ __forceinline__ T row_dot(const SellView<T>& S, int slice, int lane, 
     return acc;
 }
 
-// Thread -> (slice, part, row) for 256-thread blocks: 8/P slices per block.
+// Thread -> (slice, part, row) for blocks of wpb_for(P) warps:
+// wpb_for(P)/P slices per block.
 #define ROW_IDS(P, NROWS)                                                   \
     const int lane = threadIdx.x & 31;                                      \
     const int part = (threadIdx.x >> 5) % (P);                              \
-    const int slice = blockIdx.x * (8 / (P)) + (threadIdx.x >> 5) / (P);    \
+    const int slice = blockIdx.x * (wpb_for(P) / (P)) + (threadIdx.x >> 5) / (P); \
     const int r = slice * 32 + lane;                                        \
     const bool lead = part == 0 && r < (NROWS)
 #define ROW_DOT(P, S, X) row_dot<T, P>((S), slice, lane, part, (X))
@@ -496,8 +524,9 @@ __global__ void k_newton_pair2(SellView<T> A, const T* __restrict__ rin, const T
     if (lead) rout[r] = rin[r] - d * inv_mod2;
 }
 
-// blocks of 256 threads for n rows with P warps per 32-row slice
-inline int gk(long long n, int P) { return grid_for((n + 31) / 32, 8 / P); }
+// blocks of wpb_for(P) warps for n rows with P warps per 32-row slice
+inline int gk(long long n, int P) { return grid_for((n + 31) / 32, wpb_for(P) / P); }
+inline int bk(int P) { return 32 * wpb_for(P); }
 
 // Runs the statement with the compile-time constant KK = kv (warps per slice).
 #define WITH_K(kv, ...)                                                         \
@@ -507,6 +536,8 @@ inline int gk(long long n, int P) { return grid_for((n + 31) / 32, 8 / P); }
             case 2: { constexpr int KK = 2; __VA_ARGS__; } break;               \
             case 4: { constexpr int KK = 4; __VA_ARGS__; } break;               \
             case 8: { constexpr int KK = 8; __VA_ARGS__; } break;               \
+            case 16: { constexpr int KK = 16; __VA_ARGS__; } break;             \
+            case 32: { constexpr int KK = 32; __VA_ARGS__; } break;             \
             default: fail(AIRG_ERR_STATE, "bad warps-per-slice");               \
         }                                                                       \
     } while (0)
@@ -550,7 +581,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, int
 // Blocks loop over groups of 8/P slices (same SELL-32 x P mapping as the
 // other kernels).  roots[2i], roots[2i+1] = (re, im), im == 0 for real.
 template <class T, int P>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(32 * wpb_for(P))
 k_newton_persistent(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
                     T* __restrict__ r0, T* __restrict__ r1, T* __restrict__ t,
                     const double* __restrict__ roots, int nroots, unsigned* bar_count,
@@ -559,7 +590,7 @@ k_newton_persistent(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
     const int lane = threadIdx.x & 31;
     const int part = (threadIdx.x >> 5) % P;
     const int sl = (threadIdx.x >> 5) / P;
-    const int spb = 8 / P;
+    const int spb = wpb_for(P) / P;
     const int ngroups = (A.n_slices + spb - 1) / spb;
     const int n = A.n_rows;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
@@ -611,6 +642,88 @@ k_newton_persistent(SellView<T> A, const T* __restrict__ b, T* __restrict__ x,
             rin = rout;
             nb ^= 1;
         }
+    }
+}
+
+// Row dot for a runtime number P of warps per slice (1024-thread blocks).
+template <class T>
+__device__ __forceinline__ T row_dot_rt(const SellView<T>& S, int slice, int lane, int part, int P,
+                                        const T* __restrict__ x, T (*red)[32])
+{
+    T acc = T(0);
+    if (slice < S.n_slices) {
+        int b = S.sptr[slice], w = (S.sptr[slice + 1] - b) >> 5;
+        acc = strided_dot(S.col, S.val, x, b + lane + 32 * part, b + lane + 32 * w, 32 * P);
+    }
+    if (P > 1) {
+        const int warp = threadIdx.x >> 5;
+        red[warp][lane] = acc;
+        __syncthreads();
+        if (part == 0)
+            for (int q = 1; q < P; ++q) acc += red[warp + q][lane];
+        __syncthreads();
+    }
+    return acc;
+}
+
+struct Coefs {
+    double a[32];
+};
+
+// F-point smoothing of one level (Eq. 6) in one cooperative launch:
+//   phase 0: t = r_f - M e_c, w = a_p t
+//   phase k (k = p-1..1): w' = a_k t + A_ff w
+//   last:   e_f = W e_c + a_0 t + A_ff w
+// with a grid barrier between phases (p barriers).  Blocks of 1024 threads
+// loop over groups of 32/P slices of each operator.
+template <class T>
+__global__ void __launch_bounds__(1024)
+k_smooth_persistent(SellView<T> M, int pm, SellView<T> A, int pa, const T* __restrict__ rf,
+                    const T* __restrict__ ec, const int* __restrict__ W, T* __restrict__ ef,
+                    T* __restrict__ t, T* __restrict__ wa, T* __restrict__ wb, Coefs al, int p,
+                    unsigned* bar_count, unsigned* bar_gen, int* err)
+{
+    __shared__ T red[32][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = A.n_rows;
+    {
+        const int part = warp % pm, spb = 32 / pm, ng = (M.n_slices + spb - 1) / spb;
+        const T ap = T(al.a[p]);
+        for (int g = blockIdx.x; g < ng; g += gridDim.x) {
+            const int slice = g * spb + warp / pm, row = slice * 32 + lane;
+            T d = row_dot_rt(M, slice, lane, part, pm, ec, red);
+            if (part == 0 && row < n) {
+                T tt = rf[row] - d;
+                t[row] = tt;
+                if (p > 0) wa[row] = ap * tt;
+                else {
+                    int wc = W[row];
+                    ef[row] = (wc >= 0 ? ec[wc] : T(0)) + T(al.a[0]) * tt;
+                }
+            }
+        }
+    }
+    const int part = warp % pa, spb = 32 / pa, ng = (A.n_slices + spb - 1) / spb;
+    const T* win = wa;
+    T* wout = wb;
+    for (int k = p - 1; k >= 0; --k) {
+        grid_barrier(bar_count, bar_gen, err);
+        const T ak = T(al.a[k]);
+        for (int g = blockIdx.x; g < ng; g += gridDim.x) {
+            const int slice = g * spb + warp / pa, row = slice * 32 + lane;
+            T d = row_dot_rt(A, slice, lane, part, pa, win, red);
+            if (part == 0 && row < n) {
+                T v = fma(ak, t[row], d);
+                if (k > 0) wout[row] = v;
+                else {
+                    int wc = W[row];
+                    ef[row] = (wc >= 0 ? ec[wc] : T(0)) + v;
+                }
+            }
+        }
+        const T* tmp = wout;
+        wout = const_cast<T*>(win);
+        win = tmp;
     }
 }
 
@@ -747,9 +860,9 @@ int newton_persistent_grid(const Sell<T>& A)
     if (A.n_rows < 1) return 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    WITH_K(A.k, CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton_persistent<T, KK>, 256, 0)));
+    WITH_K(A.k, CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_newton_persistent<T, KK>, bk(KK), 0)));
     if (per_sm < 1) return 0;
-    int spb = 8 / A.k;
+    int spb = wpb_for(A.k) / A.k;
     int groups = (A.n_slices + spb - 1) / spb;
     return std::min(groups, per_sm * sms);
 }
@@ -767,7 +880,7 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         const Sell<T>& Z = ops<T>(lv).Z;
         if (lv.n_c)
             LAUNCH(S, PK_RESTRICT, Z.nnz * (VB + 4) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB,
-                   WITH_K(Z.k, k_restrict<T, KK><<<gk(lv.n_c, KK), TB, 0, st>>>(
+                   WITH_K(Z.k, k_restrict<T, KK><<<gk(lv.n_c, KK), bk(KK), 0, st>>>(
                                    view(Z), src + lv.off, src + lv.off + lv.n_f,
                                    wk.rwork + lv.off + lv.n_f)));
     }
@@ -793,7 +906,7 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
             }
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(S.newton_grid[pidx]);
-            cfg.blockDim = dim3(256);
+            cfg.blockDim = dim3(bk(A.k));
             cfg.dynamicSmemBytes = 0;
             cfg.stream = st;
             cudaLaunchAttribute attr[1];
@@ -814,16 +927,16 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
             T* rout = bufs[nb];
             if (q.im == 0.0) {
                 LAUNCH(S, PK_NEWTON, (last ? 0 : mB + 2 * nB) + (i == 0 ? 2 : 3) * nB,
-                       WITH_K(A.k, k_newton_real<T, KK><<<gk(nco, KK), TB, 0, st>>>(
+                       WITH_K(A.k, k_newton_real<T, KK><<<gk(nco, KK), bk(KK), 0, st>>>(
                                        Av, rin, rout, x, T(1.0 / q.re), i == 0, last)));
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
                 LAUNCH(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB,
-                       WITH_K(A.k, k_newton_pair1<T, KK><<<gk(nco, KK), TB, 0, st>>>(
+                       WITH_K(A.k, k_newton_pair1<T, KK><<<gk(nco, KK), bk(KK), 0, st>>>(
                                        Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
                 if (!last)
                     LAUNCH(S, PK_NEWTON, mB + 3 * nB,
-                           WITH_K(A.k, k_newton_pair2<T, KK><<<gk(nco, KK), TB, 0, st>>>(
+                           WITH_K(A.k, k_newton_pair2<T, KK><<<gk(nco, KK), bk(KK), 0, st>>>(
                                            Av, rin, wk.ct, rout, T(1.0 / mod2))));
             }
             if (!last) { rin = rout; nb ^= 1; }
@@ -843,8 +956,32 @@ coarse_done:
         int g = grid_for(nf, TB);
         int p = int(lv.alpha.size()) - 1;
         const long long fB = (long long)nf * VB;
+        const int pidx2 = sizeof(T) == 8 ? 0 : 1;
+        if (S.smooth_grid[pidx2] > 0 && p < 32) {
+            Coefs al{};
+            for (int q = 0; q <= p; ++q) al.a[q] = lv.alpha[q];
+            int need = std::max((o.M.n_slices + 32 / o.M.k - 1) / (32 / o.M.k),
+                                (o.Aff.n_slices + 32 / o.Aff.k - 1) / (32 / o.Aff.k));
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(std::max(1, std::min(S.smooth_grid[pidx2], need)));
+            cfg.blockDim = dim3(1024);
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            long long bytes = o.M.nnz * (VB + 4) + (long long)lv.n_c * VB + 3 * fB +
+                              p * (o.Aff.nnz * (VB + 4) + 3 * fB) + fB + 4LL * nf;
+            SellView<T> Mv = view(o.M), Av2 = view(o.Aff);
+            LAUNCH(S, PK_HORNER, bytes,
+                   CK(cudaLaunchKernelEx(&cfg, k_smooth_persistent<T>, Mv, o.M.k, Av2, o.Aff.k, rf, ec,
+                                         (const int*)lv.W.p, ef, wk.t, wk.wa, wk.wb, al, p, S.bar.p,
+                                         S.bar.p + 1, (int*)(S.bar.p + 2))));
+            continue;
+        }
         LAUNCH(S, PK_FRESID, o.M.nnz * (VB + 4) + (long long)lv.n_c * VB + 3 * fB,
-               WITH_K(o.M.k, k_fresid<T, KK><<<gk(nf, KK), TB, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
+               WITH_K(o.M.k, k_fresid<T, KK><<<gk(nf, KK), bk(KK), 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
                                                                        T(lv.alpha[p]))));
         if (p == 0) {
             LAUNCH(S, PK_HORNER, 3 * fB + 4LL * nf,
@@ -856,12 +993,12 @@ coarse_done:
         T* wout = wk.wb;
         for (int k = p - 1; k >= 1; --k) {
             LAUNCH(S, PK_HORNER, hB,
-                   WITH_K(o.Aff.k, k_horner<T, KK><<<gk(nf, KK), TB, 0, st>>>(view(o.Aff), wk.t, win, wout,
+                   WITH_K(o.Aff.k, k_horner<T, KK><<<gk(nf, KK), bk(KK), 0, st>>>(view(o.Aff), wk.t, win, wout,
                                                                              T(lv.alpha[k]))));
             std::swap(win, wout);
         }
         LAUNCH(S, PK_HORNER, hB + fB + 4LL * nf,
-               WITH_K(o.Aff.k, k_horner_last<T, KK><<<gk(nf, KK), TB, 0, st>>>(view(o.Aff), wk.t, win, ec,
+               WITH_K(o.Aff.k, k_horner_last<T, KK><<<gk(nf, KK), bk(KK), 0, st>>>(view(o.Aff), wk.t, win, ec,
                                                                                 lv.W.p, ef, T(lv.alpha[0]))));
     }
     CK_LAUNCH();
@@ -940,10 +1077,26 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         h2d(S->roots_dev.p, rr.data(), rr.size(), st);
         S->bar.alloc(4);
         CK(cudaMemsetAsync(S->bar.p, 0, S->bar.bytes(), st));
-        const char* np = getenv("AIRG_NO_PERSISTENT");
-        bool allow = !(np && np[0] == '1');
+        // persistent (cooperative, grid-barrier) polynomial kernels: opt-in;
+        // graph-launched per-term kernels measured faster on GB300
+        const char* pe = getenv("AIRG_PERSISTENT");
+        std::string pv = pe ? pe : "";
+        bool allow = pv == "1" || pv == "coarse";
+        bool allow_s = pv == "1" || pv == "smoother";
         if (allow && H.opt.precision != AIRG_MIXED_FP32) S->newton_grid[0] = newton_persistent_grid<double>(S->Ac);
         if (allow && H.opt.precision == AIRG_MIXED_FP32) S->newton_grid[1] = newton_persistent_grid<float>(S->Ac32);
+        if (allow_s) {
+            int dev = 0, sms = 0, per = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            if (H.opt.precision != AIRG_MIXED_FP32) {
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_smooth_persistent<double>, 1024, 0));
+                S->smooth_grid[0] = per * sms;
+            } else {
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_smooth_persistent<float>, 1024, 0));
+                S->smooth_grid[1] = per * sms;
+            }
+        }
     }
     S->ticket.alloc(1);
     CK(cudaMemsetAsync(S->ticket.p, 0, sizeof(unsigned), st));
@@ -1025,8 +1178,30 @@ void precond_launch(Hierarchy& H, const double* v, double* z, cudaStream_t st)
 void precond(Hierarchy& H, const double* v, double* z, cudaStream_t st)
 {
     SolveData& S = *H.solve;
-    if (S.prof || !S.use_graphs) {
+    if (!S.use_graphs) {
         precond_launch(H, v, z, st);
+        return;
+    }
+    if (S.prof) {
+        // profiled V-cycle: captured afresh with its event pairs, so that the
+        // kernels run as in an unprofiled solve (no host launch gaps)
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        try {
+            precond_launch(H, v, z, st);
+        } catch (...) {
+            cudaGraph_t g0;
+            cudaStreamEndCapture(st, &g0);
+            if (g0) cudaGraphDestroy(g0);
+            throw;
+        }
+        cudaGraph_t graph;
+        CK(cudaStreamEndCapture(st, &graph));
+        cudaGraphExec_t exec;
+        cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+        S.prof_execs.push_back(exec);
+        CK(cudaGraphLaunch(exec, st));
         return;
     }
     SolveData::GEntry* ge = nullptr;
@@ -1073,7 +1248,7 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
     int its = 0;
     auto residual = [&]() {
         LAUNCH(S, PK_TOPSPMV, topB,
-               WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), TB, 0, st>>>(A, S.xp.p, S.w.p)));
+               WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), bk(KK), 0, st>>>(A, S.xp.p, S.w.p)));
         LAUNCH(S, PK_KRYLOV, 24 * n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
         CK_LAUNCH();
         return dev_norm(S, S.r.p, n, st);
@@ -1091,7 +1266,7 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             double* zj = S.Zs.p + size_t(j) * n;
             precond(H, vj, zj, st);
             LAUNCH(S, PK_TOPSPMV, topB,
-                   WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), TB, 0, st>>>(A, zj, S.w.p)));
+                   WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), bk(KK), 0, st>>>(A, zj, S.w.p)));
             // classical Gram-Schmidt, twice
             for (int pass = 0; pass < 2; ++pass) {
                 LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 2),

@@ -205,10 +205,12 @@ def test_c2_full_size():
     _check_solve(c)
 
 
-@pytest.mark.parametrize("env", ["AIRG_NO_GRAPHS", "AIRG_NO_PERSISTENT"])
-def test_fallback_launch_paths(env, monkeypatch):
-    """Direct kernel launches (no CUDA graph) and the per-root coarse kernels
-    (no persistent launch) give the same parity."""
-    monkeypatch.setenv(env, "1")
+@pytest.mark.parametrize("env", [("AIRG_NO_GRAPHS", "1"), ("AIRG_PERSISTENT", "1"),
+                                 ("AIRG_PERSISTENT", "coarse"), ("AIRG_PERSISTENT", "smoother")])
+def test_alternative_launch_paths(env, monkeypatch):
+    """Direct kernel launches (no CUDA graph) and the persistent cooperative
+    polynomial kernels (coarse Newton and/or F smoother, one launch each with
+    a bounded grid barrier) give the same parity as the default path."""
+    monkeypatch.setenv(*env)
     c = Case(workload("grid", (160, 120)))
     _check_solve(c)
