@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "dev_util.cuh"
@@ -61,43 +62,49 @@ __global__ void k_scan_block(const int* in, int* out, int* sums, int n)
     if (threadIdx.x == SCAN_B - 1) sums[blockIdx.x] = incl;
 }
 
-// single block: exclusive scan of the block sums, in chunks
+// single block: exclusive scan of the block sums, in chunks, in 64-bit;
+// *total = -1 if any prefix exceeds the int32 index space
 __global__ void k_scan_sums(int* sums, int nb, int* total)
 {
-    __shared__ int wsum[32];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
+    __shared__ long long wsum[32];
+    __shared__ long long carry;
+    __shared__ int overflow;
+    if (threadIdx.x == 0) { carry = 0; overflow = 0; }
     __syncthreads();
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int base = 0; base < nb; base += SCAN_B) {
         int i = base + threadIdx.x;
-        int v = i < nb ? sums[i] : 0;
-        int x = v;
+        long long v = i < nb ? sums[i] : 0;
+        long long x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
+            long long y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) wsum[w] = x;
         __syncthreads();
         if (w == 0) {
-            int s = wsum[lane];
+            long long s = wsum[lane];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, s, o);
+                long long y = __shfl_up_sync(0xffffffffu, s, o);
                 if (lane >= o) s += y;
             }
             wsum[lane] = s;
         }
         __syncthreads();
-        int incl = x + (w > 0 ? wsum[w - 1] : 0);
-        int c = carry;
-        if (i < nb) sums[i] = c + incl - v;
+        long long incl = x + (w > 0 ? wsum[w - 1] : 0);
+        long long c = carry;
+        long long ex = c + incl - v;
+        if (i < nb) {
+            if (ex > 0x7fffffffLL) overflow = 1;
+            sums[i] = int(ex);
+        }
         __syncthreads();
         if (threadIdx.x == SCAN_B - 1) carry = c + incl;
         __syncthreads();
     }
-    if (threadIdx.x == 0) *total = carry;
+    if (threadIdx.x == 0) *total = (overflow || carry > 0x7fffffffLL) ? -1 : int(carry);
 }
 
 __global__ void k_scan_add(int* out, const int* sums, int n, const int* total)
@@ -123,7 +130,9 @@ void exclusive_scan_async(const int* in, int* out, int n, cudaStream_t st)
 int exclusive_scan(const int* in, int* out, int n, cudaStream_t st)
 {
     exclusive_scan_async(in, out, n, st);
-    return read1(out + n, st);
+    int total = read1(out + n, st);
+    if (total < 0) fail(AIRG_ERR_OOM, "index space of a setup product exceeds 2^31 entries");
+    return total;
 }
 
 namespace {
@@ -508,13 +517,14 @@ __global__ void k_gemm_bound(int m, const int* arp, const int* aci, const int* b
 
 __device__ __forceinline__ unsigned hash_col(int j) { return (unsigned)j * 2654435761u; }
 
-__global__ void k_gemm_hash(int m, const int* arp, const int* aci, const double* av,
+__global__ void k_gemm_hash(int m, int row0, const int* arp, const int* aci, const double* av,
                             const int* brp, const int* bci, const double* bv, const int* toff,
                             int* keys, double* vals, int* cnt)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
-    int base = toff[i], size = toff[i + 1] - base;
+    int li = blockIdx.x * blockDim.x + threadIdx.x;   // row within the chunk
+    if (li >= m) return;
+    int i = row0 + li;
+    int base = toff[li], size = toff[li + 1] - base;
     int c = 0;
     if (size > 0) {
         unsigned mask = (unsigned)size - 1u;
@@ -539,7 +549,13 @@ __global__ void k_gemm_hash(int m, const int* arp, const int* aci, const double*
             }
         }
     }
-    cnt[i] = c;
+    cnt[li] = c;
+}
+
+__global__ void k_shift_rowptr(int m, const int* prp, int off, int* crp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) crp[i] = prp[i] + off;
 }
 
 __global__ void k_gemm_emit(int m, const int* toff, const int* keys, const double* vals,
@@ -757,28 +773,87 @@ void submatrix(const DevCSR& A, const int* rows, int nr, const int* colmap, int 
     CK_LAUNCH();
 }
 
+// C = A B.  Rows are processed in chunks whose hash tables hold at most
+// 2^28 slots (3 GiB) together, so large fill-heavy levels neither overflow
+// the int32 table offsets nor exhaust memory; each chunk's rows are emitted
+// into a piece that is then copied into C.
 void spgemm(const DevCSR& A, const DevCSR& B, DevCSR& C, cudaStream_t st)
 {
     int m = A.n_rows;
     C.n_rows = m;
     C.n_cols = B.n_cols;
+    DBuf<int> tsize(size_t(m) + 1);
+    if (m) k_gemm_bound<<<grid_for(m, TB), TB, 0, st>>>(m, A.rp.p, A.ci.p, B.rp.p, tsize.p);
+    CK_LAUNCH();
+    std::vector<int> ts(static_cast<size_t>(m));
+    d2h(ts.data(), tsize.p, size_t(m), st);
+    static long long kLimit = 0;
+    if (!kLimit) {
+        const char* e = getenv("AIRG_SPGEMM_SLOTS");   // tuning / testing override
+        kLimit = e ? std::max(1LL, atoll(e)) : (1LL << 28);
+    }
+    std::vector<int> cut{0};
+    long long acc = 0;
+    for (int i = 0; i < m; ++i) {
+        if (acc + ts[i] > kLimit && i > cut.back()) { cut.push_back(i); acc = 0; }
+        acc += ts[i];
+    }
+    cut.push_back(m);
+    struct Piece {
+        int r0 = 0, r1 = 0, nnz = 0;
+        DBuf<int> rp, ci;
+        DBuf<double> v;
+    };
+    std::vector<Piece> pieces;
+    long long total = 0;
+    for (size_t c = 0; c + 1 < cut.size(); ++c) {
+        Piece P;
+        P.r0 = cut[c];
+        P.r1 = cut[c + 1];
+        int mc = P.r1 - P.r0;
+        DBuf<int> toff(size_t(mc) + 1);
+        if (mc) CK(cudaMemcpyAsync(toff.p, tsize.p + P.r0, size_t(mc) * sizeof(int), cudaMemcpyDeviceToDevice, st));
+        int tsz = exclusive_scan(toff.p, toff.p, mc, st);
+        DBuf<int> keys(std::max(tsz, 1));
+        DBuf<double> vals(std::max(tsz, 1));
+        CK(cudaMemsetAsync(keys.p, 0xff, keys.bytes(), st));
+        P.rp.alloc(size_t(mc) + 1);
+        if (mc) k_gemm_hash<<<grid_for(mc, TB), TB, 0, st>>>(mc, P.r0, A.rp.p, A.ci.p, A.v.p, B.rp.p,
+                                                               B.ci.p, B.v.p, toff.p, keys.p, vals.p, P.rp.p);
+        CK_LAUNCH();
+        P.nnz = exclusive_scan(P.rp.p, P.rp.p, mc, st);
+        P.ci.alloc(std::max(P.nnz, 1));
+        P.v.alloc(std::max(P.nnz, 1));
+        if (mc) k_gemm_emit<<<grid_for(mc, TB), TB, 0, st>>>(mc, toff.p, keys.p, vals.p, P.rp.p, P.ci.p,
+                                                               P.v.p);
+        CK_LAUNCH();
+        CK(cudaStreamSynchronize(st));
+        total += P.nnz;
+        pieces.push_back(std::move(P));
+    }
+    if (total > 0x7fffffffLL) fail(AIRG_ERR_OOM, "sparse product exceeds 2^31 entries");
+    C.nnz = int(total);
+    if (pieces.size() == 1) {
+        C.rp = std::move(pieces[0].rp);
+        C.ci = std::move(pieces[0].ci);
+        C.v = std::move(pieces[0].v);
+        return;
+    }
     C.rp.alloc(size_t(m) + 1);
-    DBuf<int> toff(size_t(m) + 1);
-    if (m) k_gemm_bound<<<grid_for(m, TB), TB, 0, st>>>(m, A.rp.p, A.ci.p, B.rp.p, toff.p);
-    CK_LAUNCH();
-    int tsz = exclusive_scan(toff.p, toff.p, m, st);
-    DBuf<int> keys(std::max(tsz, 1));
-    DBuf<double> vals(std::max(tsz, 1));
-    CK(cudaMemsetAsync(keys.p, 0xff, keys.bytes(), st));
-    if (m) k_gemm_hash<<<grid_for(m, TB), TB, 0, st>>>(m, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p,
-                                                         B.v.p, toff.p, keys.p, vals.p, C.rp.p);
-    CK_LAUNCH();
-    C.nnz = counts_to_rowptr(C.rp, m, st);
-    C.ci.alloc(C.nnz);
-    C.v.alloc(C.nnz);
-    if (m) k_gemm_emit<<<grid_for(m, TB), TB, 0, st>>>(m, toff.p, keys.p, vals.p, C.rp.p, C.ci.p,
-                                                         C.v.p);
-    CK_LAUNCH();
+    C.ci.alloc(std::max(C.nnz, 1));
+    C.v.alloc(std::max(C.nnz, 1));
+    int off = 0;
+    for (Piece& P : pieces) {
+        int mc = P.r1 - P.r0;
+        if (mc) k_shift_rowptr<<<grid_for(mc, TB), TB, 0, st>>>(mc, P.rp.p, off, C.rp.p + P.r0);
+        CK_LAUNCH();
+        if (P.nnz) {
+            CK(cudaMemcpyAsync(C.ci.p + off, P.ci.p, size_t(P.nnz) * sizeof(int), cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(C.v.p + off, P.v.p, size_t(P.nnz) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
+        off += P.nnz;
+    }
+    CK(cudaMemcpyAsync(C.rp.p + m, &C.nnz, sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
 }
 

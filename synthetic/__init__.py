@@ -41,15 +41,17 @@ def workload(name, n=None):
         return dict(nx=nx, ny=ny, theta=th, g=g, s=None, n_rhs=1, rtol=1e-10,
                     opts=dict(coarse_poly_order=30, trunc_rtol=1e-2),
                     desc="%dx%d theta~U[pi/12,5pi/12] g~U[0.5,2] m_c=30 trunc=1e-2" % (nx, ny))
-    if name == "c3":
+    if name in ("c3", "c3_fp64"):
         # 4096x4096, seeded theta, g ~ U[0,1] per inflow node; FP32 V-cycle
+        # inside FP64 FGMRES ("c3_fp64": the same problem with an FP64 V-cycle)
         nx = ny = n or 4096
         rng = np.random.default_rng(BASE_SEED + 3)
         th = float(rng.uniform(math.pi / 12, 5 * math.pi / 12))
         g = rng.uniform(0.0, 1.0, (1, _n_inflow(nx, ny, th)))
+        prec = 1 if name == "c3" else 0
         return dict(nx=nx, ny=ny, theta=th, g=g, s=None, n_rhs=1, rtol=1e-10,
-                    opts=dict(coarse_poly_order=30, trunc_rtol=1e-2, precision=1),
-                    desc="%dx%d theta seeded g~U[0,1] FP32 V-cycle" % (nx, ny))
+                    opts=dict(coarse_poly_order=30, trunc_rtol=1e-2, precision=prec),
+                    desc="%dx%d theta seeded g~U[0,1] %s V-cycle" % (nx, ny, "FP32" if prec else "FP64"))
     if name == "c4a":
         # 2048x2048, one operator, 64 right-hand sides: g ~ U[0,1], s ~ N(0,1)
         nx = ny = n or 2048

@@ -18,6 +18,7 @@ from oracle import airg as O  # noqa: E402
 from synthetic import velocity, workload  # noqa: E402
 
 pytestmark = pytest.mark.gpu
+T_ROOT = __import__("os").path.dirname(__import__("os").path.dirname(__import__("os").path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -214,3 +215,16 @@ def test_alternative_launch_paths(env, monkeypatch):
     monkeypatch.setenv(*env)
     c = Case(workload("grid", (160, 120)))
     _check_solve(c)
+
+
+def test_chunked_sparse_products(monkeypatch):
+    """Sparse products split into many row chunks (tiny hash-table budget)
+    give the same bits as in one chunk."""
+    monkeypatch.setenv("AIRG_SPGEMM_SLOTS", "4096")
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r); import tests.test_gpu_parity as T; "
+            "from synthetic import workload; c = T.Case(workload('grid', (150, 130))); "
+            "T._check_setup(c); T._check_solve(c)" % T_ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
