@@ -139,6 +139,19 @@ airg_status airg_assemble_rhs_advection2d(int64_t nx, int64_t ny, double vx, dou
                                           double* b, void* stream);
 
 /*
+ * Transpose of airg_assemble_rhs_advection2d, for gradients through a solve:
+ * with lambda = A^-T dL/du (airg_solve_adjoint), dL/dg = B^T lambda and
+ * dL/ds = h lambda: grad_g[k] = d * lambda[inflow[k]], grad_s[i] = h *
+ * lambda[i] on nodes that are not inflow nodes and 0 on inflow nodes (the
+ * source does not enter their rows).  nrhs systems one after the other;
+ * grad_s may be NULL.  DEVICE pointers.
+ */
+airg_status airg_rhs_adjoint_advection2d(int64_t nx, int64_t ny, double vx, double vy, double h,
+                                         int nrhs, const int64_t* inflow, int64_t n_inflow,
+                                         const double* lambda, double* grad_g, double* grad_s,
+                                         void* stream);
+
+/*
  * AIRG setup (Sec. 2): the level loop of truncation test (Sec. 2.4), CF
  * splitting (Sec. 2.1), block extraction, GMRES polynomial coefficients
  * (Eq. 4), fixed-sparsity inverse (Eq. 5), restrictor with drop, one-point

@@ -26,7 +26,8 @@ EXPORTS = ["airg_options_default", "airg_problem_advection2d", "airg_assemble_rh
            "airg_setup", "airg_solve", "airg_solve_adjoint", "airg_setup_info",
            "airg_export_matrix", "airg_export_vector", "airg_free", "airg_last_error",
            "airg_dot_exact", "airg_rng_uniform", "airg_host_gmres_coeffs", "airg_host_eigvals",
-           "airg_profile", "airg_profile_read", "airg_dot_exact_noalloc"]
+           "airg_profile", "airg_profile_read", "airg_dot_exact_noalloc",
+           "airg_rhs_adjoint_advection2d"]
 PROFILE_KINDS = ["restrict", "f_residual", "f_smoother", "coarse_newton", "top_spmv",
                  "krylov_vectors", "layout"]
 
@@ -103,6 +104,7 @@ def lib():
             "airg_host_eigvals": [ci, vp, vp, vp],
             "airg_profile": [vp, ci],
             "airg_dot_exact_noalloc": [i64, vp, vp, vp, vp],
+            "airg_rhs_adjoint_advection2d": [i64, i64, f64, f64, f64, ci, vp, i64, vp, vp, vp, vp],
             "airg_profile_read": [vp, ci, ctypes.POINTER(f64), ctypes.POINTER(i64),
                                   ctypes.POINTER(i64)],
         }
@@ -177,6 +179,24 @@ def airg_assemble_rhs_advection2d(prob, g, s=None, stream=None):
                                                _ptr(prob["inflow"]), prob["inflow"].numel(),
                                                _ptr(g), sp, _ptr(b), _stream(stream)))
     return b.view(nrhs, prob["n"]) if nrhs > 1 else b
+
+
+def airg_rhs_adjoint_advection2d(prob, lam, want_s=True, stream=None):
+    """(grad_g, grad_s) = (B^T lam, h lam off the inflow nodes) for one or
+    more adjoint vectors lam (device, float64)."""
+    import torch
+    nrhs = lam.shape[0] if lam.dim() == 2 else 1
+    nin = prob["inflow"].numel()
+    gg = torch.empty(nrhs * nin, dtype=torch.float64, device="cuda")
+    gs = torch.empty(nrhs * prob["n"], dtype=torch.float64, device="cuda") if want_s else None
+    lam = lam.contiguous()
+    _check(lib().airg_rhs_adjoint_advection2d(
+        prob["nx"], prob["ny"], float(prob["vx"]), float(prob["vy"]), float(prob["h"]), nrhs,
+        _ptr(prob["inflow"]), nin, _ptr(lam), _ptr(gg), _ptr(gs) if gs is not None else None,
+        _stream(stream)))
+    if nrhs > 1:
+        return gg.view(nrhs, nin), (gs.view(nrhs, prob["n"]) if gs is not None else None)
+    return gg, gs
 
 
 class Handle:
@@ -315,3 +335,50 @@ def airg_host_eigvals(H):
     wr, wi = np.empty(n), np.empty(n)
     _check(lib().airg_host_eigvals(n, H.ctypes.data, wr.ctypes.data, wi.ctypes.data))
     return wr + 1j * wi
+
+
+# ---------------------------------------------------------------- autograd --
+def _make_autograd():
+    import torch
+
+    class AdvectionSolveFn(torch.autograd.Function):
+        """u = A^-1 (B g + h s) with gradients by one adjoint AIRG solve on
+        A^T: dL/dg = B^T lambda, dL/ds = h lambda (inflow rows excluded),
+        lambda = A^-T dL/du."""
+
+        @staticmethod
+        def forward(ctx, g, s, solver, rtol):
+            u = solver.solve_plain(g, s, rtol)
+            ctx.solver, ctx.rtol, ctx.s_dtype = solver, rtol, s.dtype
+            return u
+
+        @staticmethod
+        def backward(ctx, gu):
+            lam, _ = airg_solve_adjoint(ctx.solver.handle, gu.contiguous().double(), rtol=ctx.rtol)
+            gg, gs = airg_rhs_adjoint_advection2d(ctx.solver.prob, lam)
+            return gg, gs.to(ctx.s_dtype), None, None
+
+    return AdvectionSolveFn
+
+
+class AdvectionSolver:
+    """The upwind advection problem of Eq. 1-2 on an nx-by-ny grid with an
+    AIRG hierarchy; solve(g, s) is differentiable in the inflow values g
+    (float64) and the source s (float32 or float64) through the adjoint."""
+
+    def __init__(self, nx, ny, vx, vy, h=None, opts=None):
+        self.prob = airg_problem_advection2d(nx, ny, vx, vy, h)
+        p = self.prob
+        self.handle = airg_setup(p["rowptr"], p["col"], p["val"], opts)
+        self._fn = None
+
+    def solve_plain(self, g, s=None, rtol=1e-10):
+        sd = s.double() if s is not None else None
+        b = airg_assemble_rhs_advection2d(self.prob, g.double(), sd)
+        u, info = airg_solve(self.handle, b, rtol=rtol)
+        return u
+
+    def solve(self, g, s, rtol=1e-10):
+        if self._fn is None:
+            self._fn = _make_autograd()
+        return self._fn.apply(g, s, self, rtol)

@@ -93,6 +93,18 @@ __global__ void k_rhs_inflow(long long nin, double d, const int64_t* inflow, con
     if (k < nin) b[inflow[k]] = __dmul_rn(d, g[k]);
 }
 
+__global__ void k_grad_g(long long nin, double d, const int64_t* inflow, const double* lam, double* gg)
+{
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nin) gg[k] = __dmul_rn(d, lam[inflow[k]]);
+}
+
+__global__ void k_zero_at(long long nin, const int64_t* idx, double* v)
+{
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nin) v[idx[k]] = 0.0;
+}
+
 __global__ void k_rp64_to_32(long long n, const int64_t* a, int* b)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -230,6 +242,33 @@ airg_status airg_assemble_rhs_advection2d(int64_t nx, int64_t ny, double vx, dou
                 k_rhs_inflow<<<airg::grid_for(n_inflow, TB), TB, 0, st>>>(n_inflow, d, inflow,
                                                                           g + size_t(q) * n_inflow,
                                                                           b + size_t(q) * n);
+            CK_LAUNCH();
+        }
+        CK(cudaStreamSynchronize(st));
+    });
+}
+
+airg_status airg_rhs_adjoint_advection2d(int64_t nx, int64_t ny, double vx, double vy, double h,
+                                         int nrhs, const int64_t* inflow, int64_t n_inflow,
+                                         const double* lambda, double* grad_g, double* grad_s,
+                                         void* stream)
+{
+    return guarded([&] {
+        if (nx < 2 || ny < 2 || nrhs < 1 || !inflow || !lambda || !grad_g || n_inflow < 0)
+            airg::fail(AIRG_ERR_ARG, "bad rhs-adjoint arguments");
+        cudaStream_t st = (cudaStream_t)stream;
+        long long n = nx * ny;
+        double d = std::fabs(vx) + std::fabs(vy);
+        for (int q = 0; q < nrhs; ++q) {
+            const double* lam = lambda + size_t(q) * n;
+            if (n_inflow)
+                k_grad_g<<<airg::grid_for(n_inflow, TB), TB, 0, st>>>(n_inflow, d, inflow, lam,
+                                                                      grad_g + size_t(q) * n_inflow);
+            if (grad_s) {
+                double* gs = grad_s + size_t(q) * n;
+                k_rhs_source<<<airg::grid_for(n, TB), TB, 0, st>>>(n, h, lam, gs);
+                if (n_inflow) k_zero_at<<<airg::grid_for(n_inflow, TB), TB, 0, st>>>(n_inflow, inflow, gs);
+            }
             CK_LAUNCH();
         }
         CK(cudaStreamSynchronize(st));
