@@ -41,7 +41,8 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c3_fp64"])
+    ap.add_argument("--workload", default="c2",
+                    choices=["c1", "c2", "c3", "c3_fp64", "c4a", "c4a_fp64", "c4b"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
 
@@ -124,11 +125,15 @@ class Clocks:
 
 # --------------------------------------------------------------- workloads --
 def problem_and_rhs(w, G, torch):
+    """Operator and the right-hand sides b (n, or k x n for k > 1) on the device."""
     from synthetic import velocity
     vx, vy = velocity(w["theta"])
     prob = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
-    g = torch.tensor(w["g"][0], device="cuda")
-    s = torch.tensor(w["s"][0], device="cuda") if w["s"] is not None else None
+    k = w["n_rhs"]
+    g = torch.tensor(w["g"] if k > 1 else w["g"][0], device="cuda")
+    s = None
+    if w["s"] is not None:
+        s = torch.tensor(w["s"] if k > 1 else w["s"][0], device="cuda")
     b = G.airg_assemble_rhs_advection2d(prob, g, s)
     return prob, b
 
@@ -179,6 +184,84 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_gpu_multi(args):
+    """Workload of many separate grids of uneven size (one hierarchy each)."""
+    import torch
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2508_17517_gb300 as G
+    from synthetic import velocity, workload
+    G.lib()
+    w = workload(args.workload)
+    csrs, bs = [], []
+    for p in w["problems"]:
+        vx, vy = velocity(p["theta"])
+        pg = G.airg_problem_advection2d(p["nx"], p["ny"], vx, vy)
+        csrs.append((pg["rowptr"], pg["col"], pg["val"]))
+        bs.append(G.airg_assemble_rhs_advection2d(pg, torch.tensor(p["g"], device="cuda")))
+    ntot = sum(p["nx"] * p["ny"] for p in w["problems"])
+    t0 = time.perf_counter()
+    B = G.airg_setup_batch(csrs, G.airg_options_default(**w["opts"]))
+    setup_s = time.perf_counter() - t0
+    xs = [torch.zeros_like(b) for b in bs]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        for x in xs:
+            x.zero_()
+        G.airg_solve_batch(B, bs, xs, rtol=w["rtol"])
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = Clocks(local_rank)
+    torch.cuda.synchronize()
+    clk.start()
+    total_ms, its = 0.0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        for x in xs:
+            x.zero_()
+        ev0.record(stream)
+        _, infos = G.airg_solve_batch(B, bs, xs, rtol=w["rtol"])
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        its.append(max(i.iterations for i in infos))
+        assert all(i.converged for i in infos)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    t_max = max_over_ranks(total_ms, world, dev)
+    value = world * ntot * args.steps / (t_max / 1e3)
+    bh = [b.cpu().pin_memory() for b in bs]
+    xh = [torch.zeros_like(b) for b in bh]
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        for x in xh:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G.airg_solve_batch(B, bh, xh, rtol=w["rtol"])
+        e2e_s += time.perf_counter() - t0
+    e2e_max = max_over_ranks(e2e_s, world, dev)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["desc"], "n": ntot, "problems": len(bs), "rtol": w["rtol"],
+                       "iterations_per_solve": statistics.median(its), "setup_s": setup_s,
+                       "l2": "flushed (256 MiB write) between timed steps"},
+            "e2e": {"value": world * ntot * args.steps / e2e_max, "unit": "DOF/s",
+                    "h2d_bytes_per_step": 16 * ntot, "d2h_bytes_per_step": 8 * ntot},
+            "roofline": None, "cpu_baseline": None, "clocks": clocks}))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def run_gpu(args):
     import torch
     rank, world, local_rank = dist_env()
@@ -191,6 +274,7 @@ def run_gpu(args):
     from synthetic import workload
     G.lib()
     w = workload(args.workload)
+    k = w["n_rhs"]
     n = w["nx"] * w["ny"]
     prob, b = problem_and_rhs(w, G, torch)
     opts = G.airg_options_default(**w["opts"])
@@ -232,10 +316,10 @@ def run_gpu(args):
     wall_s = time.perf_counter() - t_wall0
     clocks = clk.stop()
     t_max = max_over_ranks(total_ms, world, dev)
-    value = world * n * args.steps / (t_max / 1e3)
+    value = world * n * k * args.steps / (t_max / 1e3)
     # ---- end-to-end through the C ABI with host buffers (copies in the call)
     bh = b.cpu().pin_memory()
-    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
     barrier()
     e2e_s = 0.0
     for _ in range(args.steps):
@@ -246,8 +330,8 @@ def run_gpu(args):
         G.airg_solve(h, bh, xh, rtol=w["rtol"])
         e2e_s += time.perf_counter() - t0
     e2e_max = max_over_ranks(e2e_s, world, dev)
-    e2e = {"value": world * n * args.steps / e2e_max, "unit": "DOF/s",
-           "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 8 * n}
+    e2e = {"value": world * n * k * args.steps / e2e_max, "unit": "DOF/s",
+           "h2d_bytes_per_step": 2 * 8 * n * k, "d2h_bytes_per_step": 8 * n * k}
     # ---- per-kernel event timing over a second pass of the same steps
     G.airg_profile(h, True)
     for _ in range(args.steps):
@@ -268,7 +352,7 @@ def run_gpu(args):
                 "kernel_share": {k: v[0] / sum(q[0] for q in kinds.values()) for k, v in kinds.items()}}
     vc_bytes = sinfo["bytes_per_vcycle"]
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("c1", "c2"):
         cv, ts = cpu_oracle_solve(w, 1, 0)
         cpu = {"value": cv, "unit": "DOF/s", "cores": 1, "kind": "oracle",
                "sample": "1 full oracle solve of the same workload (setup untimed), %.1f s" % ts[0]}
@@ -279,7 +363,7 @@ def run_gpu(args):
             "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if w["opts"].get("precision") == 1 else "f64",
             "data": "synthetic",
-            "config": {"workload": w["desc"], "n": n, "nrhs": 1, "rtol": w["rtol"],
+            "config": {"workload": w["desc"], "n": n, "nrhs": k, "rtol": w["rtol"],
                        "parallelism": "replicas" if world > 1 else "single",
                        "levels": sinfo["levels"], "iterations_per_solve": statistics.median(its),
                        "setup_ms": sinfo["setup_ms"], "cycle_complexity": sinfo["cycle_complexity"],
@@ -300,6 +384,8 @@ def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c4b":
+        run_gpu_multi(args)
     else:
         run_gpu(args)
 

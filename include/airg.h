@@ -85,6 +85,7 @@ typedef struct {
 } airg_options;
 
 typedef struct airg_handle_s airg_handle;
+typedef struct airg_batch_s airg_batch;
 
 typedef struct {
     int iterations;            /* outer FGMRES iterations (= V-cycles)        */
@@ -189,6 +190,26 @@ airg_status airg_solve(airg_handle* h, int nrhs, const double* b, double* x, int
 airg_status airg_solve_adjoint(airg_handle* h, int nrhs, const double* rhs, double* lambda,
                                int on_device, double rtol, double atol, int maxit,
                                airg_solve_info* info, void* stream);
+
+/*
+ * Many separate problems (different operators, e.g. grids of uneven size),
+ * one AIRG hierarchy each, solved together.  airg_setup_batch builds the
+ * nprob hierarchies (As: HOST array of nprob CSR descriptors, same options
+ * for all).  airg_solve_batch runs FGMRES in lockstep across the problems:
+ * each iteration is one CUDA graph launch in which every problem's V-cycle,
+ * SpMV and Gram-Schmidt pass form an independent branch (captured once per
+ * iteration index and replayed).  bvec, xvec: HOST arrays of nprob pointers
+ * to vectors of each problem's length (DEVICE pointers if on_device, else
+ * HOST); x is the initial guess on entry.  infos: HOST array of nprob
+ * entries (may be NULL).  AIRG_ERR_NOT_CONVERGED if any problem misses the
+ * tolerance; every x and info is still written.
+ */
+airg_status airg_setup_batch(int nprob, const airg_csr* As, const airg_options* opt, void* stream,
+                             airg_batch** out);
+airg_status airg_solve_batch(airg_batch* b, const double* const* bvec, double* const* xvec,
+                             int on_device, double rtol, double atol, int maxit,
+                             airg_solve_info* infos, void* stream);
+void airg_batch_free(airg_batch* b);
 
 /* Levels, sizes and the complexities of Sec. 3.  info is a HOST pointer. */
 airg_status airg_setup_info(const airg_handle* h, airg_hierarchy_info* info);

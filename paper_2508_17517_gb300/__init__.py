@@ -27,7 +27,8 @@ EXPORTS = ["airg_options_default", "airg_problem_advection2d", "airg_assemble_rh
            "airg_export_matrix", "airg_export_vector", "airg_free", "airg_last_error",
            "airg_dot_exact", "airg_rng_uniform", "airg_host_gmres_coeffs", "airg_host_eigvals",
            "airg_profile", "airg_profile_read", "airg_dot_exact_noalloc",
-           "airg_rhs_adjoint_advection2d"]
+           "airg_rhs_adjoint_advection2d", "airg_setup_batch", "airg_solve_batch",
+           "airg_batch_free"]
 PROFILE_KINDS = ["restrict", "f_residual", "f_smoother", "coarse_newton", "top_spmv",
                  "krylov_vectors", "layout"]
 
@@ -105,6 +106,10 @@ def lib():
             "airg_profile": [vp, ci],
             "airg_dot_exact_noalloc": [i64, vp, vp, vp, vp],
             "airg_rhs_adjoint_advection2d": [i64, i64, f64, f64, f64, ci, vp, i64, vp, vp, vp, vp],
+            "airg_setup_batch": [ci, ctypes.POINTER(airg_csr), ctypes.POINTER(airg_options), vp,
+                                 ctypes.POINTER(vp)],
+            "airg_solve_batch": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ci, f64, f64, ci,
+                                 ctypes.POINTER(airg_solve_info), vp],
             "airg_profile_read": [vp, ci, ctypes.POINTER(f64), ctypes.POINTER(i64),
                                   ctypes.POINTER(i64)],
         }
@@ -114,6 +119,8 @@ def lib():
             fn.restype = ctypes.c_int
         L.airg_free.argtypes = [vp]
         L.airg_free.restype = None
+        L.airg_batch_free.argtypes = [vp]
+        L.airg_batch_free.restype = None
         L.airg_last_error.argtypes = []
         L.airg_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -230,6 +237,51 @@ def _solve(fn, handle, b, x, rtol, atol, maxit, stream, allow_nc):
             ctypes.byref(info), _stream(stream))
     _check(st, allow=(AIRG_ERR_NOT_CONVERGED,) if allow_nc else ())
     return x, info
+
+
+class BatchHandle:
+    def __init__(self, ptr, sizes):
+        self.ptr = ptr
+        self.sizes = sizes
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            airg_batch_free(self)
+
+
+def airg_setup_batch(csrs, opts=None, stream=None):
+    """csrs: list of (rowptr, col, val) tensors, one square matrix per problem."""
+    n = len(csrs)
+    arr = (airg_csr * n)()
+    for i, (rp, ci_, v) in enumerate(csrs):
+        arr[i] = airg_csr(rp.numel() - 1, rp.numel() - 1, ci_.numel(), rp.data_ptr(), ci_.data_ptr(),
+                          v.data_ptr(), int(rp.is_cuda))
+    out = ctypes.c_void_p()
+    o = opts if opts is not None else airg_options_default()
+    _check(lib().airg_setup_batch(n, arr, ctypes.byref(o), _stream(stream), ctypes.byref(out)))
+    return BatchHandle(out, [rp.numel() - 1 for rp, _, _ in csrs])
+
+
+def airg_solve_batch(batch, bs, xs=None, rtol=1e-10, atol=1e-50, maxit=200, stream=None,
+                     allow_nc=False):
+    """Solves every problem of the batch; bs, xs: lists of tensors (same device)."""
+    import torch
+    n = len(bs)
+    if xs is None:
+        xs = [torch.zeros_like(b) for b in bs]
+    pb = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+    px = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    infos = (airg_solve_info * n)()
+    st = lib().airg_solve_batch(batch.ptr, pb, px, int(bs[0].is_cuda), float(rtol), float(atol),
+                                int(maxit), infos, _stream(stream))
+    _check(st, allow=(AIRG_ERR_NOT_CONVERGED,) if allow_nc else ())
+    return xs, list(infos)
+
+
+def airg_batch_free(batch):
+    if batch.ptr:
+        lib().airg_batch_free(batch.ptr)
+        batch.ptr = None
 
 
 def airg_solve(handle, b, x=None, rtol=1e-10, atol=1e-50, maxit=200, stream=None, allow_nc=False):

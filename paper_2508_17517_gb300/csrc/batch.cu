@@ -1,0 +1,746 @@
+// Many right-hand sides on one hierarchy: the V-cycle of Eq. 6 applied to k
+// vectors at once (an SpMM-style V-cycle) inside k independent FGMRES
+// iterations advanced in lockstep.
+//
+// Layout: a batch of k vectors of length n is stored row-major, [row][rhs],
+// in the nested F/C order of the single solve.  Every operator kernel runs
+// one warp per row with the lanes over right-hand sides (q = lane + 32 j,
+// j < KW): each stored entry of the row is read once per warp (broadcast)
+// and reused for all k right-hand sides, and the gathers of x read k
+// consecutive values of one row -- contiguous, coalesced.  The operator
+// bytes of a V-cycle are thus paid once per k right-hand sides.
+//
+// A right-hand side whose FGMRES residual reaches its tolerance is frozen:
+// its next basis vector is zero and its least-squares solution uses only
+// the columns built while it was active.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "dev_util.cuh"
+#include "handle.h"
+#include "solve_internal.cuh"
+
+namespace airg {
+
+namespace {
+
+constexpr int BT = 256;          // threads per block (8 rows of the batch)
+constexpr int MAXB = 16;         // restart length of the batched FGMRES
+constexpr int MAXK = 128;        // right-hand sides per batch (KW <= 4)
+
+inline int grid_rows(long long n) { return grid_for(n * 32, BT); }
+
+// acc[j] = (row r of S) x[:, q], q = lane + 32 j
+template <class T, int KW>
+__device__ __forceinline__ void brow(const SellView<T>& S, int r, const T* __restrict__ x, int k,
+                                     int lane, T (&acc)[KW])
+{
+#pragma unroll
+    for (int j = 0; j < KW; ++j) acc[j] = T(0);
+    const int s = r >> 5;
+    const int b = S.sptr[s] + (r & 31), w = (S.sptr[s + 1] - S.sptr[s]) >> 5;
+    for (int e = 0; e < w; ++e) {
+        const int idx = b + 32 * e;
+        const T v = __ldg(S.val + idx);
+        const T* xr = x + size_t(__ldg(S.col + idx)) * k;
+#pragma unroll
+        for (int j = 0; j < KW; ++j) {
+            int q = lane + 32 * j;
+            if (q < k) acc[j] = fma(v, xr[q], acc[j]);
+        }
+    }
+}
+
+#define BROW_IDS(NROWS)                                                       \
+    const long long tid_ = (long long)blockIdx.x * blockDim.x + threadIdx.x; \
+    const int r = int(tid_ >> 5);                                            \
+    const int lane = threadIdx.x & 31;                                       \
+    if (r >= (NROWS)) return
+
+template <class T, int KW>
+__global__ void kb_spmv(SellView<T> S, const T* __restrict__ x, T* __restrict__ y, int k)
+{
+    BROW_IDS(S.n_rows);
+    T a[KW];
+    brow<T, KW>(S, r, x, k, lane, a);
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+        int q = lane + 32 * j;
+        if (q < k) y[size_t(r) * k + q] = a[j];
+    }
+}
+
+template <class T, int KW>
+__global__ void kb_restrict(SellView<T> Z, const T* __restrict__ sf, const T* __restrict__ sc,
+                            T* __restrict__ dc, int k)
+{
+    BROW_IDS(Z.n_rows);
+    T a[KW];
+    brow<T, KW>(Z, r, sf, k, lane, a);
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+        int q = lane + 32 * j;
+        if (q < k) dc[size_t(r) * k + q] = sc[size_t(r) * k + q] + a[j];
+    }
+}
+
+template <class T, int KW>
+__global__ void kb_fresid(SellView<T> M, const T* __restrict__ rf, const T* __restrict__ ec,
+                          T* __restrict__ t, T* __restrict__ w, T ap, int k)
+{
+    BROW_IDS(M.n_rows);
+    T a[KW];
+    brow<T, KW>(M, r, ec, k, lane, a);
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+        int q = lane + 32 * j;
+        if (q < k) {
+            size_t o = size_t(r) * k + q;
+            T tt = rf[o] - a[j];
+            t[o] = tt;
+            w[o] = ap * tt;
+        }
+    }
+}
+
+template <class T, int KW>
+__global__ void kb_horner(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
+                          T* __restrict__ wout, T ak, int k)
+{
+    BROW_IDS(A.n_rows);
+    T a[KW];
+    brow<T, KW>(A, r, win, k, lane, a);
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+        int q = lane + 32 * j;
+        if (q < k) {
+            size_t o = size_t(r) * k + q;
+            wout[o] = fma(ak, t[o], a[j]);
+        }
+    }
+}
+
+template <class T, int KW>
+__global__ void kb_horner_last(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
+                               const T* __restrict__ ec, const int* __restrict__ W,
+                               T* __restrict__ ef, T a0, int k)
+{
+    BROW_IDS(A.n_rows);
+    T a[KW];
+    brow<T, KW>(A, r, win, k, lane, a);
+    const int wc = W[r];
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+        int q = lane + 32 * j;
+        if (q < k) {
+            size_t o = size_t(r) * k + q;
+            T p = wc >= 0 ? ec[size_t(wc) * k + q] : T(0);
+            ef[o] = p + fma(a0, t[o], a[j]);
+        }
+    }
+}
+
+template <class T>
+__global__ void kb_smooth0(long long n, const T* __restrict__ t, const T* __restrict__ ec,
+                           const int* __restrict__ W, T* __restrict__ ef, T a0, int k)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * k) return;
+    long long r = i / k;
+    int q = int(i % k);
+    int wc = W[r];
+    ef[i] = (wc >= 0 ? ec[size_t(wc) * k + q] : T(0)) + a0 * t[i];
+}
+
+template <class T, int KW>
+__global__ void kb_newton_real(SellView<T> A, const T* __restrict__ rin, T* __restrict__ rout,
+                               T* __restrict__ x, T inv, int first, int last, int k)
+{
+    BROW_IDS(A.n_rows);
+    T a[KW];
+    if (!last) brow<T, KW>(A, r, rin, k, lane, a);
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+        int q = lane + 32 * j;
+        if (q < k) {
+            size_t o = size_t(r) * k + q;
+            T ri = rin[o];
+            x[o] = fma(ri, inv, first ? T(0) : x[o]);
+            if (!last) rout[o] = ri - a[j] * inv;
+        }
+    }
+}
+
+template <class T, int KW>
+__global__ void kb_newton_pair1(SellView<T> A, const T* __restrict__ rin, T* __restrict__ t,
+                                T* __restrict__ x, T two_a, T inv2, int first, int k)
+{
+    BROW_IDS(A.n_rows);
+    T a[KW];
+    brow<T, KW>(A, r, rin, k, lane, a);
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+        int q = lane + 32 * j;
+        if (q < k) {
+            size_t o = size_t(r) * k + q;
+            T tt = two_a * rin[o] - a[j];
+            t[o] = tt;
+            x[o] = fma(tt, inv2, first ? T(0) : x[o]);
+        }
+    }
+}
+
+template <class T, int KW>
+__global__ void kb_newton_pair2(SellView<T> A, const T* __restrict__ rin, const T* __restrict__ t,
+                                T* __restrict__ rout, T inv2, int k)
+{
+    BROW_IDS(A.n_rows);
+    T a[KW];
+    brow<T, KW>(A, r, t, k, lane, a);
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+        int q = lane + 32 * j;
+        if (q < k) {
+            size_t o = size_t(r) * k + q;
+            rout[o] = rin[o] - a[j] * inv2;
+        }
+    }
+}
+
+__global__ void kb_d2f(long long m, const double* a, float* b)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) b[i] = (float)a[i];
+}
+__global__ void kb_f2d(long long m, const float* a, double* b)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) b[i] = (double)a[i];
+}
+
+// [q][i] (caller, natural order) <-> [pos(i)][q] (batch, nested order)
+__global__ void kb_to_nested(long long n, int k, const int* pos, const double* a, double* b)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * k) return;
+    int q = int(t / n);
+    long long i = t % n;
+    b[size_t(pos[i]) * k + q] = a[t];
+}
+__global__ void kb_from_nested(long long n, int k, const int* pos, const double* a, double* b)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * k) return;
+    int q = int(t / n);
+    long long i = t % n;
+    b[t] = a[size_t(pos[i]) * k + q];
+}
+
+// ----------------------------------------------------- batched Krylov work --
+constexpr int RG = 608;   // reduction blocks
+
+// out[i*k + q] = sum_r V_i[r][q] * w[r][q] for i < m (m <= MAXB + 1); blocks
+// write partial sums, the last block adds them in a fixed order.
+__global__ void __launch_bounds__(BT)
+kb_multidot(long long n, int k, int m, const double* __restrict__ V, long long ldv,
+            const double* __restrict__ w, double* __restrict__ part, double* __restrict__ out,
+            unsigned* ticket, int selfdot = 0)
+{
+    // with selfdot the last output row is <w_q, w_q>
+    const int mm = m;
+    m += selfdot ? 1 : 0;
+    __shared__ double red[BT];
+    __shared__ bool last_block;
+    const int ng = BT / k;                 // row groups per block
+    const int q = threadIdx.x % k, grp = threadIdx.x / k;
+    double acc[MAXB + 1];
+#pragma unroll
+    for (int i = 0; i < MAXB + 1; ++i) acc[i] = 0.0;
+    if (grp < ng) {
+        for (long long r = (long long)blockIdx.x * ng + grp; r < n; r += (long long)gridDim.x * ng) {
+            double wv = w[r * k + q];
+#pragma unroll
+            for (int i = 0; i < MAXB + 1; ++i)
+                if (i < m) acc[i] = fma(i < mm ? V[i * ldv + r * k + q] : wv, wv, acc[i]);
+        }
+    }
+    for (int i = 0; i < m; ++i) {
+        red[threadIdx.x] = grp < ng ? acc[i] : 0.0;
+        __syncthreads();
+        if (threadIdx.x < k) {
+            double s = 0.0;
+            for (int g = 0; g < ng; ++g) s += red[g * k + threadIdx.x];
+            part[((long long)blockIdx.x * m + i) * k + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+    __threadfence();
+    if (threadIdx.x == 0) last_block = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last_block) return;
+    __threadfence();
+    for (int o = threadIdx.x; o < m * k; o += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) s += part[(long long)b * m * k + o];
+        out[o] = s;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// w[r][q] -= sum_i h[i*k+q] V_i[r][q]
+__global__ void kb_multiaxpy(long long n, int k, int m, const double* __restrict__ V, long long ldv,
+                             const double* __restrict__ h, double* __restrict__ w)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * k) return;
+    int q = int(t % k);
+    double s = w[t];
+    for (int i = 0; i < m; ++i) s = fma(-h[i * k + q], V[i * ldv + t], s);
+    w[t] = s;
+}
+
+// w[r][q] -= sum_i h[i*k+q] V_i[r][q], and out[q] = ||w_q||^2 of the result
+__global__ void __launch_bounds__(BT)
+kb_multiaxpy_norm(long long n, int k, int m, const double* __restrict__ V, long long ldv,
+                  const double* __restrict__ h, double* __restrict__ w, double* __restrict__ part,
+                  double* __restrict__ out, unsigned* ticket)
+{
+    __shared__ double red[BT];
+    __shared__ bool last_block;
+    const int ng = BT / k;
+    const int q = threadIdx.x % k, grp = threadIdx.x / k;
+    double ss = 0.0;
+    if (grp < ng) {
+        for (long long r = (long long)blockIdx.x * ng + grp; r < n; r += (long long)gridDim.x * ng) {
+            long long t = r * k + q;
+            double s = w[t];
+            for (int i = 0; i < m; ++i) s = fma(-h[i * k + q], V[i * ldv + t], s);
+            w[t] = s;
+            ss = fma(s, s, ss);
+        }
+    }
+    red[threadIdx.x] = grp < ng ? ss : 0.0;
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double s = 0.0;
+        for (int g = 0; g < ng; ++g) s += red[g * k + threadIdx.x];
+        part[(long long)blockIdx.x * k + threadIdx.x] = s;
+    }
+    __threadfence();
+    if (threadIdx.x == 0) last_block = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last_block) return;
+    __threadfence();
+    for (int o = threadIdx.x; o < k; o += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) s += part[(long long)b * k + o];
+        out[o] = s;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// x[r][q] += sum_i y[i*k+q] Z_i[r][q]
+__global__ void kb_update(long long n, int k, int m, const double* __restrict__ Zs, long long ldz,
+                          const double* __restrict__ y, double* __restrict__ x)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * k) return;
+    int q = int(t % k);
+    double s = x[t];
+    for (int i = 0; i < m; ++i) s = fma(y[i * k + q], Zs[i * ldz + t], s);
+    x[t] = s;
+}
+
+__global__ void kb_scale(long long n, int k, const double* __restrict__ w, const double* __restrict__ inv,
+                         double* __restrict__ v)
+{
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n * k) v[t] = w[t] * inv[t % k];
+}
+
+__global__ void kb_sub(long long m, const double* b, const double* y, double* r)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) r[i] = b[i] - y[i];
+}
+
+#define WITH_KW(k, ...)                                                   \
+    do {                                                                  \
+        if ((k) <= 32) { constexpr int KW = 1; __VA_ARGS__; }             \
+        else if ((k) <= 64) { constexpr int KW = 2; __VA_ARGS__; }        \
+        else { constexpr int KW = 4; __VA_ARGS__; }                       \
+    } while (0)
+
+}  // namespace
+
+// Work space of one batch width k.
+struct BatchData {
+    int k = 0, m = 0;
+    long long nk = 0;
+    DBuf<double> V, Zs, w, bp, xp, r, part, hdev, inv;
+    DBuf<double> rwork, t, wa, wb, cr0, cr1, ct;               // FP64 V-cycle
+    DBuf<float> rwork32, e32, vin32, t32, wa32, wb32, cr032, cr132, ct32;  // FP32 V-cycle
+    DBuf<unsigned> ticket;
+    HBuf<double> hh;
+    struct GEntry { const void* v; void* z; cudaGraphExec_t exec; long long kernels; };
+    std::vector<GEntry> graphs;
+    ~BatchData()
+    {
+        for (GEntry& g : graphs) cudaGraphExecDestroy(g.exec);
+    }
+};
+
+namespace {
+
+template <class T>
+struct BWork {
+    T* rwork; T* t; T* wa; T* wb; T* cr0; T* cr1; T* ct;
+};
+
+template <class T>
+const SolveLevelT<T>& bops(const SolveLevel& L);
+template <>
+const SolveLevelT<double>& bops<double>(const SolveLevel& L) { return L.d; }
+template <>
+const SolveLevelT<float>& bops<float>(const SolveLevel& L) { return L.f; }
+
+template <class T>
+const Sell<T>& bcoarse(const SolveData& S);
+template <>
+const Sell<double>& bcoarse<double>(const SolveData& S) { return S.Ac; }
+template <>
+const Sell<float>& bcoarse<float>(const SolveData& S) { return S.Ac32; }
+
+// e = M^-1 v for k right-hand sides (nested order, [row][rhs])
+template <class T>
+void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStream_t st)
+{
+    const int L = S.nlev;
+    constexpr long long VB = sizeof(T);
+    const long long kk = k;
+    for (int l = 0; l < L; ++l) {
+        const SolveLevel& lv = *S.lv[l];
+        const T* src = l == 0 ? v : wk.rwork;
+        const Sell<T>& Z = bops<T>(lv).Z;
+        if (lv.n_c)
+            LAUNCH(S, PK_RESTRICT, Z.nnz * (VB + 4) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
+                   WITH_KW(k, kb_restrict<T, KW><<<grid_rows(lv.n_c), BT, 0, st>>>(
+                                  view(Z), src + size_t(lv.off) * k, src + size_t(lv.off + lv.n_f) * k,
+                                  wk.rwork + size_t(lv.off + lv.n_f) * k, k)));
+    }
+    {
+        const T* rc = (L == 0 ? v : wk.rwork) + size_t(S.off_c) * k;
+        T* x = e + size_t(S.off_c) * k;
+        const Sell<T>& A = bcoarse<T>(S);
+        SellView<T> Av = view(A);
+        const int nco = S.n_coarse;
+        const long long nB = (long long)nco * VB * kk, mB = A.nnz * (VB + 4);
+        const T* rin = rc;
+        T* bufs[2] = {wk.cr0, wk.cr1};
+        int nb = 0;
+        size_t nr = S.roots.size();
+        for (size_t i = 0; i < nr; ++i) {
+            bool last = i + 1 == nr;
+            const Root& q = S.roots[i];
+            T* rout = bufs[nb];
+            if (q.im == 0.0) {
+                LAUNCH(S, PK_NEWTON, (last ? 0 : mB + 2 * nB) + (i == 0 ? 2 : 3) * nB,
+                       WITH_KW(k, kb_newton_real<T, KW><<<grid_rows(nco), BT, 0, st>>>(
+                                      Av, rin, rout, x, T(1.0 / q.re), i == 0, last, k)));
+            } else {
+                double mod2 = q.re * q.re + q.im * q.im;
+                LAUNCH(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB,
+                       WITH_KW(k, kb_newton_pair1<T, KW><<<grid_rows(nco), BT, 0, st>>>(
+                                      Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0, k)));
+                if (!last)
+                    LAUNCH(S, PK_NEWTON, mB + 3 * nB,
+                           WITH_KW(k, kb_newton_pair2<T, KW><<<grid_rows(nco), BT, 0, st>>>(
+                                          Av, rin, wk.ct, rout, T(1.0 / mod2), k)));
+            }
+            if (!last) { rin = rout; nb ^= 1; }
+        }
+        if (nr == 0) CK(cudaMemsetAsync(x, 0, sizeof(T) * size_t(nco) * k, st));
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        const SolveLevel& lv = *S.lv[l];
+        const T* src = l == 0 ? v : wk.rwork;
+        const SolveLevelT<T>& o = bops<T>(lv);
+        const T* rf = src + size_t(lv.off) * k;
+        const T* ec = e + size_t(lv.off + lv.n_f) * k;
+        T* ef = e + size_t(lv.off) * k;
+        const int nf = lv.n_f;
+        const int p = int(lv.alpha.size()) - 1;
+        const long long fB = (long long)nf * VB * kk;
+        LAUNCH(S, PK_FRESID, o.M.nnz * (VB + 4) + (long long)lv.n_c * VB * kk + 3 * fB,
+               WITH_KW(k, kb_fresid<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
+                                                                        T(lv.alpha[p]), k)));
+        if (p == 0) {
+            LAUNCH(S, PK_HORNER, 3 * fB + 4LL * nf,
+                   kb_smooth0<T><<<grid_for((long long)nf * k, BT), BT, 0, st>>>(nf, wk.t, ec, lv.W.p, ef,
+                                                                                T(lv.alpha[0]), k));
+            continue;
+        }
+        const long long hB = o.Aff.nnz * (VB + 4) + 3 * fB;
+        T* win = wk.wa;
+        T* wout = wk.wb;
+        for (int kq = p - 1; kq >= 1; --kq) {
+            LAUNCH(S, PK_HORNER, hB,
+                   WITH_KW(k, kb_horner<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.Aff), wk.t, win, wout,
+                                                                            T(lv.alpha[kq]), k)));
+            std::swap(win, wout);
+        }
+        LAUNCH(S, PK_HORNER, hB + fB + 4LL * nf,
+               WITH_KW(k, kb_horner_last<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.Aff), wk.t, win, ec,
+                                                                             lv.W.p, ef, T(lv.alpha[0]), k)));
+    }
+    CK_LAUNCH();
+}
+
+void bprecond_launch(Hierarchy& H, BatchData& B, const double* v, double* z, cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    long long nk = B.nk;
+    if (H.opt.precision == AIRG_MIXED_FP32) {
+        LAUNCH(S, PK_LAYOUT, 12 * nk, kb_d2f<<<grid_for(nk, BT), BT, 0, st>>>(nk, v, B.vin32.p));
+        BWork<float> wk{B.rwork32.p, B.t32.p, B.wa32.p, B.wb32.p, B.cr032.p, B.cr132.p, B.ct32.p};
+        bvcycle<float>(S, B.k, B.vin32.p, B.e32.p, wk, st);
+        LAUNCH(S, PK_LAYOUT, 12 * nk, kb_f2d<<<grid_for(nk, BT), BT, 0, st>>>(nk, B.e32.p, z));
+    } else {
+        BWork<double> wk{B.rwork.p, B.t.p, B.wa.p, B.wb.p, B.cr0.p, B.cr1.p, B.ct.p};
+        bvcycle<double>(S, B.k, v, z, wk, st);
+    }
+}
+
+void bprecond(Hierarchy& H, BatchData& B, const double* v, double* z, cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    if (S.prof || !S.use_graphs) {
+        bprecond_launch(H, B, v, z, st);
+        return;
+    }
+    BatchData::GEntry* ge = nullptr;
+    for (auto& g : B.graphs)
+        if (g.v == v && g.z == z) { ge = &g; break; }
+    if (!ge) {
+        long long before = S.launches;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        try {
+            bprecond_launch(H, B, v, z, st);
+        } catch (...) {
+            cudaGraph_t g0;
+            cudaStreamEndCapture(st, &g0);
+            if (g0) cudaGraphDestroy(g0);
+            throw;
+        }
+        cudaGraph_t graph;
+        CK(cudaStreamEndCapture(st, &graph));
+        cudaGraphExec_t exec;
+        cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+        long long nkern = S.launches - before;
+        S.launches = before;
+        B.graphs.push_back(BatchData::GEntry{v, z, exec, nkern});
+        ge = &B.graphs.back();
+    }
+    CK(cudaGraphLaunch(ge->exec, st));
+    S.launches += ge->kernels;
+}
+
+void ensure_batch(Hierarchy& H, int k)
+{
+    SolveData& S = *H.solve;
+    if (S.batch && S.batch->k == k) return;
+    S.batch.reset();
+    auto B = std::make_shared<BatchData>();
+    B->k = k;
+    B->m = std::min(std::max(1, H.opt.gmres_restart), MAXB);
+    long long n = S.n0;
+    B->nk = n * k;
+    size_t nk = size_t(B->nk);
+    int m = B->m;
+    B->V.alloc(size_t(m + 1) * nk);
+    B->Zs.alloc(size_t(m) * nk);
+    B->w.alloc(nk); B->bp.alloc(nk); B->xp.alloc(nk); B->r.alloc(nk);
+    B->part.alloc(size_t(RG) * (MAXB + 1) * k);
+    B->hdev.alloc(size_t(3 * (MAXB + 2)) * k);
+    B->inv.alloc(size_t(k));
+    B->hh.alloc(size_t(3 * (MAXB + 2)) * k);
+    B->ticket.alloc(1);
+    CK(cudaMemset(B->ticket.p, 0, sizeof(unsigned)));
+    size_t nf = size_t(std::max(S.max_nf, 1)) * k, nc = size_t(std::max(S.n_coarse, 1)) * k;
+    if (H.opt.precision == AIRG_MIXED_FP32) {
+        B->rwork32.alloc(nk); B->e32.alloc(nk); B->vin32.alloc(nk);
+        B->t32.alloc(nf); B->wa32.alloc(nf); B->wb32.alloc(nf);
+        B->cr032.alloc(nc); B->cr132.alloc(nc); B->ct32.alloc(nc);
+    } else {
+        B->rwork.alloc(nk);
+        B->t.alloc(nf); B->wa.alloc(nf); B->wb.alloc(nf);
+        B->cr0.alloc(nc); B->cr1.alloc(nc); B->ct.alloc(nc);
+    }
+    S.batch = B;
+}
+
+// per-RHS 2-norms of a batch
+void bnorms(SolveData& S, BatchData& B, const double* x, std::vector<double>& out, cudaStream_t st)
+{
+    long long n = S.n0;
+    int k = B.k;
+    LAUNCH(S, PK_KRYLOV, 8 * B.nk,
+           kb_multidot<<<RG, BT, 0, st>>>(n, k, 1, x, B.nk, x, B.part.p, B.hdev.p, B.ticket.p));
+    out.resize(k);
+    d2h(out.data(), B.hdev.p, size_t(k), st);
+    for (double& v : out) v = std::sqrt(std::max(v, 0.0));
+}
+
+}  // namespace
+
+// Lockstep FGMRES(m) for k right-hand sides (device b, x in the caller's
+// layout: k vectors of length n one after the other).
+void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol, double atol,
+                   int maxit, airg_solve_info& info, cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    ensure_batch(H, k);
+    BatchData& B = *S.batch;
+    const long long n = S.n0, nk = B.nk;
+    const int m = B.m;
+    const int g = grid_for(nk, BT);
+    SellView<double> A = view(S.Atop);
+    const long long topB = S.Atop.nnz * 12 + 16 * nk;
+    LAUNCH(S, PK_LAYOUT, 20 * nk, kb_to_nested<<<g, BT, 0, st>>>(n, k, S.pos0.p, b, B.bp.p));
+    LAUNCH(S, PK_LAYOUT, 20 * nk, kb_to_nested<<<g, BT, 0, st>>>(n, k, S.pos0.p, x, B.xp.p));
+    std::vector<double> bn, rn, tol(k);
+    bnorms(S, B, B.bp.p, bn, st);
+    for (int q = 0; q < k; ++q) tol[q] = std::max(rtol * bn[q], atol);
+    auto residual = [&]() {
+        LAUNCH(S, PK_TOPSPMV, topB,
+               WITH_KW(k, kb_spmv<double, KW><<<grid_rows(n), BT, 0, st>>>(A, B.xp.p, B.w.p, k)));
+        LAUNCH(S, PK_KRYLOV, 24 * nk, kb_sub<<<g, BT, 0, st>>>(nk, B.bp.p, B.w.p, B.r.p));
+        bnorms(S, B, B.r.p, rn, st);
+    };
+    residual();
+    int its = 0;
+    std::vector<double> Hm(size_t(m + 1) * m * k), cs(size_t(m) * k), sn(size_t(m) * k),
+        gv(size_t(m + 1) * k), Y(size_t(m) * k), inv(k);
+    std::vector<int> active(k), jdone(k);
+    auto hq = [&](int i, int j, int q) -> double& { return Hm[(size_t(i) * m + j) * k + q]; };
+    double* hh = B.hh.p;
+    while (its < maxit) {
+        int nact = 0;
+        for (int q = 0; q < k; ++q) {
+            active[q] = rn[q] > tol[q];
+            nact += active[q];
+            jdone[q] = 0;
+            inv[q] = active[q] ? 1.0 / rn[q] : 0.0;
+        }
+        if (!nact) break;
+        std::fill(gv.begin(), gv.end(), 0.0);
+        for (int q = 0; q < k; ++q) gv[q] = rn[q];
+        h2d(B.inv.p, inv.data(), size_t(k), st);
+        LAUNCH(S, PK_KRYLOV, 16 * nk, kb_scale<<<g, BT, 0, st>>>(n, k, B.r.p, B.inv.p, B.V.p));
+        for (int j = 0; j < m; ++j) {
+            double* vj = B.V.p + size_t(j) * nk;
+            double* zj = B.Zs.p + size_t(j) * nk;
+            bprecond(H, B, vj, zj, st);
+            LAUNCH(S, PK_TOPSPMV, topB,
+                   WITH_KW(k, kb_spmv<double, KW><<<grid_rows(n), BT, 0, st>>>(A, zj, B.w.p, k)));
+            // CGS with a second pass only if some active right-hand side lost
+            // more than half of ||w||^2 in the first ("twice is enough")
+            double* h1 = B.hdev.p;
+            double* h2 = B.hdev.p + size_t(MAXB + 2) * k;
+            double* hnp = B.hdev.p + size_t(2) * (MAXB + 2) * k;
+            LAUNCH(S, PK_KRYLOV, 8LL * nk * (j + 2),
+                   kb_multidot<<<RG, BT, 0, st>>>(n, k, j + 1, B.V.p, nk, B.w.p, B.part.p, h1, B.ticket.p, 1));
+            LAUNCH(S, PK_KRYLOV, 8LL * nk * (j + 3),
+                   kb_multiaxpy_norm<<<RG, BT, 0, st>>>(n, k, j + 1, B.V.p, nk, h1, B.w.p, B.part.p, hnp,
+                                                        B.ticket.p));
+            CK(cudaMemcpyAsync(hh, B.hdev.p, sizeof(double) * 3 * (MAXB + 2) * k, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            bool again = false;
+            for (int q = 0; q < k; ++q)
+                if (active[q] && hh[size_t(2) * (MAXB + 2) * k + q] < 0.5 * hh[size_t(j + 1) * k + q]) again = true;
+            for (int q = 0; q < k; ++q)
+                for (int i = 0; i <= j; ++i) hq(i, j, q) = hh[size_t(i) * k + q];
+            if (again) {
+                LAUNCH(S, PK_KRYLOV, 8LL * nk * (j + 2),
+                       kb_multidot<<<RG, BT, 0, st>>>(n, k, j + 1, B.V.p, nk, B.w.p, B.part.p, h2, B.ticket.p));
+                LAUNCH(S, PK_KRYLOV, 8LL * nk * (j + 3),
+                       kb_multiaxpy_norm<<<RG, BT, 0, st>>>(n, k, j + 1, B.V.p, nk, h2, B.w.p, B.part.p, hnp,
+                                                            B.ticket.p));
+                CK(cudaMemcpyAsync(hh, B.hdev.p, sizeof(double) * 3 * (MAXB + 2) * k, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                for (int q = 0; q < k; ++q)
+                    for (int i = 0; i <= j; ++i) hq(i, j, q) += hh[(size_t(MAXB + 2) + i) * k + q];
+            }
+            ++its;
+            int still = 0;
+            for (int q = 0; q < k; ++q) {
+                inv[q] = 0.0;
+                if (!active[q]) continue;
+                double hn = std::sqrt(std::max(hh[size_t(2) * (MAXB + 2) * k + q], 0.0));
+                hq(j + 1, j, q) = hn;
+                for (int i = 0; i < j; ++i) {
+                    double a = hq(i, j, q), c = hq(i + 1, j, q);
+                    hq(i, j, q) = cs[size_t(i) * k + q] * a + sn[size_t(i) * k + q] * c;
+                    hq(i + 1, j, q) = -sn[size_t(i) * k + q] * a + cs[size_t(i) * k + q] * c;
+                }
+                double a = hq(j, j, q), c = hq(j + 1, j, q);
+                double den = std::hypot(a, c);
+                cs[size_t(j) * k + q] = den > 0 ? a / den : 1.0;
+                sn[size_t(j) * k + q] = den > 0 ? c / den : 0.0;
+                hq(j, j, q) = den;
+                hq(j + 1, j, q) = 0.0;
+                gv[size_t(j + 1) * k + q] = -sn[size_t(j) * k + q] * gv[size_t(j) * k + q];
+                gv[size_t(j) * k + q] = cs[size_t(j) * k + q] * gv[size_t(j) * k + q];
+                jdone[q] = j + 1;
+                if (std::fabs(gv[size_t(j + 1) * k + q]) <= tol[q] || den == 0.0 || hn == 0.0) {
+                    active[q] = 0;
+                } else {
+                    inv[q] = 1.0 / hn;
+                    ++still;
+                }
+            }
+            if (!still || its >= maxit || j + 1 == m) break;
+            h2d(B.inv.p, inv.data(), size_t(k), st);
+            LAUNCH(S, PK_KRYLOV, 16 * nk,
+                   kb_scale<<<g, BT, 0, st>>>(n, k, B.w.p, B.inv.p, B.V.p + size_t(j + 1) * nk));
+        }
+        // least squares per right-hand side, zero-padded to the common width
+        int jmax = 0;
+        std::fill(Y.begin(), Y.end(), 0.0);
+        for (int q = 0; q < k; ++q) {
+            int jd = jdone[q];
+            jmax = std::max(jmax, jd);
+            for (int j = jd - 1; j >= 0; --j) {
+                double s = gv[size_t(j) * k + q];
+                for (int i = j + 1; i < jd; ++i) s -= hq(j, i, q) * Y[size_t(i) * k + q];
+                Y[size_t(j) * k + q] = s / hq(j, j, q);
+            }
+        }
+        if (jmax) {
+            h2d(B.hdev.p, Y.data(), size_t(jmax) * k, st);
+            LAUNCH(S, PK_KRYLOV, 8LL * nk * (jmax + 2),
+                   kb_update<<<g, BT, 0, st>>>(n, k, jmax, B.Zs.p, nk, B.hdev.p, B.xp.p));
+        }
+        residual();
+    }
+    int conv = 1;
+    double worst = 0.0;
+    for (int q = 0; q < k; ++q) {
+        double rel = bn[q] > 0 ? rn[q] / bn[q] : 0.0;
+        worst = std::max(worst, rel);
+        if (rn[q] > tol[q]) conv = 0;
+    }
+    LAUNCH(S, PK_LAYOUT, 20 * nk, kb_from_nested<<<g, BT, 0, st>>>(n, k, S.pos0.p, B.xp.p, x));
+    CK_LAUNCH();
+    info.iterations = std::max(info.iterations, its);
+    info.rel_residual = std::max(info.rel_residual, worst);
+    info.converged = info.converged && conv;
+}
+
+int batch_max_width() { return MAXK; }
+
+}  // namespace airg

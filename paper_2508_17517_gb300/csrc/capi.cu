@@ -167,6 +167,8 @@ const airg::Hierarchy* level_owner(const airg_handle* h)
 namespace airg {
 // lets entry points outside this file report through airg_last_error()
 void set_last_error(const char* msg) { g_last_error = msg; }
+// validated device copy of a caller's CSR (multi.cu)
+DevCSR upload_csr_checked(const airg_csr* A, cudaStream_t st) { return upload_csr(A, st); }
 }  // namespace airg
 
 extern "C" {

@@ -25,184 +25,13 @@
 
 #include "dev_util.cuh"
 #include "handle.h"
+#include "solve_internal.cuh"
 
 namespace airg {
 
 namespace {
 constexpr int TB = 256;
 }
-enum { PK_RESTRICT = 0, PK_FRESID = 1, PK_HORNER = 2, PK_NEWTON = 3, PK_TOPSPMV = 4, PK_KRYLOV = 5,
-       PK_LAYOUT = 6, PROF_KINDS = 7 };
-
-// A solve-phase operator in SELL-32: slices of 32 consecutive rows, entries
-// column-major inside a slice (entry k of the slice's 32 rows are adjacent),
-// each slice padded to its longest row (padding: value 0, column repeated).
-// Lane l of a warp always owns row 32s+l, so at a given entry index the 32
-// lanes read adjacent values and columns, and -- rows of these operators
-// having similar stencils -- gather nearby entries of x.  k = number of
-// warps sharing a slice: for long rows the entries of a slice are split
-// among k warps of a block (entry indices interleaved) whose partial sums
-// meet in shared memory.
-template <class T>
-struct Sell {
-    int n_rows = 0, n_cols = 0, n_slices = 0, k = 1;
-    long long nnz = 0, padded = 0;
-    DBuf<int> sptr;
-    DBuf<int> col;
-    DBuf<T> val;
-};
-
-template <class T>
-struct SellView {
-    int n_rows, n_slices;
-    const int* __restrict__ sptr;
-    const int* __restrict__ col;
-    const T* __restrict__ val;
-};
-
-template <class T>
-SellView<T> view(const Sell<T>& s) { return SellView<T>{s.n_rows, s.n_slices, s.sptr.p, s.col.p, s.val.p}; }
-
-// Warps per slice from the mean row length: the smallest power of two that
-// leaves at most `per_lane` entries per lane (default 12), capped at
-// `max_parts` (default 8).  Both can be overridden for tuning with
-// AIRG_PER_LANE / AIRG_MAX_PARTS.
-inline int choose_parts(long long nnz, int n_rows)
-{
-    static int max_parts = 0, per_lane = 0;
-    if (!max_parts) {
-        const char* e = getenv("AIRG_MAX_PARTS");
-        max_parts = e ? std::max(1, std::min(32, atoi(e))) : 8;
-        const char* q = getenv("AIRG_PER_LANE");
-        per_lane = q ? std::max(1, atoi(q)) : 12;
-    }
-    double avg = n_rows ? double(nnz) / n_rows : 0.0;
-    int p = 1;
-    while (p < max_parts && avg > double(per_lane) * p) p *= 2;
-    return p;
-}
-
-// warps per block for P warps per slice (blocks of at least 8 warps)
-__host__ __device__ constexpr int wpb_for(int P) { return P > 8 ? P : 8; }
-
-template <class T>
-struct SolveLevelT {
-    Sell<T> Z, M, Aff;
-};
-
-struct SolveLevel {
-    int off = 0, n_f = 0, n_c = 0;
-    DBuf<int> W;                 // nested-relative C position, -1 none
-    std::vector<double> alpha;
-    SolveLevelT<double> d;
-    SolveLevelT<float> f;
-};
-
-struct SolveData {
-    int n0 = 0, nlev = 0, off_c = 0, n_coarse = 0;
-    DBuf<int> pos0;              // natural index -> nested position (top level)
-    Sell<double> Atop;
-    std::vector<std::unique_ptr<SolveLevel>> lv;
-    Sell<double> Ac;
-    Sell<float> Ac32;
-    std::vector<Root> roots;
-    // persistent coarse polynomial: CSR copies, roots on the device, barrier
-    DBuf<double> roots_dev;
-    DBuf<unsigned> bar;          // [count, generation, error flag]
-    DBuf<unsigned> ticket;       // last-block ticket of the dot kernels
-    int newton_grid[2] = {0, 0}; // per precision (0: FP64, 1: FP32); 0 = not usable
-    int smooth_grid[2] = {0, 0}; // co-resident blocks of the persistent smoother
-    int max_nf = 0;
-    // V-cycle work (FP64 and FP32 copies)
-    DBuf<double> rwork, t, wa, wb, cx, cr0, cr1, ct;
-    DBuf<float> rwork32, e32, t32, wa32, wb32, cx32, cr032, cr132, ct32, vin32;
-    // outer FGMRES
-    int restart = 0;
-    DBuf<double> V, Zs, w, bp, xp, r, part;
-    DBuf<double> hdev;
-    HBuf<double> hhost;
-    long long bytes_vcycle = 0;
-    // launch count and optional per-kind CUDA-event timing of the solve kernels
-    long long launches = 0;
-    bool prof = false;
-    struct Rec { int kind; cudaEvent_t a, b; long long bytes; };
-    std::vector<cudaEvent_t> evpool;
-    size_t evnext = 0;
-    std::vector<Rec> recs;
-    std::vector<cudaGraphExec_t> prof_execs;   // profiled V-cycle graphs awaiting collect()
-    double kind_ms[PROF_KINDS] = {};
-    long long kind_launches[PROF_KINDS] = {}, kind_bytes[PROF_KINDS] = {};
-    cudaEvent_t next_event()
-    {
-        if (evnext == evpool.size()) {
-            cudaEvent_t e;
-            CK(cudaEventCreate(&e));
-            evpool.push_back(e);
-        }
-        return evpool[evnext++];
-    }
-    // inside a stream capture an event record becomes a timing node of the
-    // graph only with cudaEventRecordExternal
-    static void record(cudaEvent_t e, cudaStream_t st)
-    {
-        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-        CK(cudaStreamIsCapturing(st, &cs));
-        if (cs == cudaStreamCaptureStatusActive) CK(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal));
-        else CK(cudaEventRecord(e, st));
-    }
-    void begin(cudaStream_t st, cudaEvent_t& a)
-    {
-        ++launches;
-        if (prof) { a = next_event(); record(a, st); }
-    }
-    void end(int kind, long long bytes, cudaStream_t st, cudaEvent_t a)
-    {
-        if (!prof) return;
-        cudaEvent_t b = next_event();
-        record(b, st);
-        recs.push_back(Rec{kind, a, b, bytes});
-    }
-    // after the stream has been synchronised
-    void collect()
-    {
-        for (const Rec& r : recs) {
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, r.a, r.b));
-            kind_ms[r.kind] += ms;
-            kind_launches[r.kind] += 1;
-            kind_bytes[r.kind] += r.bytes;
-        }
-        recs.clear();
-        evnext = 0;
-        for (cudaGraphExec_t e : prof_execs) cudaGraphExecDestroy(e);
-        prof_execs.clear();
-    }
-    // private stream (capturable, unlike the legacy default stream) and the
-    // V-cycle graphs, one per (input, output) pair = FGMRES basis slot
-    cudaStream_t sst = nullptr;
-    cudaEvent_t ev_in = nullptr;
-    bool use_graphs = true;
-    struct GEntry { const void* v; void* z; cudaGraphExec_t exec; long long kernels; };
-    std::vector<GEntry> graphs;
-    ~SolveData()
-    {
-        for (cudaEvent_t e : evpool) cudaEventDestroy(e);
-        for (GEntry& g : graphs) cudaGraphExecDestroy(g.exec);
-        for (cudaGraphExec_t e : prof_execs) cudaGraphExecDestroy(e);
-        if (ev_in) cudaEventDestroy(ev_in);
-        if (sst) cudaStreamDestroy(sst);
-    }
-};
-
-// Launch through the counter / profiler: LAUNCH(S, kind, bytes, kernel<<<...>>>(...))
-#define LAUNCH(S, KIND, BYTES, ...)                  \
-    do {                                             \
-        cudaEvent_t ev_a_ = nullptr;                 \
-        (S).begin(st, ev_a_);                        \
-        __VA_ARGS__;                                 \
-        (S).end((KIND), (BYTES), st, ev_a_);         \
-    } while (0)
-
 Hierarchy::Hierarchy() = default;
 Hierarchy::~Hierarchy() = default;
 
@@ -729,20 +558,24 @@ k_smooth_persistent(SellView<T> M, int pm, SellView<T> A, int pa, const T* __res
 
 // ---------------------------------------------------------- Krylov kernels --
 constexpr int RB = 256;          // reduction block
-constexpr int RGRID = 304;       // partial sums per reduction (2 x SMs)
+constexpr int RGRID = 1216;      // partial sums per reduction (8 x SMs)
 
-// out[i] = <w, V_i> for i < m.  Blocks write partial sums; the last block to
-// finish (atomic ticket) adds them in a fixed order and resets the ticket.
+// out[i] = <w, V_i> for i < m, and out[m] = <w, w> when selfdot.  Blocks
+// write partial sums; the last block to finish (atomic ticket) adds them in
+// a fixed order and resets the ticket.
 __global__ void k_multidot(long long n, int m, const double* __restrict__ V, long long ldv,
                            const double* __restrict__ w, double* __restrict__ part,
-                           double* __restrict__ out, unsigned* ticket)
+                           double* __restrict__ out, unsigned* ticket, int selfdot = 0)
 {
     __shared__ double red[RB / 32][32];
     __shared__ bool last_block;
+    const int mm = m;
+    m += selfdot ? 1 : 0;
     for (int i = 0; i < m; ++i) {
+        const double* vi = i < mm ? V + i * ldv : w;
         double s = 0.0;
         for (long long r = (long long)blockIdx.x * RB + threadIdx.x; r < n; r += (long long)gridDim.x * RB)
-            s = fma(V[i * ldv + r], w[r], s);
+            s = fma(vi[r], w[r], s);
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][i & 31] = s;
         __syncthreads();
@@ -775,16 +608,6 @@ __global__ void k_multidot(long long n, int m, const double* __restrict__ V, lon
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// out[i] = sum_b part[b*m + i], fixed order
-__global__ void k_sum_parts(int nb, int m, const double* part, double* out)
-{
-    int i = threadIdx.x;
-    if (i >= m) return;
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[(long long)b * m + i];
-    out[i] = s;
-}
-
 // w -= sum_i h_i V_i
 __global__ void k_multiaxpy(long long n, int m, const double* __restrict__ V, long long ldv,
                             const double* __restrict__ h, double* __restrict__ w)
@@ -794,6 +617,48 @@ __global__ void k_multiaxpy(long long n, int m, const double* __restrict__ V, lo
     double s = w[r];
     for (int i = 0; i < m; ++i) s = fma(-h[i], V[i * ldv + r], s);
     w[r] = s;
+}
+
+// w -= sum_i h_i V_i, and *out = ||w||^2 of the result (partial sums per
+// block, fixed-order sum in the last block)
+__global__ void k_multiaxpy_norm(long long n, int m, const double* __restrict__ V, long long ldv,
+                                 const double* __restrict__ h, double* __restrict__ w,
+                                 double* __restrict__ part, double* __restrict__ out, unsigned* ticket)
+{
+    __shared__ double red[RB / 32];
+    __shared__ bool last_block;
+    double ss = 0.0;
+    for (long long r = (long long)blockIdx.x * RB + threadIdx.x; r < n; r += (long long)gridDim.x * RB) {
+        double s = w[r];
+        for (int i = 0; i < m; ++i) s = fma(-h[i], V[i * ldv + r], s);
+        w[r] = s;
+        ss = fma(s, s, ss);
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < RB / 32; ++q) t += red[q];
+        part[blockIdx.x] = t;
+    }
+    __threadfence();
+    if (threadIdx.x == 0) last_block = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last_block) return;
+    __threadfence();
+    double s = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += RB) s += part[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < RB / 32; ++q) t += red[q];
+        *out = t;
+        *ticket = 0u;
+    }
 }
 
 // x += sum_i y_i Z_i   (y on device)
@@ -1267,22 +1132,36 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             precond(H, vj, zj, st);
             LAUNCH(S, PK_TOPSPMV, topB,
                    WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), bk(KK), 0, st>>>(A, zj, S.w.p)));
-            // classical Gram-Schmidt, twice
-            for (int pass = 0; pass < 2; ++pass) {
-                LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 2),
-                       k_multidot<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, S.w.p, S.part.p,
-                                                        S.hdev.p + pass * (m + 2), S.ticket.p));
-                LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 3),
-                       k_multiaxpy<<<g, TB, 0, st>>>(n, j + 1, S.V.p, n, S.hdev.p + pass * (m + 2), S.w.p));
-            }
-            LAUNCH(S, PK_KRYLOV, 8 * n,
-                   k_multidot<<<RGRID, RB, 0, st>>>(n, 1, S.w.p, n, S.w.p, S.part.p,
-                                                    S.hdev.p + 2 * (m + 2), S.ticket.p));
+            // classical Gram-Schmidt; a second pass only when the first
+            // one cancelled more than half of ||w||^2 ("twice is enough",
+            // Daniel, Gragg, Kaufman & Stewart 1976): ||w'|| < ||w|| / sqrt(2)
+            double* h1 = S.hdev.p;
+            double* h2 = S.hdev.p + (m + 2);
+            double* nrm = S.hdev.p + 2 * (m + 2);
+            LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 2),
+                   k_multidot<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, S.w.p, S.part.p, h1, S.ticket.p, 1));
+            LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 3),
+                   k_multiaxpy_norm<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, h1, S.w.p, S.part.p, nrm,
+                                                          S.ticket.p));
             CK_LAUNCH();
             CK(cudaMemcpyAsync(hh, S.hdev.p, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            for (int i = 0; i <= j; ++i) Hm[size_t(i) * m + j] = hh[i] + hh[(m + 2) + i];
-            double hn = std::sqrt(std::max(hh[2 * (m + 2)], 0.0));
+            double ww = hh[j + 1], w1 = hh[2 * (m + 2)];
+            for (int i = 0; i <= j; ++i) Hm[size_t(i) * m + j] = hh[i];
+            double hsq = w1;
+            if (w1 < 0.5 * ww) {
+                LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 2),
+                       k_multidot<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, S.w.p, S.part.p, h2, S.ticket.p));
+                LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 3),
+                       k_multiaxpy_norm<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, h2, S.w.p, S.part.p, nrm,
+                                                              S.ticket.p));
+                CK_LAUNCH();
+                CK(cudaMemcpyAsync(hh, S.hdev.p, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                for (int i = 0; i <= j; ++i) Hm[size_t(i) * m + j] += hh[(m + 2) + i];
+                hsq = hh[2 * (m + 2)];
+            }
+            double hn = std::sqrt(std::max(hsq, 0.0));
             Hm[size_t(j + 1) * m + j] = hn;
             for (int i = 0; i < j; ++i) {
                 double a = Hm[size_t(i) * m + j], b = Hm[size_t(i + 1) * m + j];
@@ -1320,7 +1199,84 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
     info.converged = info.converged && (rn <= tol);
 }
 
+
+// v = w / sqrt(nrm2) when *active and nrm2 > 0, else 0 (device-side scaling,
+// so that it can sit inside a captured graph)
+__global__ void k_scale_dev(long long n, const double* __restrict__ w, const double* __restrict__ nrm2,
+                            const int* __restrict__ active, double* __restrict__ v)
+{
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double q = *nrm2;
+    double inv = (*active && q > 0.0) ? 1.0 / sqrt(q) : 0.0;
+    v[r] = w[r] * inv;
+}
+
 }  // namespace
+
+// ----------------------------------------- launch helpers for multi.cu ----
+void mp_vcycle(Hierarchy& H, const double* v, double* z, cudaStream_t st) { precond_launch(H, v, z, st); }
+
+void mp_top_spmv(Hierarchy& H, const double* x, double* y, cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    long long n = S.n0;
+    SellView<double> A = view(S.Atop);
+    LAUNCH(S, PK_TOPSPMV, S.Atop.nnz * 12 + 16 * n,
+           WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), bk(KK), 0, st>>>(A, x, y)));
+}
+
+void mp_multidot(Hierarchy& H, int m, const double* V, const double* w, double* out, int selfdot,
+                 cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    long long n = S.n0;
+    LAUNCH(S, PK_KRYLOV, 8LL * n * (m + 1),
+           k_multidot<<<RGRID, RB, 0, st>>>(n, m, V, n, w, S.part.p, out, S.ticket.p, selfdot));
+}
+
+void mp_multiaxpy_norm(Hierarchy& H, int m, const double* V, const double* h, double* w, double* out,
+                       cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    long long n = S.n0;
+    LAUNCH(S, PK_KRYLOV, 8LL * n * (m + 2),
+           k_multiaxpy_norm<<<RGRID, RB, 0, st>>>(n, m, V, n, h, w, S.part.p, out, S.ticket.p));
+}
+
+void mp_scale_dev(Hierarchy& H, const double* w, const double* nrm2, const int* active, double* v,
+                  cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    long long n = S.n0;
+    LAUNCH(S, PK_KRYLOV, 16 * n, k_scale_dev<<<grid_for(n, TB), TB, 0, st>>>(n, w, nrm2, active, v));
+}
+
+void mp_residual(Hierarchy& H, const double* b, const double* x, double* y, double* r, cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    long long n = S.n0;
+    mp_top_spmv(H, x, y, st);
+    LAUNCH(S, PK_KRYLOV, 24 * n, k_sub2<<<grid_for(n, TB), TB, 0, st>>>(n, b, y, r));
+}
+
+void mp_update(Hierarchy& H, int m, const double* Zs, const double* y, double* x, cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    long long n = S.n0;
+    LAUNCH(S, PK_KRYLOV, 8LL * n * (m + 2),
+           k_multiaxpy_plus<<<grid_for(n, TB), TB, 0, st>>>(n, m, Zs, n, y, x));
+}
+
+void mp_permute(Hierarchy& H, const double* a, double* b, bool to_nested, cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    long long n = S.n0;
+    if (to_nested)
+        LAUNCH(S, PK_LAYOUT, 20 * n, k_to_nested<<<grid_for(n, TB), TB, 0, st>>>(n, S.pos0.p, a, b));
+    else
+        LAUNCH(S, PK_LAYOUT, 20 * n, k_from_nested<<<grid_for(n, TB), TB, 0, st>>>(n, S.pos0.p, a, b));
+}
 
 void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_device, double rtol,
                   double atol, int maxit, airg_solve_info* info_out, cudaStream_t caller)
@@ -1347,6 +1303,15 @@ void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_de
         xdev = xd.p;
     }
     int g = grid_for(n, TB);
+    const char* nb = getenv("AIRG_NO_BATCH");
+    if (nrhs > 1 && !(nb && nb[0] == '1')) {
+        // many right-hand sides: lockstep FGMRES with the batched V-cycle
+        for (int q0 = 0; q0 < nrhs; q0 += batch_max_width()) {
+            int kq = std::min(batch_max_width(), nrhs - q0);
+            solve_batched(H, kq, bdev + size_t(q0) * n, xdev + size_t(q0) * n, rtol, atol, maxit, info, st);
+        }
+        nrhs = 0;
+    }
     for (int q = 0; q < nrhs; ++q) {
         LAUNCH(S, PK_LAYOUT, 20 * n, k_to_nested<<<g, TB, 0, st>>>(n, S.pos0.p, bdev + size_t(q) * n, S.bp.p));
         LAUNCH(S, PK_LAYOUT, 20 * n, k_to_nested<<<g, TB, 0, st>>>(n, S.pos0.p, xdev + size_t(q) * n, S.xp.p));

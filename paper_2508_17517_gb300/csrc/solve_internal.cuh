@@ -1,0 +1,214 @@
+// Solve-phase data structures shared by solve.cu (single right-hand side)
+// and batch.cu (many right-hand sides in lockstep): SELL-32 operators, the
+// per-level operators of the nested F/C layout, work buffers, the launch
+// counter / profiler and the captured V-cycle graphs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "dev_util.cuh"
+#include "handle.h"
+
+namespace airg {
+
+struct BatchData;   // batch.cu
+
+enum { PK_RESTRICT = 0, PK_FRESID = 1, PK_HORNER = 2, PK_NEWTON = 3, PK_TOPSPMV = 4, PK_KRYLOV = 5,
+       PK_LAYOUT = 6, PROF_KINDS = 7 };
+
+// A solve-phase operator in SELL-32: slices of 32 consecutive rows, entries
+// column-major inside a slice (entry k of the slice's 32 rows are adjacent),
+// each slice padded to its longest row (padding: value 0, column repeated).
+// Lane l of a warp always owns row 32s+l, so at a given entry index the 32
+// lanes read adjacent values and columns, and -- rows of these operators
+// having similar stencils -- gather nearby entries of x.  k = number of
+// warps sharing a slice: for long rows the entries of a slice are split
+// among k warps of a block (entry indices interleaved) whose partial sums
+// meet in shared memory.
+template <class T>
+struct Sell {
+    int n_rows = 0, n_cols = 0, n_slices = 0, k = 1;
+    long long nnz = 0, padded = 0;
+    DBuf<int> sptr;
+    DBuf<int> col;
+    DBuf<T> val;
+};
+
+template <class T>
+struct SellView {
+    int n_rows, n_slices;
+    const int* __restrict__ sptr;
+    const int* __restrict__ col;
+    const T* __restrict__ val;
+};
+
+template <class T>
+SellView<T> view(const Sell<T>& s) { return SellView<T>{s.n_rows, s.n_slices, s.sptr.p, s.col.p, s.val.p}; }
+
+// Warps per slice from the mean row length: the smallest power of two that
+// leaves at most `per_lane` entries per lane (default 12), capped at
+// `max_parts` (default 8).  Both can be overridden for tuning with
+// AIRG_PER_LANE / AIRG_MAX_PARTS.
+inline int choose_parts(long long nnz, int n_rows)
+{
+    static int max_parts = 0, per_lane = 0;
+    if (!max_parts) {
+        const char* e = getenv("AIRG_MAX_PARTS");
+        max_parts = e ? std::max(1, std::min(32, atoi(e))) : 8;
+        const char* q = getenv("AIRG_PER_LANE");
+        per_lane = q ? std::max(1, atoi(q)) : 12;
+    }
+    double avg = n_rows ? double(nnz) / n_rows : 0.0;
+    int p = 1;
+    while (p < max_parts && avg > double(per_lane) * p) p *= 2;
+    return p;
+}
+
+// warps per block for P warps per slice (blocks of at least 8 warps)
+__host__ __device__ constexpr int wpb_for(int P) { return P > 8 ? P : 8; }
+
+template <class T>
+struct SolveLevelT {
+    Sell<T> Z, M, Aff;
+};
+
+struct SolveLevel {
+    int off = 0, n_f = 0, n_c = 0;
+    DBuf<int> W;                 // nested-relative C position, -1 none
+    std::vector<double> alpha;
+    SolveLevelT<double> d;
+    SolveLevelT<float> f;
+};
+
+struct SolveData {
+    int n0 = 0, nlev = 0, off_c = 0, n_coarse = 0;
+    DBuf<int> pos0;              // natural index -> nested position (top level)
+    Sell<double> Atop;
+    std::vector<std::unique_ptr<SolveLevel>> lv;
+    Sell<double> Ac;
+    Sell<float> Ac32;
+    std::vector<Root> roots;
+    // persistent coarse polynomial: CSR copies, roots on the device, barrier
+    DBuf<double> roots_dev;
+    DBuf<unsigned> bar;          // [count, generation, error flag]
+    DBuf<unsigned> ticket;       // last-block ticket of the dot kernels
+    int newton_grid[2] = {0, 0}; // per precision (0: FP64, 1: FP32); 0 = not usable
+    int smooth_grid[2] = {0, 0}; // co-resident blocks of the persistent smoother
+    int max_nf = 0;
+    // V-cycle work (FP64 and FP32 copies)
+    DBuf<double> rwork, t, wa, wb, cx, cr0, cr1, ct;
+    DBuf<float> rwork32, e32, t32, wa32, wb32, cx32, cr032, cr132, ct32, vin32;
+    // outer FGMRES
+    int restart = 0;
+    DBuf<double> V, Zs, w, bp, xp, r, part;
+    DBuf<double> hdev;
+    HBuf<double> hhost;
+    long long bytes_vcycle = 0;
+    std::shared_ptr<BatchData> batch;   // work space of the many-RHS solve (batch.cu)
+    // launch count and optional per-kind CUDA-event timing of the solve kernels
+    long long launches = 0;
+    bool prof = false;
+    struct Rec { int kind; cudaEvent_t a, b; long long bytes; };
+    std::vector<cudaEvent_t> evpool;
+    size_t evnext = 0;
+    std::vector<Rec> recs;
+    std::vector<cudaGraphExec_t> prof_execs;   // profiled V-cycle graphs awaiting collect()
+    double kind_ms[PROF_KINDS] = {};
+    long long kind_launches[PROF_KINDS] = {}, kind_bytes[PROF_KINDS] = {};
+    cudaEvent_t next_event()
+    {
+        if (evnext == evpool.size()) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            evpool.push_back(e);
+        }
+        return evpool[evnext++];
+    }
+    // inside a stream capture an event record becomes a timing node of the
+    // graph only with cudaEventRecordExternal
+    static void record(cudaEvent_t e, cudaStream_t st)
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(st, &cs));
+        if (cs == cudaStreamCaptureStatusActive) CK(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal));
+        else CK(cudaEventRecord(e, st));
+    }
+    void begin(cudaStream_t st, cudaEvent_t& a)
+    {
+        ++launches;
+        if (prof) { a = next_event(); record(a, st); }
+    }
+    void end(int kind, long long bytes, cudaStream_t st, cudaEvent_t a)
+    {
+        if (!prof) return;
+        cudaEvent_t b = next_event();
+        record(b, st);
+        recs.push_back(Rec{kind, a, b, bytes});
+    }
+    // after the stream has been synchronised
+    void collect()
+    {
+        for (const Rec& r : recs) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, r.a, r.b));
+            kind_ms[r.kind] += ms;
+            kind_launches[r.kind] += 1;
+            kind_bytes[r.kind] += r.bytes;
+        }
+        recs.clear();
+        evnext = 0;
+        for (cudaGraphExec_t e : prof_execs) cudaGraphExecDestroy(e);
+        prof_execs.clear();
+    }
+    // private stream (capturable, unlike the legacy default stream) and the
+    // V-cycle graphs, one per (input, output) pair = FGMRES basis slot
+    cudaStream_t sst = nullptr;
+    cudaEvent_t ev_in = nullptr;
+    bool use_graphs = true;
+    struct GEntry { const void* v; void* z; cudaGraphExec_t exec; long long kernels; };
+    std::vector<GEntry> graphs;
+    ~SolveData()
+    {
+        for (cudaEvent_t e : evpool) cudaEventDestroy(e);
+        for (GEntry& g : graphs) cudaGraphExecDestroy(g.exec);
+        for (cudaGraphExec_t e : prof_execs) cudaGraphExecDestroy(e);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (sst) cudaStreamDestroy(sst);
+    }
+};
+
+// Launch through the counter / profiler: LAUNCH(S, kind, bytes, kernel<<<...>>>(...))
+#define LAUNCH(S, KIND, BYTES, ...)                  \
+    do {                                             \
+        cudaEvent_t ev_a_ = nullptr;                 \
+        (S).begin(st, ev_a_);                        \
+        __VA_ARGS__;                                 \
+        (S).end((KIND), (BYTES), st, ev_a_);         \
+    } while (0)
+
+
+// solve.cu: launch helpers of one problem's solve, for the multi-problem
+// solver (multi.cu); all launch on `st` and use the problem's own buffers
+void mp_vcycle(Hierarchy& H, const double* v, double* z, cudaStream_t st);
+void mp_top_spmv(Hierarchy& H, const double* x, double* y, cudaStream_t st);
+void mp_multidot(Hierarchy& H, int m, const double* V, const double* w, double* out, int selfdot,
+                 cudaStream_t st);
+void mp_multiaxpy_norm(Hierarchy& H, int m, const double* V, const double* h, double* w, double* out,
+                       cudaStream_t st);
+void mp_scale_dev(Hierarchy& H, const double* w, const double* nrm2, const int* active, double* v,
+                  cudaStream_t st);
+void mp_residual(Hierarchy& H, const double* b, const double* x, double* y, double* r, cudaStream_t st);
+void mp_update(Hierarchy& H, int m, const double* Zs, const double* y, double* x, cudaStream_t st);
+void mp_permute(Hierarchy& H, const double* a, double* b, bool to_nested, cudaStream_t st);
+
+// batch.cu: k right-hand sides in lockstep (k <= batch_max_width())
+void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol, double atol,
+                   int maxit, airg_solve_info& info, cudaStream_t st);
+int batch_max_width();
+
+}  // namespace airg

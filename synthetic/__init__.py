@@ -52,17 +52,34 @@ def workload(name, n=None):
         return dict(nx=nx, ny=ny, theta=th, g=g, s=None, n_rhs=1, rtol=1e-10,
                     opts=dict(coarse_poly_order=30, trunc_rtol=1e-2, precision=prec),
                     desc="%dx%d theta seeded g~U[0,1] %s V-cycle" % (nx, ny, "FP32" if prec else "FP64"))
-    if name == "c4a":
-        # 2048x2048, one operator, 64 right-hand sides: g ~ U[0,1], s ~ N(0,1)
+    if name in ("c4a", "c4a_fp64"):
+        # 2048x2048, one operator, 64 right-hand sides: g ~ U[0,1], s ~ N(0,1);
+        # batched V-cycle in FP32 ("c4a_fp64": FP64), rtol 1e-8
         nx = ny = n or 2048
         rng = np.random.default_rng(BASE_SEED + 4)
         th = float(rng.uniform(math.pi / 12, 5 * math.pi / 12))
         k = 64
         g = rng.uniform(0.0, 1.0, (k, _n_inflow(nx, ny, th)))
         s = rng.standard_normal((k, nx * ny))
+        prec = 1 if name == "c4a" else 0
         return dict(nx=nx, ny=ny, theta=th, g=g, s=s, n_rhs=k, rtol=1e-8,
+                    opts=dict(coarse_poly_order=30, trunc_rtol=1e-2, precision=prec),
+                    desc="%dx%d 64 rhs g~U[0,1] s~N(0,1) %s batched V-cycle" % (
+                        nx, ny, "FP32" if prec else "FP64"))
+    if name == "c4b":
+        # 32 separate problems: N_p ~ U{128..1024} per side (square grids),
+        # theta_p ~ U[pi/12, 5pi/12], g ~ U[0,1] per inflow node; rtol 1e-8
+        rng = np.random.default_rng(BASE_SEED + 41)
+        count = n or 32
+        probs = []
+        for _ in range(count):
+            N = int(rng.integers(128, 1025))
+            th = float(rng.uniform(math.pi / 12, 5 * math.pi / 12))
+            g = rng.uniform(0.0, 1.0, _n_inflow(N, N, th))
+            probs.append(dict(nx=N, ny=N, theta=th, g=g))
+        return dict(problems=probs, rtol=1e-8, n_rhs=1,
                     opts=dict(coarse_poly_order=30, trunc_rtol=1e-2),
-                    desc="%dx%d 64 rhs g~U[0,1] s~N(0,1)" % (nx, ny))
+                    desc="%d grids N~U{128..1024}^2 theta_p~U[pi/12,5pi/12] g~U[0,1]" % count)
     if name == "c5":
         # 1024x1024 adjoint workload: g ~ U[0,1], s ~ N(0,1), target u_t ~ N(1, 0.1^2)
         nx = ny = n or 1024

@@ -1,0 +1,58 @@
+"""Separate problems of uneven size solved together (one hierarchy each,
+lockstep FGMRES, one graph launch per iteration for all problems): each
+solution must match the oracle's solve of that problem to 1e-9 relative L2,
+with its true residual at or below rtol."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2508_17517_gb300 as G  # noqa: E402
+from oracle import airg as O  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    G.build()
+    G.lib()
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_uneven_batch_matches_oracle(host):
+    rng = np.random.default_rng(3)
+    shapes = [(37, 41), (96, 64), (130, 127), (50, 50), (200, 90)]
+    thetas = [0.4, 1.1, 2.5, 4.0, 5.6]          # all four quadrants of v
+    opts = dict(coarse_poly_order=30, trunc_rtol=1e-2)
+    probs, csrs, bs, ref = [], [], [], []
+    for (nx, ny), th in zip(shapes, thetas):
+        vx, vy = math.cos(th), math.sin(th)
+        pg = G.airg_problem_advection2d(nx, ny, vx, vy)
+        po = O.advection_2d(nx, ny, vx, vy)
+        g = rng.uniform(0.0, 1.0, po.inflow.size)
+        s = rng.standard_normal(nx * ny)
+        b = G.airg_assemble_rhs_advection2d(pg, torch.tensor(g, device="cuda"),
+                                            torch.tensor(s, device="cuda"))
+        bo = O.assemble_rhs(po, g, s)
+        assert np.array_equal(b.cpu().numpy(), bo)
+        csrs.append((pg["rowptr"], pg["col"], pg["val"]))
+        bs.append(b.cpu() if host else b)
+        Ho = O.setup(po.A, O.Options(**opts))
+        xo, _ = O.solve(Ho, po.A, bo, rtol=1e-10)
+        ref.append((po, bo, xo))
+    B = G.airg_setup_batch(csrs, G.airg_options_default(**opts))
+    xs, infos = G.airg_solve_batch(B, bs, rtol=1e-10)
+    for x, info, (po, bo, xo) in zip(xs, infos, ref):
+        xg = x.cpu().numpy()
+        assert info.converged
+        assert np.linalg.norm(bo - O.spmv(po.A, xg)) <= 1e-10 * np.linalg.norm(bo) * (1 + 1e-6)
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-9
+    # a second solve reuses the captured iteration graphs
+    xs2, infos2 = G.airg_solve_batch(B, bs, rtol=1e-10)
+    for x, x2 in zip(xs, xs2):
+        assert np.linalg.norm((x - x2).cpu().numpy()) <= 1e-12 * np.linalg.norm(x.cpu().numpy())
