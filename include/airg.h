@@ -257,6 +257,17 @@ airg_status airg_profile(airg_handle* h, int enable);
 airg_status airg_profile_read(const airg_handle* h, int kind, double* ms, int64_t* launches,
                               int64_t* bytes);
 
+/*
+ * Failure-detection check of the device-side waits: launches one block that
+ * waits, through the same bounded wait as the grid barrier of the
+ * persistent kernels, for an arrival that never comes.  The wait must give
+ * up after `spin_limit` polls of ~50 ns, record the error flag and let the
+ * kernel finish; the call then returns AIRG_ERR_TIMEOUT (the designed
+ * outcome) and the CUDA context stays usable.  Any other status means the
+ * mechanism is broken.  Nothing hangs or faults.
+ */
+airg_status airg_check_wait_timeout(int64_t spin_limit, void* stream);
+
 /* Releases every device and host buffer of the handle.  NULL is a no-op. */
 void airg_free(airg_handle* h);
 

@@ -28,7 +28,7 @@ EXPORTS = ["airg_options_default", "airg_problem_advection2d", "airg_assemble_rh
            "airg_dot_exact", "airg_rng_uniform", "airg_host_gmres_coeffs", "airg_host_eigvals",
            "airg_profile", "airg_profile_read", "airg_dot_exact_noalloc",
            "airg_rhs_adjoint_advection2d", "airg_setup_batch", "airg_solve_batch",
-           "airg_batch_free"]
+           "airg_batch_free", "airg_check_wait_timeout"]
 PROFILE_KINDS = ["restrict", "f_residual", "f_smoother", "coarse_newton", "top_spmv",
                  "krylov_vectors", "layout"]
 
@@ -106,6 +106,7 @@ def lib():
             "airg_profile": [vp, ci],
             "airg_dot_exact_noalloc": [i64, vp, vp, vp, vp],
             "airg_rhs_adjoint_advection2d": [i64, i64, f64, f64, f64, ci, vp, i64, vp, vp, vp, vp],
+            "airg_check_wait_timeout": [i64, vp],
             "airg_setup_batch": [ci, ctypes.POINTER(airg_csr), ctypes.POINTER(airg_options), vp,
                                  ctypes.POINTER(vp)],
             "airg_solve_batch": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ci, f64, f64, ci,
@@ -330,6 +331,12 @@ def airg_export_vector(handle, level, what):
     out = np.empty(max(cnt.value, 1), _VEC_DTYPES[what])
     _check(L.airg_export_vector(handle.ptr, level, what, ctypes.byref(cnt), out.ctypes.data))
     return out[: cnt.value]
+
+
+def airg_check_wait_timeout(spin_limit=20000, stream=None):
+    """Status of the bounded-wait self check (AIRG_ERR_TIMEOUT = 6 is the
+    designed outcome)."""
+    return lib().airg_check_wait_timeout(int(spin_limit), _stream(stream))
 
 
 def airg_free(handle):

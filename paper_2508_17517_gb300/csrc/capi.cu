@@ -437,6 +437,21 @@ airg_status airg_profile_read(const airg_handle* h, int kind, double* ms, int64_
     });
 }
 
+airg_status airg_check_wait_timeout(int64_t spin_limit, void* stream)
+{
+    bool gave_up = false;
+    airg_status st = guarded([&] {
+        if (spin_limit < 1) airg::fail(AIRG_ERR_ARG, "spin_limit must be positive");
+        gave_up = airg::barrier_timeout_check(spin_limit, (cudaStream_t)stream);
+        if (!gave_up) airg::fail(AIRG_ERR_STATE, "the bounded wait did not report its timeout");
+    });
+    if (st == AIRG_OK && gave_up) {
+        g_last_error = "bounded device wait gave up after spin_limit polls (as intended)";
+        return AIRG_ERR_TIMEOUT;
+    }
+    return st;
+}
+
 void airg_free(airg_handle* h) { delete h; }
 
 const char* airg_last_error(void) { return g_last_error.c_str(); }

@@ -380,7 +380,9 @@ inline int bk(int P) { return 32 * wpb_for(P); }
 // ends instead of hanging.
 constexpr long long BARRIER_SPIN_LIMIT = 20000000;   // ~1 s of 50 ns polls
 
-__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, int* err)
+// Bounded wait for `expected` arrivals (gridDim.x for a grid barrier).
+__device__ __forceinline__ void grid_barrier_n(unsigned* count, unsigned* gen, int* err,
+                                               unsigned expected, long long limit)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -388,20 +390,32 @@ __device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, int
         unsigned g = *vgen;
         __threadfence();
         unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == expected - 1) {
             atomicExch(count, 0u);
             __threadfence();
             atomicAdd(gen, 1u);
         } else {
             long long spins = 0;
             while (*vgen == g) {
-                if (++spins > BARRIER_SPIN_LIMIT) { atomicExch(err, 1); break; }
+                if (++spins > limit) { atomicExch(err, 1); break; }
                 __nanosleep(50);
             }
         }
         __threadfence();
     }
     __syncthreads();
+}
+
+__device__ __forceinline__ void grid_barrier(unsigned* count, unsigned* gen, int* err)
+{
+    grid_barrier_n(count, gen, err, gridDim.x, BARRIER_SPIN_LIMIT);
+}
+
+// Failure-detection check: one block waits for an arrival that never comes
+// (expected = 2 with a single block) and must give up after `limit` polls.
+__global__ void k_barrier_timeout_check(unsigned* state, long long limit)
+{
+    grid_barrier_n(state, state + 1, reinterpret_cast<int*>(state + 2), 2u, limit);
 }
 
 // x = q(A) b with the Newton roots of Sec. 2.3 (real: x += r/th, r -= A r/th;
@@ -1276,6 +1290,19 @@ void mp_permute(Hierarchy& H, const double* a, double* b, bool to_nested, cudaSt
         LAUNCH(S, PK_LAYOUT, 20 * n, k_to_nested<<<grid_for(n, TB), TB, 0, st>>>(n, S.pos0.p, a, b));
     else
         LAUNCH(S, PK_LAYOUT, 20 * n, k_from_nested<<<grid_for(n, TB), TB, 0, st>>>(n, S.pos0.p, a, b));
+}
+
+// Runs the bounded wait of the grid barrier against an arrival that never
+// comes; returns true if the wait gave up (error flag set) as designed.
+bool barrier_timeout_check(long long limit, cudaStream_t st)
+{
+    DBuf<unsigned> state(4);
+    CK(cudaMemsetAsync(state.p, 0, state.bytes(), st));
+    k_barrier_timeout_check<<<1, 32, 0, st>>>(state.p, limit);
+    CK_LAUNCH();
+    unsigned h[4];
+    d2h(h, state.p, 4, st);
+    return h[2] != 0;
 }
 
 void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_device, double rtol,

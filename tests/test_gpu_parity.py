@@ -228,3 +228,12 @@ def test_chunked_sparse_products(monkeypatch):
             "T._check_setup(c); T._check_solve(c)" % T_ROOT)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+
+
+def test_bounded_device_wait_reports_timeout():
+    """A device-side wait that nothing satisfies gives up after its poll
+    limit and reports AIRG_ERR_TIMEOUT; the context stays usable."""
+    assert G.airg_check_wait_timeout(20000) == 6
+    assert "gave up" in G.airg_last_error()
+    c = Case(workload("grid", (40, 30)))
+    _check_solve(c)
