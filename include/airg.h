@@ -46,6 +46,9 @@ typedef enum {
 } airg_status;
 
 enum { AIRG_FP64 = 0, AIRG_MIXED_FP32 = 1 };
+/* Outer iteration around the V-cycle: flexible GMRES (default), or the
+ * preconditioned Richardson iteration x <- x + M^-1 (b - A x) of Sec. 3. */
+enum { AIRG_OUTER_FGMRES = 0, AIRG_OUTER_RICHARDSON = 1 };
 
 /* Compressed sparse row matrix (n_rows x n_cols).  Caller-owned, read-only. */
 typedef struct {
@@ -82,6 +85,7 @@ typedef struct {
     double addroot_per;        /* decades of pof per extra root               */
     int precision;             /* AIRG_FP64 or AIRG_MIXED_FP32 (V-cycle)      */
     int gmres_restart;         /* outer FGMRES restart length                 */
+    int outer;                 /* AIRG_OUTER_FGMRES or AIRG_OUTER_RICHARDSON  */
 } airg_options;
 
 typedef struct airg_handle_s airg_handle;

@@ -848,7 +848,32 @@ def fgmres(A, b, precond, x0=None, rtol=1e-10, atol=1e-50, restart=30, maxit=200
     return x, SolveInfo(its, rn / bn if bn > 0 else 0.0, rn <= tol, hist)
 
 
-def solve(Hh, A, b, rtol=1e-10, atol=1e-50, restart=30, maxit=200, x0=None):
+def richardson(A, b, precond, x0=None, rtol=1e-10, atol=1e-50, maxit=200):
+    """Preconditioned Richardson, the outer iteration of Sec. 3: each step
+    adds one V-cycle applied to the current residual, x <- x + M^-1 (b - A x).
+    Same stopping test as fgmres (true residual, unpreconditioned norm)."""
+    n = A.n_rows
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    bn = float(np.linalg.norm(b))
+    tol = max(rtol * bn, atol)
+    r = b - spmv(A, x)
+    rn = float(np.linalg.norm(r))
+    hist = [rn / bn if bn > 0 else 0.0]
+    its = 0
+    while rn > tol and its < maxit:
+        x = x + precond(r)
+        r = b - spmv(A, x)
+        rn = float(np.linalg.norm(r))
+        its += 1
+        hist.append(rn / bn if bn > 0 else 0.0)
+    return x, SolveInfo(its, rn / bn if bn > 0 else 0.0, rn <= tol, hist)
+
+
+def solve(Hh, A, b, rtol=1e-10, atol=1e-50, restart=30, maxit=200, x0=None, outer="fgmres"):
+    if outer == "richardson":
+        return richardson(A, b, lambda v: vcycle(Hh, v), x0=x0, rtol=rtol, atol=atol, maxit=maxit)
+    if outer != "fgmres":
+        raise ValueError(outer)
     return fgmres(A, b, lambda v: vcycle(Hh, v), x0=x0, rtol=rtol, atol=atol,
                   restart=restart, maxit=maxit)
 

@@ -289,18 +289,6 @@ kb_multidot(long long n, int k, int m, const double* __restrict__ V, long long l
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// w[r][q] -= sum_i h[i*k+q] V_i[r][q]
-__global__ void kb_multiaxpy(long long n, int k, int m, const double* __restrict__ V, long long ldv,
-                             const double* __restrict__ h, double* __restrict__ w)
-{
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n * k) return;
-    int q = int(t % k);
-    double s = w[t];
-    for (int i = 0; i < m; ++i) s = fma(-h[i * k + q], V[i * ldv + t], s);
-    w[t] = s;
-}
-
 // w[r][q] -= sum_i h[i*k+q] V_i[r][q], and out[q] = ||w_q||^2 of the result
 __global__ void __launch_bounds__(BT)
 kb_multiaxpy_norm(long long n, int k, int m, const double* __restrict__ V, long long ldv,
@@ -623,12 +611,29 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
     };
     residual();
     int its = 0;
+    if (H.opt.outer == AIRG_OUTER_RICHARDSON) {
+        // lockstep Richardson: x_q += M^-1 r_q for every unconverged q
+        std::vector<double> yq(k);
+        while (its < maxit) {
+            int nact = 0;
+            for (int q = 0; q < k; ++q) {
+                yq[q] = rn[q] > tol[q] ? 1.0 : 0.0;
+                nact += rn[q] > tol[q];
+            }
+            if (!nact) break;
+            bprecond(H, B, B.r.p, B.Zs.p, st);
+            h2d(B.hdev.p, yq.data(), size_t(k), st);
+            LAUNCH(S, PK_KRYLOV, 24 * nk, kb_update<<<g, BT, 0, st>>>(n, k, 1, B.Zs.p, nk, B.hdev.p, B.xp.p));
+            residual();
+            ++its;
+        }
+    }
     std::vector<double> Hm(size_t(m + 1) * m * k), cs(size_t(m) * k), sn(size_t(m) * k),
         gv(size_t(m + 1) * k), Y(size_t(m) * k), inv(k);
     std::vector<int> active(k), jdone(k);
     auto hq = [&](int i, int j, int q) -> double& { return Hm[(size_t(i) * m + j) * k + q]; };
     double* hh = B.hh.p;
-    while (its < maxit) {
+    while (H.opt.outer == AIRG_OUTER_FGMRES && its < maxit) {
         int nact = 0;
         for (int q = 0; q < k; ++q) {
             active[q] = rn[q] > tol[q];

@@ -123,6 +123,7 @@ void check_options(const airg_options& o)
     if (o.ddc_its < 0 || !(o.ddc_fraction >= 0.0 && o.ddc_fraction <= 1.0))
         airg::fail(AIRG_ERR_ARG, "bad DDC options");
     if (o.precision != AIRG_FP64 && o.precision != AIRG_MIXED_FP32) airg::fail(AIRG_ERR_ARG, "bad precision");
+    if (o.outer != AIRG_OUTER_FGMRES && o.outer != AIRG_OUTER_RICHARDSON) airg::fail(AIRG_ERR_ARG, "bad outer");
 }
 
 airg::DevCSR upload_csr(const airg_csr* A, cudaStream_t st)
@@ -169,6 +170,7 @@ namespace airg {
 void set_last_error(const char* msg) { g_last_error = msg; }
 // validated device copy of a caller's CSR (multi.cu)
 DevCSR upload_csr_checked(const airg_csr* A, cudaStream_t st) { return upload_csr(A, st); }
+void check_options_checked(const airg_options& o) { check_options(o); }
 }  // namespace airg
 
 extern "C" {
@@ -196,6 +198,7 @@ airg_status airg_options_default(airg_options* o)
     o->addroot_per = 14.0;
     o->precision = AIRG_FP64;
     o->gmres_restart = 30;
+    o->outer = AIRG_OUTER_FGMRES;
     return AIRG_OK;
 }
 

@@ -22,6 +22,7 @@
 namespace airg {
 void set_last_error(const char* msg);
 DevCSR upload_csr_checked(const airg_csr* A, cudaStream_t st);
+void check_options_checked(const airg_options& o);
 }  // namespace airg
 
 struct airg_batch_s {
@@ -34,11 +35,13 @@ struct airg_batch_s {
     std::vector<airg::DBuf<int>> act;      // per problem: active flag read by the graph
     airg::HBuf<double> hbuf;               // pinned copies of every dv
     std::vector<cudaGraphExec_t> graphs;   // per iteration index j
+    cudaGraphExec_t rich = nullptr;        // one Richardson iteration
     int m = 0;
     ~airg_batch_s()
     {
         for (cudaGraphExec_t g : graphs)
             if (g) cudaGraphExecDestroy(g);
+        if (rich) cudaGraphExecDestroy(rich);
         for (cudaEvent_t e : join) cudaEventDestroy(e);
         if (fork) cudaEventDestroy(fork);
         for (cudaStream_t s : ps) cudaStreamDestroy(s);
@@ -127,6 +130,43 @@ cudaGraphExec_t capture_iteration(airg_batch_s& B, int j)
     return exec;
 }
 
+// graph of one Richardson iteration for all problems: per problem
+//     z = V-cycle(r) -> x += z (if active) -> r = b - A x -> <r, r>
+cudaGraphExec_t capture_richardson(airg_batch_s& B)
+{
+    const int P = int(B.H.size());
+    Off o{B.m};
+    CK(cudaStreamBeginCapture(B.master, cudaStreamCaptureModeThreadLocal));
+    try {
+        CK(cudaEventRecord(B.fork, B.master));
+        for (int p = 0; p < P; ++p) {
+            airg::Hierarchy& H = *B.H[p];
+            airg::SolveData& S = *H.solve;
+            cudaStream_t st = B.ps[p];
+            double* dv = B.dv[p].p;
+            CK(cudaStreamWaitEvent(st, B.fork, 0));
+            airg::mp_vcycle(H, S.r.p, S.Zs.p, st);
+            airg::mp_add_dev(H, S.Zs.p, B.act[p].p, S.xp.p, st);
+            airg::mp_residual(H, S.bp.p, S.xp.p, S.w.p, S.r.p, st);
+            airg::mp_multidot(H, 0, S.V.p, S.r.p, dv + o.rn(), 1, st);
+            CK(cudaEventRecord(B.join[p], st));
+            CK(cudaStreamWaitEvent(B.master, B.join[p], 0));
+        }
+    } catch (...) {
+        cudaGraph_t g0;
+        cudaStreamEndCapture(B.master, &g0);
+        if (g0) cudaGraphDestroy(g0);
+        throw;
+    }
+    cudaGraph_t graph;
+    CK(cudaStreamEndCapture(B.master, &graph));
+    cudaGraphExec_t exec;
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    return exec;
+}
+
 void read_all(airg_batch_s& B, cudaStream_t st)
 {
     Off o{B.m};
@@ -193,7 +233,27 @@ void solve_multi(airg_batch_s& B, const double* const* b, double* const* x, bool
         st[p].tol = std::max(rtol * st[p].bn, atol);
     }
     int its = 0;
-    while (its < maxit) {
+    const bool rich = B.H[0]->opt.outer == AIRG_OUTER_RICHARDSON;
+    while (rich && its < maxit) {
+        // lockstep Richardson; a converged problem keeps its x
+        int nact = 0;
+        for (int p = 0; p < P; ++p) {
+            st[p].active = st[p].rn > st[p].tol;
+            nact += st[p].active;
+            airg::h2d(B.act[p].p, &st[p].active, 1, B.ps[p]);
+        }
+        sync_all(B);
+        if (!nact) break;
+        if (!B.rich) B.rich = capture_richardson(B);
+        CK(cudaGraphLaunch(B.rich, B.master));
+        read_all(B, B.master);
+        ++its;
+        for (int p = 0; p < P; ++p) {
+            if (st[p].active) st[p].its += 1;
+            st[p].rn = std::sqrt(std::max(B.hbuf.p[p * tot + o.rn()], 0.0));
+        }
+    }
+    while (!rich && its < maxit) {
         int nact = 0;
         for (int p = 0; p < P; ++p) {
             PState& s = st[p];
@@ -325,6 +385,7 @@ airg_status airg_setup_batch(int nprob, const airg_csr* As, const airg_options* 
         airg_options o;
         if (opt) o = *opt;
         else airg_options_default(&o);
+        airg::check_options_checked(o);
         cudaStream_t st = (cudaStream_t)stream;
         auto B = std::make_unique<airg_batch_s>();
         for (int p = 0; p < nprob; ++p) {

@@ -622,17 +622,6 @@ __global__ void k_multidot(long long n, int m, const double* __restrict__ V, lon
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// w -= sum_i h_i V_i
-__global__ void k_multiaxpy(long long n, int m, const double* __restrict__ V, long long ldv,
-                            const double* __restrict__ h, double* __restrict__ w)
-{
-    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    double s = w[r];
-    for (int i = 0; i < m; ++i) s = fma(-h[i], V[i * ldv + r], s);
-    w[r] = s;
-}
-
 // w -= sum_i h_i V_i, and *out = ||w||^2 of the result (partial sums per
 // block, fixed-order sum in the last block)
 __global__ void k_multiaxpy_norm(long long n, int m, const double* __restrict__ V, long long ldv,
@@ -693,6 +682,15 @@ __global__ void k_scale_into(long long n, const double* __restrict__ w, double i
 }
 
 // r = b - y
+// x += z, unless *active is 0 (a frozen problem of a batch)
+__global__ void k_add_dev(long long n, const double* __restrict__ z, const int* __restrict__ active,
+                          double* __restrict__ x)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || (active && !*active)) return;
+    x[i] += z[i];
+}
+
 __global__ void k_sub2(long long n, const double* b, const double* y, double* r)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1112,6 +1110,9 @@ void precond(Hierarchy& H, const double* v, double* z, cudaStream_t st)
     S.launches += ge->kernels;
 }
 
+void richardson(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& info,
+                cudaStream_t st);
+
 // FGMRES(m) on the nested system; bp/xp hold b and x in nested order.
 void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& info,
             cudaStream_t st)
@@ -1213,6 +1214,38 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
     info.converged = info.converged && (rn <= tol);
 }
 
+// Preconditioned Richardson (Sec. 3): x <- x + M^-1 r, r = b - A x, until the
+// true residual meets the tolerance.  One V-cycle per iteration.
+void richardson(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& info,
+                cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    long long n = S.n0;
+    int g = grid_for(n, TB);
+    SellView<double> A = view(S.Atop);
+    const long long topB = S.Atop.nnz * 12 + 16 * n;
+    double bn = dev_norm(S, S.bp.p, n, st);
+    double tol = std::max(rtol * bn, atol);
+    auto residual = [&]() {
+        LAUNCH(S, PK_TOPSPMV, topB,
+               WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), bk(KK), 0, st>>>(A, S.xp.p, S.w.p)));
+        LAUNCH(S, PK_KRYLOV, 24 * n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
+        CK_LAUNCH();
+        return dev_norm(S, S.r.p, n, st);
+    };
+    double rn = residual();
+    int its = 0;
+    while (rn > tol && its < maxit) {
+        precond(H, S.r.p, S.Zs.p, st);
+        LAUNCH(S, PK_KRYLOV, 24 * n, k_add_dev<<<g, TB, 0, st>>>(n, S.Zs.p, nullptr, S.xp.p));
+        rn = residual();
+        ++its;
+    }
+    info.iterations = std::max(info.iterations, its);
+    double rel = bn > 0 ? rn / bn : 0.0;
+    info.rel_residual = std::max(info.rel_residual, rel);
+    info.converged = info.converged && (rn <= tol);
+}
 
 // v = w / sqrt(nrm2) when *active and nrm2 > 0, else 0 (device-side scaling,
 // so that it can sit inside a captured graph)
@@ -1282,6 +1315,13 @@ void mp_update(Hierarchy& H, int m, const double* Zs, const double* y, double* x
            k_multiaxpy_plus<<<grid_for(n, TB), TB, 0, st>>>(n, m, Zs, n, y, x));
 }
 
+void mp_add_dev(Hierarchy& H, const double* z, const int* active, double* x, cudaStream_t st)
+{
+    SolveData& S = *H.solve;
+    long long n = S.n0;
+    LAUNCH(S, PK_KRYLOV, 24 * n, k_add_dev<<<grid_for(n, TB), TB, 0, st>>>(n, z, active, x));
+}
+
 void mp_permute(Hierarchy& H, const double* a, double* b, bool to_nested, cudaStream_t st)
 {
     SolveData& S = *H.solve;
@@ -1331,19 +1371,21 @@ void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_de
     }
     int g = grid_for(n, TB);
     const char* nb = getenv("AIRG_NO_BATCH");
+    int nseq = nrhs;   // right-hand sides solved one after the other
     if (nrhs > 1 && !(nb && nb[0] == '1')) {
-        // many right-hand sides: lockstep FGMRES with the batched V-cycle
+        // many right-hand sides: lockstep outer iteration with the batched V-cycle
         for (int q0 = 0; q0 < nrhs; q0 += batch_max_width()) {
             int kq = std::min(batch_max_width(), nrhs - q0);
             solve_batched(H, kq, bdev + size_t(q0) * n, xdev + size_t(q0) * n, rtol, atol, maxit, info, st);
         }
-        nrhs = 0;
+        nseq = 0;
     }
-    for (int q = 0; q < nrhs; ++q) {
+    for (int q = 0; q < nseq; ++q) {
         LAUNCH(S, PK_LAYOUT, 20 * n, k_to_nested<<<g, TB, 0, st>>>(n, S.pos0.p, bdev + size_t(q) * n, S.bp.p));
         LAUNCH(S, PK_LAYOUT, 20 * n, k_to_nested<<<g, TB, 0, st>>>(n, S.pos0.p, xdev + size_t(q) * n, S.xp.p));
         CK_LAUNCH();
-        fgmres(H, rtol, atol, maxit, info, st);
+        if (H.opt.outer == AIRG_OUTER_RICHARDSON) richardson(H, rtol, atol, maxit, info, st);
+        else fgmres(H, rtol, atol, maxit, info, st);
         LAUNCH(S, PK_LAYOUT, 20 * n, k_from_nested<<<g, TB, 0, st>>>(n, S.pos0.p, S.xp.p, xdev + size_t(q) * n));
         CK_LAUNCH();
     }
@@ -1364,7 +1406,7 @@ void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_de
     info.kernel_launches = S.launches - launches0;
     info.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info_out) *info_out = info;
-    if (!info.converged) fail(AIRG_ERR_NOT_CONVERGED, "FGMRES did not reach the tolerance within maxit");
+    if (!info.converged) fail(AIRG_ERR_NOT_CONVERGED, "the outer iteration did not reach the tolerance within maxit");
 }
 
 void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info)

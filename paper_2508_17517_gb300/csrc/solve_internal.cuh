@@ -205,6 +205,7 @@ void mp_scale_dev(Hierarchy& H, const double* w, const double* nrm2, const int* 
 void mp_residual(Hierarchy& H, const double* b, const double* x, double* y, double* r, cudaStream_t st);
 void mp_update(Hierarchy& H, int m, const double* Zs, const double* y, double* x, cudaStream_t st);
 void mp_permute(Hierarchy& H, const double* a, double* b, bool to_nested, cudaStream_t st);
+void mp_add_dev(Hierarchy& H, const double* z, const int* active, double* x, cudaStream_t st);
 
 // batch.cu: k right-hand sides in lockstep (k <= batch_max_width())
 void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol, double atol,

@@ -56,3 +56,32 @@ def test_uneven_batch_matches_oracle(host):
     xs2, infos2 = G.airg_solve_batch(B, bs, rtol=1e-10)
     for x, x2 in zip(xs, xs2):
         assert np.linalg.norm((x - x2).cpu().numpy()) <= 1e-12 * np.linalg.norm(x.cpu().numpy())
+
+
+def test_uneven_batch_richardson():
+    """Lockstep Richardson over separate problems: each problem takes the
+    same number of iterations as the oracle's Richardson on it."""
+    rng = np.random.default_rng(8)
+    shapes = [(64, 40), (111, 97), (45, 140)]
+    thetas = [0.7, 2.2, 5.0]
+    opts = dict(coarse_poly_order=30, trunc_rtol=1e-2)
+    csrs, bs, ref = [], [], []
+    for (nx, ny), th in zip(shapes, thetas):
+        vx, vy = math.cos(th), math.sin(th)
+        pg = G.airg_problem_advection2d(nx, ny, vx, vy)
+        po = O.advection_2d(nx, ny, vx, vy)
+        g = rng.uniform(0.0, 1.0, po.inflow.size)
+        s = rng.standard_normal(nx * ny)
+        bo = O.assemble_rhs(po, g, s)
+        csrs.append((pg["rowptr"], pg["col"], pg["val"]))
+        bs.append(torch.tensor(bo, device="cuda"))
+        Ho = O.setup(po.A, O.Options(**opts))
+        xo, io = O.solve(Ho, po.A, bo, rtol=1e-10, outer="richardson")
+        ref.append((po, bo, xo, io))
+    B = G.airg_setup_batch(csrs, G.airg_options_default(outer=G.AIRG_OUTER_RICHARDSON, **opts))
+    xs, infos = G.airg_solve_batch(B, bs, rtol=1e-10)
+    for x, info, (po, bo, xo, io) in zip(xs, infos, ref):
+        xg = x.cpu().numpy()
+        assert info.converged and abs(info.iterations - io.iterations) <= 1
+        assert np.linalg.norm(bo - O.spmv(po.A, xg)) <= 1e-10 * np.linalg.norm(bo) * (1 + 1e-6)
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-9

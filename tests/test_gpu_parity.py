@@ -30,7 +30,7 @@ def _lib():
 
 
 def _oopts(d):
-    return O.Options(**{k: v for k, v in d.items() if k != "precision"})
+    return O.Options(**{k: v for k, v in d.items() if k not in ("precision", "outer")})
 
 
 def _csr_equal(M, exp, what, exact_values=True):
@@ -237,3 +237,25 @@ def test_bounded_device_wait_reports_timeout():
     assert "gave up" in G.airg_last_error()
     c = Case(workload("grid", (40, 30)))
     _check_solve(c)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_richardson_outer_matches_oracle(prec):
+    """Outer Richardson (Sec. 3): same iteration count as the oracle's
+    Richardson on the same hierarchy, solution within 1e-9 of both the
+    oracle and the sweep."""
+    w = workload("grid", (150, 131))
+    c = Case(w, {"outer": G.AIRG_OUTER_RICHARDSON, "precision": prec})
+    s = w["s"][0]
+    bo = O.assemble_rhs(c.po, w["g"][0], s)
+    bg = G.airg_assemble_rhs_advection2d(c.pg, torch.tensor(w["g"][0], device="cuda"),
+                                         torch.tensor(s, device="cuda"))
+    xo, io = O.solve(c.Ho, c.po.A, bo, rtol=1e-10, outer="richardson")
+    xg, ig = G.airg_solve(c.h, bg, rtol=1e-10)
+    xg = xg.cpu().numpy()
+    assert ig.converged and io.converged
+    assert abs(ig.iterations - io.iterations) <= (0 if prec == 0 else 1)
+    assert np.linalg.norm(bo - O.spmv(c.po.A, xg)) <= 1e-10 * np.linalg.norm(bo) * (1 + 1e-6)
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-9
+    u = O.sweep_solve(c.po.A, bo, O.sweep_order(c.po))
+    assert np.linalg.norm(xg - u) / np.linalg.norm(u) <= 1e-9
