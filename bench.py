@@ -262,6 +262,30 @@ def run_gpu_multi(args):
         dist.destroy_process_group()
 
 
+def roofline_entry(prof, per_level, peak, peak_kind):
+    """Roofline of the dominant kernel: the (kernel kind, level) pair with
+    the largest share of the profiled device time; achieved = its
+    algorithmic bytes / its event time.  Also the per-kind shares, the same
+    figure over all levels of that kind, and the largest (kind, level)
+    entries."""
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    tot = sum(v[0] for v in kinds.values())
+    (dk, dl), (ms, nl, nb) = max(per_level.items(), key=lambda kv: kv[1][0])
+    achieved = nb / (ms / 1e3) / 1e9
+    ak = kinds[dk]
+    top = sorted(per_level.items(), key=lambda kv: -kv[1][0])[:8]
+    return {"bound": "hbm", "kernel": "%s (level %d)" % (dk, dl), "achieved": achieved, "peak": peak,
+            "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "launches": nl, "avg_launch_us": 1e3 * ms / nl, "algorithmic_bytes_per_launch": nb / nl,
+            "share": ms / tot,
+            "kind_all_levels": {"kernel": dk, "achieved": ak[2] / (ak[0] / 1e3) / 1e9,
+                                "frac": ak[2] / (ak[0] / 1e3) / 1e9 / peak, "share": ak[0] / tot},
+            "kernel_share": {k: v[0] / tot for k, v in kinds.items()},
+            "top_launch_groups": [{"kernel": k, "level": l, "share": round(v[0] / tot, 4),
+                                   "gbs": round(v[2] / (v[0] / 1e3) / 1e9, 1),
+                                   "avg_us": round(1e3 * v[0] / v[1], 2)} for (k, l), v in top]}
+
+
 def run_gpu(args):
     import torch
     rank, world, local_rank = dist_env()
@@ -339,17 +363,10 @@ def run_gpu(args):
         x.zero_()
         G.airg_solve(h, b, x, rtol=w["rtol"])
     prof = G.airg_profile_read(h)
+    per_level = G.airg_profile_read_level(h, sinfo["levels"])
     G.airg_profile(h, False)
     peak, peak_kind = measured_peaks()
-    kinds = {k: v for k, v in prof.items() if v[1] > 0}
-    dom = max(kinds, key=lambda k: kinds[k][0])
-    ms, nl, nb = kinds[dom]
-    achieved = nb / (ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "launches": nl, "avg_launch_us": 1e3 * ms / nl,
-                "algorithmic_bytes_per_launch": nb / nl,
-                "kernel_share": {k: v[0] / sum(q[0] for q in kinds.values()) for k, v in kinds.items()}}
+    roofline = roofline_entry(prof, per_level, peak, peak_kind)
     vc_bytes = sinfo["bytes_per_vcycle"]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("c1", "c2"):
@@ -361,7 +378,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if w["opts"].get("precision") == 1 else "f64",
+            "vs_baseline": None, "dtype": "f32/f64" if w["opts"].get("precision") == 1 else "f64",
             "data": "synthetic",
             "config": {"workload": w["desc"], "n": n, "nrhs": k, "rtol": w["rtol"],
                        "parallelism": "replicas" if world > 1 else "single",

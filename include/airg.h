@@ -262,6 +262,15 @@ airg_status airg_profile_read(const airg_handle* h, int kind, double* ms, int64_
                               int64_t* bytes);
 
 /*
+ * The same totals restricted to one level of the hierarchy: level l's
+ * restriction, F-point residual and smoother launches, level = number of
+ * levels - 1 for the coarse Newton steps, 0 for the top-level FGMRES, layout
+ * and conversion kernels.  0 <= level < 65; AIRG_ERR_ARG otherwise.
+ */
+airg_status airg_profile_read_level(const airg_handle* h, int kind, int level, double* ms,
+                                    int64_t* launches, int64_t* bytes);
+
+/*
  * Failure-detection check of the device-side waits: launches one block that
  * waits, through the same bounded wait as the grid barrier of the
  * persistent kernels, for an arrival that never comes.  The wait must give

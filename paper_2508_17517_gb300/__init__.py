@@ -28,7 +28,7 @@ EXPORTS = ["airg_options_default", "airg_problem_advection2d", "airg_assemble_rh
            "airg_setup", "airg_solve", "airg_solve_adjoint", "airg_setup_info",
            "airg_export_matrix", "airg_export_vector", "airg_free", "airg_last_error",
            "airg_dot_exact", "airg_rng_uniform", "airg_host_gmres_coeffs", "airg_host_eigvals",
-           "airg_profile", "airg_profile_read", "airg_dot_exact_noalloc",
+           "airg_profile", "airg_profile_read", "airg_profile_read_level", "airg_dot_exact_noalloc",
            "airg_rhs_adjoint_advection2d", "airg_setup_batch", "airg_solve_batch",
            "airg_batch_free", "airg_check_wait_timeout"]
 PROFILE_KINDS = ["restrict", "f_residual", "f_smoother", "coarse_newton", "top_spmv",
@@ -114,6 +114,8 @@ def lib():
             "airg_solve_batch": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ci, f64, f64, ci,
                                  ctypes.POINTER(airg_solve_info), vp],
             "airg_profile_read": [vp, ci, ctypes.POINTER(f64), ctypes.POINTER(i64),
+                                  ctypes.POINTER(i64)],
+            "airg_profile_read_level": [vp, ci, ci, ctypes.POINTER(f64), ctypes.POINTER(i64),
                                   ctypes.POINTER(i64)],
         }
         for name, args in sig.items():
@@ -359,6 +361,20 @@ def airg_profile_read(handle):
         _check(lib().airg_profile_read(handle.ptr, k, ctypes.byref(ms), ctypes.byref(nl),
                                        ctypes.byref(nb)))
         out[name] = (ms.value, nl.value, nb.value)
+    return out
+
+
+def airg_profile_read_level(handle, levels):
+    """{(kind, level): (ms, launches, algorithmic bytes)} for levels < `levels`,
+    entries with launches only."""
+    out = {}
+    for k, name in enumerate(PROFILE_KINDS):
+        for lev in range(levels):
+            ms, nl, nb = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+            _check(lib().airg_profile_read_level(handle.ptr, k, lev, ctypes.byref(ms), ctypes.byref(nl),
+                                                 ctypes.byref(nb)))
+            if nl.value:
+                out[(name, lev)] = (ms.value, nl.value, nb.value)
     return out
 
 

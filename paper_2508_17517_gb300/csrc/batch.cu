@@ -32,13 +32,18 @@ constexpr int MAXK = 128;        // right-hand sides per batch (KW <= 4)
 
 inline int grid_rows(long long n) { return grid_for(n * 32, BT); }
 
-// acc[j] = (row r of S) x[:, q], q = lane + 32 j
+// acc[j] = (row r of S) x[:, q], q = lane + 32 j: the dense diagonal term
+// (square operators) first, then the stored entries in slice order
 template <class T, int KW>
 __device__ __forceinline__ void brow(const SellView<T>& S, int r, const T* __restrict__ x, int k,
                                      int lane, T (&acc)[KW])
 {
+    const T dg = S.diag ? __ldg(S.diag + r) : T(0);
 #pragma unroll
-    for (int j = 0; j < KW; ++j) acc[j] = T(0);
+    for (int j = 0; j < KW; ++j) {
+        int q = lane + 32 * j;
+        acc[j] = (S.diag && q < k) ? dg * x[size_t(r) * k + q] : T(0);
+    }
     const int s = r >> 5;
     const int b = S.sptr[s] + (r & 31), w = (S.sptr[s + 1] - S.sptr[s]) >> 5;
     for (int e = 0; e < w; ++e) {
@@ -241,40 +246,43 @@ __global__ void kb_from_nested(long long n, int k, const int* pos, const double*
 // ----------------------------------------------------- batched Krylov work --
 constexpr int RG = 608;   // reduction blocks
 
-// out[i*k + q] = sum_r V_i[r][q] * w[r][q] for i < m (m <= MAXB + 1); blocks
-// write partial sums, the last block adds them in a fixed order.
+// out[i*k + q] = sum_r V_i[r][q] * w[r][q] for i < M, and out[M*k + q] =
+// <w_q, w_q> when selfdot, compiled for the exact M; blocks write partial
+// sums, the last block adds them in a fixed order.
+template <int M>
 __global__ void __launch_bounds__(BT)
-kb_multidot(long long n, int k, int m, const double* __restrict__ V, long long ldv,
-            const double* __restrict__ w, double* __restrict__ part, double* __restrict__ out,
-            unsigned* ticket, int selfdot = 0)
+kb_multidot(long long n, int k, const double* __restrict__ V, long long ldv, const double* __restrict__ w,
+            double* __restrict__ part, double* __restrict__ out, unsigned* ticket, int selfdot)
 {
-    // with selfdot the last output row is <w_q, w_q>
-    const int mm = m;
-    m += selfdot ? 1 : 0;
+    const int m = M + (selfdot ? 1 : 0);
     __shared__ double red[BT];
     __shared__ bool last_block;
     const int ng = BT / k;                 // row groups per block
     const int q = threadIdx.x % k, grp = threadIdx.x / k;
-    double acc[MAXB + 1];
+    double acc[M + 1];
 #pragma unroll
-    for (int i = 0; i < MAXB + 1; ++i) acc[i] = 0.0;
+    for (int i = 0; i < M + 1; ++i) acc[i] = 0.0;
     if (grp < ng) {
         for (long long r = (long long)blockIdx.x * ng + grp; r < n; r += (long long)gridDim.x * ng) {
-            double wv = w[r * k + q];
+            const long long t = r * k + q;
+            const double wv = __ldg(w + t);
 #pragma unroll
-            for (int i = 0; i < MAXB + 1; ++i)
-                if (i < m) acc[i] = fma(i < mm ? V[i * ldv + r * k + q] : wv, wv, acc[i]);
+            for (int i = 0; i < M; ++i) acc[i] = fma(__ldg(V + i * ldv + t), wv, acc[i]);
+            acc[M] = fma(wv, wv, acc[M]);
         }
     }
-    for (int i = 0; i < m; ++i) {
-        red[threadIdx.x] = grp < ng ? acc[i] : 0.0;
-        __syncthreads();
-        if (threadIdx.x < k) {
-            double s = 0.0;
-            for (int g = 0; g < ng; ++g) s += red[g * k + threadIdx.x];
-            part[((long long)blockIdx.x * m + i) * k + threadIdx.x] = s;
+#pragma unroll
+    for (int i = 0; i < M + 1; ++i) {
+        if (i < m) {
+            red[threadIdx.x] = grp < ng ? acc[i] : 0.0;
+            __syncthreads();
+            if (threadIdx.x < k) {
+                double s = 0.0;
+                for (int g = 0; g < ng; ++g) s += red[g * k + threadIdx.x];
+                part[((long long)blockIdx.x * m + i) * k + threadIdx.x] = s;
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
     __threadfence();
     if (threadIdx.x == 0) last_block = atomicAdd(ticket, 1u) == gridDim.x - 1;
@@ -289,22 +297,30 @@ kb_multidot(long long n, int k, int m, const double* __restrict__ V, long long l
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// w[r][q] -= sum_i h[i*k+q] V_i[r][q], and out[q] = ||w_q||^2 of the result
+// w[r][q] -= sum_i h[i*k+q] V_i[r][q] (terms in the order i = 0, 1, ...),
+// and out[q] = ||w_q||^2 of the result
+template <int M>
 __global__ void __launch_bounds__(BT)
-kb_multiaxpy_norm(long long n, int k, int m, const double* __restrict__ V, long long ldv,
-                  const double* __restrict__ h, double* __restrict__ w, double* __restrict__ part,
-                  double* __restrict__ out, unsigned* ticket)
+kb_multiaxpy_norm(long long n, int k, const double* __restrict__ V, long long ldv, const double* __restrict__ h,
+                  double* __restrict__ w, double* __restrict__ part, double* __restrict__ out, unsigned* ticket)
 {
     __shared__ double red[BT];
     __shared__ bool last_block;
     const int ng = BT / k;
     const int q = threadIdx.x % k, grp = threadIdx.x / k;
+    double c[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) c[i] = -h[i * k + q];
     double ss = 0.0;
     if (grp < ng) {
         for (long long r = (long long)blockIdx.x * ng + grp; r < n; r += (long long)gridDim.x * ng) {
-            long long t = r * k + q;
+            const long long t = r * k + q;
+            double v[M];
+#pragma unroll
+            for (int i = 0; i < M; ++i) v[i] = __ldg(V + i * ldv + t);
             double s = w[t];
-            for (int i = 0; i < m; ++i) s = fma(-h[i * k + q], V[i * ldv + t], s);
+#pragma unroll
+            for (int i = 0; i < M; ++i) s = fma(c[i], v[i], s);
             w[t] = s;
             ss = fma(s, s, ss);
         }
@@ -329,15 +345,20 @@ kb_multiaxpy_norm(long long n, int k, int m, const double* __restrict__ V, long 
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// x[r][q] += sum_i y[i*k+q] Z_i[r][q]
-__global__ void kb_update(long long n, int k, int m, const double* __restrict__ Zs, long long ldz,
+// x[r][q] += sum_i y[i*k+q] Z_i[r][q] (terms in the order i = 0, 1, ...)
+template <int M>
+__global__ void kb_update(long long n, int k, const double* __restrict__ Zs, long long ldz,
                           const double* __restrict__ y, double* __restrict__ x)
 {
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * k) return;
     int q = int(t % k);
+    double v[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) v[i] = __ldg(Zs + i * ldz + t);
     double s = x[t];
-    for (int i = 0; i < m; ++i) s = fma(y[i * k + q], Zs[i * ldz + t], s);
+#pragma unroll
+    for (int i = 0; i < M; ++i) s = fma(y[i * k + q], v[i], s);
     x[t] = s;
 }
 
@@ -412,8 +433,9 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         const SolveLevel& lv = *S.lv[l];
         const T* src = l == 0 ? v : wk.rwork;
         const Sell<T>& Z = bops<T>(lv).Z;
+        S.cur_level = l;
         if (lv.n_c)
-            LAUNCH(S, PK_RESTRICT, Z.nnz * (VB + 4) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
+            LAUNCH(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
                    WITH_KW(k, kb_restrict<T, KW><<<grid_rows(lv.n_c), BT, 0, st>>>(
                                   view(Z), src + size_t(lv.off) * k, src + size_t(lv.off + lv.n_f) * k,
                                   wk.rwork + size_t(lv.off + lv.n_f) * k, k)));
@@ -424,7 +446,8 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         const Sell<T>& A = bcoarse<T>(S);
         SellView<T> Av = view(A);
         const int nco = S.n_coarse;
-        const long long nB = (long long)nco * VB * kk, mB = A.nnz * (VB + 4);
+        const long long nB = (long long)nco * VB * kk, mB = mat_bytes(A);
+        S.cur_level = L;
         const T* rin = rc;
         T* bufs[2] = {wk.cr0, wk.cr1};
         int nb = 0;
@@ -461,7 +484,8 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         const int nf = lv.n_f;
         const int p = int(lv.alpha.size()) - 1;
         const long long fB = (long long)nf * VB * kk;
-        LAUNCH(S, PK_FRESID, o.M.nnz * (VB + 4) + (long long)lv.n_c * VB * kk + 3 * fB,
+        S.cur_level = l;
+        LAUNCH(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB * kk + 3 * fB,
                WITH_KW(k, kb_fresid<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
                                                                         T(lv.alpha[p]), k)));
         if (p == 0) {
@@ -470,7 +494,7 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
                                                                                 T(lv.alpha[0]), k));
             continue;
         }
-        const long long hB = o.Aff.nnz * (VB + 4) + 3 * fB;
+        const long long hB = mat_bytes(o.Aff) + 3 * fB;
         T* win = wk.wa;
         T* wout = wk.wb;
         for (int kq = p - 1; kq >= 1; --kq) {
@@ -483,6 +507,7 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
                WITH_KW(k, kb_horner_last<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.Aff), wk.t, win, ec,
                                                                              lv.W.p, ef, T(lv.alpha[0]), k)));
     }
+    S.cur_level = 0;
     CK_LAUNCH();
 }
 
@@ -577,7 +602,7 @@ void bnorms(SolveData& S, BatchData& B, const double* x, std::vector<double>& ou
     long long n = S.n0;
     int k = B.k;
     LAUNCH(S, PK_KRYLOV, 8 * B.nk,
-           kb_multidot<<<RG, BT, 0, st>>>(n, k, 1, x, B.nk, x, B.part.p, B.hdev.p, B.ticket.p));
+           kb_multidot<1><<<RG, BT, 0, st>>>(n, k, x, B.nk, x, B.part.p, B.hdev.p, B.ticket.p, 0));
     out.resize(k);
     d2h(out.data(), B.hdev.p, size_t(k), st);
     for (double& v : out) v = std::sqrt(std::max(v, 0.0));
@@ -623,7 +648,7 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
             if (!nact) break;
             bprecond(H, B, B.r.p, B.Zs.p, st);
             h2d(B.hdev.p, yq.data(), size_t(k), st);
-            LAUNCH(S, PK_KRYLOV, 24 * nk, kb_update<<<g, BT, 0, st>>>(n, k, 1, B.Zs.p, nk, B.hdev.p, B.xp.p));
+            LAUNCH(S, PK_KRYLOV, 24 * nk, kb_update<1><<<g, BT, 0, st>>>(n, k, B.Zs.p, nk, B.hdev.p, B.xp.p));
             residual();
             ++its;
         }
@@ -658,10 +683,11 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
             double* h2 = B.hdev.p + size_t(MAXB + 2) * k;
             double* hnp = B.hdev.p + size_t(2) * (MAXB + 2) * k;
             LAUNCH(S, PK_KRYLOV, 8LL * nk * (j + 2),
-                   kb_multidot<<<RG, BT, 0, st>>>(n, k, j + 1, B.V.p, nk, B.w.p, B.part.p, h1, B.ticket.p, 1));
+                   WITH_M(j + 1, kb_multidot<MM><<<RG, BT, 0, st>>>(n, k, B.V.p, nk, B.w.p, B.part.p, h1,
+                                                                     B.ticket.p, 1)));
             LAUNCH(S, PK_KRYLOV, 8LL * nk * (j + 3),
-                   kb_multiaxpy_norm<<<RG, BT, 0, st>>>(n, k, j + 1, B.V.p, nk, h1, B.w.p, B.part.p, hnp,
-                                                        B.ticket.p));
+                   WITH_M(j + 1, kb_multiaxpy_norm<MM><<<RG, BT, 0, st>>>(n, k, B.V.p, nk, h1, B.w.p, B.part.p,
+                                                                           hnp, B.ticket.p)));
             CK(cudaMemcpyAsync(hh, B.hdev.p, sizeof(double) * 3 * (MAXB + 2) * k, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             bool again = false;
@@ -671,10 +697,11 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
                 for (int i = 0; i <= j; ++i) hq(i, j, q) = hh[size_t(i) * k + q];
             if (again) {
                 LAUNCH(S, PK_KRYLOV, 8LL * nk * (j + 2),
-                       kb_multidot<<<RG, BT, 0, st>>>(n, k, j + 1, B.V.p, nk, B.w.p, B.part.p, h2, B.ticket.p));
+                       WITH_M(j + 1, kb_multidot<MM><<<RG, BT, 0, st>>>(n, k, B.V.p, nk, B.w.p, B.part.p, h2,
+                                                                         B.ticket.p, 0)));
                 LAUNCH(S, PK_KRYLOV, 8LL * nk * (j + 3),
-                       kb_multiaxpy_norm<<<RG, BT, 0, st>>>(n, k, j + 1, B.V.p, nk, h2, B.w.p, B.part.p, hnp,
-                                                            B.ticket.p));
+                       WITH_M(j + 1, kb_multiaxpy_norm<MM><<<RG, BT, 0, st>>>(n, k, B.V.p, nk, h2, B.w.p, B.part.p,
+                                                                               hnp, B.ticket.p)));
                 CK(cudaMemcpyAsync(hh, B.hdev.p, sizeof(double) * 3 * (MAXB + 2) * k, cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
                 for (int q = 0; q < k; ++q)
@@ -728,7 +755,7 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
         if (jmax) {
             h2d(B.hdev.p, Y.data(), size_t(jmax) * k, st);
             LAUNCH(S, PK_KRYLOV, 8LL * nk * (jmax + 2),
-                   kb_update<<<g, BT, 0, st>>>(n, k, jmax, B.Zs.p, nk, B.hdev.p, B.xp.p));
+                   WITH_M(jmax, kb_update<MM><<<g, BT, 0, st>>>(n, k, B.Zs.p, nk, B.hdev.p, B.xp.p)));
         }
         residual();
     }

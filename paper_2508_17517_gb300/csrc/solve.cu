@@ -38,7 +38,10 @@ Hierarchy::~Hierarchy() = default;
 namespace {
 
 // ----------------------------------------------------------- SELL build --
-__global__ void k_sell_width(int nrows, int nslices, const int* rp, const int* src_row, int* width)
+// Slice widths (x 32).  With `split`, the entry of row r whose (mapped)
+// column is r goes to the dense diagonal and is not counted.
+__global__ void k_sell_width(int nrows, int nslices, const int* rp, const int* ci, const int* src_row,
+                             const int* cmap, int split, int* width)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslices) return;
@@ -47,14 +50,19 @@ __global__ void k_sell_width(int nrows, int nslices, const int* rp, const int* s
         int r = s * 32 + l;
         if (r >= nrows) break;
         int i = src_row ? src_row[r] : r;
-        w = max(w, rp[i + 1] - rp[i]);
+        int len = rp[i + 1] - rp[i];
+        if (split)
+            for (int j = rp[i]; j < rp[i + 1]; ++j)
+                if ((cmap ? cmap[ci[j]] : ci[j]) == r) --len;
+        w = max(w, len);
     }
     width[s] = w * 32;
 }
 
 template <class T>
 __global__ void k_sell_fill(int nrows, int nslices, const int* rp, const int* ci, const double* v,
-                            const int* src_row, const int* cmap, const int* sptr, int* col, T* val)
+                            const int* src_row, const int* cmap, const int* sptr, int* col, T* val,
+                            T* diag, unsigned long long* ndiag)
 {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nslices * 32) return;
@@ -66,42 +74,60 @@ __global__ void k_sell_fill(int nrows, int nslices, const int* rp, const int* ci
         return;
     }
     int i = src_row ? src_row[r] : r;
-    int b = rp[i], len = rp[i + 1] - rp[i];
-    int lastc = 0;
-    for (int k = 0; k < w; ++k) {
-        if (k < len) {
-            int c = ci[b + k];
-            lastc = cmap ? cmap[c] : c;
-            col[base + k * 32] = lastc;
-            val[base + k * 32] = T(v[b + k]);
-        } else {
-            col[base + k * 32] = lastc;
-            val[base + k * 32] = T(0);
+    int k = 0, lastc = 0;
+    bool found = false;
+    for (int j = rp[i]; j < rp[i + 1]; ++j) {
+        int c = cmap ? cmap[ci[j]] : ci[j];
+        if (diag && c == r) {
+            diag[r] = T(v[j]);
+            found = true;
+            continue;
         }
+        col[base + k * 32] = c;
+        val[base + k * 32] = T(v[j]);
+        lastc = c;
+        ++k;
+    }
+    for (; k < w; ++k) {
+        col[base + k * 32] = lastc;
+        val[base + k * 32] = T(0);
+    }
+    if (diag) {
+        if (found) atomicAdd(ndiag, 1ULL);
+        else diag[r] = T(0);
     }
 }
 
 template <class T>
 void build_sell(const DevCSR& A, const int* src_row, const int* cmap, int n_cols, Sell<T>& S,
-                cudaStream_t st)
+                bool split_diag, cudaStream_t st)
 {
     S.n_rows = A.n_rows;
     S.n_cols = n_cols;
     S.nnz = A.nnz;
     S.k = choose_parts(A.nnz, A.n_rows);
+    S.r = 1;
     S.n_slices = (A.n_rows + 31) / 32;
     S.sptr.alloc(size_t(S.n_slices) + 1);
     if (S.n_slices)
-        k_sell_width<<<grid_for(S.n_slices, TB), TB, 0, st>>>(A.n_rows, S.n_slices, A.rp.p, src_row,
-                                                                S.sptr.p);
+        k_sell_width<<<grid_for(S.n_slices, TB), TB, 0, st>>>(A.n_rows, S.n_slices, A.rp.p, A.ci.p, src_row,
+                                                                cmap, split_diag ? 1 : 0, S.sptr.p);
     CK_LAUNCH();
     S.padded = exclusive_scan(S.sptr.p, S.sptr.p, S.n_slices, st);
     S.col.alloc(std::max<long long>(S.padded, 1));
     S.val.alloc(std::max<long long>(S.padded, 1));
+    DBuf<unsigned long long> cnt(1);
+    CK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), st));
+    if (split_diag) S.diag.alloc(std::max(A.n_rows, 1));
     if (S.n_slices)
         k_sell_fill<T><<<grid_for((long long)S.n_slices * 32, TB), TB, 0, st>>>(
-            A.n_rows, S.n_slices, A.rp.p, A.ci.p, A.v.p, src_row, cmap, S.sptr.p, S.col.p, S.val.p);
+            A.n_rows, S.n_slices, A.rp.p, A.ci.p, A.v.p, src_row, cmap, S.sptr.p, S.col.p, S.val.p,
+            split_diag ? S.diag.p : nullptr, cnt.p);
     CK_LAUNCH();
+    unsigned long long nd = 0;
+    d2h(&nd, cnt.p, 1, st);
+    S.ndiag = (long long)nd;
+    if (!split_diag) S.diag = DBuf<T>();
 }
 
 template <class T>
@@ -124,14 +150,20 @@ void copy_sell_f32(const Sell<double>& S, Sell<float>& out, cudaStream_t st)
     out.n_cols = S.n_cols;
     out.n_slices = S.n_slices;
     out.k = S.k;
+    out.r = S.r;
     out.nnz = S.nnz;
     out.padded = S.padded;
+    out.ndiag = S.ndiag;
     out.sptr.alloc(S.sptr.n);
     out.col.alloc(S.col.n);
     out.val.alloc(S.val.n);
     CK(cudaMemcpyAsync(out.sptr.p, S.sptr.p, S.sptr.bytes(), cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(out.col.p, S.col.p, S.col.bytes(), cudaMemcpyDeviceToDevice, st));
     if (S.val.n) k_d2f<<<grid_for(S.val.n, TB), TB, 0, st>>>((long long)S.val.n, S.val.p, out.val.p);
+    if (S.diag.n) {
+        out.diag.alloc(S.diag.n);
+        k_d2f<<<grid_for(S.diag.n, TB), TB, 0, st>>>((long long)S.diag.n, S.diag.p, out.diag.p);
+    }
     CK_LAUNCH();
 }
 
@@ -200,19 +232,10 @@ __device__ __forceinline__ T strided_dot(const int* __restrict__ col, const T* _
     return (a0 + a1) + (a2 + a3);
 }
 
-template <class T>
-__device__ __forceinline__ T sell_row(const SellView<T>& S, int r, const T* __restrict__ x)
-{
-    int s = r >> 5;
-    int base = S.sptr[s] + (r & 31);
-    int w = (S.sptr[s + 1] - S.sptr[s]) >> 5;
-    return strided_dot(S.col, S.val, x, base, base + 32 * w, 32);
-}
-
 // Row (32*slice + lane) of S times x, computed by the P warps of the block
 // that share the slice (part = this warp's index among them).  Every thread
 // of the block must call it (it synchronises the block when P > 1).  The
-// sum is valid in the part-0 warp.
+// sum is valid in the part-0 warp, which also adds the dense diagonal.
 template <class T, int P>
 __device__ __forceinline__ T row_dot(const SellView<T>& S, int slice, int lane, int part,
                                      const T* __restrict__ x)
@@ -233,75 +256,169 @@ __device__ __forceinline__ T row_dot(const SellView<T>& S, int slice, int lane, 
         }
         __syncthreads();
     }
+    const int r = slice * 32 + lane;
+    if (S.diag && part == 0 && r < S.n_rows) acc = fma(S.diag[r], x[r], acc);
     return acc;
 }
 
-// Thread -> (slice, part, row) for blocks of wpb_for(P) warps:
-// wpb_for(P)/P slices per block.
-#define ROW_IDS(P, NROWS)                                                   \
-    const int lane = threadIdx.x & 31;                                      \
-    const int part = (threadIdx.x >> 5) % (P);                              \
-    const int slice = blockIdx.x * (wpb_for(P) / (P)) + (threadIdx.x >> 5) / (P); \
-    const int r = slice * 32 + lane;                                        \
-    const bool lead = part == 0 && r < (NROWS)
-#define ROW_DOT(P, S, X) row_dot<T, P>((S), slice, lane, part, (X))
-
-// y = S x
-template <class T, int K>
-__global__ void k_spmv(SellView<T> S, const T* __restrict__ x, T* __restrict__ y)
+// Rows 32 s + lane, s = s0 .. s0+R-1, of S times x for one warp (short rows,
+// one warp per slice).  Per row the arithmetic is fixed: start from
+// diag_r x_r (or 0), then add the row's stored entries in slice order with
+// one fused multiply-add each.  It does not depend on R or on which path
+// below runs, so the slices-per-warp choice never changes a result bit.
+// When every slice is at most 4 wide, all loads of the R rows are issued
+// (predicated) before their gathers, and all gathers before the sums.
+template <class T, int R>
+__device__ __forceinline__ void dot_slices(const SellView<T>& S, const T* __restrict__ x, int s0, int lane,
+                                           T (&acc)[R])
 {
-    ROW_IDS(K, S.n_rows);
-    T d = ROW_DOT(K, S, x);
-    if (lead) y[r] = d;
-}
-
-// restriction (Eq. 3): dst_c[k] = src_c[k] + (Z src_f)[k]
-template <class T, int K>
-__global__ void k_restrict(SellView<T> Z, const T* __restrict__ src_f, const T* __restrict__ src_c,
-                           T* __restrict__ dst_c)
-{
-    ROW_IDS(K, Z.n_rows);
-    T d = ROW_DOT(K, Z, src_f);
-    if (lead) dst_c[r] = src_c[r] + d;
-}
-
-// F-point residual (Eq. 6): t = r_f - M e_c, and the first Horner term w = a_p t
-template <class T, int K>
-__global__ void k_fresid(SellView<T> M, const T* __restrict__ rf, const T* __restrict__ ec,
-                         T* __restrict__ t, T* __restrict__ w, T ap)
-{
-    ROW_IDS(K, M.n_rows);
-    T d = ROW_DOT(K, M, ec);
-    if (lead) {
-        T tt = rf[r] - d;
-        t[r] = tt;
-        w[r] = ap * tt;
+    int b[R], w[R];
+    bool fits = true;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int s = s0 + q;
+        const bool ok = s < S.n_slices;
+        const int p0 = ok ? __ldg(S.sptr + s) : 0, p1 = ok ? __ldg(S.sptr + s + 1) : 0;
+        b[q] = p0 + lane;
+        w[q] = (p1 - p0) >> 5;
+        fits = fits && w[q] <= 4;
+        const int r = s * 32 + lane;
+        acc[q] = (S.diag && r < S.n_rows) ? __ldg(S.diag + r) * x[r] : T(0);
+    }
+    if (fits) {
+        int c[R][4];
+        T v[R][4], xv[R][4];
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = u < w[q];
+                c[q][u] = ok ? __ldg(S.col + b[q] + 32 * u) : 0;
+                v[q][u] = ok ? __ldg(S.val + b[q] + 32 * u) : T(0);
+            }
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[q][u] = u < w[q] ? x[c[q][u]] : T(0);
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (u < w[q]) acc[q] = fma(v[q][u], xv[q][u], acc[q]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            for (int u0 = 0; u0 < w[q]; u0 += 4) {
+                int c[4];
+                T v[4], xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool ok = u0 + u < w[q];
+                    c[u] = ok ? __ldg(S.col + b[q] + 32 * (u0 + u)) : 0;
+                    v[u] = ok ? __ldg(S.val + b[q] + 32 * (u0 + u)) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xv[u] = u0 + u < w[q] ? x[c[u]] : T(0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (u0 + u < w[q]) acc[q] = fma(v[u], xv[u], acc[q]);
+            }
+        }
     }
 }
 
+// Applies epi(r, (S x)_r, pre(r)) to every row r of S.  pre(r) loads the
+// row's other operands; it runs before the row's gathers so that its loads
+// overlap them.  K = warps per slice (K > 1 for long rows, R must then be
+// 1); R = slices per warp for K = 1.
+template <class T, int K, int R, class Pre, class Epi>
+__device__ __forceinline__ void for_rows(const SellView<T>& S, const T* __restrict__ x, const Pre& pre,
+                                         const Epi& epi)
+{
+    using PV = decltype(pre(0));
+    const int lane = threadIdx.x & 31;
+    if constexpr (K == 1) {
+        const int s0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * R;
+        PV pv[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int r = (s0 + q) * 32 + lane;
+            pv[q] = r < S.n_rows ? pre(r) : PV{};
+        }
+        T acc[R];
+        dot_slices<T, R>(S, x, s0, lane, acc);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int r = (s0 + q) * 32 + lane;
+            if (r < S.n_rows) epi(r, acc[q], pv[q]);
+        }
+    } else {
+        static_assert(R == 1, "several slices per warp only with one warp per slice");
+        const int part = (threadIdx.x >> 5) % K;
+        const int slice = blockIdx.x * (wpb_for(K) / K) + (threadIdx.x >> 5) / K;
+        const int r = slice * 32 + lane;
+        const bool lead = part == 0 && r < S.n_rows;
+        PV pv = lead ? pre(r) : PV{};
+        T d = row_dot<T, K>(S, slice, lane, part, x);
+        if (lead) epi(r, d, pv);
+    }
+}
+
+template <class T>
+struct Pair {
+    T a, b;
+};
+
+// y = S x
+template <class T, int K, int R>
+__global__ void k_spmv(SellView<T> S, const T* __restrict__ x, T* __restrict__ y)
+{
+    for_rows<T, K, R>(S, x, [](int) { return 0; }, [&](int r, T d, int) { y[r] = d; });
+}
+
+// restriction (Eq. 3): dst_c[k] = src_c[k] + (Z src_f)[k]
+template <class T, int K, int R>
+__global__ void k_restrict(SellView<T> Z, const T* __restrict__ src_f, const T* __restrict__ src_c,
+                           T* __restrict__ dst_c)
+{
+    for_rows<T, K, R>(Z, src_f, [&](int r) { return src_c[r]; },
+                      [&](int r, T d, T sc) { dst_c[r] = sc + d; });
+}
+
+// F-point residual (Eq. 6): t = r_f - M e_c, and the first Horner term w = a_p t
+template <class T, int K, int R>
+__global__ void k_fresid(SellView<T> M, const T* __restrict__ rf, const T* __restrict__ ec,
+                         T* __restrict__ t, T* __restrict__ w, T ap)
+{
+    for_rows<T, K, R>(M, ec, [&](int r) { return rf[r]; },
+                      [&](int r, T d, T f) {
+                          T tt = f - d;
+                          t[r] = tt;
+                          w[r] = ap * tt;
+                      });
+}
+
 // Horner term: wout = a_k t + A_ff win
-template <class T, int K>
+template <class T, int K, int R>
 __global__ void k_horner(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
                          T* __restrict__ wout, T ak)
 {
-    ROW_IDS(K, A.n_rows);
-    T d = ROW_DOT(K, A, win);
-    if (lead) wout[r] = fma(ak, t[r], d);
+    for_rows<T, K, R>(A, win, [&](int r) { return t[r]; },
+                      [&](int r, T d, T tr) { wout[r] = fma(ak, tr, d); });
 }
 
 // last Horner term and the correction: e_f = W e_c + (a_0 t + A_ff win)
-template <class T, int K>
+template <class T, int K, int R>
 __global__ void k_horner_last(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
                               const T* __restrict__ ec, const int* __restrict__ W,
                               T* __restrict__ ef, T a0)
 {
-    ROW_IDS(K, A.n_rows);
-    T d = ROW_DOT(K, A, win);
-    if (lead) {
-        int wc = W[r];
-        T p = wc >= 0 ? ec[wc] : T(0);
-        ef[r] = p + fma(a0, t[r], d);
-    }
+    for_rows<T, K, R>(A, win,
+                      [&](int r) {
+                          int wc = W[r];
+                          return Pair<T>{t[r], wc >= 0 ? ec[wc] : T(0)};
+                      },
+                      [&](int r, T d, Pair<T> q) { ef[r] = q.b + fma(a0, q.a, d); });
 }
 
 // degree-0 smoother: e_f = W e_c + a_0 t
@@ -316,41 +433,45 @@ __global__ void k_smooth0(int n, const T* __restrict__ t, const T* __restrict__ 
 }
 
 // Newton steps of the coarse polynomial (Sec. 2.3)
-template <class T, int K>
+// real root, not the last: x += r / theta, r' = r - A r / theta
+template <class T, int K, int R>
 __global__ void k_newton_real(SellView<T> A, const T* __restrict__ rin, T* __restrict__ rout,
-                              T* __restrict__ x, T inv_theta, int first, int last)
+                              T* __restrict__ x, T inv_theta, int first)
 {
-    ROW_IDS(K, A.n_rows);
-    T d = last ? T(0) : ROW_DOT(K, A, rin);
-    if (lead) {
-        T ri = rin[r];
-        T xv = first ? T(0) : x[r];
-        x[r] = fma(ri, inv_theta, xv);
-        if (!last) rout[r] = ri - d * inv_theta;
-    }
+    for_rows<T, K, R>(A, rin, [&](int r) { return Pair<T>{rin[r], first ? T(0) : x[r]}; },
+                      [&](int r, T d, Pair<T> q) {
+                          x[r] = fma(q.a, inv_theta, q.b);
+                          rout[r] = q.a - d * inv_theta;
+                      });
 }
 
-template <class T, int K>
+// last real root: x += r / theta (no residual update, no SpMV)
+template <class T>
+__global__ void k_newton_last(int n, const T* __restrict__ rin, T* __restrict__ x, T inv_theta, int first)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    x[r] = fma(rin[r], inv_theta, first ? T(0) : x[r]);
+}
+
+template <class T, int K, int R>
 __global__ void k_newton_pair1(SellView<T> A, const T* __restrict__ rin, T* __restrict__ t,
                                T* __restrict__ x, T two_a, T inv_mod2, int first)
 {
-    ROW_IDS(K, A.n_rows);
-    T d = ROW_DOT(K, A, rin);
-    if (lead) {
-        T tt = two_a * rin[r] - d;
-        t[r] = tt;
-        T xv = first ? T(0) : x[r];
-        x[r] = fma(tt, inv_mod2, xv);
-    }
+    for_rows<T, K, R>(A, rin, [&](int r) { return Pair<T>{rin[r], first ? T(0) : x[r]}; },
+                      [&](int r, T d, Pair<T> q) {
+                          T tt = two_a * q.a - d;
+                          t[r] = tt;
+                          x[r] = fma(tt, inv_mod2, q.b);
+                      });
 }
 
-template <class T, int K>
+template <class T, int K, int R>
 __global__ void k_newton_pair2(SellView<T> A, const T* __restrict__ rin, const T* __restrict__ t,
                                T* __restrict__ rout, T inv_mod2)
 {
-    ROW_IDS(K, A.n_rows);
-    T d = ROW_DOT(K, A, t);
-    if (lead) rout[r] = rin[r] - d * inv_mod2;
+    for_rows<T, K, R>(A, t, [&](int r) { return rin[r]; },
+                      [&](int r, T d, T ri) { rout[r] = ri - d * inv_mod2; });
 }
 
 // blocks of wpb_for(P) warps for n rows with P warps per 32-row slice
@@ -368,6 +489,36 @@ inline int bk(int P) { return 32 * wpb_for(P); }
             case 16: { constexpr int KK = 16; __VA_ARGS__; } break;             \
             case 32: { constexpr int KK = 32; __VA_ARGS__; } break;             \
             default: fail(AIRG_ERR_STATE, "bad warps-per-slice");               \
+        }                                                                       \
+    } while (0)
+
+// Grid and block of the row kernels for operator S: K = S.k warps per slice,
+// or (K = 1) S.r slices per warp.
+template <class T>
+inline int grid_rows(const Sell<T>& S)
+{
+    if (S.k > 1) return gk(S.n_rows, S.k);
+    long long warps = (S.n_slices + S.r - 1) / S.r;
+    return grid_for(warps, wpb_for(1));
+}
+template <class T>
+inline int block_rows(const Sell<T>& S) { return bk(S.k); }
+
+// Runs the statement with compile-time KK (warps per slice) and RR (slices
+// per warp) of operator S.
+#define WITH_KR(S, ...)                                                         \
+    do {                                                                        \
+        if ((S).k == 1) {                                                       \
+            constexpr int KK = 1;                                               \
+            switch ((S).r) {                                                    \
+                case 1: { constexpr int RR = 1; __VA_ARGS__; } break;           \
+                case 2: { constexpr int RR = 2; __VA_ARGS__; } break;           \
+                case 4: { constexpr int RR = 4; __VA_ARGS__; } break;           \
+                default: fail(AIRG_ERR_STATE, "bad slices-per-warp");           \
+            }                                                                   \
+        } else {                                                                \
+            constexpr int RR = 1;                                               \
+            WITH_K((S).k, __VA_ARGS__);                                         \
         }                                                                       \
     } while (0)
 
@@ -506,6 +657,8 @@ __device__ __forceinline__ T row_dot_rt(const SellView<T>& S, int slice, int lan
             for (int q = 1; q < P; ++q) acc += red[warp + q][lane];
         __syncthreads();
     }
+    const int r = slice * 32 + lane;
+    if (S.diag && part == 0 && r < S.n_rows) acc = fma(S.diag[r], x[r], acc);
     return acc;
 }
 
@@ -574,31 +727,44 @@ k_smooth_persistent(SellView<T> M, int pm, SellView<T> A, int pa, const T* __res
 constexpr int RB = 256;          // reduction block
 constexpr int RGRID = 1216;      // partial sums per reduction (8 x SMs)
 
-// out[i] = <w, V_i> for i < m, and out[m] = <w, w> when selfdot.  Blocks
-// write partial sums; the last block to finish (atomic ticket) adds them in
-// a fixed order and resets the ticket.
-__global__ void k_multidot(long long n, int m, const double* __restrict__ V, long long ldv,
-                           const double* __restrict__ w, double* __restrict__ part,
-                           double* __restrict__ out, unsigned* ticket, int selfdot = 0)
+// Basis vectors are handled in chunks of at most MCH per kernel, each
+// kernel compiled for its exact chunk size (a predicated maximum-size chunk
+// costs as much as a full one).
+constexpr int MCH = 16;
+
+// out[i] = <w, V_i> for i < M, and out[M] = <w, w> when selfdot, as one
+// pass over the rows.  Blocks write partial sums; the last block to finish
+// (atomic ticket) adds them in a fixed order and resets the ticket.
+template <int M>
+__global__ void __launch_bounds__(RB)
+k_multidot(long long n, const double* __restrict__ V, long long ldv, const double* __restrict__ w,
+           double* __restrict__ part, double* __restrict__ out, unsigned* ticket, int selfdot)
 {
-    __shared__ double red[RB / 32][32];
+    constexpr int MO = M + 1;
+    __shared__ double red[RB / 32][MO];
     __shared__ bool last_block;
-    const int mm = m;
-    m += selfdot ? 1 : 0;
-    for (int i = 0; i < m; ++i) {
-        const double* vi = i < mm ? V + i * ldv : w;
-        double s = 0.0;
-        for (long long r = (long long)blockIdx.x * RB + threadIdx.x; r < n; r += (long long)gridDim.x * RB)
-            s = fma(vi[r], w[r], s);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][i & 31] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int q = 0; q < RB / 32; ++q) t += red[q][i & 31];
-            part[(long long)blockIdx.x * m + i] = t;
-        }
-        __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int m = M + (selfdot ? 1 : 0);
+    double acc[MO];
+#pragma unroll
+    for (int u = 0; u < MO; ++u) acc[u] = 0.0;
+    for (long long r = (long long)blockIdx.x * RB + threadIdx.x; r < n; r += (long long)gridDim.x * RB) {
+        const double wv = __ldg(w + r);
+#pragma unroll
+        for (int u = 0; u < M; ++u) acc[u] = fma(__ldg(V + u * ldv + r), wv, acc[u]);
+        acc[M] = fma(wv, wv, acc[M]);
+    }
+#pragma unroll
+    for (int u = 0; u < MO; ++u) {
+        double v = acc[u];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][u] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        double t = 0.0;
+        for (int q = 0; q < RB / 32; ++q) t += red[q][threadIdx.x];
+        part[(long long)blockIdx.x * m + threadIdx.x] = t;
     }
     __threadfence();
     if (threadIdx.x == 0) last_block = atomicAdd(ticket, 1u) == gridDim.x - 1;
@@ -606,37 +772,41 @@ __global__ void k_multidot(long long n, int m, const double* __restrict__ V, lon
     if (!last_block) return;
     __threadfence();
     const int nb = gridDim.x;
-    for (int i = 0; i < m; ++i) {
-        double s = 0.0;
-        for (int q = threadIdx.x; q < nb; q += RB) s += part[(long long)q * m + i];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][0] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int q = 0; q < RB / 32; ++q) t += red[q][0];
-            out[i] = t;
-        }
-        __syncthreads();
+    for (int i = warp; i < m; i += RB / 32) {
+        double v = 0.0;
+        for (int q = lane; q < nb; q += 32) v += part[(long long)q * m + i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) out[i] = v;
     }
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// w -= sum_i h_i V_i, and *out = ||w||^2 of the result (partial sums per
-// block, fixed-order sum in the last block)
-__global__ void k_multiaxpy_norm(long long n, int m, const double* __restrict__ V, long long ldv,
-                                 const double* __restrict__ h, double* __restrict__ w,
-                                 double* __restrict__ part, double* __restrict__ out, unsigned* ticket)
+// w += sum_i c_i V_i with c_i = -h_i (neg) or h_i, the terms added in the
+// order i = 0, 1, ...; with norm, *out = ||w||^2 of the result (partial sums
+// per block, fixed-order sum in the last block).
+template <int M>
+__global__ void __launch_bounds__(RB)
+k_multiaxpy(long long n, const double* __restrict__ V, long long ldv, const double* __restrict__ h, int neg,
+            double* __restrict__ w, int norm, double* __restrict__ part, double* __restrict__ out,
+            unsigned* ticket)
 {
     __shared__ double red[RB / 32];
     __shared__ bool last_block;
+    double c[M];
+#pragma unroll
+    for (int u = 0; u < M; ++u) c[u] = neg ? -h[u] : h[u];
     double ss = 0.0;
     for (long long r = (long long)blockIdx.x * RB + threadIdx.x; r < n; r += (long long)gridDim.x * RB) {
+        double v[M];
+#pragma unroll
+        for (int u = 0; u < M; ++u) v[u] = __ldg(V + u * ldv + r);
         double s = w[r];
-        for (int i = 0; i < m; ++i) s = fma(-h[i], V[i * ldv + r], s);
+#pragma unroll
+        for (int u = 0; u < M; ++u) s = fma(c[u], v[u], s);
         w[r] = s;
         ss = fma(s, s, ss);
     }
+    if (!norm) return;
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
     __syncthreads();
@@ -664,16 +834,6 @@ __global__ void k_multiaxpy_norm(long long n, int m, const double* __restrict__ 
     }
 }
 
-// x += sum_i y_i Z_i   (y on device)
-__global__ void k_multiaxpy_plus(long long n, int m, const double* __restrict__ Zs, long long ldz,
-                                 const double* __restrict__ y, double* __restrict__ x)
-{
-    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    double s = x[r];
-    for (int i = 0; i < m; ++i) s = fma(y[i], Zs[i * ldz + r], s);
-    x[r] = s;
-}
 
 __global__ void k_scale_into(long long n, const double* __restrict__ w, double inv, double* __restrict__ v)
 {
@@ -755,11 +915,12 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         const SolveLevel& lv = *S.lv[l];
         const T* src = l == 0 ? v : wk.rwork;
         const Sell<T>& Z = ops<T>(lv).Z;
+        S.cur_level = l;
         if (lv.n_c)
-            LAUNCH(S, PK_RESTRICT, Z.nnz * (VB + 4) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB,
-                   WITH_K(Z.k, k_restrict<T, KK><<<gk(lv.n_c, KK), bk(KK), 0, st>>>(
-                                   view(Z), src + lv.off, src + lv.off + lv.n_f,
-                                   wk.rwork + lv.off + lv.n_f)));
+            LAUNCH(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB,
+                   WITH_KR(Z, k_restrict<T, KK, RR><<<grid_rows(Z), block_rows(Z), 0, st>>>(
+                                  view(Z), src + lv.off, src + lv.off + lv.n_f,
+                                  wk.rwork + lv.off + lv.n_f)));
     }
     // coarse-grid polynomial
     {
@@ -772,7 +933,8 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         T* bufs[2] = {wk.cr0, wk.cr1};
         int nb = 0;
         size_t nr = S.roots.size();
-        const long long nB = (long long)S.n_coarse * VB, mB = A.nnz * (VB + 4);
+        const long long nB = (long long)S.n_coarse * VB, mB = mat_bytes(A);
+        S.cur_level = L;
         const int pidx = sizeof(T) == 8 ? 0 : 1;
         if (S.newton_grid[pidx] > 0 && nr > 0) {
             // all Newton steps in one cooperative launch
@@ -803,18 +965,22 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
             const Root& q = S.roots[i];
             T* rout = bufs[nb];
             if (q.im == 0.0) {
-                LAUNCH(S, PK_NEWTON, (last ? 0 : mB + 2 * nB) + (i == 0 ? 2 : 3) * nB,
-                       WITH_K(A.k, k_newton_real<T, KK><<<gk(nco, KK), bk(KK), 0, st>>>(
-                                       Av, rin, rout, x, T(1.0 / q.re), i == 0, last)));
+                if (last)
+                    LAUNCH(S, PK_NEWTON, (i == 0 ? 2 : 3) * nB,
+                           k_newton_last<T><<<grid_for(nco, TB), TB, 0, st>>>(nco, rin, x, T(1.0 / q.re), i == 0));
+                else
+                    LAUNCH(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB,
+                           WITH_KR(A, k_newton_real<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
+                                          Av, rin, rout, x, T(1.0 / q.re), i == 0)));
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
                 LAUNCH(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB,
-                       WITH_K(A.k, k_newton_pair1<T, KK><<<gk(nco, KK), bk(KK), 0, st>>>(
-                                       Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
+                       WITH_KR(A, k_newton_pair1<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
+                                      Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
                 if (!last)
                     LAUNCH(S, PK_NEWTON, mB + 3 * nB,
-                           WITH_K(A.k, k_newton_pair2<T, KK><<<gk(nco, KK), bk(KK), 0, st>>>(
-                                           Av, rin, wk.ct, rout, T(1.0 / mod2))));
+                           WITH_KR(A, k_newton_pair2<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
+                                          Av, rin, wk.ct, rout, T(1.0 / mod2))));
             }
             if (!last) { rin = rout; nb ^= 1; }
         }
@@ -834,6 +1000,7 @@ coarse_done:
         int p = int(lv.alpha.size()) - 1;
         const long long fB = (long long)nf * VB;
         const int pidx2 = sizeof(T) == 8 ? 0 : 1;
+        S.cur_level = l;
         if (S.smooth_grid[pidx2] > 0 && p < 32) {
             Coefs al{};
             for (int q = 0; q <= p; ++q) al.a[q] = lv.alpha[q];
@@ -848,8 +1015,8 @@ coarse_done:
             attr[0].val.cooperative = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            long long bytes = o.M.nnz * (VB + 4) + (long long)lv.n_c * VB + 3 * fB +
-                              p * (o.Aff.nnz * (VB + 4) + 3 * fB) + fB + 4LL * nf;
+            long long bytes = mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB +
+                              p * (mat_bytes(o.Aff) + 3 * fB) + fB + 4LL * nf;
             SellView<T> Mv = view(o.M), Av2 = view(o.Aff);
             LAUNCH(S, PK_HORNER, bytes,
                    CK(cudaLaunchKernelEx(&cfg, k_smooth_persistent<T>, Mv, o.M.k, Av2, o.Aff.k, rf, ec,
@@ -857,34 +1024,93 @@ coarse_done:
                                          S.bar.p + 1, (int*)(S.bar.p + 2))));
             continue;
         }
-        LAUNCH(S, PK_FRESID, o.M.nnz * (VB + 4) + (long long)lv.n_c * VB + 3 * fB,
-               WITH_K(o.M.k, k_fresid<T, KK><<<gk(nf, KK), bk(KK), 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
-                                                                       T(lv.alpha[p]))));
+        LAUNCH(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB,
+               WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M), block_rows(o.M), 0, st>>>(
+                                view(o.M), rf, ec, wk.t, wk.wa, T(lv.alpha[p]))));
         if (p == 0) {
             LAUNCH(S, PK_HORNER, 3 * fB + 4LL * nf,
                    k_smooth0<T><<<g, TB, 0, st>>>(nf, wk.t, ec, lv.W.p, ef, T(lv.alpha[0])));
             continue;
         }
-        const long long hB = o.Aff.nnz * (VB + 4) + 3 * fB;
+        const long long hB = mat_bytes(o.Aff) + 3 * fB;
         T* win = wk.wa;
         T* wout = wk.wb;
         for (int k = p - 1; k >= 1; --k) {
             LAUNCH(S, PK_HORNER, hB,
-                   WITH_K(o.Aff.k, k_horner<T, KK><<<gk(nf, KK), bk(KK), 0, st>>>(view(o.Aff), wk.t, win, wout,
-                                                                             T(lv.alpha[k]))));
+                   WITH_KR(o.Aff, k_horner<T, KK, RR><<<grid_rows(o.Aff), block_rows(o.Aff), 0, st>>>(
+                                      view(o.Aff), wk.t, win, wout, T(lv.alpha[k]))));
             std::swap(win, wout);
         }
         LAUNCH(S, PK_HORNER, hB + fB + 4LL * nf,
-               WITH_K(o.Aff.k, k_horner_last<T, KK><<<gk(nf, KK), bk(KK), 0, st>>>(view(o.Aff), wk.t, win, ec,
-                                                                                lv.W.p, ef, T(lv.alpha[0]))));
+               WITH_KR(o.Aff, k_horner_last<T, KK, RR><<<grid_rows(o.Aff), block_rows(o.Aff), 0, st>>>(
+                                  view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0]))));
     }
+    S.cur_level = 0;
     CK_LAUNCH();
 }
 
-long long sell_bytes(long long nnz, int n_rows, int vbytes)
+long long sell_bytes(const Sell<double>& S, int vbytes)
 {
-    // values + column indices + one read of the input gathered + one write
-    return nnz * (vbytes + 4) + 2LL * n_rows * vbytes;
+    // values + column indices (none for a dense diagonal) + one read of the
+    // gathered input + one write
+    return (S.nnz - S.ndiag) * (vbytes + 4) + S.ndiag * vbytes + 2LL * S.n_rows * vbytes;
+}
+
+// Slices per warp of every short-row operator, picked by timing y = S x for
+// r = 1, 2, 4 (the per-row arithmetic does not depend on r).  forced > 0
+// (AIRG_ROWS_PER_WARP) skips the timing.
+template <class T>
+void tune_rows(Sell<T>& A, const T* x, T* y, int forced, cudaStream_t st)
+{
+    if (A.k != 1 || A.n_rows == 0) return;
+    if (forced) {
+        A.r = forced;
+        return;
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 0.f;
+    int best_r = 1;
+    for (int r : {1, 2, 4}) {
+        A.r = r;
+        SellView<T> v = view(A);
+        WITH_KR(A, k_spmv<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(v, x, y));
+        CK_LAUNCH();
+        CK(cudaEventRecord(e0, st));
+        for (int rep = 0; rep < 3; ++rep)
+            WITH_KR(A, k_spmv<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(v, x, y));
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (r == 1 || ms < best) {
+            best = ms;
+            best_r = r;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    A.r = best_r;
+}
+
+template <class T>
+void tune_all(SolveData& S, cudaStream_t st)
+{
+    const char* e = getenv("AIRG_ROWS_PER_WARP");
+    int forced = e ? atoi(e) : 0;
+    if (forced != 1 && forced != 2 && forced != 4) forced = 0;
+    size_t n = std::max(S.n0, 1);
+    DBuf<T> x(n), y(n);
+    CK(cudaMemsetAsync(x.p, 0, x.bytes(), st));
+    for (auto& lp : S.lv) {
+        SolveLevelT<T>& o = const_cast<SolveLevelT<T>&>(ops<T>(*lp));
+        tune_rows(o.Aff, x.p, y.p, forced, st);
+        tune_rows(o.M, x.p, y.p, forced, st);
+        tune_rows(o.Z, x.p, y.p, forced, st);
+    }
+    tune_rows(const_cast<Sell<T>&>(coarse_op<T>(S)), x.p, y.p, forced, st);
+    CK(cudaStreamSynchronize(st));
 }
 
 }  // namespace
@@ -925,9 +1151,9 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         DBuf<int> rel(std::max(lv.n_c, 1)), inv(std::max(lv.n_c, 1));
         if (lv.n_c)
             k_rel<<<grid_for(lv.n_c, TB), TB, 0, st>>>(lv.n_c, pos[l + 1].p, off[l + 1], rel.p, inv.p);
-        build_sell<double>(lv.A_ff, nullptr, nullptr, lv.n_f, sl->d.Aff, st);
-        build_sell<double>(lv.M, nullptr, rel.p, lv.n_c, sl->d.M, st);
-        build_sell<double>(lv.Z, inv.p, nullptr, lv.n_f, sl->d.Z, st);
+        build_sell<double>(lv.A_ff, nullptr, nullptr, lv.n_f, sl->d.Aff, true, st);
+        build_sell<double>(lv.M, nullptr, rel.p, lv.n_c, sl->d.M, false, st);
+        build_sell<double>(lv.Z, inv.p, nullptr, lv.n_f, sl->d.Z, false, st);
         sl->W.alloc(std::max(lv.n_f, 1));
         if (lv.n_f) k_map_w<<<grid_for(lv.n_f, TB), TB, 0, st>>>(lv.n_f, lv.W.p, rel.p, sl->W.p);
         CK_LAUNCH();
@@ -938,13 +1164,13 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         }
         int vb = H.opt.precision == AIRG_MIXED_FP32 ? 4 : 8;
         int p = int(lv.alpha.size()) - 1;
-        bytes += sell_bytes(lv.Z.nnz, lv.n_c, vb) + sell_bytes(lv.M.nnz, lv.n_f, vb) + 4LL * lv.n_f +
-                 p * sell_bytes(lv.A_ff.nnz, lv.n_f, vb) + 2LL * lv.n_f * vb;
+        bytes += sell_bytes(sl->d.Z, vb) + sell_bytes(sl->d.M, vb) + 4LL * lv.n_f +
+                 p * sell_bytes(sl->d.Aff, vb) + 2LL * lv.n_f * vb;
         S->max_nf = std::max(S->max_nf, lv.n_f);
         CK(cudaStreamSynchronize(st));
         S->lv.push_back(std::move(sl));
     }
-    build_sell<double>(H.coarse.A, nullptr, nullptr, S->n_coarse, S->Ac, st);
+    build_sell<double>(H.coarse.A, nullptr, nullptr, S->n_coarse, S->Ac, true, st);
     if (H.opt.precision == AIRG_MIXED_FP32) copy_sell_f32(S->Ac, S->Ac32, st);
     S->roots = H.coarse.roots;
     {
@@ -984,7 +1210,7 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
             bool last = i + 1 == S->roots.size();
             nsp += S->roots[i].im == 0.0 ? (last ? 0 : 1) : (last ? 1 : 2);
         }
-        bytes += nsp * sell_bytes(H.coarse.A.nnz, S->n_coarse, vb);
+        bytes += nsp * sell_bytes(S->Ac, vb);
     }
     S->bytes_vcycle = bytes;
     // top operator in the nested order: row pos0[i] <- natural row i
@@ -995,7 +1221,19 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         DBuf<int> dummy(std::max(S->n0, 1));
         if (S->n0) k_rel<<<grid_for(S->n0, TB), TB, 0, st>>>(S->n0, S->pos0.p, 0, dummy.p, inv0.p);
         CK_LAUNCH();
-        build_sell<double>(A0, inv0.p, S->pos0.p, S->n0, S->Atop, st);
+        build_sell<double>(A0, inv0.p, S->pos0.p, S->n0, S->Atop, true, st);
+        CK(cudaStreamSynchronize(st));
+    }
+    // slices per warp of the short-row operators, by timing
+    if (H.opt.precision == AIRG_MIXED_FP32) tune_all<float>(*S, st);
+    else tune_all<double>(*S, st);
+    {
+        const char* e = getenv("AIRG_ROWS_PER_WARP");
+        int forced = e ? atoi(e) : 0;
+        if (forced != 1 && forced != 2 && forced != 4) forced = 0;
+        DBuf<double> x(std::max(S->n0, 1)), y(std::max(S->n0, 1));
+        CK(cudaMemsetAsync(x.p, 0, x.bytes(), st));
+        tune_rows(S->Atop, x.p, y.p, forced, st);
         CK(cudaStreamSynchronize(st));
     }
     // work vectors
@@ -1025,10 +1263,42 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
 
 namespace {
 
+// out[i] = <w, V_i> for i < m, out[m] = <w, w> when selfdot (chunks of MCH)
+void launch_multidot(SolveData& S, long long n, int m, const double* V, long long ldv, const double* w,
+                     double* out, int selfdot, cudaStream_t st)
+{
+    if (m == 0) {
+        if (selfdot)
+            LAUNCH(S, PK_KRYLOV, 8 * n,
+                   k_multidot<0><<<RGRID, RB, 0, st>>>(n, V, ldv, w, S.part.p, out, S.ticket.p, 1));
+        return;
+    }
+    for (int c0 = 0; c0 < m; c0 += MCH) {
+        const int mc = std::min(MCH, m - c0);
+        const int self = selfdot && c0 + mc == m;
+        LAUNCH(S, PK_KRYLOV, 8LL * n * (mc + 1),
+               WITH_M(mc, k_multidot<MM><<<RGRID, RB, 0, st>>>(n, V + c0 * ldv, ldv, w, S.part.p, out + c0,
+                                                                S.ticket.p, self)));
+    }
+}
+
+// w += sum_i (neg ? -h_i : h_i) V_i (chunks of MCH); nrm2 (if not null)
+// receives ||w||^2 of the result
+void launch_multiaxpy(SolveData& S, long long n, int m, const double* V, long long ldv, const double* h,
+                      int neg, double* w, double* nrm2, cudaStream_t st)
+{
+    for (int c0 = 0; c0 < m; c0 += MCH) {
+        const int mc = std::min(MCH, m - c0);
+        const int norm = nrm2 && c0 + mc == m;
+        LAUNCH(S, PK_KRYLOV, 8LL * n * (mc + 2),
+               WITH_M(mc, k_multiaxpy<MM><<<RGRID, RB, 0, st>>>(n, V + c0 * ldv, ldv, h + c0, neg, w, norm,
+                                                                 S.part.p, nrm2, S.ticket.p)));
+    }
+}
+
 double dev_norm(SolveData& S, const double* x, long long n, cudaStream_t st)
 {
-    LAUNCH(S, PK_KRYLOV, 8 * n,
-           k_multidot<<<RGRID, RB, 0, st>>>(n, 1, x, n, x, S.part.p, S.hdev.p, S.ticket.p));
+    launch_multidot(S, n, 0, nullptr, n, x, S.hdev.p, 1, st);
     CK_LAUNCH();
     double v = read1(S.hdev.p, st);
     return std::sqrt(v);
@@ -1122,13 +1392,13 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
     int m = S.restart;
     int g = grid_for(n, TB);
     SellView<double> A = view(S.Atop);
-    const long long topB = S.Atop.nnz * 12 + 16 * n;
+    const long long topB = mat_bytes(S.Atop) + 16 * n;
     double bn = dev_norm(S, S.bp.p, n, st);
     double tol = std::max(rtol * bn, atol);
     int its = 0;
     auto residual = [&]() {
         LAUNCH(S, PK_TOPSPMV, topB,
-               WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), bk(KK), 0, st>>>(A, S.xp.p, S.w.p)));
+               WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop), block_rows(S.Atop), 0, st>>>(A, S.xp.p, S.w.p)));
         LAUNCH(S, PK_KRYLOV, 24 * n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
         CK_LAUNCH();
         return dev_norm(S, S.r.p, n, st);
@@ -1146,18 +1416,15 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             double* zj = S.Zs.p + size_t(j) * n;
             precond(H, vj, zj, st);
             LAUNCH(S, PK_TOPSPMV, topB,
-                   WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), bk(KK), 0, st>>>(A, zj, S.w.p)));
+                   WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop), block_rows(S.Atop), 0, st>>>(A, zj, S.w.p)));
             // classical Gram-Schmidt; a second pass only when the first
             // one cancelled more than half of ||w||^2 ("twice is enough",
             // Daniel, Gragg, Kaufman & Stewart 1976): ||w'|| < ||w|| / sqrt(2)
             double* h1 = S.hdev.p;
             double* h2 = S.hdev.p + (m + 2);
             double* nrm = S.hdev.p + 2 * (m + 2);
-            LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 2),
-                   k_multidot<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, S.w.p, S.part.p, h1, S.ticket.p, 1));
-            LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 3),
-                   k_multiaxpy_norm<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, h1, S.w.p, S.part.p, nrm,
-                                                          S.ticket.p));
+            launch_multidot(S, n, j + 1, S.V.p, n, S.w.p, h1, 1, st);
+            launch_multiaxpy(S, n, j + 1, S.V.p, n, h1, 1, S.w.p, nrm, st);
             CK_LAUNCH();
             CK(cudaMemcpyAsync(hh, S.hdev.p, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -1165,11 +1432,8 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             for (int i = 0; i <= j; ++i) Hm[size_t(i) * m + j] = hh[i];
             double hsq = w1;
             if (w1 < 0.5 * ww) {
-                LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 2),
-                       k_multidot<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, S.w.p, S.part.p, h2, S.ticket.p));
-                LAUNCH(S, PK_KRYLOV, 8LL * n * (j + 3),
-                       k_multiaxpy_norm<<<RGRID, RB, 0, st>>>(n, j + 1, S.V.p, n, h2, S.w.p, S.part.p, nrm,
-                                                              S.ticket.p));
+                launch_multidot(S, n, j + 1, S.V.p, n, S.w.p, h2, 0, st);
+                launch_multiaxpy(S, n, j + 1, S.V.p, n, h2, 1, S.w.p, nrm, st);
                 CK_LAUNCH();
                 CK(cudaMemcpyAsync(hh, S.hdev.p, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
@@ -1203,8 +1467,7 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             y[j] = s / Hm[size_t(j) * m + j];
         }
         h2d(S.hdev.p, y.data(), jdone, st);
-        LAUNCH(S, PK_KRYLOV, 8LL * n * (jdone + 2),
-               k_multiaxpy_plus<<<g, TB, 0, st>>>(n, jdone, S.Zs.p, n, S.hdev.p, S.xp.p));
+        launch_multiaxpy(S, n, jdone, S.Zs.p, n, S.hdev.p, 0, S.xp.p, nullptr, st);
         CK_LAUNCH();
         rn = residual();
     }
@@ -1223,12 +1486,12 @@ void richardson(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_in
     long long n = S.n0;
     int g = grid_for(n, TB);
     SellView<double> A = view(S.Atop);
-    const long long topB = S.Atop.nnz * 12 + 16 * n;
+    const long long topB = mat_bytes(S.Atop) + 16 * n;
     double bn = dev_norm(S, S.bp.p, n, st);
     double tol = std::max(rtol * bn, atol);
     auto residual = [&]() {
         LAUNCH(S, PK_TOPSPMV, topB,
-               WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), bk(KK), 0, st>>>(A, S.xp.p, S.w.p)));
+               WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop), block_rows(S.Atop), 0, st>>>(A, S.xp.p, S.w.p)));
         LAUNCH(S, PK_KRYLOV, 24 * n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
         CK_LAUNCH();
         return dev_norm(S, S.r.p, n, st);
@@ -1269,26 +1532,22 @@ void mp_top_spmv(Hierarchy& H, const double* x, double* y, cudaStream_t st)
     SolveData& S = *H.solve;
     long long n = S.n0;
     SellView<double> A = view(S.Atop);
-    LAUNCH(S, PK_TOPSPMV, S.Atop.nnz * 12 + 16 * n,
-           WITH_K(S.Atop.k, k_spmv<double, KK><<<gk(n, KK), bk(KK), 0, st>>>(A, x, y)));
+    LAUNCH(S, PK_TOPSPMV, mat_bytes(S.Atop) + 16 * n,
+           WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop), block_rows(S.Atop), 0, st>>>(A, x, y)));
 }
 
 void mp_multidot(Hierarchy& H, int m, const double* V, const double* w, double* out, int selfdot,
                  cudaStream_t st)
 {
     SolveData& S = *H.solve;
-    long long n = S.n0;
-    LAUNCH(S, PK_KRYLOV, 8LL * n * (m + 1),
-           k_multidot<<<RGRID, RB, 0, st>>>(n, m, V, n, w, S.part.p, out, S.ticket.p, selfdot));
+    launch_multidot(S, S.n0, m, V, S.n0, w, out, selfdot, st);
 }
 
 void mp_multiaxpy_norm(Hierarchy& H, int m, const double* V, const double* h, double* w, double* out,
                        cudaStream_t st)
 {
     SolveData& S = *H.solve;
-    long long n = S.n0;
-    LAUNCH(S, PK_KRYLOV, 8LL * n * (m + 2),
-           k_multiaxpy_norm<<<RGRID, RB, 0, st>>>(n, m, V, n, h, w, S.part.p, out, S.ticket.p));
+    launch_multiaxpy(S, S.n0, m, V, S.n0, h, 1, w, out, st);
 }
 
 void mp_scale_dev(Hierarchy& H, const double* w, const double* nrm2, const int* active, double* v,
@@ -1310,9 +1569,7 @@ void mp_residual(Hierarchy& H, const double* b, const double* x, double* y, doub
 void mp_update(Hierarchy& H, int m, const double* Zs, const double* y, double* x, cudaStream_t st)
 {
     SolveData& S = *H.solve;
-    long long n = S.n0;
-    LAUNCH(S, PK_KRYLOV, 8LL * n * (m + 2),
-           k_multiaxpy_plus<<<grid_for(n, TB), TB, 0, st>>>(n, m, Zs, n, y, x));
+    launch_multiaxpy(S, S.n0, m, Zs, S.n0, y, 0, x, nullptr, st);
 }
 
 void mp_add_dev(Hierarchy& H, const double* z, const int* active, double* x, cudaStream_t st)
@@ -1456,16 +1713,31 @@ void set_profiling(Hierarchy& H, bool on)
     S.prof = on;
     S.recs.clear();
     S.evnext = 0;
-    for (int k = 0; k < PROF_KINDS; ++k) { S.kind_ms[k] = 0; S.kind_launches[k] = 0; S.kind_bytes[k] = 0; }
+    for (int k = 0; k < PROF_KINDS; ++k) {
+        S.kind_ms[k] = 0;
+        S.kind_launches[k] = 0;
+        S.kind_bytes[k] = 0;
+        for (int l = 0; l < SolveData::PROF_LEVELS; ++l) {
+            S.lev_ms[k][l] = 0;
+            S.lev_launches[k][l] = 0;
+            S.lev_bytes[k][l] = 0;
+        }
+    }
 }
 
-bool read_profile(const Hierarchy& H, int kind, double* ms, long long* launches, long long* bytes)
+bool read_profile(const Hierarchy& H, int kind, int level, double* ms, long long* launches, long long* bytes)
 {
-    if (kind < 0 || kind >= PROF_KINDS) return false;
+    if (kind < 0 || kind >= PROF_KINDS || level < -1 || level >= SolveData::PROF_LEVELS) return false;
     const SolveData& S = *H.solve;
-    *ms = S.kind_ms[kind];
-    *launches = S.kind_launches[kind];
-    *bytes = S.kind_bytes[kind];
+    if (level < 0) {
+        *ms = S.kind_ms[kind];
+        *launches = S.kind_launches[kind];
+        *bytes = S.kind_bytes[kind];
+    } else {
+        *ms = S.lev_ms[kind][level];
+        *launches = S.lev_launches[kind][level];
+        *bytes = S.lev_bytes[kind][level];
+    }
     return true;
 }
 

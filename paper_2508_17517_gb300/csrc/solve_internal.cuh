@@ -29,14 +29,22 @@ enum { PK_RESTRICT = 0, PK_FRESID = 1, PK_HORNER = 2, PK_NEWTON = 3, PK_TOPSPMV 
 // having similar stencils -- gather nearby entries of x.  k = number of
 // warps sharing a slice: for long rows the entries of a slice are split
 // among k warps of a block (entry indices interleaved) whose partial sums
-// meet in shared memory.
+// meet in shared memory.  For short rows (k = 1) a warp instead handles r
+// consecutive slices (r = 1, 2 or 4, picked per operator by timing in the
+// setup) so that each lane keeps r rows' loads in flight.
+//
+// Square operators keep their diagonal as a dense vector `diag` (read and
+// multiplied with coalesced loads, no column index) and only the
+// off-diagonal entries in the slices; ndiag counts the diagonal entries
+// split out this way (0 when there is no split).
 template <class T>
 struct Sell {
-    int n_rows = 0, n_cols = 0, n_slices = 0, k = 1;
-    long long nnz = 0, padded = 0;
+    int n_rows = 0, n_cols = 0, n_slices = 0, k = 1, r = 1;
+    long long nnz = 0, padded = 0, ndiag = 0;
     DBuf<int> sptr;
     DBuf<int> col;
     DBuf<T> val;
+    DBuf<T> diag;
 };
 
 template <class T>
@@ -45,10 +53,22 @@ struct SellView {
     const int* __restrict__ sptr;
     const int* __restrict__ col;
     const T* __restrict__ val;
+    const T* __restrict__ diag;   // nullptr: no diagonal split
 };
 
 template <class T>
-SellView<T> view(const Sell<T>& s) { return SellView<T>{s.n_rows, s.n_slices, s.sptr.p, s.col.p, s.val.p}; }
+SellView<T> view(const Sell<T>& s)
+{
+    return SellView<T>{s.n_rows, s.n_slices, s.sptr.p, s.col.p, s.val.p, s.ndiag ? s.diag.p : nullptr};
+}
+
+// algorithmic bytes of the stored entries: value + 4-byte column index per
+// entry, value only for a diagonal held densely
+template <class T>
+long long mat_bytes(const Sell<T>& s)
+{
+    return (s.nnz - s.ndiag) * (long long)(sizeof(T) + 4) + s.ndiag * (long long)sizeof(T);
+}
 
 // Warps per slice from the mean row length: the smallest power of two that
 // leaves at most `per_lane` entries per lane (default 12), capped at
@@ -113,13 +133,17 @@ struct SolveData {
     // launch count and optional per-kind CUDA-event timing of the solve kernels
     long long launches = 0;
     bool prof = false;
-    struct Rec { int kind; cudaEvent_t a, b; long long bytes; };
+    struct Rec { int kind, level; cudaEvent_t a, b; long long bytes; };
+    int cur_level = 0;           // level of the kernels being launched (coarsest = nlev)
     std::vector<cudaEvent_t> evpool;
     size_t evnext = 0;
     std::vector<Rec> recs;
     std::vector<cudaGraphExec_t> prof_execs;   // profiled V-cycle graphs awaiting collect()
+    static constexpr int PROF_LEVELS = 65;
     double kind_ms[PROF_KINDS] = {};
     long long kind_launches[PROF_KINDS] = {}, kind_bytes[PROF_KINDS] = {};
+    double lev_ms[PROF_KINDS][PROF_LEVELS] = {};
+    long long lev_launches[PROF_KINDS][PROF_LEVELS] = {}, lev_bytes[PROF_KINDS][PROF_LEVELS] = {};
     cudaEvent_t next_event()
     {
         if (evnext == evpool.size()) {
@@ -148,7 +172,8 @@ struct SolveData {
         if (!prof) return;
         cudaEvent_t b = next_event();
         record(b, st);
-        recs.push_back(Rec{kind, a, b, bytes});
+        int lvl = cur_level < 0 ? 0 : (cur_level >= PROF_LEVELS ? PROF_LEVELS - 1 : cur_level);
+        recs.push_back(Rec{kind, lvl, a, b, bytes});
     }
     // after the stream has been synchronised
     void collect()
@@ -159,6 +184,9 @@ struct SolveData {
             kind_ms[r.kind] += ms;
             kind_launches[r.kind] += 1;
             kind_bytes[r.kind] += r.bytes;
+            lev_ms[r.kind][r.level] += ms;
+            lev_launches[r.kind][r.level] += 1;
+            lev_bytes[r.kind][r.level] += r.bytes;
         }
         recs.clear();
         evnext = 0;
@@ -181,6 +209,30 @@ struct SolveData {
         if (sst) cudaStreamDestroy(sst);
     }
 };
+
+// Runs the statement with the compile-time constant MM = mv (1..16).
+#define WITH_M(mv, ...)                                                         \
+    do {                                                                        \
+        switch (mv) {                                                           \
+            case 1: { constexpr int MM = 1; __VA_ARGS__; } break;               \
+            case 2: { constexpr int MM = 2; __VA_ARGS__; } break;               \
+            case 3: { constexpr int MM = 3; __VA_ARGS__; } break;               \
+            case 4: { constexpr int MM = 4; __VA_ARGS__; } break;               \
+            case 5: { constexpr int MM = 5; __VA_ARGS__; } break;               \
+            case 6: { constexpr int MM = 6; __VA_ARGS__; } break;               \
+            case 7: { constexpr int MM = 7; __VA_ARGS__; } break;               \
+            case 8: { constexpr int MM = 8; __VA_ARGS__; } break;               \
+            case 9: { constexpr int MM = 9; __VA_ARGS__; } break;               \
+            case 10: { constexpr int MM = 10; __VA_ARGS__; } break;             \
+            case 11: { constexpr int MM = 11; __VA_ARGS__; } break;             \
+            case 12: { constexpr int MM = 12; __VA_ARGS__; } break;             \
+            case 13: { constexpr int MM = 13; __VA_ARGS__; } break;             \
+            case 14: { constexpr int MM = 14; __VA_ARGS__; } break;             \
+            case 15: { constexpr int MM = 15; __VA_ARGS__; } break;             \
+            case 16: { constexpr int MM = 16; __VA_ARGS__; } break;             \
+            default: fail(AIRG_ERR_STATE, "bad basis chunk");                   \
+        }                                                                       \
+    } while (0)
 
 // Launch through the counter / profiler: LAUNCH(S, kind, bytes, kernel<<<...>>>(...))
 #define LAUNCH(S, KIND, BYTES, ...)                  \

@@ -259,3 +259,24 @@ def test_richardson_outer_matches_oracle(prec):
     assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-9
     u = O.sweep_solve(c.po.A, bo, O.sweep_order(c.po))
     assert np.linalg.norm(xg - u) / np.linalg.norm(u) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_slices_per_warp_never_changes_a_bit(prec, monkeypatch):
+    """The setup's timing-based choice of slices per warp (1, 2 or 4) only
+    changes how rows are mapped to warps: forcing each choice gives the
+    same solution bit for bit."""
+    w = workload("grid", (300, 257))
+    vx, vy = velocity(w["theta"])
+    pg = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
+    b = G.airg_assemble_rhs_advection2d(pg, torch.tensor(w["g"][0], device="cuda"),
+                                        torch.tensor(w["s"][0], device="cuda"))
+    xs = []
+    for r in ["1", "2", "4"]:
+        monkeypatch.setenv("AIRG_ROWS_PER_WARP", r)
+        h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"],
+                         G.airg_options_default(precision=prec, **w["opts"]))
+        x, info = G.airg_solve(h, b, rtol=1e-10)
+        assert info.converged
+        xs.append(x.cpu().numpy())
+    assert np.array_equal(xs[0], xs[1]) and np.array_equal(xs[0], xs[2])
