@@ -262,28 +262,54 @@ def run_gpu_multi(args):
         dist.destroy_process_group()
 
 
-def roofline_entry(prof, per_level, peak, peak_kind):
+# Arithmetic peaks from unit counts and the nominal 2070 MHz SM clock of the
+# GB300 (152 SMs): 2 FP64 FMA per clock per SM (1.26 TFLOP/s; an FMA-chain
+# probe measured 1.20), 128 FP32 FMA per clock per SM (80.5 TFLOP/s).
+SM_COUNT, SM_GHZ = 152, 2.07
+ALU_PEAK_TFLOPS = {"f64": 2 * 2 * SM_COUNT * SM_GHZ / 1e3, "f32": 2 * 128 * SM_COUNT * SM_GHZ / 1e3}
+VCYCLE_KINDS = ("restrict", "f_residual", "f_smoother", "coarse_newton")
+
+
+def roofline_entry(prof, per_level, peak, peak_kind, vcycle_dtype="f64"):
     """Roofline of the dominant kernel: the (kernel kind, level) pair with
-    the largest share of the profiled device time; achieved = its
-    algorithmic bytes / its event time.  Also the per-kind shares, the same
-    figure over all levels of that kind, and the largest (kind, level)
-    entries."""
+    the largest share of the profiled device time.  Its arithmetic intensity
+    I (flops / algorithmic byte) decides the bound: HBM when peak_BW * I is
+    below the arithmetic peak of its precision, else the ALU (the FP64 rate
+    of this part is low enough to bind the FP64 dot products).  Also the
+    per-kind shares, the same figure over all levels of that kind, and the
+    largest (kind, level) entries."""
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
     tot = sum(v[0] for v in kinds.values())
-    (dk, dl), (ms, nl, nb) = max(per_level.items(), key=lambda kv: kv[1][0])
-    achieved = nb / (ms / 1e3) / 1e9
+    (dk, dl), (ms, nl, nb, nf) = max(per_level.items(), key=lambda kv: kv[1][0])
+    dtype = vcycle_dtype if dk in VCYCLE_KINDS else "f64"
+    gbs = nb / (ms / 1e3) / 1e9
+    tflops = nf / (ms / 1e3) / 1e12
+    fpeak = ALU_PEAK_TFLOPS[dtype]
+    intensity = nf / nb if nb else 0.0
+    alu_bound = peak * 1e9 * intensity > fpeak * 1e12
     ak = kinds[dk]
     top = sorted(per_level.items(), key=lambda kv: -kv[1][0])[:8]
-    return {"bound": "hbm", "kernel": "%s (level %d)" % (dk, dl), "achieved": achieved, "peak": peak,
-            "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-            "launches": nl, "avg_launch_us": 1e3 * ms / nl, "algorithmic_bytes_per_launch": nb / nl,
-            "share": ms / tot,
-            "kind_all_levels": {"kernel": dk, "achieved": ak[2] / (ak[0] / 1e3) / 1e9,
-                                "frac": ak[2] / (ak[0] / 1e3) / 1e9 / peak, "share": ak[0] / tot},
-            "kernel_share": {k: v[0] / tot for k, v in kinds.items()},
-            "top_launch_groups": [{"kernel": k, "level": l, "share": round(v[0] / tot, 4),
-                                   "gbs": round(v[2] / (v[0] / 1e3) / 1e9, 1),
-                                   "avg_us": round(1e3 * v[0] / v[1], 2)} for (k, l), v in top]}
+    entry = {"kernel": "%s (level %d)" % (dk, dl), "dtype": dtype,
+             "launches": nl, "avg_launch_us": 1e3 * ms / nl, "algorithmic_bytes_per_launch": nb / nl,
+             "flops_per_launch": nf / nl, "share": ms / tot,
+             "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak},
+             "alu": {"achieved": tflops, "peak": fpeak, "unit": "TFLOP/s", "frac": tflops / fpeak,
+                     "peak_source": "unit counts x nominal clock"},
+             "kind_all_levels": {"kernel": dk, "achieved": ak[2] / (ak[0] / 1e3) / 1e9,
+                                 "frac": ak[2] / (ak[0] / 1e3) / 1e9 / peak, "share": ak[0] / tot},
+             "kernel_share": {k: v[0] / tot for k, v in kinds.items()},
+             "top_launch_groups": [{"kernel": k, "level": l, "share": round(v[0] / tot, 4),
+                                    "gbs": round(v[2] / (v[0] / 1e3) / 1e9, 1),
+                                    "tflops": round(v[3] / (v[0] / 1e3) / 1e12, 3),
+                                    "avg_us": round(1e3 * v[0] / v[1], 2)} for (k, l), v in top]}
+    if alu_bound:
+        entry.update({"bound": "alu", "achieved": tflops, "peak": fpeak, "unit": "TFLOP/s",
+                      "frac": tflops / fpeak, "peak_source": "unit counts x nominal clock"})
+    else:
+        entry.update({"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                      "peak_source": peak_kind})
+    entry["traffic"] = None
+    return entry
 
 
 def run_gpu(args):
@@ -366,7 +392,8 @@ def run_gpu(args):
     per_level = G.airg_profile_read_level(h, sinfo["levels"])
     G.airg_profile(h, False)
     peak, peak_kind = measured_peaks()
-    roofline = roofline_entry(prof, per_level, peak, peak_kind)
+    roofline = roofline_entry(prof, per_level, peak, peak_kind,
+                              "f32" if w["opts"].get("precision") == 1 else "f64")
     vc_bytes = sinfo["bytes_per_vcycle"]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("c1", "c2"):

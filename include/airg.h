@@ -4,7 +4,7 @@
  * AIRG is the reduction multigrid of Dargaville, Smedley-Stevenson, Smith &
  * Pain, "Solving advection equations with reduction multigrids on GPUs"
  * (arXiv 2508.17517): approximate ideal restriction built from GMRES
- * polynomials (Sec. 2.2, Eq. 4-5), one-point prolongation and up F-point
+ * polynomials (Sec. 2.2, Eq. 7-8), one-point prolongation and up F-point
  * smoothing only (Sec. 2, Eq. 6), a PMISR DDC coarse/fine splitting
  * (Sec. 2.1), a high-order GMRES polynomial in Newton form as the coarse-grid
  * solver (Sec. 2.3) on a hierarchy truncated automatically by that
@@ -159,7 +159,7 @@ airg_status airg_rhs_adjoint_advection2d(int64_t nx, int64_t ny, double vx, doub
 /*
  * AIRG setup (Sec. 2): the level loop of truncation test (Sec. 2.4), CF
  * splitting (Sec. 2.1), block extraction, GMRES polynomial coefficients
- * (Eq. 4), fixed-sparsity inverse (Eq. 5), restrictor with drop, one-point
+ * (Eq. 7), fixed-sparsity inverse (Eq. 8), restrictor with drop, one-point
  * prolongator, RAP with drop and lumping, then the coarse-grid Newton
  * polynomial (Sec. 2.3), all on the GPU.  A is copied; the handle owns every
  * device buffer it allocates.  Setup values are reproducible: sums run in a
@@ -265,10 +265,12 @@ airg_status airg_profile_read(const airg_handle* h, int kind, double* ms, int64_
  * The same totals restricted to one level of the hierarchy: level l's
  * restriction, F-point residual and smoother launches, level = number of
  * levels - 1 for the coarse Newton steps, 0 for the top-level FGMRES, layout
- * and conversion kernels.  0 <= level < 65; AIRG_ERR_ARG otherwise.
+ * and conversion kernels.  *flops receives the floating-point operations
+ * those launches perform on stored entries and vectors (an FMA counts as
+ * two; padding excluded).  0 <= level < 65; AIRG_ERR_ARG otherwise.
  */
 airg_status airg_profile_read_level(const airg_handle* h, int kind, int level, double* ms,
-                                    int64_t* launches, int64_t* bytes);
+                                    int64_t* launches, int64_t* bytes, int64_t* flops);
 
 /*
  * Failure-detection check of the device-side waits: launches one block that
@@ -296,7 +298,7 @@ const char* airg_last_error(void);
  *    Flood 2014) of (seed, level, purpose) into out (DEVICE, length n).
  *  airg_host_gmres_coeffs: power-basis coefficients alpha (length k, HOST) of
  *    the GMRES polynomial from an Arnoldi Hessenberg H ((k+1) x k, row-major,
- *    HOST) and beta = ||b|| (Eq. 4), by Givens least squares; CPU only.
+ *    HOST) and beta = ||b|| (Eq. 7), by Givens least squares; CPU only.
  *  airg_host_eigvals: eigenvalues (wr, wi; HOST, length n) of a real upper
  *    Hessenberg matrix (row-major n x n, HOST) by the Francis double-shift QR
  *    iteration; CPU only.  AIRG_ERR_BREAKDOWN if it does not converge.

@@ -364,7 +364,7 @@ def extract(A, row_mask, col_mask):
 
 
 # --------------------------------------------------------------------------
-# GMRES polynomials (Sec. 2.2, Eq. 4)
+# GMRES polynomials (Sec. 2.2, Eq. 7)
 # --------------------------------------------------------------------------
 def arnoldi(A, b, m, breakdown_tol, exact_tol=1e-12):
     """m steps of modified Gram-Schmidt Arnoldi from b (x0 = 0).
@@ -451,7 +451,7 @@ def givens_lsq(H, beta):
 
 
 def power_coefficients(H, beta, y):
-    """alpha with x = sum_j y_j v_j = (alpha_0 + alpha_1 A + ...) b  (Eq. 4).
+    """alpha with x = sum_j y_j v_j = (alpha_0 + alpha_1 A + ...) b  (Eq. 7).
 
     Each Arnoldi vector is a polynomial in A applied to b: c_1 = 1/beta and
     c_{j+1}(z) = (z c_j(z) - sum_{i<=j} h_ij c_i(z)) / h_{j+1,j}.
@@ -476,7 +476,7 @@ def power_coefficients(H, beta, y):
 
 
 def gmres_poly_coeffs(A_ff, opts, level):
-    """Coefficients of the degree-p GMRES polynomial q(A_ff) ~ A_ff^-1 (Eq. 4).
+    """Coefficients of the degree-p GMRES polynomial q(A_ff) ~ A_ff^-1 (Eq. 7).
 
     Reading of "order p": degree p, p+1 coefficients, p+1 Arnoldi steps from a
     uniform [0,1) random rhs.  On breakdown the degree drops and the higher
@@ -500,7 +500,7 @@ def horner_apply(A, alpha, t):
 
 
 def fixed_sparsity_inverse(A_ff, alpha):
-    """Eq. 5: alpha_0 I + alpha_1 A_ff + sum_{k>=2} alpha_k T_k on pattern(A_ff).
+    """Eq. 8: alpha_0 I + alpha_1 A_ff + sum_{k>=2} alpha_k T_k on pattern(A_ff).
 
     Reading: T_1 = A_ff, T_k = mask(A_ff T_{k-1}) (each power restricted to
     the sparsity of A_ff); entries accumulate as (i==j ? alpha_0 : 0) then
@@ -523,7 +523,7 @@ def fixed_sparsity_inverse(A_ff, alpha):
 
 
 def restrictor_block(A_cf, Ainv, r_drop):
-    """Z = -A_cf Ahat_ff^-1 (Eq. 3-4 context), then the relative drop on R."""
+    """Z = -A_cf Ahat_ff^-1 (Eq. 5 solved approximately), then the relative drop on R."""
     P = spgemm(A_cf, Ainv)
     Z = CSR(P.n_rows, P.n_cols, P.rowptr, P.col, -P.val)
     keep = np.empty(Z.nnz, dtype=np.int8)
@@ -542,7 +542,7 @@ def one_point(A, strong, is_f):
 
 
 def coarse_matrix(A, is_f, Z, W, a_drop, lump):
-    """A_coarse = R (A P), R = [Z I], P = [W; I] (Eq. 3), then drop + lump.
+    """A_coarse = R (A P), R = [Z I], P = [W; I] (Eq. 4), then drop + lump.
 
     R and P are written in the fine numbering; AP is formed first and every
     entry of both products is summed in ascending inner index.

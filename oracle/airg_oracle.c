@@ -227,7 +227,7 @@ void orc_ddc_ratio(int64_t n, const int64_t* rp, const int64_t* ci, const double
 }
 
 /* ------------------------------------------------------------------------ */
-/* One power of the fixed-sparsity approximate inverse (Eq. 5):              */
+/* One power of the fixed-sparsity approximate inverse (Eq. 8):              */
 /*   T_k = mask_{pattern(A_ff)}(A_ff T_{k-1})                                 */
 /* For each stored (i,j): t_ij = sum over l in row i of A_ff (ascending) with */
 /* (l,j) stored, of a_il * t_{k-1,lj}; from +0.0, left to right.             */
@@ -316,7 +316,7 @@ int orc_spgemm(int64_t m, const int64_t* arp, const int64_t* aci, const double* 
 void orc_free(void* p) { free(p); }
 
 /* ------------------------------------------------------------------------ */
-/* Relative drop with lumping for the coarse matrix (Sec. 2, after Eq. 4):   */
+/* Relative drop with lumping for the coarse matrix (Sec. 2, after Eq. 6):   */
 /* off-diagonal a_ij is dropped when a_ij == 0 or |a_ij| < tol * max_{k!=i}  */
 /* |a_ik|; with lump != 0 the dropped values are added to the diagonal, one  */
 /* by one in column order, starting from a_ii.  keep[k] flags survivors;     */

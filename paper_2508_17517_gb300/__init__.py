@@ -116,7 +116,7 @@ def lib():
             "airg_profile_read": [vp, ci, ctypes.POINTER(f64), ctypes.POINTER(i64),
                                   ctypes.POINTER(i64)],
             "airg_profile_read_level": [vp, ci, ci, ctypes.POINTER(f64), ctypes.POINTER(i64),
-                                  ctypes.POINTER(i64)],
+                                        ctypes.POINTER(i64), ctypes.POINTER(i64)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -365,16 +365,16 @@ def airg_profile_read(handle):
 
 
 def airg_profile_read_level(handle, levels):
-    """{(kind, level): (ms, launches, algorithmic bytes)} for levels < `levels`,
-    entries with launches only."""
+    """{(kind, level): (ms, launches, algorithmic bytes, flops)} for levels <
+    `levels`, entries with launches only."""
     out = {}
     for k, name in enumerate(PROFILE_KINDS):
         for lev in range(levels):
-            ms, nl, nb = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+            ms, nl, nb, nf = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
             _check(lib().airg_profile_read_level(handle.ptr, k, lev, ctypes.byref(ms), ctypes.byref(nl),
-                                                 ctypes.byref(nb)))
+                                                 ctypes.byref(nb), ctypes.byref(nf)))
             if nl.value:
-                out[(name, lev)] = (ms.value, nl.value, nb.value)
+                out[(name, lev)] = (ms.value, nl.value, nb.value, nf.value)
     return out
 
 

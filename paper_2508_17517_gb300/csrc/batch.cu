@@ -435,7 +435,8 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         const Sell<T>& Z = bops<T>(lv).Z;
         S.cur_level = l;
         if (lv.n_c)
-            LAUNCH(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
+            LAUNCH_F(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
+                     (2 * Z.nnz + lv.n_c) * kk,
                    WITH_KW(k, kb_restrict<T, KW><<<grid_rows(lv.n_c), BT, 0, st>>>(
                                   view(Z), src + size_t(lv.off) * k, src + size_t(lv.off + lv.n_f) * k,
                                   wk.rwork + size_t(lv.off + lv.n_f) * k, k)));
@@ -457,16 +458,17 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
             const Root& q = S.roots[i];
             T* rout = bufs[nb];
             if (q.im == 0.0) {
-                LAUNCH(S, PK_NEWTON, (last ? 0 : mB + 2 * nB) + (i == 0 ? 2 : 3) * nB,
+                LAUNCH_F(S, PK_NEWTON, (last ? 0 : mB + 2 * nB) + (i == 0 ? 2 : 3) * nB,
+                         (last ? 2LL * nco : 2 * A.nnz + 4LL * nco) * kk,
                        WITH_KW(k, kb_newton_real<T, KW><<<grid_rows(nco), BT, 0, st>>>(
                                       Av, rin, rout, x, T(1.0 / q.re), i == 0, last, k)));
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
-                LAUNCH(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB,
+                LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, (2 * A.nnz + 4LL * nco) * kk,
                        WITH_KW(k, kb_newton_pair1<T, KW><<<grid_rows(nco), BT, 0, st>>>(
                                       Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0, k)));
                 if (!last)
-                    LAUNCH(S, PK_NEWTON, mB + 3 * nB,
+                    LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, (2 * A.nnz + 2LL * nco) * kk,
                            WITH_KW(k, kb_newton_pair2<T, KW><<<grid_rows(nco), BT, 0, st>>>(
                                           Av, rin, wk.ct, rout, T(1.0 / mod2), k)));
             }
@@ -485,11 +487,11 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         const int p = int(lv.alpha.size()) - 1;
         const long long fB = (long long)nf * VB * kk;
         S.cur_level = l;
-        LAUNCH(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB * kk + 3 * fB,
+        LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB * kk + 3 * fB, (2 * o.M.nnz + 2LL * nf) * kk,
                WITH_KW(k, kb_fresid<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
                                                                         T(lv.alpha[p]), k)));
         if (p == 0) {
-            LAUNCH(S, PK_HORNER, 3 * fB + 4LL * nf,
+            LAUNCH_F(S, PK_HORNER, 3 * fB + 4LL * nf, 3LL * nf * kk,
                    kb_smooth0<T><<<grid_for((long long)nf * k, BT), BT, 0, st>>>(nf, wk.t, ec, lv.W.p, ef,
                                                                                 T(lv.alpha[0]), k));
             continue;
@@ -498,12 +500,12 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         T* win = wk.wa;
         T* wout = wk.wb;
         for (int kq = p - 1; kq >= 1; --kq) {
-            LAUNCH(S, PK_HORNER, hB,
+            LAUNCH_F(S, PK_HORNER, hB, (2 * o.Aff.nnz + 2LL * nf) * kk,
                    WITH_KW(k, kb_horner<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.Aff), wk.t, win, wout,
                                                                             T(lv.alpha[kq]), k)));
             std::swap(win, wout);
         }
-        LAUNCH(S, PK_HORNER, hB + fB + 4LL * nf,
+        LAUNCH_F(S, PK_HORNER, hB + fB + 4LL * nf, (2 * o.Aff.nnz + 3LL * nf) * kk,
                WITH_KW(k, kb_horner_last<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.Aff), wk.t, win, ec,
                                                                              lv.W.p, ef, T(lv.alpha[0]), k)));
     }
@@ -601,7 +603,7 @@ void bnorms(SolveData& S, BatchData& B, const double* x, std::vector<double>& ou
 {
     long long n = S.n0;
     int k = B.k;
-    LAUNCH(S, PK_KRYLOV, 8 * B.nk,
+    LAUNCH_F(S, PK_KRYLOV, 8 * B.nk, 2 * B.nk,
            kb_multidot<1><<<RG, BT, 0, st>>>(n, k, x, B.nk, x, B.part.p, B.hdev.p, B.ticket.p, 0));
     out.resize(k);
     d2h(out.data(), B.hdev.p, size_t(k), st);
@@ -622,16 +624,16 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
     const int m = B.m;
     const int g = grid_for(nk, BT);
     SellView<double> A = view(S.Atop);
-    const long long topB = S.Atop.nnz * 12 + 16 * nk;
+    const long long topB = mat_bytes(S.Atop) + 16 * nk;
     LAUNCH(S, PK_LAYOUT, 20 * nk, kb_to_nested<<<g, BT, 0, st>>>(n, k, S.pos0.p, b, B.bp.p));
     LAUNCH(S, PK_LAYOUT, 20 * nk, kb_to_nested<<<g, BT, 0, st>>>(n, k, S.pos0.p, x, B.xp.p));
     std::vector<double> bn, rn, tol(k);
     bnorms(S, B, B.bp.p, bn, st);
     for (int q = 0; q < k; ++q) tol[q] = std::max(rtol * bn[q], atol);
     auto residual = [&]() {
-        LAUNCH(S, PK_TOPSPMV, topB,
+        LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz * k,
                WITH_KW(k, kb_spmv<double, KW><<<grid_rows(n), BT, 0, st>>>(A, B.xp.p, B.w.p, k)));
-        LAUNCH(S, PK_KRYLOV, 24 * nk, kb_sub<<<g, BT, 0, st>>>(nk, B.bp.p, B.w.p, B.r.p));
+        LAUNCH_F(S, PK_KRYLOV, 24 * nk, nk, kb_sub<<<g, BT, 0, st>>>(nk, B.bp.p, B.w.p, B.r.p));
         bnorms(S, B, B.r.p, rn, st);
     };
     residual();
@@ -648,7 +650,7 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
             if (!nact) break;
             bprecond(H, B, B.r.p, B.Zs.p, st);
             h2d(B.hdev.p, yq.data(), size_t(k), st);
-            LAUNCH(S, PK_KRYLOV, 24 * nk, kb_update<1><<<g, BT, 0, st>>>(n, k, B.Zs.p, nk, B.hdev.p, B.xp.p));
+            LAUNCH_F(S, PK_KRYLOV, 24 * nk, 2 * nk, kb_update<1><<<g, BT, 0, st>>>(n, k, B.Zs.p, nk, B.hdev.p, B.xp.p));
             residual();
             ++its;
         }
@@ -670,22 +672,22 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
         std::fill(gv.begin(), gv.end(), 0.0);
         for (int q = 0; q < k; ++q) gv[q] = rn[q];
         h2d(B.inv.p, inv.data(), size_t(k), st);
-        LAUNCH(S, PK_KRYLOV, 16 * nk, kb_scale<<<g, BT, 0, st>>>(n, k, B.r.p, B.inv.p, B.V.p));
+        LAUNCH_F(S, PK_KRYLOV, 16 * nk, nk, kb_scale<<<g, BT, 0, st>>>(n, k, B.r.p, B.inv.p, B.V.p));
         for (int j = 0; j < m; ++j) {
             double* vj = B.V.p + size_t(j) * nk;
             double* zj = B.Zs.p + size_t(j) * nk;
             bprecond(H, B, vj, zj, st);
-            LAUNCH(S, PK_TOPSPMV, topB,
+            LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz * k,
                    WITH_KW(k, kb_spmv<double, KW><<<grid_rows(n), BT, 0, st>>>(A, zj, B.w.p, k)));
             // CGS with a second pass only if some active right-hand side lost
             // more than half of ||w||^2 in the first ("twice is enough")
             double* h1 = B.hdev.p;
             double* h2 = B.hdev.p + size_t(MAXB + 2) * k;
             double* hnp = B.hdev.p + size_t(2) * (MAXB + 2) * k;
-            LAUNCH(S, PK_KRYLOV, 8LL * nk * (j + 2),
+            LAUNCH_F(S, PK_KRYLOV, 8LL * nk * (j + 2), 2LL * nk * (j + 2),
                    WITH_M(j + 1, kb_multidot<MM><<<RG, BT, 0, st>>>(n, k, B.V.p, nk, B.w.p, B.part.p, h1,
                                                                      B.ticket.p, 1)));
-            LAUNCH(S, PK_KRYLOV, 8LL * nk * (j + 3),
+            LAUNCH_F(S, PK_KRYLOV, 8LL * nk * (j + 3), 2LL * nk * (j + 2),
                    WITH_M(j + 1, kb_multiaxpy_norm<MM><<<RG, BT, 0, st>>>(n, k, B.V.p, nk, h1, B.w.p, B.part.p,
                                                                            hnp, B.ticket.p)));
             CK(cudaMemcpyAsync(hh, B.hdev.p, sizeof(double) * 3 * (MAXB + 2) * k, cudaMemcpyDeviceToHost, st));
@@ -696,10 +698,10 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
             for (int q = 0; q < k; ++q)
                 for (int i = 0; i <= j; ++i) hq(i, j, q) = hh[size_t(i) * k + q];
             if (again) {
-                LAUNCH(S, PK_KRYLOV, 8LL * nk * (j + 2),
+                LAUNCH_F(S, PK_KRYLOV, 8LL * nk * (j + 2), 2LL * nk * (j + 1),
                        WITH_M(j + 1, kb_multidot<MM><<<RG, BT, 0, st>>>(n, k, B.V.p, nk, B.w.p, B.part.p, h2,
                                                                          B.ticket.p, 0)));
-                LAUNCH(S, PK_KRYLOV, 8LL * nk * (j + 3),
+                LAUNCH_F(S, PK_KRYLOV, 8LL * nk * (j + 3), 2LL * nk * (j + 2),
                        WITH_M(j + 1, kb_multiaxpy_norm<MM><<<RG, BT, 0, st>>>(n, k, B.V.p, nk, h2, B.w.p, B.part.p,
                                                                                hnp, B.ticket.p)));
                 CK(cudaMemcpyAsync(hh, B.hdev.p, sizeof(double) * 3 * (MAXB + 2) * k, cudaMemcpyDeviceToHost, st));
@@ -737,7 +739,7 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
             }
             if (!still || its >= maxit || j + 1 == m) break;
             h2d(B.inv.p, inv.data(), size_t(k), st);
-            LAUNCH(S, PK_KRYLOV, 16 * nk,
+            LAUNCH_F(S, PK_KRYLOV, 16 * nk, nk,
                    kb_scale<<<g, BT, 0, st>>>(n, k, B.w.p, B.inv.p, B.V.p + size_t(j + 1) * nk));
         }
         // least squares per right-hand side, zero-padded to the common width
@@ -754,7 +756,7 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
         }
         if (jmax) {
             h2d(B.hdev.p, Y.data(), size_t(jmax) * k, st);
-            LAUNCH(S, PK_KRYLOV, 8LL * nk * (jmax + 2),
+            LAUNCH_F(S, PK_KRYLOV, 8LL * nk * (jmax + 2), 2LL * nk * jmax,
                    WITH_M(jmax, kb_update<MM><<<g, BT, 0, st>>>(n, k, B.Zs.p, nk, B.hdev.p, B.xp.p)));
         }
         residual();

@@ -434,23 +434,24 @@ airg_status airg_profile_read(const airg_handle* h, int kind, double* ms, int64_
         if (!h || !h->H || !h->H->solve || !ms || !launches || !bytes)
             airg::fail(AIRG_ERR_ARG, "bad profile arguments");
         long long l = 0, b = 0;
-        if (!airg::read_profile(*h->H, kind, -1, ms, &l, &b)) airg::fail(AIRG_ERR_ARG, "bad kernel kind");
+        if (!airg::read_profile(*h->H, kind, -1, ms, &l, &b, nullptr)) airg::fail(AIRG_ERR_ARG, "bad kernel kind");
         *launches = l;
         *bytes = b;
     });
 }
 
 airg_status airg_profile_read_level(const airg_handle* h, int kind, int level, double* ms, int64_t* launches,
-                                    int64_t* bytes)
+                                    int64_t* bytes, int64_t* flops)
 {
     return guarded([&] {
-        if (!h || !h->H || !h->H->solve || !ms || !launches || !bytes)
+        if (!h || !h->H || !h->H->solve || !ms || !launches || !bytes || !flops)
             airg::fail(AIRG_ERR_ARG, "bad profile arguments");
-        long long l = 0, b = 0;
-        if (!airg::read_profile(*h->H, kind, level, ms, &l, &b))
+        long long l = 0, b = 0, f = 0;
+        if (!airg::read_profile(*h->H, kind, level, ms, &l, &b, &f))
             airg::fail(AIRG_ERR_ARG, "bad kernel kind or level");
         *launches = l;
         *bytes = b;
+        *flops = f;
     });
 }
 

@@ -67,6 +67,7 @@ void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_de
 void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info);
 void set_profiling(Hierarchy& H, bool on);
 bool barrier_timeout_check(long long limit, cudaStream_t st);
-bool read_profile(const Hierarchy& H, int kind, int level, double* ms, long long* launches, long long* bytes);
+bool read_profile(const Hierarchy& H, int kind, int level, double* ms, long long* launches, long long* bytes,
+                  long long* flops);
 
 }  // namespace airg

@@ -1,6 +1,6 @@
 // Host FP64 dense steps of the AIRG setup.  Compiled with
 // -ffp-contract=off: every operation below is one IEEE-rounded operation in
-// the order written, so the coefficient computation of Eq. 4 gives the same
+// the order written, so the coefficient computation of Eq. 7 gives the same
 // bits as any other implementation that performs the same operations.
 #include "hostmath.h"
 

@@ -1,5 +1,5 @@
 // Small dense FP64 computations of the AIRG setup that run on the host:
-// the GMRES least-squares problem and power-basis coefficients (Eq. 4), and
+// the GMRES least-squares problem and power-basis coefficients (Eq. 7), and
 // the harmonic Ritz roots of the coarse-grid Newton polynomial (Sec. 2.3).
 #pragma once
 

@@ -1,7 +1,7 @@
 // AIRG setup on the GPU (Sec. 2 of arXiv 2508.17517), level by level:
 //   truncation test (Sec. 2.4) -> strength + S+S^T -> PMISR -> DDC (Sec. 2.1)
-//   -> block extraction (Eq. 3) -> GMRES polynomial coefficients (Eq. 4)
-//   -> fixed-sparsity inverse (Eq. 5) -> Z = -A_cf Ahat^-1 with R drop
+//   -> block extraction (Eq. 3) -> GMRES polynomial coefficients (Eq. 7)
+//   -> fixed-sparsity inverse (Eq. 8) -> Z = -A_cf Ahat^-1 with R drop
 //   -> one-point W -> A_coarse = R A P with drop + lumping
 // and finally the coarse-grid Newton polynomial (Sec. 2.3).
 //
@@ -1262,7 +1262,7 @@ std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, c
         submatrix(Al, L->f_ids.p, L->n_f, L->c_index.p, L->n_c, L->A_fc, st);
         DevCSR A_cf;
         submatrix(Al, L->c_ids.p, L->n_c, L->f_index.p, L->n_f, A_cf, st);
-        // GMRES polynomial (Eq. 4) and fixed-sparsity inverse (Eq. 5)
+        // GMRES polynomial (Eq. 7) and fixed-sparsity inverse (Eq. 8)
         L->alpha = gmres_poly_coeffs(c, L->A_ff, o, level, L->alpha_k);
         DevCSR Ainv;
         fixed_sparsity_inverse(L->A_ff, L->alpha, Ainv, st);

@@ -5,7 +5,7 @@
 // [F points of level l | unknowns of level l+1], recursively, so the whole
 // hierarchy lives in one vector of the top-level length: level l occupies the
 // suffix starting at off_l = n_F,0 + ... + n_F,l-1 and its C points are
-// exactly level l+1's block.  Restriction r_{l+1} = r_c + Z r_f (Eq. 3)
+// exactly level l+1's block.  Restriction r_{l+1} = r_c + Z r_f (R of Eq. 4)
 // therefore updates the C block in place, the coarse-grid correction e_c is
 // already where the prolongation reads it, and no gather or scatter runs
 // between levels.  The outer FGMRES works on the top operator permuted into
@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 
 #include "dev_util.cuh"
@@ -106,7 +107,7 @@ void build_sell(const DevCSR& A, const int* src_row, const int* cmap, int n_cols
     S.n_cols = n_cols;
     S.nnz = A.nnz;
     S.k = choose_parts(A.nnz, A.n_rows);
-    S.r = 1;
+    S.r = S.k == 1 ? 1 : 4;
     S.n_slices = (A.n_rows + 31) / 32;
     S.sptr.alloc(size_t(S.n_slices) + 1);
     if (S.n_slices)
@@ -203,47 +204,46 @@ __global__ void k_map_w(int nf, const int* W, const int* rel, int* out)
 // loads are contiguous) and reduce with shuffles; the sum is valid in the
 // group's first lane.  Every lane of a warp reaches the shuffles.
 // Sum of val[idx] * x[col[idx]] over idx = first, first + stride, ... < end.
-// Loads of four (then two) entries are issued before their gathers so that
-// each lane keeps several memory requests in flight (the gathers depend on
-// the column loads; without this every entry costs a full round trip).
-template <class T>
+// The j-th entry of the sequence goes to partial sum j mod 4 (each partial
+// in entry order) and the result is (p0 + p1) + (p2 + p3), whatever U is.  U
+// entries' loads are issued before their gathers, so each lane keeps U
+// memory requests in flight (the gathers depend on the column loads).
+template <class T, int U = 4>
 __device__ __forceinline__ T strided_dot(const int* __restrict__ col, const T* __restrict__ val,
                                          const T* __restrict__ x, int idx, int end, int stride)
 {
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    for (; idx + 3 * stride < end; idx += 4 * stride) {
-        int c0 = __ldg(col + idx), c1 = __ldg(col + idx + stride);
-        int c2 = __ldg(col + idx + 2 * stride), c3 = __ldg(col + idx + 3 * stride);
-        T v0 = __ldg(val + idx), v1 = __ldg(val + idx + stride);
-        T v2 = __ldg(val + idx + 2 * stride), v3 = __ldg(val + idx + 3 * stride);
-        a0 = fma(v0, x[c0], a0);
-        a1 = fma(v1, x[c1], a1);
-        a2 = fma(v2, x[c2], a2);
-        a3 = fma(v3, x[c3], a3);
+    static_assert(U % 4 == 0, "U must be a multiple of 4");
+    T a[4] = {T(0), T(0), T(0), T(0)};
+    for (; idx < end; idx += U * stride) {
+        int c[U];
+        T v[U], xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool ok = idx + u * stride < end;
+            c[u] = ok ? __ldg(col + idx + u * stride) : 0;
+            v[u] = ok ? __ldg(val + idx + u * stride) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) xv[u] = idx + u * stride < end ? x[c[u]] : T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (idx + u * stride < end) a[u % 4] = fma(v[u], xv[u], a[u % 4]);
     }
-    if (idx + stride < end) {
-        int c0 = __ldg(col + idx), c1 = __ldg(col + idx + stride);
-        T v0 = __ldg(val + idx), v1 = __ldg(val + idx + stride);
-        a0 = fma(v0, x[c0], a0);
-        a1 = fma(v1, x[c1], a1);
-        idx += 2 * stride;
-    }
-    if (idx < end) a2 = fma(__ldg(val + idx), x[__ldg(col + idx)], a2);
-    return (a0 + a1) + (a2 + a3);
+    return (a[0] + a[1]) + (a[2] + a[3]);
 }
 
 // Row (32*slice + lane) of S times x, computed by the P warps of the block
 // that share the slice (part = this warp's index among them).  Every thread
 // of the block must call it (it synchronises the block when P > 1).  The
 // sum is valid in the part-0 warp, which also adds the dense diagonal.
-template <class T, int P>
+template <class T, int P, int U = 4>
 __device__ __forceinline__ T row_dot(const SellView<T>& S, int slice, int lane, int part,
                                      const T* __restrict__ x)
 {
     T acc = T(0);
     if (slice < S.n_slices) {
         int b = S.sptr[slice], w = (S.sptr[slice + 1] - b) >> 5;
-        acc = strided_dot(S.col, S.val, x, b + lane + 32 * part, b + lane + 32 * w, 32 * P);
+        acc = strided_dot<T, U>(S.col, S.val, x, b + lane + 32 * part, b + lane + 32 * w, 32 * P);
     }
     if (P > 1) {
         __shared__ T red[32][32];
@@ -329,8 +329,9 @@ __device__ __forceinline__ void dot_slices(const SellView<T>& S, const T* __rest
 
 // Applies epi(r, (S x)_r, pre(r)) to every row r of S.  pre(r) loads the
 // row's other operands; it runs before the row's gathers so that its loads
-// overlap them.  K = warps per slice (K > 1 for long rows, R must then be
-// 1); R = slices per warp for K = 1.
+// overlap them.  K = warps per slice.  R = slices per warp for K = 1, and
+// loads in flight per lane (4, 8 or 16) for K > 1; in neither case does R
+// change the arithmetic.
 template <class T, int K, int R, class Pre, class Epi>
 __device__ __forceinline__ void for_rows(const SellView<T>& S, const T* __restrict__ x, const Pre& pre,
                                          const Epi& epi)
@@ -353,13 +354,12 @@ __device__ __forceinline__ void for_rows(const SellView<T>& S, const T* __restri
             if (r < S.n_rows) epi(r, acc[q], pv[q]);
         }
     } else {
-        static_assert(R == 1, "several slices per warp only with one warp per slice");
         const int part = (threadIdx.x >> 5) % K;
         const int slice = blockIdx.x * (wpb_for(K) / K) + (threadIdx.x >> 5) / K;
         const int r = slice * 32 + lane;
         const bool lead = part == 0 && r < S.n_rows;
         PV pv = lead ? pre(r) : PV{};
-        T d = row_dot<T, K>(S, slice, lane, part, x);
+        T d = row_dot<T, K, R>(S, slice, lane, part, x);
         if (lead) epi(r, d, pv);
     }
 }
@@ -376,7 +376,7 @@ __global__ void k_spmv(SellView<T> S, const T* __restrict__ x, T* __restrict__ y
     for_rows<T, K, R>(S, x, [](int) { return 0; }, [&](int r, T d, int) { y[r] = d; });
 }
 
-// restriction (Eq. 3): dst_c[k] = src_c[k] + (Z src_f)[k]
+// restriction (R = [Z I] of Eq. 4): dst_c[k] = src_c[k] + (Z src_f)[k]
 template <class T, int K, int R>
 __global__ void k_restrict(SellView<T> Z, const T* __restrict__ src_f, const T* __restrict__ src_c,
                            T* __restrict__ dst_c)
@@ -492,6 +492,19 @@ inline int bk(int P) { return 32 * wpb_for(P); }
         }                                                                       \
     } while (0)
 
+// WITH_K for the long-row layouts only (KK > 1).
+#define WITH_K_LONG(kv, ...)                                                    \
+    do {                                                                        \
+        switch (kv) {                                                           \
+            case 2: { constexpr int KK = 2; __VA_ARGS__; } break;               \
+            case 4: { constexpr int KK = 4; __VA_ARGS__; } break;               \
+            case 8: { constexpr int KK = 8; __VA_ARGS__; } break;               \
+            case 16: { constexpr int KK = 16; __VA_ARGS__; } break;             \
+            case 32: { constexpr int KK = 32; __VA_ARGS__; } break;             \
+            default: fail(AIRG_ERR_STATE, "bad warps-per-slice");               \
+        }                                                                       \
+    } while (0)
+
 // Grid and block of the row kernels for operator S: K = S.k warps per slice,
 // or (K = 1) S.r slices per warp.
 template <class T>
@@ -505,7 +518,7 @@ template <class T>
 inline int block_rows(const Sell<T>& S) { return bk(S.k); }
 
 // Runs the statement with compile-time KK (warps per slice) and RR (slices
-// per warp) of operator S.
+// per warp for KK = 1, loads in flight per lane for KK > 1) of operator S.
 #define WITH_KR(S, ...)                                                         \
     do {                                                                        \
         if ((S).k == 1) {                                                       \
@@ -517,8 +530,12 @@ inline int block_rows(const Sell<T>& S) { return bk(S.k); }
                 default: fail(AIRG_ERR_STATE, "bad slices-per-warp");           \
             }                                                                   \
         } else {                                                                \
-            constexpr int RR = 1;                                               \
-            WITH_K((S).k, __VA_ARGS__);                                         \
+            switch ((S).r) {                                                    \
+                case 4: { constexpr int RR = 4; WITH_K_LONG((S).k, __VA_ARGS__); } break;   \
+                case 8: { constexpr int RR = 8; WITH_K_LONG((S).k, __VA_ARGS__); } break;   \
+                case 16: { constexpr int RR = 16; WITH_K_LONG((S).k, __VA_ARGS__); } break; \
+                default: fail(AIRG_ERR_STATE, "bad loads-per-lane");            \
+            }                                                                   \
         }                                                                       \
     } while (0)
 
@@ -917,7 +934,7 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         const Sell<T>& Z = ops<T>(lv).Z;
         S.cur_level = l;
         if (lv.n_c)
-            LAUNCH(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB,
+            LAUNCH_F(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Z.nnz + lv.n_c,
                    WITH_KR(Z, k_restrict<T, KK, RR><<<grid_rows(Z), block_rows(Z), 0, st>>>(
                                   view(Z), src + lv.off, src + lv.off + lv.n_f,
                                   wk.rwork + lv.off + lv.n_f)));
@@ -938,10 +955,12 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         const int pidx = sizeof(T) == 8 ? 0 : 1;
         if (S.newton_grid[pidx] > 0 && nr > 0) {
             // all Newton steps in one cooperative launch
-            long long bytes = 0;
+            long long bytes = 0, flops = 0;
             for (size_t i = 0; i < nr; ++i) {
                 bool last = i + 1 == nr;
                 bytes += S.roots[i].im == 0.0 ? (last ? 3 * nB : mB + 4 * nB) : (last ? mB + 4 * nB : 2 * mB + 8 * nB);
+                flops += S.roots[i].im == 0.0 ? (last ? 2LL * nco : 2 * A.nnz + 4LL * nco)
+                                              : (last ? 2 * A.nnz + 4LL * nco : 4 * A.nnz + 6LL * nco);
             }
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(S.newton_grid[pidx]);
@@ -954,7 +973,7 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             int nroots = int(nr);
-            LAUNCH(S, PK_NEWTON, bytes,
+            LAUNCH_F(S, PK_NEWTON, bytes, flops,
                    WITH_K(A.k, CK(cudaLaunchKernelEx(&cfg, k_newton_persistent<T, KK>, Av, rc, x, wk.cr0,
                                                      wk.cr1, wk.ct, (const double*)S.roots_dev.p, nroots,
                                                      S.bar.p, S.bar.p + 1, (int*)(S.bar.p + 2)))));
@@ -966,19 +985,19 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
             T* rout = bufs[nb];
             if (q.im == 0.0) {
                 if (last)
-                    LAUNCH(S, PK_NEWTON, (i == 0 ? 2 : 3) * nB,
+                    LAUNCH_F(S, PK_NEWTON, (i == 0 ? 2 : 3) * nB, 2LL * nco,
                            k_newton_last<T><<<grid_for(nco, TB), TB, 0, st>>>(nco, rin, x, T(1.0 / q.re), i == 0));
                 else
-                    LAUNCH(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB,
+                    LAUNCH_F(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB, 2 * A.nnz + 4LL * nco,
                            WITH_KR(A, k_newton_real<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
                                           Av, rin, rout, x, T(1.0 / q.re), i == 0)));
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
-                LAUNCH(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB,
+                LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, 2 * A.nnz + 4LL * nco,
                        WITH_KR(A, k_newton_pair1<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
                                       Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
                 if (!last)
-                    LAUNCH(S, PK_NEWTON, mB + 3 * nB,
+                    LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
                            WITH_KR(A, k_newton_pair2<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
                                           Av, rin, wk.ct, rout, T(1.0 / mod2))));
             }
@@ -1018,17 +1037,18 @@ coarse_done:
             long long bytes = mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB +
                               p * (mat_bytes(o.Aff) + 3 * fB) + fB + 4LL * nf;
             SellView<T> Mv = view(o.M), Av2 = view(o.Aff);
-            LAUNCH(S, PK_HORNER, bytes,
+            const long long flops = 2 * o.M.nnz + 2LL * nf + p * (2 * o.Aff.nnz + 2LL * nf) + nf;
+            LAUNCH_F(S, PK_HORNER, bytes, flops,
                    CK(cudaLaunchKernelEx(&cfg, k_smooth_persistent<T>, Mv, o.M.k, Av2, o.Aff.k, rf, ec,
                                          (const int*)lv.W.p, ef, wk.t, wk.wa, wk.wb, al, p, S.bar.p,
                                          S.bar.p + 1, (int*)(S.bar.p + 2))));
             continue;
         }
-        LAUNCH(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB,
+        LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
                WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M), block_rows(o.M), 0, st>>>(
                                 view(o.M), rf, ec, wk.t, wk.wa, T(lv.alpha[p]))));
         if (p == 0) {
-            LAUNCH(S, PK_HORNER, 3 * fB + 4LL * nf,
+            LAUNCH_F(S, PK_HORNER, 3 * fB + 4LL * nf, 3LL * nf,
                    k_smooth0<T><<<g, TB, 0, st>>>(nf, wk.t, ec, lv.W.p, ef, T(lv.alpha[0])));
             continue;
         }
@@ -1036,12 +1056,12 @@ coarse_done:
         T* win = wk.wa;
         T* wout = wk.wb;
         for (int k = p - 1; k >= 1; --k) {
-            LAUNCH(S, PK_HORNER, hB,
+            LAUNCH_F(S, PK_HORNER, hB, 2 * o.Aff.nnz + 2LL * nf,
                    WITH_KR(o.Aff, k_horner<T, KK, RR><<<grid_rows(o.Aff), block_rows(o.Aff), 0, st>>>(
                                       view(o.Aff), wk.t, win, wout, T(lv.alpha[k]))));
             std::swap(win, wout);
         }
-        LAUNCH(S, PK_HORNER, hB + fB + 4LL * nf,
+        LAUNCH_F(S, PK_HORNER, hB + fB + 4LL * nf, 2 * o.Aff.nnz + 3LL * nf,
                WITH_KR(o.Aff, k_horner_last<T, KK, RR><<<grid_rows(o.Aff), block_rows(o.Aff), 0, st>>>(
                                   view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0]))));
     }
@@ -1056,13 +1076,16 @@ long long sell_bytes(const Sell<double>& S, int vbytes)
     return (S.nnz - S.ndiag) * (vbytes + 4) + S.ndiag * vbytes + 2LL * S.n_rows * vbytes;
 }
 
-// Slices per warp of every short-row operator, picked by timing y = S x for
-// r = 1, 2, 4 (the per-row arithmetic does not depend on r).  forced > 0
-// (AIRG_ROWS_PER_WARP) skips the timing.
+// Row-kernel variant of every operator, picked by timing y = S x: slices
+// per warp r = 1, 2, 4 for short rows (one warp per slice), loads in flight
+// per lane r = 4, 8, 16 for long rows (several warps per slice).  Neither
+// changes the arithmetic.  forced > 0 (AIRG_ROWS_PER_WARP for short rows,
+// AIRG_LOADS_PER_LANE for long rows) skips the timing.
 template <class T>
-void tune_rows(Sell<T>& A, const T* x, T* y, int forced, cudaStream_t st)
+void tune_rows(Sell<T>& A, const T* x, T* y, int forced_short, int forced_long, cudaStream_t st)
 {
-    if (A.k != 1 || A.n_rows == 0) return;
+    if (A.n_rows == 0) return;
+    const int forced = A.k == 1 ? forced_short : forced_long;
     if (forced) {
         A.r = forced;
         return;
@@ -1071,9 +1094,11 @@ void tune_rows(Sell<T>& A, const T* x, T* y, int forced, cudaStream_t st)
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 0.f;
-    int best_r = 1;
-    for (int r : {1, 2, 4}) {
-        A.r = r;
+    int best_r = A.k == 1 ? 1 : 4;
+    const int cand_short[3] = {1, 2, 4}, cand_long[3] = {4, 8, 16};
+    const int* cand = A.k == 1 ? cand_short : cand_long;
+    for (int ci = 0; ci < 3; ++ci) {
+        A.r = cand[ci];
         SellView<T> v = view(A);
         WITH_KR(A, k_spmv<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(v, x, y));
         CK_LAUNCH();
@@ -1084,9 +1109,9 @@ void tune_rows(Sell<T>& A, const T* x, T* y, int forced, cudaStream_t st)
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (r == 1 || ms < best) {
+        if (ci == 0 || ms < best) {
             best = ms;
-            best_r = r;
+            best_r = cand[ci];
         }
     }
     cudaEventDestroy(e0);
@@ -1094,22 +1119,30 @@ void tune_rows(Sell<T>& A, const T* x, T* y, int forced, cudaStream_t st)
     A.r = best_r;
 }
 
+int env_choice(const char* name, std::initializer_list<int> allowed)
+{
+    const char* e = getenv(name);
+    int v = e ? atoi(e) : 0;
+    for (int a : allowed)
+        if (v == a) return v;
+    return 0;
+}
+
 template <class T>
 void tune_all(SolveData& S, cudaStream_t st)
 {
-    const char* e = getenv("AIRG_ROWS_PER_WARP");
-    int forced = e ? atoi(e) : 0;
-    if (forced != 1 && forced != 2 && forced != 4) forced = 0;
+    const int fs = env_choice("AIRG_ROWS_PER_WARP", {1, 2, 4});
+    const int fl = env_choice("AIRG_LOADS_PER_LANE", {4, 8, 16});
     size_t n = std::max(S.n0, 1);
     DBuf<T> x(n), y(n);
     CK(cudaMemsetAsync(x.p, 0, x.bytes(), st));
     for (auto& lp : S.lv) {
         SolveLevelT<T>& o = const_cast<SolveLevelT<T>&>(ops<T>(*lp));
-        tune_rows(o.Aff, x.p, y.p, forced, st);
-        tune_rows(o.M, x.p, y.p, forced, st);
-        tune_rows(o.Z, x.p, y.p, forced, st);
+        tune_rows(o.Aff, x.p, y.p, fs, fl, st);
+        tune_rows(o.M, x.p, y.p, fs, fl, st);
+        tune_rows(o.Z, x.p, y.p, fs, fl, st);
     }
-    tune_rows(const_cast<Sell<T>&>(coarse_op<T>(S)), x.p, y.p, forced, st);
+    tune_rows(const_cast<Sell<T>&>(coarse_op<T>(S)), x.p, y.p, fs, fl, st);
     CK(cudaStreamSynchronize(st));
 }
 
@@ -1228,12 +1261,10 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
     if (H.opt.precision == AIRG_MIXED_FP32) tune_all<float>(*S, st);
     else tune_all<double>(*S, st);
     {
-        const char* e = getenv("AIRG_ROWS_PER_WARP");
-        int forced = e ? atoi(e) : 0;
-        if (forced != 1 && forced != 2 && forced != 4) forced = 0;
         DBuf<double> x(std::max(S->n0, 1)), y(std::max(S->n0, 1));
         CK(cudaMemsetAsync(x.p, 0, x.bytes(), st));
-        tune_rows(S->Atop, x.p, y.p, forced, st);
+        tune_rows(S->Atop, x.p, y.p, env_choice("AIRG_ROWS_PER_WARP", {1, 2, 4}),
+                  env_choice("AIRG_LOADS_PER_LANE", {4, 8, 16}), st);
         CK(cudaStreamSynchronize(st));
     }
     // work vectors
@@ -1269,14 +1300,14 @@ void launch_multidot(SolveData& S, long long n, int m, const double* V, long lon
 {
     if (m == 0) {
         if (selfdot)
-            LAUNCH(S, PK_KRYLOV, 8 * n,
+            LAUNCH_F(S, PK_KRYLOV, 8 * n, 2 * n,
                    k_multidot<0><<<RGRID, RB, 0, st>>>(n, V, ldv, w, S.part.p, out, S.ticket.p, 1));
         return;
     }
     for (int c0 = 0; c0 < m; c0 += MCH) {
         const int mc = std::min(MCH, m - c0);
         const int self = selfdot && c0 + mc == m;
-        LAUNCH(S, PK_KRYLOV, 8LL * n * (mc + 1),
+        LAUNCH_F(S, PK_KRYLOV, 8LL * n * (mc + 1), 2LL * n * (mc + self),
                WITH_M(mc, k_multidot<MM><<<RGRID, RB, 0, st>>>(n, V + c0 * ldv, ldv, w, S.part.p, out + c0,
                                                                 S.ticket.p, self)));
     }
@@ -1290,7 +1321,7 @@ void launch_multiaxpy(SolveData& S, long long n, int m, const double* V, long lo
     for (int c0 = 0; c0 < m; c0 += MCH) {
         const int mc = std::min(MCH, m - c0);
         const int norm = nrm2 && c0 + mc == m;
-        LAUNCH(S, PK_KRYLOV, 8LL * n * (mc + 2),
+        LAUNCH_F(S, PK_KRYLOV, 8LL * n * (mc + 2), 2LL * n * (mc + (norm ? 1 : 0)),
                WITH_M(mc, k_multiaxpy<MM><<<RGRID, RB, 0, st>>>(n, V + c0 * ldv, ldv, h + c0, neg, w, norm,
                                                                  S.part.p, nrm2, S.ticket.p)));
     }
@@ -1397,9 +1428,9 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
     double tol = std::max(rtol * bn, atol);
     int its = 0;
     auto residual = [&]() {
-        LAUNCH(S, PK_TOPSPMV, topB,
+        LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz,
                WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop), block_rows(S.Atop), 0, st>>>(A, S.xp.p, S.w.p)));
-        LAUNCH(S, PK_KRYLOV, 24 * n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
+        LAUNCH_F(S, PK_KRYLOV, 24 * n, n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
         CK_LAUNCH();
         return dev_norm(S, S.r.p, n, st);
     };
@@ -1407,7 +1438,7 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
     std::vector<double> Hm(size_t(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
     double* hh = S.hhost.p;
     while (rn > tol && its < maxit) {
-        LAUNCH(S, PK_KRYLOV, 16 * n, k_scale_into<<<g, TB, 0, st>>>(n, S.r.p, 1.0 / rn, S.V.p));
+        LAUNCH_F(S, PK_KRYLOV, 16 * n, n, k_scale_into<<<g, TB, 0, st>>>(n, S.r.p, 1.0 / rn, S.V.p));
         std::fill(gv.begin(), gv.end(), 0.0);
         gv[0] = rn;
         int jdone = 0;
@@ -1415,7 +1446,7 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             double* vj = S.V.p + size_t(j) * n;
             double* zj = S.Zs.p + size_t(j) * n;
             precond(H, vj, zj, st);
-            LAUNCH(S, PK_TOPSPMV, topB,
+            LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz,
                    WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop), block_rows(S.Atop), 0, st>>>(A, zj, S.w.p)));
             // classical Gram-Schmidt; a second pass only when the first
             // one cancelled more than half of ||w||^2 ("twice is enough",
@@ -1458,7 +1489,7 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             ++its;
             jdone = j + 1;
             if (std::fabs(gv[j + 1]) <= tol || its >= maxit || den == 0.0 || hn == 0.0) break;
-            LAUNCH(S, PK_KRYLOV, 16 * n,
+            LAUNCH_F(S, PK_KRYLOV, 16 * n, n,
                    k_scale_into<<<g, TB, 0, st>>>(n, S.w.p, 1.0 / hn, S.V.p + size_t(j + 1) * n));
         }
         for (int j = jdone - 1; j >= 0; --j) {
@@ -1490,9 +1521,9 @@ void richardson(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_in
     double bn = dev_norm(S, S.bp.p, n, st);
     double tol = std::max(rtol * bn, atol);
     auto residual = [&]() {
-        LAUNCH(S, PK_TOPSPMV, topB,
+        LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz,
                WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop), block_rows(S.Atop), 0, st>>>(A, S.xp.p, S.w.p)));
-        LAUNCH(S, PK_KRYLOV, 24 * n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
+        LAUNCH_F(S, PK_KRYLOV, 24 * n, n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
         CK_LAUNCH();
         return dev_norm(S, S.r.p, n, st);
     };
@@ -1500,7 +1531,7 @@ void richardson(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_in
     int its = 0;
     while (rn > tol && its < maxit) {
         precond(H, S.r.p, S.Zs.p, st);
-        LAUNCH(S, PK_KRYLOV, 24 * n, k_add_dev<<<g, TB, 0, st>>>(n, S.Zs.p, nullptr, S.xp.p));
+        LAUNCH_F(S, PK_KRYLOV, 24 * n, n, k_add_dev<<<g, TB, 0, st>>>(n, S.Zs.p, nullptr, S.xp.p));
         rn = residual();
         ++its;
     }
@@ -1532,7 +1563,7 @@ void mp_top_spmv(Hierarchy& H, const double* x, double* y, cudaStream_t st)
     SolveData& S = *H.solve;
     long long n = S.n0;
     SellView<double> A = view(S.Atop);
-    LAUNCH(S, PK_TOPSPMV, mat_bytes(S.Atop) + 16 * n,
+    LAUNCH_F(S, PK_TOPSPMV, mat_bytes(S.Atop) + 16 * n, 2 * S.Atop.nnz,
            WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop), block_rows(S.Atop), 0, st>>>(A, x, y)));
 }
 
@@ -1555,7 +1586,7 @@ void mp_scale_dev(Hierarchy& H, const double* w, const double* nrm2, const int* 
 {
     SolveData& S = *H.solve;
     long long n = S.n0;
-    LAUNCH(S, PK_KRYLOV, 16 * n, k_scale_dev<<<grid_for(n, TB), TB, 0, st>>>(n, w, nrm2, active, v));
+    LAUNCH_F(S, PK_KRYLOV, 16 * n, n, k_scale_dev<<<grid_for(n, TB), TB, 0, st>>>(n, w, nrm2, active, v));
 }
 
 void mp_residual(Hierarchy& H, const double* b, const double* x, double* y, double* r, cudaStream_t st)
@@ -1563,7 +1594,7 @@ void mp_residual(Hierarchy& H, const double* b, const double* x, double* y, doub
     SolveData& S = *H.solve;
     long long n = S.n0;
     mp_top_spmv(H, x, y, st);
-    LAUNCH(S, PK_KRYLOV, 24 * n, k_sub2<<<grid_for(n, TB), TB, 0, st>>>(n, b, y, r));
+    LAUNCH_F(S, PK_KRYLOV, 24 * n, n, k_sub2<<<grid_for(n, TB), TB, 0, st>>>(n, b, y, r));
 }
 
 void mp_update(Hierarchy& H, int m, const double* Zs, const double* y, double* x, cudaStream_t st)
@@ -1576,7 +1607,7 @@ void mp_add_dev(Hierarchy& H, const double* z, const int* active, double* x, cud
 {
     SolveData& S = *H.solve;
     long long n = S.n0;
-    LAUNCH(S, PK_KRYLOV, 24 * n, k_add_dev<<<grid_for(n, TB), TB, 0, st>>>(n, z, active, x));
+    LAUNCH_F(S, PK_KRYLOV, 24 * n, n, k_add_dev<<<grid_for(n, TB), TB, 0, st>>>(n, z, active, x));
 }
 
 void mp_permute(Hierarchy& H, const double* a, double* b, bool to_nested, cudaStream_t st)
@@ -1721,11 +1752,13 @@ void set_profiling(Hierarchy& H, bool on)
             S.lev_ms[k][l] = 0;
             S.lev_launches[k][l] = 0;
             S.lev_bytes[k][l] = 0;
+            S.lev_flops[k][l] = 0;
         }
     }
 }
 
-bool read_profile(const Hierarchy& H, int kind, int level, double* ms, long long* launches, long long* bytes)
+bool read_profile(const Hierarchy& H, int kind, int level, double* ms, long long* launches, long long* bytes,
+                  long long* flops)
 {
     if (kind < 0 || kind >= PROF_KINDS || level < -1 || level >= SolveData::PROF_LEVELS) return false;
     const SolveData& S = *H.solve;
@@ -1733,10 +1766,14 @@ bool read_profile(const Hierarchy& H, int kind, int level, double* ms, long long
         *ms = S.kind_ms[kind];
         *launches = S.kind_launches[kind];
         *bytes = S.kind_bytes[kind];
+        long long f = 0;
+        for (int l = 0; l < SolveData::PROF_LEVELS; ++l) f += S.lev_flops[kind][l];
+        if (flops) *flops = f;
     } else {
         *ms = S.lev_ms[kind][level];
         *launches = S.lev_launches[kind][level];
         *bytes = S.lev_bytes[kind][level];
+        if (flops) *flops = S.lev_flops[kind][level];
     }
     return true;
 }

@@ -133,7 +133,7 @@ struct SolveData {
     // launch count and optional per-kind CUDA-event timing of the solve kernels
     long long launches = 0;
     bool prof = false;
-    struct Rec { int kind, level; cudaEvent_t a, b; long long bytes; };
+    struct Rec { int kind, level; cudaEvent_t a, b; long long bytes, flops; };
     int cur_level = 0;           // level of the kernels being launched (coarsest = nlev)
     std::vector<cudaEvent_t> evpool;
     size_t evnext = 0;
@@ -144,6 +144,7 @@ struct SolveData {
     long long kind_launches[PROF_KINDS] = {}, kind_bytes[PROF_KINDS] = {};
     double lev_ms[PROF_KINDS][PROF_LEVELS] = {};
     long long lev_launches[PROF_KINDS][PROF_LEVELS] = {}, lev_bytes[PROF_KINDS][PROF_LEVELS] = {};
+    long long lev_flops[PROF_KINDS][PROF_LEVELS] = {};
     cudaEvent_t next_event()
     {
         if (evnext == evpool.size()) {
@@ -167,13 +168,13 @@ struct SolveData {
         ++launches;
         if (prof) { a = next_event(); record(a, st); }
     }
-    void end(int kind, long long bytes, cudaStream_t st, cudaEvent_t a)
+    void end(int kind, long long bytes, long long flops, cudaStream_t st, cudaEvent_t a)
     {
         if (!prof) return;
         cudaEvent_t b = next_event();
         record(b, st);
         int lvl = cur_level < 0 ? 0 : (cur_level >= PROF_LEVELS ? PROF_LEVELS - 1 : cur_level);
-        recs.push_back(Rec{kind, lvl, a, b, bytes});
+        recs.push_back(Rec{kind, lvl, a, b, bytes, flops});
     }
     // after the stream has been synchronised
     void collect()
@@ -187,6 +188,7 @@ struct SolveData {
             lev_ms[r.kind][r.level] += ms;
             lev_launches[r.kind][r.level] += 1;
             lev_bytes[r.kind][r.level] += r.bytes;
+            lev_flops[r.kind][r.level] += r.flops;
         }
         recs.clear();
         evnext = 0;
@@ -234,14 +236,17 @@ struct SolveData {
         }                                                                       \
     } while (0)
 
-// Launch through the counter / profiler: LAUNCH(S, kind, bytes, kernel<<<...>>>(...))
-#define LAUNCH(S, KIND, BYTES, ...)                  \
+// Launch through the counter / profiler:
+//   LAUNCH_F(S, kind, algorithmic bytes, floating-point operations, kernel<<<...>>>(...))
+// (an FMA counts as two operations); LAUNCH for kernels that only move data.
+#define LAUNCH_F(S, KIND, BYTES, FLOPS, ...)         \
     do {                                             \
         cudaEvent_t ev_a_ = nullptr;                 \
         (S).begin(st, ev_a_);                        \
         __VA_ARGS__;                                 \
-        (S).end((KIND), (BYTES), st, ev_a_);         \
+        (S).end((KIND), (BYTES), (FLOPS), st, ev_a_); \
     } while (0)
+#define LAUNCH(S, KIND, BYTES, ...) LAUNCH_F(S, KIND, BYTES, 0LL, __VA_ARGS__)
 
 
 // solve.cu: launch helpers of one problem's solve, for the multi-problem

@@ -1,0 +1,29 @@
+"""Host logic of bench.py's roofline entry (no GPU): the bound follows the
+roofline model, min(peak_BW * intensity, arithmetic peak)."""
+import bench
+
+
+def test_fp64_dot_products_are_alu_bound():
+    # 8 bytes and one FMA (2 flops) per element: 0.25 flop/B * 6.77 TB/s
+    # = 1.69 TFLOP/s > 1.26 TFLOP/s FP64 peak
+    prof = {"krylov_vectors": (10.0, 100, 8 * 10**10)}
+    per = {("krylov_vectors", 0): (10.0, 100, 8 * 10**10, 2 * 10**10)}
+    e = bench.roofline_entry(prof, per, 6769.4, "measured")
+    assert e["bound"] == "alu" and e["unit"] == "TFLOP/s"
+    assert abs(e["achieved"] - 2.0) < 1e-12
+    assert e["kernel"] == "krylov_vectors (level 0)"
+
+
+def test_spmv_is_hbm_bound_and_dominant_group_wins():
+    # FP32 SpMV, 8 bytes per stored entry and one FMA: 0.25 flop/B is far
+    # below the FP32 peak; the larger of two groups is reported
+    prof = {"f_smoother": (12.0, 60, 6 * 10**10), "restrict": (3.0, 10, 10**10)}
+    per = {("f_smoother", 0): (8.0, 30, 4 * 10**10, 10**10),
+           ("f_smoother", 3): (4.0, 30, 2 * 10**10, 5 * 10**9),
+           ("restrict", 0): (3.0, 10, 10**10, 2 * 10**9)}
+    e = bench.roofline_entry(prof, per, 6769.4, "measured", "f32")
+    assert e["bound"] == "hbm" and e["unit"] == "GB/s"
+    assert e["kernel"] == "f_smoother (level 0)"
+    assert abs(e["achieved"] - 4 * 10**10 / 8e-3 / 1e9) < 1e-6
+    assert abs(e["share"] - 8.0 / 15.0) < 1e-12
+    assert e["dtype"] == "f32"

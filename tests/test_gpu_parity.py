@@ -263,8 +263,9 @@ def test_richardson_outer_matches_oracle(prec):
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_slices_per_warp_never_changes_a_bit(prec, monkeypatch):
-    """The setup's timing-based choice of slices per warp (1, 2 or 4) only
-    changes how rows are mapped to warps: forcing each choice gives the
+    """The setup's timing-based choices -- slices per warp (1, 2 or 4) for
+    short rows, loads in flight per lane (4, 8 or 16) for long rows -- only
+    change how rows are mapped to threads: forcing each choice gives the
     same solution bit for bit."""
     w = workload("grid", (300, 257))
     vx, vy = velocity(w["theta"])
@@ -272,8 +273,9 @@ def test_slices_per_warp_never_changes_a_bit(prec, monkeypatch):
     b = G.airg_assemble_rhs_advection2d(pg, torch.tensor(w["g"][0], device="cuda"),
                                         torch.tensor(w["s"][0], device="cuda"))
     xs = []
-    for r in ["1", "2", "4"]:
+    for r, u in [("1", "4"), ("2", "8"), ("4", "16")]:
         monkeypatch.setenv("AIRG_ROWS_PER_WARP", r)
+        monkeypatch.setenv("AIRG_LOADS_PER_LANE", u)
         h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"],
                          G.airg_options_default(precision=prec, **w["opts"]))
         x, info = G.airg_solve(h, b, rtol=1e-10)

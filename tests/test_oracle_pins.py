@@ -266,7 +266,7 @@ def _diag_dominant(n, seed):
 
 @pytest.mark.parametrize("p", [1, 2, 4, 6])
 def test_gmres_coeffs_equal_bruteforce_least_squares(p):
-    """alpha minimises ||b - A q(A) b|| over degree-p polynomials (Eq. 4)."""
+    """alpha minimises ||b - A q(A) b|| over degree-p polynomials (Eq. 7)."""
     A, D = _diag_dominant(40, p)
     opts = O.Options(poly_order=p)
     alpha, k, broke = O.gmres_poly_coeffs(A, opts, 3)
