@@ -169,18 +169,20 @@ void copy_sell_f32(const Sell<double>& S, Sell<float>& out, cudaStream_t st)
 }
 
 // ------------------------------------------------------- nested ordering --
-__global__ void k_pos_coarse(int n, int off, int* pos)
+// Nested positions.  perm (may be null: identity) places the F points of a
+// level, or the coarsest level's unknowns, inside their block.
+__global__ void k_pos_coarse(int n, int off, const int* perm, int* pos)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) pos[i] = off + i;
+    if (i < n) pos[i] = off + (perm ? perm[i] : i);
 }
 
 __global__ void k_pos_level(int n, const int8_t* is_f, const int* f_index, const int* c_index,
-                            int off, const int* pos_next, int* pos)
+                            int off, const int* perm_f, const int* pos_next, int* pos)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    pos[i] = is_f[i] ? off + f_index[i] : pos_next[c_index[i]];
+    pos[i] = is_f[i] ? off + (perm_f ? perm_f[f_index[i]] : f_index[i]) : pos_next[c_index[i]];
 }
 
 __global__ void k_rel(int n, const int* pos, int off, int* rel, int* inv)
@@ -192,10 +194,18 @@ __global__ void k_rel(int n, const int* pos, int off, int* rel, int* inv)
     if (inv) inv[r] = i;
 }
 
-__global__ void k_map_w(int nf, const int* W, const int* rel, int* out)
+// W of F point i (C-local target) -> relative C position, stored at the F
+// point's position in its block
+__global__ void k_map_w(int nf, const int* W, const int* rel, const int* perm_f, int* out)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nf) out[i] = W[i] >= 0 ? rel[W[i]] : -1;
+    if (i < nf) out[perm_f ? perm_f[i] : i] = W[i] >= 0 ? rel[W[i]] : -1;
+}
+
+__global__ void k_invert_perm(int n, const int* perm, int* inv)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) inv[perm[i]] = i;
 }
 
 // ------------------------------------------------------- V-cycle kernels --
@@ -1148,6 +1158,40 @@ void tune_all(SolveData& S, cudaStream_t st)
 
 }  // namespace
 
+// Order of the rows of a block inside their window: within each window of
+// `win` consecutive rows (in the setup's order), rows sorted by decreasing
+// stored-entry count, ties by index.  Rows of one SELL slice then have
+// nearly equal lengths, which removes most of the slice padding (bytes and
+// the FMAs on padding) while keeping every row near its neighbours, so the
+// gathers of x stay local.  perm[i] = position of row i in the block; empty
+// for win <= 1.  A row's own arithmetic does not change.
+std::vector<int> window_sort_perm(const DevCSR& A, int win, cudaStream_t st)
+{
+    std::vector<int> perm;
+    const int n = A.n_rows;
+    if (win <= 1 || n == 0) return perm;
+    std::vector<int> rp(size_t(n) + 1);
+    d2h(rp.data(), A.rp.p, rp.size(), st);
+    perm.resize(n);
+    std::vector<int> idx;
+    for (int w0 = 0; w0 < n; w0 += win) {
+        const int w1 = std::min(n, w0 + win);
+        idx.resize(w1 - w0);
+        for (int i = w0; i < w1; ++i) idx[i - w0] = i;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+            return rp[a + 1] - rp[a] > rp[b + 1] - rp[b];
+        });
+        for (int q = 0; q < w1 - w0; ++q) perm[idx[q]] = w0 + q;
+    }
+    return perm;
+}
+
+int sort_window()
+{
+    const char* e = getenv("AIRG_SORT_WINDOW");
+    return e ? std::max(0, atoi(e)) : 256;
+}
+
 // ===========================================================================
 void build_solve_data(Hierarchy& H, cudaStream_t st)
 {
@@ -1160,15 +1204,30 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
     for (int l = 0; l < L; ++l) off[l + 1] = off[l] + H.levels[l]->n_f;
     S->off_c = off[L];
     S->n_coarse = H.coarse.A.n_rows;
+    // row order inside the F blocks and the coarsest block (window sort)
+    const int win = sort_window();
+    std::vector<DBuf<int>> perm(L + 1), iperm(L + 1);
+    auto upload_perm = [&](const DevCSR& A, int l) {
+        std::vector<int> p = window_sort_perm(A, win, st);
+        if (p.empty()) return;
+        perm[l].alloc(p.size());
+        iperm[l].alloc(p.size());
+        h2d(perm[l].p, p.data(), p.size(), st);
+        k_invert_perm<<<grid_for((long long)p.size(), TB), TB, 0, st>>>(int(p.size()), perm[l].p, iperm[l].p);
+        CK_LAUNCH();
+    };
+    for (int l = 0; l < L; ++l) upload_perm(H.levels[l]->A_ff, l);
+    upload_perm(H.coarse.A, L);
     // nested positions, coarsest upward
     std::vector<DBuf<int>> pos(L + 1);
     pos[L].alloc(std::max(S->n_coarse, 1));
-    if (S->n_coarse) k_pos_coarse<<<grid_for(S->n_coarse, TB), TB, 0, st>>>(S->n_coarse, off[L], pos[L].p);
+    if (S->n_coarse)
+        k_pos_coarse<<<grid_for(S->n_coarse, TB), TB, 0, st>>>(S->n_coarse, off[L], perm[L].p, pos[L].p);
     for (int l = L - 1; l >= 0; --l) {
         SetupLevel& lv = *H.levels[l];
         pos[l].alloc(lv.n);
         k_pos_level<<<grid_for(lv.n, TB), TB, 0, st>>>(lv.n, lv.is_f.p, lv.f_index.p, lv.c_index.p,
-                                                       off[l], pos[l + 1].p, pos[l].p);
+                                                       off[l], perm[l].p, pos[l + 1].p, pos[l].p);
     }
     CK_LAUNCH();
     // level operators
@@ -1184,11 +1243,12 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         DBuf<int> rel(std::max(lv.n_c, 1)), inv(std::max(lv.n_c, 1));
         if (lv.n_c)
             k_rel<<<grid_for(lv.n_c, TB), TB, 0, st>>>(lv.n_c, pos[l + 1].p, off[l + 1], rel.p, inv.p);
-        build_sell<double>(lv.A_ff, nullptr, nullptr, lv.n_f, sl->d.Aff, true, st);
-        build_sell<double>(lv.M, nullptr, rel.p, lv.n_c, sl->d.M, false, st);
-        build_sell<double>(lv.Z, inv.p, nullptr, lv.n_f, sl->d.Z, false, st);
+        // SELL row r of A_ff / M is the F point at position r of the block
+        build_sell<double>(lv.A_ff, iperm[l].p, perm[l].p, lv.n_f, sl->d.Aff, true, st);
+        build_sell<double>(lv.M, iperm[l].p, rel.p, lv.n_c, sl->d.M, false, st);
+        build_sell<double>(lv.Z, inv.p, perm[l].p, lv.n_f, sl->d.Z, false, st);
         sl->W.alloc(std::max(lv.n_f, 1));
-        if (lv.n_f) k_map_w<<<grid_for(lv.n_f, TB), TB, 0, st>>>(lv.n_f, lv.W.p, rel.p, sl->W.p);
+        if (lv.n_f) k_map_w<<<grid_for(lv.n_f, TB), TB, 0, st>>>(lv.n_f, lv.W.p, rel.p, perm[l].p, sl->W.p);
         CK_LAUNCH();
         if (H.opt.precision == AIRG_MIXED_FP32) {
             copy_sell_f32(sl->d.Aff, sl->f.Aff, st);
@@ -1203,7 +1263,7 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         CK(cudaStreamSynchronize(st));
         S->lv.push_back(std::move(sl));
     }
-    build_sell<double>(H.coarse.A, nullptr, nullptr, S->n_coarse, S->Ac, true, st);
+    build_sell<double>(H.coarse.A, iperm[L].p, perm[L].p, S->n_coarse, S->Ac, true, st);
     if (H.opt.precision == AIRG_MIXED_FP32) copy_sell_f32(S->Ac, S->Ac32, st);
     S->roots = H.coarse.roots;
     {
