@@ -42,7 +42,7 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c2",
-                    choices=["c1", "c2", "c3", "c3_fp64", "c4a", "c4a_fp64", "c4b"])
+                    choices=["c1", "c2", "c3", "c3_fp64", "c3_bf16", "c4a", "c4a_fp64", "c4a_bf16", "c4b"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
 
@@ -393,7 +393,7 @@ def run_gpu(args):
     G.airg_profile(h, False)
     peak, peak_kind = measured_peaks()
     roofline = roofline_entry(prof, per_level, peak, peak_kind,
-                              "f32" if w["opts"].get("precision") == 1 else "f64")
+                              "f32" if w["opts"].get("precision", 0) in (1, 2) else "f64")
     vc_bytes = sinfo["bytes_per_vcycle"]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("c1", "c2"):
@@ -405,7 +405,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32/f64" if w["opts"].get("precision") == 1 else "f64",
+            "vs_baseline": None, "dtype": {0: "f64", 1: "f32/f64", 2: "bf16/f32/f64"}[w["opts"].get("precision", 0)],
             "data": "synthetic",
             "config": {"workload": w["desc"], "n": n, "nrhs": k, "rtol": w["rtol"],
                        "parallelism": "replicas" if world > 1 else "single",

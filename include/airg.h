@@ -45,7 +45,10 @@ typedef enum {
     AIRG_ERR_STATE = 7           /* handle not in a state that allows the call  */
 } airg_status;
 
-enum { AIRG_FP64 = 0, AIRG_MIXED_FP32 = 1 };
+/* Precision of the V-cycle: FP64; FP32 (vectors, operators, polynomials);
+ * FP32 with the restrictor values Z (R = [Z I], Eq. 4) stored in bfloat16.
+ * The outer iteration, its orthogonalisation and residuals stay FP64. */
+enum { AIRG_FP64 = 0, AIRG_MIXED_FP32 = 1, AIRG_MIXED_FP32_BF16R = 2 };
 /* Outer iteration around the V-cycle: flexible GMRES (default), or the
  * preconditioned Richardson iteration x <- x + M^-1 (b - A x) of Sec. 3. */
 enum { AIRG_OUTER_FGMRES = 0, AIRG_OUTER_RICHARDSON = 1 };
@@ -83,7 +86,7 @@ typedef struct {
                                   (the polynomial already inverts exactly)   */
     double addroot_log10;      /* extra-root threshold on log10(pof)          */
     double addroot_per;        /* decades of pof per extra root               */
-    int precision;             /* AIRG_FP64 or AIRG_MIXED_FP32 (V-cycle)      */
+    int precision;             /* AIRG_FP64, AIRG_MIXED_FP32, _BF16R           */
     int gmres_restart;         /* outer FGMRES restart length                 */
     int outer;                 /* AIRG_OUTER_FGMRES or AIRG_OUTER_RICHARDSON  */
 } airg_options;

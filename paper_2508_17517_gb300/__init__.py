@@ -20,6 +20,7 @@ AIRG_OUTER_FGMRES = 0
 AIRG_OUTER_RICHARDSON = 1
 AIRG_FP64 = 0
 AIRG_MIXED_FP32 = 1
+AIRG_MIXED_FP32_BF16R = 2
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_BREAKDOWN",
                 5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_STATE"}
 

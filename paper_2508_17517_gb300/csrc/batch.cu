@@ -34,8 +34,8 @@ inline int grid_rows(long long n) { return grid_for(n * 32, BT); }
 
 // acc[j] = (row r of S) x[:, q], q = lane + 32 j: the dense diagonal term
 // (square operators) first, then the stored entries in slice order
-template <class T, int KW>
-__device__ __forceinline__ void brow(const SellView<T>& S, int r, const T* __restrict__ x, int k,
+template <class T, int KW, class V = T>
+__device__ __forceinline__ void brow(const SellView<T, V>& S, int r, const T* __restrict__ x, int k,
                                      int lane, T (&acc)[KW])
 {
     const T dg = S.diag ? __ldg(S.diag + r) : T(0);
@@ -48,7 +48,7 @@ __device__ __forceinline__ void brow(const SellView<T>& S, int r, const T* __res
     const int b = S.sptr[s] + (r & 31), w = (S.sptr[s + 1] - S.sptr[s]) >> 5;
     for (int e = 0; e < w; ++e) {
         const int idx = b + 32 * e;
-        const T v = __ldg(S.val + idx);
+        const T v = ldval<T>(S.val + idx);
         const T* xr = x + size_t(__ldg(S.col + idx)) * k;
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
@@ -77,13 +77,13 @@ __global__ void kb_spmv(SellView<T> S, const T* __restrict__ x, T* __restrict__ 
     }
 }
 
-template <class T, int KW>
-__global__ void kb_restrict(SellView<T> Z, const T* __restrict__ sf, const T* __restrict__ sc,
+template <class T, int KW, class V = T>
+__global__ void kb_restrict(SellView<T, V> Z, const T* __restrict__ sf, const T* __restrict__ sc,
                             T* __restrict__ dc, int k)
 {
     BROW_IDS(Z.n_rows);
     T a[KW];
-    brow<T, KW>(Z, r, sf, k, lane, a);
+    brow<T, KW, V>(Z, r, sf, k, lane, a);
 #pragma unroll
     for (int j = 0; j < KW; ++j) {
         int q = lane + 32 * j;
@@ -433,8 +433,15 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         const SolveLevel& lv = *S.lv[l];
         const T* src = l == 0 ? v : wk.rwork;
         const Sell<T>& Z = bops<T>(lv).Z;
+        const Sell<T, bf16s>& Zb = bops<T>(lv).Zb;
         S.cur_level = l;
-        if (lv.n_c)
+        if (lv.n_c && Zb.val.n)
+            LAUNCH_F(S, PK_RESTRICT, mat_bytes(Zb) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
+                     (2 * Zb.nnz + lv.n_c) * kk,
+                     WITH_KW(k, kb_restrict<T, KW, bf16s><<<grid_rows(lv.n_c), BT, 0, st>>>(
+                                    view(Zb), src + size_t(lv.off) * k, src + size_t(lv.off + lv.n_f) * k,
+                                    wk.rwork + size_t(lv.off + lv.n_f) * k, k)));
+        else if (lv.n_c)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
                      (2 * Z.nnz + lv.n_c) * kk,
                    WITH_KW(k, kb_restrict<T, KW><<<grid_rows(lv.n_c), BT, 0, st>>>(
@@ -517,7 +524,7 @@ void bprecond_launch(Hierarchy& H, BatchData& B, const double* v, double* z, cud
 {
     SolveData& S = *H.solve;
     long long nk = B.nk;
-    if (H.opt.precision == AIRG_MIXED_FP32) {
+    if (mixed_precision(H.opt)) {
         LAUNCH(S, PK_LAYOUT, 12 * nk, kb_d2f<<<grid_for(nk, BT), BT, 0, st>>>(nk, v, B.vin32.p));
         BWork<float> wk{B.rwork32.p, B.t32.p, B.wa32.p, B.wb32.p, B.cr032.p, B.cr132.p, B.ct32.p};
         bvcycle<float>(S, B.k, B.vin32.p, B.e32.p, wk, st);
@@ -586,7 +593,7 @@ void ensure_batch(Hierarchy& H, int k)
     B->ticket.alloc(1);
     CK(cudaMemset(B->ticket.p, 0, sizeof(unsigned)));
     size_t nf = size_t(std::max(S.max_nf, 1)) * k, nc = size_t(std::max(S.n_coarse, 1)) * k;
-    if (H.opt.precision == AIRG_MIXED_FP32) {
+    if (mixed_precision(H.opt)) {
         B->rwork32.alloc(nk); B->e32.alloc(nk); B->vin32.alloc(nk);
         B->t32.alloc(nf); B->wa32.alloc(nf); B->wb32.alloc(nf);
         B->cr032.alloc(nc); B->cr132.alloc(nc); B->ct32.alloc(nc);

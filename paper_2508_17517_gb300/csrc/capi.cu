@@ -122,7 +122,8 @@ void check_options(const airg_options& o)
     if (o.gmres_restart < 1 || o.gmres_restart > 30) airg::fail(AIRG_ERR_ARG, "gmres_restart must be in [1, 30]");
     if (o.ddc_its < 0 || !(o.ddc_fraction >= 0.0 && o.ddc_fraction <= 1.0))
         airg::fail(AIRG_ERR_ARG, "bad DDC options");
-    if (o.precision != AIRG_FP64 && o.precision != AIRG_MIXED_FP32) airg::fail(AIRG_ERR_ARG, "bad precision");
+    if (o.precision != AIRG_FP64 && o.precision != AIRG_MIXED_FP32 && o.precision != AIRG_MIXED_FP32_BF16R)
+        airg::fail(AIRG_ERR_ARG, "bad precision");
     if (o.outer != AIRG_OUTER_FGMRES && o.outer != AIRG_OUTER_RICHARDSON) airg::fail(AIRG_ERR_ARG, "bad outer");
 }
 

@@ -145,6 +145,40 @@ __global__ void k_f2d(long long n, const float* a, double* b)
     if (i < n) b[i] = (double)a[i];
 }
 
+// FP64 value -> FP32 (round to nearest) -> bfloat16, rounding the 16
+// dropped bits to nearest with ties to even (NaN kept quiet)
+__global__ void k_d2bf(long long n, const double* a, bf16s* b)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned u = __float_as_uint(__double2float_rn(a[i]));
+    unsigned short h;
+    if ((u & 0x7fffffffu) > 0x7f800000u) h = (unsigned short)((u >> 16) | 0x0040u);
+    else h = (unsigned short)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+    b[i].bits = h;
+}
+
+// the FP64 operator S with its values rounded to bfloat16 (no diagonal split)
+void copy_sell_bf16(const Sell<double>& S, Sell<float, bf16s>& out, cudaStream_t st)
+{
+    if (S.ndiag) fail(AIRG_ERR_STATE, "bfloat16 copy of an operator with a dense diagonal");
+    out.n_rows = S.n_rows;
+    out.n_cols = S.n_cols;
+    out.n_slices = S.n_slices;
+    out.k = S.k;
+    out.r = S.r;
+    out.nnz = S.nnz;
+    out.padded = S.padded;
+    out.ndiag = 0;
+    out.sptr.alloc(S.sptr.n);
+    out.col.alloc(S.col.n);
+    out.val.alloc(S.val.n);
+    CK(cudaMemcpyAsync(out.sptr.p, S.sptr.p, S.sptr.bytes(), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(out.col.p, S.col.p, S.col.bytes(), cudaMemcpyDeviceToDevice, st));
+    if (S.val.n) k_d2bf<<<grid_for(S.val.n, TB), TB, 0, st>>>((long long)S.val.n, S.val.p, out.val.p);
+    CK_LAUNCH();
+}
+
 void copy_sell_f32(const Sell<double>& S, Sell<float>& out, cudaStream_t st)
 {
     out.n_rows = S.n_rows;
@@ -215,29 +249,44 @@ __global__ void k_invert_perm(int n, const int* perm, int* inv)
 // group's first lane.  Every lane of a warp reaches the shuffles.
 // Sum of val[idx] * x[col[idx]] over idx = first, first + stride, ... < end.
 // The j-th entry of the sequence goes to partial sum j mod 4 (each partial
-// in entry order) and the result is (p0 + p1) + (p2 + p3), whatever U is.  U
-// entries' loads are issued before their gathers, so each lane keeps U
-// memory requests in flight (the gathers depend on the column loads).
-template <class T, int U = 4>
-__device__ __forceinline__ T strided_dot(const int* __restrict__ col, const T* __restrict__ val,
+// in entry order) and the result is (p0 + p1) + (p2 + p3), whatever U is.
+// Full chunks of U entries issue their U loads before their gathers, so
+// each lane keeps U requests in flight; the remainder runs in chunks of 4,
+// so at most 3 issued slots per row carry no entry (predicated slots still
+// occupy the FP64 pipe, which is the scarce unit for FP64 on this part).
+template <class T, int U = 4, class V = T>
+__device__ __forceinline__ T strided_dot(const int* __restrict__ col, const V* __restrict__ val,
                                          const T* __restrict__ x, int idx, int end, int stride)
 {
     static_assert(U % 4 == 0, "U must be a multiple of 4");
     T a[4] = {T(0), T(0), T(0), T(0)};
-    for (; idx < end; idx += U * stride) {
+    for (; idx + (U - 1) * stride < end; idx += U * stride) {
         int c[U];
         T v[U], xv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const bool ok = idx + u * stride < end;
-            c[u] = ok ? __ldg(col + idx + u * stride) : 0;
-            v[u] = ok ? __ldg(val + idx + u * stride) : T(0);
+            c[u] = __ldg(col + idx + u * stride);
+            v[u] = ldval<T>(val + idx + u * stride);
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) xv[u] = idx + u * stride < end ? x[c[u]] : T(0);
+        for (int u = 0; u < U; ++u) xv[u] = x[c[u]];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (idx + u * stride < end) a[u % 4] = fma(v[u], xv[u], a[u % 4]);
+        for (int u = 0; u < U; ++u) a[u % 4] = fma(v[u], xv[u], a[u % 4]);
+    }
+    for (; idx < end; idx += 4 * stride) {
+        int c[4];
+        T v[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool ok = idx + u * stride < end;
+            c[u] = ok ? __ldg(col + idx + u * stride) : 0;
+            v[u] = ok ? ldval<T>(val + idx + u * stride) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = idx + u * stride < end ? x[c[u]] : T(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (idx + u * stride < end) a[u] = fma(v[u], xv[u], a[u]);
     }
     return (a[0] + a[1]) + (a[2] + a[3]);
 }
@@ -246,8 +295,8 @@ __device__ __forceinline__ T strided_dot(const int* __restrict__ col, const T* _
 // that share the slice (part = this warp's index among them).  Every thread
 // of the block must call it (it synchronises the block when P > 1).  The
 // sum is valid in the part-0 warp, which also adds the dense diagonal.
-template <class T, int P, int U = 4>
-__device__ __forceinline__ T row_dot(const SellView<T>& S, int slice, int lane, int part,
+template <class T, int P, int U = 4, class V = T>
+__device__ __forceinline__ T row_dot(const SellView<T, V>& S, int slice, int lane, int part,
                                      const T* __restrict__ x)
 {
     T acc = T(0);
@@ -278,8 +327,8 @@ __device__ __forceinline__ T row_dot(const SellView<T>& S, int slice, int lane, 
 // below runs, so the slices-per-warp choice never changes a result bit.
 // When every slice is at most 4 wide, all loads of the R rows are issued
 // (predicated) before their gathers, and all gathers before the sums.
-template <class T, int R>
-__device__ __forceinline__ void dot_slices(const SellView<T>& S, const T* __restrict__ x, int s0, int lane,
+template <class T, int R, class V>
+__device__ __forceinline__ void dot_slices(const SellView<T, V>& S, const T* __restrict__ x, int s0, int lane,
                                            T (&acc)[R])
 {
     int b[R], w[R];
@@ -304,7 +353,7 @@ __device__ __forceinline__ void dot_slices(const SellView<T>& S, const T* __rest
             for (int u = 0; u < 4; ++u) {
                 const bool ok = u < w[q];
                 c[q][u] = ok ? __ldg(S.col + b[q] + 32 * u) : 0;
-                v[q][u] = ok ? __ldg(S.val + b[q] + 32 * u) : T(0);
+                v[q][u] = ok ? ldval<T>(S.val + b[q] + 32 * u) : T(0);
             }
 #pragma unroll
         for (int q = 0; q < R; ++q)
@@ -325,7 +374,7 @@ __device__ __forceinline__ void dot_slices(const SellView<T>& S, const T* __rest
                 for (int u = 0; u < 4; ++u) {
                     const bool ok = u0 + u < w[q];
                     c[u] = ok ? __ldg(S.col + b[q] + 32 * (u0 + u)) : 0;
-                    v[u] = ok ? __ldg(S.val + b[q] + 32 * (u0 + u)) : T(0);
+                    v[u] = ok ? ldval<T>(S.val + b[q] + 32 * (u0 + u)) : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) xv[u] = u0 + u < w[q] ? x[c[u]] : T(0);
@@ -342,8 +391,8 @@ __device__ __forceinline__ void dot_slices(const SellView<T>& S, const T* __rest
 // overlap them.  K = warps per slice.  R = slices per warp for K = 1, and
 // loads in flight per lane (4, 8 or 16) for K > 1; in neither case does R
 // change the arithmetic.
-template <class T, int K, int R, class Pre, class Epi>
-__device__ __forceinline__ void for_rows(const SellView<T>& S, const T* __restrict__ x, const Pre& pre,
+template <class T, int K, int R, class V, class Pre, class Epi>
+__device__ __forceinline__ void for_rows(const SellView<T, V>& S, const T* __restrict__ x, const Pre& pre,
                                          const Epi& epi)
 {
     using PV = decltype(pre(0));
@@ -357,7 +406,7 @@ __device__ __forceinline__ void for_rows(const SellView<T>& S, const T* __restri
             pv[q] = r < S.n_rows ? pre(r) : PV{};
         }
         T acc[R];
-        dot_slices<T, R>(S, x, s0, lane, acc);
+        dot_slices<T, R, V>(S, x, s0, lane, acc);
 #pragma unroll
         for (int q = 0; q < R; ++q) {
             const int r = (s0 + q) * 32 + lane;
@@ -369,7 +418,7 @@ __device__ __forceinline__ void for_rows(const SellView<T>& S, const T* __restri
         const int r = slice * 32 + lane;
         const bool lead = part == 0 && r < S.n_rows;
         PV pv = lead ? pre(r) : PV{};
-        T d = row_dot<T, K, R>(S, slice, lane, part, x);
+        T d = row_dot<T, K, R, V>(S, slice, lane, part, x);
         if (lead) epi(r, d, pv);
     }
 }
@@ -380,15 +429,16 @@ struct Pair {
 };
 
 // y = S x
-template <class T, int K, int R>
-__global__ void k_spmv(SellView<T> S, const T* __restrict__ x, T* __restrict__ y)
+template <class T, int K, int R, class V = T>
+__global__ void k_spmv(SellView<T, V> S, const T* __restrict__ x, T* __restrict__ y)
 {
     for_rows<T, K, R>(S, x, [](int) { return 0; }, [&](int r, T d, int) { y[r] = d; });
 }
 
-// restriction (R = [Z I] of Eq. 4): dst_c[k] = src_c[k] + (Z src_f)[k]
-template <class T, int K, int R>
-__global__ void k_restrict(SellView<T> Z, const T* __restrict__ src_f, const T* __restrict__ src_c,
+// restriction (R = [Z I] of Eq. 4): dst_c[k] = src_c[k] + (Z src_f)[k]; the
+// values of Z may be stored narrower than T (V)
+template <class T, int K, int R, class V = T>
+__global__ void k_restrict(SellView<T, V> Z, const T* __restrict__ src_f, const T* __restrict__ src_c,
                            T* __restrict__ dst_c)
 {
     for_rows<T, K, R>(Z, src_f, [&](int r) { return src_c[r]; },
@@ -517,15 +567,15 @@ inline int bk(int P) { return 32 * wpb_for(P); }
 
 // Grid and block of the row kernels for operator S: K = S.k warps per slice,
 // or (K = 1) S.r slices per warp.
-template <class T>
-inline int grid_rows(const Sell<T>& S)
+template <class T, class V>
+inline int grid_rows(const Sell<T, V>& S)
 {
     if (S.k > 1) return gk(S.n_rows, S.k);
     long long warps = (S.n_slices + S.r - 1) / S.r;
     return grid_for(warps, wpb_for(1));
 }
-template <class T>
-inline int block_rows(const Sell<T>& S) { return bk(S.k); }
+template <class T, class V>
+inline int block_rows(const Sell<T, V>& S) { return bk(S.k); }
 
 // Runs the statement with compile-time KK (warps per slice) and RR (slices
 // per warp for KK = 1, loads in flight per lane for KK > 1) of operator S.
@@ -942,8 +992,14 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         const SolveLevel& lv = *S.lv[l];
         const T* src = l == 0 ? v : wk.rwork;
         const Sell<T>& Z = ops<T>(lv).Z;
+        const Sell<T, bf16s>& Zb = ops<T>(lv).Zb;
         S.cur_level = l;
-        if (lv.n_c)
+        if (lv.n_c && Zb.val.n)
+            LAUNCH_F(S, PK_RESTRICT, mat_bytes(Zb) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Zb.nnz + lv.n_c,
+                   WITH_KR(Zb, k_restrict<T, KK, RR, bf16s><<<grid_rows(Zb), block_rows(Zb), 0, st>>>(
+                                   view(Zb), src + lv.off, src + lv.off + lv.n_f,
+                                   wk.rwork + lv.off + lv.n_f)));
+        else if (lv.n_c)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Z.nnz + lv.n_c,
                    WITH_KR(Z, k_restrict<T, KK, RR><<<grid_rows(Z), block_rows(Z), 0, st>>>(
                                   view(Z), src + lv.off, src + lv.off + lv.n_f,
@@ -1091,8 +1147,8 @@ long long sell_bytes(const Sell<double>& S, int vbytes)
 // per lane r = 4, 8, 16 for long rows (several warps per slice).  Neither
 // changes the arithmetic.  forced > 0 (AIRG_ROWS_PER_WARP for short rows,
 // AIRG_LOADS_PER_LANE for long rows) skips the timing.
-template <class T>
-void tune_rows(Sell<T>& A, const T* x, T* y, int forced_short, int forced_long, cudaStream_t st)
+template <class T, class V>
+void tune_rows(Sell<T, V>& A, const T* x, T* y, int forced_short, int forced_long, cudaStream_t st)
 {
     if (A.n_rows == 0) return;
     const int forced = A.k == 1 ? forced_short : forced_long;
@@ -1109,12 +1165,12 @@ void tune_rows(Sell<T>& A, const T* x, T* y, int forced_short, int forced_long, 
     const int* cand = A.k == 1 ? cand_short : cand_long;
     for (int ci = 0; ci < 3; ++ci) {
         A.r = cand[ci];
-        SellView<T> v = view(A);
-        WITH_KR(A, k_spmv<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(v, x, y));
+        SellView<T, V> v = view(A);
+        WITH_KR(A, k_spmv<T, KK, RR, V><<<grid_rows(A), block_rows(A), 0, st>>>(v, x, y));
         CK_LAUNCH();
         CK(cudaEventRecord(e0, st));
         for (int rep = 0; rep < 3; ++rep)
-            WITH_KR(A, k_spmv<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(v, x, y));
+            WITH_KR(A, k_spmv<T, KK, RR, V><<<grid_rows(A), block_rows(A), 0, st>>>(v, x, y));
         CK(cudaEventRecord(e1, st));
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -1151,6 +1207,7 @@ void tune_all(SolveData& S, cudaStream_t st)
         tune_rows(o.Aff, x.p, y.p, fs, fl, st);
         tune_rows(o.M, x.p, y.p, fs, fl, st);
         tune_rows(o.Z, x.p, y.p, fs, fl, st);
+        tune_rows(o.Zb, x.p, y.p, fs, fl, st);
     }
     tune_rows(const_cast<Sell<T>&>(coarse_op<T>(S)), x.p, y.p, fs, fl, st);
     CK(cudaStreamSynchronize(st));
@@ -1250,21 +1307,24 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         sl->W.alloc(std::max(lv.n_f, 1));
         if (lv.n_f) k_map_w<<<grid_for(lv.n_f, TB), TB, 0, st>>>(lv.n_f, lv.W.p, rel.p, perm[l].p, sl->W.p);
         CK_LAUNCH();
-        if (H.opt.precision == AIRG_MIXED_FP32) {
+        if (mixed_precision(H.opt)) {
             copy_sell_f32(sl->d.Aff, sl->f.Aff, st);
             copy_sell_f32(sl->d.M, sl->f.M, st);
-            copy_sell_f32(sl->d.Z, sl->f.Z, st);
+            if (H.opt.precision == AIRG_MIXED_FP32_BF16R) copy_sell_bf16(sl->d.Z, sl->f.Zb, st);
+            else copy_sell_f32(sl->d.Z, sl->f.Z, st);
         }
-        int vb = H.opt.precision == AIRG_MIXED_FP32 ? 4 : 8;
+        int vb = mixed_precision(H.opt) ? 4 : 8;
         int p = int(lv.alpha.size()) - 1;
-        bytes += sell_bytes(sl->d.Z, vb) + sell_bytes(sl->d.M, vb) + 4LL * lv.n_f +
+        bytes += (H.opt.precision == AIRG_MIXED_FP32_BF16R ? sell_bytes(sl->d.Z, vb) - 2LL * lv.Z.nnz
+                                                            : sell_bytes(sl->d.Z, vb)) +
+                 sell_bytes(sl->d.M, vb) + 4LL * lv.n_f +
                  p * sell_bytes(sl->d.Aff, vb) + 2LL * lv.n_f * vb;
         S->max_nf = std::max(S->max_nf, lv.n_f);
         CK(cudaStreamSynchronize(st));
         S->lv.push_back(std::move(sl));
     }
     build_sell<double>(H.coarse.A, iperm[L].p, perm[L].p, S->n_coarse, S->Ac, true, st);
-    if (H.opt.precision == AIRG_MIXED_FP32) copy_sell_f32(S->Ac, S->Ac32, st);
+    if (mixed_precision(H.opt)) copy_sell_f32(S->Ac, S->Ac32, st);
     S->roots = H.coarse.roots;
     {
         std::vector<double> rr;
@@ -1279,13 +1339,13 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         std::string pv = pe ? pe : "";
         bool allow = pv == "1" || pv == "coarse";
         bool allow_s = pv == "1" || pv == "smoother";
-        if (allow && H.opt.precision != AIRG_MIXED_FP32) S->newton_grid[0] = newton_persistent_grid<double>(S->Ac);
-        if (allow && H.opt.precision == AIRG_MIXED_FP32) S->newton_grid[1] = newton_persistent_grid<float>(S->Ac32);
+        if (allow && !mixed_precision(H.opt)) S->newton_grid[0] = newton_persistent_grid<double>(S->Ac);
+        if (allow && mixed_precision(H.opt)) S->newton_grid[1] = newton_persistent_grid<float>(S->Ac32);
         if (allow_s) {
             int dev = 0, sms = 0, per = 0;
             CK(cudaGetDevice(&dev));
             CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-            if (H.opt.precision != AIRG_MIXED_FP32) {
+            if (!mixed_precision(H.opt)) {
                 CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_smooth_persistent<double>, 1024, 0));
                 S->smooth_grid[0] = per * sms;
             } else {
@@ -1297,7 +1357,7 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
     S->ticket.alloc(1);
     CK(cudaMemsetAsync(S->ticket.p, 0, sizeof(unsigned), st));
     {
-        int vb = H.opt.precision == AIRG_MIXED_FP32 ? 4 : 8;
+        int vb = mixed_precision(H.opt) ? 4 : 8;
         long long nsp = 0;
         for (size_t i = 0; i < S->roots.size(); ++i) {
             bool last = i + 1 == S->roots.size();
@@ -1318,7 +1378,7 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         CK(cudaStreamSynchronize(st));
     }
     // slices per warp of the short-row operators, by timing
-    if (H.opt.precision == AIRG_MIXED_FP32) tune_all<float>(*S, st);
+    if (mixed_precision(H.opt)) tune_all<float>(*S, st);
     else tune_all<double>(*S, st);
     {
         DBuf<double> x(std::max(S->n0, 1)), y(std::max(S->n0, 1));
@@ -1332,7 +1392,7 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
     S->rwork.alloc(n0);
     S->t.alloc(nf); S->wa.alloc(nf); S->wb.alloc(nf);
     S->cr0.alloc(nc); S->cr1.alloc(nc); S->ct.alloc(nc);
-    if (H.opt.precision == AIRG_MIXED_FP32) {
+    if (mixed_precision(H.opt)) {
         S->rwork32.alloc(n0); S->e32.alloc(n0); S->vin32.alloc(n0);
         S->t32.alloc(nf); S->wa32.alloc(nf); S->wb32.alloc(nf);
         S->cr032.alloc(nc); S->cr132.alloc(nc); S->ct32.alloc(nc);
@@ -1399,7 +1459,7 @@ void precond_launch(Hierarchy& H, const double* v, double* z, cudaStream_t st)
 {
     SolveData& S = *H.solve;
     long long n = S.n0;
-    if (H.opt.precision == AIRG_MIXED_FP32) {
+    if (mixed_precision(H.opt)) {
         LAUNCH(S, PK_LAYOUT, 12 * n, k_d2f<<<grid_for(n, TB), TB, 0, st>>>(n, v, S.vin32.p));
         VWork<float> wk{S.rwork32.p, S.t32.p, S.wa32.p, S.wb32.p, nullptr, S.cr032.p, S.cr132.p, S.ct32.p};
         vcycle<float>(S, S.vin32.p, S.e32.p, wk, st);

@@ -37,37 +37,67 @@ enum { PK_RESTRICT = 0, PK_FRESID = 1, PK_HORNER = 2, PK_NEWTON = 3, PK_TOPSPMV 
 // multiplied with coalesced loads, no column index) and only the
 // off-diagonal entries in the slices; ndiag counts the diagonal entries
 // split out this way (0 when there is no split).
-template <class T>
+// FP32 V-cycle (with FP32 or bfloat16 restrictor values)
+inline bool mixed_precision(const airg_options& o)
+{
+    return o.precision == AIRG_MIXED_FP32 || o.precision == AIRG_MIXED_FP32_BF16R;
+}
+
+// Stored values may be narrower than the arithmetic type T: V = bf16s keeps
+// bfloat16 values (the upper 16 bits of an FP32 number), widened exactly to
+// FP32 when loaded.
+struct bf16s {
+    unsigned short bits;
+};
+
+template <class T, class V = T>
 struct Sell {
     int n_rows = 0, n_cols = 0, n_slices = 0, k = 1, r = 1;
     long long nnz = 0, padded = 0, ndiag = 0;
     DBuf<int> sptr;
     DBuf<int> col;
-    DBuf<T> val;
+    DBuf<V> val;
     DBuf<T> diag;
 };
 
-template <class T>
+template <class T, class V = T>
 struct SellView {
     int n_rows, n_slices;
     const int* __restrict__ sptr;
     const int* __restrict__ col;
-    const T* __restrict__ val;
+    const V* __restrict__ val;
     const T* __restrict__ diag;   // nullptr: no diagonal split
 };
 
-template <class T>
-SellView<T> view(const Sell<T>& s)
+template <class T, class V>
+SellView<T, V> view(const Sell<T, V>& s)
 {
-    return SellView<T>{s.n_rows, s.n_slices, s.sptr.p, s.col.p, s.val.p, s.ndiag ? s.diag.p : nullptr};
+    return SellView<T, V>{s.n_rows, s.n_slices, s.sptr.p, s.col.p, s.val.p, s.ndiag ? s.diag.p : nullptr};
+}
+
+// stored value -> arithmetic type
+template <class T, class V>
+__device__ __forceinline__ T ldval(const V* p)
+{
+    return T(__ldg(p));
+}
+template <>
+__device__ __forceinline__ float ldval<float, bf16s>(const bf16s* p)
+{
+    return __uint_as_float(unsigned(__ldg(reinterpret_cast<const unsigned short*>(p))) << 16);
+}
+template <>
+__device__ __forceinline__ double ldval<double, bf16s>(const bf16s* p)
+{
+    return double(ldval<float, bf16s>(p));
 }
 
 // algorithmic bytes of the stored entries: value + 4-byte column index per
 // entry, value only for a diagonal held densely
-template <class T>
-long long mat_bytes(const Sell<T>& s)
+template <class T, class V>
+long long mat_bytes(const Sell<T, V>& s)
 {
-    return (s.nnz - s.ndiag) * (long long)(sizeof(T) + 4) + s.ndiag * (long long)sizeof(T);
+    return (s.nnz - s.ndiag) * (long long)(sizeof(V) + 4) + s.ndiag * (long long)sizeof(T);
 }
 
 // Warps per slice from the mean row length: the smallest power of two that
@@ -95,6 +125,7 @@ __host__ __device__ constexpr int wpb_for(int P) { return P > 8 ? P : 8; }
 template <class T>
 struct SolveLevelT {
     Sell<T> Z, M, Aff;
+    Sell<T, bf16s> Zb;   // Z with bfloat16 values (precision AIRG_MIXED_FP32_BF16R)
 };
 
 struct SolveLevel {

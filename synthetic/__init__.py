@@ -41,18 +41,20 @@ def workload(name, n=None):
         return dict(nx=nx, ny=ny, theta=th, g=g, s=None, n_rhs=1, rtol=1e-10,
                     opts=dict(coarse_poly_order=30, trunc_rtol=1e-2),
                     desc="%dx%d theta~U[pi/12,5pi/12] g~U[0.5,2] m_c=30 trunc=1e-2" % (nx, ny))
-    if name in ("c3", "c3_fp64"):
+    if name in ("c3", "c3_fp64", "c3_bf16"):
         # 4096x4096, seeded theta, g ~ U[0,1] per inflow node; FP32 V-cycle
-        # inside FP64 FGMRES ("c3_fp64": the same problem with an FP64 V-cycle)
+        # inside FP64 FGMRES ("c3_fp64": the same problem with an FP64 V-cycle;
+        # "c3_bf16": FP32 V-cycle with the restrictor values in bfloat16)
         nx = ny = n or 4096
         rng = np.random.default_rng(BASE_SEED + 3)
         th = float(rng.uniform(math.pi / 12, 5 * math.pi / 12))
         g = rng.uniform(0.0, 1.0, (1, _n_inflow(nx, ny, th)))
-        prec = 1 if name == "c3" else 0
+        prec = {"c3": 1, "c3_fp64": 0, "c3_bf16": 2}[name]
         return dict(nx=nx, ny=ny, theta=th, g=g, s=None, n_rhs=1, rtol=1e-10,
                     opts=dict(coarse_poly_order=30, trunc_rtol=1e-2, precision=prec),
-                    desc="%dx%d theta seeded g~U[0,1] %s V-cycle" % (nx, ny, "FP32" if prec else "FP64"))
-    if name in ("c4a", "c4a_fp64"):
+                    desc="%dx%d theta seeded g~U[0,1] %s V-cycle" % (
+                        nx, ny, {0: "FP64", 1: "FP32", 2: "FP32 (bf16 R)"}[prec]))
+    if name in ("c4a", "c4a_fp64", "c4a_bf16"):
         # 2048x2048, one operator, 64 right-hand sides: g ~ U[0,1], s ~ N(0,1);
         # batched V-cycle in FP32 ("c4a_fp64": FP64), rtol 1e-8
         nx = ny = n or 2048
@@ -61,11 +63,11 @@ def workload(name, n=None):
         k = 64
         g = rng.uniform(0.0, 1.0, (k, _n_inflow(nx, ny, th)))
         s = rng.standard_normal((k, nx * ny))
-        prec = 1 if name == "c4a" else 0
+        prec = {"c4a": 1, "c4a_fp64": 0, "c4a_bf16": 2}[name]
         return dict(nx=nx, ny=ny, theta=th, g=g, s=s, n_rhs=k, rtol=1e-8,
                     opts=dict(coarse_poly_order=30, trunc_rtol=1e-2, precision=prec),
                     desc="%dx%d 64 rhs g~U[0,1] s~N(0,1) %s batched V-cycle" % (
-                        nx, ny, "FP32" if prec else "FP64"))
+                        nx, ny, {0: "FP64", 1: "FP32", 2: "FP32 (bf16 R)"}[prec]))
     if name == "c4b":
         # 32 separate problems: N_p ~ U{128..1024} per side (square grids),
         # theta_p ~ U[pi/12, 5pi/12], g ~ U[0,1] per inflow node; rtol 1e-8

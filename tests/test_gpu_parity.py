@@ -282,3 +282,31 @@ def test_slices_per_warp_never_changes_a_bit(prec, monkeypatch):
         assert info.converged
         xs.append(x.cpu().numpy())
     assert np.array_equal(xs[0], xs[1]) and np.array_equal(xs[0], xs[2])
+
+
+def test_bf16_restrictor_storage_error():
+    """Restrictor values in bfloat16 (FP32 V-cycle): the outer FP64 iteration
+    still meets rtol and the solution matches the oracle and the sweep to
+    1e-9; the cost of the narrower R is reported as extra iterations, at
+    most two over the FP32 V-cycle."""
+    w = workload("grid", (257, 300))
+    vx, vy = velocity(w["theta"])
+    po = O.advection_2d(w["nx"], w["ny"], vx, vy)
+    pg = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
+    bo = O.assemble_rhs(po, w["g"][0], w["s"][0])
+    b = torch.tensor(bo, device="cuda")
+    u = O.sweep_solve(po.A, bo, O.sweep_order(po))
+    Ho = O.setup(po.A, _oopts(w["opts"]))
+    xo, io = O.solve(Ho, po.A, bo, rtol=1e-10)
+    its = {}
+    for prec in [G.AIRG_FP64, G.AIRG_MIXED_FP32, G.AIRG_MIXED_FP32_BF16R]:
+        h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"], G.airg_options_default(precision=prec, **w["opts"]))
+        x, info = G.airg_solve(h, b, rtol=1e-10)
+        xg = x.cpu().numpy()
+        assert info.converged
+        assert np.linalg.norm(bo - O.spmv(po.A, xg)) <= 1e-10 * np.linalg.norm(bo) * (1 + 1e-6)
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-9
+        assert np.linalg.norm(xg - u) / np.linalg.norm(u) <= 1e-9
+        its[prec] = info.iterations
+    assert its[G.AIRG_MIXED_FP32_BF16R] <= its[G.AIRG_MIXED_FP32] + 2, its
+
