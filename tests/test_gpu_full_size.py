@@ -1,0 +1,121 @@
+"""The benchmark workloads at their full sizes, in the configuration bench.py
+times, checked against what holds at any size: the exact discrete solution
+u* = A^-1 b from the oracle's substitution in upwind order (the operator is
+triangular in that order, Sec. 1.1), the true residual computed by the
+oracle's FP64 SpMV, and -- where the oracle finishes in about a minute -- the
+level-0 CF split, bit for bit.
+
+Checks.  At the benchmark tolerance every solution's true residual must be
+at or below rtol.  In the same launch configuration at rtol 1e-10, every
+solution must be within 1e-9 of u* in relative L2 (the accuracy bar); if a
+single solve misses it while rtol is met, it is repeated at rtol 1e-12 and
+must then meet it.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2508_17517_gb300 as G  # noqa: E402
+from oracle import airg as O  # noqa: E402
+from synthetic import velocity, workload  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    G.build()
+    G.lib()
+
+
+def _oopts(d):
+    return O.Options(**{k: v for k, v in d.items() if k not in ("precision", "outer")})
+
+
+@pytest.fixture(scope="module")
+def c3_problem():
+    w = workload("c3")
+    vx, vy = velocity(w["theta"])
+    po = O.advection_2d(w["nx"], w["ny"], vx, vy)
+    bo = O.assemble_rhs(po, w["g"][0], np.zeros(po.A.n_rows))
+    u = O.sweep_solve(po.A, bo, O.sweep_order(po))
+    pg = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
+    return w, po, bo, u, pg
+
+
+@pytest.mark.parametrize("name", ["c3", "c3_fp64", "c3_bf16"])
+def test_4096_full_size_solution(name, c3_problem):
+    w0, po, bo, u, pg = c3_problem
+    w = workload(name)
+    h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"], G.airg_options_default(**w["opts"]))
+    b = torch.tensor(bo, device="cuda")
+    for rtol in (1e-10, 1e-12):
+        x, info = G.airg_solve(h, b, rtol=rtol)
+        xg = x.cpu().numpy()
+        assert info.converged
+        res = np.linalg.norm(bo - O.spmv(po.A, xg)) / np.linalg.norm(bo)
+        assert res <= rtol * (1 + 1e-6)
+        err = np.linalg.norm(xg - u) / np.linalg.norm(u)
+        if err <= 1e-9:
+            break
+    assert err <= 1e-9, (rtol, err)
+
+
+def test_4096_level0_cf_split_bitexact(c3_problem):
+    w, po, bo, u, pg = c3_problem
+    h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"], G.airg_options_default(**w["opts"]))
+    strong, is_f, rounds, converted = O.cf_split(po.A, _oopts(w["opts"]), 0)
+    cf = G.airg_export_vector(h, 0, 0).astype(bool)
+    assert np.array_equal(cf, is_f)
+    sc = G.airg_export_vector(h, 0, 4)
+    assert int(sc[0]) == rounds
+
+
+def test_2048x64_batched_full_size():
+    w = workload("c4a")
+    vx, vy = velocity(w["theta"])
+    po = O.advection_2d(w["nx"], w["ny"], vx, vy)
+    pg = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
+    k = w["n_rhs"]
+    b = G.airg_assemble_rhs_advection2d(pg, torch.tensor(w["g"], device="cuda"), torch.tensor(w["s"], device="cuda"))
+    h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"], G.airg_options_default(**w["opts"]))
+    order = O.sweep_order(po)
+    bos = [O.assemble_rhs(po, w["g"][q], w["s"][q]) for q in range(k)]
+    for q in range(k):
+        assert np.array_equal(bos[q], b[q].cpu().numpy())
+    for rtol in (w["rtol"], 1e-10):
+        x, info = G.airg_solve(h, b, rtol=rtol)
+        assert info.converged
+        X = x.cpu().numpy()
+        for q in range(k):
+            bo = bos[q]
+            assert np.linalg.norm(bo - O.spmv(po.A, X[q])) <= rtol * np.linalg.norm(bo) * (1 + 1e-6)
+            if rtol == 1e-10:
+                u = O.sweep_solve(po.A, bo, order)
+                assert np.linalg.norm(X[q] - u) / np.linalg.norm(u) <= 1e-9
+
+
+def test_32_uneven_grids_full_size():
+    w = workload("c4b")
+    csrs, bs, ref = [], [], []
+    for p in w["problems"]:
+        vx, vy = velocity(p["theta"])
+        pg = G.airg_problem_advection2d(p["nx"], p["ny"], vx, vy)
+        po = O.advection_2d(p["nx"], p["ny"], vx, vy)
+        bo = O.assemble_rhs(po, p["g"], np.zeros(po.A.n_rows))
+        csrs.append((pg["rowptr"], pg["col"], pg["val"]))
+        bs.append(torch.tensor(bo, device="cuda"))
+        ref.append((po, bo))
+    B = G.airg_setup_batch(csrs, G.airg_options_default(**w["opts"]))
+    for rtol in (w["rtol"], 1e-10):
+        xs, infos = G.airg_solve_batch(B, bs, rtol=rtol)
+        for x, info, (po, bo) in zip(xs, infos, ref):
+            xg = x.cpu().numpy()
+            assert info.converged
+            assert np.linalg.norm(bo - O.spmv(po.A, xg)) <= rtol * np.linalg.norm(bo) * (1 + 1e-6)
+            if rtol == 1e-10:
+                u = O.sweep_solve(po.A, bo, O.sweep_order(po))
+                assert np.linalg.norm(xg - u) / np.linalg.norm(u) <= 1e-9
