@@ -167,8 +167,12 @@ airg_status airg_rhs_adjoint_advection2d(int64_t nx, int64_t ny, double vx, doub
  * polynomial (Sec. 2.3), all on the GPU.  A is copied; the handle owns every
  * device buffer it allocates.  Setup values are reproducible: sums run in a
  * fixed order and dot products are correctly rounded.
- * Errors: AIRG_ERR_ARG (bad sizes, unsorted columns, missing diagonal),
- * AIRG_ERR_OOM, AIRG_ERR_CUDA, AIRG_ERR_BREAKDOWN.
+ * A is validated before use (host or device arrays alike): square, n and
+ * nnz below 2^31, rowptr[0] = 0 <= rowptr[i] <= rowptr[i+1] <= rowptr[n] =
+ * nnz, columns strictly ascending within [0, n), a stored diagonal in every
+ * row, finite values.  A row's entries are read only after its row pointers
+ * pass.  Errors: AIRG_ERR_ARG (any of these), AIRG_ERR_OOM, AIRG_ERR_CUDA,
+ * AIRG_ERR_BREAKDOWN.
  */
 airg_status airg_setup(const airg_csr* A, const airg_options* opt, void* stream,
                        airg_handle** out);

@@ -105,10 +105,14 @@ __global__ void k_zero_at(long long nin, const int64_t* idx, double* v)
     if (k < nin) v[idx[k]] = 0.0;
 }
 
-__global__ void k_rp64_to_32(long long n, const int64_t* a, int* b)
+// 64-bit row pointers -> 32-bit; a value outside [0, nnz] becomes -1, which
+// the validation rejects before any entry is read
+__global__ void k_rp64_to_32(long long n, const int64_t* a, long long nnz, int* b)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i <= n) b[i] = int(a[i]);
+    if (i > n) return;
+    const int64_t v = a[i];
+    b[i] = (v < 0 || v > nnz) ? -1 : int(v);
 }
 
 int sgn(double x) { return x > 0.0 ? 1 : (x < 0.0 ? -1 : 0); }
@@ -138,7 +142,7 @@ airg::DevCSR upload_csr(const airg_csr* A, cudaStream_t st)
     D.alloc(int(A->n_rows), int(A->n_cols), int(A->nnz));
     long long n = A->n_rows;
     if (A->on_device) {
-        k_rp64_to_32<<<airg::grid_for(n + 1, TB), TB, 0, st>>>(n, A->rowptr, D.rp.p);
+        k_rp64_to_32<<<airg::grid_for(n + 1, TB), TB, 0, st>>>(n, A->rowptr, A->nnz, D.rp.p);
         CK_LAUNCH();
         CK(cudaMemcpyAsync(D.ci.p, A->col, A->nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
         CK(cudaMemcpyAsync(D.v.p, A->val, A->nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));

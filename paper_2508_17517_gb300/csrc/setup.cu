@@ -175,17 +175,27 @@ __global__ void k_rng_u32(unsigned long long key, long long n, unsigned* out)
 }
 
 // ------------------------------------------------------------- validation --
-__global__ void k_validate(int n_rows, int n_cols, const int* rp, const int* ci, int square,
-                           int* flags)
+// Row i of a caller's CSR.  The row pointers are checked first (0 = rp[0] <=
+// rp[i] <= rp[i+1] <= rp[n] = nnz); only a row whose bounds pass has its
+// entries read.  flags: [0] columns out of range or not strictly
+// ascending, [1] no stored diagonal, [2] bad row pointers, [3] a value that
+// is not finite.
+__global__ void k_validate(int n_rows, int n_cols, int nnz, const int* rp, const int* ci, const double* v,
+                           int square, int* flags)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_rows) return;
+    const int a = rp[i], b = rp[i + 1];
+    if (a < 0 || b < a || b > nnz || (i == 0 && a != 0) || (i == n_rows - 1 && b != nnz)) {
+        flags[2] = 1;
+        return;
+    }
     int prev = -1;
     bool diag = false;
-    if (rp[i + 1] < rp[i]) flags[0] = 1;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+    for (int k = a; k < b; ++k) {
         int j = ci[k];
         if (j <= prev || j < 0 || j >= n_cols) flags[0] = 1;
+        if (!isfinite(v[k])) flags[3] = 1;
         prev = j;
         if (j == i) diag = true;
     }
@@ -1177,16 +1187,18 @@ void rng_uniform_device(uint64_t seed, long long level, long long purpose, long 
 
 void validate_csr(const DevCSR& A, bool square, cudaStream_t st)
 {
-    DBuf<int> flags(2);
+    DBuf<int> flags(4);
     CK(cudaMemsetAsync(flags.p, 0, flags.bytes(), st));
     if (A.n_rows)
-        k_validate<<<grid_for(A.n_rows, TB), TB, 0, st>>>(A.n_rows, A.n_cols, A.rp.p, A.ci.p,
+        k_validate<<<grid_for(A.n_rows, TB), TB, 0, st>>>(A.n_rows, A.n_cols, A.nnz, A.rp.p, A.ci.p, A.v.p,
                                                             square ? 1 : 0, flags.p);
     CK_LAUNCH();
-    int f[2];
-    d2h(f, flags.p, 2, st);
+    int f[4];
+    d2h(f, flags.p, 4, st);
+    if (f[2]) fail(AIRG_ERR_ARG, "row pointers not monotone within [0, nnz] with rowptr[0] = 0, rowptr[n] = nnz");
     if (f[0]) fail(AIRG_ERR_ARG, "CSR columns out of range or not strictly ascending");
     if (f[1]) fail(AIRG_ERR_ARG, "a row has no stored diagonal");
+    if (f[3]) fail(AIRG_ERR_ARG, "a matrix value is not finite");
 }
 
 void csr_transpose(const DevCSR& A, DevCSR& T, cudaStream_t st)
