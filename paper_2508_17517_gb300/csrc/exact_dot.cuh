@@ -97,9 +97,9 @@ k_xdot_accumulate(long long n, const double* __restrict__ x, const double* __res
     }
 }
 
-// One thread: carry propagation and round-to-nearest-even of the global
-// accumulator.  Writes the double to *out, optionally its square root to
-// *out_sqrt, and clears the accumulator for the next use.
+// One thread: carry propagation and round-to-nearest-even of an accumulator
+// (a copy in shared memory; the callers load the global digits in parallel
+// first).  Returns the double and leaves the digits cleared.
 static __device__ inline double xd_round(unsigned long long* g)
 {
     long long* d = reinterpret_cast<long long*>(g);
@@ -150,14 +150,60 @@ static __device__ inline double xd_round(unsigned long long* g)
     return neg ? -r : r;
 }
 
+// One warp: takes the global digits into shared memory (reading and
+// clearing each word in one atomic exchange), then one thread rounds.
+// Writes the double to *out and optionally its square root to *out_sqrt.
 static __global__ void k_xdot_finalize(unsigned long long* gacc, const int* bad, double* out,
-                                double* out_sqrt)
+                                       double* out_sqrt)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double r = xd_round(gacc);
-    if (*bad) r = __longlong_as_double(0x7ff8000000000000LL);
+    __shared__ unsigned long long d[XD_DIGITS];
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    for (int t = threadIdx.x; t < XD_DIGITS; t += 32) d[t] = atomicExch(gacc + t, 0ULL);
+    __syncwarp();
+    if (threadIdx.x != 0) return;
+    double r = xd_round(d);
+    if (*(volatile const int*)bad) r = __longlong_as_double(0x7ff8000000000000LL);
     if (out) *out = r;
     if (out_sqrt) *out_sqrt = __dsqrt_rn(r);
+}
+
+// Accumulation and rounding in one launch: blocks deposit as in
+// k_xdot_accumulate; the last block to finish (atomic ticket, reset for the
+// next call) takes the global digits, clearing them, and rounds.
+static __global__ void __launch_bounds__(XD_THREADS)
+k_xdot(long long n, const double* __restrict__ x, const double* __restrict__ y,
+       unsigned long long* __restrict__ gacc, int* bad, unsigned* ticket, double* out, double* out_sqrt)
+{
+    __shared__ unsigned long long sacc[XD_WARPS][XD_DIGITS];
+    __shared__ bool last;
+    for (int t = threadIdx.x; t < XD_WARPS * XD_DIGITS; t += blockDim.x)
+        (&sacc[0][0])[t] = 0ULL;
+    __syncthreads();
+    unsigned long long* mine = sacc[threadIdx.x >> 5];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        xd_add_product(mine, x[i], y[i], bad);
+    __syncthreads();
+    for (int t = threadIdx.x; t < XD_DIGITS; t += blockDim.x) {
+        unsigned long long s = 0ULL;
+#pragma unroll
+        for (int w = 0; w < XD_WARPS; ++w) s += sacc[w][t];
+        if (s) atomicAdd(gacc + t, s);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int t = threadIdx.x; t < XD_DIGITS; t += blockDim.x) sacc[0][t] = atomicExch(gacc + t, 0ULL);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double r = xd_round(sacc[0]);
+    if (*(volatile const int*)bad) r = __longlong_as_double(0x7ff8000000000000LL);
+    if (out) *out = r;
+    if (out_sqrt) *out_sqrt = __dsqrt_rn(r);
+    *ticket = 0u;
 }
 
 }  // namespace airg

@@ -568,11 +568,13 @@ __global__ void k_shift_rowptr(int m, const int* prp, int off, int* crp)
     if (i < m) crp[i] = prp[i] + off;
 }
 
+// Emit of the rows longer than `skip` entries: one thread per row,
+// insertion into column order.
 __global__ void k_gemm_emit(int m, const int* toff, const int* keys, const double* vals,
-                            const int* crp, int* cci, double* cv)
+                            const int* crp, int* cci, double* cv, int skip)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
+    if (i >= m || crp[i + 1] - crp[i] <= skip) return;
     int o = crp[i], s = crp[i];
     for (int t = toff[i]; t < toff[i + 1]; ++t) {
         int j = keys[t];
@@ -583,6 +585,74 @@ __global__ void k_gemm_emit(int m, const int* toff, const int* keys, const doubl
         cci[b + 1] = j;
         cv[b + 1] = v;
         ++o;
+    }
+}
+
+// Emit of the rows of at most EMIT_CAP entries: one warp per row takes the
+// valid slots of the row's table into shared memory (ballot / prefix
+// count), sorts them by column with a bitonic network and writes them out.
+// The values were summed in the hash phase; only their order is set here.
+constexpr int EMIT_CAP = 1024;
+constexpr int EMIT_WARPS = 4;
+
+__global__ void __launch_bounds__(EMIT_WARPS * 32)
+k_gemm_emit_warp(int m, const int* toff, const int* keys, const double* vals, const int* crp, int* cci,
+                 double* cv)
+{
+    __shared__ int sk[EMIT_WARPS][EMIT_CAP];
+    __shared__ double sv[EMIT_WARPS][EMIT_CAP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * EMIT_WARPS + w;
+    if (i >= m) return;
+    const int n = crp[i + 1] - crp[i];
+    if (n > EMIT_CAP) return;
+    int* k = sk[w];
+    double* v = sv[w];
+    const int t0 = toff[i], t1 = toff[i + 1];
+    int filled = 0;
+    for (int tb = t0; tb < t1; tb += 32) {
+        const int t = tb + lane;
+        const int key = t < t1 ? keys[t] : -1;
+        const unsigned ball = __ballot_sync(0xffffffffu, key >= 0);
+        if (key >= 0) {
+            const int pos = filled + __popc(ball & ((1u << lane) - 1u));
+            if (pos < EMIT_CAP) {
+                k[pos] = key;
+                v[pos] = vals[t];
+            }
+        }
+        filled += __popc(ball);
+    }
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int t = n + lane; t < P; t += 32) {
+        k[t] = 0x7fffffff;
+        v[t] = 0.0;
+    }
+    __syncwarp();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < P; t += 32) {
+                const int u = t ^ stride;
+                if (u > t) {
+                    const bool up = (t & size) == 0;
+                    const int a = k[t], b = k[u];
+                    if ((a > b) == up && a != b) {
+                        k[t] = b;
+                        k[u] = a;
+                        const double x = v[t];
+                        v[t] = v[u];
+                        v[u] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    const int o = crp[i];
+    for (int t = lane; t < n; t += 32) {
+        cci[o + t] = k[t];
+        cv[o + t] = v[t];
     }
 }
 
@@ -735,12 +805,15 @@ struct Ctx {
     cudaStream_t st;
     DBuf<unsigned long long> xacc;   // exact-dot accumulator
     DBuf<int> xbad;
+    DBuf<unsigned> xticket;          // last-block ticket of k_xdot
     explicit Ctx(cudaStream_t s) : st(s)
     {
         xacc.alloc(XD_DIGITS);
         xbad.alloc(1);
+        xticket.alloc(1);
         CK(cudaMemsetAsync(xacc.p, 0, xacc.bytes(), st));
         CK(cudaMemsetAsync(xbad.p, 0, xbad.bytes(), st));
+        CK(cudaMemsetAsync(xticket.p, 0, xticket.bytes(), st));
     }
 };
 
@@ -759,8 +832,7 @@ void xdot(Ctx& c, long long n, const double* x, const double* y, double* out, do
 {
     int grid = (int)std::min<long long>(std::max<long long>(1, (n + XD_THREADS - 1) / XD_THREADS),
                                         2LL * num_sms());
-    k_xdot_accumulate<<<grid, XD_THREADS, 0, c.st>>>(n, x, y, c.xacc.p, c.xbad.p);
-    k_xdot_finalize<<<1, 32, 0, c.st>>>(c.xacc.p, c.xbad.p, out, out_sqrt);
+    k_xdot<<<grid, XD_THREADS, 0, c.st>>>(n, x, y, c.xacc.p, c.xbad.p, c.xticket.p, out, out_sqrt);
     CK_LAUNCH();
 }
 
@@ -834,8 +906,12 @@ void spgemm(const DevCSR& A, const DevCSR& B, DevCSR& C, cudaStream_t st)
         P.nnz = exclusive_scan(P.rp.p, P.rp.p, mc, st);
         P.ci.alloc(std::max(P.nnz, 1));
         P.v.alloc(std::max(P.nnz, 1));
-        if (mc) k_gemm_emit<<<grid_for(mc, TB), TB, 0, st>>>(mc, toff.p, keys.p, vals.p, P.rp.p, P.ci.p,
-                                                               P.v.p);
+        if (mc) {
+            k_gemm_emit_warp<<<grid_for(mc, EMIT_WARPS), EMIT_WARPS * 32, 0, st>>>(mc, toff.p, keys.p, vals.p,
+                                                                                   P.rp.p, P.ci.p, P.v.p);
+            k_gemm_emit<<<grid_for(mc, TB), TB, 0, st>>>(mc, toff.p, keys.p, vals.p, P.rp.p, P.ci.p, P.v.p,
+                                                         EMIT_CAP);
+        }
         CK_LAUNCH();
         CK(cudaStreamSynchronize(st));
         total += P.nnz;
