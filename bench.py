@@ -270,6 +270,22 @@ ALU_PEAK_TFLOPS = {"f64": 2 * 2 * SM_COUNT * SM_GHZ / 1e3, "f32": 2 * 128 * SM_C
 VCYCLE_KINDS = ("restrict", "f_residual", "f_smoother", "coarse_newton")
 
 
+def measured_traffic(workload, kind, level):
+    """DRAM bytes per launch of a (kind, level) group from the committed ncu
+    summary (profiles/coarse_newton_traffic.md), or None."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "coarse_newton_traffic.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) == 7 and cells[0] == workload and cells[1] == kind and cells[2] == str(level):
+            try:
+                return float(cells[5])
+            except ValueError:
+                return None
+    return None
+
+
 def roofline_entry(prof, per_level, peak, peak_kind, vcycle_dtype="f64"):
     """Roofline of the dominant kernel: the (kernel kind, level) pair with
     the largest share of the profiled device time.  Its arithmetic intensity
@@ -394,6 +410,10 @@ def run_gpu(args):
     peak, peak_kind = measured_peaks()
     roofline = roofline_entry(prof, per_level, peak, peak_kind,
                               "f32" if w["opts"].get("precision", 0) in (1, 2) else "f64")
+    dk, dl = roofline["kernel"].split(" (level ")
+    roofline["traffic"] = measured_traffic(args.workload, dk, int(dl.rstrip(")")))
+    if roofline["traffic"] is not None:
+        roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold cache"
     vc_bytes = sinfo["bytes_per_vcycle"]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("c1", "c2"):

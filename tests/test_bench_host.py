@@ -27,3 +27,14 @@ def test_spmv_is_hbm_bound_and_dominant_group_wins():
     assert abs(e["achieved"] - 4 * 10**10 / 8e-3 / 1e9) < 1e-6
     assert abs(e["share"] - 8.0 / 15.0) < 1e-12
     assert e["dtype"] == "f32"
+
+
+def test_traffic_table_lookup():
+    """The roofline's traffic comes from the committed ncu summary: found for
+    the captured (workload, kind, level) groups, absent otherwise."""
+    t2 = bench.measured_traffic("c2", "coarse_newton", 8)
+    t3 = bench.measured_traffic("c3", "coarse_newton", 11)
+    assert t2 is not None and 3e7 < t2 < 5e7
+    assert t3 is not None and 1.5e8 < t3 < 2.5e8
+    assert bench.measured_traffic("c2", "f_smoother", 0) is None
+    assert bench.measured_traffic("c4a", "coarse_newton", 8) is None
