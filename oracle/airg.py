@@ -232,6 +232,7 @@ class Options:
     exact_tol: float = 1e-12         # rank reading of Sec. 2.3: GMRES residual <= tol * beta
     addroot_log10: float = 4.0       # Loe-Morgan extra-root threshold (unpinned)
     addroot_per: float = 14.0
+    smoother: str = "polynomial"     # "assembled": e_f += Ahat_ff^-1 t with the Eq. 8 matrix
 
 
 # --------------------------------------------------------------------------
@@ -704,6 +705,7 @@ class Level:
     pmisr_rounds: int
     ddc_converted: list
     trunc_rel: float = float("nan")
+    Ainv: CSR = None                 # fixed-sparsity Ahat_ff^-1 (Eq. 8)
 
 
 @dataclass
@@ -754,7 +756,7 @@ def setup(A, opts=None):
         W = one_point(A, strong, is_f)
         Ac = coarse_matrix(A, is_f, Z, W, opts.a_drop, opts.a_lump)
         Hh.levels.append(Level(n, A, strong, is_f, A_ff, A_fc, Z, W, alpha, k, rounds, conv,
-                               trunc_rel))
+                               trunc_rel, Ainv))
         A = Ac
         level += 1
 
@@ -765,7 +767,9 @@ def setup(A, opts=None):
 def vcycle(Hh, r, level=0):
     """e = M^-1 r with zero initial guess: restrict, coarse-correct,
     prolongate with W, then one F-point smooth e_f += q(A_ff)(r_f - A_fc e_c -
-    A_ff e_f) (Eq. 6)."""
+    A_ff e_f) (Eq. 6).  With smoother "assembled" the approximate inverse is
+    the stored fixed-sparsity matrix of Eq. 8 instead of the matrix-free
+    polynomial (the alternative the paper times in Sec. 2.2)."""
     if level == len(Hh.levels):
         return newton_apply(Hh.A_coarse, Hh.roots, r)
     L = Hh.levels[level]
@@ -774,7 +778,10 @@ def vcycle(Hh, r, level=0):
     ec = vcycle(Hh, rc, level + 1)
     ef = np.where(L.W >= 0, ec[np.maximum(L.W, 0)], 0.0)
     t = rf - spmv(L.A_fc, ec) - spmv(L.A_ff, ef)
-    ef = ef + horner_apply(L.A_ff, L.alpha, t)
+    if Hh.opts is not None and Hh.opts.smoother == "assembled":
+        ef = ef + spmv(L.Ainv, t)
+    else:
+        ef = ef + horner_apply(L.A_ff, L.alpha, t)
     e = np.empty(L.n)
     e[L.is_f] = ef
     e[~L.is_f] = ec
@@ -886,12 +893,18 @@ def complexities(Hh):
     nnz(A_top).  Cycle complexity: flops of one V-cycle over the flops of one
     top-level SpMV (2 flops per stored entry)."""
     top = Hh.levels[0].A.nnz if Hh.levels else Hh.A_coarse.nnz
+    assembled = Hh.opts is not None and Hh.opts.smoother == "assembled"
     store = 0
     flops = 0
     for L in Hh.levels:
         p = len(L.alpha) - 1
         store += L.A_ff.nnz + L.A_fc.nnz + L.Z.nnz
-        flops += 2 * L.Z.nnz + 2 * L.A_fc.nnz + 2 * L.A_ff.nnz * (p + 1)
+        flops += 2 * L.Z.nnz + 2 * L.A_fc.nnz
+        if assembled:
+            store += L.Ainv.nnz
+            flops += 2 * L.A_ff.nnz + 2 * L.Ainv.nnz
+        else:
+            flops += 2 * L.A_ff.nnz * (p + 1)
     nr = len(Hh.roots)
     store += Hh.A_coarse.nnz
     flops += 2 * Hh.A_coarse.nnz * max(nr - 1, 0)
