@@ -44,9 +44,10 @@ def parse(argv=None):
     ap.add_argument("--workload", default="c2",
                     choices=["c1", "c2", "c3", "c3_fp64", "c3_bf16", "c4a", "c4a_fp64", "c4a_bf16", "c4b"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sweep", choices=["coarse-order"], default=None,
-                    help="instead of the throughput line: the coarse-grid polynomial order and "
-                         "truncation sweep of Sec. 3.1 on one GPU (one JSON line with a row per setting)")
+    ap.add_argument("--sweep", choices=["coarse-order", "smoother"], default=None,
+                    help="instead of the throughput line, one JSON line with a row per setting: "
+                         "coarse-order = the coarse polynomial order / truncation study of Sec. 3.1; "
+                         "smoother = matrix-free polynomial vs assembled Eq. 8 smoother (Sec. 2.2)")
     return ap.parse_args(argv)
 
 
@@ -447,14 +448,47 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def _sweep_row(G, torch, prob, b, opts, args):
+    """Setup then median device time of `steps` solves to rtol 1e-10."""
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    h = G.airg_setup(prob["rowptr"], prob["col"], prob["val"], opts)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    info = G.airg_setup_info(h)
+    x = torch.zeros_like(b)
+    for _ in range(args.warmup):
+        x.zero_()
+        G.airg_solve(h, b, x, rtol=1e-10)
+    times, its = [], []
+    for _ in range(args.steps):
+        x.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, si = G.airg_solve(h, b, x, rtol=1e-10)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        its.append(si.iterations)
+    solve_ms = statistics.median(times)
+    nit = statistics.median(its)
+    return {"levels": info["levels"], "coarse_rows": info["n"][-1], "truncated": info["truncated"],
+            "cycle_complexity": round(info["cycle_complexity"], 2),
+            "storage_complexity": round(info["storage_complexity"], 2),
+            "setup_s": round(setup_s, 3), "iterations": nit, "solve_ms": round(solve_ms, 3),
+            "ms_per_iteration": round(solve_ms / max(nit, 1), 3)}
+
+
 def run_sweep(args):
-    """Coarse-grid solver order and truncation (Sec. 3.1) on one GPU: theta =
-    pi/4 on a 4096^2 grid (16.8M DOFs, the per-GPU size class of that
-    experiment), inflow g = 1, smoother order 6; for m_c in {5, 10, 30, 100},
-    truncation at alpha_trunc = 0.1 on every level vs no truncation: levels,
-    cycle and storage complexity, setup time, iterations and solve time to
-    rtol 1e-10 (FP64 V-cycle).  The solve time is the median of `steps`
-    device-timed solves after `warmup` untimed ones."""
+    """One GPU, theta = pi/4 on a 4096^2 grid (16.8M DOFs, the per-GPU size
+    class of the paper's studies), inflow g = 1, smoother order 6, rtol 1e-10.
+    coarse-order (Sec. 3.1): m_c in {5, 10, 30, 100} with truncation at
+    alpha_trunc = 0.1 on every level vs no truncation, FP64.  smoother
+    (Sec. 2.2): the matrix-free GMRES polynomial vs the assembled
+    fixed-sparsity matrix of Eq. 8, FP64 and FP32 V-cycles, m_c = 30 with
+    truncation at 1e-2.  Solve times are the median of `steps` device-timed
+    solves after `warmup` untimed ones."""
     import torch
     torch.cuda.set_device(0)
     import paper_2508_17517_gb300 as G
@@ -465,41 +499,22 @@ def run_sweep(args):
     prob = G.airg_problem_advection2d(n, n, vx, vy)
     g = torch.ones(prob["inflow"].numel(), dtype=torch.float64, device="cuda")
     b = G.airg_assemble_rhs_advection2d(prob, g)
-    stream = torch.cuda.current_stream()
     rows = []
-    for mc in (5, 10, 30, 100):
-        for trunc in (0.1, 0.0):
-            opts = G.airg_options_default(coarse_poly_order=mc, trunc_rtol=trunc)
-            t0 = time.perf_counter()
-            h = G.airg_setup(prob["rowptr"], prob["col"], prob["val"], opts)
-            torch.cuda.synchronize()
-            setup_s = time.perf_counter() - t0
-            info = G.airg_setup_info(h)
-            x = torch.zeros_like(b)
-            for _ in range(args.warmup):
-                x.zero_()
-                G.airg_solve(h, b, x, rtol=1e-10)
-            times, its = [], []
-            for _ in range(args.steps):
-                x.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                _, si = G.airg_solve(h, b, x, rtol=1e-10)
-                e1.record(stream)
-                e1.synchronize()
-                times.append(e0.elapsed_time(e1))
-                its.append(si.iterations)
-            rows.append({"coarse_order": mc, "truncation": trunc, "levels": info["levels"],
-                         "coarse_rows": info["n"][-1], "truncated": info["truncated"],
-                         "cycle_complexity": round(info["cycle_complexity"], 2),
-                         "storage_complexity": round(info["storage_complexity"], 2),
-                         "setup_s": round(setup_s, 3), "iterations": statistics.median(its),
-                         "solve_ms": round(statistics.median(times), 3)})
-            del h
-    print(json.dumps({"sweep": "coarse-order", "grid": "%dx%d" % (n, n), "theta": "pi/4", "g": 1.0,
-                      "rtol": 1e-10, "dtype": "f64", "steps": args.steps, "warmup": args.warmup,
-                      "rows": rows}))
+    if args.sweep == "coarse-order":
+        for mc in (5, 10, 30, 100):
+            for trunc in (0.1, 0.0):
+                r = _sweep_row(G, torch, prob, b, G.airg_options_default(coarse_poly_order=mc, trunc_rtol=trunc), args)
+                rows.append(dict({"coarse_order": mc, "truncation": trunc}, **r))
+    else:
+        for prec in (G.AIRG_FP64, G.AIRG_MIXED_FP32):
+            for sm in (G.AIRG_SMOOTH_POLYNOMIAL, G.AIRG_SMOOTH_ASSEMBLED):
+                opts = G.airg_options_default(coarse_poly_order=30, trunc_rtol=1e-2, precision=prec, smoother=sm)
+                r = _sweep_row(G, torch, prob, b, opts, args)
+                rows.append(dict({"precision": "f64" if prec == G.AIRG_FP64 else "f32",
+                                  "smoother": "polynomial" if sm == G.AIRG_SMOOTH_POLYNOMIAL else "assembled"},
+                                 **r))
+    print(json.dumps({"sweep": args.sweep, "grid": "%dx%d" % (n, n), "theta": "pi/4", "g": 1.0,
+                      "rtol": 1e-10, "steps": args.steps, "warmup": args.warmup, "rows": rows}))
 
 
 def main(argv=None):

@@ -52,6 +52,11 @@ enum { AIRG_FP64 = 0, AIRG_MIXED_FP32 = 1, AIRG_MIXED_FP32_BF16R = 2 };
 /* Outer iteration around the V-cycle: flexible GMRES (default), or the
  * preconditioned Richardson iteration x <- x + M^-1 (b - A x) of Sec. 3. */
 enum { AIRG_OUTER_FGMRES = 0, AIRG_OUTER_RICHARDSON = 1 };
+/* F-point smoother: the matrix-free GMRES polynomial q(A_ff) by Horner
+ * (Eq. 6-7), or the assembled fixed-sparsity approximation of Eq. 8 applied
+ * as one SpMV (the alternative timed in Sec. 2.2; stores one more matrix per
+ * level). */
+enum { AIRG_SMOOTH_POLYNOMIAL = 0, AIRG_SMOOTH_ASSEMBLED = 1 };
 
 /* Compressed sparse row matrix (n_rows x n_cols).  Caller-owned, read-only. */
 typedef struct {
@@ -89,6 +94,7 @@ typedef struct {
     int precision;             /* AIRG_FP64, AIRG_MIXED_FP32, _BF16R           */
     int gmres_restart;         /* outer FGMRES restart length                 */
     int outer;                 /* AIRG_OUTER_FGMRES or AIRG_OUTER_RICHARDSON  */
+    int smoother;              /* AIRG_SMOOTH_POLYNOMIAL or _ASSEMBLED        */
 } airg_options;
 
 typedef struct airg_handle_s airg_handle;
@@ -230,6 +236,7 @@ airg_status airg_setup_info(const airg_handle* h, airg_hierarchy_info* info);
  * (points in increasing index, F/C-local indices in increasing index), for
  * checking against an independent implementation.  `what`:
  *   0 A_l (the level operator)   1 A_ff   2 A_fc   3 Z (restrictor block, after drop)
+ *   4 the fixed-sparsity Ahat_ff^-1 of Eq. 8 (kept only with AIRG_SMOOTH_ASSEMBLED)
  * Two-call protocol with HOST buffers: pass NULL arrays to get *n_rows,
  * *n_cols, *nnz; then pass arrays of those sizes.  `what` = 0 on the coarsest
  * level returns the coarse operator.

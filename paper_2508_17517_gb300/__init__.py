@@ -16,6 +16,8 @@ from ._build import LIB, build  # noqa: F401
 
 AIRG_OK = 0
 AIRG_ERR_NOT_CONVERGED = 5
+AIRG_SMOOTH_POLYNOMIAL = 0
+AIRG_SMOOTH_ASSEMBLED = 1
 AIRG_OUTER_FGMRES = 0
 AIRG_OUTER_RICHARDSON = 1
 AIRG_FP64 = 0
@@ -46,7 +48,7 @@ class airg_options(ctypes.Structure):
                 ("breakdown_tol", ctypes.c_double), ("exact_tol", ctypes.c_double),
                 ("addroot_log10", ctypes.c_double),
                 ("addroot_per", ctypes.c_double), ("precision", ctypes.c_int),
-                ("gmres_restart", ctypes.c_int), ("outer", ctypes.c_int)]
+                ("gmres_restart", ctypes.c_int), ("outer", ctypes.c_int), ("smoother", ctypes.c_int)]
 
 
 class airg_csr(ctypes.Structure):

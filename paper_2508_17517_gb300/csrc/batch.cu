@@ -497,6 +497,13 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB * kk + 3 * fB, (2 * o.M.nnz + 2LL * nf) * kk,
                WITH_KW(k, kb_fresid<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
                                                                         T(lv.alpha[p]), k)));
+        if (o.Ainv.n_rows) {
+            // assembled smoother: e_f = W e_c + Ahat^-1 t (last Horner kernel, a0 = 0)
+            LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, (2 * o.Ainv.nnz + 3LL * nf) * kk,
+                     WITH_KW(k, kb_horner_last<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.Ainv), wk.t, wk.t, ec,
+                                                                                   lv.W.p, ef, T(0), k)));
+            continue;
+        }
         if (p == 0) {
             LAUNCH_F(S, PK_HORNER, 3 * fB + 4LL * nf, 3LL * nf * kk,
                    kb_smooth0<T><<<grid_for((long long)nf * k, BT), BT, 0, st>>>(nf, wk.t, ec, lv.W.p, ef,

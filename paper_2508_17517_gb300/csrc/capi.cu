@@ -129,6 +129,8 @@ void check_options(const airg_options& o)
     if (o.precision != AIRG_FP64 && o.precision != AIRG_MIXED_FP32 && o.precision != AIRG_MIXED_FP32_BF16R)
         airg::fail(AIRG_ERR_ARG, "bad precision");
     if (o.outer != AIRG_OUTER_FGMRES && o.outer != AIRG_OUTER_RICHARDSON) airg::fail(AIRG_ERR_ARG, "bad outer");
+    if (o.smoother != AIRG_SMOOTH_POLYNOMIAL && o.smoother != AIRG_SMOOTH_ASSEMBLED)
+        airg::fail(AIRG_ERR_ARG, "bad smoother");
 }
 
 airg::DevCSR upload_csr(const airg_csr* A, cudaStream_t st)
@@ -204,6 +206,7 @@ airg_status airg_options_default(airg_options* o)
     o->precision = AIRG_FP64;
     o->gmres_restart = 30;
     o->outer = AIRG_OUTER_FGMRES;
+    o->smoother = AIRG_SMOOTH_POLYNOMIAL;
     return AIRG_OK;
 }
 
@@ -364,6 +367,10 @@ airg_status airg_export_matrix(const airg_handle* h, int level, int what, int64_
                 case 1: M = &lv.A_ff; break;
                 case 2: M = &lv.A_fc; break;
                 case 3: M = &lv.Z; break;
+                case 4:
+                    if (!lv.Ainv.n_rows && lv.n_f) airg::fail(AIRG_ERR_ARG, "the approximate inverse is kept only with the assembled smoother");
+                    M = &lv.Ainv;
+                    break;
                 default: airg::fail(AIRG_ERR_ARG, "bad matrix id");
             }
         }

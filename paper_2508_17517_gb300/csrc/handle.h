@@ -22,6 +22,7 @@ struct SetupLevel {
     DBuf<int> f_ids, c_ids;       // row of each F / C point
     DevCSR A_ff, A_fc, Z;     // blocks of Eq. 3; Z = -A_cf Ahat_ff^-1 after drop
     DevCSR M;                 // rows of A P at the F points = A_fc + A_ff W
+    DevCSR Ainv;              // fixed-sparsity Ahat_ff^-1 (Eq. 8), kept for the assembled smoother
     DBuf<int> W;              // one-point prolongator: C-local index or -1
     std::vector<double> alpha;    // p+1 smoother coefficients (zero-padded)
     int alpha_k = 0;              // Krylov dimension reached (p+1 unless breakdown)

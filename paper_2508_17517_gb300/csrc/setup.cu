@@ -1357,6 +1357,7 @@ std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, c
         // Z = -A_cf Ahat^-1, then the relative drop on R
         DevCSR Zfull;
         spgemm(A_cf, Ainv, Zfull, st);
+        if (o.smoother == AIRG_SMOOTH_ASSEMBLED) L->Ainv = std::move(Ainv);
         if (Zfull.nnz) k_scale<<<grid_for(Zfull.nnz, TB), TB, 0, st>>>(Zfull.nnz, Zfull.v.p, -1.0);
         {
             DBuf<int8_t> keep(std::max(Zfull.nnz, 1));

@@ -1086,6 +1086,17 @@ coarse_done:
         const long long fB = (long long)nf * VB;
         const int pidx2 = sizeof(T) == 8 ? 0 : 1;
         S.cur_level = l;
+        if (o.Ainv.n_rows) {
+            // assembled smoother (Eq. 8 matrix): t = r_f - M e_c, then
+            // e_f = W e_c + Ahat^-1 t, the last Horner kernel with a0 = 0
+            LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
+                     WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M), block_rows(o.M), 0, st>>>(
+                                      view(o.M), rf, ec, wk.t, wk.wa, T(0))));
+            LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, 2 * o.Ainv.nnz + 3LL * nf,
+                     WITH_KR(o.Ainv, k_horner_last<T, KK, RR><<<grid_rows(o.Ainv), block_rows(o.Ainv), 0, st>>>(
+                                         view(o.Ainv), wk.t, wk.t, ec, lv.W.p, ef, T(0))));
+            continue;
+        }
         if (S.smooth_grid[pidx2] > 0 && p < 32) {
             Coefs al{};
             for (int q = 0; q <= p; ++q) al.a[q] = lv.alpha[q];
@@ -1208,6 +1219,7 @@ void tune_all(SolveData& S, cudaStream_t st)
         tune_rows(o.M, x.p, y.p, fs, fl, st);
         tune_rows(o.Z, x.p, y.p, fs, fl, st);
         tune_rows(o.Zb, x.p, y.p, fs, fl, st);
+        tune_rows(o.Ainv, x.p, y.p, fs, fl, st);
     }
     tune_rows(const_cast<Sell<T>&>(coarse_op<T>(S)), x.p, y.p, fs, fl, st);
     CK(cudaStreamSynchronize(st));
@@ -1304,6 +1316,7 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         build_sell<double>(lv.A_ff, iperm[l].p, perm[l].p, lv.n_f, sl->d.Aff, true, st);
         build_sell<double>(lv.M, iperm[l].p, rel.p, lv.n_c, sl->d.M, false, st);
         build_sell<double>(lv.Z, inv.p, perm[l].p, lv.n_f, sl->d.Z, false, st);
+        if (lv.Ainv.n_rows) build_sell<double>(lv.Ainv, iperm[l].p, perm[l].p, lv.n_f, sl->d.Ainv, true, st);
         sl->W.alloc(std::max(lv.n_f, 1));
         if (lv.n_f) k_map_w<<<grid_for(lv.n_f, TB), TB, 0, st>>>(lv.n_f, lv.W.p, rel.p, perm[l].p, sl->W.p);
         CK_LAUNCH();
@@ -1312,13 +1325,15 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
             copy_sell_f32(sl->d.M, sl->f.M, st);
             if (H.opt.precision == AIRG_MIXED_FP32_BF16R) copy_sell_bf16(sl->d.Z, sl->f.Zb, st);
             else copy_sell_f32(sl->d.Z, sl->f.Z, st);
+            if (lv.Ainv.n_rows) copy_sell_f32(sl->d.Ainv, sl->f.Ainv, st);
         }
         int vb = mixed_precision(H.opt) ? 4 : 8;
         int p = int(lv.alpha.size()) - 1;
         bytes += (H.opt.precision == AIRG_MIXED_FP32_BF16R ? sell_bytes(sl->d.Z, vb) - 2LL * lv.Z.nnz
                                                             : sell_bytes(sl->d.Z, vb)) +
                  sell_bytes(sl->d.M, vb) + 4LL * lv.n_f +
-                 p * sell_bytes(sl->d.Aff, vb) + 2LL * lv.n_f * vb;
+                 (lv.Ainv.n_rows ? sell_bytes(sl->d.Ainv, vb) : p * sell_bytes(sl->d.Aff, vb)) +
+                 2LL * lv.n_f * vb;
         S->max_nf = std::max(S->max_nf, lv.n_f);
         CK(cudaStreamSynchronize(st));
         S->lv.push_back(std::move(sl));
@@ -1836,7 +1851,13 @@ void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info)
         int p = int(lv.alpha.size()) - 1;
         // kept for the solve: A_ff, A_fc, R = [Z I], P = [W; I] (Sec. 3)
         store += lv.A_ff.nnz + lv.A_fc.nnz + (lv.Z.nnz + lv.n_c) + (lv.n_f + lv.n_c);
-        flops += 2LL * lv.Z.nnz + 2LL * lv.A_fc.nnz + 2LL * lv.A_ff.nnz * (p + 1);
+        flops += 2LL * lv.Z.nnz + 2LL * lv.A_fc.nnz;
+        if (lv.Ainv.n_rows) {   // assembled smoother: the Eq. 8 matrix is kept and applied once
+            store += lv.Ainv.nnz;
+            flops += 2LL * lv.A_ff.nnz + 2LL * lv.Ainv.nnz;
+        } else {
+            flops += 2LL * lv.A_ff.nnz * (p + 1);
+        }
     }
     if (L < 64) {
         info->n[L] = H.coarse.A.n_rows;

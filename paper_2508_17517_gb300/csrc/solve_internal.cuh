@@ -126,6 +126,7 @@ template <class T>
 struct SolveLevelT {
     Sell<T> Z, M, Aff;
     Sell<T, bf16s> Zb;   // Z with bfloat16 values (precision AIRG_MIXED_FP32_BF16R)
+    Sell<T> Ainv;        // assembled Ahat_ff^-1 (smoother AIRG_SMOOTH_ASSEMBLED)
 };
 
 struct SolveLevel {

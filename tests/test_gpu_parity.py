@@ -30,7 +30,10 @@ def _lib():
 
 
 def _oopts(d):
-    return O.Options(**{k: v for k, v in d.items() if k not in ("precision", "outer")})
+    o = {k: v for k, v in d.items() if k not in ("precision", "outer", "smoother")}
+    if d.get("smoother", 0) == 1:
+        o["smoother"] = "assembled"
+    return O.Options(**o)
 
 
 def _csr_equal(M, exp, what, exact_values=True):
@@ -310,3 +313,16 @@ def test_bf16_restrictor_storage_error():
         its[prec] = info.iterations
     assert its[G.AIRG_MIXED_FP32_BF16R] <= its[G.AIRG_MIXED_FP32] + 2, its
 
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_assembled_smoother_matches_oracle(prec):
+    """Smoother = the assembled fixed-sparsity matrix of Eq. 8 (Sec. 2.2):
+    the stored matrices equal the oracle's bit for bit, and the solve matches
+    the oracle's solve with the same smoother and the sweep to 1e-9."""
+    w = workload("grid", (170, 143))
+    c = Case(w, {"smoother": G.AIRG_SMOOTH_ASSEMBLED, "precision": prec})
+    _check_setup(c)
+    for l, L in enumerate(c.Ho.levels):
+        _csr_equal(L.Ainv, G.airg_export_matrix(c.h, l, 4), "Ahat^-1 level %d" % l)
+    _check_solve(c)
