@@ -30,121 +30,143 @@ constexpr int BT = 256;          // threads per block (8 rows of the batch)
 constexpr int MAXB = 16;         // restart length of the batched FGMRES
 constexpr int MAXK = 128;        // right-hand sides per batch (KW <= 4)
 
-inline int grid_rows(long long n) { return grid_for(n * 32, BT); }
 
-// acc[j] = (row r of S) x[:, q], q = lane + 32 j: the dense diagonal term
-// (square operators) first, then the stored entries in slice order
-template <class T, int KW, class V = T>
-__device__ __forceinline__ void brow(const SellView<T, V>& S, int r, const T* __restrict__ x, int k,
-                                     int lane, T (&acc)[KW])
+// Rows of operator S times the k right-hand sides x ([row][rhs]): row r is
+// handled by PW warps of a block (BT/32/PW rows per block), lanes over the
+// right-hand sides (q = lane + 32 j, j < KW).  Warp `part` of a row adds the
+// row's stored entries e = part, part + PW, ... in order (after the dense
+// diagonal term, part 0); with PW > 1 the partial rows meet in shared memory
+// and are added in part order.  PW is fixed per operator from its row
+// lengths (1 for short rows, 4 for long ones), so results do not depend on
+// timing.  Then epi(r, acc) runs once per row.  `dot` = false skips the
+// product (acc = 0).  Every thread of the block reaches the barrier.
+template <class T, int KW, int PW, class V, class Epi>
+__device__ __forceinline__ void bfor_rows(const SellView<T, V>& S, const T* __restrict__ x, int k, bool dot,
+                                          const Epi& epi)
 {
-    const T dg = S.diag ? __ldg(S.diag + r) : T(0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int part = warp % PW;
+    const int r = blockIdx.x * (BT / 32 / PW) + warp / PW;
+    const bool valid = r < S.n_rows;
+    T acc[KW];
 #pragma unroll
-    for (int j = 0; j < KW; ++j) {
-        int q = lane + 32 * j;
-        acc[j] = (S.diag && q < k) ? dg * x[size_t(r) * k + q] : T(0);
+    for (int j = 0; j < KW; ++j) acc[j] = T(0);
+    if (valid && dot) {
+        if (part == 0 && S.diag) {
+            const T dg = __ldg(S.diag + r);
+#pragma unroll
+            for (int j = 0; j < KW; ++j) {
+                int q = lane + 32 * j;
+                if (q < k) acc[j] = dg * x[size_t(r) * k + q];
+            }
+        }
+        const int s = r >> 5;
+        const int b = S.sptr[s] + (r & 31), w = (S.sptr[s + 1] - S.sptr[s]) >> 5;
+        for (int e = part; e < w; e += PW) {
+            const int idx = b + 32 * e;
+            const T v = ldval<T>(S.val + idx);
+            const T* xr = x + size_t(__ldg(S.col + idx)) * k;
+#pragma unroll
+            for (int j = 0; j < KW; ++j) {
+                int q = lane + 32 * j;
+                if (q < k) acc[j] = fma(v, xr[q], acc[j]);
+            }
+        }
     }
-    const int s = r >> 5;
-    const int b = S.sptr[s] + (r & 31), w = (S.sptr[s + 1] - S.sptr[s]) >> 5;
-    for (int e = 0; e < w; ++e) {
-        const int idx = b + 32 * e;
-        const T v = ldval<T>(S.val + idx);
-        const T* xr = x + size_t(__ldg(S.col + idx)) * k;
+    if constexpr (PW > 1) {
+        __shared__ T red[BT / 32][KW * 32];
+#pragma unroll
+        for (int j = 0; j < KW; ++j) red[warp][j * 32 + lane] = acc[j];
+        __syncthreads();
+        if (part == 0) {
+#pragma unroll
+            for (int p = 1; p < PW; ++p)
+#pragma unroll
+                for (int j = 0; j < KW; ++j) acc[j] += red[warp + p][j * 32 + lane];
+        }
+    }
+    if (valid && part == 0) epi(r, lane, acc);
+}
+
+// blocks for n rows at PW warps per row
+inline int grid_rows(long long n, int pw) { return grid_for(n * pw, BT / 32); }
+
+template <class T, int KW, int PW>
+__global__ void kb_spmv(SellView<T> S, const T* __restrict__ x, T* __restrict__ y, int k)
+{
+    bfor_rows<T, KW, PW>(S, x, k, true, [&](int r, int lane, const T (&a)[KW]) {
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
             int q = lane + 32 * j;
-            if (q < k) acc[j] = fma(v, xr[q], acc[j]);
+            if (q < k) y[size_t(r) * k + q] = a[j];
         }
-    }
+    });
 }
 
-#define BROW_IDS(NROWS)                                                       \
-    const long long tid_ = (long long)blockIdx.x * blockDim.x + threadIdx.x; \
-    const int r = int(tid_ >> 5);                                            \
-    const int lane = threadIdx.x & 31;                                       \
-    if (r >= (NROWS)) return
-
-template <class T, int KW>
-__global__ void kb_spmv(SellView<T> S, const T* __restrict__ x, T* __restrict__ y, int k)
-{
-    BROW_IDS(S.n_rows);
-    T a[KW];
-    brow<T, KW>(S, r, x, k, lane, a);
-#pragma unroll
-    for (int j = 0; j < KW; ++j) {
-        int q = lane + 32 * j;
-        if (q < k) y[size_t(r) * k + q] = a[j];
-    }
-}
-
-template <class T, int KW, class V = T>
+template <class T, int KW, int PW, class V = T>
 __global__ void kb_restrict(SellView<T, V> Z, const T* __restrict__ sf, const T* __restrict__ sc,
                             T* __restrict__ dc, int k)
 {
-    BROW_IDS(Z.n_rows);
-    T a[KW];
-    brow<T, KW, V>(Z, r, sf, k, lane, a);
+    bfor_rows<T, KW, PW>(Z, sf, k, true, [&](int r, int lane, const T (&a)[KW]) {
 #pragma unroll
-    for (int j = 0; j < KW; ++j) {
-        int q = lane + 32 * j;
-        if (q < k) dc[size_t(r) * k + q] = sc[size_t(r) * k + q] + a[j];
-    }
+        for (int j = 0; j < KW; ++j) {
+            int q = lane + 32 * j;
+            if (q < k) dc[size_t(r) * k + q] = sc[size_t(r) * k + q] + a[j];
+        }
+    });
 }
 
-template <class T, int KW>
+template <class T, int KW, int PW>
 __global__ void kb_fresid(SellView<T> M, const T* __restrict__ rf, const T* __restrict__ ec,
                           T* __restrict__ t, T* __restrict__ w, T ap, int k)
 {
-    BROW_IDS(M.n_rows);
-    T a[KW];
-    brow<T, KW>(M, r, ec, k, lane, a);
+    bfor_rows<T, KW, PW>(M, ec, k, true, [&](int r, int lane, const T (&a)[KW]) {
 #pragma unroll
-    for (int j = 0; j < KW; ++j) {
-        int q = lane + 32 * j;
-        if (q < k) {
-            size_t o = size_t(r) * k + q;
-            T tt = rf[o] - a[j];
-            t[o] = tt;
-            w[o] = ap * tt;
+        for (int j = 0; j < KW; ++j) {
+            int q = lane + 32 * j;
+            if (q < k) {
+                size_t o = size_t(r) * k + q;
+                T tt = rf[o] - a[j];
+                t[o] = tt;
+                w[o] = ap * tt;
+            }
         }
-    }
+    });
 }
 
-template <class T, int KW>
+template <class T, int KW, int PW>
 __global__ void kb_horner(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
                           T* __restrict__ wout, T ak, int k)
 {
-    BROW_IDS(A.n_rows);
-    T a[KW];
-    brow<T, KW>(A, r, win, k, lane, a);
+    bfor_rows<T, KW, PW>(A, win, k, true, [&](int r, int lane, const T (&a)[KW]) {
 #pragma unroll
-    for (int j = 0; j < KW; ++j) {
-        int q = lane + 32 * j;
-        if (q < k) {
-            size_t o = size_t(r) * k + q;
-            wout[o] = fma(ak, t[o], a[j]);
+        for (int j = 0; j < KW; ++j) {
+            int q = lane + 32 * j;
+            if (q < k) {
+                size_t o = size_t(r) * k + q;
+                wout[o] = fma(ak, t[o], a[j]);
+            }
         }
-    }
+    });
 }
 
-template <class T, int KW>
+template <class T, int KW, int PW>
 __global__ void kb_horner_last(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
                                const T* __restrict__ ec, const int* __restrict__ W,
                                T* __restrict__ ef, T a0, int k)
 {
-    BROW_IDS(A.n_rows);
-    T a[KW];
-    brow<T, KW>(A, r, win, k, lane, a);
-    const int wc = W[r];
+    bfor_rows<T, KW, PW>(A, win, k, true, [&](int r, int lane, const T (&a)[KW]) {
+        const int wc = W[r];
 #pragma unroll
-    for (int j = 0; j < KW; ++j) {
-        int q = lane + 32 * j;
-        if (q < k) {
-            size_t o = size_t(r) * k + q;
-            T p = wc >= 0 ? ec[size_t(wc) * k + q] : T(0);
-            ef[o] = p + fma(a0, t[o], a[j]);
+        for (int j = 0; j < KW; ++j) {
+            int q = lane + 32 * j;
+            if (q < k) {
+                size_t o = size_t(r) * k + q;
+                T p = wc >= 0 ? ec[size_t(wc) * k + q] : T(0);
+                ef[o] = p + fma(a0, t[o], a[j]);
+            }
         }
-    }
+    });
 }
 
 template <class T>
@@ -159,59 +181,56 @@ __global__ void kb_smooth0(long long n, const T* __restrict__ t, const T* __rest
     ef[i] = (wc >= 0 ? ec[size_t(wc) * k + q] : T(0)) + a0 * t[i];
 }
 
-template <class T, int KW>
+template <class T, int KW, int PW>
 __global__ void kb_newton_real(SellView<T> A, const T* __restrict__ rin, T* __restrict__ rout,
                                T* __restrict__ x, T inv, int first, int last, int k)
 {
-    BROW_IDS(A.n_rows);
-    T a[KW];
-    if (!last) brow<T, KW>(A, r, rin, k, lane, a);
+    bfor_rows<T, KW, PW>(A, rin, k, !last, [&](int r, int lane, const T (&a)[KW]) {
 #pragma unroll
-    for (int j = 0; j < KW; ++j) {
-        int q = lane + 32 * j;
-        if (q < k) {
-            size_t o = size_t(r) * k + q;
-            T ri = rin[o];
-            x[o] = fma(ri, inv, first ? T(0) : x[o]);
-            if (!last) rout[o] = ri - a[j] * inv;
+        for (int j = 0; j < KW; ++j) {
+            int q = lane + 32 * j;
+            if (q < k) {
+                size_t o = size_t(r) * k + q;
+                T ri = rin[o];
+                x[o] = fma(ri, inv, first ? T(0) : x[o]);
+                if (!last) rout[o] = ri - a[j] * inv;
+            }
         }
-    }
+    });
 }
 
-template <class T, int KW>
+template <class T, int KW, int PW>
 __global__ void kb_newton_pair1(SellView<T> A, const T* __restrict__ rin, T* __restrict__ t,
                                 T* __restrict__ x, T two_a, T inv2, int first, int k)
 {
-    BROW_IDS(A.n_rows);
-    T a[KW];
-    brow<T, KW>(A, r, rin, k, lane, a);
+    bfor_rows<T, KW, PW>(A, rin, k, true, [&](int r, int lane, const T (&a)[KW]) {
 #pragma unroll
-    for (int j = 0; j < KW; ++j) {
-        int q = lane + 32 * j;
-        if (q < k) {
-            size_t o = size_t(r) * k + q;
-            T tt = two_a * rin[o] - a[j];
-            t[o] = tt;
-            x[o] = fma(tt, inv2, first ? T(0) : x[o]);
+        for (int j = 0; j < KW; ++j) {
+            int q = lane + 32 * j;
+            if (q < k) {
+                size_t o = size_t(r) * k + q;
+                T tt = two_a * rin[o] - a[j];
+                t[o] = tt;
+                x[o] = fma(tt, inv2, first ? T(0) : x[o]);
+            }
         }
-    }
+    });
 }
 
-template <class T, int KW>
+template <class T, int KW, int PW>
 __global__ void kb_newton_pair2(SellView<T> A, const T* __restrict__ rin, const T* __restrict__ t,
                                 T* __restrict__ rout, T inv2, int k)
 {
-    BROW_IDS(A.n_rows);
-    T a[KW];
-    brow<T, KW>(A, r, t, k, lane, a);
+    bfor_rows<T, KW, PW>(A, t, k, true, [&](int r, int lane, const T (&a)[KW]) {
 #pragma unroll
-    for (int j = 0; j < KW; ++j) {
-        int q = lane + 32 * j;
-        if (q < k) {
-            size_t o = size_t(r) * k + q;
-            rout[o] = rin[o] - a[j] * inv2;
+        for (int j = 0; j < KW; ++j) {
+            int q = lane + 32 * j;
+            if (q < k) {
+                size_t o = size_t(r) * k + q;
+                rout[o] = rin[o] - a[j] * inv2;
+            }
         }
-    }
+    });
 }
 
 __global__ void kb_d2f(long long m, const double* a, float* b)
@@ -382,6 +401,14 @@ __global__ void kb_sub(long long m, const double* b, const double* y, double* r)
         else { constexpr int KW = 4; __VA_ARGS__; }                       \
     } while (0)
 
+// Runs the statement with KW (right-hand sides per lane) and PW (warps per
+// row: 1 for operators with short rows, 4 for long rows) of operator S.
+#define WITH_KWPW(k, S, ...)                                              \
+    do {                                                                  \
+        if ((S).k == 1) { constexpr int PW = 1; WITH_KW(k, __VA_ARGS__); } \
+        else { constexpr int PW = 4; WITH_KW(k, __VA_ARGS__); }           \
+    } while (0)
+
 }  // namespace
 
 // Work space of one batch width k.
@@ -438,13 +465,13 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         if (lv.n_c && Zb.val.n)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Zb) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
                      (2 * Zb.nnz + lv.n_c) * kk,
-                     WITH_KW(k, kb_restrict<T, KW, bf16s><<<grid_rows(lv.n_c), BT, 0, st>>>(
+                     WITH_KWPW(k, Zb, kb_restrict<T, KW, PW, bf16s><<<grid_rows(lv.n_c, PW), BT, 0, st>>>(
                                     view(Zb), src + size_t(lv.off) * k, src + size_t(lv.off + lv.n_f) * k,
                                     wk.rwork + size_t(lv.off + lv.n_f) * k, k)));
         else if (lv.n_c)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
                      (2 * Z.nnz + lv.n_c) * kk,
-                   WITH_KW(k, kb_restrict<T, KW><<<grid_rows(lv.n_c), BT, 0, st>>>(
+                   WITH_KWPW(k, Z, kb_restrict<T, KW, PW><<<grid_rows(lv.n_c, PW), BT, 0, st>>>(
                                   view(Z), src + size_t(lv.off) * k, src + size_t(lv.off + lv.n_f) * k,
                                   wk.rwork + size_t(lv.off + lv.n_f) * k, k)));
     }
@@ -467,16 +494,16 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
             if (q.im == 0.0) {
                 LAUNCH_F(S, PK_NEWTON, (last ? 0 : mB + 2 * nB) + (i == 0 ? 2 : 3) * nB,
                          (last ? 2LL * nco : 2 * A.nnz + 4LL * nco) * kk,
-                       WITH_KW(k, kb_newton_real<T, KW><<<grid_rows(nco), BT, 0, st>>>(
+                       WITH_KWPW(k, A, kb_newton_real<T, KW, PW><<<grid_rows(nco, PW), BT, 0, st>>>(
                                       Av, rin, rout, x, T(1.0 / q.re), i == 0, last, k)));
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
                 LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, (2 * A.nnz + 4LL * nco) * kk,
-                       WITH_KW(k, kb_newton_pair1<T, KW><<<grid_rows(nco), BT, 0, st>>>(
+                       WITH_KWPW(k, A, kb_newton_pair1<T, KW, PW><<<grid_rows(nco, PW), BT, 0, st>>>(
                                       Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0, k)));
                 if (!last)
                     LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, (2 * A.nnz + 2LL * nco) * kk,
-                           WITH_KW(k, kb_newton_pair2<T, KW><<<grid_rows(nco), BT, 0, st>>>(
+                           WITH_KWPW(k, A, kb_newton_pair2<T, KW, PW><<<grid_rows(nco, PW), BT, 0, st>>>(
                                           Av, rin, wk.ct, rout, T(1.0 / mod2), k)));
             }
             if (!last) { rin = rout; nb ^= 1; }
@@ -495,12 +522,12 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         const long long fB = (long long)nf * VB * kk;
         S.cur_level = l;
         LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB * kk + 3 * fB, (2 * o.M.nnz + 2LL * nf) * kk,
-               WITH_KW(k, kb_fresid<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
+               WITH_KWPW(k, o.M, kb_fresid<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
                                                                         T(lv.alpha[p]), k)));
         if (o.Ainv.n_rows) {
             // assembled smoother: e_f = W e_c + Ahat^-1 t (last Horner kernel, a0 = 0)
             LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, (2 * o.Ainv.nnz + 3LL * nf) * kk,
-                     WITH_KW(k, kb_horner_last<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.Ainv), wk.t, wk.t, ec,
+                     WITH_KWPW(k, o.Ainv, kb_horner_last<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Ainv), wk.t, wk.t, ec,
                                                                                    lv.W.p, ef, T(0), k)));
             continue;
         }
@@ -515,12 +542,12 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         T* wout = wk.wb;
         for (int kq = p - 1; kq >= 1; --kq) {
             LAUNCH_F(S, PK_HORNER, hB, (2 * o.Aff.nnz + 2LL * nf) * kk,
-                   WITH_KW(k, kb_horner<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.Aff), wk.t, win, wout,
+                   WITH_KWPW(k, o.Aff, kb_horner<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Aff), wk.t, win, wout,
                                                                             T(lv.alpha[kq]), k)));
             std::swap(win, wout);
         }
         LAUNCH_F(S, PK_HORNER, hB + fB + 4LL * nf, (2 * o.Aff.nnz + 3LL * nf) * kk,
-               WITH_KW(k, kb_horner_last<T, KW><<<grid_rows(nf), BT, 0, st>>>(view(o.Aff), wk.t, win, ec,
+               WITH_KWPW(k, o.Aff, kb_horner_last<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Aff), wk.t, win, ec,
                                                                              lv.W.p, ef, T(lv.alpha[0]), k)));
     }
     S.cur_level = 0;
@@ -646,7 +673,7 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
     for (int q = 0; q < k; ++q) tol[q] = std::max(rtol * bn[q], atol);
     auto residual = [&]() {
         LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz * k,
-               WITH_KW(k, kb_spmv<double, KW><<<grid_rows(n), BT, 0, st>>>(A, B.xp.p, B.w.p, k)));
+               WITH_KWPW(k, S.Atop, kb_spmv<double, KW, PW><<<grid_rows(n, PW), BT, 0, st>>>(A, B.xp.p, B.w.p, k)));
         LAUNCH_F(S, PK_KRYLOV, 24 * nk, nk, kb_sub<<<g, BT, 0, st>>>(nk, B.bp.p, B.w.p, B.r.p));
         bnorms(S, B, B.r.p, rn, st);
     };
@@ -692,7 +719,7 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
             double* zj = B.Zs.p + size_t(j) * nk;
             bprecond(H, B, vj, zj, st);
             LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz * k,
-                   WITH_KW(k, kb_spmv<double, KW><<<grid_rows(n), BT, 0, st>>>(A, zj, B.w.p, k)));
+                   WITH_KWPW(k, S.Atop, kb_spmv<double, KW, PW><<<grid_rows(n, PW), BT, 0, st>>>(A, zj, B.w.p, k)));
             // CGS with a second pass only if some active right-hand side lost
             // more than half of ||w||^2 in the first ("twice is enough")
             double* h1 = B.hdev.p;
