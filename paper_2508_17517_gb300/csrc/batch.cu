@@ -245,22 +245,53 @@ __global__ void kb_f2d(long long m, const float* a, double* b)
 }
 
 // [q][i] (caller, natural order) <-> [pos(i)][q] (batch, nested order)
-__global__ void kb_to_nested(long long n, int k, const int* pos, const double* a, double* b)
+// [q][i] (caller: right-hand sides one after the other, natural order) <->
+// [pos(i)][q] (batch: rows in nested order, right-hand sides adjacent), a
+// transpose with a row permutation.  A block moves a tile of 32 rows x 32
+// right-hand sides through shared memory so that both the reads and the
+// writes are runs of 32 consecutive doubles.  Block: 32 x 8 threads; grid:
+// (ceil(n/32), ceil(k/32)).
+constexpr int TT = 32;
+__global__ void __launch_bounds__(256)
+kb_to_nested(long long n, int k, const int* pos, const double* a, double* b)
 {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n * k) return;
-    int q = int(t / n);
-    long long i = t % n;
-    b[size_t(pos[i]) * k + q] = a[t];
+    __shared__ double tile[TT][TT + 1];
+    const long long i0 = (long long)blockIdx.x * TT;
+    const int q0 = blockIdx.y * TT;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int qq = ty; qq < TT; qq += 8) {              // read: consecutive i
+        const long long i = i0 + tx;
+        const int q = q0 + qq;
+        if (i < n && q < k) tile[qq][tx] = a[size_t(q) * n + i];
+    }
+    __syncthreads();
+    for (int ii = ty; ii < TT; ii += 8) {              // write: consecutive q
+        const long long i = i0 + ii;
+        const int q = q0 + tx;
+        if (i < n && q < k) b[size_t(pos[i]) * k + q] = tile[tx][ii];
+    }
 }
-__global__ void kb_from_nested(long long n, int k, const int* pos, const double* a, double* b)
+__global__ void __launch_bounds__(256)
+kb_from_nested(long long n, int k, const int* pos, const double* a, double* b)
 {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n * k) return;
-    int q = int(t / n);
-    long long i = t % n;
-    b[t] = a[size_t(pos[i]) * k + q];
+    __shared__ double tile[TT][TT + 1];
+    const long long i0 = (long long)blockIdx.x * TT;
+    const int q0 = blockIdx.y * TT;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int ii = ty; ii < TT; ii += 8) {              // read: consecutive q
+        const long long i = i0 + ii;
+        const int q = q0 + tx;
+        if (i < n && q < k) tile[tx][ii] = a[size_t(pos[i]) * k + q];
+    }
+    __syncthreads();
+    for (int qq = ty; qq < TT; qq += 8) {              // write: consecutive i
+        const long long i = i0 + tx;
+        const int q = q0 + qq;
+        if (i < n && q < k) b[size_t(q) * n + i] = tile[qq][tx];
+    }
 }
+
+inline dim3 grid_tiles(long long n, int k) { return dim3(unsigned((n + TT - 1) / TT), unsigned((k + TT - 1) / TT)); }
 
 // ----------------------------------------------------- batched Krylov work --
 constexpr int RG = 608;   // reduction blocks
@@ -666,8 +697,8 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
     const int g = grid_for(nk, BT);
     SellView<double> A = view(S.Atop);
     const long long topB = mat_bytes(S.Atop) + 16 * nk;
-    LAUNCH(S, PK_LAYOUT, 20 * nk, kb_to_nested<<<g, BT, 0, st>>>(n, k, S.pos0.p, b, B.bp.p));
-    LAUNCH(S, PK_LAYOUT, 20 * nk, kb_to_nested<<<g, BT, 0, st>>>(n, k, S.pos0.p, x, B.xp.p));
+    LAUNCH(S, PK_LAYOUT, 20 * nk, kb_to_nested<<<grid_tiles(n, k), 256, 0, st>>>(n, k, S.pos0.p, b, B.bp.p));
+    LAUNCH(S, PK_LAYOUT, 20 * nk, kb_to_nested<<<grid_tiles(n, k), 256, 0, st>>>(n, k, S.pos0.p, x, B.xp.p));
     std::vector<double> bn, rn, tol(k);
     bnorms(S, B, B.bp.p, bn, st);
     for (int q = 0; q < k; ++q) tol[q] = std::max(rtol * bn[q], atol);
@@ -809,7 +840,7 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
         worst = std::max(worst, rel);
         if (rn[q] > tol[q]) conv = 0;
     }
-    LAUNCH(S, PK_LAYOUT, 20 * nk, kb_from_nested<<<g, BT, 0, st>>>(n, k, S.pos0.p, B.xp.p, x));
+    LAUNCH(S, PK_LAYOUT, 20 * nk, kb_from_nested<<<grid_tiles(n, k), 256, 0, st>>>(n, k, S.pos0.p, B.xp.p, x));
     CK_LAUNCH();
     info.iterations = std::max(info.iterations, its);
     info.rel_residual = std::max(info.rel_residual, worst);
