@@ -191,7 +191,9 @@ airg_status airg_setup(const airg_csr* A, const airg_options* opt, void* stream,
  * unpreconditioned norm of Sec. 3.  b and x hold nrhs vectors of length n,
  * one after the other; x is the initial guess on entry and the solution on
  * exit.  on_device = 1: b and x are DEVICE pointers; 0: HOST pointers (the
- * copies in and out are part of the call).  info (HOST, may be NULL)
+ * copies in and out are part of the call; they go through device buffers
+ * that the handle keeps, grown to the largest call, so pinned host memory
+ * gives copies at link speed and no allocation per call).  info (HOST, may be NULL)
  * receives the worst iteration count / residual over the right-hand sides.
  * AIRG_ERR_NOT_CONVERGED still returns x and info.
  */

@@ -1781,16 +1781,18 @@ void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_de
     long long launches0 = S.launches;
     airg_solve_info info{};
     info.converged = 1;
-    DBuf<double> bd, xd;
     const double* bdev = b;
     double* xdev = x;
     if (!on_device) {
-        bd.alloc(size_t(n) * nrhs);
-        xd.alloc(size_t(n) * nrhs);
-        h2d(bd.p, b, size_t(n) * nrhs, st);
-        h2d(xd.p, x, size_t(n) * nrhs, st);
-        bdev = bd.p;
-        xdev = xd.p;
+        // staging buffers grow to the largest call and are reused, so a call
+        // with host buffers costs its copies and no allocation
+        const size_t need = size_t(n) * nrhs;
+        if (S.stage_b.n < need) S.stage_b.alloc(need);
+        if (S.stage_x.n < need) S.stage_x.alloc(need);
+        h2d(S.stage_b.p, b, need, st);
+        h2d(S.stage_x.p, x, need, st);
+        bdev = S.stage_b.p;
+        xdev = S.stage_x.p;
     }
     int g = grid_for(n, TB);
     const char* nb = getenv("AIRG_NO_BATCH");
@@ -1813,7 +1815,7 @@ void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_de
         CK_LAUNCH();
     }
     if (!on_device) {
-        CK(cudaMemcpyAsync(x, xd.p, sizeof(double) * n * nrhs, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(x, S.stage_x.p, sizeof(double) * n * nrhs, cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
     S.collect();

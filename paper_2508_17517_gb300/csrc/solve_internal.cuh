@@ -162,6 +162,7 @@ struct SolveData {
     HBuf<double> hhost;
     long long bytes_vcycle = 0;
     std::shared_ptr<BatchData> batch;   // work space of the many-RHS solve (batch.cu)
+    DBuf<double> stage_b, stage_x;      // device copies of host b and x, kept between calls
     // launch count and optional per-kind CUDA-event timing of the solve kernels
     long long launches = 0;
     bool prof = false;
