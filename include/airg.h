@@ -228,6 +228,11 @@ airg_status airg_setup_batch(int nprob, const airg_csr* As, const airg_options* 
 airg_status airg_solve_batch(airg_batch* b, const double* const* bvec, double* const* xvec,
                              int on_device, double rtol, double atol, int maxit,
                              airg_solve_info* infos, void* stream);
+/* Levels, sizes, complexities and V-cycle bytes of problem i (0 <= i <
+ * nprob) of a batch, as airg_setup_info gives them for one hierarchy.  info
+ * is a HOST pointer.  AIRG_ERR_ARG for a null batch or info or i out of
+ * range. */
+airg_status airg_batch_setup_info(const airg_batch* b, int i, airg_hierarchy_info* info);
 void airg_batch_free(airg_batch* b);
 
 /* Levels, sizes and the complexities of Sec. 3.  info is a HOST pointer. */

@@ -33,7 +33,7 @@ EXPORTS = ["airg_options_default", "airg_problem_advection2d", "airg_assemble_rh
            "airg_dot_exact", "airg_rng_uniform", "airg_host_gmres_coeffs", "airg_host_eigvals",
            "airg_profile", "airg_profile_read", "airg_profile_read_level", "airg_dot_exact_noalloc",
            "airg_rhs_adjoint_advection2d", "airg_setup_batch", "airg_solve_batch",
-           "airg_batch_free", "airg_check_wait_timeout"]
+           "airg_batch_free", "airg_batch_setup_info", "airg_check_wait_timeout"]
 PROFILE_KINDS = ["restrict", "f_residual", "f_smoother", "coarse_newton", "top_spmv",
                  "krylov_vectors", "layout"]
 
@@ -101,6 +101,7 @@ def lib():
             "airg_solve_adjoint": [vp, ci, vp, vp, ci, f64, f64, ci,
                                    ctypes.POINTER(airg_solve_info), vp],
             "airg_setup_info": [vp, ctypes.POINTER(airg_hierarchy_info)],
+            "airg_batch_setup_info": [vp, ci, ctypes.POINTER(airg_hierarchy_info)],
             "airg_export_matrix": [vp, ci, ci, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                    ctypes.POINTER(i64), vp, vp, vp],
             "airg_export_vector": [vp, ci, ci, ctypes.POINTER(i64), vp],
@@ -305,6 +306,17 @@ def airg_solve_adjoint(handle, rhs, lam=None, rtol=1e-10, atol=1e-50, maxit=200,
 def airg_setup_info(handle):
     info = airg_hierarchy_info()
     _check(lib().airg_setup_info(handle.ptr, ctypes.byref(info)))
+    return _info_dict(info)
+
+
+def airg_batch_setup_info(batch, i):
+    """airg_setup_info of problem i of a batch."""
+    info = airg_hierarchy_info()
+    _check(lib().airg_batch_setup_info(batch.ptr, int(i), ctypes.byref(info)))
+    return _info_dict(info)
+
+
+def _info_dict(info):
     L = info.levels
     return {"levels": L, "truncated": bool(info.truncated), "coarse_roots": info.coarse_roots,
             "coarse_krylov": info.coarse_krylov,

@@ -36,6 +36,9 @@ struct airg_batch_s {
     airg::HBuf<double> hbuf;               // pinned copies of every dv
     std::vector<cudaGraphExec_t> graphs;   // per iteration index j
     cudaGraphExec_t rich = nullptr;        // one Richardson iteration
+    std::vector<std::vector<long long>> gk;   // kernels per problem in graphs[j]
+    std::vector<long long> rk;                // kernels per problem in rich
+    std::vector<airg::DBuf<double>> stage_b, stage_x;   // device copies of host b, x
     int m = 0;
     ~airg_batch_s()
     {
@@ -197,8 +200,23 @@ void solve_multi(airg_batch_s& B, const double* const* b, double* const* x, bool
     for (cudaStream_t s : B.ps) CK(cudaStreamWaitEvent(s, ev, 0));
     CK(cudaStreamWaitEvent(B.master, ev, 0));
     CK(cudaEventDestroy(ev));
-    std::vector<airg::DBuf<double>> hb(P), hx(P);
+    std::vector<airg::DBuf<double>>& hb = B.stage_b;
+    std::vector<airg::DBuf<double>>& hx = B.stage_x;
     std::vector<PState> st(P);
+    // kernel launches per problem: the ones issued eagerly, plus every
+    // graph launch's kernels; the captures themselves run nothing
+    std::vector<long long> l0(P), cap(P, 0), run(P, 0);
+    for (int p = 0; p < P; ++p) l0[p] = B.H[p]->solve->launches;
+    auto counted = [&](std::vector<long long>& k, auto&& capture) {
+        k.assign(size_t(P), 0);
+        for (int p = 0; p < P; ++p) k[p] = -B.H[p]->solve->launches;
+        cudaGraphExec_t g = capture();
+        for (int p = 0; p < P; ++p) {
+            k[p] += B.H[p]->solve->launches;
+            cap[p] += k[p];
+        }
+        return g;
+    };
     // inputs into the nested order, norms of b and of the first residual
     for (int p = 0; p < P; ++p) {
         airg::Hierarchy& H = *B.H[p];
@@ -207,8 +225,8 @@ void solve_multi(airg_batch_s& B, const double* const* b, double* const* x, bool
         const double* bd = b[p];
         const double* xd = x[p];
         if (!on_device) {
-            hb[p].alloc(n);
-            hx[p].alloc(n);
+            if (hb[p].n < size_t(n)) hb[p].alloc(size_t(n));
+            if (hx[p].n < size_t(n)) hx[p].alloc(size_t(n));
             airg::h2d(hb[p].p, b[p], size_t(n), B.ps[p]);
             airg::h2d(hx[p].p, x[p], size_t(n), B.ps[p]);
             bd = hb[p].p;
@@ -244,8 +262,9 @@ void solve_multi(airg_batch_s& B, const double* const* b, double* const* x, bool
         }
         sync_all(B);
         if (!nact) break;
-        if (!B.rich) B.rich = capture_richardson(B);
+        if (!B.rich) B.rich = counted(B.rk, [&] { return capture_richardson(B); });
         CK(cudaGraphLaunch(B.rich, B.master));
+        for (int p = 0; p < P; ++p) run[p] += B.rk[p];
         read_all(B, B.master);
         ++its;
         for (int p = 0; p < P; ++p) {
@@ -270,8 +289,9 @@ void solve_multi(airg_batch_s& B, const double* const* b, double* const* x, bool
         sync_all(B);
         if (!nact) break;
         for (int j = 0; j < m; ++j) {
-            if (!B.graphs[j]) B.graphs[j] = capture_iteration(B, j);
+            if (!B.graphs[j]) B.graphs[j] = counted(B.gk[j], [&] { return capture_iteration(B, j); });
             CK(cudaGraphLaunch(B.graphs[j], B.master));
+            for (int p = 0; p < P; ++p) run[p] += B.gk[j][p];
             read_all(B, B.master);
             ++its;
             // second Gram-Schmidt pass where the first cancelled too much
@@ -362,7 +382,7 @@ void solve_multi(airg_batch_s& B, const double* const* b, double* const* x, bool
             infos[p].iterations = st[p].its;
             infos[p].rel_residual = st[p].bn > 0 ? st[p].rn / st[p].bn : 0.0;
             infos[p].converged = conv;
-            infos[p].kernel_launches = 0;
+            infos[p].kernel_launches = B.H[p]->solve->launches - l0[p] - cap[p] + run[p];
         }
     }
     sync_all(B);
@@ -412,6 +432,9 @@ airg_status airg_setup_batch(int nprob, const airg_csr* As, const airg_options* 
         CK(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
         B->hbuf.alloc(size_t(nprob) * of.total());
         B->graphs.assign(size_t(B->m), nullptr);
+        B->gk.assign(size_t(B->m), {});
+        B->stage_b.resize(size_t(nprob));
+        B->stage_x.resize(size_t(nprob));
         *out = B.release();
     });
 }
@@ -425,6 +448,14 @@ airg_status airg_solve_batch(airg_batch* b, const double* const* bvec, double* c
         for (size_t p = 0; p < b->H.size(); ++p)
             if (!bvec[p] || !xvec[p]) fail(AIRG_ERR_ARG, "null vector in the batch");
         solve_multi(*b, bvec, xvec, on_device != 0, rtol, atol, maxit, infos, (cudaStream_t)stream);
+    });
+}
+
+airg_status airg_batch_setup_info(const airg_batch* b, int i, airg_hierarchy_info* info)
+{
+    return guarded([&] {
+        if (!b || !info || i < 0 || size_t(i) >= b->H.size()) fail(AIRG_ERR_ARG, "bad batch index or info");
+        airg::fill_setup_info(*b->H[size_t(i)], info);
     });
 }
 

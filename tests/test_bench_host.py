@@ -38,3 +38,11 @@ def test_traffic_table_lookup():
     assert t3 is not None and 1.5e8 < t3 < 2.5e8
     assert bench.measured_traffic("c2", "f_smoother", 0) is None
     assert bench.measured_traffic("c4a", "coarse_newton", 8) is None
+
+
+def test_many_grid_aggregate_roofline():
+    """The many-grid line reports V-cycle bytes over the whole solve's time."""
+    e = bench.multi_roofline(6 * 10**9, 2.0, 6769.4, "measured")
+    assert e["bound"] == "hbm" and e["unit"] == "GB/s"
+    assert abs(e["achieved"] - 3000.0) < 1e-9
+    assert abs(e["frac"] - 3000.0 / 6769.4) < 1e-12

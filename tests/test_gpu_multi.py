@@ -56,6 +56,13 @@ def test_uneven_batch_matches_oracle(host):
     xs2, infos2 = G.airg_solve_batch(B, bs, rtol=1e-10)
     for x, x2 in zip(xs, xs2):
         assert np.linalg.norm((x - x2).cpu().numpy()) <= 1e-12 * np.linalg.norm(x.cpu().numpy())
+    # both solves ran the same kernels: graph replays count like the first run
+    for i, (a, b2) in enumerate(zip(infos, infos2)):
+        assert a.kernel_launches > 0 and a.kernel_launches == b2.kernel_launches
+        si = G.airg_batch_setup_info(B, i)
+        assert si["n"][0] == shapes[i][0] * shapes[i][1] and si["bytes_per_vcycle"] > 0
+    with pytest.raises(G.AirgError):
+        G.airg_batch_setup_info(B, len(shapes))
 
 
 def test_uneven_batch_richardson():
