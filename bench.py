@@ -44,10 +44,11 @@ def parse(argv=None):
     ap.add_argument("--workload", default="c2",
                     choices=["c1", "c2", "c3", "c3_fp64", "c3_bf16", "c4a", "c4a_fp64", "c4a_bf16", "c4b"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sweep", choices=["coarse-order", "smoother"], default=None,
+    ap.add_argument("--sweep", choices=["coarse-order", "smoother", "cases"], default=None,
                     help="instead of the throughput line, one JSON line with a row per setting: "
                          "coarse-order = the coarse polynomial order / truncation study of Sec. 3.1; "
-                         "smoother = matrix-free polynomial vs assembled Eq. 8 smoother (Sec. 2.2)")
+                         "smoother = matrix-free polynomial vs assembled Eq. 8 smoother (Sec. 2.2); "
+                         "cases = hard direction (Sec. 3.3.2) and rectangular domain (Sec. 3.4)")
     return ap.parse_args(argv)
 
 
@@ -493,10 +494,12 @@ def _sweep_row(G, torch, prob, b, opts, args):
     solve_ms = statistics.median(times)
     nit = statistics.median(its)
     return {"levels": info["levels"], "coarse_rows": info["n"][-1], "truncated": info["truncated"],
+            "grid_complexity": round(sum(info["n"]) / info["n"][0], 3),
             "cycle_complexity": round(info["cycle_complexity"], 2),
             "storage_complexity": round(info["storage_complexity"], 2),
             "setup_s": round(setup_s, 3), "iterations": nit, "solve_ms": round(solve_ms, 3),
-            "ms_per_iteration": round(solve_ms / max(nit, 1), 3)}
+            "ms_per_iteration": round(solve_ms / max(nit, 1), 3),
+            "dof_per_s_per_vcycle": info["n"][0] * nit / (solve_ms / 1e3)}
 
 
 def run_sweep(args):
@@ -512,6 +515,9 @@ def run_sweep(args):
     torch.cuda.set_device(0)
     import paper_2508_17517_gb300 as G
     G.lib()
+    if args.sweep == "cases":
+        run_cases(G, torch, args)
+        return
     n = 4096
     th = math.pi / 4
     vx, vy = math.cos(th), math.sin(th)
@@ -534,6 +540,26 @@ def run_sweep(args):
                                  **r))
     print(json.dumps({"sweep": args.sweep, "grid": "%dx%d" % (n, n), "theta": "pi/4", "g": 1.0,
                       "rtol": 1e-10, "steps": args.steps, "warmup": args.warmup, "rows": rows}))
+
+
+def run_cases(G, torch, args):
+    """The paper's two other single-direction studies at one GPU's share:
+    the hard direction v = (sqrt(2/3), sqrt(1/3)) with strong threshold 0.4
+    on 2896^2 (Sec. 3.3.2), and the 500 x 26000 rectangle at theta = pi/4
+    with coarse order 10 (Sec. 3.4).  FP64, g = 1, s = 0, rtol 1e-10."""
+    from synthetic import velocity, workload
+    rows = []
+    for name in ("hard", "rect"):
+        w = workload(name)
+        vx, vy = velocity(w["theta"])
+        prob = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
+        b = G.airg_assemble_rhs_advection2d(prob, torch.tensor(w["g"][0], device="cuda"))
+        r = _sweep_row(G, torch, prob, b, G.airg_options_default(**w["opts"]), args)
+        rows.append(dict({"case": name, "workload": w["desc"]}, **r))
+        del prob, b
+        torch.cuda.empty_cache()
+    print(json.dumps({"sweep": "cases", "rtol": 1e-10, "steps": args.steps, "warmup": args.warmup,
+                      "rows": rows}))
 
 
 def main(argv=None):

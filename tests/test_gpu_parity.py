@@ -164,6 +164,16 @@ def test_ragged_grids(shape):
     _check_solve(c)
 
 
+@pytest.mark.parametrize("name,shape", [("hard", (150, 150)), ("rect", (30, 1200))])
+def test_hard_direction_and_rectangle(name, shape):
+    """The paper's other studies at oracle size: v = (sqrt(2/3), sqrt(1/3))
+    with strong threshold 0.4 (Sec. 3.3.2), and a long thin rectangle at
+    pi/4 with coarse order 10 (Sec. 3.4)."""
+    c = Case(workload(name, shape))
+    _check_setup(c)
+    _check_solve(c)
+
+
 def test_host_buffer_path():
     c = Case(workload("grid", (120, 90)))
     _check_solve(c, host=True)

@@ -146,6 +146,21 @@ def test_strength_hand_cases():
     assert not np.any(s2[P2.A.col == rid])                       # diagonal never strong
 
 
+def test_strength_hard_direction_threshold():
+    """v = (sqrt(2/3), sqrt(1/3)) (Sec. 3.3.2): the y-upwind entry is
+    sqrt(1/2) = 0.707 of the x-upwind one, so the default threshold 0.99
+    keeps only the x neighbour and the paper's 0.4 keeps both."""
+    th = math.atan2(math.sqrt(1 / 3), math.sqrt(2 / 3))
+    P = _grid(8, 8, th)
+    assert abs(math.cos(th) - math.sqrt(2 / 3)) < 1e-15
+    rid = P.A.row_ids()
+    s = O.strength(P.A, 0.99)
+    assert s.sum() == 64 - 15 and np.all(P.A.col[s] - rid[s] == -1)
+    s4 = O.strength(P.A, 0.4)
+    assert s4.sum() == 2 * (64 - 15)
+    assert sorted(set((P.A.col[s4] - rid[s4]).tolist())) == [-8, -1]
+
+
 def _path_graph(n):
     r = np.concatenate([np.arange(n - 1), np.arange(1, n)])
     c = np.concatenate([np.arange(1, n), np.arange(n - 1)])
