@@ -11,7 +11,7 @@ Functions pinned by tests against closed forms, brute force or library
 routines: exact dot, SpMV, problem builder + sweep, strength, PMISR, DDC,
 extract, GMRES polynomial coefficients, fixed-sparsity inverse, restrictor,
 one-point prolongator, RAP + drop/lump, harmonic Ritz / Newton application,
-V-cycle, FGMRES, dense adjoint.
+V-cycle (F, FC and FCF smoothing), FGMRES, dense adjoint.
 Parity unpinned (internal choices with no closed form in the paper): the
 value of the R drop tolerance, the PMISR measure direction, the one-point
 weight, and the Loe-Morgan added-root thresholds.
@@ -29,6 +29,7 @@ PURPOSE_COEF = 1      # random rhs for the smoother polynomial coefficients (Sec
 PURPOSE_PMISR = 2     # Luby weights of PMISR (Sec. 2.1)
 PURPOSE_COARSE = 3    # random rhs for the coarse-grid polynomial (Sec. 2.3)
 PURPOSE_TRUNC = 4     # second random rhs of the truncation test (Sec. 2.4)
+PURPOSE_COEF_C = 5    # random rhs for the C-point smoother polynomial (reading: a stream of its own)
 
 
 def _p(a):
@@ -233,6 +234,7 @@ class Options:
     addroot_log10: float = 4.0       # Loe-Morgan extra-root threshold (unpinned)
     addroot_per: float = 14.0
     smoother: str = "polynomial"     # "assembled": e_f += Ahat_ff^-1 t with the Eq. 8 matrix
+    smooth_type: str = "f"           # "fc": F- then C-point smoothing; "fcf": F, C, F (Sec. 2, 3.3.2)
 
 
 # --------------------------------------------------------------------------
@@ -476,15 +478,16 @@ def power_coefficients(H, beta, y):
     return alpha
 
 
-def gmres_poly_coeffs(A_ff, opts, level):
+def gmres_poly_coeffs(A_ff, opts, level, purpose=PURPOSE_COEF):
     """Coefficients of the degree-p GMRES polynomial q(A_ff) ~ A_ff^-1 (Eq. 7).
 
     Reading of "order p": degree p, p+1 coefficients, p+1 Arnoldi steps from a
     uniform [0,1) random rhs.  On breakdown the degree drops and the higher
-    coefficients are zero.
+    coefficients are zero.  The C-point smoother builds the same polynomial
+    for A_cc from its own random stream (purpose PURPOSE_COEF_C).
     """
     p = opts.poly_order
-    b = rng_uniform(opts.seed, level, PURPOSE_COEF, A_ff.n_rows)
+    b = rng_uniform(opts.seed, level, purpose, A_ff.n_rows)
     H, k, broke, beta = arnoldi(A_ff, b, p + 1, opts.breakdown_tol, opts.exact_tol)
     y = givens_lsq(H, beta)
     alpha = power_coefficients(H, beta, y)
@@ -706,6 +709,10 @@ class Level:
     ddc_converted: list
     trunc_rel: float = float("nan")
     Ainv: CSR = None                 # fixed-sparsity Ahat_ff^-1 (Eq. 8)
+    A_cf: CSR = None                 # kept for C-point smoothing only
+    A_cc: CSR = None
+    alpha_c: np.ndarray = None       # GMRES polynomial of A_cc (C-point smoother)
+    alpha_c_k: int = 0
 
 
 @dataclass
@@ -723,6 +730,10 @@ def setup(A, opts=None):
     """AIRG setup, level by level, in the order of Sec. 2 (Sec. 2.4: the
     truncation test comes before the CF splitting on each level)."""
     opts = opts or Options()
+    if opts.smooth_type not in ("f", "fc", "fcf"):
+        raise ValueError("smooth_type must be f, fc or fcf")
+    if opts.smooth_type != "f" and opts.smoother == "assembled":
+        raise ValueError("C-point smoothing is built with the matrix-free polynomial smoother only")
     Hh = Hierarchy(opts=opts)
     level = 0
     while True:
@@ -755,8 +766,15 @@ def setup(A, opts=None):
         Z = restrictor_block(A_cf, Ainv, opts.r_drop)
         W = one_point(A, strong, is_f)
         Ac = coarse_matrix(A, is_f, Z, W, opts.a_drop, opts.a_lump)
-        Hh.levels.append(Level(n, A, strong, is_f, A_ff, A_fc, Z, W, alpha, k, rounds, conv,
-                               trunc_rel, Ainv))
+        lev = Level(n, A, strong, is_f, A_ff, A_fc, Z, W, alpha, k, rounds, conv, trunc_rel, Ainv)
+        if opts.smooth_type != "f":
+            # C-point smoothing keeps A_cf and A_cc (Sec. 2) and applies a
+            # GMRES polynomial of A_cc matrix-free, as the F-point smoother
+            # does for A_ff
+            lev.A_cf = A_cf
+            lev.A_cc = extract(A, ~is_f, ~is_f)
+            lev.alpha_c, lev.alpha_c_k, _ = gmres_poly_coeffs(lev.A_cc, opts, level, PURPOSE_COEF_C)
+        Hh.levels.append(lev)
         A = Ac
         level += 1
 
@@ -769,7 +787,13 @@ def vcycle(Hh, r, level=0):
     prolongate with W, then one F-point smooth e_f += q(A_ff)(r_f - A_fc e_c -
     A_ff e_f) (Eq. 6).  With smoother "assembled" the approximate inverse is
     the stored fixed-sparsity matrix of Eq. 8 instead of the matrix-free
-    polynomial (the alternative the paper times in Sec. 2.2)."""
+    polynomial (the alternative the paper times in Sec. 2.2).
+
+    smooth_type "fc" follows the F-point smooth with a C-point smooth, and
+    "fcf" with a C-point and a second F-point smooth (the options the paper
+    lists in Sec. 3.3.2; Sec. 2 says C-point smoothing needs A_cc and
+    A_cf).  Reading: the C-point smooth is the block analogue of Eq. 6 with a
+    GMRES polynomial of A_cc of the same order."""
     if level == len(Hh.levels):
         return newton_apply(Hh.A_coarse, Hh.roots, r)
     L = Hh.levels[level]
@@ -781,6 +805,16 @@ def vcycle(Hh, r, level=0):
     if Hh.opts is not None and Hh.opts.smoother == "assembled":
         ef = ef + spmv(L.Ainv, t)
     else:
+        ef = ef + horner_apply(L.A_ff, L.alpha, t)
+    st = Hh.opts.smooth_type if Hh.opts is not None else "f"
+    if st in ("fc", "fcf"):
+        # C-point smooth on the level's own C residual (the value before
+        # restriction): e_c += q_c(A_cc)(r_c - A_cf e_f - A_cc e_c)
+        tc = r[~L.is_f] - spmv(L.A_cf, ef) - spmv(L.A_cc, ec)
+        ec = ec + horner_apply(L.A_cc, L.alpha_c, tc)
+    if st == "fcf":
+        # a second F-point smooth, Eq. 6 with the current e_c and e_f
+        t = rf - spmv(L.A_fc, ec) - spmv(L.A_ff, ef)
         ef = ef + horner_apply(L.A_ff, L.alpha, t)
     e = np.empty(L.n)
     e[L.is_f] = ef
@@ -894,6 +928,7 @@ def complexities(Hh):
     top-level SpMV (2 flops per stored entry)."""
     top = Hh.levels[0].A.nnz if Hh.levels else Hh.A_coarse.nnz
     assembled = Hh.opts is not None and Hh.opts.smoother == "assembled"
+    st = Hh.opts.smooth_type if Hh.opts is not None else "f"
     store = 0
     flops = 0
     for L in Hh.levels:
@@ -905,6 +940,11 @@ def complexities(Hh):
             flops += 2 * L.A_ff.nnz + 2 * L.Ainv.nnz
         else:
             flops += 2 * L.A_ff.nnz * (p + 1)
+        if st != "f":
+            store += L.A_cf.nnz + L.A_cc.nnz
+            flops += 2 * L.A_cf.nnz + 2 * L.A_cc.nnz * len(L.alpha_c)
+        if st == "fcf":
+            flops += 2 * L.A_fc.nnz + 2 * L.A_ff.nnz * (p + 1)
     nr = len(Hh.roots)
     store += Hh.A_coarse.nnz
     flops += 2 * Hh.A_coarse.nnz * max(nr - 1, 0)

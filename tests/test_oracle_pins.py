@@ -555,3 +555,43 @@ def test_assembled_smoother_exact_and_convergent():
     ca, cp = O.complexities(ha), O.complexities(hp)
     extra = sum(L.Ainv.nnz for L in ha.levels) / P.A.nnz
     assert abs(ca["storage"] - cp["storage"] - extra) < 1e-12
+
+
+@pytest.mark.parametrize("theta", [0.5, 1.0, 3.5])
+def test_c_point_smoothing_zeroes_its_block_residual(theta):
+    """Block smoothing with an exact block inverse zeroes that block's
+    residual (Sec. 2, Eq. 6 and its C-point analogue): on a 7 x 6 grid every
+    level is small enough that the GMRES polynomials of A_ff and A_cc reach
+    the exact inverse (the Krylov space breaks down), and the coarse
+    polynomial is exact.  After one V-cycle from zero, the residual r - A e
+    is zero on the F points when the last smooth is an F-point smooth (f,
+    fcf) and zero on the C points after an fc cycle; the other block's
+    residual is not (the check is not vacuous)."""
+    P = _grid(7, 6, theta)
+    r = np.random.default_rng(0).standard_normal(P.A.n_rows)
+    res = {}
+    for st in ("f", "fc", "fcf"):
+        H = O.setup(P.A, O.Options(poly_order=45, coarse_poly_order=100, trunc_rtol=0.0, smooth_type=st))
+        L = H.levels[0]
+        assert L.alpha_k <= L.A_ff.n_rows and (st == "f" or L.alpha_c_k <= L.A_cc.n_rows)
+        e = O.vcycle(H, r)
+        rr = r - O.spmv(P.A, e)
+        res[st] = (np.linalg.norm(rr[L.is_f]), np.linalg.norm(rr[~L.is_f]))
+    nr = np.linalg.norm(r)
+    assert res["f"][0] <= 1e-12 * nr and res["f"][1] > 1e-3 * nr
+    assert res["fc"][1] <= 1e-12 * nr and res["fc"][0] > 1e-3 * nr
+    assert res["fcf"][0] <= 1e-12 * nr and res["fcf"][1] > 1e-4 * nr
+
+
+def test_c_point_smoothing_storage_is_the_rest_of_a():
+    """C-point smoothing keeps A_cf and A_cc, so per level the stored blocks
+    add up to all of A_l (the four blocks of Eq. 3 partition A)."""
+    P = _grid(40, 36, 0.9)
+    Hf = O.setup(P.A, O.Options(smooth_type="f"))
+    Hc = O.setup(P.A, O.Options(smooth_type="fc"))
+    top = P.A.nnz
+    extra = sum(L.A.nnz - L.A_ff.nnz - L.A_fc.nnz for L in Hc.levels)
+    sf, sc = O.complexities(Hf)["storage"], O.complexities(Hc)["storage"]
+    assert abs((sc - sf) * top - extra) < 1e-6
+    for L in Hc.levels:
+        assert L.A_cf.nnz + L.A_cc.nnz + L.A_ff.nnz + L.A_fc.nnz == L.A.nnz
