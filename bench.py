@@ -47,7 +47,8 @@ def parse(argv=None):
     ap.add_argument("--sweep", choices=["coarse-order", "smoother", "cases"], default=None,
                     help="instead of the throughput line, one JSON line with a row per setting: "
                          "coarse-order = the coarse polynomial order / truncation study of Sec. 3.1; "
-                         "smoother = matrix-free polynomial vs assembled Eq. 8 smoother (Sec. 2.2); "
+                         "smoother = matrix-free polynomial vs assembled Eq. 8 smoother (Sec. 2.2) and F vs FC/FCF "
+                         "smoothing (Sec. 2); "
                          "cases = hard direction (Sec. 3.3.2) and rectangular domain (Sec. 3.4)")
     return ap.parse_args(argv)
 
@@ -508,8 +509,9 @@ def run_sweep(args):
     coarse-order (Sec. 3.1): m_c in {5, 10, 30, 100} with truncation at
     alpha_trunc = 0.1 on every level vs no truncation, FP64.  smoother
     (Sec. 2.2): the matrix-free GMRES polynomial vs the assembled
-    fixed-sparsity matrix of Eq. 8, FP64 and FP32 V-cycles, m_c = 30 with
-    truncation at 1e-2.  Solve times are the median of `steps` device-timed
+    fixed-sparsity matrix of Eq. 8, and F-point vs FC and FCF smoothing
+    (Sec. 2, Sec. 3.3.2), FP64 and FP32 V-cycles, m_c = 30 with truncation
+    at 1e-2.  Solve times are the median of `steps` device-timed
     solves after `warmup` untimed ones."""
     import torch
     torch.cuda.set_device(0)
@@ -531,12 +533,16 @@ def run_sweep(args):
                 r = _sweep_row(G, torch, prob, b, G.airg_options_default(coarse_poly_order=mc, trunc_rtol=trunc), args)
                 rows.append(dict({"coarse_order": mc, "truncation": trunc}, **r))
     else:
+        settings = [(G.AIRG_SMOOTH_POLYNOMIAL, G.AIRG_SMOOTH_F), (G.AIRG_SMOOTH_ASSEMBLED, G.AIRG_SMOOTH_F),
+                    (G.AIRG_SMOOTH_POLYNOMIAL, G.AIRG_SMOOTH_FC), (G.AIRG_SMOOTH_POLYNOMIAL, G.AIRG_SMOOTH_FCF)]
         for prec in (G.AIRG_FP64, G.AIRG_MIXED_FP32):
-            for sm in (G.AIRG_SMOOTH_POLYNOMIAL, G.AIRG_SMOOTH_ASSEMBLED):
-                opts = G.airg_options_default(coarse_poly_order=30, trunc_rtol=1e-2, precision=prec, smoother=sm)
+            for sm, stype in settings:
+                opts = G.airg_options_default(coarse_poly_order=30, trunc_rtol=1e-2, precision=prec, smoother=sm,
+                                              smooth_type=stype)
                 r = _sweep_row(G, torch, prob, b, opts, args)
                 rows.append(dict({"precision": "f64" if prec == G.AIRG_FP64 else "f32",
-                                  "smoother": "polynomial" if sm == G.AIRG_SMOOTH_POLYNOMIAL else "assembled"},
+                                  "smoother": "polynomial" if sm == G.AIRG_SMOOTH_POLYNOMIAL else "assembled",
+                                  "points": ("f", "fc", "fcf")[stype]},
                                  **r))
     print(json.dumps({"sweep": args.sweep, "grid": "%dx%d" % (n, n), "theta": "pi/4", "g": 1.0,
                       "rtol": 1e-10, "steps": args.steps, "warmup": args.warmup, "rows": rows}))

@@ -57,6 +57,15 @@ enum { AIRG_OUTER_FGMRES = 0, AIRG_OUTER_RICHARDSON = 1 };
  * as one SpMV (the alternative timed in Sec. 2.2; stores one more matrix per
  * level). */
 enum { AIRG_SMOOTH_POLYNOMIAL = 0, AIRG_SMOOTH_ASSEMBLED = 1 };
+/* Which points are smoothed on the way up (Sec. 2; the options listed in
+ * Sec. 3.3.2): F points only (the paper's default, Eq. 6); F then C points;
+ * F, C, then F again.  A C-point smooth applies a GMRES polynomial of A_cc
+ * of the same degree, matrix-free, to r_c - A_cf e_f - A_cc e_c, where r_c
+ * is the level's C residual before restriction; it keeps A_cf and A_cc on
+ * every level.  FC and FCF need the matrix-free polynomial smoother
+ * (AIRG_ERR_ARG otherwise); airg_solve with nrhs > 1 then solves the
+ * right-hand sides one after the other, and airg_setup_batch rejects them. */
+enum { AIRG_SMOOTH_F = 0, AIRG_SMOOTH_FC = 1, AIRG_SMOOTH_FCF = 2 };
 
 /* Compressed sparse row matrix (n_rows x n_cols).  Caller-owned, read-only. */
 typedef struct {
@@ -95,6 +104,7 @@ typedef struct {
     int gmres_restart;         /* outer FGMRES restart length                 */
     int outer;                 /* AIRG_OUTER_FGMRES or AIRG_OUTER_RICHARDSON  */
     int smoother;              /* AIRG_SMOOTH_POLYNOMIAL or _ASSEMBLED        */
+    int smooth_type;           /* AIRG_SMOOTH_F, _FC or _FCF                  */
 } airg_options;
 
 typedef struct airg_handle_s airg_handle;

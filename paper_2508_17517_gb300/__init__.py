@@ -18,6 +18,9 @@ AIRG_OK = 0
 AIRG_ERR_NOT_CONVERGED = 5
 AIRG_SMOOTH_POLYNOMIAL = 0
 AIRG_SMOOTH_ASSEMBLED = 1
+AIRG_SMOOTH_F = 0
+AIRG_SMOOTH_FC = 1
+AIRG_SMOOTH_FCF = 2
 AIRG_OUTER_FGMRES = 0
 AIRG_OUTER_RICHARDSON = 1
 AIRG_FP64 = 0
@@ -48,7 +51,8 @@ class airg_options(ctypes.Structure):
                 ("breakdown_tol", ctypes.c_double), ("exact_tol", ctypes.c_double),
                 ("addroot_log10", ctypes.c_double),
                 ("addroot_per", ctypes.c_double), ("precision", ctypes.c_int),
-                ("gmres_restart", ctypes.c_int), ("outer", ctypes.c_int), ("smoother", ctypes.c_int)]
+                ("gmres_restart", ctypes.c_int), ("outer", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("smooth_type", ctypes.c_int)]
 
 
 class airg_csr(ctypes.Structure):

@@ -131,6 +131,10 @@ void check_options(const airg_options& o)
     if (o.outer != AIRG_OUTER_FGMRES && o.outer != AIRG_OUTER_RICHARDSON) airg::fail(AIRG_ERR_ARG, "bad outer");
     if (o.smoother != AIRG_SMOOTH_POLYNOMIAL && o.smoother != AIRG_SMOOTH_ASSEMBLED)
         airg::fail(AIRG_ERR_ARG, "bad smoother");
+    if (o.smooth_type != AIRG_SMOOTH_F && o.smooth_type != AIRG_SMOOTH_FC && o.smooth_type != AIRG_SMOOTH_FCF)
+        airg::fail(AIRG_ERR_ARG, "bad smooth_type");
+    if (o.smooth_type != AIRG_SMOOTH_F && o.smoother != AIRG_SMOOTH_POLYNOMIAL)
+        airg::fail(AIRG_ERR_ARG, "C-point smoothing needs the matrix-free polynomial smoother");
 }
 
 airg::DevCSR upload_csr(const airg_csr* A, cudaStream_t st)
@@ -207,6 +211,7 @@ airg_status airg_options_default(airg_options* o)
     o->gmres_restart = 30;
     o->outer = AIRG_OUTER_FGMRES;
     o->smoother = AIRG_SMOOTH_POLYNOMIAL;
+    o->smooth_type = AIRG_SMOOTH_F;
     return AIRG_OK;
 }
 
@@ -371,6 +376,10 @@ airg_status airg_export_matrix(const airg_handle* h, int level, int what, int64_
                     if (!lv.Ainv.n_rows && lv.n_f) airg::fail(AIRG_ERR_ARG, "the approximate inverse is kept only with the assembled smoother");
                     M = &lv.Ainv;
                     break;
+                case 5:
+                    if (H->opt.smooth_type == AIRG_SMOOTH_F) airg::fail(AIRG_ERR_ARG, "A_cc is kept only with C-point smoothing");
+                    M = &lv.A_cc;
+                    break;
                 default: airg::fail(AIRG_ERR_ARG, "bad matrix id");
             }
         }
@@ -426,6 +435,11 @@ airg_status airg_export_vector(const airg_handle* h, int level, int what, int64_
                 if (out) std::memcpy(out, s.data(), s.size() * sizeof(double));
                 break;
             }
+            case 5:
+                if (H->opt.smooth_type == AIRG_SMOOTH_F) airg::fail(AIRG_ERR_ARG, "no C-point smoother");
+                *count = int64_t(lv.alpha_c.size());
+                if (out) std::memcpy(out, lv.alpha_c.data(), lv.alpha_c.size() * sizeof(double));
+                break;
             default: airg::fail(AIRG_ERR_ARG, "bad vector id");
         }
     });

@@ -23,6 +23,12 @@ struct SetupLevel {
     DevCSR A_ff, A_fc, Z;     // blocks of Eq. 3; Z = -A_cf Ahat_ff^-1 after drop
     DevCSR M;                 // rows of A P at the F points = A_fc + A_ff W
     DevCSR Ainv;              // fixed-sparsity Ahat_ff^-1 (Eq. 8), kept for the assembled smoother
+    // C-point smoothing only: A_cc, the C rows [A_cf A_cc] and the F rows
+    // [A_ff A_fc] of A_l with the level's own column numbering, and the
+    // GMRES polynomial of A_cc
+    DevCSR A_cc, Crows, Frows;
+    std::vector<double> alpha_c;
+    int alpha_c_k = 0;
     DBuf<int> W;              // one-point prolongator: C-local index or -1
     std::vector<double> alpha;    // p+1 smoother coefficients (zero-padded)
     int alpha_k = 0;              // Krylov dimension reached (p+1 unless breakdown)

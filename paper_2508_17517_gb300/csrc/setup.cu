@@ -28,7 +28,7 @@ namespace airg {
 namespace {
 
 constexpr int TB = 256;
-enum { PURPOSE_COEF = 1, PURPOSE_PMISR = 2, PURPOSE_COARSE = 3, PURPOSE_TRUNC = 4 };
+enum { PURPOSE_COEF = 1, PURPOSE_PMISR = 2, PURPOSE_COARSE = 3, PURPOSE_TRUNC = 4, PURPOSE_COEF_C = 5 };
 
 // ------------------------------------------------------------- prefix sum --
 constexpr int SCAN_B = 1024;
@@ -1046,12 +1046,12 @@ ArnoldiOut arnoldi(Ctx& c, const DevCSR& A, const double* b, int m, double tol, 
 }
 
 std::vector<double> gmres_poly_coeffs(Ctx& c, const DevCSR& Aff, const airg_options& o, int level,
-                                      int& kout)
+                                      int& kout, int purpose = PURPOSE_COEF)
 {
     int p = o.poly_order;
     long long n = Aff.n_rows;
     DBuf<double> b(n);
-    k_rng_uniform<<<grid_for(n, TB), TB, 0, c.st>>>(stream_key(o.seed, level, PURPOSE_COEF), n, b.p);
+    k_rng_uniform<<<grid_for(n, TB), TB, 0, c.st>>>(stream_key(o.seed, level, purpose), n, b.p);
     CK_LAUNCH();
     ArnoldiOut ar = arnoldi(c, Aff, b.p, p + 1, o.breakdown_tol, o.exact_tol);
     std::vector<double> y = givens_lsq(ar.H, ar.k, ar.beta);
@@ -1358,6 +1358,14 @@ std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, c
         DevCSR Zfull;
         spgemm(A_cf, Ainv, Zfull, st);
         if (o.smoother == AIRG_SMOOTH_ASSEMBLED) L->Ainv = std::move(Ainv);
+        if (o.smooth_type != AIRG_SMOOTH_F) {
+            // C-point smoothing (Sec. 2): the GMRES polynomial of A_cc from
+            // its own random stream, and the row blocks its residuals use
+            submatrix(Al, L->c_ids.p, L->n_c, L->c_index.p, L->n_c, L->A_cc, st);
+            submatrix(Al, L->c_ids.p, L->n_c, nullptr, n, L->Crows, st);
+            if (o.smooth_type == AIRG_SMOOTH_FCF) submatrix(Al, L->f_ids.p, L->n_f, nullptr, n, L->Frows, st);
+            L->alpha_c = gmres_poly_coeffs(c, L->A_cc, o, level, L->alpha_c_k, PURPOSE_COEF_C);
+        }
         if (Zfull.nnz) k_scale<<<grid_for(Zfull.nnz, TB), TB, 0, st>>>(Zfull.nnz, Zfull.v.p, -1.0);
         {
             DBuf<int8_t> keep(std::max(Zfull.nnz, 1));

@@ -492,6 +492,30 @@ __global__ void k_smooth0(int n, const T* __restrict__ t, const T* __restrict__ 
     ef[r] = (wc >= 0 ? ec[wc] : T(0)) + a0 * t[r];
 }
 
+// last Horner term of a smoother that corrects in place: e += a_0 t + A win
+// (the C-point smooth, and the second F-point smooth of FCF)
+template <class T, int K, int R>
+__global__ void k_horner_acc(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win, T* e, T a0)
+{
+    for_rows<T, K, R>(A, win, [&](int r) { return Pair<T>{t[r], e[r]}; },
+                      [&](int r, T d, Pair<T> q) { e[r] = q.b + fma(a0, q.a, d); });
+}
+
+// degree-0 in-place correction: e += a_0 t
+template <class T>
+__global__ void k_acc0(int n, const T* __restrict__ t, T* __restrict__ e, T a0)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) e[r] = e[r] + a0 * t[r];
+}
+
+template <class T>
+__global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n) b[r] = a[r];
+}
+
 // Newton steps of the coarse polynomial (Sec. 2.3)
 // real root, not the last: x += r / theta, r' = r - A r / theta
 template <class T, int K, int R>
@@ -950,6 +974,7 @@ __global__ void k_from_nested(long long n, const int* pos, const double* a, doub
 template <class T>
 struct VWork {
     T* rwork; T* t; T* wa; T* wb; T* cx; T* cr0; T* cr1; T* ct;
+    T* rcs;    // C residuals before restriction (C-point smoothing)
 };
 
 template <class T>
@@ -981,6 +1006,147 @@ int newton_persistent_grid(const Sell<T>& A)
     return std::min(groups, per_sm * sms);
 }
 
+// Prolongation and the F-point smooth of level l (Eq. 6): t = r_f - M e_c
+// with M = A_fc + A_ff W, then e_f = W e_c + q(A_ff) t
+template <class T>
+void f_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
+{
+    constexpr long long VB = sizeof(T);
+    const SolveLevel& lv = *S.lv[l];
+    const T* src = l == 0 ? v : wk.rwork;
+    const SolveLevelT<T>& o = ops<T>(lv);
+    const T* rf = src + lv.off;
+    const T* ec = e + lv.off + lv.n_f;
+    T* ef = e + lv.off;
+    int nf = lv.n_f;
+    int g = grid_for(nf, TB);
+    int p = int(lv.alpha.size()) - 1;
+    const long long fB = (long long)nf * VB;
+    const int pidx2 = sizeof(T) == 8 ? 0 : 1;
+    S.cur_level = l;
+    if (o.Ainv.n_rows) {
+        // assembled smoother (Eq. 8 matrix): t = r_f - M e_c, then
+        // e_f = W e_c + Ahat^-1 t, the last Horner kernel with a0 = 0
+        LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
+                 WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M), block_rows(o.M), 0, st>>>(
+                                  view(o.M), rf, ec, wk.t, wk.wa, T(0))));
+        LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, 2 * o.Ainv.nnz + 3LL * nf,
+                 WITH_KR(o.Ainv, k_horner_last<T, KK, RR><<<grid_rows(o.Ainv), block_rows(o.Ainv), 0, st>>>(
+                                     view(o.Ainv), wk.t, wk.t, ec, lv.W.p, ef, T(0))));
+        return;
+    }
+    if (S.smooth_grid[pidx2] > 0 && p < 32) {
+        Coefs al{};
+        for (int q = 0; q <= p; ++q) al.a[q] = lv.alpha[q];
+        int need = std::max((o.M.n_slices + 32 / o.M.k - 1) / (32 / o.M.k),
+                            (o.Aff.n_slices + 32 / o.Aff.k - 1) / (32 / o.Aff.k));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(std::max(1, std::min(S.smooth_grid[pidx2], need)));
+        cfg.blockDim = dim3(1024);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        long long bytes = mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB +
+                          p * (mat_bytes(o.Aff) + 3 * fB) + fB + 4LL * nf;
+        SellView<T> Mv = view(o.M), Av2 = view(o.Aff);
+        const long long flops = 2 * o.M.nnz + 2LL * nf + p * (2 * o.Aff.nnz + 2LL * nf) + nf;
+        LAUNCH_F(S, PK_HORNER, bytes, flops,
+               CK(cudaLaunchKernelEx(&cfg, k_smooth_persistent<T>, Mv, o.M.k, Av2, o.Aff.k, rf, ec,
+                                     (const int*)lv.W.p, ef, wk.t, wk.wa, wk.wb, al, p, S.bar.p,
+                                     S.bar.p + 1, (int*)(S.bar.p + 2))));
+        return;
+    }
+    LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
+           WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M), block_rows(o.M), 0, st>>>(
+                            view(o.M), rf, ec, wk.t, wk.wa, T(lv.alpha[p]))));
+    if (p == 0) {
+        LAUNCH_F(S, PK_HORNER, 3 * fB + 4LL * nf, 3LL * nf,
+               k_smooth0<T><<<g, TB, 0, st>>>(nf, wk.t, ec, lv.W.p, ef, T(lv.alpha[0])));
+        return;
+    }
+    const long long hB = mat_bytes(o.Aff) + 3 * fB;
+    T* win = wk.wa;
+    T* wout = wk.wb;
+    for (int k = p - 1; k >= 1; --k) {
+        LAUNCH_F(S, PK_HORNER, hB, 2 * o.Aff.nnz + 2LL * nf,
+               WITH_KR(o.Aff, k_horner<T, KK, RR><<<grid_rows(o.Aff), block_rows(o.Aff), 0, st>>>(
+                                  view(o.Aff), wk.t, win, wout, T(lv.alpha[k]))));
+        std::swap(win, wout);
+    }
+    LAUNCH_F(S, PK_HORNER, hB + fB + 4LL * nf, 2 * o.Aff.nnz + 3LL * nf,
+           WITH_KR(o.Aff, k_horner_last<T, KK, RR><<<grid_rows(o.Aff), block_rows(o.Aff), 0, st>>>(
+                              view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0]))));
+}
+
+// e += q(A) t by Horner, with w = a_p t already in wk.wa (written by the
+// residual kernel) and t in wk.t; n rows
+template <class T>
+void horner_into(SolveData& S, const Sell<T>& A, const std::vector<double>& al, const VWork<T>& wk, T* e,
+                 int n, cudaStream_t st)
+{
+    constexpr long long VB = sizeof(T);
+    const int p = int(al.size()) - 1;
+    const long long fB = (long long)n * VB;
+    if (p == 0) {
+        LAUNCH_F(S, PK_HORNER, 3 * fB, 2LL * n, k_acc0<T><<<grid_for(n, TB), TB, 0, st>>>(n, wk.t, e, T(al[0])));
+        return;
+    }
+    const long long hB = mat_bytes(A) + 3 * fB;
+    T* win = wk.wa;
+    T* wout = wk.wb;
+    for (int k = p - 1; k >= 1; --k) {
+        LAUNCH_F(S, PK_HORNER, hB, 2 * A.nnz + 2LL * n,
+                 WITH_KR(A, k_horner<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(view(A), wk.t, win,
+                                                                                        wout, T(al[k]))));
+        std::swap(win, wout);
+    }
+    LAUNCH_F(S, PK_HORNER, hB + fB, 2 * A.nnz + 3LL * n,
+             WITH_KR(A, k_horner_acc<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(view(A), wk.t, win, e,
+                                                                                        T(al[0]))));
+}
+
+// C-point smooth of level l (Sec. 2): t_c = r_c - [A_cf A_cc] e_l with the
+// level's C residual from before restriction, then e_c += q_c(A_cc) t_c
+template <class T>
+void c_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
+{
+    constexpr long long VB = sizeof(T);
+    const SolveLevel& lv = *S.lv[l];
+    const SolveLevelT<T>& o = ops<T>(lv);
+    const int nc = lv.n_c;
+    if (!nc) return;
+    const T* rc = (l == 0 ? v : wk.rcs) + lv.off + lv.n_f;
+    T* el = e + lv.off;
+    const int p = int(lv.alpha_c.size()) - 1;
+    const long long cB = (long long)nc * VB;
+    LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mc) + (long long)(lv.n_f + nc) * VB + 3 * cB, 2 * o.Mc.nnz + 2LL * nc,
+             WITH_KR(o.Mc, k_fresid<T, KK, RR><<<grid_rows(o.Mc), block_rows(o.Mc), 0, st>>>(
+                              view(o.Mc), rc, el, wk.t, wk.wa, T(lv.alpha_c[p]))));
+    horner_into<T>(S, o.Acc, lv.alpha_c, wk, el + lv.n_f, nc, st);
+}
+
+// second F-point smooth of FCF: t = r_f - [A_ff A_fc] e_l, e_f += q(A_ff) t
+template <class T>
+void f_smooth_again(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
+{
+    constexpr long long VB = sizeof(T);
+    const SolveLevel& lv = *S.lv[l];
+    const SolveLevelT<T>& o = ops<T>(lv);
+    const int nf = lv.n_f;
+    if (!nf) return;
+    const T* rf = (l == 0 ? v : wk.rwork) + lv.off;
+    T* el = e + lv.off;
+    const int p = int(lv.alpha.size()) - 1;
+    const long long fB = (long long)nf * VB;
+    LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mf) + (long long)(nf + lv.n_c) * VB + 3 * fB, 2 * o.Mf.nnz + 2LL * nf,
+             WITH_KR(o.Mf, k_fresid<T, KK, RR><<<grid_rows(o.Mf), block_rows(o.Mf), 0, st>>>(
+                              view(o.Mf), rf, el, wk.t, wk.wa, T(lv.alpha[p]))));
+    horner_into<T>(S, o.Aff, lv.alpha, wk, el, nf, st);
+}
+
 // e = M^-1 v in the nested order.  v is only read; e is written everywhere.
 template <class T>
 void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
@@ -994,6 +1160,10 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         const Sell<T>& Z = ops<T>(lv).Z;
         const Sell<T, bf16s>& Zb = ops<T>(lv).Zb;
         S.cur_level = l;
+        if (l > 0 && lv.n_c && S.smooth_type != AIRG_SMOOTH_F)   // restriction overwrites r_c in place
+            LAUNCH_F(S, PK_RESTRICT, 2LL * lv.n_c * VB, 0,
+                     k_copy<T><<<grid_for(lv.n_c, TB), TB, 0, st>>>(lv.n_c, src + lv.off + lv.n_f,
+                                                                    wk.rcs + lv.off + lv.n_f));
         if (lv.n_c && Zb.val.n)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Zb) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Zb.nnz + lv.n_c,
                    WITH_KR(Zb, k_restrict<T, KK, RR, bf16s><<<grid_rows(Zb), block_rows(Zb), 0, st>>>(
@@ -1072,75 +1242,14 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         if (nr == 0) CK(cudaMemsetAsync(x, 0, sizeof(T) * S.n_coarse, st));
     }
 coarse_done:
-    // up: prolongation + F-point smoothing, bottom to top
+    // up: prolongation + smoothing, bottom to top
     for (int l = L - 1; l >= 0; --l) {
-        const SolveLevel& lv = *S.lv[l];
-        const T* src = l == 0 ? v : wk.rwork;
-        const SolveLevelT<T>& o = ops<T>(lv);
-        const T* rf = src + lv.off;
-        const T* ec = e + lv.off + lv.n_f;
-        T* ef = e + lv.off;
-        int nf = lv.n_f;
-        int g = grid_for(nf, TB);
-        int p = int(lv.alpha.size()) - 1;
-        const long long fB = (long long)nf * VB;
-        const int pidx2 = sizeof(T) == 8 ? 0 : 1;
         S.cur_level = l;
-        if (o.Ainv.n_rows) {
-            // assembled smoother (Eq. 8 matrix): t = r_f - M e_c, then
-            // e_f = W e_c + Ahat^-1 t, the last Horner kernel with a0 = 0
-            LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
-                     WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M), block_rows(o.M), 0, st>>>(
-                                      view(o.M), rf, ec, wk.t, wk.wa, T(0))));
-            LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, 2 * o.Ainv.nnz + 3LL * nf,
-                     WITH_KR(o.Ainv, k_horner_last<T, KK, RR><<<grid_rows(o.Ainv), block_rows(o.Ainv), 0, st>>>(
-                                         view(o.Ainv), wk.t, wk.t, ec, lv.W.p, ef, T(0))));
-            continue;
+        f_smooth<T>(S, l, v, e, wk, st);
+        if (S.smooth_type != AIRG_SMOOTH_F) {
+            c_smooth<T>(S, l, v, e, wk, st);
+            if (S.smooth_type == AIRG_SMOOTH_FCF) f_smooth_again<T>(S, l, v, e, wk, st);
         }
-        if (S.smooth_grid[pidx2] > 0 && p < 32) {
-            Coefs al{};
-            for (int q = 0; q <= p; ++q) al.a[q] = lv.alpha[q];
-            int need = std::max((o.M.n_slices + 32 / o.M.k - 1) / (32 / o.M.k),
-                                (o.Aff.n_slices + 32 / o.Aff.k - 1) / (32 / o.Aff.k));
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(std::max(1, std::min(S.smooth_grid[pidx2], need)));
-            cfg.blockDim = dim3(1024);
-            cfg.stream = st;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeCooperative;
-            attr[0].val.cooperative = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            long long bytes = mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB +
-                              p * (mat_bytes(o.Aff) + 3 * fB) + fB + 4LL * nf;
-            SellView<T> Mv = view(o.M), Av2 = view(o.Aff);
-            const long long flops = 2 * o.M.nnz + 2LL * nf + p * (2 * o.Aff.nnz + 2LL * nf) + nf;
-            LAUNCH_F(S, PK_HORNER, bytes, flops,
-                   CK(cudaLaunchKernelEx(&cfg, k_smooth_persistent<T>, Mv, o.M.k, Av2, o.Aff.k, rf, ec,
-                                         (const int*)lv.W.p, ef, wk.t, wk.wa, wk.wb, al, p, S.bar.p,
-                                         S.bar.p + 1, (int*)(S.bar.p + 2))));
-            continue;
-        }
-        LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
-               WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M), block_rows(o.M), 0, st>>>(
-                                view(o.M), rf, ec, wk.t, wk.wa, T(lv.alpha[p]))));
-        if (p == 0) {
-            LAUNCH_F(S, PK_HORNER, 3 * fB + 4LL * nf, 3LL * nf,
-                   k_smooth0<T><<<g, TB, 0, st>>>(nf, wk.t, ec, lv.W.p, ef, T(lv.alpha[0])));
-            continue;
-        }
-        const long long hB = mat_bytes(o.Aff) + 3 * fB;
-        T* win = wk.wa;
-        T* wout = wk.wb;
-        for (int k = p - 1; k >= 1; --k) {
-            LAUNCH_F(S, PK_HORNER, hB, 2 * o.Aff.nnz + 2LL * nf,
-                   WITH_KR(o.Aff, k_horner<T, KK, RR><<<grid_rows(o.Aff), block_rows(o.Aff), 0, st>>>(
-                                      view(o.Aff), wk.t, win, wout, T(lv.alpha[k]))));
-            std::swap(win, wout);
-        }
-        LAUNCH_F(S, PK_HORNER, hB + fB + 4LL * nf, 2 * o.Aff.nnz + 3LL * nf,
-               WITH_KR(o.Aff, k_horner_last<T, KK, RR><<<grid_rows(o.Aff), block_rows(o.Aff), 0, st>>>(
-                                  view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0]))));
     }
     S.cur_level = 0;
     CK_LAUNCH();
@@ -1220,6 +1329,9 @@ void tune_all(SolveData& S, cudaStream_t st)
         tune_rows(o.Z, x.p, y.p, fs, fl, st);
         tune_rows(o.Zb, x.p, y.p, fs, fl, st);
         tune_rows(o.Ainv, x.p, y.p, fs, fl, st);
+        tune_rows(o.Mc, x.p, y.p, fs, fl, st);
+        tune_rows(o.Acc, x.p, y.p, fs, fl, st);
+        tune_rows(o.Mf, x.p, y.p, fs, fl, st);
     }
     tune_rows(const_cast<Sell<T>&>(coarse_op<T>(S)), x.p, y.p, fs, fl, st);
     CK(cudaStreamSynchronize(st));
@@ -1301,6 +1413,8 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
     CK_LAUNCH();
     // level operators
     long long bytes = 0;
+    int max_nc = 0;
+    S->smooth_type = H.opt.smooth_type;
     for (int l = 0; l < L; ++l) {
         SetupLevel& lv = *H.levels[l];
         auto sl = std::make_unique<SolveLevel>();
@@ -1320,12 +1434,27 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         sl->W.alloc(std::max(lv.n_f, 1));
         if (lv.n_f) k_map_w<<<grid_for(lv.n_f, TB), TB, 0, st>>>(lv.n_f, lv.W.p, rel.p, perm[l].p, sl->W.p);
         CK_LAUNCH();
+        if (!lv.alpha_c.empty()) {
+            // C-point smoothing: row blocks of A_l over the level's nested
+            // positions (rl = position relative to the level's offset)
+            sl->alpha_c = lv.alpha_c;
+            DBuf<int> rl(std::max(lv.n, 1)), rinv(std::max(lv.n, 1));
+            k_rel<<<grid_for(lv.n, TB), TB, 0, st>>>(lv.n, pos[l].p, off[l], rl.p, rinv.p);
+            CK_LAUNCH();
+            build_sell<double>(lv.Crows, inv.p, rl.p, lv.n, sl->d.Mc, false, st);
+            build_sell<double>(lv.A_cc, inv.p, rel.p, lv.n_c, sl->d.Acc, true, st);
+            if (lv.Frows.n_rows) build_sell<double>(lv.Frows, iperm[l].p, rl.p, lv.n, sl->d.Mf, false, st);
+            max_nc = std::max(max_nc, lv.n_c);
+        }
         if (mixed_precision(H.opt)) {
             copy_sell_f32(sl->d.Aff, sl->f.Aff, st);
             copy_sell_f32(sl->d.M, sl->f.M, st);
             if (H.opt.precision == AIRG_MIXED_FP32_BF16R) copy_sell_bf16(sl->d.Z, sl->f.Zb, st);
             else copy_sell_f32(sl->d.Z, sl->f.Z, st);
             if (lv.Ainv.n_rows) copy_sell_f32(sl->d.Ainv, sl->f.Ainv, st);
+            if (sl->d.Mc.n_rows) copy_sell_f32(sl->d.Mc, sl->f.Mc, st);
+            if (sl->d.Acc.n_rows) copy_sell_f32(sl->d.Acc, sl->f.Acc, st);
+            if (sl->d.Mf.n_rows) copy_sell_f32(sl->d.Mf, sl->f.Mf, st);
         }
         int vb = mixed_precision(H.opt) ? 4 : 8;
         int p = int(lv.alpha.size()) - 1;
@@ -1334,6 +1463,12 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
                  sell_bytes(sl->d.M, vb) + 4LL * lv.n_f +
                  (lv.Ainv.n_rows ? sell_bytes(sl->d.Ainv, vb) : p * sell_bytes(sl->d.Aff, vb)) +
                  2LL * lv.n_f * vb;
+        if (!lv.alpha_c.empty()) {
+            const int pc = int(lv.alpha_c.size()) - 1;
+            bytes += sell_bytes(sl->d.Mc, vb) + pc * sell_bytes(sl->d.Acc, vb) + 2LL * lv.n_c * vb +
+                     (l > 0 ? 2LL * lv.n_c * vb : 0);
+            if (sl->d.Mf.n_rows) bytes += sell_bytes(sl->d.Mf, vb) + p * sell_bytes(sl->d.Aff, vb) + 2LL * lv.n_f * vb;
+        }
         S->max_nf = std::max(S->max_nf, lv.n_f);
         CK(cudaStreamSynchronize(st));
         S->lv.push_back(std::move(sl));
@@ -1403,10 +1538,14 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         CK(cudaStreamSynchronize(st));
     }
     // work vectors
-    size_t n0 = std::max(S->n0, 1), nf = std::max(S->max_nf, 1), nc = std::max(S->n_coarse, 1);
+    size_t n0 = std::max(S->n0, 1), nf = std::max({S->max_nf, max_nc, 1}), nc = std::max(S->n_coarse, 1);
     S->rwork.alloc(n0);
     S->t.alloc(nf); S->wa.alloc(nf); S->wb.alloc(nf);
     S->cr0.alloc(nc); S->cr1.alloc(nc); S->ct.alloc(nc);
+    if (S->smooth_type != AIRG_SMOOTH_F) {
+        if (mixed_precision(H.opt)) S->rcs32.alloc(n0);
+        else S->rcs.alloc(n0);
+    }
     if (mixed_precision(H.opt)) {
         S->rwork32.alloc(n0); S->e32.alloc(n0); S->vin32.alloc(n0);
         S->t32.alloc(nf); S->wa32.alloc(nf); S->wb32.alloc(nf);
@@ -1476,12 +1615,13 @@ void precond_launch(Hierarchy& H, const double* v, double* z, cudaStream_t st)
     long long n = S.n0;
     if (mixed_precision(H.opt)) {
         LAUNCH(S, PK_LAYOUT, 12 * n, k_d2f<<<grid_for(n, TB), TB, 0, st>>>(n, v, S.vin32.p));
-        VWork<float> wk{S.rwork32.p, S.t32.p, S.wa32.p, S.wb32.p, nullptr, S.cr032.p, S.cr132.p, S.ct32.p};
+        VWork<float> wk{S.rwork32.p, S.t32.p, S.wa32.p, S.wb32.p, nullptr, S.cr032.p, S.cr132.p, S.ct32.p,
+                        S.rcs32.p};
         vcycle<float>(S, S.vin32.p, S.e32.p, wk, st);
         LAUNCH(S, PK_LAYOUT, 12 * n, k_f2d<<<grid_for(n, TB), TB, 0, st>>>(n, S.e32.p, z));
         CK_LAUNCH();
     } else {
-        VWork<double> wk{S.rwork.p, S.t.p, S.wa.p, S.wb.p, nullptr, S.cr0.p, S.cr1.p, S.ct.p};
+        VWork<double> wk{S.rwork.p, S.t.p, S.wa.p, S.wb.p, nullptr, S.cr0.p, S.cr1.p, S.ct.p, S.rcs.p};
         vcycle<double>(S, v, z, wk, st);
     }
 }
@@ -1797,8 +1937,9 @@ void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_de
     int g = grid_for(n, TB);
     const char* nb = getenv("AIRG_NO_BATCH");
     int nseq = nrhs;   // right-hand sides solved one after the other
-    if (nrhs > 1 && !(nb && nb[0] == '1')) {
+    if (nrhs > 1 && !(nb && nb[0] == '1') && S.smooth_type == AIRG_SMOOTH_F) {
         // many right-hand sides: lockstep outer iteration with the batched V-cycle
+        // (C-point smoothing has only the one-vector V-cycle: solved in turn below)
         for (int q0 = 0; q0 < nrhs; q0 += batch_max_width()) {
             int kq = std::min(batch_max_width(), nrhs - q0);
             solve_batched(H, kq, bdev + size_t(q0) * n, xdev + size_t(q0) * n, rtol, atol, maxit, info, st);
@@ -1860,6 +2001,11 @@ void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info)
         } else {
             flops += 2LL * lv.A_ff.nnz * (p + 1);
         }
+        if (!lv.alpha_c.empty()) {   // C-point smoothing keeps A_cf and A_cc
+            store += lv.Crows.nnz;
+            flops += 2LL * lv.Crows.nnz + 2LL * lv.A_cc.nnz * (long long)(lv.alpha_c.size() - 1);
+        }
+        if (lv.Frows.n_rows) flops += 2LL * lv.Frows.nnz + 2LL * lv.A_ff.nnz * p;
     }
     if (L < 64) {
         info->n[L] = H.coarse.A.n_rows;

@@ -127,12 +127,17 @@ struct SolveLevelT {
     Sell<T> Z, M, Aff;
     Sell<T, bf16s> Zb;   // Z with bfloat16 values (precision AIRG_MIXED_FP32_BF16R)
     Sell<T> Ainv;        // assembled Ahat_ff^-1 (smoother AIRG_SMOOTH_ASSEMBLED)
+    // C-point smoothing: the C rows [A_cf A_cc] and (FCF) the F rows
+    // [A_ff A_fc] of A_l over the level's nested positions, and A_cc over
+    // the next level's
+    Sell<T> Mc, Acc, Mf;
 };
 
 struct SolveLevel {
     int off = 0, n_f = 0, n_c = 0;
     DBuf<int> W;                 // nested-relative C position, -1 none
     std::vector<double> alpha;
+    std::vector<double> alpha_c;     // C-point smoother polynomial (empty: none)
     SolveLevelT<double> d;
     SolveLevelT<float> f;
 };
@@ -155,6 +160,9 @@ struct SolveData {
     // V-cycle work (FP64 and FP32 copies)
     DBuf<double> rwork, t, wa, wb, cx, cr0, cr1, ct;
     DBuf<float> rwork32, e32, t32, wa32, wb32, cx32, cr032, cr132, ct32, vin32;
+    int smooth_type = 0;         // AIRG_SMOOTH_F, _FC or _FCF
+    DBuf<double> rcs;            // C residuals before restriction (C-point smoothing)
+    DBuf<float> rcs32;
     // outer FGMRES
     int restart = 0;
     DBuf<double> V, Zs, w, bp, xp, r, part;

@@ -30,9 +30,10 @@ def _lib():
 
 
 def _oopts(d):
-    o = {k: v for k, v in d.items() if k not in ("precision", "outer", "smoother")}
+    o = {k: v for k, v in d.items() if k not in ("precision", "outer", "smoother", "smooth_type")}
     if d.get("smoother", 0) == 1:
         o["smoother"] = "assembled"
+    o["smooth_type"] = ("f", "fc", "fcf")[d.get("smooth_type", 0)]
     return O.Options(**o)
 
 
@@ -75,6 +76,9 @@ def _check_setup(c):
         _csr_equal(L.Z, G.airg_export_matrix(h, l, 3), "Z level %d" % l)
         assert np.array_equal(G.airg_export_vector(h, l, 1), L.W), "W level %d" % l
         assert np.array_equal(G.airg_export_vector(h, l, 2), L.alpha), "alpha level %d" % l
+        if L.A_cc is not None:
+            _csr_equal(L.A_cc, G.airg_export_matrix(h, l, 5), "A_cc level %d" % l)
+            assert np.array_equal(G.airg_export_vector(h, l, 5), L.alpha_c), "alpha_c level %d" % l
         sc = G.airg_export_vector(h, l, 4)
         assert int(sc[0]) == L.pmisr_rounds
         assert [int(x) for x in sc[1:-2]] == list(L.ddc_converted)
@@ -336,3 +340,40 @@ def test_assembled_smoother_matches_oracle(prec):
     for l, L in enumerate(c.Ho.levels):
         _csr_equal(L.Ainv, G.airg_export_matrix(c.h, l, 4), "Ahat^-1 level %d" % l)
     _check_solve(c)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("smooth_type", [1, 2])
+def test_c_point_smoothing_matches_oracle(smooth_type, prec):
+    """FC and FCF smoothing (Sec. 2, the options of Sec. 3.3.2): A_cc and the
+    C-point polynomial bit for bit, the solution within 1e-9 of the oracle
+    (FP64 and FP32 V-cycles), and the complexities of the extra blocks."""
+    w = workload("grid", (203, 157))
+    c = Case(w, dict(smooth_type=smooth_type, precision=prec))
+    _check_setup(c)
+    _check_solve(c)
+    cf = G.airg_setup_info(G.airg_setup(c.pg["rowptr"], c.pg["col"], c.pg["val"],
+                                        G.airg_options_default(**w["opts"])))
+    cs = G.airg_setup_info(c.h)
+    extra = sum(L.A.nnz - L.A_ff.nnz - L.A_fc.nnz for L in c.Ho.levels)
+    assert abs((cs["storage_complexity"] - cf["storage_complexity"]) * c.po.A.nnz - extra) < 1e-6 * c.po.A.nnz
+    assert cs["cycle_complexity"] > cf["cycle_complexity"]
+
+
+def test_c_point_smoothing_many_rhs_and_rejections():
+    """With C-point smoothing several right-hand sides are solved in turn and
+    each matches its own solve; the assembled smoother and batches of grids
+    reject it."""
+    w = workload("grid", (90, 70))
+    vx, vy = velocity(w["theta"])
+    pg = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
+    h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"], G.airg_options_default(smooth_type=2, **w["opts"]))
+    B = torch.rand(3, w["nx"] * w["ny"], dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    X, info = G.airg_solve(h, B, rtol=1e-10)
+    for q in range(3):
+        xq, _ = G.airg_solve(h, B[q].contiguous(), rtol=1e-10)
+        assert torch.equal(xq, X[q])
+    with pytest.raises(G.AirgError):
+        G.airg_setup(pg["rowptr"], pg["col"], pg["val"], G.airg_options_default(smooth_type=1, smoother=1))
+    with pytest.raises(G.AirgError):
+        G.airg_setup_batch([(pg["rowptr"], pg["col"], pg["val"])], G.airg_options_default(smooth_type=1))
