@@ -344,7 +344,7 @@ def airg_export_matrix(handle, level, what):
     return nr.value, nc.value, rp, ci[: nnz.value], v[: nnz.value]
 
 
-_VEC_DTYPES = {0: np.int8, 1: np.int32, 2: np.float64, 3: np.float64, 4: np.float64}
+_VEC_DTYPES = {0: np.int8, 1: np.int32, 2: np.float64, 3: np.float64, 4: np.float64, 5: np.float64}
 
 
 def airg_export_vector(handle, level, what):
