@@ -11,7 +11,8 @@ Functions pinned by tests against closed forms, brute force or library
 routines: exact dot, SpMV, problem builder + sweep, strength, PMISR, DDC,
 extract, GMRES polynomial coefficients, fixed-sparsity inverse, restrictor,
 one-point prolongator, RAP + drop/lump, harmonic Ritz / Newton application,
-V-cycle (F, FC and FCF smoothing), FGMRES, dense adjoint.
+V-cycle (F, FC and FCF smoothing), nAIR Neumann coefficients, FGMRES,
+dense adjoint.
 Parity unpinned (internal choices with no closed form in the paper): the
 value of the R drop tolerance, the PMISR measure direction, the one-point
 weight, and the Loe-Morgan added-root thresholds.
@@ -235,6 +236,7 @@ class Options:
     addroot_per: float = 14.0
     smoother: str = "polynomial"     # "assembled": e_f += Ahat_ff^-1 t with the Eq. 8 matrix
     smooth_type: str = "f"           # "fc": F- then C-point smoothing; "fcf": F, C, F (Sec. 2, 3.3.2)
+    inverse_type: str = "gmres"      # "neumann": the nAIR polynomial of Sec. 3.3.1 instead of Eq. 7
 
 
 # --------------------------------------------------------------------------
@@ -494,6 +496,37 @@ def gmres_poly_coeffs(A_ff, opts, level, purpose=PURPOSE_COEF):
     return np.array(alpha + [0.0] * (p + 1 - k)), k, broke
 
 
+def neumann_coeffs(A, opts):
+    """Power-basis coefficients of the nAIR smoother polynomial (Sec. 3.3.1:
+    AIRG with the GMRES polynomial replaced by a Neumann polynomial).
+
+    Reading: the degree-p truncated Neumann series of the diagonally scaled
+    block, q(A) = w * sum_{k=0..p} (I - w A)^k with the scalar w = 1 / max_i
+    |a_ii|.  When the diagonal is constant (every level of this problem) it
+    is the Jacobi-scaled series sum_k (I - D^-1 A)^k D^-1 of nAIR.  Expanded,
+    alpha_j = w (-w)^j C(p+1, j+1); (-w)^j is formed by repeated products.
+    """
+    p = opts.poly_order
+    rid = A.row_ids()
+    dmax = float(np.max(np.abs(A.val[A.col == rid]))) if A.n_rows else 1.0
+    w = 1.0 / dmax
+    alpha = np.empty(p + 1)
+    pw = 1.0
+    for j in range(p + 1):
+        alpha[j] = (w * pw) * float(math.comb(p + 1, j + 1))
+        pw = pw * -w
+    return alpha
+
+
+def smoother_coeffs(A, opts, level, purpose=PURPOSE_COEF):
+    """(alpha, Krylov dimension) of the block smoother polynomial: the GMRES
+    polynomial of Eq. 7, or with inverse_type "neumann" the nAIR one."""
+    if opts.inverse_type == "neumann":
+        return neumann_coeffs(A, opts), opts.poly_order + 1
+    alpha, k, _ = gmres_poly_coeffs(A, opts, level, purpose)
+    return alpha, k
+
+
 def horner_apply(A, alpha, t):
     """q(A) t with q(z) = sum alpha_k z^k: w = alpha_p t; w = alpha_k t + A w."""
     p = len(alpha) - 1
@@ -732,6 +765,8 @@ def setup(A, opts=None):
     opts = opts or Options()
     if opts.smooth_type not in ("f", "fc", "fcf"):
         raise ValueError("smooth_type must be f, fc or fcf")
+    if opts.inverse_type not in ("gmres", "neumann"):
+        raise ValueError("inverse_type must be gmres or neumann")
     if opts.smooth_type != "f" and opts.smoother == "assembled":
         raise ValueError("C-point smoothing is built with the matrix-free polynomial smoother only")
     Hh = Hierarchy(opts=opts)
@@ -761,7 +796,7 @@ def setup(A, opts=None):
         A_ff = extract(A, is_f, is_f)
         A_fc = extract(A, is_f, ~is_f)
         A_cf = extract(A, ~is_f, is_f)
-        alpha, k, broke = gmres_poly_coeffs(A_ff, opts, level)
+        alpha, k = smoother_coeffs(A_ff, opts, level)
         Ainv = fixed_sparsity_inverse(A_ff, alpha)
         Z = restrictor_block(A_cf, Ainv, opts.r_drop)
         W = one_point(A, strong, is_f)
@@ -773,7 +808,7 @@ def setup(A, opts=None):
             # does for A_ff
             lev.A_cf = A_cf
             lev.A_cc = extract(A, ~is_f, ~is_f)
-            lev.alpha_c, lev.alpha_c_k, _ = gmres_poly_coeffs(lev.A_cc, opts, level, PURPOSE_COEF_C)
+            lev.alpha_c, lev.alpha_c_k = smoother_coeffs(lev.A_cc, opts, level, PURPOSE_COEF_C)
         Hh.levels.append(lev)
         A = Ac
         level += 1

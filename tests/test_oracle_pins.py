@@ -595,3 +595,60 @@ def test_c_point_smoothing_storage_is_the_rest_of_a():
     assert abs((sc - sf) * top - extra) < 1e-6
     for L in Hc.levels:
         assert L.A_cf.nnz + L.A_cc.nnz + L.A_ff.nnz + L.A_fc.nnz == L.A.nnz
+
+
+def _neumann_q(A, p):
+    """Dense q(A) from the oracle's power-basis Neumann coefficients."""
+    al = O.neumann_coeffs(A, O.Options(poly_order=p))
+    D = A.to_dense()
+    Q = np.zeros_like(D)
+    Pk = np.eye(D.shape[0])
+    for a in al:
+        Q += a * Pk
+        Pk = Pk @ D
+    return al, D, Q
+
+
+@pytest.mark.parametrize("p", [0, 1, 4, 6])
+def test_neumann_residual_polynomial(p):
+    """The truncated Neumann series fixes its own residual: with w = 1 / max
+    |a_ii|, I - A q(A) = (I - w A)^(p+1) (Sec. 3.3.1 nAIR; the identity of a
+    geometric sum).  Checked on the A_ff of a real level, whose diagonal is
+    the constant |vx| + |vy|."""
+    P = _grid(12, 10, 0.7)
+    H = O.setup(P.A, O.Options(max_levels=2, trunc_rtol=0.0))
+    A_ff = H.levels[0].A_ff
+    al, D, Q = _neumann_q(A_ff, p)
+    w = 1.0 / np.max(np.abs(np.diag(D)))
+    assert abs(w - 1.0 / (math.cos(0.7) + math.sin(0.7))) < 1e-15
+    E = np.linalg.matrix_power(np.eye(D.shape[0]) - w * D, p + 1)
+    assert np.max(np.abs(np.eye(D.shape[0]) - D @ Q - E)) < 1e-13
+
+
+def test_neumann_exact_on_nilpotent_part():
+    """A = d (I - N) with N strictly lower bidiagonal (nilpotent, N^n = 0):
+    the series of degree n - 1 is the exact inverse; A = d I gives q = 1/d
+    at every degree."""
+    n, d = 6, 1.7
+    rows = list(range(n)) + list(range(1, n))
+    cols = list(range(n)) + list(range(n - 1))
+    vals = [d] * n + [-0.9] * (n - 1)
+    o = np.lexsort((cols, rows))
+    A = O.csr_from_entries(n, n, np.array(rows)[o], np.array(cols)[o], np.array(vals)[o])
+    _, D, Q = _neumann_q(A, n - 1)
+    assert np.max(np.abs(Q - np.linalg.inv(D))) < 1e-12
+    I = O.csr_from_entries(4, 4, np.arange(4), np.arange(4), np.full(4, d))
+    for p in (0, 3):
+        _, _, Qi = _neumann_q(I, p)
+        assert np.max(np.abs(Qi - np.eye(4) / d)) < 1e-15
+
+
+def test_nair_solves_the_constant_inflow_problem():
+    """nAIR (Neumann smoother and Neumann-based Z) on the 64 x 64 problem with
+    g = 1, s = 0 converges to the closed-form u = 1 (Eq. 1-2)."""
+    P = _grid(64, 64, 3 * math.pi / 8)
+    b = O.assemble_rhs(P, np.ones(P.inflow.size), np.zeros(P.A.n_rows))
+    H = O.setup(P.A, O.Options(poly_order=4, inverse_type="neumann", trunc_start_level=4))
+    x, info = O.solve(H, P.A, b, rtol=1e-10)
+    assert info.converged and np.max(np.abs(x - 1.0)) < 1e-8
+    assert H.levels[0].alpha_k == 5
