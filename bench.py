@@ -509,9 +509,10 @@ def run_sweep(args):
     coarse-order (Sec. 3.1): m_c in {5, 10, 30, 100} with truncation at
     alpha_trunc = 0.1 on every level vs no truncation, FP64.  smoother
     (Sec. 2.2): the matrix-free GMRES polynomial vs the assembled
-    fixed-sparsity matrix of Eq. 8, and F-point vs FC and FCF smoothing
-    (Sec. 2, Sec. 3.3.2), FP64 and FP32 V-cycles, m_c = 30 with truncation
-    at 1e-2.  Solve times are the median of `steps` device-timed
+    fixed-sparsity matrix of Eq. 8, F-point vs FC and FCF smoothing
+    (Sec. 2, Sec. 3.3.2), and the GMRES (AIRG) vs Neumann (nAIR, Sec.
+    3.3.1) polynomial, FP64 and FP32 V-cycles, m_c = 30 with truncation at
+    1e-2.  Solve times are the median of `steps` device-timed
     solves after `warmup` untimed ones."""
     import torch
     torch.cuda.set_device(0)
@@ -533,16 +534,18 @@ def run_sweep(args):
                 r = _sweep_row(G, torch, prob, b, G.airg_options_default(coarse_poly_order=mc, trunc_rtol=trunc), args)
                 rows.append(dict({"coarse_order": mc, "truncation": trunc}, **r))
     else:
-        settings = [(G.AIRG_SMOOTH_POLYNOMIAL, G.AIRG_SMOOTH_F), (G.AIRG_SMOOTH_ASSEMBLED, G.AIRG_SMOOTH_F),
-                    (G.AIRG_SMOOTH_POLYNOMIAL, G.AIRG_SMOOTH_FC), (G.AIRG_SMOOTH_POLYNOMIAL, G.AIRG_SMOOTH_FCF)]
+        P, A, GM, NE = G.AIRG_SMOOTH_POLYNOMIAL, G.AIRG_SMOOTH_ASSEMBLED, G.AIRG_INVERSE_GMRES, G.AIRG_INVERSE_NEUMANN
+        settings = [(P, G.AIRG_SMOOTH_F, GM), (A, G.AIRG_SMOOTH_F, GM), (P, G.AIRG_SMOOTH_FC, GM),
+                    (P, G.AIRG_SMOOTH_FCF, GM), (P, G.AIRG_SMOOTH_F, NE)]
         for prec in (G.AIRG_FP64, G.AIRG_MIXED_FP32):
-            for sm, stype in settings:
+            for sm, stype, inv in settings:
                 opts = G.airg_options_default(coarse_poly_order=30, trunc_rtol=1e-2, precision=prec, smoother=sm,
-                                              smooth_type=stype)
+                                              smooth_type=stype, inverse_type=inv)
                 r = _sweep_row(G, torch, prob, b, opts, args)
                 rows.append(dict({"precision": "f64" if prec == G.AIRG_FP64 else "f32",
-                                  "smoother": "polynomial" if sm == G.AIRG_SMOOTH_POLYNOMIAL else "assembled",
-                                  "points": ("f", "fc", "fcf")[stype]},
+                                  "smoother": "polynomial" if sm == P else "assembled",
+                                  "points": ("f", "fc", "fcf")[stype],
+                                  "inverse": "gmres (AIRG)" if inv == GM else "neumann (nAIR)"},
                                  **r))
     print(json.dumps({"sweep": args.sweep, "grid": "%dx%d" % (n, n), "theta": "pi/4", "g": 1.0,
                       "rtol": 1e-10, "steps": args.steps, "warmup": args.warmup, "rows": rows}))

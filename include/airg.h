@@ -66,6 +66,12 @@ enum { AIRG_SMOOTH_POLYNOMIAL = 0, AIRG_SMOOTH_ASSEMBLED = 1 };
  * (AIRG_ERR_ARG otherwise); airg_solve with nrhs > 1 then solves the
  * right-hand sides one after the other, and airg_setup_batch rejects them. */
 enum { AIRG_SMOOTH_F = 0, AIRG_SMOOTH_FC = 1, AIRG_SMOOTH_FCF = 2 };
+/* Block approximate inverse behind the smoother and the restrictor: the
+ * GMRES polynomial of Eq. 7 (AIRG), or the Neumann polynomial of nAIR
+ * (Sec. 3.3.1), read as q(A) = w sum_{k<=p} (I - w A)^k with w = 1 / max_i
+ * |a_ii|: the Jacobi-scaled Neumann series whenever the block's diagonal is
+ * constant.  The coarse-grid polynomial is the GMRES one in both. */
+enum { AIRG_INVERSE_GMRES = 0, AIRG_INVERSE_NEUMANN = 1 };
 
 /* Compressed sparse row matrix (n_rows x n_cols).  Caller-owned, read-only. */
 typedef struct {
@@ -105,6 +111,7 @@ typedef struct {
     int outer;                 /* AIRG_OUTER_FGMRES or AIRG_OUTER_RICHARDSON  */
     int smoother;              /* AIRG_SMOOTH_POLYNOMIAL or _ASSEMBLED        */
     int smooth_type;           /* AIRG_SMOOTH_F, _FC or _FCF                  */
+    int inverse_type;          /* AIRG_INVERSE_GMRES or AIRG_INVERSE_NEUMANN  */
 } airg_options;
 
 typedef struct airg_handle_s airg_handle;

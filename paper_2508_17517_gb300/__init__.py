@@ -21,6 +21,8 @@ AIRG_SMOOTH_ASSEMBLED = 1
 AIRG_SMOOTH_F = 0
 AIRG_SMOOTH_FC = 1
 AIRG_SMOOTH_FCF = 2
+AIRG_INVERSE_GMRES = 0
+AIRG_INVERSE_NEUMANN = 1
 AIRG_OUTER_FGMRES = 0
 AIRG_OUTER_RICHARDSON = 1
 AIRG_FP64 = 0
@@ -52,7 +54,7 @@ class airg_options(ctypes.Structure):
                 ("addroot_log10", ctypes.c_double),
                 ("addroot_per", ctypes.c_double), ("precision", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("outer", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("smooth_type", ctypes.c_int)]
+                ("smooth_type", ctypes.c_int), ("inverse_type", ctypes.c_int)]
 
 
 class airg_csr(ctypes.Structure):

@@ -133,6 +133,8 @@ void check_options(const airg_options& o)
         airg::fail(AIRG_ERR_ARG, "bad smoother");
     if (o.smooth_type != AIRG_SMOOTH_F && o.smooth_type != AIRG_SMOOTH_FC && o.smooth_type != AIRG_SMOOTH_FCF)
         airg::fail(AIRG_ERR_ARG, "bad smooth_type");
+    if (o.inverse_type != AIRG_INVERSE_GMRES && o.inverse_type != AIRG_INVERSE_NEUMANN)
+        airg::fail(AIRG_ERR_ARG, "bad inverse_type");
     if (o.smooth_type != AIRG_SMOOTH_F && o.smoother != AIRG_SMOOTH_POLYNOMIAL)
         airg::fail(AIRG_ERR_ARG, "C-point smoothing needs the matrix-free polynomial smoother");
 }
@@ -212,6 +214,7 @@ airg_status airg_options_default(airg_options* o)
     o->outer = AIRG_OUTER_FGMRES;
     o->smoother = AIRG_SMOOTH_POLYNOMIAL;
     o->smooth_type = AIRG_SMOOTH_F;
+    o->inverse_type = AIRG_INVERSE_GMRES;
     return AIRG_OK;
 }
 

@@ -1061,6 +1061,61 @@ std::vector<double> gmres_poly_coeffs(Ctx& c, const DevCSR& Aff, const airg_opti
     return alpha;
 }
 
+// max_i |a_ii| as the bit pattern of a non-negative double (such patterns
+// order like the values), so the atomic maximum is exact and order-free
+__global__ void k_diag_absmax(int n, const int* rp, const int* ci, const double* v, unsigned long long* out)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    for (int k = rp[r]; k < rp[r + 1]; ++k)
+        if (ci[k] == r) {
+            atomicMax(out, (unsigned long long)__double_as_longlong(fabs(v[k])));
+            break;
+        }
+}
+
+// nAIR (Sec. 3.3.1): power-basis coefficients of w sum_{k<=p} (I - w A)^k,
+// w = 1 / max |a_ii|, i.e. alpha_j = w (-w)^j C(p+1, j+1), with (-w)^j formed
+// by repeated products
+std::vector<double> neumann_coeffs(const DevCSR& A, const airg_options& o, cudaStream_t st)
+{
+    const int p = o.poly_order;
+    double dmax = 1.0;
+    if (A.n_rows) {
+        DBuf<unsigned long long> m(1);
+        CK(cudaMemsetAsync(m.p, 0, sizeof(unsigned long long), st));
+        k_diag_absmax<<<grid_for(A.n_rows, TB), TB, 0, st>>>(A.n_rows, A.rp.p, A.ci.p, A.v.p, m.p);
+        CK_LAUNCH();
+        unsigned long long bits = 0;
+        d2h(&bits, m.p, 1, st);
+        std::memcpy(&dmax, &bits, sizeof dmax);
+        if (!(dmax > 0.0)) fail(AIRG_ERR_BREAKDOWN, "block without a nonzero diagonal (Neumann polynomial)");
+    }
+    const double w = 1.0 / dmax;
+    // binomial C(p+1, j+1) from Pascal's triangle (exact in 64 bits for p <= 30)
+    std::vector<unsigned long long> row(size_t(p) + 2, 0);
+    row[0] = 1;
+    for (int i = 1; i <= p + 1; ++i)
+        for (int j = i; j >= 1; --j) row[j] += row[j - 1];
+    std::vector<double> alpha(size_t(p) + 1);
+    double pw = 1.0;
+    for (int j = 0; j <= p; ++j) {
+        alpha[j] = (w * pw) * (double)row[j + 1];
+        pw = pw * -w;
+    }
+    return alpha;
+}
+
+std::vector<double> smoother_coeffs(Ctx& c, const DevCSR& A, const airg_options& o, int level, int& kout,
+                                    int purpose)
+{
+    if (o.inverse_type == AIRG_INVERSE_NEUMANN) {
+        kout = o.poly_order + 1;
+        return neumann_coeffs(A, o, c.st);
+    }
+    return gmres_poly_coeffs(c, A, o, level, kout, purpose);
+}
+
 void fixed_sparsity_inverse(const DevCSR& Aff, const std::vector<double>& alpha, DevCSR& out,
                             cudaStream_t st)
 {
@@ -1351,7 +1406,7 @@ std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, c
         DevCSR A_cf;
         submatrix(Al, L->c_ids.p, L->n_c, L->f_index.p, L->n_f, A_cf, st);
         // GMRES polynomial (Eq. 7) and fixed-sparsity inverse (Eq. 8)
-        L->alpha = gmres_poly_coeffs(c, L->A_ff, o, level, L->alpha_k);
+        L->alpha = smoother_coeffs(c, L->A_ff, o, level, L->alpha_k, PURPOSE_COEF);
         DevCSR Ainv;
         fixed_sparsity_inverse(L->A_ff, L->alpha, Ainv, st);
         // Z = -A_cf Ahat^-1, then the relative drop on R
@@ -1364,7 +1419,7 @@ std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, c
             submatrix(Al, L->c_ids.p, L->n_c, L->c_index.p, L->n_c, L->A_cc, st);
             submatrix(Al, L->c_ids.p, L->n_c, nullptr, n, L->Crows, st);
             if (o.smooth_type == AIRG_SMOOTH_FCF) submatrix(Al, L->f_ids.p, L->n_f, nullptr, n, L->Frows, st);
-            L->alpha_c = gmres_poly_coeffs(c, L->A_cc, o, level, L->alpha_c_k, PURPOSE_COEF_C);
+            L->alpha_c = smoother_coeffs(c, L->A_cc, o, level, L->alpha_c_k, PURPOSE_COEF_C);
         }
         if (Zfull.nnz) k_scale<<<grid_for(Zfull.nnz, TB), TB, 0, st>>>(Zfull.nnz, Zfull.v.p, -1.0);
         {

@@ -30,10 +30,11 @@ def _lib():
 
 
 def _oopts(d):
-    o = {k: v for k, v in d.items() if k not in ("precision", "outer", "smoother", "smooth_type")}
+    o = {k: v for k, v in d.items() if k not in ("precision", "outer", "smoother", "smooth_type", "inverse_type")}
     if d.get("smoother", 0) == 1:
         o["smoother"] = "assembled"
     o["smooth_type"] = ("f", "fc", "fcf")[d.get("smooth_type", 0)]
+    o["inverse_type"] = ("gmres", "neumann")[d.get("inverse_type", 0)]
     return O.Options(**o)
 
 
@@ -377,3 +378,23 @@ def test_c_point_smoothing_many_rhs_and_rejections():
         G.airg_setup(pg["rowptr"], pg["col"], pg["val"], G.airg_options_default(smooth_type=1, smoother=1))
     with pytest.raises(G.AirgError):
         G.airg_setup_batch([(pg["rowptr"], pg["col"], pg["val"])], G.airg_options_default(smooth_type=1))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_nair_matches_oracle(prec):
+    """nAIR (Sec. 3.3.1): the Neumann coefficients bit for bit (they decide
+    Z and every coarse operator), the hierarchy bit for bit, and the solution
+    within 1e-9 of the oracle; the batched many-RHS form agrees too."""
+    w = workload("grid", (203, 157))
+    c = Case(w, dict(inverse_type=1, precision=prec))
+    _check_setup(c)
+    _check_solve(c)
+    B = torch.rand(4, w["nx"] * w["ny"], dtype=torch.float64, device="cuda",
+                   generator=torch.Generator("cuda").manual_seed(9))
+    X, _ = G.airg_solve(c.h, B, rtol=1e-10)
+    for q in range(4):
+        bo = B[q].cpu().numpy()
+        xo, _ = O.solve(c.Ho, c.po.A, bo, rtol=1e-10)
+        xg = X[q].cpu().numpy()
+        assert np.linalg.norm(bo - O.spmv(c.po.A, xg)) <= 1e-10 * np.linalg.norm(bo) * (1 + 1e-6)
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-9
