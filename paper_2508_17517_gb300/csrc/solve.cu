@@ -1118,7 +1118,7 @@ void c_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
     const SolveLevelT<T>& o = ops<T>(lv);
     const int nc = lv.n_c;
     if (!nc) return;
-    const T* rc = (l == 0 ? v : wk.rcs) + lv.off + lv.n_f;
+    const T* rc = l == 0 ? v + lv.off + lv.n_f : wk.rcs + lv.rc_off;
     T* el = e + lv.off;
     const int p = int(lv.alpha_c.size()) - 1;
     const long long cB = (long long)nc * VB;
@@ -1163,7 +1163,7 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         if (l > 0 && lv.n_c && S.smooth_type != AIRG_SMOOTH_F)   // restriction overwrites r_c in place
             LAUNCH_F(S, PK_RESTRICT, 2LL * lv.n_c * VB, 0,
                      k_copy<T><<<grid_for(lv.n_c, TB), TB, 0, st>>>(lv.n_c, src + lv.off + lv.n_f,
-                                                                    wk.rcs + lv.off + lv.n_f));
+                                                                    wk.rcs + lv.rc_off));
         if (lv.n_c && Zb.val.n)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Zb) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Zb.nnz + lv.n_c,
                    WITH_KR(Zb, k_restrict<T, KK, RR, bf16s><<<grid_rows(Zb), block_rows(Zb), 0, st>>>(
@@ -1414,6 +1414,7 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
     // level operators
     long long bytes = 0;
     int max_nc = 0;
+    long long rc_total = 0;
     S->smooth_type = H.opt.smooth_type;
     for (int l = 0; l < L; ++l) {
         SetupLevel& lv = *H.levels[l];
@@ -1445,6 +1446,10 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
             build_sell<double>(lv.A_cc, inv.p, rel.p, lv.n_c, sl->d.Acc, true, st);
             if (lv.Frows.n_rows) build_sell<double>(lv.Frows, iperm[l].p, rl.p, lv.n, sl->d.Mf, false, st);
             max_nc = std::max(max_nc, lv.n_c);
+            if (l > 0) {
+                sl->rc_off = rc_total;
+                rc_total += lv.n_c;
+            }
         }
         if (mixed_precision(H.opt)) {
             copy_sell_f32(sl->d.Aff, sl->f.Aff, st);
@@ -1543,8 +1548,9 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
     S->t.alloc(nf); S->wa.alloc(nf); S->wb.alloc(nf);
     S->cr0.alloc(nc); S->cr1.alloc(nc); S->ct.alloc(nc);
     if (S->smooth_type != AIRG_SMOOTH_F) {
-        if (mixed_precision(H.opt)) S->rcs32.alloc(n0);
-        else S->rcs.alloc(n0);
+        const size_t nrc = size_t(std::max<long long>(rc_total, 1));
+        if (mixed_precision(H.opt)) S->rcs32.alloc(nrc);
+        else S->rcs.alloc(nrc);
     }
     if (mixed_precision(H.opt)) {
         S->rwork32.alloc(n0); S->e32.alloc(n0); S->vin32.alloc(n0);

@@ -135,6 +135,7 @@ struct SolveLevelT {
 
 struct SolveLevel {
     int off = 0, n_f = 0, n_c = 0;
+    long long rc_off = 0;        // start of this level's saved C residual (C-point smoothing)
     DBuf<int> W;                 // nested-relative C position, -1 none
     std::vector<double> alpha;
     std::vector<double> alpha_c;     // C-point smoother polynomial (empty: none)
@@ -161,7 +162,8 @@ struct SolveData {
     DBuf<double> rwork, t, wa, wb, cx, cr0, cr1, ct;
     DBuf<float> rwork32, e32, t32, wa32, wb32, cx32, cr032, cr132, ct32, vin32;
     int smooth_type = 0;         // AIRG_SMOOTH_F, _FC or _FCF
-    DBuf<double> rcs;            // C residuals before restriction (C-point smoothing)
+    DBuf<double> rcs;            // C residuals before restriction, one slot per level l >= 1
+                                 // (nested C blocks overlap, so they cannot share positions)
     DBuf<float> rcs32;
     // outer FGMRES
     int restart = 0;
