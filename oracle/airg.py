@@ -746,6 +746,7 @@ class Level:
     A_cc: CSR = None
     alpha_c: np.ndarray = None       # GMRES polynomial of A_cc (C-point smoother)
     alpha_c_k: int = 0
+    Ainv_cc: CSR = None              # fixed-sparsity Ahat_cc^-1 (assembled C-point smoother)
 
 
 @dataclass
@@ -767,8 +768,6 @@ def setup(A, opts=None):
         raise ValueError("smooth_type must be f, fc or fcf")
     if opts.inverse_type not in ("gmres", "neumann"):
         raise ValueError("inverse_type must be gmres or neumann")
-    if opts.smooth_type != "f" and opts.smoother == "assembled":
-        raise ValueError("C-point smoothing is built with the matrix-free polynomial smoother only")
     Hh = Hierarchy(opts=opts)
     level = 0
     while True:
@@ -809,6 +808,10 @@ def setup(A, opts=None):
             lev.A_cf = A_cf
             lev.A_cc = extract(A, ~is_f, ~is_f)
             lev.alpha_c, lev.alpha_c_k = smoother_coeffs(lev.A_cc, opts, level, PURPOSE_COEF_C)
+            if opts.smoother == "assembled":
+                # the assembled form of both smoothers (Sec. 3.3: storage
+                # with assembled F- and C-point approximations)
+                lev.Ainv_cc = fixed_sparsity_inverse(lev.A_cc, lev.alpha_c)
         Hh.levels.append(lev)
         A = Ac
         level += 1
@@ -837,7 +840,8 @@ def vcycle(Hh, r, level=0):
     ec = vcycle(Hh, rc, level + 1)
     ef = np.where(L.W >= 0, ec[np.maximum(L.W, 0)], 0.0)
     t = rf - spmv(L.A_fc, ec) - spmv(L.A_ff, ef)
-    if Hh.opts is not None and Hh.opts.smoother == "assembled":
+    assembled = Hh.opts is not None and Hh.opts.smoother == "assembled"
+    if assembled:
         ef = ef + spmv(L.Ainv, t)
     else:
         ef = ef + horner_apply(L.A_ff, L.alpha, t)
@@ -846,11 +850,11 @@ def vcycle(Hh, r, level=0):
         # C-point smooth on the level's own C residual (the value before
         # restriction): e_c += q_c(A_cc)(r_c - A_cf e_f - A_cc e_c)
         tc = r[~L.is_f] - spmv(L.A_cf, ef) - spmv(L.A_cc, ec)
-        ec = ec + horner_apply(L.A_cc, L.alpha_c, tc)
+        ec = ec + (spmv(L.Ainv_cc, tc) if assembled else horner_apply(L.A_cc, L.alpha_c, tc))
     if st == "fcf":
         # a second F-point smooth, Eq. 6 with the current e_c and e_f
         t = rf - spmv(L.A_fc, ec) - spmv(L.A_ff, ef)
-        ef = ef + horner_apply(L.A_ff, L.alpha, t)
+        ef = ef + (spmv(L.Ainv, t) if assembled else horner_apply(L.A_ff, L.alpha, t))
     e = np.empty(L.n)
     e[L.is_f] = ef
     e[~L.is_f] = ec
@@ -977,9 +981,13 @@ def complexities(Hh):
             flops += 2 * L.A_ff.nnz * (p + 1)
         if st != "f":
             store += L.A_cf.nnz + L.A_cc.nnz
-            flops += 2 * L.A_cf.nnz + 2 * L.A_cc.nnz * len(L.alpha_c)
+            if assembled:
+                store += L.Ainv_cc.nnz
+                flops += 2 * L.A_cf.nnz + 2 * L.A_cc.nnz + 2 * L.Ainv_cc.nnz
+            else:
+                flops += 2 * L.A_cf.nnz + 2 * L.A_cc.nnz * len(L.alpha_c)
         if st == "fcf":
-            flops += 2 * L.A_fc.nnz + 2 * L.A_ff.nnz * (p + 1)
+            flops += 2 * L.A_fc.nnz + 2 * L.A_ff.nnz + (2 * L.Ainv.nnz if assembled else 2 * L.A_ff.nnz * p)
     nr = len(Hh.roots)
     store += Hh.A_coarse.nnz
     flops += 2 * Hh.A_coarse.nnz * max(nr - 1, 0)

@@ -652,3 +652,22 @@ def test_nair_solves_the_constant_inflow_problem():
     x, info = O.solve(H, P.A, b, rtol=1e-10)
     assert info.converged and np.max(np.abs(x - 1.0)) < 1e-8
     assert H.levels[0].alpha_k == 5
+
+
+@pytest.mark.parametrize("st", ["fc", "fcf"])
+def test_assembled_c_point_smoothing_equals_matrix_free_at_degree_one(st):
+    """At degree p = 1 the polynomial a_0 I + a_1 A already has the pattern
+    of A plus the diagonal, so the fixed-sparsity inverse of Eq. 8 is the
+    polynomial itself.  The assembled F- and C-point smoothers must then
+    give the same V-cycle as the matrix-free ones (pinned by block
+    exactness above), for FC and FCF alike."""
+    P = _grid(30, 26, 1.1)
+    r = np.random.default_rng(2).standard_normal(P.A.n_rows)
+    out = {}
+    for sm in ("polynomial", "assembled"):
+        H = O.setup(P.A, O.Options(poly_order=1, coarse_poly_order=30, trunc_rtol=1e-2, smooth_type=st,
+                                   smoother=sm))
+        out[sm] = O.vcycle(H, r)
+        if sm == "assembled":
+            assert all(L.Ainv_cc is not None for L in H.levels)
+    assert np.linalg.norm(out["assembled"] - out["polynomial"]) <= 1e-13 * np.linalg.norm(out["polynomial"])
