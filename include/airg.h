@@ -62,9 +62,10 @@ enum { AIRG_SMOOTH_POLYNOMIAL = 0, AIRG_SMOOTH_ASSEMBLED = 1 };
  * F, C, then F again.  A C-point smooth applies a GMRES polynomial of A_cc
  * of the same degree, matrix-free, to r_c - A_cf e_f - A_cc e_c, where r_c
  * is the level's C residual before restriction; it keeps A_cf and A_cc on
- * every level.  FC and FCF need the matrix-free polynomial smoother
- * (AIRG_ERR_ARG otherwise); airg_solve with nrhs > 1 then solves the
- * right-hand sides one after the other, and airg_setup_batch rejects them. */
+ * every level.  With AIRG_SMOOTH_ASSEMBLED the C-point smooth applies the
+ * fixed-sparsity Ahat_cc^-1 of Eq. 8 instead (one more matrix per level).
+ * With FC or FCF, airg_solve with nrhs > 1 solves the right-hand sides one
+ * after the other, and airg_setup_batch rejects them. */
 enum { AIRG_SMOOTH_F = 0, AIRG_SMOOTH_FC = 1, AIRG_SMOOTH_FCF = 2 };
 /* Block approximate inverse behind the smoother and the restrictor: the
  * GMRES polynomial of Eq. 7 (AIRG), or the Neumann polynomial of nAIR
@@ -261,6 +262,8 @@ airg_status airg_setup_info(const airg_handle* h, airg_hierarchy_info* info);
  * checking against an independent implementation.  `what`:
  *   0 A_l (the level operator)   1 A_ff   2 A_fc   3 Z (restrictor block, after drop)
  *   4 the fixed-sparsity Ahat_ff^-1 of Eq. 8 (kept only with AIRG_SMOOTH_ASSEMBLED)
+ *   5 A_cc (kept only with C-point smoothing)
+ *   6 the fixed-sparsity Ahat_cc^-1 (C-point smoothing with AIRG_SMOOTH_ASSEMBLED)
  * Two-call protocol with HOST buffers: pass NULL arrays to get *n_rows,
  * *n_cols, *nnz; then pass arrays of those sizes.  `what` = 0 on the coarsest
  * level returns the coarse operator.

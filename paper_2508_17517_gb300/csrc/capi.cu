@@ -135,8 +135,6 @@ void check_options(const airg_options& o)
         airg::fail(AIRG_ERR_ARG, "bad smooth_type");
     if (o.inverse_type != AIRG_INVERSE_GMRES && o.inverse_type != AIRG_INVERSE_NEUMANN)
         airg::fail(AIRG_ERR_ARG, "bad inverse_type");
-    if (o.smooth_type != AIRG_SMOOTH_F && o.smoother != AIRG_SMOOTH_POLYNOMIAL)
-        airg::fail(AIRG_ERR_ARG, "C-point smoothing needs the matrix-free polynomial smoother");
 }
 
 airg::DevCSR upload_csr(const airg_csr* A, cudaStream_t st)
@@ -382,6 +380,10 @@ airg_status airg_export_matrix(const airg_handle* h, int level, int what, int64_
                 case 5:
                     if (H->opt.smooth_type == AIRG_SMOOTH_F) airg::fail(AIRG_ERR_ARG, "A_cc is kept only with C-point smoothing");
                     M = &lv.A_cc;
+                    break;
+                case 6:
+                    if (!lv.Ainv_cc.n_rows && lv.n_c) airg::fail(AIRG_ERR_ARG, "Ahat_cc^-1 is kept only with assembled C-point smoothing");
+                    M = &lv.Ainv_cc;
                     break;
                 default: airg::fail(AIRG_ERR_ARG, "bad matrix id");
             }

@@ -27,6 +27,7 @@ struct SetupLevel {
     // [A_ff A_fc] of A_l with the level's own column numbering, and the
     // GMRES polynomial of A_cc
     DevCSR A_cc, Crows, Frows;
+    DevCSR Ainv_cc;           // fixed-sparsity Ahat_cc^-1 (assembled C-point smoother)
     std::vector<double> alpha_c;
     int alpha_c_k = 0;
     DBuf<int> W;              // one-point prolongator: C-local index or -1

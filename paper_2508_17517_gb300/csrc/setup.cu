@@ -1420,6 +1420,7 @@ std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, c
             submatrix(Al, L->c_ids.p, L->n_c, nullptr, n, L->Crows, st);
             if (o.smooth_type == AIRG_SMOOTH_FCF) submatrix(Al, L->f_ids.p, L->n_f, nullptr, n, L->Frows, st);
             L->alpha_c = smoother_coeffs(c, L->A_cc, o, level, L->alpha_c_k, PURPOSE_COEF_C);
+            if (o.smoother == AIRG_SMOOTH_ASSEMBLED) fixed_sparsity_inverse(L->A_cc, L->alpha_c, L->Ainv_cc, st);
         }
         if (Zfull.nnz) k_scale<<<grid_for(Zfull.nnz, TB), TB, 0, st>>>(Zfull.nnz, Zfull.v.p, -1.0);
         {

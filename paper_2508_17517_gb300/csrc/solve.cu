@@ -1125,6 +1125,12 @@ void c_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mc) + (long long)(lv.n_f + nc) * VB + 3 * cB, 2 * o.Mc.nnz + 2LL * nc,
              WITH_KR(o.Mc, k_fresid<T, KK, RR><<<grid_rows(o.Mc), block_rows(o.Mc), 0, st>>>(
                               view(o.Mc), rc, el, wk.t, wk.wa, T(lv.alpha_c[p]))));
+    if (o.Ainvc.n_rows) {   // assembled: e_c += Ahat_cc^-1 t_c
+        LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainvc) + 4 * cB, 2 * o.Ainvc.nnz + 2LL * nc,
+                 WITH_KR(o.Ainvc, k_horner_acc<T, KK, RR><<<grid_rows(o.Ainvc), block_rows(o.Ainvc), 0, st>>>(
+                                     view(o.Ainvc), wk.t, wk.t, el + lv.n_f, T(0))));
+        return;
+    }
     horner_into<T>(S, o.Acc, lv.alpha_c, wk, el + lv.n_f, nc, st);
 }
 
@@ -1144,6 +1150,12 @@ void f_smooth_again(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, c
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mf) + (long long)(nf + lv.n_c) * VB + 3 * fB, 2 * o.Mf.nnz + 2LL * nf,
              WITH_KR(o.Mf, k_fresid<T, KK, RR><<<grid_rows(o.Mf), block_rows(o.Mf), 0, st>>>(
                               view(o.Mf), rf, el, wk.t, wk.wa, T(lv.alpha[p]))));
+    if (o.Ainv.n_rows) {    // assembled: e_f += Ahat_ff^-1 t
+        LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB, 2 * o.Ainv.nnz + 2LL * nf,
+                 WITH_KR(o.Ainv, k_horner_acc<T, KK, RR><<<grid_rows(o.Ainv), block_rows(o.Ainv), 0, st>>>(
+                                    view(o.Ainv), wk.t, wk.t, el, T(0))));
+        return;
+    }
     horner_into<T>(S, o.Aff, lv.alpha, wk, el, nf, st);
 }
 
@@ -1332,6 +1344,7 @@ void tune_all(SolveData& S, cudaStream_t st)
         tune_rows(o.Mc, x.p, y.p, fs, fl, st);
         tune_rows(o.Acc, x.p, y.p, fs, fl, st);
         tune_rows(o.Mf, x.p, y.p, fs, fl, st);
+        tune_rows(o.Ainvc, x.p, y.p, fs, fl, st);
     }
     tune_rows(const_cast<Sell<T>&>(coarse_op<T>(S)), x.p, y.p, fs, fl, st);
     CK(cudaStreamSynchronize(st));
@@ -1445,6 +1458,7 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
             build_sell<double>(lv.Crows, inv.p, rl.p, lv.n, sl->d.Mc, false, st);
             build_sell<double>(lv.A_cc, inv.p, rel.p, lv.n_c, sl->d.Acc, true, st);
             if (lv.Frows.n_rows) build_sell<double>(lv.Frows, iperm[l].p, rl.p, lv.n, sl->d.Mf, false, st);
+            if (lv.Ainv_cc.n_rows) build_sell<double>(lv.Ainv_cc, inv.p, rel.p, lv.n_c, sl->d.Ainvc, true, st);
             max_nc = std::max(max_nc, lv.n_c);
             if (l > 0) {
                 sl->rc_off = rc_total;
@@ -1460,6 +1474,7 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
             if (sl->d.Mc.n_rows) copy_sell_f32(sl->d.Mc, sl->f.Mc, st);
             if (sl->d.Acc.n_rows) copy_sell_f32(sl->d.Acc, sl->f.Acc, st);
             if (sl->d.Mf.n_rows) copy_sell_f32(sl->d.Mf, sl->f.Mf, st);
+            if (sl->d.Ainvc.n_rows) copy_sell_f32(sl->d.Ainvc, sl->f.Ainvc, st);
         }
         int vb = mixed_precision(H.opt) ? 4 : 8;
         int p = int(lv.alpha.size()) - 1;
@@ -1470,9 +1485,11 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
                  2LL * lv.n_f * vb;
         if (!lv.alpha_c.empty()) {
             const int pc = int(lv.alpha_c.size()) - 1;
-            bytes += sell_bytes(sl->d.Mc, vb) + pc * sell_bytes(sl->d.Acc, vb) + 2LL * lv.n_c * vb +
-                     (l > 0 ? 2LL * lv.n_c * vb : 0);
-            if (sl->d.Mf.n_rows) bytes += sell_bytes(sl->d.Mf, vb) + p * sell_bytes(sl->d.Aff, vb) + 2LL * lv.n_f * vb;
+            bytes += sell_bytes(sl->d.Mc, vb) + 2LL * lv.n_c * vb + (l > 0 ? 2LL * lv.n_c * vb : 0) +
+                     (sl->d.Ainvc.n_rows ? sell_bytes(sl->d.Ainvc, vb) : pc * sell_bytes(sl->d.Acc, vb));
+            if (sl->d.Mf.n_rows)
+                bytes += sell_bytes(sl->d.Mf, vb) + 2LL * lv.n_f * vb +
+                         (lv.Ainv.n_rows ? sell_bytes(sl->d.Ainv, vb) : p * sell_bytes(sl->d.Aff, vb));
         }
         S->max_nf = std::max(S->max_nf, lv.n_f);
         CK(cudaStreamSynchronize(st));
@@ -2008,10 +2025,12 @@ void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info)
             flops += 2LL * lv.A_ff.nnz * (p + 1);
         }
         if (!lv.alpha_c.empty()) {   // C-point smoothing keeps A_cf and A_cc
-            store += lv.Crows.nnz;
-            flops += 2LL * lv.Crows.nnz + 2LL * lv.A_cc.nnz * (long long)(lv.alpha_c.size() - 1);
+            store += lv.Crows.nnz + lv.Ainv_cc.nnz;
+            flops += 2LL * lv.Crows.nnz + (lv.Ainv_cc.n_rows ? 2LL * lv.Ainv_cc.nnz
+                                                              : 2LL * lv.A_cc.nnz * (long long)(lv.alpha_c.size() - 1));
         }
-        if (lv.Frows.n_rows) flops += 2LL * lv.Frows.nnz + 2LL * lv.A_ff.nnz * p;
+        if (lv.Frows.n_rows)
+            flops += 2LL * lv.Frows.nnz + (lv.Ainv.n_rows ? 2LL * lv.Ainv.nnz : 2LL * lv.A_ff.nnz * p);
     }
     if (L < 64) {
         info->n[L] = H.coarse.A.n_rows;

@@ -131,6 +131,7 @@ struct SolveLevelT {
     // [A_ff A_fc] of A_l over the level's nested positions, and A_cc over
     // the next level's
     Sell<T> Mc, Acc, Mf;
+    Sell<T> Ainvc;       // assembled Ahat_cc^-1 (C-point smoothing, AIRG_SMOOTH_ASSEMBLED)
 };
 
 struct SolveLevel {

@@ -79,6 +79,8 @@ def _check_setup(c):
         assert np.array_equal(G.airg_export_vector(h, l, 2), L.alpha), "alpha level %d" % l
         if L.A_cc is not None:
             _csr_equal(L.A_cc, G.airg_export_matrix(h, l, 5), "A_cc level %d" % l)
+        if L.Ainv_cc is not None:
+            _csr_equal(L.Ainv_cc, G.airg_export_matrix(h, l, 6), "Ahat_cc^-1 level %d" % l)
             assert np.array_equal(G.airg_export_vector(h, l, 5), L.alpha_c), "alpha_c level %d" % l
         sc = G.airg_export_vector(h, l, 4)
         assert int(sc[0]) == L.pmisr_rounds
@@ -360,31 +362,32 @@ def test_assembled_smoother_matches_oracle(prec):
     _check_solve(c)
 
 
+@pytest.mark.parametrize("smoother", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("smooth_type", [1, 2])
-def test_c_point_smoothing_matches_oracle(smooth_type, prec):
+def test_c_point_smoothing_matches_oracle(smooth_type, prec, smoother):
     """FC and FCF smoothing (Sec. 2, the options of Sec. 3.3.2): A_cc and the
     C-point polynomial bit for bit, the solution within 1e-9 of the oracle
     (FP64 and FP32 V-cycles), and the complexities of the extra blocks."""
     w = workload("grid", (203, 157))
-    c = Case(w, dict(smooth_type=smooth_type, precision=prec))
+    c = Case(w, dict(smooth_type=smooth_type, precision=prec, smoother=smoother))
     _check_setup(c)
     xg, ig, io = _check_solve(c)
     # the preconditioner itself must match, not only the converged solution
     _check_one_cycle(c, 1e-12 if prec == 0 else 1e-4)
     assert abs(ig.iterations - io.iterations) <= (1 if prec == 0 else 2), (ig.iterations, io.iterations)
     cf = G.airg_setup_info(G.airg_setup(c.pg["rowptr"], c.pg["col"], c.pg["val"],
-                                        G.airg_options_default(**w["opts"])))
+                                        G.airg_options_default(smoother=smoother, **w["opts"])))
     cs = G.airg_setup_info(c.h)
-    extra = sum(L.A.nnz - L.A_ff.nnz - L.A_fc.nnz for L in c.Ho.levels)
+    extra = sum(L.A.nnz - L.A_ff.nnz - L.A_fc.nnz + (L.Ainv_cc.nnz if L.Ainv_cc is not None else 0)
+                for L in c.Ho.levels)
     assert abs((cs["storage_complexity"] - cf["storage_complexity"]) * c.po.A.nnz - extra) < 1e-6 * c.po.A.nnz
     assert cs["cycle_complexity"] > cf["cycle_complexity"]
 
 
 def test_c_point_smoothing_many_rhs_and_rejections():
     """With C-point smoothing several right-hand sides are solved in turn and
-    each matches its own solve; the assembled smoother and batches of grids
-    reject it."""
+    each matches its own solve; batches of grids reject it."""
     w = workload("grid", (90, 70))
     vx, vy = velocity(w["theta"])
     pg = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
@@ -394,8 +397,6 @@ def test_c_point_smoothing_many_rhs_and_rejections():
     for q in range(3):
         xq, _ = G.airg_solve(h, B[q].contiguous(), rtol=1e-10)
         assert torch.equal(xq, X[q])
-    with pytest.raises(G.AirgError):
-        G.airg_setup(pg["rowptr"], pg["col"], pg["val"], G.airg_options_default(smooth_type=1, smoother=1))
     with pytest.raises(G.AirgError):
         G.airg_setup_batch([(pg["rowptr"], pg["col"], pg["val"])], G.airg_options_default(smooth_type=1))
 
