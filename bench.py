@@ -538,7 +538,7 @@ def run_sweep(args):
     else:
         P, A, GM, NE = G.AIRG_SMOOTH_POLYNOMIAL, G.AIRG_SMOOTH_ASSEMBLED, G.AIRG_INVERSE_GMRES, G.AIRG_INVERSE_NEUMANN
         settings = [(P, G.AIRG_SMOOTH_F, GM), (A, G.AIRG_SMOOTH_F, GM), (P, G.AIRG_SMOOTH_FC, GM),
-                    (P, G.AIRG_SMOOTH_FCF, GM), (P, G.AIRG_SMOOTH_F, NE)]
+                    (P, G.AIRG_SMOOTH_FCF, GM), (A, G.AIRG_SMOOTH_FC, GM), (P, G.AIRG_SMOOTH_F, NE)]
         for prec in (G.AIRG_FP64, G.AIRG_MIXED_FP32):
             for sm, stype, inv in settings:
                 opts = G.airg_options_default(coarse_poly_order=30, trunc_rtol=1e-2, precision=prec, smoother=sm,
