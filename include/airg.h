@@ -64,8 +64,8 @@ enum { AIRG_SMOOTH_POLYNOMIAL = 0, AIRG_SMOOTH_ASSEMBLED = 1 };
  * is the level's C residual before restriction; it keeps A_cf and A_cc on
  * every level.  With AIRG_SMOOTH_ASSEMBLED the C-point smooth applies the
  * fixed-sparsity Ahat_cc^-1 of Eq. 8 instead (one more matrix per level).
- * With FC or FCF, airg_solve with nrhs > 1 solves the right-hand sides one
- * after the other, and airg_setup_batch rejects them. */
+ * Every solve entry point (one or many right-hand sides, batches of grids,
+ * adjoint) supports all three. */
 enum { AIRG_SMOOTH_F = 0, AIRG_SMOOTH_FC = 1, AIRG_SMOOTH_FCF = 2 };
 /* Block approximate inverse behind the smoother and the restrictor: the
  * GMRES polynomial of Eq. 7 (AIRG), or the Neumann polynomial of nAIR

@@ -169,6 +169,39 @@ __global__ void kb_horner_last(SellView<T> A, const T* __restrict__ t, const T* 
     });
 }
 
+// last Horner term of an in-place smoother: e += a_0 t + A win (C-point
+// smooth, second F-point smooth of FCF; with win = t and a_0 = 0 it applies
+// an assembled inverse)
+template <class T, int KW, int PW>
+__global__ void kb_horner_acc(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win, T* e, T a0,
+                              int k)
+{
+    bfor_rows<T, KW, PW>(A, win, k, true, [&](int r, int lane, const T (&a)[KW]) {
+#pragma unroll
+        for (int j = 0; j < KW; ++j) {
+            int q = lane + 32 * j;
+            if (q < k) {
+                size_t o = size_t(r) * k + q;
+                e[o] = e[o] + fma(a0, t[o], a[j]);
+            }
+        }
+    });
+}
+
+// degree-0 in-place correction e += a_0 t, and a copy, over m values
+template <class T>
+__global__ void kb_acc0(long long m, const T* __restrict__ t, T* __restrict__ e, T a0)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) e[i] = e[i] + a0 * t[i];
+}
+template <class T>
+__global__ void kb_copy(long long m, const T* __restrict__ a, T* __restrict__ b)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) b[i] = a[i];
+}
+
 template <class T>
 __global__ void kb_smooth0(long long n, const T* __restrict__ t, const T* __restrict__ ec,
                            const int* __restrict__ W, T* __restrict__ ef, T a0, int k)
@@ -447,8 +480,8 @@ struct BatchData {
     int k = 0, m = 0;
     long long nk = 0;
     DBuf<double> V, Zs, w, bp, xp, r, part, hdev, inv;
-    DBuf<double> rwork, t, wa, wb, cr0, cr1, ct;               // FP64 V-cycle
-    DBuf<float> rwork32, e32, vin32, t32, wa32, wb32, cr032, cr132, ct32;  // FP32 V-cycle
+    DBuf<double> rwork, t, wa, wb, cr0, cr1, ct, rcs;          // FP64 V-cycle
+    DBuf<float> rwork32, e32, vin32, t32, wa32, wb32, cr032, cr132, ct32, rcs32;  // FP32 V-cycle
     DBuf<unsigned> ticket;
     HBuf<double> hh;
     struct GEntry { const void* v; void* z; cudaGraphExec_t exec; long long kernels; };
@@ -464,6 +497,7 @@ namespace {
 template <class T>
 struct BWork {
     T* rwork; T* t; T* wa; T* wb; T* cr0; T* cr1; T* ct;
+    T* rcs;    // saved C residuals, one slot per level l >= 1 (C-point smoothing)
 };
 
 template <class T>
@@ -480,6 +514,135 @@ const Sell<double>& bcoarse<double>(const SolveData& S) { return S.Ac; }
 template <>
 const Sell<float>& bcoarse<float>(const SolveData& S) { return S.Ac32; }
 
+// Prolongation and F-point smooth of level l for k right-hand sides (Eq. 6)
+template <class T>
+void bf_smooth(SolveData& S, int l, int k, const T* v, T* e, const BWork<T>& wk, cudaStream_t st)
+{
+    constexpr long long VB = sizeof(T);
+    const long long kk = k;
+    const SolveLevel& lv = *S.lv[l];
+    const T* src = l == 0 ? v : wk.rwork;
+    const SolveLevelT<T>& o = bops<T>(lv);
+    const T* rf = src + size_t(lv.off) * k;
+    const T* ec = e + size_t(lv.off + lv.n_f) * k;
+    T* ef = e + size_t(lv.off) * k;
+    const int nf = lv.n_f;
+    const int p = int(lv.alpha.size()) - 1;
+    const long long fB = (long long)nf * VB * kk;
+    S.cur_level = l;
+    LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB * kk + 3 * fB, (2 * o.M.nnz + 2LL * nf) * kk,
+           WITH_KWPW(k, o.M, kb_fresid<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
+                                                                    T(lv.alpha[p]), k)));
+    if (o.Ainv.n_rows) {
+        // assembled smoother: e_f = W e_c + Ahat^-1 t (last Horner kernel, a0 = 0)
+        LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, (2 * o.Ainv.nnz + 3LL * nf) * kk,
+                 WITH_KWPW(k, o.Ainv, kb_horner_last<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Ainv), wk.t, wk.t, ec,
+                                                                               lv.W.p, ef, T(0), k)));
+        return;
+    }
+    if (p == 0) {
+        LAUNCH_F(S, PK_HORNER, 3 * fB + 4LL * nf, 3LL * nf * kk,
+               kb_smooth0<T><<<grid_for((long long)nf * k, BT), BT, 0, st>>>(nf, wk.t, ec, lv.W.p, ef,
+                                                                            T(lv.alpha[0]), k));
+        return;
+    }
+    const long long hB = mat_bytes(o.Aff) + 3 * fB;
+    T* win = wk.wa;
+    T* wout = wk.wb;
+    for (int kq = p - 1; kq >= 1; --kq) {
+        LAUNCH_F(S, PK_HORNER, hB, (2 * o.Aff.nnz + 2LL * nf) * kk,
+               WITH_KWPW(k, o.Aff, kb_horner<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Aff), wk.t, win, wout,
+                                                                        T(lv.alpha[kq]), k)));
+        std::swap(win, wout);
+    }
+    LAUNCH_F(S, PK_HORNER, hB + fB + 4LL * nf, (2 * o.Aff.nnz + 3LL * nf) * kk,
+           WITH_KWPW(k, o.Aff, kb_horner_last<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Aff), wk.t, win, ec,
+                                                                         lv.W.p, ef, T(lv.alpha[0]), k)));
+}
+
+// e += q(A) t by Horner for k right-hand sides, w = a_p t already in wk.wa
+template <class T>
+void bhorner_into(SolveData& S, const Sell<T>& A, const std::vector<double>& al, const BWork<T>& wk, T* e,
+                  int n, int k, cudaStream_t st)
+{
+    constexpr long long VB = sizeof(T);
+    const long long kk = k, fB = (long long)n * VB * kk;
+    const int p = int(al.size()) - 1;
+    if (p == 0) {
+        LAUNCH_F(S, PK_HORNER, 3 * fB, 2LL * n * kk,
+                 kb_acc0<T><<<grid_for((long long)n * k, BT), BT, 0, st>>>((long long)n * k, wk.t, e, T(al[0])));
+        return;
+    }
+    const long long hB = mat_bytes(A) + 3 * fB;
+    T* win = wk.wa;
+    T* wout = wk.wb;
+    for (int kq = p - 1; kq >= 1; --kq) {
+        LAUNCH_F(S, PK_HORNER, hB, (2 * A.nnz + 2LL * n) * kk,
+                 WITH_KWPW(k, A, kb_horner<T, KW, PW><<<grid_rows(n, PW), BT, 0, st>>>(view(A), wk.t, win, wout,
+                                                                                      T(al[kq]), k)));
+        std::swap(win, wout);
+    }
+    LAUNCH_F(S, PK_HORNER, hB + fB, (2 * A.nnz + 3LL * n) * kk,
+             WITH_KWPW(k, A, kb_horner_acc<T, KW, PW><<<grid_rows(n, PW), BT, 0, st>>>(view(A), wk.t, win, e,
+                                                                                      T(al[0]), k)));
+}
+
+// C-point smooth of level l for k right-hand sides (Sec. 2):
+// t_c = r_c - [A_cf A_cc] e_l, e_c += q_c(A_cc) t_c (or Ahat_cc^-1 t_c)
+template <class T>
+void bc_smooth(SolveData& S, int l, int k, const T* v, T* e, const BWork<T>& wk, cudaStream_t st)
+{
+    constexpr long long VB = sizeof(T);
+    const long long kk = k;
+    const SolveLevel& lv = *S.lv[l];
+    const SolveLevelT<T>& o = bops<T>(lv);
+    const int nc = lv.n_c;
+    if (!nc) return;
+    const T* rc = l == 0 ? v + size_t(lv.off + lv.n_f) * k : wk.rcs + size_t(lv.rc_off) * k;
+    T* el = e + size_t(lv.off) * k;
+    T* ec = el + size_t(lv.n_f) * k;
+    const int p = int(lv.alpha_c.size()) - 1;
+    const long long cB = (long long)nc * VB * kk;
+    LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mc) + (long long)(lv.n_f + nc) * VB * kk + 3 * cB,
+             (2 * o.Mc.nnz + 2LL * nc) * kk,
+             WITH_KWPW(k, o.Mc, kb_fresid<T, KW, PW><<<grid_rows(nc, PW), BT, 0, st>>>(view(o.Mc), rc, el, wk.t, wk.wa,
+                                                                                   T(lv.alpha_c[p]), k)));
+    if (o.Ainvc.n_rows) {
+        LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainvc) + 4 * cB, (2 * o.Ainvc.nnz + 2LL * nc) * kk,
+                 WITH_KWPW(k, o.Ainvc, kb_horner_acc<T, KW, PW><<<grid_rows(nc, PW), BT, 0, st>>>(
+                                           view(o.Ainvc), wk.t, wk.t, ec, T(0), k)));
+        return;
+    }
+    bhorner_into<T>(S, o.Acc, lv.alpha_c, wk, ec, nc, k, st);
+}
+
+// second F-point smooth of FCF for k right-hand sides
+template <class T>
+void bf_smooth_again(SolveData& S, int l, int k, const T* v, T* e, const BWork<T>& wk, cudaStream_t st)
+{
+    constexpr long long VB = sizeof(T);
+    const long long kk = k;
+    const SolveLevel& lv = *S.lv[l];
+    const SolveLevelT<T>& o = bops<T>(lv);
+    const int nf = lv.n_f;
+    if (!nf) return;
+    const T* rf = (l == 0 ? v : wk.rwork) + size_t(lv.off) * k;
+    T* el = e + size_t(lv.off) * k;
+    const int p = int(lv.alpha.size()) - 1;
+    const long long fB = (long long)nf * VB * kk;
+    LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mf) + (long long)(nf + lv.n_c) * VB * kk + 3 * fB,
+             (2 * o.Mf.nnz + 2LL * nf) * kk,
+             WITH_KWPW(k, o.Mf, kb_fresid<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Mf), rf, el, wk.t, wk.wa,
+                                                                                   T(lv.alpha[p]), k)));
+    if (o.Ainv.n_rows) {
+        LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB, (2 * o.Ainv.nnz + 2LL * nf) * kk,
+                 WITH_KWPW(k, o.Ainv, kb_horner_acc<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(
+                                          view(o.Ainv), wk.t, wk.t, el, T(0), k)));
+        return;
+    }
+    bhorner_into<T>(S, o.Aff, lv.alpha, wk, el, nf, k, st);
+}
+
 // e = M^-1 v for k right-hand sides (nested order, [row][rhs])
 template <class T>
 void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStream_t st)
@@ -493,6 +656,10 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         const Sell<T>& Z = bops<T>(lv).Z;
         const Sell<T, bf16s>& Zb = bops<T>(lv).Zb;
         S.cur_level = l;
+        if (l > 0 && lv.n_c && S.smooth_type != AIRG_SMOOTH_F)   // restriction overwrites r_c in place
+            LAUNCH_F(S, PK_RESTRICT, 2LL * lv.n_c * VB * kk, 0,
+                     kb_copy<T><<<grid_for((long long)lv.n_c * k, BT), BT, 0, st>>>(
+                         (long long)lv.n_c * k, src + size_t(lv.off + lv.n_f) * k, wk.rcs + size_t(lv.rc_off) * k));
         if (lv.n_c && Zb.val.n)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Zb) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
                      (2 * Zb.nnz + lv.n_c) * kk,
@@ -542,44 +709,12 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         if (nr == 0) CK(cudaMemsetAsync(x, 0, sizeof(T) * size_t(nco) * k, st));
     }
     for (int l = L - 1; l >= 0; --l) {
-        const SolveLevel& lv = *S.lv[l];
-        const T* src = l == 0 ? v : wk.rwork;
-        const SolveLevelT<T>& o = bops<T>(lv);
-        const T* rf = src + size_t(lv.off) * k;
-        const T* ec = e + size_t(lv.off + lv.n_f) * k;
-        T* ef = e + size_t(lv.off) * k;
-        const int nf = lv.n_f;
-        const int p = int(lv.alpha.size()) - 1;
-        const long long fB = (long long)nf * VB * kk;
         S.cur_level = l;
-        LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB * kk + 3 * fB, (2 * o.M.nnz + 2LL * nf) * kk,
-               WITH_KWPW(k, o.M, kb_fresid<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
-                                                                        T(lv.alpha[p]), k)));
-        if (o.Ainv.n_rows) {
-            // assembled smoother: e_f = W e_c + Ahat^-1 t (last Horner kernel, a0 = 0)
-            LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, (2 * o.Ainv.nnz + 3LL * nf) * kk,
-                     WITH_KWPW(k, o.Ainv, kb_horner_last<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Ainv), wk.t, wk.t, ec,
-                                                                                   lv.W.p, ef, T(0), k)));
-            continue;
+        bf_smooth<T>(S, l, k, v, e, wk, st);
+        if (S.smooth_type != AIRG_SMOOTH_F) {
+            bc_smooth<T>(S, l, k, v, e, wk, st);
+            if (S.smooth_type == AIRG_SMOOTH_FCF) bf_smooth_again<T>(S, l, k, v, e, wk, st);
         }
-        if (p == 0) {
-            LAUNCH_F(S, PK_HORNER, 3 * fB + 4LL * nf, 3LL * nf * kk,
-                   kb_smooth0<T><<<grid_for((long long)nf * k, BT), BT, 0, st>>>(nf, wk.t, ec, lv.W.p, ef,
-                                                                                T(lv.alpha[0]), k));
-            continue;
-        }
-        const long long hB = mat_bytes(o.Aff) + 3 * fB;
-        T* win = wk.wa;
-        T* wout = wk.wb;
-        for (int kq = p - 1; kq >= 1; --kq) {
-            LAUNCH_F(S, PK_HORNER, hB, (2 * o.Aff.nnz + 2LL * nf) * kk,
-                   WITH_KWPW(k, o.Aff, kb_horner<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Aff), wk.t, win, wout,
-                                                                            T(lv.alpha[kq]), k)));
-            std::swap(win, wout);
-        }
-        LAUNCH_F(S, PK_HORNER, hB + fB + 4LL * nf, (2 * o.Aff.nnz + 3LL * nf) * kk,
-               WITH_KWPW(k, o.Aff, kb_horner_last<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Aff), wk.t, win, ec,
-                                                                             lv.W.p, ef, T(lv.alpha[0]), k)));
     }
     S.cur_level = 0;
     CK_LAUNCH();
@@ -591,11 +726,11 @@ void bprecond_launch(Hierarchy& H, BatchData& B, const double* v, double* z, cud
     long long nk = B.nk;
     if (mixed_precision(H.opt)) {
         LAUNCH(S, PK_LAYOUT, 12 * nk, kb_d2f<<<grid_for(nk, BT), BT, 0, st>>>(nk, v, B.vin32.p));
-        BWork<float> wk{B.rwork32.p, B.t32.p, B.wa32.p, B.wb32.p, B.cr032.p, B.cr132.p, B.ct32.p};
+        BWork<float> wk{B.rwork32.p, B.t32.p, B.wa32.p, B.wb32.p, B.cr032.p, B.cr132.p, B.ct32.p, B.rcs32.p};
         bvcycle<float>(S, B.k, B.vin32.p, B.e32.p, wk, st);
         LAUNCH(S, PK_LAYOUT, 12 * nk, kb_f2d<<<grid_for(nk, BT), BT, 0, st>>>(nk, B.e32.p, z));
     } else {
-        BWork<double> wk{B.rwork.p, B.t.p, B.wa.p, B.wb.p, B.cr0.p, B.cr1.p, B.ct.p};
+        BWork<double> wk{B.rwork.p, B.t.p, B.wa.p, B.wb.p, B.cr0.p, B.cr1.p, B.ct.p, B.rcs.p};
         bvcycle<double>(S, B.k, v, z, wk, st);
     }
 }
@@ -657,15 +792,18 @@ void ensure_batch(Hierarchy& H, int k)
     B->hh.alloc(size_t(3 * (MAXB + 2)) * k);
     B->ticket.alloc(1);
     CK(cudaMemset(B->ticket.p, 0, sizeof(unsigned)));
-    size_t nf = size_t(std::max(S.max_nf, 1)) * k, nc = size_t(std::max(S.n_coarse, 1)) * k;
+    size_t nf = size_t(std::max({S.max_nf, S.max_nc, 1})) * k, nc = size_t(std::max(S.n_coarse, 1)) * k;
+    const size_t nrc = S.smooth_type != AIRG_SMOOTH_F ? size_t(std::max<long long>(S.rc_total, 1)) * k : 0;
     if (mixed_precision(H.opt)) {
         B->rwork32.alloc(nk); B->e32.alloc(nk); B->vin32.alloc(nk);
         B->t32.alloc(nf); B->wa32.alloc(nf); B->wb32.alloc(nf);
         B->cr032.alloc(nc); B->cr132.alloc(nc); B->ct32.alloc(nc);
+        if (nrc) B->rcs32.alloc(nrc);
     } else {
         B->rwork.alloc(nk);
         B->t.alloc(nf); B->wa.alloc(nf); B->wb.alloc(nf);
         B->cr0.alloc(nc); B->cr1.alloc(nc); B->ct.alloc(nc);
+        if (nrc) B->rcs.alloc(nrc);
     }
     S.batch = B;
 }

@@ -406,7 +406,6 @@ airg_status airg_setup_batch(int nprob, const airg_csr* As, const airg_options* 
         if (opt) o = *opt;
         else airg_options_default(&o);
         airg::check_options_checked(o);
-        if (o.smooth_type != AIRG_SMOOTH_F) fail(AIRG_ERR_ARG, "C-point smoothing is not built for batches of grids");
         cudaStream_t st = (cudaStream_t)stream;
         auto B = std::make_unique<airg_batch_s>();
         for (int p = 0; p < nprob; ++p) {

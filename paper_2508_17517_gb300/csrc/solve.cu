@@ -1560,6 +1560,8 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         CK(cudaStreamSynchronize(st));
     }
     // work vectors
+    S->max_nc = max_nc;
+    S->rc_total = rc_total;
     size_t n0 = std::max(S->n0, 1), nf = std::max({S->max_nf, max_nc, 1}), nc = std::max(S->n_coarse, 1);
     S->rwork.alloc(n0);
     S->t.alloc(nf); S->wa.alloc(nf); S->wb.alloc(nf);
@@ -1960,9 +1962,8 @@ void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_de
     int g = grid_for(n, TB);
     const char* nb = getenv("AIRG_NO_BATCH");
     int nseq = nrhs;   // right-hand sides solved one after the other
-    if (nrhs > 1 && !(nb && nb[0] == '1') && S.smooth_type == AIRG_SMOOTH_F) {
+    if (nrhs > 1 && !(nb && nb[0] == '1')) {
         // many right-hand sides: lockstep outer iteration with the batched V-cycle
-        // (C-point smoothing has only the one-vector V-cycle: solved in turn below)
         for (int q0 = 0; q0 < nrhs; q0 += batch_max_width()) {
             int kq = std::min(batch_max_width(), nrhs - q0);
             solve_batched(H, kq, bdev + size_t(q0) * n, xdev + size_t(q0) * n, rtol, atol, maxit, info, st);

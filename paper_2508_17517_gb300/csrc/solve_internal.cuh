@@ -158,7 +158,8 @@ struct SolveData {
     DBuf<unsigned> ticket;       // last-block ticket of the dot kernels
     int newton_grid[2] = {0, 0}; // per precision (0: FP64, 1: FP32); 0 = not usable
     int smooth_grid[2] = {0, 0}; // co-resident blocks of the persistent smoother
-    int max_nf = 0;
+    int max_nf = 0, max_nc = 0;  // largest F block; largest C block with C-point smoothing
+    long long rc_total = 0;      // rows of all saved C residuals (C-point smoothing)
     // V-cycle work (FP64 and FP32 copies)
     DBuf<double> rwork, t, wa, wb, cx, cr0, cr1, ct;
     DBuf<float> rwork32, e32, t32, wa32, wb32, cx32, cr032, cr132, ct32, vin32;

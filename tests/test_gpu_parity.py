@@ -385,21 +385,42 @@ def test_c_point_smoothing_matches_oracle(smooth_type, prec, smoother):
     assert cs["cycle_complexity"] > cf["cycle_complexity"]
 
 
-def test_c_point_smoothing_many_rhs_and_rejections():
-    """With C-point smoothing several right-hand sides are solved in turn and
-    each matches its own solve; batches of grids reject it."""
+@pytest.mark.parametrize("smoother", [0, 1])
+def test_c_point_smoothing_many_rhs_and_grids(smoother):
+    """FCF smoothing in the batched many-RHS V-cycle and in a batch of grids:
+    one V-cycle (a single outer step from zero) and the converged solutions
+    match the oracle for every right-hand side."""
     w = workload("grid", (90, 70))
+    opts = dict(w["opts"], smooth_type=2, smoother=smoother)
     vx, vy = velocity(w["theta"])
     pg = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
-    h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"], G.airg_options_default(smooth_type=2, **w["opts"]))
-    B = torch.rand(3, w["nx"] * w["ny"], dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
-    X, info = G.airg_solve(h, B, rtol=1e-10)
+    po = O.advection_2d(w["nx"], w["ny"], vx, vy)
+    Ho = O.setup(po.A, _oopts(opts))
+    h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"], G.airg_options_default(**opts))
+    B = torch.rand(3, w["nx"] * w["ny"], dtype=torch.float64, device="cuda",
+                   generator=torch.Generator("cuda").manual_seed(5))
+    X1, _ = G.airg_solve(h, B, rtol=1e-300, maxit=1, allow_nc=True)
+    X, _ = G.airg_solve(h, B, rtol=1e-10)
     for q in range(3):
-        xq, _ = G.airg_solve(h, B[q].contiguous(), rtol=1e-10)
-        assert torch.equal(xq, X[q])
-    with pytest.raises(G.AirgError):
-        G.airg_setup_batch([(pg["rowptr"], pg["col"], pg["val"])], G.airg_options_default(smooth_type=1))
-
+        bo = B[q].cpu().numpy()
+        x1, _ = O.solve(Ho, po.A, bo, rtol=1e-300, maxit=1)
+        assert np.linalg.norm(X1[q].cpu().numpy() - x1) <= 1e-12 * np.linalg.norm(x1)
+        xo, _ = O.solve(Ho, po.A, bo, rtol=1e-10)
+        xg = X[q].cpu().numpy()
+        assert np.linalg.norm(bo - O.spmv(po.A, xg)) <= 1e-10 * np.linalg.norm(bo) * (1 + 1e-6)
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-9
+    w2 = workload("grid", (61, 77))
+    vx2, vy2 = velocity(w2["theta"])
+    pg2 = G.airg_problem_advection2d(w2["nx"], w2["ny"], vx2, vy2)
+    po2 = O.advection_2d(w2["nx"], w2["ny"], vx2, vy2)
+    Bt = G.airg_setup_batch([(pg["rowptr"], pg["col"], pg["val"]), (pg2["rowptr"], pg2["col"], pg2["val"])],
+                            G.airg_options_default(**opts))
+    bs = [B[0].contiguous(), torch.ones(w2["nx"] * w2["ny"], dtype=torch.float64, device="cuda")]
+    xs, infos = G.airg_solve_batch(Bt, bs, rtol=1e-10)
+    for x, b, P in zip(xs, bs, (po, po2)):
+        Hp = O.setup(P.A, _oopts(opts))
+        xo, _ = O.solve(Hp, P.A, b.cpu().numpy(), rtol=1e-10)
+        assert np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo) <= 1e-9
 
 @pytest.mark.parametrize("prec", [0, 1])
 def test_nair_matches_oracle(prec):
