@@ -11,8 +11,10 @@ between steps.  `e2e` repeats the solves through the C ABI with host
 buffers, copies included.  The roofline entry comes from a second pass of
 the same steps with per-kernel CUDA events (airg_profile).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c3|c1]
+  python bench.py [--gpus N] [--steps K] [--warmup W]
+                  [--workload c1|c2|c3|c3_fp64|c3_bf16|c4a|c4a_fp64|c4a_bf16|c4b]
   python bench.py --impl reference ...   (the CPU oracle as the reference arm)
+  python bench.py --sweep coarse-order|smoother|cases   (one JSON line of study rows)
 """
 import argparse
 import json
