@@ -108,3 +108,33 @@ def test_valid_solve_after_errors():
     b = torch.ones(rp.numel() - 1, dtype=torch.float64, device="cuda")
     x, info = G.airg_solve(h, b, rtol=1e-10)
     assert info.converged and info.rel_residual <= 1e-10
+
+
+def test_degenerate_inputs():
+    """Edge cases of the problem itself: an empty operator is rejected; a
+    1 x 1 grid (one inflow node, Eq. 2) solves to u = g; a zero right-hand
+    side returns x = 0 at once, for one and for several right-hand sides."""
+    e_rp = torch.zeros(1, dtype=torch.int64, device="cuda")
+    e_c = torch.zeros(0, dtype=torch.int32, device="cuda")
+    e_v = torch.zeros(0, dtype=torch.float64, device="cuda")
+    assert _status(e_rp, e_c, e_v) == 1
+    w = workload("grid", (1, 1))
+    vx, vy = velocity(w["theta"])
+    pg = G.airg_problem_advection2d(1, 1, vx, vy)
+    assert pg["rowptr"].numel() == 2 and pg["inflow"].numel() == 1
+    h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"])
+    g = torch.tensor([0.75], dtype=torch.float64, device="cuda")
+    b = G.airg_assemble_rhs_advection2d(pg, g)
+    x, info = G.airg_solve(h, b, rtol=1e-12)
+    assert info.converged and abs(float(x[0]) - 0.75) <= 1e-15
+    rp, c, v = _good(33, 29)
+    h = G.airg_setup(rp, c, v)
+    n = rp.numel() - 1
+    x, info = G.airg_solve(h, torch.zeros(n, dtype=torch.float64, device="cuda"), rtol=1e-10)
+    assert info.converged and info.iterations == 0 and not bool(x.any())
+    X, info = G.airg_solve(h, torch.zeros(3, n, dtype=torch.float64, device="cuda"), rtol=1e-10)
+    assert info.converged and not bool(X.any())
+    # maxit = 0 with a nonzero right-hand side: nothing to do, reported as not converged
+    x, info = G.airg_solve(h, torch.ones(n, dtype=torch.float64, device="cuda"), rtol=1e-10, maxit=0,
+                           allow_nc=True)
+    assert not info.converged and not bool(x.any())
