@@ -38,16 +38,22 @@ constexpr int MAXK = 128;        // right-hand sides per batch (KW <= 4)
 // diagonal term, part 0); with PW > 1 the partial rows meet in shared memory
 // and are added in part order.  PW is fixed per operator from its row
 // lengths (1 for short rows, 4 for long ones), so results do not depend on
-// timing.  Then epi(r, acc) runs once per row.  `dot` = false skips the
-// product (acc = 0).  Every thread of the block reaches the barrier.
-template <class T, int KW, int PW, class V, class Epi>
+// timing.  pre(r, lane) loads the row's other operands before the product,
+// so those loads overlap the gathers; entries are taken four at a time with
+// all their loads issued before their FMAs, which run in entry order.  Then
+// epi(r, lane, acc, pre) runs once per row.  `dot` = false skips the product
+// (acc = 0).  Every thread of the block reaches the barrier.
+template <class T, int KW, int PW, class V, class Pre, class Epi>
 __device__ __forceinline__ void bfor_rows(const SellView<T, V>& S, const T* __restrict__ x, int k, bool dot,
-                                          const Epi& epi)
+                                          const Pre& pre, const Epi& epi)
 {
+    using PV = decltype(pre(0, 0));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int part = warp % PW;
     const int r = blockIdx.x * (BT / 32 / PW) + warp / PW;
     const bool valid = r < S.n_rows;
+    const bool lead = valid && part == 0;
+    const PV pv = lead ? pre(r, lane) : PV{};
     T acc[KW];
 #pragma unroll
     for (int j = 0; j < KW; ++j) acc[j] = T(0);
@@ -62,7 +68,30 @@ __device__ __forceinline__ void bfor_rows(const SellView<T, V>& S, const T* __re
         }
         const int s = r >> 5;
         const int b = S.sptr[s] + (r & 31), w = (S.sptr[s + 1] - S.sptr[s]) >> 5;
-        for (int e = part; e < w; e += PW) {
+        int e = part;
+        for (; e + 3 * PW < w; e += 4 * PW) {
+            T v[4];
+            const T* xr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = b + 32 * (e + u * PW);
+                v[u] = ldval<T>(S.val + idx);
+                xr[u] = x + size_t(__ldg(S.col + idx)) * k;
+            }
+            T xv[4][KW];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int j = 0; j < KW; ++j) {
+                    int q = lane + 32 * j;
+                    xv[u][j] = q < k ? xr[u][q] : T(0);
+                }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int j = 0; j < KW; ++j) acc[j] = fma(v[u], xv[u][j], acc[j]);
+        }
+        for (; e < w; e += PW) {
             const int idx = b + 32 * e;
             const T v = ldval<T>(S.val + idx);
             const T* xr = x + size_t(__ldg(S.col + idx)) * k;
@@ -85,7 +114,26 @@ __device__ __forceinline__ void bfor_rows(const SellView<T, V>& S, const T* __re
                 for (int j = 0; j < KW; ++j) acc[j] += red[warp + p][j * 32 + lane];
         }
     }
-    if (valid && part == 0) epi(r, lane, acc);
+    if (lead) epi(r, lane, acc, pv);
+}
+
+// this lane's values of row r of v ([row][rhs]); b: a second vector
+template <class T, int KW>
+struct RowVals {
+    T a[KW], b[KW];
+};
+template <class T, int KW>
+__device__ __forceinline__ RowVals<T, KW> row_vals(const T* __restrict__ va, const T* __restrict__ vb,
+                                                   long long ra, long long rb, int lane, int k)
+{
+    RowVals<T, KW> o;
+#pragma unroll
+    for (int j = 0; j < KW; ++j) {
+        int q = lane + 32 * j;
+        o.a[j] = (va && q < k) ? va[size_t(ra) * k + q] : T(0);
+        o.b[j] = (vb && rb >= 0 && q < k) ? vb[size_t(rb) * k + q] : T(0);
+    }
+    return o;
 }
 
 // blocks for n rows at PW warps per row
@@ -94,7 +142,7 @@ inline int grid_rows(long long n, int pw) { return grid_for(n * pw, BT / 32); }
 template <class T, int KW, int PW>
 __global__ void kb_spmv(SellView<T> S, const T* __restrict__ x, T* __restrict__ y, int k)
 {
-    bfor_rows<T, KW, PW>(S, x, k, true, [&](int r, int lane, const T (&a)[KW]) {
+    bfor_rows<T, KW, PW>(S, x, k, true, [](int, int) { return 0; }, [&](int r, int lane, const T (&a)[KW], int) {
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
             int q = lane + 32 * j;
@@ -107,11 +155,13 @@ template <class T, int KW, int PW, class V = T>
 __global__ void kb_restrict(SellView<T, V> Z, const T* __restrict__ sf, const T* __restrict__ sc,
                             T* __restrict__ dc, int k)
 {
-    bfor_rows<T, KW, PW>(Z, sf, k, true, [&](int r, int lane, const T (&a)[KW]) {
+    bfor_rows<T, KW, PW>(Z, sf, k, true,
+                         [&](int r, int lane) { return row_vals<T, KW>(sc, nullptr, r, -1, lane, k); },
+                         [&](int r, int lane, const T (&a)[KW], const RowVals<T, KW>& pv) {
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
             int q = lane + 32 * j;
-            if (q < k) dc[size_t(r) * k + q] = sc[size_t(r) * k + q] + a[j];
+            if (q < k) dc[size_t(r) * k + q] = pv.a[j] + a[j];
         }
     });
 }
@@ -120,13 +170,15 @@ template <class T, int KW, int PW>
 __global__ void kb_fresid(SellView<T> M, const T* __restrict__ rf, const T* __restrict__ ec,
                           T* __restrict__ t, T* __restrict__ w, T ap, int k)
 {
-    bfor_rows<T, KW, PW>(M, ec, k, true, [&](int r, int lane, const T (&a)[KW]) {
+    bfor_rows<T, KW, PW>(M, ec, k, true,
+                         [&](int r, int lane) { return row_vals<T, KW>(rf, nullptr, r, -1, lane, k); },
+                         [&](int r, int lane, const T (&a)[KW], const RowVals<T, KW>& pv) {
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
             int q = lane + 32 * j;
             if (q < k) {
                 size_t o = size_t(r) * k + q;
-                T tt = rf[o] - a[j];
+                T tt = pv.a[j] - a[j];
                 t[o] = tt;
                 w[o] = ap * tt;
             }
@@ -138,14 +190,13 @@ template <class T, int KW, int PW>
 __global__ void kb_horner(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
                           T* __restrict__ wout, T ak, int k)
 {
-    bfor_rows<T, KW, PW>(A, win, k, true, [&](int r, int lane, const T (&a)[KW]) {
+    bfor_rows<T, KW, PW>(A, win, k, true,
+                         [&](int r, int lane) { return row_vals<T, KW>(t, nullptr, r, -1, lane, k); },
+                         [&](int r, int lane, const T (&a)[KW], const RowVals<T, KW>& pv) {
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
             int q = lane + 32 * j;
-            if (q < k) {
-                size_t o = size_t(r) * k + q;
-                wout[o] = fma(ak, t[o], a[j]);
-            }
+            if (q < k) wout[size_t(r) * k + q] = fma(ak, pv.a[j], a[j]);
         }
     });
 }
@@ -155,16 +206,13 @@ __global__ void kb_horner_last(SellView<T> A, const T* __restrict__ t, const T* 
                                const T* __restrict__ ec, const int* __restrict__ W,
                                T* __restrict__ ef, T a0, int k)
 {
-    bfor_rows<T, KW, PW>(A, win, k, true, [&](int r, int lane, const T (&a)[KW]) {
-        const int wc = W[r];
+    bfor_rows<T, KW, PW>(A, win, k, true,
+                         [&](int r, int lane) { return row_vals<T, KW>(t, ec, r, W[r], lane, k); },
+                         [&](int r, int lane, const T (&a)[KW], const RowVals<T, KW>& pv) {
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
             int q = lane + 32 * j;
-            if (q < k) {
-                size_t o = size_t(r) * k + q;
-                T p = wc >= 0 ? ec[size_t(wc) * k + q] : T(0);
-                ef[o] = p + fma(a0, t[o], a[j]);
-            }
+            if (q < k) ef[size_t(r) * k + q] = pv.b[j] + fma(a0, pv.a[j], a[j]);
         }
     });
 }
@@ -176,14 +224,13 @@ template <class T, int KW, int PW>
 __global__ void kb_horner_acc(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win, T* e, T a0,
                               int k)
 {
-    bfor_rows<T, KW, PW>(A, win, k, true, [&](int r, int lane, const T (&a)[KW]) {
+    bfor_rows<T, KW, PW>(A, win, k, true,
+                         [&](int r, int lane) { return row_vals<T, KW>(t, e, r, r, lane, k); },
+                         [&](int r, int lane, const T (&a)[KW], const RowVals<T, KW>& pv) {
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
             int q = lane + 32 * j;
-            if (q < k) {
-                size_t o = size_t(r) * k + q;
-                e[o] = e[o] + fma(a0, t[o], a[j]);
-            }
+            if (q < k) e[size_t(r) * k + q] = pv.b[j] + fma(a0, pv.a[j], a[j]);
         }
     });
 }
@@ -214,19 +261,21 @@ __global__ void kb_smooth0(long long n, const T* __restrict__ t, const T* __rest
     ef[i] = (wc >= 0 ? ec[size_t(wc) * k + q] : T(0)) + a0 * t[i];
 }
 
+// Newton steps of the coarse polynomial (Sec. 2.3) for k right-hand sides
 template <class T, int KW, int PW>
 __global__ void kb_newton_real(SellView<T> A, const T* __restrict__ rin, T* __restrict__ rout,
                                T* __restrict__ x, T inv, int first, int last, int k)
 {
-    bfor_rows<T, KW, PW>(A, rin, k, !last, [&](int r, int lane, const T (&a)[KW]) {
+    bfor_rows<T, KW, PW>(A, rin, k, !last,
+                         [&](int r, int lane) { return row_vals<T, KW>(rin, first ? nullptr : x, r, r, lane, k); },
+                         [&](int r, int lane, const T (&a)[KW], const RowVals<T, KW>& pv) {
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
             int q = lane + 32 * j;
             if (q < k) {
                 size_t o = size_t(r) * k + q;
-                T ri = rin[o];
-                x[o] = fma(ri, inv, first ? T(0) : x[o]);
-                if (!last) rout[o] = ri - a[j] * inv;
+                x[o] = fma(pv.a[j], inv, pv.b[j]);
+                if (!last) rout[o] = pv.a[j] - a[j] * inv;
             }
         }
     });
@@ -236,15 +285,17 @@ template <class T, int KW, int PW>
 __global__ void kb_newton_pair1(SellView<T> A, const T* __restrict__ rin, T* __restrict__ t,
                                 T* __restrict__ x, T two_a, T inv2, int first, int k)
 {
-    bfor_rows<T, KW, PW>(A, rin, k, true, [&](int r, int lane, const T (&a)[KW]) {
+    bfor_rows<T, KW, PW>(A, rin, k, true,
+                         [&](int r, int lane) { return row_vals<T, KW>(rin, first ? nullptr : x, r, r, lane, k); },
+                         [&](int r, int lane, const T (&a)[KW], const RowVals<T, KW>& pv) {
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
             int q = lane + 32 * j;
             if (q < k) {
                 size_t o = size_t(r) * k + q;
-                T tt = two_a * rin[o] - a[j];
+                T tt = two_a * pv.a[j] - a[j];
                 t[o] = tt;
-                x[o] = fma(tt, inv2, first ? T(0) : x[o]);
+                x[o] = fma(tt, inv2, pv.b[j]);
             }
         }
     });
@@ -254,14 +305,13 @@ template <class T, int KW, int PW>
 __global__ void kb_newton_pair2(SellView<T> A, const T* __restrict__ rin, const T* __restrict__ t,
                                 T* __restrict__ rout, T inv2, int k)
 {
-    bfor_rows<T, KW, PW>(A, t, k, true, [&](int r, int lane, const T (&a)[KW]) {
+    bfor_rows<T, KW, PW>(A, t, k, true,
+                         [&](int r, int lane) { return row_vals<T, KW>(rin, nullptr, r, -1, lane, k); },
+                         [&](int r, int lane, const T (&a)[KW], const RowVals<T, KW>& pv) {
 #pragma unroll
         for (int j = 0; j < KW; ++j) {
             int q = lane + 32 * j;
-            if (q < k) {
-                size_t o = size_t(r) * k + q;
-                rout[o] = rin[o] - a[j] * inv2;
-            }
+            if (q < k) rout[size_t(r) * k + q] = pv.a[j] - a[j] * inv2;
         }
     });
 }
