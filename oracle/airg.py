@@ -158,7 +158,8 @@ def advection_2d(nx, ny, vx, vy, h=None):
     with the row d*u = d*g.  Zero velocity components store no entry.
     """
     if h is None:
-        h = 1.0 / (nx - 1)
+        # a single column (or node) has no x spacing: the y spacing, else 1
+        h = 1.0 / (nx - 1) if nx > 1 else (1.0 / (ny - 1) if ny > 1 else 1.0)
     n = nx * ny
     ax, ay = abs(vx), abs(vy)
     d = ax + ay

@@ -175,7 +175,8 @@ def airg_options_default(**overrides):
 def airg_problem_advection2d(nx, ny, vx, vy, h=None, stream=None):
     """Device CSR (rowptr int64, col int32, val f64) and inflow node list."""
     import torch
-    h = 1.0 / (nx - 1) if h is None else h
+    if h is None:   # grid spacing; a single column (or node) falls back to the y spacing, else 1
+        h = 1.0 / (nx - 1) if nx > 1 else (1.0 / (ny - 1) if ny > 1 else 1.0)
     n = nx * ny
     dev = torch.device("cuda")
     rowptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
