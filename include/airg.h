@@ -153,6 +153,8 @@ airg_status airg_options_default(airg_options* opt);
  * no entry.  All pointers are DEVICE pointers, caller-allocated:
  *   rowptr: n+1, col: 3n, val: 3n, inflow: nx+ny (sorted node indices).
  * *nnz_out and *n_inflow_out (HOST pointers) receive the counts.
+ * AIRG_ERR_ARG unless nx, ny >= 2, 3 nx ny < 2^31, h > 0 and vx, vy finite
+ * (a smaller system can be passed to airg_setup as a CSR matrix directly).
  */
 airg_status airg_problem_advection2d(int64_t nx, int64_t ny, double vx, double vy, double h,
                                      int64_t* rowptr, int32_t* col, double* val,

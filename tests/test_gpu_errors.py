@@ -111,21 +111,23 @@ def test_valid_solve_after_errors():
 
 
 def test_degenerate_inputs():
-    """Edge cases of the problem itself: an empty operator is rejected; a
-    1 x 1 grid (one inflow node, Eq. 2) solves to u = g; a zero right-hand
-    side returns x = 0 at once, for one and for several right-hand sides."""
+    """Edge cases of the problem itself: an empty operator is rejected; the
+    single-node system (one inflow node, Eq. 2) solves to u = g; a zero
+    right-hand side returns x = 0 at once, for one and for several
+    right-hand sides; maxit = 0 returns x0 as not converged."""
     e_rp = torch.zeros(1, dtype=torch.int64, device="cuda")
     e_c = torch.zeros(0, dtype=torch.int32, device="cuda")
     e_v = torch.zeros(0, dtype=torch.float64, device="cuda")
     assert _status(e_rp, e_c, e_v) == 1
-    w = workload("grid", (1, 1))
-    vx, vy = velocity(w["theta"])
-    pg = G.airg_problem_advection2d(1, 1, vx, vy)
-    assert pg["rowptr"].numel() == 2 and pg["inflow"].numel() == 1
-    h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"])
-    g = torch.tensor([0.75], dtype=torch.float64, device="cuda")
-    b = G.airg_assemble_rhs_advection2d(pg, g)
-    x, info = G.airg_solve(h, b, rtol=1e-12)
+    # the grid builder needs two nodes per side; a single inflow node is the
+    # 1 x 1 system d u = d g, passed as a CSR matrix
+    with pytest.raises(G.AirgError):
+        G.airg_problem_advection2d(1, 1, 0.6, 0.8)
+    d = 1.4
+    h = G.airg_setup(torch.tensor([0, 1], dtype=torch.int64, device="cuda"),
+                     torch.tensor([0], dtype=torch.int32, device="cuda"),
+                     torch.tensor([d], dtype=torch.float64, device="cuda"))
+    x, info = G.airg_solve(h, torch.tensor([d * 0.75], dtype=torch.float64, device="cuda"), rtol=1e-12)
     assert info.converged and abs(float(x[0]) - 0.75) <= 1e-15
     rp, c, v = _good(33, 29)
     h = G.airg_setup(rp, c, v)
