@@ -355,11 +355,11 @@ airg_status airg_host_eigvals(int n, const double* H, double* wr, double* wi);
 
 /*
  * airg_dot_exact_noalloc: the same correctly rounded <x, y> as
- * airg_dot_exact, for callers that cannot allocate device memory (code
- * running during CUDA graph capture, inside a framework whose pool owns every
- * allocation, or on a latency-critical path where cudaMalloc's implicit
- * synchronisation is not allowed).  The paper has no counterpart: it is a
- * service of this library.
+ * airg_dot_exact, for callers that cannot allocate device memory: code
+ * inside a framework whose caching pool has reserved the device's memory (a
+ * cudaMalloc behind its back can fail or fragment it), or a latency-critical
+ * loop where cudaMalloc / cudaFree would synchronise the device.  The paper
+ * has no counterpart: it is a service of this library.
  *  - Allocates nothing: its scratch is a file-scope __device__ array of
  *    141 x 8 bytes (accumulator + inf/nan flag) that every GPU loading the
  *    library keeps until the process exits.

@@ -1,8 +1,9 @@
 // airg_dot_exact_noalloc: the correctly rounded dot product of
 // exact_dot.cuh for callers that must not allocate device memory -- for
-// example code running while a CUDA graph is being captured, inside a
-// framework that owns every allocation through its own pool, or in a
-// real-time loop where cudaMalloc's implicit synchronisation is not allowed.
+// example code inside a framework whose caching pool has reserved the
+// device's memory (a cudaMalloc behind its back can fail or fragment it), or
+// a latency-critical loop where cudaMalloc / cudaFree would synchronise the
+// device.
 //
 // Its only scratch (the 140-digit fixed-point accumulator and an inf/nan
 // flag, 1.1 KiB) is a file-scope __device__ array: every GPU that loads the

@@ -1,6 +1,7 @@
 """airg_dot_exact_noalloc: the allocation-free dot product for callers that
-cannot allocate device memory (graph capture, pool-owned frameworks,
-latency-critical loops), checked against the allocating airg_dot_exact.
+cannot allocate device memory (frameworks whose caching pool has reserved the
+device's memory, latency-critical loops where cudaMalloc would synchronise the
+device), checked against the allocating airg_dot_exact.
 
 Collected last on purpose, and runs either alone or after the other tests.
 """
