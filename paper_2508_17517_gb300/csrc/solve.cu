@@ -558,6 +558,82 @@ __global__ void k_newton_pair2(SellView<T> A, const T* __restrict__ rin, const T
                       [&](int r, T d, T ri) { rout[r] = ri - d * inv_mod2; });
 }
 
+// ------------------------------------- coarse steps with x in shared memory --
+// The coarsest operator is small and dense-ish (at 1024^2, 17k rows of ~170
+// entries), and its input vector fits in shared memory.  In this opt-in
+// form (tune_coarse_xs) each block first copies the whole of x there (one
+// coalesced pass) and every gather then reads shared memory instead of L2.
+// The copy takes most of an SM's shared memory, so blocks are XS_THREADS
+// wide, one per SM, and loop over groups of slices.  Each row is computed by
+// row_dot exactly as in for_rows with the same K and R, so results are
+// bit-identical to the unstaged kernels.
+constexpr int XS_THREADS = 1024;
+
+template <class T, int K, int R, class V, class Pre, class Epi>
+__device__ __forceinline__ void for_rows_xs(const SellView<T, V>& S, const T* __restrict__ x, int n_x,
+                                            const Pre& pre, const Epi& epi)
+{
+    extern __shared__ __align__(16) unsigned char xs_raw[];
+    T* xs = reinterpret_cast<T*>(xs_raw);
+    for (int i = threadIdx.x; i < n_x; i += XS_THREADS) xs[i] = x[i];
+    __syncthreads();
+    using PV = decltype(pre(0));
+    constexpr int spb = XS_THREADS / 32 / K;
+    const int lane = threadIdx.x & 31;
+    const int part = (threadIdx.x >> 5) % K;
+    const int ngroups = (S.n_slices + spb - 1) / spb;
+    for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {   // uniform over the block
+        const int slice = g * spb + (threadIdx.x >> 5) / K;
+        const int r = slice * 32 + lane;
+        const bool lead = part == 0 && r < S.n_rows;
+        PV pv = lead ? pre(r) : PV{};
+        T d = row_dot<T, K, R, V>(S, slice, lane, part, xs);
+        if (lead) epi(r, d, pv);
+    }
+}
+
+// y = S x (used to time the staged form against the unstaged one)
+template <class T, int K, int R>
+__global__ void __launch_bounds__(XS_THREADS, 1)
+k_spmv_xs(SellView<T> S, const T* __restrict__ x, int n_x, T* __restrict__ y)
+{
+    for_rows_xs<T, K, R>(S, x, n_x, [](int) { return 0; }, [&](int r, T d, int) { y[r] = d; });
+}
+
+template <class T, int K, int R>
+__global__ void __launch_bounds__(XS_THREADS, 1)
+k_newton_real_xs(SellView<T> A, const T* __restrict__ rin, int n_x, T* __restrict__ rout,
+                 T* __restrict__ x, T inv_theta, int first)
+{
+    for_rows_xs<T, K, R>(A, rin, n_x, [&](int r) { return Pair<T>{rin[r], first ? T(0) : x[r]}; },
+                         [&](int r, T d, Pair<T> q) {
+                             x[r] = fma(q.a, inv_theta, q.b);
+                             rout[r] = q.a - d * inv_theta;
+                         });
+}
+
+template <class T, int K, int R>
+__global__ void __launch_bounds__(XS_THREADS, 1)
+k_newton_pair1_xs(SellView<T> A, const T* __restrict__ rin, int n_x, T* __restrict__ t,
+                  T* __restrict__ x, T two_a, T inv_mod2, int first)
+{
+    for_rows_xs<T, K, R>(A, rin, n_x, [&](int r) { return Pair<T>{rin[r], first ? T(0) : x[r]}; },
+                         [&](int r, T d, Pair<T> q) {
+                             T tt = two_a * q.a - d;
+                             t[r] = tt;
+                             x[r] = fma(tt, inv_mod2, q.b);
+                         });
+}
+
+template <class T, int K, int R>
+__global__ void __launch_bounds__(XS_THREADS, 1)
+k_newton_pair2_xs(SellView<T> A, const T* __restrict__ rin, const T* __restrict__ t, int n_x,
+                  T* __restrict__ rout, T inv_mod2)
+{
+    for_rows_xs<T, K, R>(A, t, n_x, [&](int r) { return rin[r]; },
+                         [&](int r, T d, T ri) { rout[r] = ri - d * inv_mod2; });
+}
+
 // blocks of wpb_for(P) warps for n rows with P warps per 32-row slice
 inline int gk(long long n, int P) { return grid_for((n + 31) / 32, wpb_for(P) / P); }
 inline int bk(int P) { return 32 * wpb_for(P); }
@@ -622,6 +698,33 @@ inline int block_rows(const Sell<T, V>& S) { return bk(S.k); }
             }                                                                   \
         }                                                                       \
     } while (0)
+
+// WITH_KR for the staged coarse kernels: long rows only (S.k > 1), 4 or 8
+// loads in flight per lane (their 1024-thread blocks leave 64 registers a
+// thread, too few for 16 FP64 loads in flight).
+#define WITH_KR_XS(S, ...)                                                      \
+    do {                                                                        \
+        switch ((S).r) {                                                        \
+            case 4: { constexpr int RR = 4; WITH_K_LONG((S).k, __VA_ARGS__); } break;   \
+            case 8: { constexpr int RR = 8; WITH_K_LONG((S).k, __VA_ARGS__); } break;   \
+            default: fail(AIRG_ERR_STATE, "bad loads-per-lane");                \
+        }                                                                       \
+    } while (0)
+
+// Grid of the staged coarse kernels: one block per SM, at most one per
+// group of slices.  Their dynamic shared memory holds x (n_cols entries).
+template <class T>
+int xs_grid_for(const Sell<T>& A)
+{
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int spb = XS_THREADS / 32 / A.k;
+    const int groups = (A.n_slices + spb - 1) / spb;
+    return std::max(1, std::min(groups, sms));
+}
+template <class T>
+size_t xs_smem(const Sell<T>& A) { return sizeof(T) * size_t(A.n_cols); }
 
 // ------------------------------------------ persistent coarse polynomial --
 // Grid-wide barrier for a cooperative launch.  Thread 0 of each block
@@ -1235,16 +1338,29 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
                 if (last)
                     LAUNCH_F(S, PK_NEWTON, (i == 0 ? 2 : 3) * nB, 2LL * nco,
                            k_newton_last<T><<<grid_for(nco, TB), TB, 0, st>>>(nco, rin, x, T(1.0 / q.re), i == 0));
+                else if (A.xs)
+                    LAUNCH_F(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB, 2 * A.nnz + 4LL * nco,
+                           WITH_KR_XS(A, k_newton_real_xs<T, KK, RR><<<A.xs, XS_THREADS, xs_smem(A), st>>>(
+                                               Av, rin, A.n_cols, rout, x, T(1.0 / q.re), i == 0)));
                 else
                     LAUNCH_F(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB, 2 * A.nnz + 4LL * nco,
                            WITH_KR(A, k_newton_real<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
                                           Av, rin, rout, x, T(1.0 / q.re), i == 0)));
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
-                LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, 2 * A.nnz + 4LL * nco,
-                       WITH_KR(A, k_newton_pair1<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
-                                      Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
-                if (!last)
+                if (A.xs)
+                    LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, 2 * A.nnz + 4LL * nco,
+                           WITH_KR_XS(A, k_newton_pair1_xs<T, KK, RR><<<A.xs, XS_THREADS, xs_smem(A), st>>>(
+                                               Av, rin, A.n_cols, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
+                else
+                    LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, 2 * A.nnz + 4LL * nco,
+                           WITH_KR(A, k_newton_pair1<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
+                                          Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
+                if (!last && A.xs)
+                    LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
+                           WITH_KR_XS(A, k_newton_pair2_xs<T, KK, RR><<<A.xs, XS_THREADS, xs_smem(A), st>>>(
+                                               Av, rin, wk.ct, A.n_cols, rout, T(1.0 / mod2))));
+                else if (!last)
                     LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
                            WITH_KR(A, k_newton_pair2<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
                                           Av, rin, wk.ct, rout, T(1.0 / mod2))));
@@ -1279,14 +1395,15 @@ long long sell_bytes(const Sell<double>& S, int vbytes)
 // per lane r = 4, 8, 16 for long rows (several warps per slice).  Neither
 // changes the arithmetic.  forced > 0 (AIRG_ROWS_PER_WARP for short rows,
 // AIRG_LOADS_PER_LANE for long rows) skips the timing.
+// Returns the time of 3 launches of the chosen variant (0 when not timed).
 template <class T, class V>
-void tune_rows(Sell<T, V>& A, const T* x, T* y, int forced_short, int forced_long, cudaStream_t st)
+float tune_rows(Sell<T, V>& A, const T* x, T* y, int forced_short, int forced_long, cudaStream_t st)
 {
-    if (A.n_rows == 0) return;
+    if (A.n_rows == 0) return 0.f;
     const int forced = A.k == 1 ? forced_short : forced_long;
     if (forced) {
         A.r = forced;
-        return;
+        return 0.f;
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -1315,6 +1432,84 @@ void tune_rows(Sell<T, V>& A, const T* x, T* y, int forced_short, int forced_lon
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     A.r = best_r;
+    return best;
+}
+
+// Lets staged kernel `f` take the shared memory of any x that fits beside
+// its static shared memory; false if `need` bytes do not fit.
+template <class F>
+bool xs_allow(F* f, size_t need, int optin)
+{
+    cudaFuncAttributes fa;
+    CK(cudaFuncGetAttributes(&fa, f));
+    if (fa.sharedSizeBytes + need > size_t(optin)) return false;
+    CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - int(fa.sharedSizeBytes)));
+    return true;
+}
+
+template <class T, int K, int R>
+bool xs_allow_all(size_t need, int optin)
+{
+    return xs_allow(k_spmv_xs<T, K, R>, need, optin) && xs_allow(k_newton_real_xs<T, K, R>, need, optin) &&
+           xs_allow(k_newton_pair1_xs<T, K, R>, need, optin) && xs_allow(k_newton_pair2_xs<T, K, R>, need, optin);
+}
+
+// Staged form of the coarsest operator's SpMVs (x in shared memory, for
+// long rows when x fits), opt-in: AIRG_COARSE_XS=1 stages whenever x fits,
+// with 4 or 8 loads in flight per lane (the faster by timing y = A x);
+// AIRG_COARSE_XS=2 stages only when that also times faster than the best
+// unstaged form (`unstaged_ms` for 3 launches, 0 when not timed).  Neither
+// form changes the arithmetic.  Off by default: on the 1024^2 workload the
+// staged step measured 17.6 against 17.0 us, since the step is bound by the
+// FP64 pipe and the matrix loads, not by the gathers of x.
+template <class T>
+void tune_coarse_xs(Sell<T>& A, float unstaged_ms, const T* x, T* y, cudaStream_t st)
+{
+    A.xs = 0;
+    if (A.n_rows == 0 || A.k < 2) return;
+    const char* env = getenv("AIRG_COARSE_XS");
+    const int mode = env ? atoi(env) : 0;
+    if (mode != 1 && mode != 2) return;
+    if (mode == 2 && unstaged_ms <= 0.f) return;
+    int dev = 0, optin = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t need = xs_smem(A);
+    const int r0 = A.r, cand[2] = {4, 8};
+    bool fits = true;
+    for (int ci = 0; ci < 2 && fits; ++ci) {
+        A.r = cand[ci];
+        WITH_KR_XS(A, fits = xs_allow_all<T, KK, RR>(need, optin));
+    }
+    A.r = r0;
+    if (!fits) return;
+    const int grid = xs_grid_for(A);
+    const SellView<T> v = view(A);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = mode == 2 ? unstaged_ms : 0.f;
+    int best_r = 0;
+    for (int ci = 0; ci < 2; ++ci) {
+        A.r = cand[ci];
+        WITH_KR_XS(A, k_spmv_xs<T, KK, RR><<<grid, XS_THREADS, need, st>>>(v, x, A.n_cols, y));
+        CK_LAUNCH();
+        CK(cudaEventRecord(e0, st));
+        for (int rep = 0; rep < 3; ++rep)
+            WITH_KR_XS(A, k_spmv_xs<T, KK, RR><<<grid, XS_THREADS, need, st>>>(v, x, A.n_cols, y));
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if ((mode == 1 && best_r == 0) || ms < best) {   // mode 1: the faster R
+            best = ms;
+            best_r = cand[ci];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    A.r = best_r ? best_r : r0;
+    A.xs = best_r ? grid : 0;
 }
 
 int env_choice(const char* name, std::initializer_list<int> allowed)
@@ -1346,7 +1541,8 @@ void tune_all(SolveData& S, cudaStream_t st)
         tune_rows(o.Mf, x.p, y.p, fs, fl, st);
         tune_rows(o.Ainvc, x.p, y.p, fs, fl, st);
     }
-    tune_rows(const_cast<Sell<T>&>(coarse_op<T>(S)), x.p, y.p, fs, fl, st);
+    Sell<T>& Ac = const_cast<Sell<T>&>(coarse_op<T>(S));
+    tune_coarse_xs(Ac, tune_rows(Ac, x.p, y.p, fs, fl, st), x.p, y.p, st);
     CK(cudaStreamSynchronize(st));
 }
 

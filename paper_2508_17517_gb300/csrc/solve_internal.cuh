@@ -53,6 +53,7 @@ struct bf16s {
 template <class T, class V = T>
 struct Sell {
     int n_rows = 0, n_cols = 0, n_slices = 0, k = 1, r = 1;
+    int xs = 0;   // coarsest operator only: > 0 = its SpMVs stage x in shared memory, on xs blocks (solve.cu)
     long long nnz = 0, padded = 0, ndiag = 0;
     DBuf<int> sptr;
     DBuf<int> col;

@@ -253,6 +253,36 @@ def test_alternative_launch_paths(env, monkeypatch):
     _check_solve(c)
 
 
+@pytest.mark.parametrize("n,prec", [(1024, 0), (2048, 1)])
+def test_coarse_steps_with_x_in_shared_memory(n, prec, monkeypatch):
+    """The coarse Newton steps with x staged in shared memory
+    (AIRG_COARSE_XS=1) give the same bits as the unstaged steps
+    (AIRG_COARSE_XS=0): they compute every row with the same summation
+    order.  1024^2 in FP64 (17k coarse rows of ~170 entries, 8 warps per
+    slice, the last slice ragged) and 2048^2 with the FP32 V-cycle."""
+    w = workload("c2", n)
+    vx, vy = velocity(w["theta"])
+    pg = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
+    opts = G.airg_options_default(**dict(w["opts"], precision=prec))
+    b = G.airg_assemble_rhs_advection2d(pg, torch.tensor(w["g"][0], device="cuda"))
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("AIRG_COARSE_XS", mode)
+        h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"], opts)
+        info = G.airg_setup_info(h)
+        nco, nnz = info["n"][info["levels"] - 1], info["nnz_a"][info["levels"] - 1]
+        x, si = G.airg_solve(h, b, rtol=w["rtol"])
+        out[mode] = (x, si.iterations, si.rel_residual)
+    # the staged form applies: long rows (several warps per slice) and x fits
+    # in shared memory beside the 32 x 32 reduction tile
+    vb = 8 if prec == 0 else 4
+    assert nnz / nco > 24 and nco * vb + 32 * 32 * vb <= 227 * 1024, (nco, nnz)
+    (x0, it0, rr0), (x1, it1, rr1) = out["0"], out["1"]
+    assert it0 == it1 and rr0 == rr1
+    assert torch.equal(x0, x1)
+    assert rr1 <= w["rtol"]
+
+
 def test_chunked_sparse_products(monkeypatch):
     """Sparse products split into many row chunks (tiny hash-table budget)
     give the same bits as in one chunk."""
