@@ -34,6 +34,31 @@ def test_library_exports_every_declared_symbol(L):
         assert hasattr(L, name), name
 
 
+def test_binding_argument_types_match_header_prototypes(L):
+    """Every ctypes signature of the binding agrees with its prototype in
+    include/airg.h: same number of arguments, pointers where the header has
+    pointers, and scalars of the same width and kind (integer or floating)."""
+    import ctypes
+    txt = open(os.path.join(ROOT, "include", "airg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    protos = re.findall(r"\b(airg_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", txt)
+    assert sorted(n for n, _ in protos) == _declared()
+    scalars = {"int": ctypes.c_int, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64,
+               "uint64_t": ctypes.c_uint64, "double": ctypes.c_double, "float": ctypes.c_float}
+    floating = (ctypes.c_double, ctypes.c_float)
+    for name, args in protos:
+        args = [a.strip() for a in args.split(",") if a.strip() not in ("", "void")]
+        at = getattr(L, name).argtypes
+        assert at is not None and len(at) == len(args), name
+        for a, t in zip(args, at):
+            decl = re.sub(r"\bconst\b", "", a).split()
+            if "*" in a:
+                assert t is ctypes.c_void_p or issubclass(t, ctypes._Pointer), (name, a, t)
+            elif decl[0] in scalars:
+                e = scalars[decl[0]]
+                assert ctypes.sizeof(t) == ctypes.sizeof(e) and (t in floating) == (e in floating), (name, a, t)
+
+
 def test_options_default_are_paper_values(L):
     o = G.airg_options_default()
     assert (o.strong_threshold, o.ddc_fraction, o.ddc_its, o.poly_order) == (0.99, 0.01, 2, 6)
