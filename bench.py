@@ -459,6 +459,8 @@ def run_gpu(args):
             "config": {"workload": w["desc"], "n": n, "nrhs": k, "rtol": w["rtol"],
                        "parallelism": "replicas" if world > 1 else "single",
                        "levels": sinfo["levels"], "iterations_per_solve": statistics.median(its),
+                       # DOFs x V-cycles per second, the paper's per-V-cycle rate (Sec. 3.2)
+                       "dofs_per_s_per_vcycle": value * statistics.median(its),
                        "setup_ms": sinfo["setup_ms"], "cycle_complexity": sinfo["cycle_complexity"],
                        "storage_complexity": sinfo["storage_complexity"],
                        "vcycle_algorithmic_bytes": vc_bytes,
