@@ -417,6 +417,31 @@ def test_newton_form_equals_power_form():
     assert np.allclose(x, K @ ybf, rtol=1e-8)
 
 
+@pytest.mark.parametrize("roots", [[(2.0, 0.0), (1.5, 0.7), (3.0, 0.0)],
+                                   [(2.5, 0.0), (1.2, 0.4)],
+                                   [(1.7, 0.0)],
+                                   [(0.9, 1.1), (2.2, 0.3)]])
+def test_truncation_residual_is_residual_polynomial(roots):
+    """Sec. 2.4 tests ||b2 - A q(A) b2|| / ||b2||.  For q in Newton form
+    (Sec. 2.3), b2 - A q(A) b2 = prod_i (I - A / theta_i) b2 over every root,
+    a pair a +- ib contributing both conjugates: the product is formed
+    densely in complex arithmetic, for real roots and pairs in any position
+    (the last one included)."""
+    n, level = 30, 3
+    A, D = _diag_dominant(n, 5)
+    opts = O.Options()
+    R = np.eye(n, dtype=complex)
+    for a, bi in roots:
+        for th in ([complex(a, 0.0)] if bi == 0.0 else [complex(a, bi), complex(a, -bi)]):
+            R = R @ (np.eye(n) - D / th)
+    b2 = O.rng_uniform(opts.seed, level, O.PURPOSE_TRUNC, n)
+    rb = R @ b2
+    assert np.max(np.abs(rb.imag)) < 1e-12 * np.max(np.abs(rb.real))
+    expected = np.linalg.norm(rb.real) / np.linalg.norm(b2)
+    got = O.truncation_residual(A, roots, opts, level)
+    assert abs(got - expected) <= 1e-12 * expected
+
+
 # ------------------------------------------------------------- V-cycle ----
 def test_grid_aligned_direction_is_exact_solver():
     """v = (1, 0): uncoupled 1D chains; A_ff diagonal, ideal R, exact
