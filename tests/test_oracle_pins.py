@@ -417,6 +417,25 @@ def test_newton_form_equals_power_form():
     assert np.allclose(x, K @ ybf, rtol=1e-8)
 
 
+def test_leja_order_hand_examples():
+    """Leja order (Sec. 2.3): the largest root first, then each next root
+    maximises the product of distances to the roots already taken (both
+    members of a taken pair count); a conjugate pair is one entry (im > 0).
+    Worked by hand: {1, 2, 4, 8} -> 8 (largest); 1 (distance 7); 4 (4*3 = 12
+    against 6*1 = 6 for 2); 2.  {3, 0.5, 1 +- i} -> 3; 0.5 (2.5 against
+    |1 + i - 3| = 2.24); the pair."""
+    opts = O.Options(addroot_log10=1e300)           # no added copies
+    assert O.order_roots([1.0, 2.0, 4.0, 8.0], opts) == [(8.0, 0.0), (1.0, 0.0), (4.0, 0.0), (2.0, 0.0)]
+    got = O.order_roots([1 + 1j, 0.5, 1 - 1j, 3.0], opts)
+    assert got == [(3.0, 0.0), (0.5, 0.0), (1.0, 1.0)]
+    # the added-copy reading: a root whose other factors |1 - z/theta_i|
+    # multiply to 10^6 > 10^4 gets ceil((6 - 4) / 14) = 1 copy, appended
+    opts = O.Options()
+    assert (opts.addroot_log10, opts.addroot_per) == (4.0, 14.0)
+    got = O.order_roots([1.0, 1000001.0], opts)
+    assert got == [(1000001.0, 0.0), (1.0, 0.0), (1000001.0, 0.0)]
+
+
 @pytest.mark.parametrize("roots", [[(2.0, 0.0), (1.5, 0.7), (3.0, 0.0)],
                                    [(2.5, 0.0), (1.2, 0.4)],
                                    [(1.7, 0.0)],
