@@ -417,6 +417,30 @@ def test_newton_form_equals_power_form():
     assert np.allclose(x, K @ ybf, rtol=1e-8)
 
 
+@pytest.mark.parametrize("k", [3, 5, 7])
+def test_harmonic_ritz_values_from_their_definition(k):
+    """Harmonic Ritz values (Sec. 2.3) of A over K_k(A, b) are the theta with
+    (A - theta I) y orthogonal to A K_k for some y in K_k.  With an
+    orthonormal basis V of K_k (numpy QR of the monomial basis) and W = A V
+    that is the generalised eigenproblem (W^T W) g = theta (W^T V) g, solved
+    here by scipy: it must give the oracle's eig(H_k + h^2 H_k^-T e_k e_k^T)
+    from its Arnoldi Hessenberg (k below n, so the h^2 term is present)."""
+    sla = pytest.importorskip("scipy.linalg")
+    n = 40
+    A, D = _diag_dominant(n, 17 + k)
+    b = O.rng_uniform(3, 0, O.PURPOSE_COARSE, n)
+    H, kk, broke, _ = O.arnoldi(A, b, k, 1e-14, 0.0)
+    assert kk == k and not broke and H[k, k - 1] > 1e-3
+    K = np.stack([np.linalg.matrix_power(D, j) @ b for j in range(k)], 1)
+    V, _ = np.linalg.qr(K)
+    W = D @ V
+    ref = np.sort_complex(sla.eigvals(W.T @ W, W.T @ V))
+    got = np.sort_complex(O.harmonic_ritz(H, kk, broke))
+    assert np.allclose(got, ref, rtol=1e-8, atol=1e-10)
+    # and they differ from the plain Ritz values eig(H_k) when h_{k+1,k} != 0
+    assert not np.allclose(np.sort_complex(np.linalg.eigvals(H[:k, :k])), ref, rtol=1e-6)
+
+
 def test_leja_order_hand_examples():
     """Leja order (Sec. 2.3): the largest root first, then each next root
     maximises the product of distances to the roots already taken (both
