@@ -963,17 +963,24 @@ def solve(Hh, A, b, rtol=1e-10, atol=1e-50, restart=30, maxit=200, x0=None, oute
 # Complexities (Sec. 3)
 # --------------------------------------------------------------------------
 def complexities(Hh):
-    """Storage complexity: nnz of the matrices kept for the solve over
-    nnz(A_top).  Cycle complexity: flops of one V-cycle over the flops of one
-    top-level SpMV (2 flops per stored entry)."""
+    """The two measures of Sec. 3.  Storage complexity: the non-zeros of every
+    matrix the solve needs over nnz(A_top) -- A_top itself (the outer
+    residual), and per level A_ff, A_fc, R = [Z I] (nnz(Z) + n_c) and the
+    one-point P = [W; I] (one index per F row + n_c), plus the coarse matrix.
+    Cycle complexity: the flops of one V-cycle's SpMVs over those of one
+    top-level SpMV (2 flops per stored entry); in the coarse Newton
+    polynomial a real root costs one SpMV and a conjugate pair two, except
+    that the last root skips its residual update."""
     top = Hh.levels[0].A.nnz if Hh.levels else Hh.A_coarse.nnz
     assembled = Hh.opts is not None and Hh.opts.smoother == "assembled"
     st = Hh.opts.smooth_type if Hh.opts is not None else "f"
-    store = 0
+    store = top
     flops = 0
     for L in Hh.levels:
         p = len(L.alpha) - 1
-        store += L.A_ff.nnz + L.A_fc.nnz + L.Z.nnz
+        n_f = int(L.is_f.sum())
+        n_c = L.n - n_f
+        store += L.A_ff.nnz + L.A_fc.nnz + (L.Z.nnz + n_c) + (n_f + n_c)
         flops += 2 * L.Z.nnz + 2 * L.A_fc.nnz
         if assembled:
             store += L.Ainv.nnz
@@ -990,8 +997,10 @@ def complexities(Hh):
         if st == "fcf":
             flops += 2 * L.A_fc.nnz + 2 * L.A_ff.nnz + (2 * L.Ainv.nnz if assembled else 2 * L.A_ff.nnz * p)
     nr = len(Hh.roots)
+    nspmv = sum((0 if i == nr - 1 else 1) if im == 0.0 else (1 if i == nr - 1 else 2)
+                for i, (_, im) in enumerate(Hh.roots))
     store += Hh.A_coarse.nnz
-    flops += 2 * Hh.A_coarse.nnz * max(nr - 1, 0)
+    flops += 2 * Hh.A_coarse.nnz * nspmv
     return {"storage": store / top, "cycle": flops / (2.0 * top),
             "levels": len(Hh.levels) + 1}
 

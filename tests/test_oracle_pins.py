@@ -544,6 +544,38 @@ def test_complexities_in_paper_range():
     assert 2 < cx["storage"] < 20
 
 
+@pytest.mark.parametrize("opts", [dict(), dict(smoother="assembled"), dict(smooth_type="fc"),
+                                  dict(smooth_type="fcf", smoother="assembled"), dict(poly_order=0)])
+def test_complexities_count_what_one_vcycle_does(opts, monkeypatch):
+    """Sec. 3 defines the cycle complexity as the FLOPs of one V-cycle over
+    those of one top-level SpMV, and the storage complexity as the non-zeros
+    of every matrix the solve needs over nnz(A_top).  Every SpMV of the
+    oracle's V-cycle is counted here as it runs (2 flops per stored entry),
+    and the distinct matrices it touches are collected; the top matrix (the
+    outer residual), R's identity block (n_c) and the one-point P (one index
+    per F row plus its identity block) complete the storage.  The coarse
+    polynomial of this case has real roots and conjugate pairs."""
+    P = _grid(48, 40, 0.9)
+    H = O.setup(P.A, O.Options(trunc_start_level=1, **opts))
+    assert any(im > 0 for _, im in H.roots) and any(im == 0 for _, im in H.roots)
+    flops, mats = [0], {}
+    real_spmv = O.spmv
+
+    def counting_spmv(A, x):
+        flops[0] += 2 * A.nnz
+        mats[id(A)] = A.nnz
+        return real_spmv(A, x)
+
+    monkeypatch.setattr(O, "spmv", counting_spmv)
+    O.vcycle(H, np.random.default_rng(1).standard_normal(P.A.n_rows))
+    monkeypatch.setattr(O, "spmv", real_spmv)
+    top = P.A.nnz
+    cx = O.complexities(H)
+    assert cx["cycle"] == flops[0] / (2.0 * top)
+    blocks = sum(2 * int((~L.is_f).sum()) + int(L.is_f.sum()) for L in H.levels)
+    assert cx["storage"] == (top + sum(mats.values()) + blocks) / top
+
+
 def test_dense_adjoint():
     P = _grid(12, 12, 0.5)
     rhs = np.random.default_rng(0).standard_normal(144)
