@@ -297,6 +297,22 @@ def test_gmres_coeffs_equal_bruteforce_least_squares(p):
     assert np.allclose(O.horner_apply(A, alpha, t), qd @ t, rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("k", [1, 2, 5, 9])
+def test_givens_least_squares_against_lapack(k):
+    """The Givens solution of min ||beta e1 - H y|| for a (k+1) x k upper
+    Hessenberg H, and its residual (the Arnoldi stopping test of reading 8),
+    equal numpy's least-squares solution and residual."""
+    rng = np.random.default_rng(40 + k)
+    H = np.triu(rng.standard_normal((k + 1, k)), -1)
+    beta = 0.5 + rng.random()
+    e1 = np.zeros(k + 1)
+    e1[0] = beta
+    y_ref = np.linalg.lstsq(H, e1, rcond=None)[0]
+    res_ref = np.linalg.norm(e1 - H @ y_ref)
+    assert np.allclose(O.givens_lsq(H, beta), y_ref, rtol=1e-10, atol=1e-12)
+    assert abs(O.givens_residual(H, beta) - res_ref) <= 1e-12 * max(res_ref, beta)
+
+
 def test_gmres_coeffs_scaled_identity_breakdown():
     n, d = 30, 2.5
     A = O.csr_from_entries(n, n, np.arange(n), np.arange(n), np.full(n, d))
