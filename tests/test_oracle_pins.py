@@ -599,6 +599,32 @@ def test_dense_adjoint():
     assert np.allclose(P.A.to_dense().T @ lam, rhs, atol=1e-12)
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_fgmres_iterate_minimises_residual_over_its_space(k):
+    """With a fixed linear preconditioner M^-1 (one V-cycle), k steps of
+    right-preconditioned (flexible) GMRES from x0 = 0 give the x in
+    M^-1 K_k(A M^-1, b) with the smallest ||b - A x||_2: formed here from
+    dense M^-1 (the V-cycle applied to the unit vectors), a monomial Krylov
+    basis and numpy least squares.  The recorded residual history equals
+    the true residual of that iterate."""
+    P = _grid(13, 11, 0.7)
+    n = P.A.n_rows
+    H = O.setup(P.A, O.Options(poly_order=2, trunc_start_level=1))
+    b = O.assemble_rhs(P, np.random.default_rng(9).random(P.inflow.size),
+                       np.random.default_rng(10).standard_normal(n))
+    Minv = np.stack([O.vcycle(H, e) for e in np.eye(n)], 1)
+    A = P.A.to_dense()
+    B = A @ Minv
+    K = np.stack([np.linalg.matrix_power(B, j) @ b for j in range(k)], 1)
+    y = np.linalg.lstsq(B @ K, b, rcond=None)[0]
+    x_ref = Minv @ (K @ y)
+    x, info = O.fgmres(P.A, b, lambda r: O.vcycle(H, r), rtol=0.0, restart=30, maxit=k)
+    assert info.iterations == k
+    nb = np.linalg.norm(b)
+    assert np.linalg.norm(x - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+    assert abs(info.history[k] - np.linalg.norm(b - A @ x) / nb) <= 1e-10
+
+
 def test_richardson_iterates_match_closed_form():
     """The V-cycle is a fixed linear map B (fixed polynomials, fixed
     operators), so Richardson from x0 = 0 gives the partial Neumann sums
