@@ -9,10 +9,11 @@ same readings are listed in the design notes of the repository).
 
 Functions pinned by tests against closed forms, brute force or library
 routines: exact dot, SpMV, problem builder + sweep, strength, PMISR, DDC,
-extract, GMRES polynomial coefficients, fixed-sparsity inverse, restrictor,
-one-point prolongator, RAP + drop/lump, harmonic Ritz / Newton application,
-V-cycle (F, FC and FCF smoothing), nAIR Neumann coefficients, FGMRES,
-dense adjoint.
+extract, Givens least squares, GMRES polynomial coefficients, fixed-sparsity
+inverse, restrictor, one-point prolongator, RAP + drop/lump, harmonic Ritz
+values, Leja order, Newton application, truncation residual, V-cycle (F, FC
+and FCF smoothing), complexities, nAIR Neumann coefficients, FGMRES,
+Richardson, dense adjoint.
 Parity unpinned (internal choices with no closed form in the paper): the
 value of the R drop tolerance, the PMISR measure direction, the one-point
 weight, and the Loe-Morgan added-root thresholds.
