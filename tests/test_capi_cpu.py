@@ -112,3 +112,58 @@ def test_host_eigvals_of_arnoldi_hessenberg(L):
     got = np.sort_complex(G.airg_host_eigvals(H[:k, :k]))
     ref = np.sort_complex(np.linalg.eigvals(H[:k, :k]))
     assert np.allclose(got, ref, rtol=1e-9, atol=1e-10)
+
+
+def test_host_argument_checks_need_no_gpu(L):
+    """Invalid calls are rejected by host-side checks, before any CUDA call,
+    with the documented status (AIRG_ERR_ARG = 1, AIRG_ERR_STATE = 7) and a
+    message; nothing here reaches the device, so it runs without a GPU."""
+    import ctypes
+    ARG, STATE = 1, 7
+    fake = ctypes.c_void_p(64)          # never dereferenced: every call fails first
+    i64 = ctypes.c_int64()
+
+    def err():
+        return L.airg_last_error().decode()
+
+    assert L.airg_options_default(None) == ARG and "null options" in err()
+    h = ctypes.c_void_p()
+    assert L.airg_setup(None, None, None, None) == ARG and "output handle" in err()
+    assert L.airg_setup(None, None, None, ctypes.byref(h)) == ARG and "null CSR" in err()
+    assert h.value is None
+    for field, value, msg in [("poly_order", 31, "poly_order"), ("coarse_poly_order", 0, "coarse_poly_order"),
+                              ("gmres_restart", 31, "gmres_restart"), ("precision", 9, "precision"),
+                              ("smooth_type", 5, "smooth_type"), ("ddc_fraction", 1.5, "DDC")]:
+        o = G.airg_options()
+        L.airg_options_default(ctypes.byref(o))
+        setattr(o, field, value)
+        csr = G.airg_csr(4, 4, 4, fake, fake, fake, 0)
+        assert L.airg_setup(ctypes.byref(csr), ctypes.byref(o), None, ctypes.byref(h)) == ARG, field
+        assert msg in err(), (field, err())
+    for n_rows, n_cols, nnz, msg in [(4, 5, 4, "square"), (0, 0, 0, "square"), (1 << 31, 1 << 31, 4, "2^31"),
+                                     (4, 4, -1, "2^31")]:
+        csr = G.airg_csr(n_rows, n_cols, nnz, fake, fake, fake, 0)
+        assert L.airg_setup(ctypes.byref(csr), None, None, ctypes.byref(h)) == ARG and msg in err()
+    assert L.airg_solve(None, 1, fake, fake, 1, 1e-10, 0.0, 10, None, None) == STATE
+    assert L.airg_solve_adjoint(None, 1, fake, fake, 1, 1e-10, 0.0, 10, None, None) == STATE
+    assert L.airg_setup_info(None, None) == ARG
+    assert L.airg_export_matrix(None, 0, 0, ctypes.byref(i64), ctypes.byref(i64), ctypes.byref(i64),
+                                None, None, None) == STATE
+    assert L.airg_export_vector(None, 0, 0, ctypes.byref(i64), None) == STATE
+    assert L.airg_profile(None, 1) == STATE
+    one = G.airg_csr(4, 4, 4, fake, fake, fake, 0)
+    assert L.airg_setup_batch(0, ctypes.byref(one), None, None, ctypes.byref(h)) == ARG
+    assert L.airg_setup_batch(1, None, None, None, ctypes.byref(h)) == ARG
+    assert L.airg_solve_batch(None, fake, fake, 1, 1e-10, 0.0, 10, None, None) == ARG
+    assert L.airg_batch_setup_info(None, 0, None) == ARG
+    assert L.airg_problem_advection2d(1, 8, 1.0, 0.0, 0.1, fake, fake, fake, fake, ctypes.byref(i64),
+                                      ctypes.byref(i64), None) == ARG
+    assert L.airg_problem_advection2d(8, 8, float("nan"), 0.0, 0.1, fake, fake, fake, fake,
+                                      ctypes.byref(i64), ctypes.byref(i64), None) == ARG
+    assert L.airg_assemble_rhs_advection2d(8, 8, 1.0, 0.0, 0.1, 0, fake, 8, fake, None, fake, None) == ARG
+    assert L.airg_rhs_adjoint_advection2d(8, 8, 1.0, 0.0, 0.1, 1, fake, -1, fake, fake, None, None) == ARG
+    assert L.airg_dot_exact_noalloc(-1, fake, fake, fake, None) == ARG
+    assert L.airg_dot_exact_noalloc(1 << 31, fake, fake, fake, None) == ARG and "2^31" in err()
+    assert L.airg_check_wait_timeout(0, None) == ARG
+    L.airg_free(None)
+    L.airg_batch_free(None)
