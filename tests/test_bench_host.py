@@ -46,3 +46,15 @@ def test_many_grid_aggregate_roofline():
     assert e["bound"] == "hbm" and e["unit"] == "GB/s"
     assert abs(e["achieved"] - 3000.0) < 1e-9
     assert abs(e["frac"] - 3000.0 / 6769.4) < 1e-12
+
+
+def test_cpu_baseline_sample_runs_at_least_min_seconds():
+    """The oracle baseline repeats whole solves until the sample reaches its
+    minimum duration, and reports DOFs per second over all of them."""
+    from synthetic import workload
+    w = workload("c1")
+    v, ts = bench.cpu_oracle_solve(w, 1, 0, min_seconds=0.05)
+    assert len(ts) >= 1 and sum(ts) >= 0.05
+    assert abs(v - w["nx"] * w["ny"] * len(ts) / sum(ts)) <= 1e-9 * v
+    v2, ts2 = bench.cpu_oracle_solve(w, 2, 0)
+    assert len(ts2) == 2
