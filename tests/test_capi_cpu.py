@@ -167,3 +167,36 @@ def test_host_argument_checks_need_no_gpu(L):
     assert L.airg_check_wait_timeout(0, None) == ARG
     L.airg_free(None)
     L.airg_batch_free(None)
+
+
+def test_header_is_plain_c_and_links_from_c(L, tmp_path):
+    """include/airg.h compiles as strict C99 and a C program links against
+    the library and calls it (defaults and a host-side argument check; no
+    GPU call)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not found")
+    src = tmp_path / "use_airg.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "airg.h"\n'
+        "int main(void) {\n"
+        "  airg_options o;\n"
+        "  airg_handle* h = 0;\n"
+        "  if (airg_options_default(&o) != AIRG_OK) return 1;\n"
+        "  o.poly_order = 99;\n"
+        "  if (airg_setup(0, &o, 0, &h) != AIRG_ERR_ARG || h) return 2;\n"
+        '  printf("%d %d %.2f %s\\n", o.ddc_its, o.coarse_poly_order, o.strong_threshold, airg_last_error());\n'
+        "  airg_free(h);\n"
+        "  return 0;\n"
+        "}\n")
+    libdir = os.path.dirname(G.LIB)
+    exe = tmp_path / "use_airg"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lairg",
+                        "-Wl,-rpath," + libdir, "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert r.stdout.split()[:3] == ["2", "100", "0.99"] and "poly_order" in r.stdout
