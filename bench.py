@@ -169,6 +169,27 @@ def cpu_oracle_solve(w, steps, warmup, min_seconds=0.0):
     return n * len(ts) / sum(ts), ts
 
 
+def cpu_sweep(w, repeats=5):
+    """Context for the CPU baseline: the exact solution by substitution in
+    upwind order (Sec. 1.1), the O(n) serial solver of this lower-triangular
+    system that the paper sets against multigrid because it does not
+    parallelise.  Oracle code, one core; best of `repeats`.  Returns (DOFs/s,
+    seconds)."""
+    from oracle import airg as O
+    from synthetic import velocity
+    vx, vy = velocity(w["theta"])
+    po = O.advection_2d(w["nx"], w["ny"], vx, vy)
+    s = w["s"][0] if w["s"] is not None else [0.0] * po.A.n_rows
+    bo = O.assemble_rhs(po, w["g"][0], s)
+    order = O.sweep_order(po)
+    best = math.inf
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        O.sweep_solve(po.A, bo, order)
+        best = min(best, time.perf_counter() - t0)
+    return po.A.n_rows / best, best
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -445,12 +466,15 @@ def run_gpu(args):
     if roofline["traffic"] is not None:
         roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold cache"
     vc_bytes = sinfo["bytes_per_vcycle"]
-    cpu = None
+    cpu, sweep = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("c1", "c2"):
         cv, ts = cpu_oracle_solve(w, 1, 0, min_seconds=10.0)
         cpu = {"value": cv, "unit": "DOF/s", "cores": 1, "kind": "oracle",
                "sample": "%d full oracle solves of the same workload (setup untimed), %.1f s in total"
                          % (len(ts), sum(ts))}
+        sv, sts = cpu_sweep(w)
+        sweep = {"value": sv, "unit": "DOF/s", "cores": 1, "seconds": sts,
+                 "kind": "exact substitution in upwind order (serial; context, not a baseline)"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world,
@@ -470,6 +494,8 @@ def run_gpu(args):
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": launches, "wall_s_timed": wall_s,
         }
+        if sweep is not None:
+            line["context_sweep"] = sweep
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -58,3 +58,12 @@ def test_cpu_baseline_sample_runs_at_least_min_seconds():
     assert abs(v - w["nx"] * w["ny"] * len(ts) / sum(ts)) <= 1e-9 * v
     v2, ts2 = bench.cpu_oracle_solve(w, 2, 0)
     assert len(ts2) == 2
+
+
+def test_sequential_sweep_context():
+    """The serial substitution timed beside the oracle baseline reports the
+    DOFs per second of its best run."""
+    from synthetic import workload
+    w = workload("c1")
+    v, t = bench.cpu_sweep(w, repeats=2)
+    assert t > 0 and abs(v - w["nx"] * w["ny"] / t) <= 1e-9 * v
