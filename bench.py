@@ -1,22 +1,28 @@
 #!/usr/bin/env python3
 """Benchmark of the AIRG solve phase: DOFs solved per second to rtol 1e-10.
 
-A step is one complete solve (FP64 FGMRES preconditioned by AIRG V-cycles,
-Sec. 2-3 of arXiv 2508.17517) of the 1024x1024 upwind advection workload
-(seeded direction and inflow, coarse polynomial order 30, truncation
-tolerance 1e-2) from x0 = 0, with the hierarchy set up once beforehand (the
-paper times the second solve).  `value` = DOFs solved per second over all
-ranks, timed on the device with CUDA events around each solve, L2 flushed
-between steps.  `e2e` repeats the solves through the C ABI with host
-buffers, copies included.  The roofline entry comes from a second pass of
-the same steps with per-kernel CUDA events (airg_profile).
+Default workload (`--workload c3`): the 4096x4096 upwind advection problem
+(seeded direction, inflow values U[0,1], coarse polynomial order 30,
+truncation tolerance 1e-2), 16.8M DOFs, the per-GPU size class of the paper's
+runs (Sec. 3).  A step is one complete solve (FP64 FGMRES preconditioned by
+AIRG V-cycles, Sec. 2-3 of arXiv 2508.17517) from x0 = 0 with the hierarchy
+set up once beforehand (the paper times the second solve).  `value` = DOFs
+solved per second with the FP64 V-cycle, timed on the device with CUDA
+events around each solve, L2 flushed between steps; `mixed` (FP32 V-cycle
+inside the FP64 outer iteration) and `mixed_bf16r` (the same with the
+restrictor stored in bfloat16) are timed the same way on the same right-hand
+side, with their error against the FP64 solution and the exact solution.
+`e2e` repeats the solves through the C ABI with host buffers, copies
+included.  The roofline entry times its kernel group alone with CUDA events
+(airg_profile_group) after a first pass has ranked the groups.
 
   python bench.py [--gpus N] [--steps K] [--warmup W]
-                  [--workload c1|c2|c3|c3_fp64|c3_bf16|c4a|c4a_fp64|c4a_bf16|c4b]
+                  [--workload c3|c1|c2|c3_fp64|c3_fp32|c3_bf16|c4a|c4a_fp64|c4a_bf16|c4b]
   python bench.py --impl reference ...   (the CPU oracle as the reference arm)
-  python bench.py --sweep coarse-order|smoother|cases   (one JSON line of study rows)
+  python bench.py --sweep coarse-order|smoother|cases|readings   (one JSON line of study rows)
 """
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -35,6 +41,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DOFs solved/s to rtol 1e-10 (mixed vs FP64 on GPU); V-cycle HBM GB/s vs peak"
 L2_FLUSH_BYTES = 256 << 20
+# bench workload name -> synthetic workload name (c3 is the paired FP64 / mixed run)
+SINGLE = {"c1": "c1", "c2": "c2", "c3_fp64": "c3_fp64", "c3_fp32": "c3", "c3_bf16": "c3_bf16",
+          "c4a": "c4a", "c4a_fp64": "c4a_fp64", "c4a_bf16": "c4a_bf16", "c4b": "c4b"}
+# side of the lower-left corner of the 4096^2 grid that the CPU oracle solves
+# as its bounded sample (upwind dependence makes the corner a closed problem)
+CORNER = 1024
 
 
 def parse(argv=None):
@@ -43,15 +55,15 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c2",
-                    choices=["c1", "c2", "c3", "c3_fp64", "c3_bf16", "c4a", "c4a_fp64", "c4a_bf16", "c4b"])
+    ap.add_argument("--workload", default="c3", choices=["c3"] + sorted(SINGLE))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sweep", choices=["coarse-order", "smoother", "cases"], default=None,
+    ap.add_argument("--sweep", choices=["coarse-order", "smoother", "cases", "readings"], default=None,
                     help="instead of the throughput line, one JSON line with a row per setting: "
                          "coarse-order = the coarse polynomial order / truncation study of Sec. 3.1; "
                          "smoother = matrix-free polynomial vs assembled Eq. 8 smoother (Sec. 2.2) and F vs FC/FCF "
                          "smoothing (Sec. 2); "
-                         "cases = hard direction (Sec. 3.3.2) and rectangular domain (Sec. 3.4)")
+                         "cases = hard direction (Sec. 3.3.2) and rectangular domain (Sec. 3.4); "
+                         "readings = R drop tolerance and DDC settings against levels and complexities")
     return ap.parse_args(argv)
 
 
@@ -146,34 +158,53 @@ def problem_and_rhs(w, G, torch):
     return prob, b
 
 
+def reference_sample(args):
+    """The workload the CPU oracle times, and what it is.  For the 4096^2
+    workloads the oracle's setup alone would take many minutes, so its sample
+    is the CORNER x CORNER lower-left corner of the same problem (a closed
+    sub-problem with the same direction, inflow values and options); other
+    workloads are sampled whole."""
+    from synthetic import corner, workload
+    name = "c3_fp64" if args.workload == "c3" else SINGLE[args.workload]
+    w = workload(name)
+    if w.get("n_rhs", 1) != 1 or "problems" in w:
+        return w, None
+    if w["nx"] * w["ny"] > CORNER * CORNER:
+        return corner(w, CORNER), "the %dx%d lower-left corner of the workload" % (CORNER, CORNER)
+    return w, "the workload"
+
+
 def cpu_oracle_solve(w, steps, warmup, min_seconds=0.0):
-    """Times the oracle's solve (after an untimed oracle setup) of the same
-    workload: `steps` solves, more while their total stays below
-    `min_seconds`; returns (DOFs/s, per-step seconds)."""
+    """Times the oracle's solve (after an untimed oracle setup) of workload
+    w: `steps` solves, more while their total stays below `min_seconds`;
+    returns (DOFs/s, per-step seconds, oracle iterations, setup seconds)."""
     from oracle import airg as O
     from synthetic import velocity
     vx, vy = velocity(w["theta"])
     po = O.advection_2d(w["nx"], w["ny"], vx, vy)
     opts = O.Options(**{k: v for k, v in w["opts"].items() if k != "precision"})
+    t0 = time.perf_counter()
     Ho = O.setup(po.A, opts)
+    setup_s = time.perf_counter() - t0
     s = w["s"][0] if w["s"] is not None else [0.0] * po.A.n_rows
     bo = O.assemble_rhs(po, w["g"][0], s)
     for _ in range(warmup):
         O.solve(Ho, po.A, bo, rtol=w["rtol"])
-    ts = []
+    ts, its = [], 0
     while len(ts) < steps or sum(ts) < min_seconds:
         t0 = time.perf_counter()
-        O.solve(Ho, po.A, bo, rtol=w["rtol"])
+        _, info = O.solve(Ho, po.A, bo, rtol=w["rtol"])
         ts.append(time.perf_counter() - t0)
+        its = info.iterations
     n = po.A.n_rows
-    return n * len(ts) / sum(ts), ts
+    return n * len(ts) / sum(ts), ts, its, setup_s
 
 
-def cpu_sweep(w, repeats=5):
-    """Context for the CPU baseline: the exact solution by substitution in
-    upwind order (Sec. 1.1), the O(n) serial solver of this lower-triangular
-    system that the paper sets against multigrid because it does not
-    parallelise.  Oracle code, one core; best of `repeats`.  Returns (DOFs/s,
+def cpu_exact(w, repeats=3):
+    """The exact discrete solution of workload w by substitution in upwind
+    order (Sec. 1.1), the O(n) serial solver of this lower-triangular system
+    that the paper sets against multigrid because it does not parallelise.
+    Oracle code, one core.  Returns (u*, DOFs/s of the best of `repeats`,
     seconds)."""
     from oracle import airg as O
     from synthetic import velocity
@@ -182,32 +213,49 @@ def cpu_sweep(w, repeats=5):
     s = w["s"][0] if w["s"] is not None else [0.0] * po.A.n_rows
     bo = O.assemble_rhs(po, w["g"][0], s)
     order = O.sweep_order(po)
-    best = math.inf
+    best, u = math.inf, None
     for _ in range(repeats):
         t0 = time.perf_counter()
-        O.sweep_solve(po.A, bo, order)
+        u = O.sweep_solve(po.A, bo, order)
         best = min(best, time.perf_counter() - t0)
-    return po.A.n_rows / best, best
+    return u, po.A.n_rows / best, best
+
+
+def cpu_baseline_entry(args, min_seconds=10.0):
+    """The oracle on its bounded sample: setup untimed, then at least
+    `min_seconds` of solves."""
+    ws, what = reference_sample(args)
+    if what is None:
+        return None
+    cv, ts, its, setup_s = cpu_oracle_solve(ws, 1, 0, min_seconds=min_seconds)
+    return {"value": cv, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": "%s (%d DOFs; oracle setup untimed, %.0f s): %d full solves to rtol %g, "
+                      "%d iterations each, %.1f s in total" % (what, ws["nx"] * ws["ny"], setup_s, len(ts),
+                                                               ws["rtol"], its, sum(ts))}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from synthetic import workload
-    w = workload(args.workload)
-    n = w["nx"] * w["ny"]
+    ws, what = reference_sample(args)
+    if what is None:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no solve of this batched workload"}))
+        return
     t0 = time.time()
-    value, ts = cpu_oracle_solve(w, args.steps, args.warmup)
+    value, ts, its, setup_s = cpu_oracle_solve(ws, args.steps, args.warmup)
+    from synthetic import workload
+    full = workload("c3_fp64" if args.workload == "c3" else SINGLE[args.workload])
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(ts) / len(ts), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w["desc"], "n": n, "nrhs": 1, "rtol": w["rtol"]},
+        "config": {"workload": full["desc"], "n": full["nx"] * full["ny"], "nrhs": 1, "rtol": full["rtol"]},
         "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d full oracle solves of the workload (single-threaded C "
-                                   "kernels + numpy, FP64), setup untimed" % args.steps},
+                         "sample": "each step one full oracle solve of %s (%d DOFs, %d iterations; "
+                                   "single-threaded C kernels + numpy, FP64), setup untimed (%.0f s)"
+                                   % (what, ws["nx"] * ws["ny"], its, setup_s)},
         "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.time() - t0,
     }
@@ -307,61 +355,153 @@ ALU_PEAK_TFLOPS = {"f64": 2 * 2 * SM_COUNT * SM_GHZ / 1e3, "f32": 2 * 128 * SM_C
 VCYCLE_KINDS = ("restrict", "f_residual", "f_smoother", "coarse_newton")
 
 
+def kernel_source_hash():
+    """Short hash of the solve kernels' source (the V-cycle and SpMV code):
+    a DRAM-traffic figure measured on other source no longer applies."""
+    h = hashlib.sha256()
+    for f in ("solve.cu", "solve_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2508_17517_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def measured_traffic(workload, kind, level):
     """DRAM bytes per launch of a (kind, level) group from the committed ncu
-    summary (profiles/coarse_newton_traffic.md), or None."""
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "coarse_newton_traffic.md")
+    summary (profiles/coarse_newton_traffic.md), taken on the current kernel
+    source; (bytes, source hash) or (None, reason)."""
+    path = os.path.join(ROOT, "profiles", "coarse_newton_traffic.md")
+    src = kernel_source_hash()
     if not os.path.exists(path):
-        return None
+        return None, "no ncu traffic summary"
     for line in open(path):
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) == 7 and cells[0] == workload and cells[1] == kind and cells[2] == str(level):
+        if len(cells) >= 7 and cells[0] == workload and cells[1] == kind and cells[2] == str(level):
+            if cells[3] != src:
+                return None, "ncu traffic was measured on kernel source %s, not the current %s" % (cells[3], src)
             try:
-                return float(cells[5])
+                return float(cells[6]), src
             except ValueError:
-                return None
-    return None
+                return None, "unreadable traffic entry"
+    return None, "no ncu traffic entry for this kernel group and workload"
 
 
-def roofline_entry(prof, per_level, peak, peak_kind, vcycle_dtype="f64"):
-    """Roofline of the dominant kernel: the (kernel kind, level) pair with
-    the largest share of the profiled device time.  Its arithmetic intensity
-    I (flops / algorithmic byte) decides the bound: HBM when peak_BW * I is
-    below the arithmetic peak of its precision, else the ALU (the FP64 rate
-    of this part is low enough to bind the FP64 dot products).  Also the
-    per-kind shares, the same figure over all levels of that kind, and the
-    largest (kind, level) entries."""
+def solve_timed(G, torch, h, b, x, rtol, flush, steps):
+    """`steps` solves from x0 = 0, L2 flushed before each; device time of
+    each solve by CUDA events on the launching stream.  Returns (total ms,
+    iterations per solve, kernel launches, last info)."""
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    total_ms, its, launches, info = 0.0, [], 0, None
+    for _ in range(steps):
+        flush.zero_()
+        x.zero_()
+        ev0.record(stream)
+        _, info = G.airg_solve(h, b, x, rtol=rtol)
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        its.append(info.iterations)
+        launches += info.kernel_launches
+        assert info.converged and info.rel_residual <= rtol, (info.converged, info.rel_residual)
+    return total_ms, its, launches, info
+
+
+def roofline_groups(G, torch, h, b, x, rtol, flush, levels):
+    """Pass 1: every solve kernel timed with its own event pair (one solve);
+    ranks the (kind, level) groups.  Per-kernel events inflate the small
+    kernels, so these shares only rank."""
+    G.airg_profile(h, True)
+    flush.zero_()
+    x.zero_()
+    G.airg_solve(h, b, x, rtol=rtol)
+    torch.cuda.synchronize()
+    prof = G.airg_profile_read(h)
+    per_level = G.airg_profile_read_level(h, levels)
+    G.airg_profile(h, False)
+    return prof, per_level
+
+
+def group_timed(G, torch, h, b, x, rtol, flush, steps, kind, level, levels):
+    """Pass 2: only the launches of one (kind, level) group are timed (one
+    event pair per V-cycle for a V-cycle group).  Returns the group's (ms,
+    launches, bytes, flops) over `steps` solves and the ms per solve of that
+    instrumented pass."""
+    G.airg_profile_group(h, kind, level)
+    tot, _, _, _ = solve_timed(G, torch, h, b, x, rtol, flush, steps)
+    per = G.airg_profile_read_level(h, levels).get((kind, level))
+    G.airg_profile(h, False)
+    return per, tot / steps
+
+
+def dominant_group(per_level):
+    """The (kind, level) group with the largest time of the ranking pass."""
+    return max(per_level.items(), key=lambda kv: kv[1][0])[0]
+
+
+def roofline_from(prof, per_level, group, steps, ms_per_step, inst_ms, peak, peak_kind, vcycle_dtype="f64"):
+    """Roofline entry of one kernel group (host logic).  prof / per_level:
+    the ranking pass (per kind; per (kind, level): ms, launches, bytes[,
+    flops]); group: (ms, launches, bytes, flops) of the dominant group timed
+    alone over `steps` solves; ms_per_step: the uninstrumented solve time;
+    inst_ms: the solve time of the pass that timed the group.  The group's
+    arithmetic intensity I (flops / algorithmic byte) decides the bound: HBM
+    when peak_BW * I is below the arithmetic peak of its precision, else the
+    ALU (the FP64 rate of this part is low enough to bind the FP64 dot
+    products).  `share` = the group's device time per solve over
+    ms_per_step."""
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
     tot = sum(v[0] for v in kinds.values())
-    (dk, dl), (ms, nl, nb, nf) = max(per_level.items(), key=lambda kv: kv[1][0])
+    dk, dl = dominant_group(per_level)
+    ms, nl, nb, nf = group
     dtype = vcycle_dtype if dk in VCYCLE_KINDS else "f64"
     gbs = nb / (ms / 1e3) / 1e9
     tflops = nf / (ms / 1e3) / 1e12
     fpeak = ALU_PEAK_TFLOPS[dtype]
     intensity = nf / nb if nb else 0.0
     alu_bound = peak * 1e9 * intensity > fpeak * 1e12
-    ak = kinds[dk]
     top = sorted(per_level.items(), key=lambda kv: -kv[1][0])[:8]
     entry = {"kernel": "%s (level %d)" % (dk, dl), "dtype": dtype,
              "launches": nl, "avg_launch_us": 1e3 * ms / nl, "algorithmic_bytes_per_launch": nb / nl,
-             "flops_per_launch": nf / nl, "share": ms / tot,
+             "flops_per_launch": nf / nl,
+             "share": (ms / steps) / ms_per_step,
+             "group_ms_per_step": ms / steps,
+             "timing": "group timed alone with CUDA events (one pair per V-cycle), %d solves; "
+                       "that pass ran at %.3f ms per solve against %.3f uninstrumented"
+                       % (steps, inst_ms, ms_per_step),
              "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak},
              "alu": {"achieved": tflops, "peak": fpeak, "unit": "TFLOP/s", "frac": tflops / fpeak,
                      "peak_source": "unit counts x nominal clock"},
-             "kind_all_levels": {"kernel": dk, "achieved": ak[2] / (ak[0] / 1e3) / 1e9,
-                                 "frac": ak[2] / (ak[0] / 1e3) / 1e9 / peak, "share": ak[0] / tot},
-             "kernel_share": {k: v[0] / tot for k, v in kinds.items()},
-             "top_launch_groups": [{"kernel": k, "level": l, "share": round(v[0] / tot, 4),
-                                    "gbs": round(v[2] / (v[0] / 1e3) / 1e9, 1),
-                                    "tflops": round(v[3] / (v[0] / 1e3) / 1e12, 3),
-                                    "avg_us": round(1e3 * v[0] / v[1], 2)} for (k, l), v in top]}
+             "ranking_pass": {
+                 "note": "one solve with an event pair around every kernel (inflates small kernels)",
+                 "kernel_share": {k: round(v[0] / tot, 4) for k, v in kinds.items()},
+                 "top_launch_groups": [{"kernel": k, "level": l, "share": round(v[0] / tot, 4),
+                                        "gbs": round(v[2] / (v[0] / 1e3) / 1e9, 1),
+                                        "avg_us": round(1e3 * v[0] / v[1], 2)} for (k, l), v in top]}}
     if alu_bound:
         entry.update({"bound": "alu", "achieved": tflops, "peak": fpeak, "unit": "TFLOP/s",
                       "frac": tflops / fpeak, "peak_source": "unit counts x nominal clock"})
     else:
         entry.update({"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                       "peak_source": peak_kind})
-    entry["traffic"] = None
+    return entry
+
+
+def roofline_entry(G, torch, h, b, x, rtol, flush, steps, levels, ms_per_step, peak, peak_kind,
+                   vcycle_dtype="f64", workload_key=None):
+    """Roofline of the dominant kernel group of a solve: ranked by one
+    per-kernel-event solve, then timed alone over `steps` solves."""
+    prof, per_level = roofline_groups(G, torch, h, b, x, rtol, flush, levels)
+    dk, dl = dominant_group(per_level)
+    group, inst_ms = group_timed(G, torch, h, b, x, rtol, flush, steps, dk, dl, levels)
+    entry = roofline_from(prof, per_level, group, steps, ms_per_step, inst_ms, peak, peak_kind, vcycle_dtype)
+    traffic, src = measured_traffic(workload_key, dk, dl) if workload_key else (None, "not captured")
+    entry["traffic"] = traffic
+    if traffic is not None:
+        entry["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "
+                                   "(kernel source %s)" % src)
+    else:
+        entry["traffic_source"] = src
     return entry
 
 
@@ -378,18 +518,65 @@ def multi_roofline(vcycle_bytes, total_ms, peak, peak_kind):
             "algorithmic_bytes": vcycle_bytes, "traffic": None}
 
 
-def run_gpu(args):
-    import torch
+def _dist_setup(torch):
     rank, world, local_rank = dist_env()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    return rank, world, local_rank, dev
+
+
+def _barrier(world, torch):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def _dist_end(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e_timed(G, torch, h, b, rtol, flush, steps):
+    """Seconds of `steps` solves through the C ABI with pinned host buffers:
+    the copies of b and x in and of x out are inside the call."""
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    G.airg_solve(h, bh, xh, rtol=rtol)     # warm-up of the host path (staging buffers)
+    torch.cuda.synchronize()
+    e2e_s = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        xh.zero_()
+        t0 = time.perf_counter()
+        G.airg_solve(h, bh, xh, rtol=rtol)
+        e2e_s += time.perf_counter() - t0
+    return e2e_s
+
+
+def hierarchy_entry(sinfo):
+    return {"levels": sinfo["levels"], "coarse_rows": sinfo["n"][-1],
+            "cycle_complexity": sinfo["cycle_complexity"], "storage_complexity": sinfo["storage_complexity"],
+            "vcycle_algorithmic_bytes": sinfo["bytes_per_vcycle"],
+            "setup_ms": sinfo["setup_ms"],
+            "setup_breakdown_ms": {k: round(v, 2) for k, v in sinfo["setup_breakdown_ms"].items()},
+            "setup_exact_dots": sinfo["exact_dots"]}
+
+
+def run_gpu(args):
+    """One single-problem workload (c1, c2, c3_fp64, c3_fp32, c3_bf16, c4a...)."""
+    import torch
+    rank, world, local_rank, dev = _dist_setup(torch)
     import paper_2508_17517_gb300 as G
     from synthetic import workload
     G.lib()
-    w = workload(args.workload)
+    w = workload(SINGLE[args.workload])
     k = w["n_rhs"]
     n = w["nx"] * w["ny"]
     prob, b = problem_and_rhs(w, G, torch)
@@ -397,84 +584,30 @@ def run_gpu(args):
     h = G.airg_setup(prob["rowptr"], prob["col"], prob["val"], opts)
     sinfo = G.airg_setup_info(h)
     x = torch.zeros_like(b)
-    stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
     for _ in range(args.warmup):
         x.zero_()
         G.airg_solve(h, b, x, rtol=w["rtol"])
-    # ---- timed region: device time of each solve (CUDA events on the solve stream)
     clk = Clocks(local_rank)
-    barrier()
+    _barrier(world, torch)
     clk.start()
-    total_ms, its, launches = 0.0, [], 0
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     t_wall0 = time.perf_counter()
-    for _ in range(args.steps):
-        flush.zero_()
-        x.zero_()
-        ev0.record(stream)
-        _, info = G.airg_solve(h, b, x, rtol=w["rtol"])
-        ev1.record(stream)
-        ev1.synchronize()
-        total_ms += ev0.elapsed_time(ev1)
-        its.append(info.iterations)
-        launches += info.kernel_launches
-        assert info.converged and info.rel_residual <= w["rtol"]
-    barrier()
+    total_ms, its, launches, _ = solve_timed(G, torch, h, b, x, w["rtol"], flush, args.steps)
+    _barrier(world, torch)
     wall_s = time.perf_counter() - t_wall0
     clocks = clk.stop()
     t_max = max_over_ranks(total_ms, world, dev)
     value = world * n * k * args.steps / (t_max / 1e3)
-    # ---- end-to-end through the C ABI with host buffers (copies in the call)
-    bh = b.cpu().pin_memory()
-    xh = torch.zeros_like(bh).pin_memory()
-    G.airg_solve(h, bh, xh, rtol=w["rtol"])     # warm-up of the host path (staging buffers)
-    barrier()
-    e2e_s = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        xh.zero_()
-        t0 = time.perf_counter()
-        G.airg_solve(h, bh, xh, rtol=w["rtol"])
-        e2e_s += time.perf_counter() - t0
-    e2e_max = max_over_ranks(e2e_s, world, dev)
+    e2e_max = max_over_ranks(e2e_timed(G, torch, h, b, w["rtol"], flush, args.steps), world, dev)
     e2e = {"value": world * n * k * args.steps / e2e_max, "unit": "DOF/s",
            "h2d_bytes_per_step": 2 * 8 * n * k, "d2h_bytes_per_step": 8 * n * k}
-    # ---- per-kernel event timing over a second pass of the same steps
-    G.airg_profile(h, True)
-    for _ in range(args.steps):
-        flush.zero_()
-        x.zero_()
-        G.airg_solve(h, b, x, rtol=w["rtol"])
-    prof = G.airg_profile_read(h)
-    per_level = G.airg_profile_read_level(h, sinfo["levels"])
-    G.airg_profile(h, False)
     peak, peak_kind = measured_peaks()
-    roofline = roofline_entry(prof, per_level, peak, peak_kind,
-                              "f32" if w["opts"].get("precision", 0) in (1, 2) else "f64")
-    dk, dl = roofline["kernel"].split(" (level ")
-    roofline["traffic"] = measured_traffic(args.workload, dk, int(dl.rstrip(")")))
-    if roofline["traffic"] is not None:
-        roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold cache"
-    vc_bytes = sinfo["bytes_per_vcycle"]
-    cpu, sweep = None, None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("c1", "c2"):
-        cv, ts = cpu_oracle_solve(w, 1, 0, min_seconds=10.0)
-        cpu = {"value": cv, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-               "sample": "%d full oracle solves of the same workload (setup untimed), %.1f s in total"
-                         % (len(ts), sum(ts))}
-        sv, sts = cpu_sweep(w)
-        sweep = {"value": sv, "unit": "DOF/s", "cores": 1, "seconds": sts,
-                 "kind": "exact substitution in upwind order (serial; context, not a baseline)"}
+    vdt = "f32" if w["opts"].get("precision", 0) in (1, 2) else "f64"
+    roofline = roofline_entry(G, torch, h, b, x, w["rtol"], flush, args.steps, sinfo["levels"],
+                              t_max / args.steps, peak, peak_kind, vdt, args.workload)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_entry(args)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world,
@@ -483,24 +616,118 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": {0: "f64", 1: "f32/f64", 2: "bf16/f32/f64"}[w["opts"].get("precision", 0)],
             "data": "synthetic",
             "config": {"workload": w["desc"], "n": n, "nrhs": k, "rtol": w["rtol"],
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "levels": sinfo["levels"], "iterations_per_solve": statistics.median(its),
-                       # DOFs x V-cycles per second, the paper's per-V-cycle rate (Sec. 3.2)
-                       "dofs_per_s_per_vcycle": value * statistics.median(its),
-                       "setup_ms": sinfo["setup_ms"], "cycle_complexity": sinfo["cycle_complexity"],
-                       "storage_complexity": sinfo["storage_complexity"],
-                       "vcycle_algorithmic_bytes": vc_bytes,
                        "l2": "flushed (256 MiB write) between timed steps"},
+            "parallelism": "replicas" if world > 1 else "single",
+            "iterations_per_solve": statistics.median(its),
+            # DOFs x V-cycles per second, the paper's per-V-cycle rate (Sec. 3.2)
+            "dofs_per_s_per_vcycle": value * statistics.median(its),
+            "hierarchy": hierarchy_entry(sinfo),
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": launches, "wall_s_timed": wall_s,
         }
-        if sweep is not None:
-            line["context_sweep"] = sweep
         print(json.dumps(line))
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.destroy_process_group()
+    _dist_end(world)
+
+
+def rel_err(a, b):
+    import torch
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def run_gpu_pair(args):
+    """The metric's own comparison on the 4096^2 workload: the FP64 V-cycle
+    solve (`value`) against the FP32 V-cycle (`mixed`) and FP32 with a
+    bfloat16 restrictor (`mixed_bf16r`), all inside the FP64 outer
+    iteration, on the same operator and right-hand side, each to rtol 1e-10
+    in the true FP64 residual."""
+    import torch
+    rank, world, local_rank, dev = _dist_setup(torch)
+    import paper_2508_17517_gb300 as G
+    from synthetic import workload
+    G.lib()
+    arms = [("value", workload("c3_fp64")), ("mixed", workload("c3")), ("mixed_bf16r", workload("c3_bf16"))]
+    w = arms[0][1]
+    n = w["nx"] * w["ny"]
+    rtol = w["rtol"]
+    prob, b = problem_and_rhs(w, G, torch)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    peak, peak_kind = measured_peaks()
+    res = {}
+    clk = Clocks(local_rank)
+    clk_started = False
+    for key, wa in arms:
+        h = G.airg_setup(prob["rowptr"], prob["col"], prob["val"], G.airg_options_default(**wa["opts"]))
+        sinfo = G.airg_setup_info(h)
+        x = torch.zeros_like(b)
+        for _ in range(args.warmup):
+            x.zero_()
+            G.airg_solve(h, b, x, rtol=rtol)
+        _barrier(world, torch)
+        if not clk_started:
+            clk.start()
+            clk_started = True
+        t_wall0 = time.perf_counter()
+        total_ms, its, launches, info = solve_timed(G, torch, h, b, x, rtol, flush, args.steps)
+        _barrier(world, torch)
+        wall_s = time.perf_counter() - t_wall0
+        t_max = max_over_ranks(total_ms, world, dev)
+        e2e_max = max_over_ranks(e2e_timed(G, torch, h, b, rtol, flush, args.steps), world, dev)
+        vdt = "f32" if wa["opts"].get("precision", 0) in (1, 2) else "f64"
+        roof = roofline_entry(G, torch, h, b, x, rtol, flush, args.steps, sinfo["levels"], t_max / args.steps,
+                              peak, peak_kind, vdt, {"value": "c3_fp64", "mixed": "c3_fp32",
+                                                     "mixed_bf16r": "c3_bf16"}[key])
+        x.zero_()
+        _, info = G.airg_solve(h, b, x, rtol=rtol)
+        res[key] = dict(value=world * n * args.steps / (t_max / 1e3), ms=t_max / args.steps,
+                        its=statistics.median(its), launches=launches, wall_s=wall_s, x=x.clone(),
+                        rel_residual=info.rel_residual, hier=hierarchy_entry(sinfo), roofline=roof,
+                        e2e=world * n * args.steps / e2e_max)
+        G.airg_free(h)
+        del x
+        torch.cuda.empty_cache()
+    clocks = clk.stop()
+    x64 = res["value"]["x"]
+    cpu, exact = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_entry(args)
+        u, sv, sts = cpu_exact(w, repeats=1)
+        ut = torch.tensor(u, device=dev)
+        exact = {k: rel_err(r["x"], ut) for k, r in res.items()}
+        exact["sweep"] = {"value": sv, "unit": "DOF/s", "cores": 1, "seconds": sts,
+                          "kind": "exact substitution in upwind order (serial; context, not a baseline)"}
+    if rank == 0:
+        v = res["value"]
+
+        def arm(key):
+            r = res[key]
+            return {"value": r["value"], "unit": "DOF/s", "dtype": {"mixed": "f32/f64", "mixed_bf16r": "bf16/f32/f64"}[key],
+                    "ms_per_step": r["ms"], "iterations_per_solve": r["its"],
+                    "speedup_vs_fp64": r["value"] / v["value"],
+                    "rel_residual": r["rel_residual"],
+                    "rel_err_vs_fp64_solution": rel_err(r["x"], x64),
+                    "rel_err_vs_exact": exact[key] if exact else None,
+                    "e2e": {"value": r["e2e"], "unit": "DOF/s"},
+                    "gpu_launches": r["launches"], "hierarchy": r["hier"], "roofline": r["roofline"]}
+        line = {
+            "metric": METRIC, "value": v["value"], "unit": "DOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["desc"], "n": n, "nrhs": 1, "rtol": rtol,
+                       "l2": "flushed (256 MiB write) between timed steps"},
+            "parallelism": "replicas" if world > 1 else "single",
+            "iterations_per_solve": v["its"], "dofs_per_s_per_vcycle": v["value"] * v["its"],
+            "rel_residual": v["rel_residual"],
+            "rel_err_vs_exact": exact["value"] if exact else None,
+            "hierarchy": v["hier"],
+            "e2e": {"value": v["e2e"], "unit": "DOF/s", "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n},
+            "roofline": v["roofline"],
+            "mixed": arm("mixed"), "mixed_bf16r": arm("mixed_bf16r"),
+            "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": v["launches"], "wall_s_timed": v["wall_s"],
+        }
+        if exact:
+            line["context_sweep"] = exact["sweep"]
+        print(json.dumps(line))
+    _dist_end(world)
 
 
 def _sweep_row(G, torch, prob, b, opts, args):
@@ -613,6 +840,8 @@ def main(argv=None):
         run_reference(args)
     elif args.workload == "c4b":
         run_gpu_multi(args)
+    elif args.workload == "c3":
+        run_gpu_pair(args)
     else:
         run_gpu(args)
 

@@ -126,6 +126,23 @@ typedef struct {
     int64_t kernel_launches;   /* CUDA kernels this call launched             */
 } airg_solve_info;
 
+/* Phases of airg_setup timed in airg_hierarchy_info.setup_phase_ms (the
+ * setup breakdown of Sec. 3.1), summed over levels: the truncation test
+ * (coarse polynomial and its residual on levels that were not truncated,
+ * Sec. 2.4); CF splitting (strength, PMISR, DDC, Sec. 2.1); extraction of
+ * the blocks of Eq. 3; the smoother's GMRES polynomial coefficients
+ * (Arnoldi, Eq. 7); the fixed-sparsity inverse (Eq. 8); the restrictor
+ * Z = -A_cf Ahat^-1 and its drop; the one-point prolongator and the P/R
+ * assembly; the RAP sparse products; the drop and lumping of A_coarse; the
+ * coarse-grid Newton polynomial (Sec. 2.3); the solve layout (SELL
+ * conversion, row-kernel tuning and buffers). */
+enum {
+    AIRG_PHASE_TRUNCATION = 0, AIRG_PHASE_CF_SPLIT = 1, AIRG_PHASE_EXTRACT = 2,
+    AIRG_PHASE_SMOOTHER_POLY = 3, AIRG_PHASE_FIXED_SPARSITY = 4, AIRG_PHASE_RESTRICTOR = 5,
+    AIRG_PHASE_PROLONGATOR = 6, AIRG_PHASE_RAP = 7, AIRG_PHASE_DROP_LUMP = 8,
+    AIRG_PHASE_COARSE_POLY = 9, AIRG_PHASE_SOLVE_LAYOUT = 10, AIRG_SETUP_PHASES = 11
+};
+
 typedef struct {
     int levels;                /* number of levels, coarsest included         */
     int truncated;             /* 1 if the hierarchy was truncated (Sec. 2.4) */
@@ -138,6 +155,9 @@ typedef struct {
     int64_t n_f[64];           /* F points per level (0 on the coarsest)      */
     int64_t nnz_a[64];         /* nnz of the level operator A_l               */
     int64_t bytes_per_vcycle;  /* algorithmic bytes of one V-cycle            */
+    double setup_phase_ms[16]; /* wall time of each AIRG_PHASE_* (stream
+                                  synchronised at every phase boundary)      */
+    int64_t exact_dots;        /* correctly rounded dot products the setup ran */
 } airg_hierarchy_info;
 
 /* Fills `opt` with the defaults above.  AIRG_ERR_ARG if opt is NULL. */
@@ -301,6 +321,17 @@ airg_status airg_export_vector(const airg_handle* h, int level, int what, int64_
  * conversions.  Outputs are HOST pointers.
  */
 airg_status airg_profile(airg_handle* h, int enable);
+/*
+ * Like airg_profile(h, 1), but times only the launches of one kernel kind on
+ * one level (the group that dominates the solve, say), so that the timed
+ * solve carries as few event records as possible: consecutive launches of
+ * the group inside one V-cycle (a kind 0-3 group: the restriction, F-point
+ * residual, smoother or coarse Newton steps of a level) share one event
+ * pair, while groups of kinds 4-6 get one pair per launch.  The totals are
+ * read with airg_profile_read_level; airg_profile(h, 0) stops.  AIRG_ERR_ARG
+ * for a kind outside 0..6 or a level outside 0..64.
+ */
+airg_status airg_profile_group(airg_handle* h, int kind, int level);
 airg_status airg_profile_read(const airg_handle* h, int kind, double* ms, int64_t* launches,
                               int64_t* bytes);
 
@@ -336,7 +367,8 @@ const char* airg_last_error(void);
  * Building blocks exposed for testing (same contracts as their use inside
  * the setup):
  *  airg_dot_exact: <x, y> correctly rounded from the exact sum of exact
- *    products; x, y DEVICE (length n), result to *out (HOST).
+ *    products; x, y DEVICE (length n), result to *out (HOST).  n must be
+ *    <= 2^31 - 1 (the accumulator's carry headroom); AIRG_ERR_ARG beyond.
  *  airg_rng_uniform: uniform [0,1) counter stream (SplitMix64, Steele, Lea &
  *    Flood 2014) of (seed, level, purpose) into out (DEVICE, length n).
  *  airg_host_gmres_coeffs: power-basis coefficients alpha (length k, HOST) of
@@ -369,6 +401,10 @@ airg_status airg_host_eigvals(int n, const double* H, double* wr, double* wi);
  *    AIRG_ERR_ARG beyond that, before any GPU work.
  *  - The first call on a device looks up the scratch array's device address
  *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    The address is kept per device ordinal for the life of the process: it
+ *    does not survive cudaDeviceReset or a switch to another context on the
+ *    same device: after either, this entry point must not be called again
+ *    in the process.
  *  - All calls on a device share the scratch: each call clears it first, and
  *    calls that overlap on the GPU (different streams, no ordering) race.
  */

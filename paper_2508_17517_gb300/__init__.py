@@ -38,9 +38,12 @@ EXPORTS = ["airg_options_default", "airg_problem_advection2d", "airg_assemble_rh
            "airg_dot_exact", "airg_rng_uniform", "airg_host_gmres_coeffs", "airg_host_eigvals",
            "airg_profile", "airg_profile_read", "airg_profile_read_level", "airg_dot_exact_noalloc",
            "airg_rhs_adjoint_advection2d", "airg_setup_batch", "airg_solve_batch",
-           "airg_batch_free", "airg_batch_setup_info", "airg_check_wait_timeout"]
+           "airg_batch_free", "airg_batch_setup_info", "airg_check_wait_timeout", "airg_profile_group"]
 PROFILE_KINDS = ["restrict", "f_residual", "f_smoother", "coarse_newton", "top_spmv",
                  "krylov_vectors", "layout"]
+# airg_hierarchy_info.setup_phase_ms entries (AIRG_PHASE_* of the header)
+SETUP_PHASES = ["truncation_test", "cf_split", "extract", "smoother_poly", "fixed_sparsity_inverse",
+                "restrictor", "prolongator", "rap", "drop_lump", "coarse_poly", "solve_layout"]
 
 
 class airg_options(ctypes.Structure):
@@ -75,7 +78,8 @@ class airg_hierarchy_info(ctypes.Structure):
                 ("cycle_complexity", ctypes.c_double),
                 ("storage_complexity", ctypes.c_double), ("setup_ms", ctypes.c_double),
                 ("n", ctypes.c_int64 * 64), ("n_f", ctypes.c_int64 * 64),
-                ("nnz_a", ctypes.c_int64 * 64), ("bytes_per_vcycle", ctypes.c_int64)]
+                ("nnz_a", ctypes.c_int64 * 64), ("bytes_per_vcycle", ctypes.c_int64),
+                ("setup_phase_ms", ctypes.c_double * 16), ("exact_dots", ctypes.c_int64)]
 
 
 class AirgError(RuntimeError):
@@ -116,6 +120,7 @@ def lib():
             "airg_host_gmres_coeffs": [ci, vp, f64, vp],
             "airg_host_eigvals": [ci, vp, vp, vp],
             "airg_profile": [vp, ci],
+            "airg_profile_group": [vp, ci, ci],
             "airg_dot_exact_noalloc": [i64, vp, vp, vp, vp],
             "airg_rhs_adjoint_advection2d": [i64, i64, f64, f64, f64, ci, vp, i64, vp, vp, vp, vp],
             "airg_check_wait_timeout": [i64, vp],
@@ -330,7 +335,9 @@ def _info_dict(info):
             "cycle_complexity": info.cycle_complexity,
             "storage_complexity": info.storage_complexity, "setup_ms": info.setup_ms,
             "n": list(info.n[:L]), "n_f": list(info.n_f[:L]), "nnz_a": list(info.nnz_a[:L]),
-            "bytes_per_vcycle": info.bytes_per_vcycle}
+            "bytes_per_vcycle": info.bytes_per_vcycle,
+            "setup_breakdown_ms": {k: info.setup_phase_ms[i] for i, k in enumerate(SETUP_PHASES)},
+            "exact_dots": info.exact_dots}
 
 
 def airg_export_matrix(handle, level, what):
@@ -375,6 +382,13 @@ def airg_profile(handle, enable):
     _check(lib().airg_profile(handle.ptr, int(enable)))
 
 
+def airg_profile_group(handle, kind, level):
+    """Time only the launches of one (kernel kind, level) group; kind is a
+    name of PROFILE_KINDS or its index."""
+    k = PROFILE_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    _check(lib().airg_profile_group(handle.ptr, k, int(level)))
+
+
 def airg_profile_read(handle):
     """{kind: (ms, launches, algorithmic bytes)} for every kernel kind."""
     out = {}
@@ -400,16 +414,37 @@ def airg_profile_read_level(handle, levels):
     return out
 
 
+def _dev_f64(t, name):
+    """Rejects anything but a contiguous float64 CUDA tensor (the C entry
+    points read raw device addresses and cannot check them)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda \
+            or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+
+
+def _dot_operands(x, y):
+    _dev_f64(x, "x")
+    _dev_f64(y, "y")
+    if x.numel() != y.numel():
+        raise ValueError("x and y differ in length (%d, %d)" % (x.numel(), y.numel()))
+    return x.numel()
+
+
 def airg_dot_exact(x, y, stream=None):
+    n = _dot_operands(x, y)
     out = ctypes.c_double()
-    _check(lib().airg_dot_exact(x.numel(), _ptr(x), _ptr(y), ctypes.byref(out), _stream(stream)))
+    _check(lib().airg_dot_exact(n, _ptr(x), _ptr(y), ctypes.byref(out), _stream(stream)))
     return out.value
 
 
-def airg_dot_exact_noalloc(x, y, out, stream=None, n=None):
+def airg_dot_exact_noalloc(x, y, out, stream=None):
     """Correctly rounded <x, y> into the device tensor `out` (one double),
     without any device allocation; asynchronous on the stream."""
-    n = x.numel() if n is None else n
+    n = _dot_operands(x, y)
+    _dev_f64(out, "out")
+    if out.numel() < 1:
+        raise ValueError("out must hold one element")
     _check(lib().airg_dot_exact_noalloc(n, _ptr(x), _ptr(y), _ptr(out), _stream(stream)))
 
 

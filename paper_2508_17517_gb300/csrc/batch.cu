@@ -766,6 +766,7 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
             if (S.smooth_type == AIRG_SMOOTH_FCF) bf_smooth_again<T>(S, l, k, v, e, wk, st);
         }
     }
+    S.close_run(st);
     S.cur_level = 0;
     CK_LAUNCH();
 }

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "dev_util.cuh"
+#include "exact_dot_limits.h"
 #include "handle.h"
 
 struct airg_handle_s {
@@ -458,6 +459,15 @@ airg_status airg_profile(airg_handle* h, int enable)
     });
 }
 
+airg_status airg_profile_group(airg_handle* h, int kind, int level)
+{
+    return guarded([&] {
+        if (!h || !h->H || !h->H->solve) airg::fail(AIRG_ERR_STATE, "handle not set up");
+        if (kind < 0 || kind > 6 || level < 0 || level > 64) airg::fail(AIRG_ERR_ARG, "bad kernel kind or level");
+        airg::set_profiling(*h->H, true, kind, level);
+    });
+}
+
 airg_status airg_profile_read(const airg_handle* h, int kind, double* ms, int64_t* launches,
                               int64_t* bytes)
 {
@@ -509,6 +519,7 @@ airg_status airg_dot_exact(int64_t n, const double* x, const double* y, double* 
 {
     return guarded([&] {
         if (n < 0 || !out || (n && (!x || !y))) airg::fail(AIRG_ERR_ARG, "bad dot arguments");
+        if (n > airg::XD_MAX_N) airg::fail(AIRG_ERR_ARG, "airg_dot_exact: n exceeds 2^31 - 1 (accumulator limit)");
         cudaStream_t st = (cudaStream_t)stream;
         airg::DBuf<double> r(1);
         airg::dot_exact_device(n, x, y, r.p, nullptr, st);

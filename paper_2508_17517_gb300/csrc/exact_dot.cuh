@@ -24,6 +24,8 @@
 
 #include <cstdint>
 
+#include "exact_dot_limits.h"
+
 namespace airg {
 
 constexpr int XD_DIGITS = 140;   // 140 * 32 = 4480 bits >= 2148 + 2046 + 2

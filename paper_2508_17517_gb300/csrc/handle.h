@@ -53,6 +53,8 @@ struct Hierarchy {
     std::vector<std::unique_ptr<SetupLevel>> levels;
     CoarseLevel coarse;
     double setup_ms = 0.0;
+    double phase_ms[AIRG_SETUP_PHASES] = {};   // setup breakdown (AIRG_PHASE_*)
+    long long exact_dots = 0;                  // correctly rounded dots of the setup
     std::unique_ptr<SolveData> solve;
     Hierarchy();
     ~Hierarchy();
@@ -73,7 +75,10 @@ void build_solve_data(Hierarchy& H, cudaStream_t st);
 void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_device,
                   double rtol, double atol, int maxit, airg_solve_info* info, cudaStream_t st);
 void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info);
-void set_profiling(Hierarchy& H, bool on);
+// on: time the solve kernels; kind >= 0 restricts the timing to the
+// launches of that kind on `level` (consecutive V-cycle launches of the
+// group share one event pair)
+void set_profiling(Hierarchy& H, bool on, int kind = -1, int level = -1);
 bool barrier_timeout_check(long long limit, cudaStream_t st);
 bool read_profile(const Hierarchy& H, int kind, int level, double* ms, long long* launches, long long* bytes,
                   long long* flops);

@@ -27,10 +27,6 @@ namespace {
 constexpr int kScratchWords = airg::XD_DIGITS + 1;
 static __device__ __align__(256) unsigned long long g_dot_scratch[kScratchWords];
 
-// Largest n: each 64-bit digit receives at most one 32-bit piece per
-// product, so n < 2^31 products cannot overflow a digit.
-constexpr long long kMaxN = (1LL << 31) - 1;
-
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned long long* g_scratch_ptr[kMaxDevices] = {};
@@ -74,7 +70,7 @@ airg_status airg_dot_exact_noalloc(int64_t n, const double* x, const double* y, 
 {
     if (n < 0 || !out || (n > 0 && (!x || !y)))
         return set_err(AIRG_ERR_ARG, "airg_dot_exact_noalloc: bad arguments", cudaSuccess);
-    if (n > kMaxN)
+    if (n > airg::XD_MAX_N)
         return set_err(AIRG_ERR_ARG, "airg_dot_exact_noalloc: n exceeds 2^31 - 1 (accumulator limit)",
                        cudaSuccess);
     unsigned long long* scratch = nullptr;

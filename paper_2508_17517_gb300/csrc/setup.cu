@@ -806,6 +806,7 @@ struct Ctx {
     DBuf<unsigned long long> xacc;   // exact-dot accumulator
     DBuf<int> xbad;
     DBuf<unsigned> xticket;          // last-block ticket of k_xdot
+    long long ndots = 0;             // exact dot products launched
     explicit Ctx(cudaStream_t s) : st(s)
     {
         xacc.alloc(XD_DIGITS);
@@ -834,7 +835,27 @@ void xdot(Ctx& c, long long n, const double* x, const double* y, double* out, do
                                         2LL * num_sms());
     k_xdot<<<grid, XD_THREADS, 0, c.st>>>(n, x, y, c.xacc.p, c.xbad.p, c.xticket.p, out, out_sqrt);
     CK_LAUNCH();
+    ++c.ndots;
 }
+
+// Wall time of one setup phase, added to *acc: the stream is synchronised
+// when the phase starts and when it ends, so the time covers the phase's
+// kernels and its host work and nothing else.
+struct PhaseTimer {
+    cudaStream_t st;
+    double* acc;
+    std::chrono::steady_clock::time_point t0;
+    PhaseTimer(cudaStream_t s, double* a) : st(s), acc(a)
+    {
+        CK(cudaStreamSynchronize(st));
+        t0 = std::chrono::steady_clock::now();
+    }
+    ~PhaseTimer()
+    {
+        cudaStreamSynchronize(st);   // errors surface at the next checked call
+        *acc += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
 
 // Builds CSR from per-row counts already in rp[0..n-1]; returns nnz.
 int counts_to_rowptr(DBuf<int>& rp, int n, cudaStream_t st) { return exclusive_scan(rp.p, rp.p, n, st); }
@@ -1367,11 +1388,19 @@ std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, c
         bool last = level >= o.max_levels - 1 || n <= o.coarse_min_rows;
         int m_c = std::min(o.coarse_poly_order, n);
         double trunc_rel = NAN;
+        const double trunc_before = H->phase_ms[AIRG_PHASE_TRUNCATION];
         if (!last && o.trunc_rtol > 0.0 && level >= o.trunc_start_level) {
             int k = 0;
-            std::vector<Root> roots = coarse_polynomial(c, A, o, level, m_c, k);
-            trunc_rel = truncation_residual(c, A, roots, o, level);
+            std::vector<Root> roots;
+            {
+                PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_TRUNCATION]);
+                roots = coarse_polynomial(c, A, o, level, m_c, k);
+                trunc_rel = truncation_residual(c, A, roots, o, level);
+            }
             if (trunc_rel <= o.trunc_rtol) {
+                // the test's polynomial becomes the coarse solver
+                H->phase_ms[AIRG_PHASE_COARSE_POLY] += H->phase_ms[AIRG_PHASE_TRUNCATION] - trunc_before;
+                H->phase_ms[AIRG_PHASE_TRUNCATION] = trunc_before;
                 H->coarse.A = std::move(A);
                 H->coarse.roots = std::move(roots);
                 H->coarse.k = k;
@@ -1384,12 +1413,14 @@ std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, c
         L->n = n;
         L->A = std::move(A);
         if (!last) {
+            PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_CF_SPLIT]);
             cf_split(c, *L, o, level);
             L->n_f = local_index(L->is_f, n, 1, L->f_index, L->f_ids, st);
             L->n_c = n - L->n_f;
             if (L->n_f == 0 || L->n_f == n) last = true;
         }
         if (last) {
+            PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_COARSE_POLY]);
             int k = 0;
             H->coarse.roots = coarse_polynomial(c, L->A, o, level, m_c, k);
             H->coarse.k = k;
@@ -1398,32 +1429,52 @@ std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, c
             break;
         }
         L->trunc_rel = trunc_rel;
-        local_index(L->is_f, n, 0, L->c_index, L->c_ids, st);
         const DevCSR& Al = L->A;
-        // blocks of Eq. 3
-        submatrix(Al, L->f_ids.p, L->n_f, L->f_index.p, L->n_f, L->A_ff, st);
-        submatrix(Al, L->f_ids.p, L->n_f, L->c_index.p, L->n_c, L->A_fc, st);
         DevCSR A_cf;
-        submatrix(Al, L->c_ids.p, L->n_c, L->f_index.p, L->n_f, A_cf, st);
+        {
+            PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_EXTRACT]);
+            local_index(L->is_f, n, 0, L->c_index, L->c_ids, st);
+            // blocks of Eq. 3
+            submatrix(Al, L->f_ids.p, L->n_f, L->f_index.p, L->n_f, L->A_ff, st);
+            submatrix(Al, L->f_ids.p, L->n_f, L->c_index.p, L->n_c, L->A_fc, st);
+            submatrix(Al, L->c_ids.p, L->n_c, L->f_index.p, L->n_f, A_cf, st);
+        }
         // GMRES polynomial (Eq. 7) and fixed-sparsity inverse (Eq. 8)
-        L->alpha = smoother_coeffs(c, L->A_ff, o, level, L->alpha_k, PURPOSE_COEF);
+        {
+            PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_SMOOTHER_POLY]);
+            L->alpha = smoother_coeffs(c, L->A_ff, o, level, L->alpha_k, PURPOSE_COEF);
+        }
         DevCSR Ainv;
-        fixed_sparsity_inverse(L->A_ff, L->alpha, Ainv, st);
+        {
+            PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_FIXED_SPARSITY]);
+            fixed_sparsity_inverse(L->A_ff, L->alpha, Ainv, st);
+        }
         // Z = -A_cf Ahat^-1, then the relative drop on R
         DevCSR Zfull;
-        spgemm(A_cf, Ainv, Zfull, st);
+        {
+            PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_RESTRICTOR]);
+            spgemm(A_cf, Ainv, Zfull, st);
+        }
         if (o.smoother == AIRG_SMOOTH_ASSEMBLED) L->Ainv = std::move(Ainv);
         if (o.smooth_type != AIRG_SMOOTH_F) {
             // C-point smoothing (Sec. 2): the GMRES polynomial of A_cc from
             // its own random stream, and the row blocks its residuals use
-            submatrix(Al, L->c_ids.p, L->n_c, L->c_index.p, L->n_c, L->A_cc, st);
-            submatrix(Al, L->c_ids.p, L->n_c, nullptr, n, L->Crows, st);
-            if (o.smooth_type == AIRG_SMOOTH_FCF) submatrix(Al, L->f_ids.p, L->n_f, nullptr, n, L->Frows, st);
-            L->alpha_c = smoother_coeffs(c, L->A_cc, o, level, L->alpha_c_k, PURPOSE_COEF_C);
+            {
+                PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_EXTRACT]);
+                submatrix(Al, L->c_ids.p, L->n_c, L->c_index.p, L->n_c, L->A_cc, st);
+                submatrix(Al, L->c_ids.p, L->n_c, nullptr, n, L->Crows, st);
+                if (o.smooth_type == AIRG_SMOOTH_FCF) submatrix(Al, L->f_ids.p, L->n_f, nullptr, n, L->Frows, st);
+            }
+            {
+                PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_SMOOTHER_POLY]);
+                L->alpha_c = smoother_coeffs(c, L->A_cc, o, level, L->alpha_c_k, PURPOSE_COEF_C);
+            }
+            PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_FIXED_SPARSITY]);
             if (o.smoother == AIRG_SMOOTH_ASSEMBLED) fixed_sparsity_inverse(L->A_cc, L->alpha_c, L->Ainv_cc, st);
         }
-        if (Zfull.nnz) k_scale<<<grid_for(Zfull.nnz, TB), TB, 0, st>>>(Zfull.nnz, Zfull.v.p, -1.0);
         {
+            PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_RESTRICTOR]);
+            if (Zfull.nnz) k_scale<<<grid_for(Zfull.nnz, TB), TB, 0, st>>>(Zfull.nnz, Zfull.v.p, -1.0);
             DBuf<int8_t> keep(std::max(Zfull.nnz, 1));
             DBuf<int> cnt(size_t(L->n_c) + 1);
             if (L->n_c) k_drop_rows<<<grid_for(L->n_c, TB), TB, 0, st>>>(L->n_c, Zfull.rp.p, Zfull.v.p,
@@ -1432,6 +1483,7 @@ std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, c
             compact(Zfull, keep.p, cnt, L->Z, st);
         }
         // one-point prolongator
+        std::unique_ptr<PhaseTimer> pt_p = std::make_unique<PhaseTimer>(st, &H->phase_ms[AIRG_PHASE_PROLONGATOR]);
         L->W.alloc(std::max(L->n_f, 1));
         k_one_point<<<grid_for(n, TB), TB, 0, st>>>(n, Al.rp.p, Al.ci.p, Al.v.p, L->strong.p,
                                                     L->is_f.p, L->c_index.p, L->f_index.p, L->W.p);
@@ -1459,12 +1511,17 @@ std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, c
         k_r_fill<<<grid_for(L->n_c, TB), TB, 0, st>>>(L->n_c, L->Z.rp.p, L->Z.ci.p, L->Z.v.p,
                                                       L->f_ids.p, L->c_ids.p, R.rp.p, R.ci.p, R.v.p);
         CK_LAUNCH();
+        pt_p.reset();
         // A_coarse = R (A P), then drop + lump
-        spgemm(Al, P, AP, st);
-        spgemm(R, AP, Ac, st);
-        // rows of AP at the F points: A_fc + A_ff W (the solve's residual operator)
-        submatrix(AP, L->f_ids.p, L->n_f, nullptr, L->n_c, L->M, st);
         {
+            PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_RAP]);
+            spgemm(Al, P, AP, st);
+            spgemm(R, AP, Ac, st);
+            // rows of AP at the F points: A_fc + A_ff W (the solve's residual operator)
+            submatrix(AP, L->f_ids.p, L->n_f, nullptr, L->n_c, L->M, st);
+        }
+        {
+            PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_DROP_LUMP]);
             int nc = Ac.n_rows;
             DBuf<int8_t> keep(std::max(Ac.nnz, 1));
             DBuf<double> vout(std::max(Ac.nnz, 1));
@@ -1483,7 +1540,11 @@ std::unique_ptr<Hierarchy> build_hierarchy(DevCSR&& A0, const airg_options& o, c
         H->levels.push_back(std::move(L));
         ++level;
     }
-    build_solve_data(*H, st);
+    {
+        PhaseTimer pt(st, &H->phase_ms[AIRG_PHASE_SOLVE_LAYOUT]);
+        build_solve_data(*H, st);
+    }
+    H->exact_dots = c.ndots;
     CK(cudaStreamSynchronize(st));
     H->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return H;

@@ -1379,6 +1379,7 @@ coarse_done:
             if (S.smooth_type == AIRG_SMOOTH_FCF) f_smooth_again<T>(S, l, v, e, wk, st);
         }
     }
+    S.close_run(st);
     S.cur_level = 0;
     CK_LAUNCH();
 }
@@ -2243,16 +2244,21 @@ void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info)
     info->storage_complexity = top ? double(store) / double(top) : 0.0;
     info->cycle_complexity = top ? double(flops) / (2.0 * double(top)) : 0.0;
     info->bytes_per_vcycle = H.solve ? H.solve->bytes_vcycle : 0;
+    for (int k = 0; k < AIRG_SETUP_PHASES; ++k) info->setup_phase_ms[k] = H.phase_ms[k];
+    info->exact_dots = H.exact_dots;
 }
 
 }  // namespace airg
 
 namespace airg {
 
-void set_profiling(Hierarchy& H, bool on)
+void set_profiling(Hierarchy& H, bool on, int kind, int level)
 {
     SolveData& S = *H.solve;
     S.prof = on;
+    S.prof_kind = on ? kind : -1;
+    S.prof_level = on ? level : -1;
+    S.run_open = false;
     S.recs.clear();
     S.evnext = 0;
     for (int k = 0; k < PROF_KINDS; ++k) {

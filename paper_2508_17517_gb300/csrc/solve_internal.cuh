@@ -179,7 +179,17 @@ struct SolveData {
     // launch count and optional per-kind CUDA-event timing of the solve kernels
     long long launches = 0;
     bool prof = false;
-    struct Rec { int kind, level; cudaEvent_t a, b; long long bytes, flops; };
+    // Group timing: with prof_kind >= 0 only the launches of kind prof_kind
+    // on level prof_level are timed.  Consecutive V-cycle launches of that
+    // group (a run, e.g. the whole chain of coarse Newton steps) share one
+    // event pair, so the timed step carries two event records per V-cycle
+    // instead of two per kernel.
+    int prof_kind = -1, prof_level = -1;
+    bool run_open = false;
+    cudaEvent_t run_a = nullptr;
+    int run_level = 0;
+    long long run_bytes = 0, run_flops = 0, run_n = 0;
+    struct Rec { int kind, level; cudaEvent_t a, b; long long bytes, flops, n; };
     int cur_level = 0;           // level of the kernels being launched (coarsest = nlev)
     std::vector<cudaEvent_t> evpool;
     size_t evnext = 0;
@@ -209,18 +219,49 @@ struct SolveData {
         if (cs == cudaStreamCaptureStatusActive) CK(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal));
         else CK(cudaEventRecord(e, st));
     }
-    void begin(cudaStream_t st, cudaEvent_t& a)
+    int prof_lvl() const { return cur_level < 0 ? 0 : (cur_level >= PROF_LEVELS ? PROF_LEVELS - 1 : cur_level); }
+    bool timed(int kind) const { return prof_kind < 0 || (kind == prof_kind && prof_lvl() == prof_level); }
+    // V-cycle kinds run back to back inside one V-cycle: their runs merge
+    static bool merges(int kind) { return kind <= PK_NEWTON; }
+    // ends an open run of the timed group at the current point of the stream
+    void close_run(cudaStream_t st)
+    {
+        if (!run_open) return;
+        cudaEvent_t b = next_event();
+        record(b, st);
+        recs.push_back(Rec{prof_kind, run_level, run_a, b, run_bytes, run_flops, run_n});
+        run_open = false;
+    }
+    void begin(cudaStream_t st, cudaEvent_t& a, int kind)
     {
         ++launches;
-        if (prof) { a = next_event(); record(a, st); }
+        if (!prof) return;
+        if (prof_kind >= 0 && !timed(kind)) { close_run(st); return; }
+        if (prof_kind >= 0 && merges(kind)) {
+            if (!run_open) {
+                run_a = next_event();
+                record(run_a, st);
+                run_open = true;
+                run_level = prof_lvl();
+                run_bytes = run_flops = run_n = 0;
+            }
+            return;
+        }
+        a = next_event();
+        record(a, st);
     }
     void end(int kind, long long bytes, long long flops, cudaStream_t st, cudaEvent_t a)
     {
-        if (!prof) return;
+        if (!prof || !timed(kind)) return;
+        if (prof_kind >= 0 && merges(kind)) {
+            run_bytes += bytes;
+            run_flops += flops;
+            ++run_n;
+            return;
+        }
         cudaEvent_t b = next_event();
         record(b, st);
-        int lvl = cur_level < 0 ? 0 : (cur_level >= PROF_LEVELS ? PROF_LEVELS - 1 : cur_level);
-        recs.push_back(Rec{kind, lvl, a, b, bytes, flops});
+        recs.push_back(Rec{kind, prof_lvl(), a, b, bytes, flops, 1});
     }
     // after the stream has been synchronised
     void collect()
@@ -229,10 +270,10 @@ struct SolveData {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, r.a, r.b));
             kind_ms[r.kind] += ms;
-            kind_launches[r.kind] += 1;
+            kind_launches[r.kind] += r.n;
             kind_bytes[r.kind] += r.bytes;
             lev_ms[r.kind][r.level] += ms;
-            lev_launches[r.kind][r.level] += 1;
+            lev_launches[r.kind][r.level] += r.n;
             lev_bytes[r.kind][r.level] += r.bytes;
             lev_flops[r.kind][r.level] += r.flops;
         }
@@ -288,7 +329,7 @@ struct SolveData {
 #define LAUNCH_F(S, KIND, BYTES, FLOPS, ...)         \
     do {                                             \
         cudaEvent_t ev_a_ = nullptr;                 \
-        (S).begin(st, ev_a_);                        \
+        (S).begin(st, ev_a_, (KIND));                \
         __VA_ARGS__;                                 \
         (S).end((KIND), (BYTES), (FLOPS), st, ev_a_); \
     } while (0)

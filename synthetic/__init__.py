@@ -129,5 +129,22 @@ def workload(name, n=None):
     raise KeyError(name)
 
 
+def corner(w, m):
+    """The m x m lower-left corner of a single-right-hand-side workload w
+    whose velocity has both components positive: same direction, options and
+    tolerance, and the inflow values of w at the corner's inflow nodes.  The
+    upwind stencil of every node looks back in x and y only, so the corner is
+    a closed problem whose exact solution is w's restricted to the corner
+    (for zero source).  Inflow nodes are ordered by node index: the j = 0 row
+    (i = 0..nx-1), then the i = 0 column (j = 1..ny-1)."""
+    vx, vy = velocity(w["theta"])
+    assert vx > 0 and vy > 0 and w["s"] is None and w["n_rhs"] == 1
+    assert m <= w["nx"] and m <= w["ny"]
+    nx = w["nx"]
+    g = np.concatenate([w["g"][0][:m], w["g"][0][nx:nx + m - 1]])[None, :]
+    assert g.shape[1] == _n_inflow(m, m, w["theta"])
+    return dict(w, nx=m, ny=m, g=g, desc="%dx%d lower-left corner of %s" % (m, m, w["desc"]))
+
+
 def velocity(theta):
     return math.cos(theta), math.sin(theta)

@@ -164,6 +164,9 @@ def test_host_argument_checks_need_no_gpu(L):
     assert L.airg_rhs_adjoint_advection2d(8, 8, 1.0, 0.0, 0.1, 1, fake, -1, fake, fake, None, None) == ARG
     assert L.airg_dot_exact_noalloc(-1, fake, fake, fake, None) == ARG
     assert L.airg_dot_exact_noalloc(1 << 31, fake, fake, fake, None) == ARG and "2^31" in err()
+    d = ctypes.c_double()
+    assert L.airg_dot_exact(-1, fake, fake, ctypes.byref(d), None) == ARG
+    assert L.airg_dot_exact(1 << 31, fake, fake, ctypes.byref(d), None) == ARG and "2^31" in err()
     assert L.airg_check_wait_timeout(0, None) == ARG
     L.airg_free(None)
     L.airg_batch_free(None)

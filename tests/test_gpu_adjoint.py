@@ -58,8 +58,56 @@ def test_adjoint_matches_dense_adjoint_64():
     assert np.allclose(gs.cpu().numpy(), exp_s, rtol=1e-15, atol=0)
 
 
+def _exact(po, g, s, order):
+    """Exact discrete solution (substitution in upwind order, Sec. 1.1)."""
+    return O.sweep_solve(po.A, O.assemble_rhs(po, g, s), order)
+
+
 @pytest.mark.parametrize("size", [256, 1024])
-def test_autograd_gradients_match_central_differences(size):
+def test_gradients_match_central_differences_of_the_exact_loss(size):
+    """dL/dg and dL/ds from the adjoint AIRG solve against central
+    differences (step 1e-6) of L at exact solutions.  u is affine in (g, s),
+    so L is quadratic and the central difference has no truncation error:
+    L(+) - L(-) = sum (u+ - u-)(u+ + u- - 2 u_t), evaluated in that form so
+    that only rounding of the exact solutions remains (~1e-10 relative).
+    dL/dg (FP64): <= 1e-8 relative on every direction.  dL/ds is returned
+    in the FP32 of s, so its bound is the FP32 rounding of each entry:
+    |fd - <gs, ds>| <= 2^-24 sum |gs_i ds_i| + 1e-8 |fd|."""
+    w = workload("c5", size)
+    sv, vx, vy = _solver(w)
+    g = torch.tensor(w["g"][0], device="cuda", requires_grad=True)
+    s32 = torch.tensor(w["s"][0], device="cuda", dtype=torch.float32, requires_grad=True)
+    ut = w["ut"]
+    u = sv.solve(g, s32, 1e-13)
+    L = ((u - torch.tensor(ut, device="cuda")) ** 2).sum()
+    L.backward()
+    gg = g.grad.cpu().numpy()
+    gs = s32.grad.double().cpu().numpy()
+    assert s32.grad.dtype == torch.float32
+    po = O.advection_2d(size, size, vx, vy)
+    order = O.sweep_order(po)
+    g0 = w["g"][0]
+    s0 = s32.detach().double().cpu().numpy()
+    eps = 1e-6
+    ndir = 32 if size == 1024 else 8
+    for k in range(ndir):
+        dg, ds = w["dirs_g"][k], w["dirs_s"][k]
+        up, um = _exact(po, g0 + eps * dg, s0, order), _exact(po, g0 - eps * dg, s0, order)
+        fd = float(np.sum((up - um) / (2 * eps) * (up + um - 2 * ut)))
+        an = float(gg @ dg)
+        assert abs(fd - an) <= 1e-8 * abs(fd), ("g direction", k, fd, an)
+        up, um = _exact(po, g0, s0 + eps * ds, order), _exact(po, g0, s0 - eps * ds, order)
+        fd = float(np.sum((up - um) / (2 * eps) * (up + um - 2 * ut)))
+        an = float(gs @ ds)
+        bound = 2.0 ** -24 * float(np.sum(np.abs(gs * ds))) + 1e-8 * abs(fd)
+        assert abs(fd - an) <= bound, ("s direction", k, fd, an, bound)
+
+
+@pytest.mark.parametrize("size", [256, 1024])
+def test_autograd_gradients_match_differences_of_gpu_solves(size):
+    """End to end: central differences of L through the GPU's own forward
+    solves (rtol 1e-13).  Their solution error divided by the step 1e-6
+    limits the agreement to ~1e-6 relative."""
     w = workload("c5", size)
     sv, vx, vy = _solver(w)
     g = torch.tensor(w["g"][0], device="cuda", requires_grad=True)
