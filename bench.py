@@ -57,6 +57,9 @@ def parse(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c3"] + sorted(SINGLE))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=None,
+                    help="grid side of a single-problem workload (a smaller case of the same kind, "
+                         "for profiling)")
     ap.add_argument("--sweep", choices=["coarse-order", "smoother", "cases", "readings"], default=None,
                     help="instead of the throughput line, one JSON line with a row per setting: "
                          "coarse-order = the coarse polynomial order / truncation study of Sec. 3.1; "
@@ -166,7 +169,7 @@ def reference_sample(args):
     workloads are sampled whole."""
     from synthetic import corner, workload
     name = "c3_fp64" if args.workload == "c3" else SINGLE[args.workload]
-    w = workload(name)
+    w = workload(name, n=args.grid)
     if w.get("n_rhs", 1) != 1 or "problems" in w:
         return w, None
     if w["nx"] * w["ny"] > CORNER * CORNER:
@@ -263,14 +266,12 @@ def run_reference(args):
 
 
 def run_gpu_multi(args):
-    """Workload of many separate grids of uneven size (one hierarchy each)."""
+    """Workload of many separate grids of uneven size (one hierarchy each):
+    `value` from the default form, each lockstep FGMRES iteration of all
+    problems as one persistent work-list launch; `graph_form` times the same
+    solves with one graph of per-problem branches per iteration."""
     import torch
-    rank, world, local_rank = dist_env()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    rank, world, local_rank, dev = _dist_setup(torch)
     import paper_2508_17517_gb300 as G
     from synthetic import velocity, workload
     G.lib()
@@ -287,35 +288,67 @@ def run_gpu_multi(args):
     setup_s = time.perf_counter() - t0
     xs = [torch.zeros_like(b) for b in bs]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    for _ in range(args.warmup):
-        for x in xs:
-            x.zero_()
-        G.airg_solve_batch(B, bs, xs, rtol=w["rtol"])
     stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    peak, peak_kind = measured_peaks()
+
+    def timed(form, steps, warmup, label):
+        os.environ["AIRG_MULTI"] = form
+        for _ in range(warmup):
+            for x in xs:
+                x.zero_()
+            G.airg_solve_batch(B, bs, xs, rtol=w["rtol"])
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        _barrier(world, torch)
+        total_ms, its, launches = 0.0, [], 0
+        torch.cuda.nvtx.range_push(label)
+        for _ in range(steps):
+            flush.zero_()
+            for x in xs:
+                x.zero_()
+            ev0.record(stream)
+            _, infos = G.airg_solve_batch(B, bs, xs, rtol=w["rtol"])
+            ev1.record(stream)
+            ev1.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+            its.append(max(i.iterations for i in infos))
+            launches += sum(i.kernel_launches for i in infos)
+            assert all(i.converged for i in infos)
+        torch.cuda.nvtx.range_pop()
+        _barrier(world, torch)
+        return total_ms, its, launches
+
+    def iteration_roofline(form, steps):
+        """Event-timed iteration launches of one form (one pair per launch)."""
+        os.environ["AIRG_MULTI"] = form
+        G.airg_batch_profile(B, True)
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            for x in xs:
+                x.zero_()
+            t, _, _ = timed(form, 1, 0, "iteration timing")
+            tot += t
+        ms, nl, nb = G.airg_batch_profile_read(B)
+        G.airg_batch_profile(B, False)
+        gbs = nb / (ms / 1e3) / 1e9
+        return {"kernel": {"worklist": "k_worklist (all problems' iteration, one launch)",
+                           "graph": "iteration graph (per-problem branches)"}[form],
+                "bound": "hbm", "launches": nl, "avg_launch_us": 1e3 * ms / nl,
+                "algorithmic_bytes_per_launch": nb / nl, "share": ms / tot,
+                "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_source": peak_kind,
+                "timing": "each iteration launch between CUDA events on the batch stream, %d solves" % steps}
+
     clk = Clocks(local_rank)
-    torch.cuda.synchronize()
     clk.start()
-    total_ms, its = 0.0, []
-    vbytes = [G.airg_batch_setup_info(B, i)["bytes_per_vcycle"] for i in range(len(bs))]
-    moved = launches = 0
-    for _ in range(args.steps):
-        flush.zero_()
-        for x in xs:
-            x.zero_()
-        ev0.record(stream)
-        _, infos = G.airg_solve_batch(B, bs, xs, rtol=w["rtol"])
-        ev1.record(stream)
-        ev1.synchronize()
-        total_ms += ev0.elapsed_time(ev1)
-        its.append(max(i.iterations for i in infos))
-        moved += sum(vb * i.iterations for vb, i in zip(vbytes, infos))
-        launches += sum(i.kernel_launches for i in infos)
-        assert all(i.converged for i in infos)
-    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    total_ms, its, launches = timed("worklist", args.steps, args.warmup, "timed")
+    wall_s = time.perf_counter() - t_wall0
+    g_ms, g_its, g_launches = timed("graph", args.steps, args.warmup, "graph form")
     clocks = clk.stop()
     t_max = max_over_ranks(total_ms, world, dev)
+    g_max = max_over_ranks(g_ms, world, dev)
     value = world * ntot * args.steps / (t_max / 1e3)
+    os.environ["AIRG_MULTI"] = "worklist"
     bh = [b.cpu().pin_memory() for b in bs]
     xh = [torch.zeros_like(b).pin_memory() for b in bh]
     G.airg_solve_batch(B, bh, xh, rtol=w["rtol"])     # warm-up of the host path (staging buffers)
@@ -328,23 +361,25 @@ def run_gpu_multi(args):
         G.airg_solve_batch(B, bh, xh, rtol=w["rtol"])
         e2e_s += time.perf_counter() - t0
     e2e_max = max_over_ranks(e2e_s, world, dev)
-    peak, peak_kind = measured_peaks()
-    roofline = multi_roofline(moved, total_ms, peak, peak_kind)
+    roof = iteration_roofline("worklist", args.steps)
+    g_roof = iteration_roofline("graph", args.steps)
+    os.environ.pop("AIRG_MULTI", None)
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["desc"], "n": ntot, "problems": len(bs), "rtol": w["rtol"],
-                       "iterations_per_solve": statistics.median(its), "setup_s": setup_s,
                        "l2": "flushed (256 MiB write) between timed steps"},
+            "iterations_per_solve": statistics.median(its), "setup_s": setup_s,
             "e2e": {"value": world * ntot * args.steps / e2e_max, "unit": "DOF/s",
                     "h2d_bytes_per_step": 16 * ntot, "d2h_bytes_per_step": 8 * ntot},
-            "roofline": roofline, "cpu_baseline": None, "clocks": clocks, "gpu_launches": launches}))
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.destroy_process_group()
+            "roofline": roof,
+            "graph_form": {"value": world * ntot * args.steps / (g_max / 1e3), "unit": "DOF/s",
+                           "ms_per_step": g_max / args.steps, "iterations_per_solve": statistics.median(g_its),
+                           "gpu_launches": g_launches, "roofline": g_roof},
+            "cpu_baseline": None, "clocks": clocks, "gpu_launches": launches, "wall_s_timed": wall_s}))
+    _dist_end(world)
 
 
 # Arithmetic peaks from unit counts and the nominal 2070 MHz SM clock of the
@@ -385,7 +420,7 @@ def measured_traffic(workload, kind, level):
     return None, "no ncu traffic entry for this kernel group and workload"
 
 
-def solve_timed(G, torch, h, b, x, rtol, flush, steps):
+def solve_timed(G, torch, h, b, x, rtol, flush, steps, label="timed"):
     """`steps` solves from x0 = 0, L2 flushed before each; device time of
     each solve by CUDA events on the launching stream.  Returns (total ms,
     iterations per solve, kernel launches, last info)."""
@@ -393,6 +428,7 @@ def solve_timed(G, torch, h, b, x, rtol, flush, steps):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     total_ms, its, launches, info = 0.0, [], 0, None
+    torch.cuda.nvtx.range_push(label)     # lets a profiler take the timed solves alone
     for _ in range(steps):
         flush.zero_()
         x.zero_()
@@ -404,6 +440,7 @@ def solve_timed(G, torch, h, b, x, rtol, flush, steps):
         its.append(info.iterations)
         launches += info.kernel_launches
         assert info.converged and info.rel_residual <= rtol, (info.converged, info.rel_residual)
+    torch.cuda.nvtx.range_pop()
     return total_ms, its, launches, info
 
 
@@ -428,7 +465,7 @@ def group_timed(G, torch, h, b, x, rtol, flush, steps, kind, level, levels):
     launches, bytes, flops) over `steps` solves and the ms per solve of that
     instrumented pass."""
     G.airg_profile_group(h, kind, level)
-    tot, _, _, _ = solve_timed(G, torch, h, b, x, rtol, flush, steps)
+    tot, _, _, _ = solve_timed(G, torch, h, b, x, rtol, flush, steps, label="group timing")
     per = G.airg_profile_read_level(h, levels).get((kind, level))
     G.airg_profile(h, False)
     return per, tot / steps
@@ -505,19 +542,6 @@ def roofline_entry(G, torch, h, b, x, rtol, flush, steps, levels, ms_per_step, p
     return entry
 
 
-def multi_roofline(vcycle_bytes, total_ms, peak, peak_kind):
-    """Roofline of the many-grid solve.  Its problems run as concurrent graph
-    branches, so per-kernel event times overlap and no single kernel group
-    can be timed; the figure is the aggregate instead: the algorithmic bytes
-    of every V-cycle of every problem over the device time of the whole
-    solve.  Krylov and top-level SpMV traffic is left out, so it is a lower
-    bound on the bandwidth the step draws."""
-    gbs = vcycle_bytes / (total_ms / 1e3) / 1e9 if total_ms > 0 else 0.0
-    return {"bound": "hbm", "kernel": "all V-cycle kernels, concurrent branches (aggregate)",
-            "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_source": peak_kind,
-            "algorithmic_bytes": vcycle_bytes, "traffic": None}
-
-
 def _dist_setup(torch):
     rank, world, local_rank = dist_env()
     torch.cuda.set_device(local_rank)
@@ -576,12 +600,14 @@ def run_gpu(args):
     import paper_2508_17517_gb300 as G
     from synthetic import workload
     G.lib()
-    w = workload(SINGLE[args.workload])
+    w = workload(SINGLE[args.workload], n=args.grid)
     k = w["n_rhs"]
     n = w["nx"] * w["ny"]
     prob, b = problem_and_rhs(w, G, torch)
     opts = G.airg_options_default(**w["opts"])
+    torch.cuda.nvtx.range_push("setup")
     h = G.airg_setup(prob["rowptr"], prob["col"], prob["val"], opts)
+    torch.cuda.nvtx.range_pop()
     sinfo = G.airg_setup_info(h)
     x = torch.zeros_like(b)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -604,7 +630,8 @@ def run_gpu(args):
     peak, peak_kind = measured_peaks()
     vdt = "f32" if w["opts"].get("precision", 0) in (1, 2) else "f64"
     roofline = roofline_entry(G, torch, h, b, x, w["rtol"], flush, args.steps, sinfo["levels"],
-                              t_max / args.steps, peak, peak_kind, vdt, args.workload)
+                              t_max / args.steps, peak, peak_kind, vdt,
+                              args.workload if args.grid is None else "%s@%d" % (args.workload, args.grid))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_entry(args)
@@ -782,6 +809,9 @@ def run_sweep(args):
     if args.sweep == "cases":
         run_cases(G, torch, args)
         return
+    if args.sweep == "readings":
+        run_readings(G, torch, args)
+        return
     n = 4096
     th = math.pi / 4
     vx, vy = math.cos(th), math.sin(th)
@@ -810,6 +840,66 @@ def run_sweep(args):
                                  **r))
     print(json.dumps({"sweep": args.sweep, "grid": "%dx%d" % (n, n), "theta": "pi/4", "g": 1.0,
                       "rtol": 1e-10, "steps": args.steps, "warmup": args.warmup, "rows": rows}))
+
+
+def run_readings(G, torch, args):
+    """Which reading of the unstated parameters drives the cycle complexity:
+    the R drop tolerance r_drop (reading R8) and DDC on / off (ddc_its 2 /
+    0, reading R4) on the 1024^2 workload (seeded direction, m_c = 30,
+    truncation 1e-2; with --grid N, the N^2 grid of the 4096^2 workload's
+    family as well), FP64, rtol 1e-10.  Each row splits the
+    cycle complexity into the part of the levels (restriction, residual,
+    smoother) and that of the coarse Newton polynomial, whose SpMVs on the
+    coarsest operator are counted from its roots (a real root one SpMV, a
+    conjugate pair two, the last root one less)."""
+    from synthetic import velocity, workload
+    rows = []
+    for name in ("c2", "c3_fp64") if args.grid else ("c2",):
+        w = workload(name, n=args.grid if name == "c3_fp64" else None)
+        vx, vy = velocity(w["theta"])
+        prob = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
+        b = G.airg_assemble_rhs_advection2d(prob, torch.tensor(w["g"][0], device="cuda"))
+        for ddc in (2, 0):
+            # from the largest tolerance down; r_drop = 0 (no drop) fills the
+            # coarse operators so much that a 1024^2 setup did not finish in 30 min
+            for rd in (5e-2, 2e-2, 1e-2, 5e-3):
+                opts = dict(w["opts"], r_drop=rd, ddc_its=ddc)
+                t0 = time.perf_counter()
+                h = G.airg_setup(prob["rowptr"], prob["col"], prob["val"], G.airg_options_default(**opts))
+                torch.cuda.synchronize()
+                setup_s = time.perf_counter() - t0
+                info = G.airg_setup_info(h)
+                L = info["levels"] - 1
+                roots = G.airg_export_vector(h, L, 3).reshape(-1, 2)
+                nsp = sum((0 if i + 1 == len(roots) else 1) if im == 0.0 else (1 if i + 1 == len(roots) else 2)
+                          for i, (_, im) in enumerate(roots))
+                cc_coarse = nsp * info["nnz_a"][L] / info["nnz_a"][0]
+                x = torch.zeros_like(b)
+                times, its = [], []
+                for k in range(args.warmup + args.steps):
+                    x.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    _, si = G.airg_solve(h, b, x, rtol=1e-10)
+                    e1.record()
+                    e1.synchronize()
+                    if k >= args.warmup:
+                        times.append(e0.elapsed_time(e1))
+                        its.append(si.iterations)
+                rows.append({"workload": name, "r_drop": rd, "ddc_its": ddc, "levels": info["levels"],
+                             "coarse_rows": info["n"][L],
+                             "coarse_nnz_per_row": round(info["nnz_a"][L] / max(info["n"][L], 1), 1),
+                             "cycle_complexity": round(info["cycle_complexity"], 2),
+                             "cc_coarse": round(cc_coarse, 2),
+                             "cc_levels": round(info["cycle_complexity"] - cc_coarse, 2),
+                             "storage_complexity": round(info["storage_complexity"], 2),
+                             "iterations": statistics.median(its), "solve_ms": round(statistics.median(times), 3),
+                             "setup_s": round(setup_s, 2)})
+                G.airg_free(h)
+        del prob, b
+        torch.cuda.empty_cache()
+    print(json.dumps({"sweep": "readings", "rtol": 1e-10, "steps": args.steps, "warmup": args.warmup,
+                      "rows": rows}))
 
 
 def run_cases(G, torch, args):

@@ -170,11 +170,14 @@ airg_status airg_options_default(airg_options* opt);
  * interior rows d*u_ij - |vx| u_(upwind x) - |vy| u_(upwind y) = h s_ij with
  * d = |vx| + |vy|; inflow nodes (v.n < 0) keep their unknowns with the row
  * d*u = d*g (boundary DOFs not eliminated).  Zero velocity components store
- * no entry.  All pointers are DEVICE pointers, caller-allocated:
+ * no entry.  h = 0 selects the spacing of the unit square's node grid,
+ * 1 / (nx - 1), here and in the two right-hand-side calls below.  All
+ * pointers are DEVICE pointers, caller-allocated:
  *   rowptr: n+1, col: 3n, val: 3n, inflow: nx+ny (sorted node indices).
  * *nnz_out and *n_inflow_out (HOST pointers) receive the counts.
- * AIRG_ERR_ARG unless nx, ny >= 2, 3 nx ny < 2^31, h > 0 and vx, vy finite
- * (a smaller system can be passed to airg_setup as a CSR matrix directly).
+ * AIRG_ERR_ARG unless nx, ny >= 2, 3 nx ny < 2^31, h >= 0 finite and vx, vy
+ * finite (a smaller system can be passed to airg_setup as a CSR matrix
+ * directly).
  */
 airg_status airg_problem_advection2d(int64_t nx, int64_t ny, double vx, double vy, double h,
                                      int64_t* rowptr, int32_t* col, double* val,
@@ -254,10 +257,17 @@ airg_status airg_solve_adjoint(airg_handle* h, int nrhs, const double* rhs, doub
  * Many separate problems (different operators, e.g. grids of uneven size),
  * one AIRG hierarchy each, solved together.  airg_setup_batch builds the
  * nprob hierarchies (As: HOST array of nprob CSR descriptors, same options
- * for all).  airg_solve_batch runs FGMRES in lockstep across the problems:
- * each iteration is one CUDA graph launch in which every problem's V-cycle,
- * SpMV and Gram-Schmidt pass form an independent branch (captured once per
- * iteration index and replayed).  bvec, xvec: HOST arrays of nprob pointers
+ * for all).  airg_solve_batch runs FGMRES in lockstep across the problems.
+ * Each iteration of all problems -- scale v_j, V-cycle, SpMV, Gram-Schmidt
+ * pass -- is one persistent kernel launch (captured in a CUDA graph once per
+ * iteration index and replayed) whose blocks take the tiles of every
+ * problem's operations from a device work list in dependency order.  With
+ * the environment variable AIRG_MULTI=graph, or for layouts the work list
+ * does not implement (C-point smoothing, the assembled smoother, bfloat16
+ * restrictor values, the opt-in persistent or staged kernels), each
+ * iteration is instead one graph launch in which every problem forms an
+ * independent branch of per-operator kernels.  A bounded wait of the work
+ * list that gives up returns AIRG_ERR_TIMEOUT.  bvec, xvec: HOST arrays of nprob pointers
  * to vectors of each problem's length (DEVICE pointers if on_device, else
  * HOST); x is the initial guess on entry.  infos: HOST array of nprob
  * entries (may be NULL).  AIRG_ERR_NOT_CONVERGED if any problem misses the
@@ -273,6 +283,18 @@ airg_status airg_solve_batch(airg_batch* b, const double* const* bvec, double* c
  * is a HOST pointer.  AIRG_ERR_ARG for a null batch or info or i out of
  * range. */
 airg_status airg_batch_setup_info(const airg_batch* b, int i, airg_hierarchy_info* info);
+/*
+ * Timing of the lockstep iterations of airg_solve_batch: with profiling
+ * enabled (which clears the totals), a CUDA event pair brackets each
+ * iteration's launch -- the one work-list kernel, or the graph of
+ * per-problem branches -- on the batch's stream.  airg_batch_profile_read
+ * returns the summed event time (ms), the number of such launches and the
+ * algorithmic bytes of the operations of the problems still active in them
+ * (stored entries, column indices and each vector read or written once).
+ * Outputs are HOST pointers.  AIRG_ERR_ARG for a null batch or output.
+ */
+airg_status airg_batch_profile(airg_batch* b, int enable);
+airg_status airg_batch_profile_read(const airg_batch* b, double* ms, int64_t* launches, int64_t* bytes);
 void airg_batch_free(airg_batch* b);
 
 /* Levels, sizes and the complexities of Sec. 3.  info is a HOST pointer. */

@@ -38,7 +38,8 @@ EXPORTS = ["airg_options_default", "airg_problem_advection2d", "airg_assemble_rh
            "airg_dot_exact", "airg_rng_uniform", "airg_host_gmres_coeffs", "airg_host_eigvals",
            "airg_profile", "airg_profile_read", "airg_profile_read_level", "airg_dot_exact_noalloc",
            "airg_rhs_adjoint_advection2d", "airg_setup_batch", "airg_solve_batch",
-           "airg_batch_free", "airg_batch_setup_info", "airg_check_wait_timeout", "airg_profile_group"]
+           "airg_batch_free", "airg_batch_setup_info", "airg_check_wait_timeout", "airg_profile_group",
+           "airg_batch_profile", "airg_batch_profile_read"]
 PROFILE_KINDS = ["restrict", "f_residual", "f_smoother", "coarse_newton", "top_spmv",
                  "krylov_vectors", "layout"]
 # airg_hierarchy_info.setup_phase_ms entries (AIRG_PHASE_* of the header)
@@ -121,6 +122,8 @@ def lib():
             "airg_host_eigvals": [ci, vp, vp, vp],
             "airg_profile": [vp, ci],
             "airg_profile_group": [vp, ci, ci],
+            "airg_batch_profile": [vp, ci],
+            "airg_batch_profile_read": [vp, ctypes.POINTER(f64), ctypes.POINTER(i64), ctypes.POINTER(i64)],
             "airg_dot_exact_noalloc": [i64, vp, vp, vp, vp],
             "airg_rhs_adjoint_advection2d": [i64, i64, f64, f64, f64, ci, vp, i64, vp, vp, vp, vp],
             "airg_check_wait_timeout": [i64, vp],
@@ -178,10 +181,10 @@ def airg_options_default(**overrides):
 
 
 def airg_problem_advection2d(nx, ny, vx, vy, h=None, stream=None):
-    """Device CSR (rowptr int64, col int32, val f64) and inflow node list."""
+    """Device CSR (rowptr int64, col int32, val f64) and inflow node list.
+    h = None: the library's default spacing of the unit square (passed as 0)."""
     import torch
-    if h is None:   # grid spacing; a single column (or node) falls back to the y spacing, else 1
-        h = 1.0 / (nx - 1) if nx > 1 else (1.0 / (ny - 1) if ny > 1 else 1.0)
+    h = 0.0 if h is None else h
     n = nx * ny
     dev = torch.device("cuda")
     rowptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
@@ -297,6 +300,17 @@ def airg_solve_batch(batch, bs, xs=None, rtol=1e-10, atol=1e-50, maxit=200, stre
                                 int(maxit), infos, _stream(stream))
     _check(st, allow=(AIRG_ERR_NOT_CONVERGED,) if allow_nc else ())
     return xs, list(infos)
+
+
+def airg_batch_profile(batch, enable):
+    _check(lib().airg_batch_profile(batch.ptr, int(enable)))
+
+
+def airg_batch_profile_read(batch):
+    """(ms, launches, algorithmic bytes) of the timed iteration launches."""
+    ms, nl, nb = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().airg_batch_profile_read(batch.ptr, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(nb)))
+    return ms.value, nl.value, nb.value
 
 
 def airg_batch_free(batch):

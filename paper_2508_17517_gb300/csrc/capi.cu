@@ -40,6 +40,10 @@ airg_status guarded(F&& f)
 
 constexpr int TB = 256;
 
+// Node spacing of the unit square's grid, nodes i * h for i = 0 .. nx - 1
+// (the non-dimensionalisation of Sec. 3), used when the caller passes h = 0.
+double default_spacing(long long nx) { return 1.0 / double(nx - 1); }
+
 __global__ void k_adv_count(long long nx, long long ny, int sx, int sy, int* cnt, int* inflow_flag)
 {
     long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -223,8 +227,10 @@ airg_status airg_problem_advection2d(int64_t nx, int64_t ny, double vx, double v
 {
     return guarded([&] {
         if (nx < 2 || ny < 2 || nx * ny >= (1LL << 31) / 3 || !rowptr || !col || !val || !inflow ||
-            !nnz_out || !n_inflow_out || !(h > 0.0) || !std::isfinite(vx) || !std::isfinite(vy))
+            !nnz_out || !n_inflow_out || !(h >= 0.0) || !std::isfinite(h) || !std::isfinite(vx) ||
+            !std::isfinite(vy))
             airg::fail(AIRG_ERR_ARG, "bad advection2d arguments");
+        if (h == 0.0) h = default_spacing(nx);
         cudaStream_t st = (cudaStream_t)stream;
         long long n = nx * ny;
         airg::DBuf<int> cnt(n + 1), flag(n + 1);
@@ -250,8 +256,10 @@ airg_status airg_assemble_rhs_advection2d(int64_t nx, int64_t ny, double vx, dou
                                           const double* g, const double* s, double* b, void* stream)
 {
     return guarded([&] {
-        if (nx < 2 || ny < 2 || nrhs < 1 || !inflow || !g || !b || n_inflow < 0)
+        if (nx < 2 || ny < 2 || nrhs < 1 || !inflow || !g || !b || n_inflow < 0 || !(h >= 0.0) ||
+            !std::isfinite(h))
             airg::fail(AIRG_ERR_ARG, "bad rhs arguments");
+        if (h == 0.0) h = default_spacing(nx);
         cudaStream_t st = (cudaStream_t)stream;
         long long n = nx * ny;
         double d = std::fabs(vx) + std::fabs(vy);
@@ -274,8 +282,10 @@ airg_status airg_rhs_adjoint_advection2d(int64_t nx, int64_t ny, double vx, doub
                                          void* stream)
 {
     return guarded([&] {
-        if (nx < 2 || ny < 2 || nrhs < 1 || !inflow || !lambda || !grad_g || n_inflow < 0)
+        if (nx < 2 || ny < 2 || nrhs < 1 || !inflow || !lambda || !grad_g || n_inflow < 0 || !(h >= 0.0) ||
+            !std::isfinite(h))
             airg::fail(AIRG_ERR_ARG, "bad rhs-adjoint arguments");
+        if (h == 0.0) h = default_spacing(nx);
         cudaStream_t st = (cudaStream_t)stream;
         long long n = nx * ny;
         double d = std::fabs(vx) + std::fabs(vy);

@@ -44,26 +44,35 @@ __device__ __forceinline__ bool xd_split(double x, unsigned long long& m, int& e
     return m != 0ULL;
 }
 
-// Adds +-(hi:lo) * 2^(pos) to the digits (pos >= 0 in accumulator bits).
-__device__ __forceinline__ void xd_deposit(unsigned long long* acc, unsigned long long hi,
-                                           unsigned long long lo, int pos, int neg)
+// A thread's register window over six consecutive digits d0 .. d0+5 of the
+// accumulator.  A product's five pieces land in digits d .. d+4 with
+// d = pos >> 5; products of similar magnitude share d, so most of them are
+// added in registers and only a window move (or the end of the thread's
+// loop) deposits the window's digits into the shared accumulator.  The
+// sums are exact integer sums, so the result does not depend on when they
+// are deposited.  Headroom: each slot receives at most one 32-bit piece per
+// product, like a digit of the accumulator.
+struct XdWin {
+    unsigned long long r[6];
+    int d0;
+};
+
+__device__ __forceinline__ void xd_win_init(XdWin& w)
 {
-    int d = pos >> 5;
-    int sh = pos & 31;
-    // 160-bit value (w2:w1:w0 as 64-bit words) = (hi:lo) << sh
-    unsigned long long w0 = lo << sh;
-    unsigned long long w1 = sh ? ((hi << sh) | (lo >> (64 - sh))) : hi;
-    unsigned long long w2 = sh ? (hi >> (64 - sh)) : 0ULL;
-    unsigned long long piece[5] = {w0 & 0xffffffffULL, w0 >> 32, w1 & 0xffffffffULL, w1 >> 32,
-                                   w2 & 0xffffffffULL};
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        if (piece[k]) atomicAdd(acc + d + k, neg ? (0ULL - piece[k]) : piece[k]);
-    }
+    for (int k = 0; k < 6; ++k) w.r[k] = 0ULL;
+    w.d0 = -8;
 }
 
-__device__ __forceinline__ void xd_add_product(unsigned long long* acc, double x, double y,
-                                               int* bad)
+__device__ __forceinline__ void xd_win_flush(unsigned long long* acc, XdWin& w)
+{
+    if (w.d0 < 0) return;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        if (w.r[k]) atomicAdd(acc + w.d0 + k, w.r[k]);
+}
+
+__device__ __forceinline__ void xd_win_add(unsigned long long* acc, XdWin& w, double x, double y, int* bad)
 {
     unsigned long long mx, my;
     int ex, ey, nx, ny;
@@ -73,7 +82,37 @@ __device__ __forceinline__ void xd_add_product(unsigned long long* acc, double x
     if (zx || zy) return;
     unsigned long long lo = mx * my;
     unsigned long long hi = __umul64hi(mx, my);
-    xd_deposit(acc, hi, lo, ex + ey + XD_BIAS, nx ^ ny);
+    const int pos = ex + ey + XD_BIAS;
+    const int d = pos >> 5, sh = pos & 31;
+    unsigned long long w0 = lo << sh;
+    unsigned long long w1 = sh ? ((hi << sh) | (lo >> (64 - sh))) : hi;
+    unsigned long long w2 = sh ? (hi >> (64 - sh)) : 0ULL;
+    unsigned long long p[5] = {w0 & 0xffffffffULL, w0 >> 32, w1 & 0xffffffffULL, w1 >> 32,
+                               w2 & 0xffffffffULL};
+    if (nx ^ ny) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) p[k] = 0ULL - p[k];
+    }
+    if (d == w.d0 - 1) {
+        // move the window down one digit (depositing its top digit)
+        if (w.r[5]) atomicAdd(acc + w.d0 + 5, w.r[5]);
+#pragma unroll
+        for (int k = 5; k > 0; --k) w.r[k] = w.r[k - 1];
+        w.r[0] = 0ULL;
+        w.d0 = d;
+    } else if (d != w.d0 && d != w.d0 + 1) {
+        xd_win_flush(acc, w);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w.r[k] = 0ULL;
+        w.d0 = d;
+    }
+    if (d == w.d0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) w.r[k] += p[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) w.r[k + 1] += p[k];
+    }
 }
 
 // Block: XD_THREADS threads.  gacc: XD_DIGITS words, zero on entry of the
@@ -87,9 +126,12 @@ k_xdot_accumulate(long long n, const double* __restrict__ x, const double* __res
         (&sacc[0][0])[t] = 0ULL;
     __syncthreads();
     unsigned long long* mine = sacc[threadIdx.x >> 5];
+    XdWin win;
+    xd_win_init(win);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        xd_add_product(mine, x[i], y[i], bad);
+        xd_win_add(mine, win, x[i], y[i], bad);
+    xd_win_flush(mine, win);
     __syncthreads();
     for (int t = threadIdx.x; t < XD_DIGITS; t += blockDim.x) {
         unsigned long long s = 0ULL;
@@ -182,14 +224,69 @@ k_xdot(long long n, const double* __restrict__ x, const double* __restrict__ y,
         (&sacc[0][0])[t] = 0ULL;
     __syncthreads();
     unsigned long long* mine = sacc[threadIdx.x >> 5];
+    XdWin win;
+    xd_win_init(win);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        xd_add_product(mine, x[i], y[i], bad);
+        xd_win_add(mine, win, x[i], y[i], bad);
+    xd_win_flush(mine, win);
     __syncthreads();
     for (int t = threadIdx.x; t < XD_DIGITS; t += blockDim.x) {
         unsigned long long s = 0ULL;
 #pragma unroll
         for (int w = 0; w < XD_WARPS; ++w) s += sacc[w][t];
+        if (s) atomicAdd(gacc + t, s);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int t = threadIdx.x; t < XD_DIGITS; t += blockDim.x) sacc[0][t] = atomicExch(gacc + t, 0ULL);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double r = xd_round(sacc[0]);
+    if (*(volatile const int*)bad) r = __longlong_as_double(0x7ff8000000000000LL);
+    if (out) *out = r;
+    if (out_sqrt) *out_sqrt = __dsqrt_rn(r);
+    *ticket = 0u;
+}
+
+// One modified Gram-Schmidt step fused with the next correctly rounded dot
+// product, in one pass: when vprev is given, w_i <- w_i - (h * vprev_i)
+// with h = *hprev (product rounded, then the difference: the same two
+// roundings as a separate update kernel); then <w, y> (y = w itself when
+// null) accumulated exactly and rounded by the last block, as k_xdot.
+static __global__ void __launch_bounds__(XD_THREADS)
+k_mgs_xdot(long long n, double* __restrict__ w, const double* __restrict__ vprev, const double* hprev,
+           const double* __restrict__ y, unsigned long long* __restrict__ gacc, int* bad, unsigned* ticket,
+           double* out, double* out_sqrt)
+{
+    __shared__ unsigned long long sacc[XD_WARPS][XD_DIGITS];
+    __shared__ bool last;
+    for (int t = threadIdx.x; t < XD_WARPS * XD_DIGITS; t += blockDim.x)
+        (&sacc[0][0])[t] = 0ULL;
+    __syncthreads();
+    unsigned long long* mine = sacc[threadIdx.x >> 5];
+    XdWin win;
+    xd_win_init(win);
+    const double h = vprev ? *hprev : 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double wi = w[i];
+        if (vprev) {
+            wi = __dsub_rn(wi, __dmul_rn(h, vprev[i]));
+            w[i] = wi;
+        }
+        xd_win_add(mine, win, wi, y ? y[i] : wi, bad);
+    }
+    xd_win_flush(mine, win);
+    __syncthreads();
+    for (int t = threadIdx.x; t < XD_DIGITS; t += blockDim.x) {
+        unsigned long long s = 0ULL;
+#pragma unroll
+        for (int q = 0; q < XD_WARPS; ++q) s += sacc[q][t];
         if (s) atomicAdd(gacc + t, s);
     }
     __threadfence();

@@ -18,6 +18,7 @@
 #include "dev_util.cuh"
 #include "handle.h"
 #include "solve_internal.cuh"
+#include "worklist.h"
 
 namespace airg {
 void set_last_error(const char* msg);
@@ -39,9 +40,22 @@ struct airg_batch_s {
     std::vector<std::vector<long long>> gk;   // kernels per problem in graphs[j]
     std::vector<long long> rk;                // kernels per problem in rich
     std::vector<airg::DBuf<double>> stage_b, stage_x;   // device copies of host b, x
+    // persistent work-list form: one list and one captured launch per j
+    std::vector<std::shared_ptr<airg::WorkList>> wls;
+    std::vector<cudaGraphExec_t> wgraphs;
+    // optional timing of the iteration launches (airg_batch_profile)
+    bool prof = false;
+    double prof_ms = 0.0;
+    long long prof_launches = 0, prof_bytes = 0;
+    cudaEvent_t pev[2] = {nullptr, nullptr};
+    std::vector<std::vector<long long>> it_bytes;   // [j][p] algorithmic bytes of iteration j
     int m = 0;
     ~airg_batch_s()
     {
+        for (cudaEvent_t e : pev)
+            if (e) cudaEventDestroy(e);
+        for (cudaGraphExec_t g : wgraphs)
+            if (g) cudaGraphExecDestroy(g);
         for (cudaGraphExec_t g : graphs)
             if (g) cudaGraphExecDestroy(g);
         if (rich) cudaGraphExecDestroy(rich);
@@ -170,6 +184,60 @@ cudaGraphExec_t capture_richardson(airg_batch_s& B)
     return exec;
 }
 
+// Iteration j of all problems as one persistent work-list launch, captured
+// (counter reset + kernel) in a graph of its own.
+cudaGraphExec_t capture_worklist(airg_batch_s& B, int j)
+{
+    Off o{B.m};
+    if (!B.wls[j]) {
+        std::vector<airg::WlProblem> probs;
+        for (size_t p = 0; p < B.H.size(); ++p)
+            probs.push_back(airg::WlProblem{B.H[p].get(), B.dv[p].p + o.h1(), B.dv[p].p + o.nrm(), B.act[p].p});
+        B.wls[j] = airg::build_worklist(probs, j, B.master);
+    }
+    CK(cudaStreamBeginCapture(B.master, cudaStreamCaptureModeThreadLocal));
+    try {
+        airg::launch_worklist(*B.wls[j], B.master);
+    } catch (...) {
+        cudaGraph_t g0;
+        cudaStreamEndCapture(B.master, &g0);
+        if (g0) cudaGraphDestroy(g0);
+        throw;
+    }
+    cudaGraph_t graph;
+    CK(cudaStreamEndCapture(B.master, &graph));
+    cudaGraphExec_t exec;
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(e);
+    return exec;
+}
+
+long long iteration_bytes_of(airg_batch_s& B, int p, int j)
+{
+    if (B.it_bytes.size() <= size_t(j)) B.it_bytes.resize(size_t(j) + 1);
+    std::vector<long long>& v = B.it_bytes[size_t(j)];
+    if (v.empty()) {
+        Off o{B.m};
+        for (size_t q = 0; q < B.H.size(); ++q)
+            v.push_back(airg::iteration_bytes(
+                airg::WlProblem{B.H[q].get(), B.dv[q].p + o.h1(), B.dv[q].p + o.nrm(), B.act[q].p}, j));
+    }
+    return v[size_t(p)];
+}
+
+// Form of the lockstep FGMRES iteration: the persistent work list (default
+// where every hierarchy's layout allows it) or one graph with a branch per
+// problem (AIRG_MULTI=graph, or a layout the work list does not implement).
+bool use_worklist(const airg_batch_s& B)
+{
+    const char* e = getenv("AIRG_MULTI");
+    if (e && std::strcmp(e, "graph") == 0) return false;
+    std::vector<airg::Hierarchy*> hs;
+    for (const auto& H : B.H) hs.push_back(H.get());
+    return airg::worklist_supported(hs);
+}
+
 void read_all(airg_batch_s& B, cudaStream_t st)
 {
     Off o{B.m};
@@ -252,6 +320,7 @@ void solve_multi(airg_batch_s& B, const double* const* b, double* const* x, bool
     }
     int its = 0;
     const bool rich = B.H[0]->opt.outer == AIRG_OUTER_RICHARDSON;
+    const bool wl = !rich && use_worklist(B);
     while (rich && its < maxit) {
         // lockstep Richardson; a converged problem keeps its x
         int nact = 0;
@@ -289,10 +358,26 @@ void solve_multi(airg_batch_s& B, const double* const* b, double* const* x, bool
         sync_all(B);
         if (!nact) break;
         for (int j = 0; j < m; ++j) {
-            if (!B.graphs[j]) B.graphs[j] = counted(B.gk[j], [&] { return capture_iteration(B, j); });
-            CK(cudaGraphLaunch(B.graphs[j], B.master));
-            for (int p = 0; p < P; ++p) run[p] += B.gk[j][p];
+            if (wl && !B.wgraphs[j]) B.wgraphs[j] = capture_worklist(B, j);
+            if (!wl && !B.graphs[j]) B.graphs[j] = counted(B.gk[j], [&] { return capture_iteration(B, j); });
+            if (B.prof) CK(cudaEventRecord(B.pev[0], B.master));
+            if (wl) {
+                CK(cudaGraphLaunch(B.wgraphs[j], B.master));
+                run[0] += 1;   // one kernel for all problems
+            } else {
+                CK(cudaGraphLaunch(B.graphs[j], B.master));
+                for (int p = 0; p < P; ++p) run[p] += B.gk[j][p];
+            }
+            if (B.prof) CK(cudaEventRecord(B.pev[1], B.master));
             read_all(B, B.master);
+            if (B.prof) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, B.pev[0], B.pev[1]));
+                B.prof_ms += ms;
+                B.prof_launches += 1;
+                for (int p = 0; p < P; ++p)
+                    if (st[p].active) B.prof_bytes += iteration_bytes_of(B, p, j);
+            }
             ++its;
             // second Gram-Schmidt pass where the first cancelled too much
             bool again = false;
@@ -386,6 +471,10 @@ void solve_multi(airg_batch_s& B, const double* const* b, double* const* x, bool
         }
     }
     sync_all(B);
+    bool gave_up = false;
+    for (auto& w : B.wls)
+        if (w && airg::worklist_timed_out(*w, B.master)) gave_up = true;
+    if (gave_up) fail(AIRG_ERR_TIMEOUT, "a wait of the work-list kernel gave up");
     double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (infos)
         for (int p = 0; p < P; ++p) infos[p].solve_ms = ms;
@@ -433,6 +522,8 @@ airg_status airg_setup_batch(int nprob, const airg_csr* As, const airg_options* 
         B->hbuf.alloc(size_t(nprob) * of.total());
         B->graphs.assign(size_t(B->m), nullptr);
         B->gk.assign(size_t(B->m), {});
+        B->wls.assign(size_t(B->m), nullptr);
+        B->wgraphs.assign(size_t(B->m), nullptr);
         B->stage_b.resize(size_t(nprob));
         B->stage_x.resize(size_t(nprob));
         *out = B.release();
@@ -448,6 +539,28 @@ airg_status airg_solve_batch(airg_batch* b, const double* const* bvec, double* c
         for (size_t p = 0; p < b->H.size(); ++p)
             if (!bvec[p] || !xvec[p]) fail(AIRG_ERR_ARG, "null vector in the batch");
         solve_multi(*b, bvec, xvec, on_device != 0, rtol, atol, maxit, infos, (cudaStream_t)stream);
+    });
+}
+
+airg_status airg_batch_profile(airg_batch* b, int enable)
+{
+    return guarded([&] {
+        if (!b) fail(AIRG_ERR_ARG, "null batch");
+        for (cudaEvent_t& e : b->pev)
+            if (!e) CK(cudaEventCreate(&e));
+        b->prof = enable != 0;
+        b->prof_ms = 0.0;
+        b->prof_launches = b->prof_bytes = 0;
+    });
+}
+
+airg_status airg_batch_profile_read(const airg_batch* b, double* ms, int64_t* launches, int64_t* bytes)
+{
+    return guarded([&] {
+        if (!b || !ms || !launches || !bytes) fail(AIRG_ERR_ARG, "bad batch profile arguments");
+        *ms = b->prof_ms;
+        *launches = b->prof_launches;
+        *bytes = b->prof_bytes;
     });
 }
 

@@ -417,14 +417,6 @@ __global__ void k_spmv_det(int n, const int* rp, const int* ci, const double* v,
     y[i] = s;
 }
 
-__global__ void k_axpy_dev(long long n, double* w, const double* vi, const double* h)
-{
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double hh = *h;
-    w[i] = __dsub_rn(w[i], __dmul_rn(hh, vi[i]));
-}
-
 __global__ void k_div_dev(long long n, double* out, const double* w, const double* h)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -838,6 +830,19 @@ void xdot(Ctx& c, long long n, const double* x, const double* y, double* out, do
     ++c.ndots;
 }
 
+// MGS step w -= (*hprev) vprev (skipped when vprev is null) fused with the
+// correctly rounded <w, y> (y null: <w, w>) into out / out_sqrt.
+void mgs_xdot(Ctx& c, long long n, double* w, const double* vprev, const double* hprev, const double* y,
+              double* out, double* out_sqrt)
+{
+    int grid = (int)std::min<long long>(std::max<long long>(1, (n + XD_THREADS - 1) / XD_THREADS),
+                                        2LL * num_sms());
+    k_mgs_xdot<<<grid, XD_THREADS, 0, c.st>>>(n, w, vprev, hprev, y, c.xacc.p, c.xbad.p, c.xticket.p, out,
+                                               out_sqrt);
+    CK_LAUNCH();
+    ++c.ndots;
+}
+
 // Wall time of one setup phase, added to *acc: the stream is synchronised
 // when the phase starts and when it ends, so the time covers the phase's
 // kernels and its host work and nothing else.
@@ -1021,14 +1026,15 @@ ArnoldiOut arnoldi(Ctx& c, const DevCSR& A, const double* b, int m, double tol, 
     for (int j = 0; j < m; ++j) {
         k_spmv_det<<<grid_for(n, TB), TB, 0, st>>>(int(n), A.rp.p, A.ci.p, A.v.p, V.p + size_t(j) * n, w.p);
         CK_LAUNCH();
+        // h_ij = <w, v_i> then w -= h_ij v_i, for i = 0..j (modified
+        // Gram-Schmidt); each update is fused with the next dot product
         for (int i = 0; i <= j; ++i) {
             double* hij = Hd.p + size_t(i) * m + j;
-            xdot(c, n, w.p, V.p + size_t(i) * n, hij, nullptr);
-            k_axpy_dev<<<g, TB, 0, st>>>(n, w.p, V.p + size_t(i) * n, hij);
-            CK_LAUNCH();
+            const double* hprev = i ? Hd.p + size_t(i - 1) * m + j : nullptr;
+            mgs_xdot(c, n, w.p, i ? V.p + size_t(i - 1) * n : nullptr, hprev, V.p + size_t(i) * n, hij, nullptr);
         }
         double* hn = Hd.p + size_t(j + 1) * m + j;
-        xdot(c, n, w.p, w.p, nullptr, hn);
+        mgs_xdot(c, n, w.p, V.p + size_t(j) * n, Hd.p + size_t(j) * m + j, nullptr, nullptr, hn);
         // read column j (rows 0..j+1)
         for (int i = 0; i <= j + 1; ++i)
             CK(cudaMemcpyAsync(&col[i], Hd.p + size_t(i) * m + j, sizeof(double),

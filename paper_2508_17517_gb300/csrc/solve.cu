@@ -23,6 +23,9 @@
 #include <cstring>
 #include <initializer_list>
 #include <string>
+#include <type_traits>
+#include <unordered_map>
+#include <mutex>
 
 #include "dev_util.cuh"
 #include "handle.h"
@@ -133,6 +136,26 @@ void build_sell(const DevCSR& A, const int* src_row, const int* cmap, int n_cols
 
 template <class T>
 void sell_to_f32(const Sell<double>& S, Sell<T>& out, cudaStream_t st);
+
+__global__ void k_col16(long long n, const int* __restrict__ col, unsigned short* __restrict__ col16)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) col16[i] = (unsigned short)col[i];
+}
+
+// 16-bit copy of the column indices of a long-row operator with at most
+// 65536 columns (the coarsest operator): its single-vector row kernels then
+// read 2 instead of 4 bytes of index per entry, with the same values.
+// AIRG_COL16=0 keeps 32-bit indices (for comparison).
+template <class T>
+void add_col16(Sell<T>& S, cudaStream_t st)
+{
+    const char* e = getenv("AIRG_COL16");
+    if ((e && e[0] == '0') || S.k < 2 || S.n_cols > 65536 || S.padded == 0) return;
+    S.col16.alloc(size_t(S.padded));
+    k_col16<<<grid_for(S.padded, TB), TB, 0, st>>>(S.padded, S.col.p, S.col16.p);
+    CK_LAUNCH();
+}
 
 __global__ void k_d2f(long long n, const double* a, float* b)
 {
@@ -254,9 +277,18 @@ __global__ void k_invert_perm(int n, const int* perm, int* inv)
 // each lane keeps U requests in flight; the remainder runs in chunks of 4,
 // so at most 3 issued slots per row carry no entry (predicated slots still
 // occupy the FP64 pipe, which is the scarce unit for FP64 on this part).
-template <class T, int U = 4, class V = T>
-__device__ __forceinline__ T strided_dot(const int* __restrict__ col, const V* __restrict__ val,
-                                         const T* __restrict__ x, int idx, int end, int stride)
+template <bool C16>
+__device__ __forceinline__ int ldcol(const int* __restrict__ col, const unsigned short* __restrict__ col16, int i)
+{
+    if constexpr (C16) return int(__ldg(col16 + i));
+    else return __ldg(col + i);
+}
+
+// C16: column indices from the 16-bit copy (same values)
+template <class T, int U = 4, class V = T, bool C16 = false>
+__device__ __forceinline__ T strided_dot(const int* __restrict__ col, const unsigned short* __restrict__ col16,
+                                         const V* __restrict__ val, const T* __restrict__ x, int idx, int end,
+                                         int stride)
 {
     static_assert(U % 4 == 0, "U must be a multiple of 4");
     T a[4] = {T(0), T(0), T(0), T(0)};
@@ -265,7 +297,7 @@ __device__ __forceinline__ T strided_dot(const int* __restrict__ col, const V* _
         T v[U], xv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            c[u] = __ldg(col + idx + u * stride);
+            c[u] = ldcol<C16>(col, col16, idx + u * stride);
             v[u] = ldval<T>(val + idx + u * stride);
         }
 #pragma unroll
@@ -279,7 +311,7 @@ __device__ __forceinline__ T strided_dot(const int* __restrict__ col, const V* _
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const bool ok = idx + u * stride < end;
-            c[u] = ok ? __ldg(col + idx + u * stride) : 0;
+            c[u] = ok ? ldcol<C16>(col, col16, idx + u * stride) : 0;
             v[u] = ok ? ldval<T>(val + idx + u * stride) : T(0);
         }
 #pragma unroll
@@ -295,14 +327,15 @@ __device__ __forceinline__ T strided_dot(const int* __restrict__ col, const V* _
 // that share the slice (part = this warp's index among them).  Every thread
 // of the block must call it (it synchronises the block when P > 1).  The
 // sum is valid in the part-0 warp, which also adds the dense diagonal.
-template <class T, int P, int U = 4, class V = T>
+template <class T, int P, int U = 4, class V = T, bool C16 = false>
 __device__ __forceinline__ T row_dot(const SellView<T, V>& S, int slice, int lane, int part,
                                      const T* __restrict__ x)
 {
     T acc = T(0);
     if (slice < S.n_slices) {
         int b = S.sptr[slice], w = (S.sptr[slice + 1] - b) >> 5;
-        acc = strided_dot<T, U>(S.col, S.val, x, b + lane + 32 * part, b + lane + 32 * w, 32 * P);
+        acc = strided_dot<T, U, V, C16>(S.col, S.col16, S.val, x, b + lane + 32 * part, b + lane + 32 * w,
+                                        32 * P);
     }
     if (P > 1) {
         __shared__ T red[32][32];
@@ -391,35 +424,44 @@ __device__ __forceinline__ void dot_slices(const SellView<T, V>& S, const T* __r
 // overlap them.  K = warps per slice.  R = slices per warp for K = 1, and
 // loads in flight per lane (4, 8 or 16) for K > 1; in neither case does R
 // change the arithmetic.
-template <class T, int K, int R, class V, class Pre, class Epi>
+template <class T, int K, int R, bool C16 = false, class V, class Pre, class Epi>
 __device__ __forceinline__ void for_rows(const SellView<T, V>& S, const T* __restrict__ x, const Pre& pre,
                                          const Epi& epi)
 {
+    static_assert(!C16 || K > 1, "16-bit columns are read by the long-row path only");
     using PV = decltype(pre(0));
     const int lane = threadIdx.x & 31;
+    // A grid smaller than the operator's (a resident grid, Sell::persist)
+    // strides over the slices; each row is computed the same way either way.
     if constexpr (K == 1) {
-        const int s0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * R;
-        PV pv[R];
+        const int nw = (gridDim.x * blockDim.x) >> 5;
+        for (int s0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * R; s0 < S.n_slices; s0 += nw * R) {
+            PV pv[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int r = (s0 + q) * 32 + lane;
-            pv[q] = r < S.n_rows ? pre(r) : PV{};
-        }
-        T acc[R];
-        dot_slices<T, R, V>(S, x, s0, lane, acc);
+            for (int q = 0; q < R; ++q) {
+                const int r = (s0 + q) * 32 + lane;
+                pv[q] = r < S.n_rows ? pre(r) : PV{};
+            }
+            T acc[R];
+            dot_slices<T, R, V>(S, x, s0, lane, acc);
 #pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int r = (s0 + q) * 32 + lane;
-            if (r < S.n_rows) epi(r, acc[q], pv[q]);
+            for (int q = 0; q < R; ++q) {
+                const int r = (s0 + q) * 32 + lane;
+                if (r < S.n_rows) epi(r, acc[q], pv[q]);
+            }
         }
     } else {
+        constexpr int SPB = wpb_for(K) / K;   // slices per block-group
         const int part = (threadIdx.x >> 5) % K;
-        const int slice = blockIdx.x * (wpb_for(K) / K) + (threadIdx.x >> 5) / K;
-        const int r = slice * 32 + lane;
-        const bool lead = part == 0 && r < S.n_rows;
-        PV pv = lead ? pre(r) : PV{};
-        T d = row_dot<T, K, R, V>(S, slice, lane, part, x);
-        if (lead) epi(r, d, pv);
+        const int ngroups = (S.n_slices + SPB - 1) / SPB;
+        for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {   // uniform over the block
+            const int slice = g * SPB + (threadIdx.x >> 5) / K;
+            const int r = slice * 32 + lane;
+            const bool lead = part == 0 && r < S.n_rows;
+            PV pv = lead ? pre(r) : PV{};
+            T d = row_dot<T, K, R, V, C16>(S, slice, lane, part, x);
+            if (lead) epi(r, d, pv);
+        }
     }
 }
 
@@ -429,10 +471,10 @@ struct Pair {
 };
 
 // y = S x
-template <class T, int K, int R, class V = T>
+template <class T, int K, int R, class V = T, bool C16 = false>
 __global__ void k_spmv(SellView<T, V> S, const T* __restrict__ x, T* __restrict__ y)
 {
-    for_rows<T, K, R>(S, x, [](int) { return 0; }, [&](int r, T d, int) { y[r] = d; });
+    for_rows<T, K, R, C16>(S, x, [](int) { return 0; }, [&](int r, T d, int) { y[r] = d; });
 }
 
 // restriction (R = [Z I] of Eq. 4): dst_c[k] = src_c[k] + (Z src_f)[k]; the
@@ -518,11 +560,11 @@ __global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b)
 
 // Newton steps of the coarse polynomial (Sec. 2.3)
 // real root, not the last: x += r / theta, r' = r - A r / theta
-template <class T, int K, int R>
+template <class T, int K, int R, bool C16 = false>
 __global__ void k_newton_real(SellView<T> A, const T* __restrict__ rin, T* __restrict__ rout,
                               T* __restrict__ x, T inv_theta, int first)
 {
-    for_rows<T, K, R>(A, rin, [&](int r) { return Pair<T>{rin[r], first ? T(0) : x[r]}; },
+    for_rows<T, K, R, C16>(A, rin, [&](int r) { return Pair<T>{rin[r], first ? T(0) : x[r]}; },
                       [&](int r, T d, Pair<T> q) {
                           x[r] = fma(q.a, inv_theta, q.b);
                           rout[r] = q.a - d * inv_theta;
@@ -538,11 +580,11 @@ __global__ void k_newton_last(int n, const T* __restrict__ rin, T* __restrict__ 
     x[r] = fma(rin[r], inv_theta, first ? T(0) : x[r]);
 }
 
-template <class T, int K, int R>
+template <class T, int K, int R, bool C16 = false>
 __global__ void k_newton_pair1(SellView<T> A, const T* __restrict__ rin, T* __restrict__ t,
                                T* __restrict__ x, T two_a, T inv_mod2, int first)
 {
-    for_rows<T, K, R>(A, rin, [&](int r) { return Pair<T>{rin[r], first ? T(0) : x[r]}; },
+    for_rows<T, K, R, C16>(A, rin, [&](int r) { return Pair<T>{rin[r], first ? T(0) : x[r]}; },
                       [&](int r, T d, Pair<T> q) {
                           T tt = two_a * q.a - d;
                           t[r] = tt;
@@ -550,11 +592,11 @@ __global__ void k_newton_pair1(SellView<T> A, const T* __restrict__ rin, T* __re
                       });
 }
 
-template <class T, int K, int R>
+template <class T, int K, int R, bool C16 = false>
 __global__ void k_newton_pair2(SellView<T> A, const T* __restrict__ rin, const T* __restrict__ t,
                                T* __restrict__ rout, T inv_mod2)
 {
-    for_rows<T, K, R>(A, t, [&](int r) { return rin[r]; },
+    for_rows<T, K, R, C16>(A, t, [&](int r) { return rin[r]; },
                       [&](int r, T d, T ri) { rout[r] = ri - d * inv_mod2; });
 }
 
@@ -667,12 +709,35 @@ inline int bk(int P) { return 32 * wpb_for(P); }
 
 // Grid and block of the row kernels for operator S: K = S.k warps per slice,
 // or (K = 1) S.r slices per warp.
-template <class T, class V>
-inline int grid_rows(const Sell<T, V>& S)
+// Blocks of `kernel` that fit on the GPU at once (block size `block`),
+// looked up once per kernel.
+template <class F>
+int resident_grid(F* kernel, int block)
 {
-    if (S.k > 1) return gk(S.n_rows, S.k);
-    long long warps = (S.n_slices + S.r - 1) / S.r;
-    return grid_for(warps, wpb_for(1));
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(reinterpret_cast<const void*>(kernel));
+    if (it != cache.end()) return it->second;
+    int dev = 0, sms = 0, per = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, 0));
+    const int g = std::max(1, per * sms);
+    cache[reinterpret_cast<const void*>(kernel)] = g;
+    return g;
+}
+
+// Grid of a row kernel for operator S: one block per group of slices (or
+// warp per R slices), or with S.persist the resident blocks of `kernel`.
+template <class T, class V, class F>
+inline int grid_rows(const Sell<T, V>& S, F* kernel)
+{
+    int g;
+    if (S.k > 1) g = gk(S.n_rows, S.k);
+    else g = grid_for((S.n_slices + S.r - 1) / S.r, wpb_for(1));
+    if (S.persist) g = std::min(g, resident_grid(kernel, bk(S.k)));
+    return g;
 }
 template <class T, class V>
 inline int block_rows(const Sell<T, V>& S) { return bk(S.k); }
@@ -696,6 +761,24 @@ inline int block_rows(const Sell<T, V>& S) { return bk(S.k); }
                 case 16: { constexpr int RR = 16; WITH_K_LONG((S).k, __VA_ARGS__); } break; \
                 default: fail(AIRG_ERR_STATE, "bad loads-per-lane");            \
             }                                                                   \
+        }                                                                       \
+    } while (0)
+
+// WITH_KR with the compile-time flag C16 = whether S's row kernels read
+// its 16-bit column indices (long rows only).
+#define WITH_KR_COL(S, ...)                                                     \
+    do {                                                                        \
+        if ((S).col16.n) {                                                      \
+            constexpr bool C16 = true;                                          \
+            switch ((S).r) {                                                    \
+                case 4: { constexpr int RR = 4; WITH_K_LONG((S).k, __VA_ARGS__); } break;   \
+                case 8: { constexpr int RR = 8; WITH_K_LONG((S).k, __VA_ARGS__); } break;   \
+                case 16: { constexpr int RR = 16; WITH_K_LONG((S).k, __VA_ARGS__); } break; \
+                default: fail(AIRG_ERR_STATE, "bad loads-per-lane");            \
+            }                                                                   \
+        } else {                                                                \
+            constexpr bool C16 = false;                                         \
+            WITH_KR(S, __VA_ARGS__);                                            \
         }                                                                       \
     } while (0)
 
@@ -851,7 +934,7 @@ __device__ __forceinline__ T row_dot_rt(const SellView<T>& S, int slice, int lan
     T acc = T(0);
     if (slice < S.n_slices) {
         int b = S.sptr[slice], w = (S.sptr[slice + 1] - b) >> 5;
-        acc = strided_dot(S.col, S.val, x, b + lane + 32 * part, b + lane + 32 * w, 32 * P);
+        acc = strided_dot(S.col, S.col16, S.val, x, b + lane + 32 * part, b + lane + 32 * w, 32 * P);
     }
     if (P > 1) {
         const int warp = threadIdx.x >> 5;
@@ -1131,10 +1214,10 @@ void f_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
         // assembled smoother (Eq. 8 matrix): t = r_f - M e_c, then
         // e_f = W e_c + Ahat^-1 t, the last Horner kernel with a0 = 0
         LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
-                 WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M), block_rows(o.M), 0, st>>>(
+                 WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M, k_fresid<T, KK, RR>), block_rows(o.M), 0, st>>>(
                                   view(o.M), rf, ec, wk.t, wk.wa, T(0))));
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, 2 * o.Ainv.nnz + 3LL * nf,
-                 WITH_KR(o.Ainv, k_horner_last<T, KK, RR><<<grid_rows(o.Ainv), block_rows(o.Ainv), 0, st>>>(
+                 WITH_KR(o.Ainv, k_horner_last<T, KK, RR><<<grid_rows(o.Ainv, k_horner_last<T, KK, RR>), block_rows(o.Ainv), 0, st>>>(
                                      view(o.Ainv), wk.t, wk.t, ec, lv.W.p, ef, T(0))));
         return;
     }
@@ -1163,7 +1246,7 @@ void f_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
         return;
     }
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
-           WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M), block_rows(o.M), 0, st>>>(
+           WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M, k_fresid<T, KK, RR>), block_rows(o.M), 0, st>>>(
                             view(o.M), rf, ec, wk.t, wk.wa, T(lv.alpha[p]))));
     if (p == 0) {
         LAUNCH_F(S, PK_HORNER, 3 * fB + 4LL * nf, 3LL * nf,
@@ -1175,12 +1258,12 @@ void f_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
     T* wout = wk.wb;
     for (int k = p - 1; k >= 1; --k) {
         LAUNCH_F(S, PK_HORNER, hB, 2 * o.Aff.nnz + 2LL * nf,
-               WITH_KR(o.Aff, k_horner<T, KK, RR><<<grid_rows(o.Aff), block_rows(o.Aff), 0, st>>>(
+               WITH_KR(o.Aff, k_horner<T, KK, RR><<<grid_rows(o.Aff, k_horner<T, KK, RR>), block_rows(o.Aff), 0, st>>>(
                                   view(o.Aff), wk.t, win, wout, T(lv.alpha[k]))));
         std::swap(win, wout);
     }
     LAUNCH_F(S, PK_HORNER, hB + fB + 4LL * nf, 2 * o.Aff.nnz + 3LL * nf,
-           WITH_KR(o.Aff, k_horner_last<T, KK, RR><<<grid_rows(o.Aff), block_rows(o.Aff), 0, st>>>(
+           WITH_KR(o.Aff, k_horner_last<T, KK, RR><<<grid_rows(o.Aff, k_horner_last<T, KK, RR>), block_rows(o.Aff), 0, st>>>(
                               view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0]))));
 }
 
@@ -1202,12 +1285,12 @@ void horner_into(SolveData& S, const Sell<T>& A, const std::vector<double>& al, 
     T* wout = wk.wb;
     for (int k = p - 1; k >= 1; --k) {
         LAUNCH_F(S, PK_HORNER, hB, 2 * A.nnz + 2LL * n,
-                 WITH_KR(A, k_horner<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(view(A), wk.t, win,
+                 WITH_KR(A, k_horner<T, KK, RR><<<grid_rows(A, k_horner<T, KK, RR>), block_rows(A), 0, st>>>(view(A), wk.t, win,
                                                                                         wout, T(al[k]))));
         std::swap(win, wout);
     }
     LAUNCH_F(S, PK_HORNER, hB + fB, 2 * A.nnz + 3LL * n,
-             WITH_KR(A, k_horner_acc<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(view(A), wk.t, win, e,
+             WITH_KR(A, k_horner_acc<T, KK, RR><<<grid_rows(A, k_horner_acc<T, KK, RR>), block_rows(A), 0, st>>>(view(A), wk.t, win, e,
                                                                                         T(al[0]))));
 }
 
@@ -1226,11 +1309,11 @@ void c_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
     const int p = int(lv.alpha_c.size()) - 1;
     const long long cB = (long long)nc * VB;
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mc) + (long long)(lv.n_f + nc) * VB + 3 * cB, 2 * o.Mc.nnz + 2LL * nc,
-             WITH_KR(o.Mc, k_fresid<T, KK, RR><<<grid_rows(o.Mc), block_rows(o.Mc), 0, st>>>(
+             WITH_KR(o.Mc, k_fresid<T, KK, RR><<<grid_rows(o.Mc, k_fresid<T, KK, RR>), block_rows(o.Mc), 0, st>>>(
                               view(o.Mc), rc, el, wk.t, wk.wa, T(lv.alpha_c[p]))));
     if (o.Ainvc.n_rows) {   // assembled: e_c += Ahat_cc^-1 t_c
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainvc) + 4 * cB, 2 * o.Ainvc.nnz + 2LL * nc,
-                 WITH_KR(o.Ainvc, k_horner_acc<T, KK, RR><<<grid_rows(o.Ainvc), block_rows(o.Ainvc), 0, st>>>(
+                 WITH_KR(o.Ainvc, k_horner_acc<T, KK, RR><<<grid_rows(o.Ainvc, k_horner_acc<T, KK, RR>), block_rows(o.Ainvc), 0, st>>>(
                                      view(o.Ainvc), wk.t, wk.t, el + lv.n_f, T(0))));
         return;
     }
@@ -1251,11 +1334,11 @@ void f_smooth_again(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, c
     const int p = int(lv.alpha.size()) - 1;
     const long long fB = (long long)nf * VB;
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mf) + (long long)(nf + lv.n_c) * VB + 3 * fB, 2 * o.Mf.nnz + 2LL * nf,
-             WITH_KR(o.Mf, k_fresid<T, KK, RR><<<grid_rows(o.Mf), block_rows(o.Mf), 0, st>>>(
+             WITH_KR(o.Mf, k_fresid<T, KK, RR><<<grid_rows(o.Mf, k_fresid<T, KK, RR>), block_rows(o.Mf), 0, st>>>(
                               view(o.Mf), rf, el, wk.t, wk.wa, T(lv.alpha[p]))));
     if (o.Ainv.n_rows) {    // assembled: e_f += Ahat_ff^-1 t
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB, 2 * o.Ainv.nnz + 2LL * nf,
-                 WITH_KR(o.Ainv, k_horner_acc<T, KK, RR><<<grid_rows(o.Ainv), block_rows(o.Ainv), 0, st>>>(
+                 WITH_KR(o.Ainv, k_horner_acc<T, KK, RR><<<grid_rows(o.Ainv, k_horner_acc<T, KK, RR>), block_rows(o.Ainv), 0, st>>>(
                                     view(o.Ainv), wk.t, wk.t, el, T(0))));
         return;
     }
@@ -1281,12 +1364,12 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
                                                                     wk.rcs + lv.rc_off));
         if (lv.n_c && Zb.val.n)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Zb) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Zb.nnz + lv.n_c,
-                   WITH_KR(Zb, k_restrict<T, KK, RR, bf16s><<<grid_rows(Zb), block_rows(Zb), 0, st>>>(
+                   WITH_KR(Zb, k_restrict<T, KK, RR, bf16s><<<grid_rows(Zb, k_restrict<T, KK, RR, bf16s>), block_rows(Zb), 0, st>>>(
                                    view(Zb), src + lv.off, src + lv.off + lv.n_f,
                                    wk.rwork + lv.off + lv.n_f)));
         else if (lv.n_c)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Z.nnz + lv.n_c,
-                   WITH_KR(Z, k_restrict<T, KK, RR><<<grid_rows(Z), block_rows(Z), 0, st>>>(
+                   WITH_KR(Z, k_restrict<T, KK, RR><<<grid_rows(Z, k_restrict<T, KK, RR>), block_rows(Z), 0, st>>>(
                                   view(Z), src + lv.off, src + lv.off + lv.n_f,
                                   wk.rwork + lv.off + lv.n_f)));
     }
@@ -1344,7 +1427,7 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
                                                Av, rin, A.n_cols, rout, x, T(1.0 / q.re), i == 0)));
                 else
                     LAUNCH_F(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB, 2 * A.nnz + 4LL * nco,
-                           WITH_KR(A, k_newton_real<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
+                           WITH_KR_COL(A, k_newton_real<T, KK, RR, C16><<<grid_rows(A, k_newton_real<T, KK, RR, C16>), block_rows(A), 0, st>>>(
                                           Av, rin, rout, x, T(1.0 / q.re), i == 0)));
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
@@ -1354,7 +1437,7 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
                                                Av, rin, A.n_cols, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
                 else
                     LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, 2 * A.nnz + 4LL * nco,
-                           WITH_KR(A, k_newton_pair1<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
+                           WITH_KR_COL(A, k_newton_pair1<T, KK, RR, C16><<<grid_rows(A, k_newton_pair1<T, KK, RR, C16>), block_rows(A), 0, st>>>(
                                           Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
                 if (!last && A.xs)
                     LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
@@ -1362,7 +1445,7 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
                                                Av, rin, wk.ct, A.n_cols, rout, T(1.0 / mod2))));
                 else if (!last)
                     LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
-                           WITH_KR(A, k_newton_pair2<T, KK, RR><<<grid_rows(A), block_rows(A), 0, st>>>(
+                           WITH_KR_COL(A, k_newton_pair2<T, KK, RR, C16><<<grid_rows(A, k_newton_pair2<T, KK, RR, C16>), block_rows(A), 0, st>>>(
                                           Av, rin, wk.ct, rout, T(1.0 / mod2))));
             }
             if (!last) { rin = rout; nb ^= 1; }
@@ -1388,51 +1471,68 @@ long long sell_bytes(const Sell<double>& S, int vbytes)
 {
     // values + column indices (none for a dense diagonal) + one read of the
     // gathered input + one write
-    return (S.nnz - S.ndiag) * (vbytes + 4) + S.ndiag * vbytes + 2LL * S.n_rows * vbytes;
+    return (S.nnz - S.ndiag) * (vbytes + (S.col16.n ? 2 : 4)) + S.ndiag * vbytes + 2LL * S.n_rows * vbytes;
 }
 
 // Row-kernel variant of every operator, picked by timing y = S x: slices
 // per warp r = 1, 2, 4 for short rows (one warp per slice), loads in flight
-// per lane r = 4, 8, 16 for long rows (several warps per slice).  Neither
-// changes the arithmetic.  forced > 0 (AIRG_ROWS_PER_WARP for short rows,
-// AIRG_LOADS_PER_LANE for long rows) skips the timing.
+// per lane r = 4, 8, 16 for long rows (several warps per slice), each with
+// the operator's own grid or a resident grid striding over the slices
+// (persist; it removes the partly idle last wave).  None of them changes
+// the arithmetic.  forced > 0 (AIRG_ROWS_PER_WARP for short rows,
+// AIRG_LOADS_PER_LANE for long rows) fixes r, AIRG_PERSIST_GRID=0|1 the
+// grid; with both fixed nothing is timed.
 // Returns the time of 3 launches of the chosen variant (0 when not timed).
 template <class T, class V>
 float tune_rows(Sell<T, V>& A, const T* x, T* y, int forced_short, int forced_long, cudaStream_t st)
 {
     if (A.n_rows == 0) return 0.f;
     const int forced = A.k == 1 ? forced_short : forced_long;
-    if (forced) {
+    const char* pe = getenv("AIRG_PERSIST_GRID");
+    const int forced_p = pe && (pe[0] == '0' || pe[0] == '1') ? pe[0] - '0' : -1;
+    if (forced && forced_p >= 0) {
         A.r = forced;
+        A.persist = forced_p;
         return 0.f;
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 0.f;
-    int best_r = A.k == 1 ? 1 : 4;
+    int best_r = A.k == 1 ? 1 : 4, best_p = 0;
     const int cand_short[3] = {1, 2, 4}, cand_long[3] = {4, 8, 16};
     const int* cand = A.k == 1 ? cand_short : cand_long;
-    for (int ci = 0; ci < 3; ++ci) {
-        A.r = cand[ci];
+    bool first = true;
+    for (int ci = 0; ci < 6; ++ci) {
+        A.r = forced ? forced : cand[ci % 3];
+        A.persist = ci / 3;
+        if ((forced && ci % 3) || (forced_p >= 0 && A.persist != forced_p)) continue;
         SellView<T, V> v = view(A);
-        WITH_KR(A, k_spmv<T, KK, RR, V><<<grid_rows(A), block_rows(A), 0, st>>>(v, x, y));
+        auto launch = [&]() {
+            if constexpr (std::is_same<T, V>::value)
+                WITH_KR_COL(A, k_spmv<T, KK, RR, V, C16><<<grid_rows(A, k_spmv<T, KK, RR, V, C16>), block_rows(A), 0, st>>>(v, x, y));
+            else
+                WITH_KR(A, k_spmv<T, KK, RR, V><<<grid_rows(A, k_spmv<T, KK, RR, V>), block_rows(A), 0, st>>>(v, x, y));
+        };
+        launch();
         CK_LAUNCH();
         CK(cudaEventRecord(e0, st));
-        for (int rep = 0; rep < 3; ++rep)
-            WITH_KR(A, k_spmv<T, KK, RR, V><<<grid_rows(A), block_rows(A), 0, st>>>(v, x, y));
+        for (int rep = 0; rep < 3; ++rep) launch();
         CK(cudaEventRecord(e1, st));
         CK(cudaEventSynchronize(e1));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ci == 0 || ms < best) {
+        if (first || ms < best) {
             best = ms;
-            best_r = cand[ci];
+            best_r = A.r;
+            best_p = A.persist;
+            first = false;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     A.r = best_r;
+    A.persist = best_p;
     return best;
 }
 
@@ -1694,6 +1794,8 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
     }
     build_sell<double>(H.coarse.A, iperm[L].p, perm[L].p, S->n_coarse, S->Ac, true, st);
     if (mixed_precision(H.opt)) copy_sell_f32(S->Ac, S->Ac32, st);
+    add_col16(S->Ac, st);
+    add_col16(S->Ac32, st);
     S->roots = H.coarse.roots;
     {
         std::vector<double> rr;
@@ -1926,7 +2028,7 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
     int its = 0;
     auto residual = [&]() {
         LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz,
-               WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop), block_rows(S.Atop), 0, st>>>(A, S.xp.p, S.w.p)));
+               WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop, k_spmv<double, KK, RR>), block_rows(S.Atop), 0, st>>>(A, S.xp.p, S.w.p)));
         LAUNCH_F(S, PK_KRYLOV, 24 * n, n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
         CK_LAUNCH();
         return dev_norm(S, S.r.p, n, st);
@@ -1944,7 +2046,7 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             double* zj = S.Zs.p + size_t(j) * n;
             precond(H, vj, zj, st);
             LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz,
-                   WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop), block_rows(S.Atop), 0, st>>>(A, zj, S.w.p)));
+                   WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop, k_spmv<double, KK, RR>), block_rows(S.Atop), 0, st>>>(A, zj, S.w.p)));
             // classical Gram-Schmidt; a second pass only when the first
             // one cancelled more than half of ||w||^2 ("twice is enough",
             // Daniel, Gragg, Kaufman & Stewart 1976): ||w'|| < ||w|| / sqrt(2)
@@ -2019,7 +2121,7 @@ void richardson(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_in
     double tol = std::max(rtol * bn, atol);
     auto residual = [&]() {
         LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz,
-               WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop), block_rows(S.Atop), 0, st>>>(A, S.xp.p, S.w.p)));
+               WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop, k_spmv<double, KK, RR>), block_rows(S.Atop), 0, st>>>(A, S.xp.p, S.w.p)));
         LAUNCH_F(S, PK_KRYLOV, 24 * n, n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
         CK_LAUNCH();
         return dev_norm(S, S.r.p, n, st);
@@ -2061,7 +2163,7 @@ void mp_top_spmv(Hierarchy& H, const double* x, double* y, cudaStream_t st)
     long long n = S.n0;
     SellView<double> A = view(S.Atop);
     LAUNCH_F(S, PK_TOPSPMV, mat_bytes(S.Atop) + 16 * n, 2 * S.Atop.nnz,
-           WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop), block_rows(S.Atop), 0, st>>>(A, x, y)));
+           WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop, k_spmv<double, KK, RR>), block_rows(S.Atop), 0, st>>>(A, x, y)));
 }
 
 void mp_multidot(Hierarchy& H, int m, const double* V, const double* w, double* out, int selfdot,

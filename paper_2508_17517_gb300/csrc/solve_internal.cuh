@@ -50,13 +50,20 @@ struct bf16s {
     unsigned short bits;
 };
 
+//
+// col16: the same column indices in 16 bits, kept for long-row operators
+// with at most 65536 columns (the coarsest operator): their single-vector
+// row kernels read 2 instead of 4 bytes of index per entry.  `col` stays
+// for the kernels that do not read col16.
 template <class T, class V = T>
 struct Sell {
     int n_rows = 0, n_cols = 0, n_slices = 0, k = 1, r = 1;
+    int persist = 0;   // 1: row kernels run on a grid of resident blocks that stride over the slices
     int xs = 0;   // coarsest operator only: > 0 = its SpMVs stage x in shared memory, on xs blocks (solve.cu)
     long long nnz = 0, padded = 0, ndiag = 0;
     DBuf<int> sptr;
     DBuf<int> col;
+    DBuf<unsigned short> col16;
     DBuf<V> val;
     DBuf<T> diag;
 };
@@ -68,12 +75,14 @@ struct SellView {
     const int* __restrict__ col;
     const V* __restrict__ val;
     const T* __restrict__ diag;   // nullptr: no diagonal split
+    const unsigned short* __restrict__ col16;   // nullptr: none
 };
 
 template <class T, class V>
 SellView<T, V> view(const Sell<T, V>& s)
 {
-    return SellView<T, V>{s.n_rows, s.n_slices, s.sptr.p, s.col.p, s.val.p, s.ndiag ? s.diag.p : nullptr};
+    return SellView<T, V>{s.n_rows, s.n_slices, s.sptr.p, s.col.p, s.val.p, s.ndiag ? s.diag.p : nullptr,
+                          s.col16.n ? s.col16.p : nullptr};
 }
 
 // stored value -> arithmetic type
@@ -93,12 +102,13 @@ __device__ __forceinline__ double ldval<double, bf16s>(const bf16s* p)
     return double(ldval<float, bf16s>(p));
 }
 
-// algorithmic bytes of the stored entries: value + 4-byte column index per
-// entry, value only for a diagonal held densely
+// algorithmic bytes of the stored entries: value + column index per entry
+// (2 bytes when the row kernels read col16, else 4), value only for a
+// diagonal held densely
 template <class T, class V>
 long long mat_bytes(const Sell<T, V>& s)
 {
-    return (s.nnz - s.ndiag) * (long long)(sizeof(V) + 4) + s.ndiag * (long long)sizeof(T);
+    return (s.nnz - s.ndiag) * (long long)(sizeof(V) + (s.col16.n ? 2 : 4)) + s.ndiag * (long long)sizeof(T);
 }
 
 // Warps per slice from the mean row length: the smallest power of two that

@@ -60,14 +60,6 @@ def test_traffic_lookup_is_tied_to_the_kernel_source(tmp_path, monkeypatch):
     assert t is None
 
 
-def test_many_grid_aggregate_roofline():
-    """The many-grid line reports V-cycle bytes over the whole solve's time."""
-    e = bench.multi_roofline(6 * 10**9, 2.0, 6769.4, "measured")
-    assert e["bound"] == "hbm" and e["unit"] == "GB/s"
-    assert abs(e["achieved"] - 3000.0) < 1e-9
-    assert abs(e["frac"] - 3000.0 / 6769.4) < 1e-12
-
-
 def test_cpu_baseline_sample_runs_at_least_min_seconds():
     """The oracle baseline repeats whole solves until the sample reaches its
     minimum duration, and reports DOFs per second over all of them."""

@@ -160,6 +160,11 @@ def test_host_argument_checks_need_no_gpu(L):
                                       ctypes.byref(i64), None) == ARG
     assert L.airg_problem_advection2d(8, 8, float("nan"), 0.0, 0.1, fake, fake, fake, fake,
                                       ctypes.byref(i64), ctypes.byref(i64), None) == ARG
+    for bad_h in (-0.1, float("nan"), float("inf")):
+        assert L.airg_problem_advection2d(8, 8, 1.0, 0.0, bad_h, fake, fake, fake, fake,
+                                          ctypes.byref(i64), ctypes.byref(i64), None) == ARG
+        assert L.airg_assemble_rhs_advection2d(8, 8, 1.0, 0.0, bad_h, 1, fake, 8, fake, None, fake, None) == ARG
+        assert L.airg_rhs_adjoint_advection2d(8, 8, 1.0, 0.0, bad_h, 1, fake, 8, fake, fake, None, None) == ARG
     assert L.airg_assemble_rhs_advection2d(8, 8, 1.0, 0.0, 0.1, 0, fake, 8, fake, None, fake, None) == ARG
     assert L.airg_rhs_adjoint_advection2d(8, 8, 1.0, 0.0, 0.1, 1, fake, -1, fake, fake, None, None) == ARG
     assert L.airg_dot_exact_noalloc(-1, fake, fake, fake, None) == ARG

@@ -98,7 +98,9 @@ def test_2048x64_batched_full_size():
                 assert np.linalg.norm(X[q] - u) / np.linalg.norm(u) <= 1e-9
 
 
-def test_32_uneven_grids_full_size():
+@pytest.mark.parametrize("form", ["worklist", "graph"])
+def test_32_uneven_grids_full_size(form, monkeypatch):
+    monkeypatch.setenv("AIRG_MULTI", form)
     w = workload("c4b")
     csrs, bs, ref = [], [], []
     for p in w["problems"]:

@@ -149,6 +149,20 @@ def test_exact_dot_bitwise():
         assert got == O.xdot(x, y)
     assert G.airg_dot_exact(torch.zeros(5, device="cuda", dtype=torch.float64),
                             torch.ones(5, device="cuda", dtype=torch.float64)) == 0.0
+    # magnitudes that keep a thread's products in one digit window, that
+    # walk the window up and down, extreme and subnormal exponents, and
+    # exact cancellation
+    n = 1 << 21
+    cases = [(rng.uniform(0.5, 1.0, n), rng.uniform(-1.0, 1.0, n)),
+             (np.exp2(np.linspace(-60, 60, n)), rng.standard_normal(n)),
+             (np.exp2(np.linspace(60, -60, n)), rng.standard_normal(n)),
+             (rng.standard_normal(n) * np.exp2(rng.integers(-1000, 1000, n)), rng.standard_normal(n)),
+             (rng.standard_normal(4099) * 1e-310, rng.standard_normal(4099))]
+    z = rng.standard_normal(n // 2)
+    cases.append((np.concatenate([z, z]), np.concatenate([z, -z])))
+    for x, y in cases:
+        got = G.airg_dot_exact(torch.tensor(x, device="cuda"), torch.tensor(y, device="cuda"))
+        assert got == O.xdot(x, y)
 
 
 def test_rng_bitwise():
@@ -330,7 +344,8 @@ def test_richardson_outer_matches_oracle(prec):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_slices_per_warp_never_changes_a_bit(prec, monkeypatch):
     """The setup's timing-based choices -- slices per warp (1, 2 or 4) for
-    short rows, loads in flight per lane (4, 8 or 16) for long rows -- only
+    short rows, loads in flight per lane (4, 8 or 16) for long rows, the
+    operator's own grid or a resident grid striding over the slices -- only
     change how rows are mapped to threads: forcing each choice gives the
     same solution bit for bit."""
     w = workload("grid", (300, 257))
@@ -339,15 +354,45 @@ def test_slices_per_warp_never_changes_a_bit(prec, monkeypatch):
     b = G.airg_assemble_rhs_advection2d(pg, torch.tensor(w["g"][0], device="cuda"),
                                         torch.tensor(w["s"][0], device="cuda"))
     xs = []
-    for r, u in [("1", "4"), ("2", "8"), ("4", "16")]:
+    for r, u, pg_ in [("1", "4", "0"), ("2", "8", "0"), ("4", "16", "0"), ("1", "4", "1"), ("4", "16", "1")]:
         monkeypatch.setenv("AIRG_ROWS_PER_WARP", r)
         monkeypatch.setenv("AIRG_LOADS_PER_LANE", u)
+        monkeypatch.setenv("AIRG_PERSIST_GRID", pg_)
         h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"],
                          G.airg_options_default(precision=prec, **w["opts"]))
         x, info = G.airg_solve(h, b, rtol=1e-10)
         assert info.converged
         xs.append(x.cpu().numpy())
-    assert np.array_equal(xs[0], xs[1]) and np.array_equal(xs[0], xs[2])
+    for x in xs[1:]:
+        assert np.array_equal(xs[0], x)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_coarse_16bit_columns_never_change_a_bit(prec, monkeypatch):
+    """The coarsest operator's 16-bit column indices (long rows, at most
+    65536 columns) hold the same values as the 32-bit ones: solutions are
+    equal bit for bit with and without them, at every loads-per-lane
+    setting of the coarse kernels."""
+    w = workload("c2", n=640)
+    vx, vy = velocity(w["theta"])
+    pg = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
+    b = G.airg_assemble_rhs_advection2d(pg, torch.tensor(w["g"][0], device="cuda"))
+    xs, vbytes = [], []
+    for col16, u in [("0", "4"), ("1", "4"), ("1", "8"), ("1", "16")]:
+        monkeypatch.setenv("AIRG_COL16", col16)
+        monkeypatch.setenv("AIRG_LOADS_PER_LANE", u)
+        h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"],
+                         G.airg_options_default(precision=prec, **w["opts"]))
+        info = G.airg_setup_info(h)
+        assert info["n"][-1] <= 65536
+        vbytes.append(info["bytes_per_vcycle"])
+        x, si = G.airg_solve(h, b, rtol=1e-10)
+        assert si.converged
+        xs.append(x.cpu().numpy())
+    # the 16-bit path was taken: 2 index bytes fewer per coarse entry
+    assert vbytes[1] < vbytes[0] and vbytes[1] == vbytes[2] == vbytes[3]
+    for x in xs[1:]:
+        assert np.array_equal(xs[0], x)
 
 
 def test_bf16_restrictor_storage_error():
