@@ -268,8 +268,8 @@ def run_reference(args):
 def run_gpu_multi(args):
     """Workload of many separate grids of uneven size (one hierarchy each):
     `value` from the default form, each lockstep FGMRES iteration of all
-    problems as one persistent work-list launch; `graph_form` times the same
-    solves with one graph of per-problem branches per iteration."""
+    problems as one graph of per-problem branches; `worklist_form` times the
+    same solves with each iteration as one persistent work-list launch."""
     import torch
     rank, world, local_rank, dev = _dist_setup(torch)
     import paper_2508_17517_gb300 as G
@@ -341,14 +341,14 @@ def run_gpu_multi(args):
     clk = Clocks(local_rank)
     clk.start()
     t_wall0 = time.perf_counter()
-    total_ms, its, launches = timed("worklist", args.steps, args.warmup, "timed")
+    total_ms, its, launches = timed("graph", args.steps, args.warmup, "timed")
     wall_s = time.perf_counter() - t_wall0
-    g_ms, g_its, g_launches = timed("graph", args.steps, args.warmup, "graph form")
+    g_ms, g_its, g_launches = timed("worklist", args.steps, args.warmup, "work-list form")
     clocks = clk.stop()
     t_max = max_over_ranks(total_ms, world, dev)
     g_max = max_over_ranks(g_ms, world, dev)
     value = world * ntot * args.steps / (t_max / 1e3)
-    os.environ["AIRG_MULTI"] = "worklist"
+    os.environ["AIRG_MULTI"] = "graph"
     bh = [b.cpu().pin_memory() for b in bs]
     xh = [torch.zeros_like(b).pin_memory() for b in bh]
     G.airg_solve_batch(B, bh, xh, rtol=w["rtol"])     # warm-up of the host path (staging buffers)
@@ -361,8 +361,8 @@ def run_gpu_multi(args):
         G.airg_solve_batch(B, bh, xh, rtol=w["rtol"])
         e2e_s += time.perf_counter() - t0
     e2e_max = max_over_ranks(e2e_s, world, dev)
-    roof = iteration_roofline("worklist", args.steps)
-    g_roof = iteration_roofline("graph", args.steps)
+    roof = iteration_roofline("graph", args.steps)
+    g_roof = iteration_roofline("worklist", args.steps)
     os.environ.pop("AIRG_MULTI", None)
     if rank == 0:
         print(json.dumps({
@@ -375,7 +375,7 @@ def run_gpu_multi(args):
             "e2e": {"value": world * ntot * args.steps / e2e_max, "unit": "DOF/s",
                     "h2d_bytes_per_step": 16 * ntot, "d2h_bytes_per_step": 8 * ntot},
             "roofline": roof,
-            "graph_form": {"value": world * ntot * args.steps / (g_max / 1e3), "unit": "DOF/s",
+            "worklist_form": {"value": world * ntot * args.steps / (g_max / 1e3), "unit": "DOF/s",
                            "ms_per_step": g_max / args.steps, "iterations_per_solve": statistics.median(g_its),
                            "gpu_launches": g_launches, "roofline": g_roof},
             "cpu_baseline": None, "clocks": clocks, "gpu_launches": launches, "wall_s_timed": wall_s}))
@@ -400,23 +400,28 @@ def kernel_source_hash():
     return h.hexdigest()[:12]
 
 
-def measured_traffic(workload, kind, level):
+def measured_traffic(workload, kind, level, alg_bytes=None):
     """DRAM bytes per launch of a (kind, level) group from the committed ncu
     summary (profiles/coarse_newton_traffic.md), taken on the current kernel
-    source; (bytes, source hash) or (None, reason)."""
+    source and on the same operator (algorithmic bytes per launch within 1%
+    of `alg_bytes` when given); (bytes, source hash) or (None, reason)."""
     path = os.path.join(ROOT, "profiles", "coarse_newton_traffic.md")
     src = kernel_source_hash()
     if not os.path.exists(path):
         return None, "no ncu traffic summary"
     for line in open(path):
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
-        if len(cells) >= 7 and cells[0] == workload and cells[1] == kind and cells[2] == str(level):
+        if len(cells) >= 8 and cells[0] == workload and cells[1] == kind and cells[2] == str(level):
             if cells[3] != src:
                 return None, "ncu traffic was measured on kernel source %s, not the current %s" % (cells[3], src)
             try:
-                return float(cells[6]), src
+                alg, traffic = float(cells[5]), float(cells[6])
             except ValueError:
                 return None, "unreadable traffic entry"
+            if alg_bytes is not None and abs(alg - alg_bytes) > 0.01 * alg_bytes:
+                return None, ("ncu traffic was measured on an operator of %.4g algorithmic bytes per launch, "
+                              "not the current %.4g" % (alg, alg_bytes))
+            return traffic, src
     return None, "no ncu traffic entry for this kernel group and workload"
 
 
@@ -532,7 +537,8 @@ def roofline_entry(G, torch, h, b, x, rtol, flush, steps, levels, ms_per_step, p
     dk, dl = dominant_group(per_level)
     group, inst_ms = group_timed(G, torch, h, b, x, rtol, flush, steps, dk, dl, levels)
     entry = roofline_from(prof, per_level, group, steps, ms_per_step, inst_ms, peak, peak_kind, vcycle_dtype)
-    traffic, src = measured_traffic(workload_key, dk, dl) if workload_key else (None, "not captured")
+    traffic, src = (measured_traffic(workload_key, dk, dl, entry["algorithmic_bytes_per_launch"])
+                    if workload_key else (None, "not captured"))
     entry["traffic"] = traffic
     if traffic is not None:
         entry["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch "

@@ -259,15 +259,16 @@ airg_status airg_solve_adjoint(airg_handle* h, int nrhs, const double* rhs, doub
  * nprob hierarchies (As: HOST array of nprob CSR descriptors, same options
  * for all).  airg_solve_batch runs FGMRES in lockstep across the problems.
  * Each iteration of all problems -- scale v_j, V-cycle, SpMV, Gram-Schmidt
- * pass -- is one persistent kernel launch (captured in a CUDA graph once per
- * iteration index and replayed) whose blocks take the tiles of every
- * problem's operations from a device work list in dependency order.  With
- * the environment variable AIRG_MULTI=graph, or for layouts the work list
- * does not implement (C-point smoothing, the assembled smoother, bfloat16
- * restrictor values, the opt-in persistent or staged kernels), each
- * iteration is instead one graph launch in which every problem forms an
- * independent branch of per-operator kernels.  A bounded wait of the work
- * list that gives up returns AIRG_ERR_TIMEOUT.  bvec, xvec: HOST arrays of nprob pointers
+ * pass -- is one CUDA graph launch (captured once per iteration index and
+ * replayed) in which every problem forms an independent branch of
+ * per-operator kernels.  With the environment variable AIRG_MULTI=worklist
+ * it is instead one persistent kernel launch (also captured) whose blocks
+ * take the tiles of every problem's operations from a device work list in
+ * dependency order, except for layouts the work list does not implement
+ * (C-point smoothing, the assembled smoother, bfloat16 restrictor values,
+ * the opt-in persistent or staged kernels), which stay in the graph form.
+ * A bounded wait of the work list that gives up returns AIRG_ERR_TIMEOUT.
+ * bvec, xvec: HOST arrays of nprob pointers
  * to vectors of each problem's length (DEVICE pointers if on_device, else
  * HOST); x is the initial guess on entry.  infos: HOST array of nprob
  * entries (may be NULL).  AIRG_ERR_NOT_CONVERGED if any problem misses the

@@ -230,7 +230,7 @@ class Options:
     coarse_min_rows: int = 1
     a_drop: float = 1e-6
     a_lump: bool = True
-    r_drop: float = 1e-2             # parity unpinned: the paper gives no value
+    r_drop: float = 2e-2             # parity unpinned: the paper gives no value
     seed: int = 2508175
     breakdown_tol: float = 1e-8      # rank reading of Sec. 2.3: h_{j+1,j} <= tol * ||H(:,j)||
     exact_tol: float = 1e-12         # rank reading of Sec. 2.3: GMRES residual <= tol * beta

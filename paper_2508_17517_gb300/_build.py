@@ -14,8 +14,8 @@ SRC_DIR = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(LIB_DIR, "obj")
 LIB = os.path.join(LIB_DIR, "libairg.so")
-SOURCES = ["capi.cu", "setup.cu", "solve.cu", "batch.cu", "multi.cu", "worklist.cu", "noalloc.cu",
-           "hostmath.cpp"]
+SOURCES = ["capi.cu", "setup.cu", "solve.cu", "batch.cu", "multi.cu", "worklist.cu", "coarse_stream.cu",
+           "noalloc.cu", "hostmath.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -206,7 +206,7 @@ airg_status airg_options_default(airg_options* o)
     o->coarse_min_rows = 1;
     o->a_drop = 1e-6;
     o->a_lump = 1;
-    o->r_drop = 1e-2;
+    o->r_drop = 2e-2;   // not in the paper: chosen on measured solve time (1024^2 and 4096^2)
     o->seed = 2508175ULL;
     o->breakdown_tol = 1e-8;
     o->exact_tol = 1e-12;

@@ -470,17 +470,44 @@ __device__ __forceinline__ int find_col(const int* ci, int lo, int hi, int j)
     return lo;
 }
 
+// Rows of at least FSP_WARP_ROW entries are computed by k_fsp_power_warp.
+constexpr int FSP_WARP_ROW = 16;
+
 __global__ void k_fsp_power(int n, const int* rp, const int* ci, const double* a,
                             const double* tprev, double* tout)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (rp[i + 1] - rp[i] >= FSP_WARP_ROW) return;
     for (int q = rp[i]; q < rp[i + 1]; ++q) {
         int j = ci[q];
         double s = 0.0;
         for (int p = rp[i]; p < rp[i + 1]; ++p) {
             int l = ci[p];
             int r = find_col(ci, rp[l], rp[l + 1], j);
+            if (r < rp[l + 1] && ci[r] == j) s = __dadd_rn(s, __dmul_rn(a[p], tprev[r]));
+        }
+        tout[q] = s;
+    }
+}
+
+// The long rows of k_fsp_power, one warp each: lane t computes the entries
+// q = rp[i] + t, t + 32, ... of the row, each summed over the row's entries
+// p in column order exactly as the one-thread kernel does.
+__global__ void k_fsp_power_warp(int n, const int* rp, const int* ci, const double* a,
+                                 const double* tprev, double* tout)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const int r0 = rp[i], r1 = rp[i + 1];
+    if (r1 - r0 < FSP_WARP_ROW) return;
+    for (int q = r0 + lane; q < r1; q += 32) {
+        const int j = ci[q];
+        double s = 0.0;
+        for (int p = r0; p < r1; ++p) {
+            const int l = ci[p];
+            const int r = find_col(ci, rp[l], rp[l + 1], j);
             if (r < rp[l + 1] && ci[r] == j) s = __dadd_rn(s, __dmul_rn(a[p], tprev[r]));
         }
         tout[q] = s;
@@ -519,6 +546,10 @@ __global__ void k_gemm_bound(int m, const int* arp, const int* aci, const int* b
 
 __device__ __forceinline__ unsigned hash_col(int j) { return (unsigned)j * 2654435761u; }
 
+// Rows whose table has at least HASH_WARP_SLOTS slots are accumulated by a
+// warp (k_gemm_hash_warp), the others by one thread (k_gemm_hash).
+constexpr int HASH_WARP_SLOTS = 64;
+
 __global__ void k_gemm_hash(int m, int row0, const int* arp, const int* aci, const double* av,
                             const int* brp, const int* bci, const double* bv, const int* toff,
                             int* keys, double* vals, int* cnt)
@@ -527,6 +558,7 @@ __global__ void k_gemm_hash(int m, int row0, const int* arp, const int* aci, con
     if (li >= m) return;
     int i = row0 + li;
     int base = toff[li], size = toff[li + 1] - base;
+    if (size >= HASH_WARP_SLOTS) return;
     int c = 0;
     if (size > 0) {
         unsigned mask = (unsigned)size - 1u;
@@ -552,6 +584,55 @@ __global__ void k_gemm_hash(int m, int row0, const int* arp, const int* aci, con
         }
     }
     cnt[li] = c;
+}
+
+// The rows with large tables, one warp each.  The entries of A's row are
+// taken one at a time, in column order, by the whole warp; the lanes share
+// that entry's row of B.  Within one entry of A the columns j of B's row are
+// distinct, so no two lanes add to the same j (a lane claims a new slot with
+// an atomic compare-and-swap), and the warp synchronises before the next
+// entry: every output entry is still summed in ascending inner index with
+// the same roundings as the one-thread kernel.
+__global__ void k_gemm_hash_warp(int m, int row0, const int* arp, const int* aci, const double* av,
+                                 const int* brp, const int* bci, const double* bv, const int* toff,
+                                 int* keys, double* vals, int* cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int li = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (li >= m) return;                       // uniform over the warp
+    const int i = row0 + li;
+    const int base = toff[li], size = toff[li + 1] - base;
+    if (size < HASH_WARP_SLOTS) return;
+    const unsigned mask = (unsigned)size - 1u;
+    int c = 0;
+    for (int p = arp[i]; p < arp[i + 1]; ++p) {
+        const int l = aci[p];
+        const double a = av[p];
+        for (int q = brp[l] + lane; q < brp[l + 1]; q += 32) {
+            const int j = bci[q];
+            const double prod = __dmul_rn(a, bv[q]);
+            unsigned h = hash_col(j) & mask;
+            while (true) {
+                int key = *(volatile int*)(keys + base + h);
+                if (key == -1) {
+                    key = atomicCAS(keys + base + h, -1, j);
+                    if (key == -1) {
+                        vals[base + h] = __dadd_rn(0.0, prod);
+                        ++c;
+                        break;
+                    }
+                }
+                if (key == j) {
+                    vals[base + h] = __dadd_rn(vals[base + h], prod);
+                    break;
+                }
+                h = (h + 1u) & mask;
+            }
+        }
+        __syncwarp();
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[li] = c;
 }
 
 __global__ void k_shift_rowptr(int m, const int* prp, int off, int* crp)
@@ -580,6 +661,52 @@ __global__ void k_gemm_emit(int m, const int* toff, const int* keys, const doubl
     }
 }
 
+// Emit of the rows of at most 32 entries: one warp per row, one entry per
+// lane, sorted by column with a bitonic network of warp shuffles.
+__global__ void k_gemm_emit_small(int m, const int* toff, const int* keys, const double* vals,
+                                  const int* crp, int* cci, double* cv)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= m) return;                        // uniform over the warp
+    const int n = crp[i + 1] - crp[i];
+    if (n > 32) return;
+    int k = 0x7fffffff;
+    double v = 0.0;
+    int filled = 0;
+    for (int tb = toff[i]; tb < toff[i + 1]; tb += 32) {
+        const int t = tb + lane;
+        const int key = t < toff[i + 1] ? keys[t] : -1;
+        const unsigned ball = __ballot_sync(0xffffffffu, key >= 0);
+        const int pos = filled + __popc(ball & ((1u << lane) - 1u));
+        const double val = key >= 0 ? vals[t] : 0.0;
+        // lane pos receives this entry
+        for (int src = 0; src < 32; ++src) {
+            if (!((ball >> src) & 1u)) continue;
+            const int sp = __shfl_sync(0xffffffffu, pos, src);
+            const int sk = __shfl_sync(0xffffffffu, key, src);
+            const double sv = __shfl_sync(0xffffffffu, val, src);
+            if (lane == sp) { k = sk; v = sv; }
+        }
+        filled += __popc(ball);
+    }
+    for (int size = 2; size <= 32; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const int ok = __shfl_xor_sync(0xffffffffu, k, stride);
+            const double ov = __shfl_xor_sync(0xffffffffu, v, stride);
+            const bool lower = (lane & stride) == 0;
+            const bool up = (lane & size) == 0;
+            // the lower lane of a pair keeps the smaller key when sorting up
+            const bool take = lower == up ? ok < k : ok > k;
+            if (take) { k = ok; v = ov; }
+        }
+    }
+    if (lane < n) {
+        cci[crp[i] + lane] = k;
+        cv[crp[i] + lane] = v;
+    }
+}
+
 // Emit of the rows of at most EMIT_CAP entries: one warp per row takes the
 // valid slots of the row's table into shared memory (ballot / prefix
 // count), sorts them by column with a bitonic network and writes them out.
@@ -597,7 +724,7 @@ k_gemm_emit_warp(int m, const int* toff, const int* keys, const double* vals, co
     const int i = blockIdx.x * EMIT_WARPS + w;
     if (i >= m) return;
     const int n = crp[i + 1] - crp[i];
-    if (n > EMIT_CAP) return;
+    if (n > EMIT_CAP || n <= 32) return;
     int* k = sk[w];
     double* v = sv[w];
     const int t0 = toff[i], t1 = toff[i + 1];
@@ -926,13 +1053,19 @@ void spgemm(const DevCSR& A, const DevCSR& B, DevCSR& C, cudaStream_t st)
         DBuf<double> vals(std::max(tsz, 1));
         CK(cudaMemsetAsync(keys.p, 0xff, keys.bytes(), st));
         P.rp.alloc(size_t(mc) + 1);
-        if (mc) k_gemm_hash<<<grid_for(mc, TB), TB, 0, st>>>(mc, P.r0, A.rp.p, A.ci.p, A.v.p, B.rp.p,
-                                                               B.ci.p, B.v.p, toff.p, keys.p, vals.p, P.rp.p);
+        if (mc) {
+            k_gemm_hash<<<grid_for(mc, TB), TB, 0, st>>>(mc, P.r0, A.rp.p, A.ci.p, A.v.p, B.rp.p, B.ci.p,
+                                                         B.v.p, toff.p, keys.p, vals.p, P.rp.p);
+            k_gemm_hash_warp<<<grid_for(mc, TB / 32), TB, 0, st>>>(mc, P.r0, A.rp.p, A.ci.p, A.v.p, B.rp.p,
+                                                                   B.ci.p, B.v.p, toff.p, keys.p, vals.p, P.rp.p);
+        }
         CK_LAUNCH();
         P.nnz = exclusive_scan(P.rp.p, P.rp.p, mc, st);
         P.ci.alloc(std::max(P.nnz, 1));
         P.v.alloc(std::max(P.nnz, 1));
         if (mc) {
+            k_gemm_emit_small<<<grid_for(mc, TB / 32), TB, 0, st>>>(mc, toff.p, keys.p, vals.p, P.rp.p,
+                                                                     P.ci.p, P.v.p);
             k_gemm_emit_warp<<<grid_for(mc, EMIT_WARPS), EMIT_WARPS * 32, 0, st>>>(mc, toff.p, keys.p, vals.p,
                                                                                    P.rp.p, P.ci.p, P.v.p);
             k_gemm_emit<<<grid_for(mc, TB), TB, 0, st>>>(mc, toff.p, keys.p, vals.p, P.rp.p, P.ci.p, P.v.p,
@@ -1157,6 +1290,7 @@ void fixed_sparsity_inverse(const DevCSR& Aff, const std::vector<double>& alpha,
     for (size_t k = 1; k < alpha.size(); ++k) {
         if (k >= 2) {
             k_fsp_power<<<grid_for(n, TB), TB, 0, st>>>(n, Aff.rp.p, Aff.ci.p, Aff.v.p, T.p, Tn.p);
+            k_fsp_power_warp<<<grid_for(n, TB / 32), TB, 0, st>>>(n, Aff.rp.p, Aff.ci.p, Aff.v.p, T.p, Tn.p);
             std::swap(T.p, Tn.p);
         }
         k_fsp_acc<<<grid_for(nnz, TB), TB, 0, st>>>(nnz, out.v.p, T.p, alpha[k]);

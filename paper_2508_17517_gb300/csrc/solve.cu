@@ -1417,10 +1417,15 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
             bool last = i + 1 == nr;
             const Root& q = S.roots[i];
             T* rout = bufs[nb];
+            unsigned* serr = reinterpret_cast<unsigned*>(S.bar.p + 2);
             if (q.im == 0.0) {
                 if (last)
                     LAUNCH_F(S, PK_NEWTON, (i == 0 ? 2 : 3) * nB, 2LL * nco,
                            k_newton_last<T><<<grid_for(nco, TB), TB, 0, st>>>(nco, rin, x, T(1.0 / q.re), i == 0));
+                else if (A.stream)
+                    LAUNCH_F(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB, 2 * A.nnz + 4LL * nco,
+                             coarse_stream_launch<T>(A, CS_REAL, rin, nullptr, rout, x, T(1.0 / q.re), T(0), i == 0,
+                                                     serr, st));
                 else if (A.xs)
                     LAUNCH_F(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB, 2 * A.nnz + 4LL * nco,
                            WITH_KR_XS(A, k_newton_real_xs<T, KK, RR><<<A.xs, XS_THREADS, xs_smem(A), st>>>(
@@ -1431,7 +1436,11 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
                                           Av, rin, rout, x, T(1.0 / q.re), i == 0)));
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
-                if (A.xs)
+                if (A.stream)
+                    LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, 2 * A.nnz + 4LL * nco,
+                             coarse_stream_launch<T>(A, CS_PAIR1, rin, nullptr, wk.ct, x, T(2.0 * q.re),
+                                                     T(1.0 / mod2), i == 0, serr, st));
+                else if (A.xs)
                     LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, 2 * A.nnz + 4LL * nco,
                            WITH_KR_XS(A, k_newton_pair1_xs<T, KK, RR><<<A.xs, XS_THREADS, xs_smem(A), st>>>(
                                                Av, rin, A.n_cols, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
@@ -1439,7 +1448,11 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
                     LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, 2 * A.nnz + 4LL * nco,
                            WITH_KR_COL(A, k_newton_pair1<T, KK, RR, C16><<<grid_rows(A, k_newton_pair1<T, KK, RR, C16>), block_rows(A), 0, st>>>(
                                           Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
-                if (!last && A.xs)
+                if (!last && A.stream)
+                    LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
+                             coarse_stream_launch<T>(A, CS_PAIR2, wk.ct, rin, rout, nullptr, T(0), T(1.0 / mod2), 0,
+                                                     serr, st));
+                else if (!last && A.xs)
                     LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
                            WITH_KR_XS(A, k_newton_pair2_xs<T, KK, RR><<<A.xs, XS_THREADS, xs_smem(A), st>>>(
                                                Av, rin, wk.ct, A.n_cols, rout, T(1.0 / mod2))));
@@ -1613,6 +1626,43 @@ void tune_coarse_xs(Sell<T>& A, float unstaged_ms, const T* x, T* y, cudaStream_
     A.xs = best_r ? grid : 0;
 }
 
+// Streamed form of the coarsest operator's steps (coarse_stream.cu), kept
+// where it times faster than the best row-kernel form (`unstaged_ms` for 3
+// launches of y = A x); AIRG_COARSE_STREAM=0 never uses it, =1 always (when
+// the layout allows).  Neither form changes the arithmetic.
+template <class T>
+void tune_coarse_stream(Sell<T>& A, float unstaged_ms, const T* x, T* y, cudaStream_t st)
+{
+    A.stream = 0;
+    const char* env = getenv("AIRG_COARSE_STREAM");
+    const int mode = env ? atoi(env) : 0;
+    if (mode == 0 || A.xs || !coarse_stream_ok(A)) return;
+    if (mode == 1) {
+        A.stream = 1;
+        return;
+    }
+    if (unstaged_ms <= 0.f) return;
+    DBuf<unsigned> err(1);
+    CK(cudaMemsetAsync(err.p, 0, sizeof(unsigned), st));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    coarse_stream_launch<T>(A, CS_SPMV, x, nullptr, y, nullptr, T(0), T(0), 0, err.p, st);
+    CK(cudaEventRecord(e0, st));
+    for (int rep = 0; rep < 3; ++rep)
+        coarse_stream_launch<T>(A, CS_SPMV, x, nullptr, y, nullptr, T(0), T(0), 0, err.p, st);
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    unsigned bad = 0;
+    d2h(&bad, err.p, 1, st);
+    if (bad) fail(AIRG_ERR_TIMEOUT, "a bounded wait of the streamed coarse kernel gave up");
+    if (ms < unstaged_ms) A.stream = 1;
+}
+
 int env_choice(const char* name, std::initializer_list<int> allowed)
 {
     const char* e = getenv(name);
@@ -1643,7 +1693,9 @@ void tune_all(SolveData& S, cudaStream_t st)
         tune_rows(o.Ainvc, x.p, y.p, fs, fl, st);
     }
     Sell<T>& Ac = const_cast<Sell<T>&>(coarse_op<T>(S));
-    tune_coarse_xs(Ac, tune_rows(Ac, x.p, y.p, fs, fl, st), x.p, y.p, st);
+    const float unstaged = tune_rows(Ac, x.p, y.p, fs, fl, st);
+    tune_coarse_xs(Ac, unstaged, x.p, y.p, st);
+    tune_coarse_stream(Ac, unstaged, x.p, y.p, st);
     CK(cudaStreamSynchronize(st));
 }
 

@@ -59,6 +59,7 @@ template <class T, class V = T>
 struct Sell {
     int n_rows = 0, n_cols = 0, n_slices = 0, k = 1, r = 1;
     int persist = 0;   // 1: row kernels run on a grid of resident blocks that stride over the slices
+    int stream = 0;    // coarsest operator only: 1 = its steps stream it through shared memory (coarse_stream.cu)
     int xs = 0;   // coarsest operator only: > 0 = its SpMVs stage x in shared memory, on xs blocks (solve.cu)
     long long nnz = 0, padded = 0, ndiag = 0;
     DBuf<int> sptr;
@@ -345,6 +346,18 @@ struct SolveData {
     } while (0)
 #define LAUNCH(S, KIND, BYTES, ...) LAUNCH_F(S, KIND, BYTES, 0LL, __VA_ARGS__)
 
+
+// coarse_stream.cu: the coarsest operator's steps with the operator
+// streamed through shared memory by bulk asynchronous copies, for a long-row
+// operator of 8 warps per slice with 16-bit columns (coarse_stream_ok);
+// bit-identical to the K = 8 row kernels.  err: error word set when a
+// bounded wait gives up.
+enum { CS_SPMV = 0, CS_REAL = 1, CS_PAIR1 = 2, CS_PAIR2 = 3 };
+template <class T>
+bool coarse_stream_ok(const Sell<T>& A);
+template <class T>
+void coarse_stream_launch(const Sell<T>& A, int kind, const T* xin, const T* aux, T* out, T* xacc, T sa, T sb,
+                          int first, unsigned* err, cudaStream_t st);
 
 // solve.cu: launch helpers of one problem's solve, for the multi-problem
 // solver (multi.cu); all launch on `st` and use the problem's own buffers

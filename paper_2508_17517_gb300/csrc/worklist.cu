@@ -5,9 +5,10 @@
 // Newton steps, the F-point residual and Horner terms per level; w = A z_j;
 // the Gram-Schmidt dots and update, each followed by a one-tile fixed-order
 // sum of its partials).  Operations are cut into tiles of consecutive SELL
-// slices (or rows).  The tiles of all problems are queued step-major --
-// step s of every problem before step s + 1 of any -- and the blocks of one
-// kernel take them in queue order with one atomic counter.  A tile starts
+// slices (or rows).  The tiles of all problems are queued by the share of
+// its problem's work that comes before each operation, so that all problems
+// advance at the same relative pace, and the blocks of one kernel take them
+// in queue order with one atomic counter.  A tile starts
 // once every tile of the operation before it in its problem's chain has
 // finished (a completion counter per operation).  A block only waits on
 // tiles queued before its own, which blocks that are already running hold,
@@ -91,6 +92,7 @@ constexpr int WL_GROUPS = 4;                    // block-groups of slices per ti
 constexpr int WL_SHORT_SLICES = 64;             // slices per tile (short rows: 2 per warp, 4 times)
 constexpr int WL_VEC_UNIT = 2048;               // rows per tile of a vector op
 constexpr int WL_MAX_DOT_TILES = 1024;          // partial sums per reduction
+constexpr int WL_DOT_CHUNK = 8;                 // basis vectors per pass of a dot tile
 
 // Row (32 slice + lane) of the SELL operator times x, computed by the K
 // warps of the block sharing the slice (part = this warp's index among
@@ -445,23 +447,23 @@ __device__ void wl_outer(const WOp& op, int tile, double (*red)[32])
             break;
         }
         case W_DOT: {
-            // partial <V_i, w> (i < m) and <w, w> of rows [r0, r1), eight at a time
+            // partial <V_i, w> (i < m) and <w, w> of rows [r0, r1), WL_DOT_CHUNK at a time
             const double* V = static_cast<const double*>(op.in);
             const double* w = static_cast<const double*>(op.in2);
             const int mo = op.m + 1;
-            for (int c0 = 0; c0 < mo; c0 += 8) {
-                double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int c0 = 0; c0 < mo; c0 += WL_DOT_CHUNK) {
+                double acc[WL_DOT_CHUNK] = {};
                 for (int r = r0 + threadIdx.x; r < r1; r += WL_THREADS) {
                     const double wv = w[r];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < WL_DOT_CHUNK; ++u) {
                         const int i = c0 + u;
                         if (i < op.m) acc[u] = fma(V[i * op.ld + r], wv, acc[u]);
                         else if (i == op.m) acc[u] = fma(wv, wv, acc[u]);
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
+                for (int u = 0; u < WL_DOT_CHUNK; ++u) {
                     const double s = wl_block_sum(acc[u], red);
                     if (threadIdx.x == 0 && c0 + u < mo) op.part[(long long)tile * mo + c0 + u] = s;
                 }
@@ -879,14 +881,38 @@ std::shared_ptr<WorkList> build_worklist(const std::vector<WlProblem>& probs, in
         }
         maxlen = std::max(maxlen, chains[p].ops.size());
     }
-    // tiles, step-major
-    std::vector<int2> tiles;
-    for (size_t s = 0; s < maxlen; ++s)
-        for (size_t p = 0; p < chains.size(); ++p) {
-            if (s >= idx[p].size()) continue;
-            const int oi = idx[p][s];
-            for (int t = 0; t < all[oi].tiles; ++t) tiles.push_back(make_int2(oi, t));
+    // Queue order of the operations: by the share of its chain's work done
+    // before an operation's midpoint (algorithmic bytes), so that every
+    // problem advances at the same relative pace and large and small
+    // problems finish together; ties by problem, then by position in the
+    // chain.  An operation's predecessor always has a smaller key, so its
+    // tiles are queued first.
+    struct Key {
+        double f;
+        int p, s;
+    };
+    std::vector<Key> keys;
+    for (size_t p = 0; p < chains.size(); ++p) {
+        double tot = 0.0;
+        for (int oi : idx[p]) tot += double(std::max<long long>(all[oi].bytes, 1));
+        double pre = 0.0;
+        for (size_t s = 0; s < idx[p].size(); ++s) {
+            const double w = double(std::max<long long>(all[idx[p][s]].bytes, 1));
+            keys.push_back(Key{(pre + 0.5 * w) / tot, int(p), int(s)});
+            pre += w;
         }
+    }
+    std::sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+        if (a.f != b.f) return a.f < b.f;
+        if (a.p != b.p) return a.p < b.p;
+        return a.s < b.s;
+    });
+    std::vector<int2> tiles;
+    for (const Key& k : keys) {
+        const int oi = idx[size_t(k.p)][size_t(k.s)];
+        for (int t = 0; t < all[oi].tiles; ++t) tiles.push_back(make_int2(oi, t));
+    }
+    (void)maxlen;
     auto wl = std::make_shared<WorkList>();
     wl->nops = int(all.size());
     wl->ntiles = int(tiles.size());

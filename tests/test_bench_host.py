@@ -45,15 +45,19 @@ def test_traffic_lookup_is_tied_to_the_kernel_source(tmp_path, monkeypatch):
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "coarse_newton_traffic.md").write_text(
-        "| workload | kind | level | kernel source | launches | algorithmic B | DRAM B per launch |\n"
-        "|---|---|---|---|---|---|---|\n"
-        "| c3_fp64 | coarse_newton | 11 | %s | 3 | 1.0e8 | 1.1e8 |\n"
-        "| c3_fp32 | coarse_newton | 11 | 000000000000 | 3 | 5.0e7 | 5.5e7 |\n" % src)
+        "| workload | kind | level | kernel source | launches | algorithmic B per launch | DRAM B per launch | us |\n"
+        "|---|---|---|---|---|---|---|---|\n"
+        "| c3_fp64 | coarse_newton | 11 | %s | 3 | 1.0e8 | 1.1e8 | 50 |\n"
+        "| c3_fp32 | coarse_newton | 11 | 000000000000 | 3 | 5.0e7 | 5.5e7 | 40 |\n" % src)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     (tmp_path / "paper_2508_17517_gb300").symlink_to(
         os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2508_17517_gb300"))
     t, s = bench.measured_traffic("c3_fp64", "coarse_newton", 11)
     assert t == 1.1e8 and s == src
+    t, s = bench.measured_traffic("c3_fp64", "coarse_newton", 11, alg_bytes=1.005e8)
+    assert t == 1.1e8
+    t, s = bench.measured_traffic("c3_fp64", "coarse_newton", 11, alg_bytes=0.9e8)
+    assert t is None and "operator" in s
     t, s = bench.measured_traffic("c3_fp32", "coarse_newton", 11)
     assert t is None and "not the current" in s
     t, s = bench.measured_traffic("c2", "f_smoother", 0)

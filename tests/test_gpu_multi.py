@@ -1,7 +1,7 @@
 """Separate problems of uneven size solved together (one hierarchy each,
-lockstep FGMRES; each iteration of all problems is one persistent work-list
-launch, or with AIRG_MULTI=graph one graph launch with a branch per
-problem): each solution must match the oracle's solve of that problem to
+lockstep FGMRES; each iteration of all problems is one graph launch with a
+branch per problem, or with AIRG_MULTI=worklist one persistent work-list
+launch): each solution must match the oracle's solve of that problem to
 1e-9 relative L2, with its true residual at or below rtol."""
 import math
 
@@ -143,8 +143,9 @@ def test_worklist_and_graph_forms_agree(prec, monkeypatch):
 
 def test_worklist_falls_back_for_c_point_smoothing(monkeypatch):
     """Layouts the work list does not implement (here FC smoothing) run in
-    the graph form and still match the exact solution."""
-    monkeypatch.delenv("AIRG_MULTI", raising=False)
+    the graph form even when the work list is asked for, and still match the
+    exact solution."""
+    monkeypatch.setenv("AIRG_MULTI", "worklist")
     rng = np.random.default_rng(22)
     shapes, thetas = [(90, 70), (40, 120)], [0.5, 2.5]
     opts = dict(coarse_poly_order=30, trunc_rtol=1e-2, smooth_type=G.AIRG_SMOOTH_FC)
