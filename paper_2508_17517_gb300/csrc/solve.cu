@@ -1626,10 +1626,12 @@ void tune_coarse_xs(Sell<T>& A, float unstaged_ms, const T* x, T* y, cudaStream_
     A.xs = best_r ? grid : 0;
 }
 
-// Streamed form of the coarsest operator's steps (coarse_stream.cu), kept
+// Streamed form of the coarsest operator's steps (coarse_stream.cu),
+// opt-in: AIRG_COARSE_STREAM=1 uses it whenever the layout allows, =2 only
 // where it times faster than the best row-kernel form (`unstaged_ms` for 3
-// launches of y = A x); AIRG_COARSE_STREAM=0 never uses it, =1 always (when
-// the layout allows).  Neither form changes the arithmetic.
+// launches of y = A x).  Off by default: on the 4096^2 workload its step
+// measured 37.3 against 35.0 us (FP32) and 86.5 against 56.5 us (FP64).
+// Neither form changes the arithmetic.
 template <class T>
 void tune_coarse_stream(Sell<T>& A, float unstaged_ms, const T* x, T* y, cudaStream_t st)
 {
