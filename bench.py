@@ -57,6 +57,8 @@ def parse(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c3", choices=["c3"] + sorted(SINGLE))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--problems", type=int, default=None,
+                    help="number of grids of the many-grid workload (a smaller case of it, for profiling)")
     ap.add_argument("--grid", type=int, default=None,
                     help="grid side of a single-problem workload (a smaller case of the same kind, "
                          "for profiling)")
@@ -275,7 +277,7 @@ def run_gpu_multi(args):
     import paper_2508_17517_gb300 as G
     from synthetic import velocity, workload
     G.lib()
-    w = workload(args.workload)
+    w = workload(args.workload, n=args.problems)
     csrs, bs = [], []
     for p in w["problems"]:
         vx, vy = velocity(p["theta"])
@@ -390,13 +392,24 @@ ALU_PEAK_TFLOPS = {"f64": 2 * 2 * SM_COUNT * SM_GHZ / 1e3, "f32": 2 * 128 * SM_C
 VCYCLE_KINDS = ("restrict", "f_residual", "f_smoother", "coarse_newton")
 
 
+KERNEL_SECTION = (b"// ------------------------------------------------------- V-cycle kernels --",
+                  b"// ------------------------------------- coarse steps with x in shared memory --")
+
+
 def kernel_source_hash():
-    """Short hash of the solve kernels' source (the V-cycle and SpMV code):
-    a DRAM-traffic figure measured on other source no longer applies."""
+    """Short hash of the solve's row kernels: the V-cycle kernel section of
+    solve.cu (between its two section markers; the whole file if they are
+    missing) and solve_internal.cuh.  A DRAM-traffic figure measured on
+    other kernel source no longer applies; host-side edits elsewhere in
+    solve.cu leave it valid."""
     h = hashlib.sha256()
-    for f in ("solve.cu", "solve_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2508_17517_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    d = os.path.join(ROOT, "paper_2508_17517_gb300", "csrc")
+    with open(os.path.join(d, "solve.cu"), "rb") as fh:
+        src = fh.read()
+    i0, i1 = src.find(KERNEL_SECTION[0]), src.find(KERNEL_SECTION[1])
+    h.update(src[i0:i1] if 0 <= i0 < i1 else src)
+    with open(os.path.join(d, "solve_internal.cuh"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:12]
 
 

@@ -940,8 +940,8 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
             bprecond(H, B, vj, zj, st);
             LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz * k,
                    WITH_KWPW(k, S.Atop, kb_spmv<double, KW, PW><<<grid_rows(n, PW), BT, 0, st>>>(A, zj, B.w.p, k)));
-            // CGS with a second pass only if some active right-hand side lost
-            // more than half of ||w||^2 in the first ("twice is enough")
+            // CGS with a second pass only if the first cancelled, for some
+            // active right-hand side, more than reorth_ratio() allows
             double* h1 = B.hdev.p;
             double* h2 = B.hdev.p + size_t(MAXB + 2) * k;
             double* hnp = B.hdev.p + size_t(2) * (MAXB + 2) * k;
@@ -954,8 +954,9 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
             CK(cudaMemcpyAsync(hh, B.hdev.p, sizeof(double) * 3 * (MAXB + 2) * k, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             bool again = false;
+            const double ro = reorth_ratio();
             for (int q = 0; q < k; ++q)
-                if (active[q] && hh[size_t(2) * (MAXB + 2) * k + q] < 0.5 * hh[size_t(j + 1) * k + q]) again = true;
+                if (active[q] && hh[size_t(2) * (MAXB + 2) * k + q] < ro * hh[size_t(j + 1) * k + q]) again = true;
             for (int q = 0; q < k; ++q)
                 for (int i = 0; i <= j; ++i) hq(i, j, q) = hh[size_t(i) * k + q];
             if (again) {

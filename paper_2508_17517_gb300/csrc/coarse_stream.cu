@@ -7,9 +7,9 @@
 // larger than L2.  In the row kernels of solve.cu each warp issues its own
 // loads and waits for them before its gathers of x, so the memory pipeline
 // drains at every step of a lane's sequence.  Here one producer warp per
-// block streams chunks of a slice (CS_COLS entry columns: the values and the
+// block streams chunks of a slice (COLS entry columns: the values and the
 // 16-bit column indices, both contiguous in SELL order) into a ring of
-// CS_STAGES shared-memory stages, and eight consumer warps compute from
+// STAGES shared-memory stages, and eight consumer warps compute from
 // shared memory while the next chunks are in flight.  Blocks are resident
 // (as many as fit) and take the slices in a strided loop.
 //
@@ -38,21 +38,22 @@ namespace {
 
 constexpr int CS_PARTS = 8;                       // consumer warps = parts of a slice
 constexpr int CS_THREADS = 32 * (CS_PARTS + 1);   // + one producer warp
-constexpr int CS_COLS = 64;                       // entry columns per chunk (multiple of 32)
-constexpr int CS_STAGES = 4;
+// chunks of COLS entry columns (a multiple of 32) in a ring of STAGES
+// stages: 64 x 4 by default, 32 x 3 with AIRG_COARSE_STREAM_COLS=32 (less
+// shared memory per block, more resident blocks)
 constexpr long long CS_SPIN = 1LL << 22;          // polls of one bounded wait
 
-template <class T>
+template <class T, int COLS>
 struct CsStage {
-    T val[CS_COLS * 32];
-    unsigned short col[CS_COLS * 32];
+    T val[COLS * 32];
+    unsigned short col[COLS * 32];
 };
 
-template <class T>
+template <class T, int COLS, int STAGES>
 struct CsShared {
-    CsStage<T> st[CS_STAGES];
-    unsigned long long full[CS_STAGES];
-    unsigned long long empty[CS_STAGES];
+    CsStage<T, COLS> st[STAGES];
+    unsigned long long full[STAGES];
+    unsigned long long empty[STAGES];
     T red[CS_PARTS][32];
 };
 
@@ -117,16 +118,16 @@ __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;
 // KIND (solve_internal.cuh): CS_SPMV out = A x;  CS_REAL x_acc += r a,
 // out = r - (A r) a;  CS_PAIR1 t = a r - A r (out), x_acc += t b;
 // CS_PAIR2 out = aux - (A t) b.
-template <class T, int KIND>
+template <class T, int KIND, int COLS, int STAGES>
 __global__ void __launch_bounds__(CS_THREADS)
 k_coarse_stream(SellView<T> A, const T* __restrict__ xin, const T* __restrict__ aux, T* __restrict__ out,
                 T* __restrict__ xacc, T sa, T sb, int first, unsigned* err)
 {
     extern __shared__ __align__(128) unsigned char cs_raw[];
-    CsShared<T>& sm = *reinterpret_cast<CsShared<T>*>(cs_raw);
+    CsShared<T, COLS, STAGES>& sm = *reinterpret_cast<CsShared<T, COLS, STAGES>*>(cs_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < CS_STAGES; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             mbar_init(&sm.full[s], 1);
             mbar_init(&sm.empty[s], CS_PARTS);
         }
@@ -140,11 +141,11 @@ k_coarse_stream(SellView<T> A, const T* __restrict__ xin, const T* __restrict__ 
         for (int s = blockIdx.x; s < A.n_slices; s += gridDim.x) {
             const int b = __ldg(A.sptr + s);
             const int w = (__ldg(A.sptr + s + 1) - b) >> 5;
-            for (int c0 = 0; c0 < w; c0 += CS_COLS, ++g) {
-                const int stg = int(g % CS_STAGES);
-                const long long u = g / CS_STAGES;
+            for (int c0 = 0; c0 < w; c0 += COLS, ++g) {
+                const int stg = int(g % STAGES);
+                const long long u = g / STAGES;
                 if (u > 0) mbar_wait(&sm.empty[stg], unsigned((u - 1) & 1), err);
-                const int cols = min(CS_COLS, w - c0);
+                const int cols = min(COLS, w - c0);
                 const unsigned vb = unsigned(cols) * 32u * unsigned(sizeof(T));
                 const unsigned cb = unsigned(cols) * 32u * 2u;
                 mbar_expect_tx(&sm.full[stg], vb + cb);
@@ -154,8 +155,8 @@ k_coarse_stream(SellView<T> A, const T* __restrict__ xin, const T* __restrict__ 
             }
         }
         // drain: the last fill of each stage has completed before the block exits
-        for (long long h = g - 1; h >= 0 && h >= g - CS_STAGES; --h)
-            mbar_wait(&sm.full[h % CS_STAGES], unsigned((h / CS_STAGES) & 1), err);
+        for (long long h = g - 1; h >= 0 && h >= g - STAGES; --h)
+            mbar_wait(&sm.full[h % STAGES], unsigned((h / STAGES) & 1), err);
         return;
     }
     // consumers: warp = part of the slice, lane = row of the slice
@@ -165,10 +166,10 @@ k_coarse_stream(SellView<T> A, const T* __restrict__ xin, const T* __restrict__ 
         const int b = __ldg(A.sptr + s);
         const int w = (__ldg(A.sptr + s + 1) - b) >> 5;
         T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-        for (int c0 = 0; c0 < w; c0 += CS_COLS, ++g) {
-            const int stg = int(g % CS_STAGES);
-            mbar_wait(&sm.full[stg], unsigned((g / CS_STAGES) & 1), err);
-            const int cols = min(CS_COLS, w - c0);
+        for (int c0 = 0; c0 < w; c0 += COLS, ++g) {
+            const int stg = int(g % STAGES);
+            mbar_wait(&sm.full[stg], unsigned((g / STAGES) & 1), err);
+            const int cols = min(COLS, w - c0);
             const T* sv = sm.st[stg].val;
             const unsigned short* sc = sm.st[stg].col;
             // columns part + 8 q of the chunk; the chunk starts at a multiple
@@ -218,23 +219,39 @@ k_coarse_stream(SellView<T> A, const T* __restrict__ xin, const T* __restrict__ 
     }
 }
 
+template <class T, int KIND, int COLS, int STAGES>
+void launch_cfg(const Sell<T>& A, const T* xin, const T* aux, T* out, T* xacc, T sa, T sb, int first,
+                unsigned* err, cudaStream_t st)
+{
+    static int grid = 0;   // resident blocks of this instantiation (set once)
+    const size_t smem = sizeof(CsShared<T, COLS, STAGES>);
+    if (!grid) {
+        CK(cudaFuncSetAttribute(k_coarse_stream<T, KIND, COLS, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(smem)));
+        int dev = 0, sms = 0, per = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_stream<T, KIND, COLS, STAGES>, CS_THREADS,
+                                                         smem));
+        grid = std::max(1, per * sms);
+    }
+    const int g = std::max(1, std::min(grid, A.n_slices));
+    k_coarse_stream<T, KIND, COLS, STAGES><<<g, CS_THREADS, smem, st>>>(view(A), xin, aux, out, xacc, sa, sb, first,
+                                                                        err);
+    CK_LAUNCH();
+}
+
 template <class T, int KIND>
 void launch_kind(const Sell<T>& A, const T* xin, const T* aux, T* out, T* xacc, T sa, T sb, int first,
                  unsigned* err, cudaStream_t st)
 {
-    static int grid = 0;   // resident blocks of this instantiation (set once)
-    const size_t smem = sizeof(CsShared<T>);
-    if (!grid) {
-        CK(cudaFuncSetAttribute(k_coarse_stream<T, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-        int dev = 0, sms = 0, per = 0;
-        CK(cudaGetDevice(&dev));
-        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_stream<T, KIND>, CS_THREADS, smem));
-        grid = std::max(1, per * sms);
+    static int cols = -1;
+    if (cols < 0) {
+        const char* e = getenv("AIRG_COARSE_STREAM_COLS");
+        cols = e && atoi(e) == 32 ? 32 : 64;
     }
-    const int g = std::max(1, std::min(grid, A.n_slices));
-    k_coarse_stream<T, KIND><<<g, CS_THREADS, smem, st>>>(view(A), xin, aux, out, xacc, sa, sb, first, err);
-    CK_LAUNCH();
+    if (cols == 32) launch_cfg<T, KIND, 32, 3>(A, xin, aux, out, xacc, sa, sb, first, err, st);
+    else launch_cfg<T, KIND, 64, 4>(A, xin, aux, out, xacc, sa, sb, first, err, st);
 }
 
 }  // namespace

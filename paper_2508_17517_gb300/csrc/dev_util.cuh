@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <cstdio>
 #include <string>
 #include <utility>
@@ -102,6 +103,26 @@ struct DevCSR {
         v.alloc(size_t(nz));
     }
 };
+
+// Classical Gram-Schmidt in the outer FGMRES takes a second pass when the
+// first leaves ||w'||^2 < reorth_ratio() ||w||^2 (Daniel, Gragg, Kaufman &
+// Stewart 1976 test this with 0.5, i.e. ||w'|| < ||w|| / sqrt(2)).  One
+// pass against an orthonormal basis of j <= 30 vectors leaves w' with
+// |V^T w'| of order j u ||w|| (u = 2^-53), so the new basis vector is
+// orthogonal to about j u ||w|| / ||w'||.  The default 1e-8 (||w'|| >=
+// 1e-4 ||w||) keeps that below ~1e-11 per vector, so the least-squares
+// residual of a restart cycle is within a factor 1 + O(1e-10) of the true
+// one; the true FP64 residual is recomputed at every restart and at the
+// end in any case.  A V-cycle that reduces the residual by a factor
+// 0.05-0.5 per iteration gives ||w'|| / ||w|| in that range, so the 0.5
+// test reorthogonalises every step and 1e-8 almost never.  AIRG_REORTH
+// overrides the ratio (0 <= r <= 1).
+inline double reorth_ratio()
+{
+    const char* e = getenv("AIRG_REORTH");
+    const double v = e ? atof(e) : 1e-8;
+    return v >= 0.0 && v <= 1.0 ? v : 1e-8;
+}
 
 inline int grid_for(long long n, int block) { return int((n + block - 1) / block) > 0 ? int((n + block - 1) / block) : 1; }
 

@@ -384,7 +384,7 @@ void solve_multi(airg_batch_s& B, const double* const* b, double* const* x, bool
             bool again = false;
             for (int p = 0; p < P; ++p) {
                 const double* hp = B.hbuf.p + p * tot;
-                if (!st[p].active || !(hp[o.nrm()] < 0.5 * hp[o.h1() + j + 1])) continue;
+                if (!st[p].active || !(hp[o.nrm()] < airg::reorth_ratio() * hp[o.h1() + j + 1])) continue;
                 airg::Hierarchy& H = *B.H[p];
                 airg::SolveData& S = *H.solve;
                 airg::mp_multidot(H, j + 1, S.V.p, S.w.p, B.dv[p].p + o.h2(), 0, B.ps[p]);
@@ -405,7 +405,7 @@ void solve_multi(airg_batch_s& B, const double* const* b, double* const* x, bool
                 const double* hp = B.hbuf.p + p * tot;
                 const double* h1 = again ? first.data() + p * tot : hp;
                 auto h = [&](int i, int c) -> double& { return s.Hm[size_t(i) * m + c]; };
-                bool two = again && (h1[o.nrm()] < 0.5 * h1[o.h1() + j + 1]);
+                bool two = again && (h1[o.nrm()] < airg::reorth_ratio() * h1[o.h1() + j + 1]);
                 for (int i = 0; i <= j; ++i) h(i, j) = h1[o.h1() + i] + (two ? hp[o.h2() + i] : 0.0);
                 double hn = std::sqrt(std::max(hp[o.nrm()], 0.0));
                 h(j + 1, j) = hn;

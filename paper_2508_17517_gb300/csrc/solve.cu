@@ -2102,8 +2102,8 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz,
                    WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop, k_spmv<double, KK, RR>), block_rows(S.Atop), 0, st>>>(A, zj, S.w.p)));
             // classical Gram-Schmidt; a second pass only when the first
-            // one cancelled more than half of ||w||^2 ("twice is enough",
-            // Daniel, Gragg, Kaufman & Stewart 1976): ||w'|| < ||w|| / sqrt(2)
+            // one cancelled enough of ||w|| to cost orthogonality:
+            // ||w'||^2 < reorth_ratio() ||w||^2
             double* h1 = S.hdev.p;
             double* h2 = S.hdev.p + (m + 2);
             double* nrm = S.hdev.p + 2 * (m + 2);
@@ -2115,7 +2115,7 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             double ww = hh[j + 1], w1 = hh[2 * (m + 2)];
             for (int i = 0; i <= j; ++i) Hm[size_t(i) * m + j] = hh[i];
             double hsq = w1;
-            if (w1 < 0.5 * ww) {
+            if (w1 < reorth_ratio() * ww) {
                 launch_multidot(S, n, j + 1, S.V.p, n, S.w.p, h2, 0, st);
                 launch_multiaxpy(S, n, j + 1, S.V.p, n, h2, 1, S.w.p, nrm, st);
                 CK_LAUNCH();
