@@ -159,11 +159,15 @@ void add_col16(Sell<T>& S, cudaStream_t st)
 
 __global__ void k_d2f(long long n, const double* a, float* b)
 {
+    pdl_wait();
+    pdl_trigger();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
 }
 __global__ void k_f2d(long long n, const float* a, double* b)
 {
+    pdl_wait();
+    pdl_trigger();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (double)a[i];
 }
@@ -431,6 +435,10 @@ __device__ __forceinline__ void for_rows(const SellView<T, V>& S, const T* __res
     static_assert(!C16 || K > 1, "16-bit columns are read by the long-row path only");
     using PV = decltype(pre(0));
     const int lane = threadIdx.x & 31;
+    // launched by launch_pdl: wait for the previous kernel's results, then
+    // let the next kernel's blocks be scheduled into this one's tail
+    pdl_wait();
+    pdl_trigger();
     // A grid smaller than the operator's (a resident grid, Sell::persist)
     // strides over the slices; each row is computed the same way either way.
     if constexpr (K == 1) {
@@ -528,6 +536,8 @@ template <class T>
 __global__ void k_smooth0(int n, const T* __restrict__ t, const T* __restrict__ ec,
                           const int* __restrict__ W, T* __restrict__ ef, T a0)
 {
+    pdl_wait();
+    pdl_trigger();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     int wc = W[r];
@@ -547,6 +557,8 @@ __global__ void k_horner_acc(SellView<T> A, const T* __restrict__ t, const T* __
 template <class T>
 __global__ void k_acc0(int n, const T* __restrict__ t, T* __restrict__ e, T a0)
 {
+    pdl_wait();
+    pdl_trigger();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) e[r] = e[r] + a0 * t[r];
 }
@@ -554,6 +566,8 @@ __global__ void k_acc0(int n, const T* __restrict__ t, T* __restrict__ e, T a0)
 template <class T>
 __global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b)
 {
+    pdl_wait();
+    pdl_trigger();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) b[r] = a[r];
 }
@@ -575,6 +589,8 @@ __global__ void k_newton_real(SellView<T> A, const T* __restrict__ rin, T* __res
 template <class T>
 __global__ void k_newton_last(int n, const T* __restrict__ rin, T* __restrict__ x, T inv_theta, int first)
 {
+    pdl_wait();
+    pdl_trigger();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     x[r] = fma(rin[r], inv_theta, first ? T(0) : x[r]);
@@ -615,6 +631,8 @@ template <class T, int K, int R, class V, class Pre, class Epi>
 __device__ __forceinline__ void for_rows_xs(const SellView<T, V>& S, const T* __restrict__ x, int n_x,
                                             const Pre& pre, const Epi& epi)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char xs_raw[];
     T* xs = reinterpret_cast<T*>(xs_raw);
     for (int i = threadIdx.x; i < n_x; i += XS_THREADS) xs[i] = x[i];
@@ -1214,10 +1232,10 @@ void f_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
         // assembled smoother (Eq. 8 matrix): t = r_f - M e_c, then
         // e_f = W e_c + Ahat^-1 t, the last Horner kernel with a0 = 0
         LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
-                 WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M, k_fresid<T, KK, RR>), block_rows(o.M), 0, st>>>(
+                 WITH_KR(o.M, launch_pdl(st, grid_rows(o.M, k_fresid<T, KK, RR>), block_rows(o.M), 0, k_fresid<T, KK, RR>, 
                                   view(o.M), rf, ec, wk.t, wk.wa, T(0))));
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, 2 * o.Ainv.nnz + 3LL * nf,
-                 WITH_KR(o.Ainv, k_horner_last<T, KK, RR><<<grid_rows(o.Ainv, k_horner_last<T, KK, RR>), block_rows(o.Ainv), 0, st>>>(
+                 WITH_KR(o.Ainv, launch_pdl(st, grid_rows(o.Ainv, k_horner_last<T, KK, RR>), block_rows(o.Ainv), 0, k_horner_last<T, KK, RR>, 
                                      view(o.Ainv), wk.t, wk.t, ec, lv.W.p, ef, T(0))));
         return;
     }
@@ -1246,11 +1264,11 @@ void f_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
         return;
     }
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
-           WITH_KR(o.M, k_fresid<T, KK, RR><<<grid_rows(o.M, k_fresid<T, KK, RR>), block_rows(o.M), 0, st>>>(
+           WITH_KR(o.M, launch_pdl(st, grid_rows(o.M, k_fresid<T, KK, RR>), block_rows(o.M), 0, k_fresid<T, KK, RR>, 
                             view(o.M), rf, ec, wk.t, wk.wa, T(lv.alpha[p]))));
     if (p == 0) {
         LAUNCH_F(S, PK_HORNER, 3 * fB + 4LL * nf, 3LL * nf,
-               k_smooth0<T><<<g, TB, 0, st>>>(nf, wk.t, ec, lv.W.p, ef, T(lv.alpha[0])));
+               launch_pdl(st, g, TB, 0, k_smooth0<T>, nf, wk.t, ec, lv.W.p, ef, T(lv.alpha[0])));
         return;
     }
     const long long hB = mat_bytes(o.Aff) + 3 * fB;
@@ -1258,12 +1276,12 @@ void f_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
     T* wout = wk.wb;
     for (int k = p - 1; k >= 1; --k) {
         LAUNCH_F(S, PK_HORNER, hB, 2 * o.Aff.nnz + 2LL * nf,
-               WITH_KR(o.Aff, k_horner<T, KK, RR><<<grid_rows(o.Aff, k_horner<T, KK, RR>), block_rows(o.Aff), 0, st>>>(
+               WITH_KR(o.Aff, launch_pdl(st, grid_rows(o.Aff, k_horner<T, KK, RR>), block_rows(o.Aff), 0, k_horner<T, KK, RR>, 
                                   view(o.Aff), wk.t, win, wout, T(lv.alpha[k]))));
         std::swap(win, wout);
     }
     LAUNCH_F(S, PK_HORNER, hB + fB + 4LL * nf, 2 * o.Aff.nnz + 3LL * nf,
-           WITH_KR(o.Aff, k_horner_last<T, KK, RR><<<grid_rows(o.Aff, k_horner_last<T, KK, RR>), block_rows(o.Aff), 0, st>>>(
+           WITH_KR(o.Aff, launch_pdl(st, grid_rows(o.Aff, k_horner_last<T, KK, RR>), block_rows(o.Aff), 0, k_horner_last<T, KK, RR>, 
                               view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0]))));
 }
 
@@ -1277,7 +1295,7 @@ void horner_into(SolveData& S, const Sell<T>& A, const std::vector<double>& al, 
     const int p = int(al.size()) - 1;
     const long long fB = (long long)n * VB;
     if (p == 0) {
-        LAUNCH_F(S, PK_HORNER, 3 * fB, 2LL * n, k_acc0<T><<<grid_for(n, TB), TB, 0, st>>>(n, wk.t, e, T(al[0])));
+        LAUNCH_F(S, PK_HORNER, 3 * fB, 2LL * n, launch_pdl(st, grid_for(n, TB), TB, 0, k_acc0<T>, n, wk.t, e, T(al[0])));
         return;
     }
     const long long hB = mat_bytes(A) + 3 * fB;
@@ -1285,12 +1303,12 @@ void horner_into(SolveData& S, const Sell<T>& A, const std::vector<double>& al, 
     T* wout = wk.wb;
     for (int k = p - 1; k >= 1; --k) {
         LAUNCH_F(S, PK_HORNER, hB, 2 * A.nnz + 2LL * n,
-                 WITH_KR(A, k_horner<T, KK, RR><<<grid_rows(A, k_horner<T, KK, RR>), block_rows(A), 0, st>>>(view(A), wk.t, win,
+                 WITH_KR(A, launch_pdl(st, grid_rows(A, k_horner<T, KK, RR>), block_rows(A), 0, k_horner<T, KK, RR>, view(A), wk.t, win,
                                                                                         wout, T(al[k]))));
         std::swap(win, wout);
     }
     LAUNCH_F(S, PK_HORNER, hB + fB, 2 * A.nnz + 3LL * n,
-             WITH_KR(A, k_horner_acc<T, KK, RR><<<grid_rows(A, k_horner_acc<T, KK, RR>), block_rows(A), 0, st>>>(view(A), wk.t, win, e,
+             WITH_KR(A, launch_pdl(st, grid_rows(A, k_horner_acc<T, KK, RR>), block_rows(A), 0, k_horner_acc<T, KK, RR>, view(A), wk.t, win, e,
                                                                                         T(al[0]))));
 }
 
@@ -1309,11 +1327,11 @@ void c_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
     const int p = int(lv.alpha_c.size()) - 1;
     const long long cB = (long long)nc * VB;
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mc) + (long long)(lv.n_f + nc) * VB + 3 * cB, 2 * o.Mc.nnz + 2LL * nc,
-             WITH_KR(o.Mc, k_fresid<T, KK, RR><<<grid_rows(o.Mc, k_fresid<T, KK, RR>), block_rows(o.Mc), 0, st>>>(
+             WITH_KR(o.Mc, launch_pdl(st, grid_rows(o.Mc, k_fresid<T, KK, RR>), block_rows(o.Mc), 0, k_fresid<T, KK, RR>, 
                               view(o.Mc), rc, el, wk.t, wk.wa, T(lv.alpha_c[p]))));
     if (o.Ainvc.n_rows) {   // assembled: e_c += Ahat_cc^-1 t_c
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainvc) + 4 * cB, 2 * o.Ainvc.nnz + 2LL * nc,
-                 WITH_KR(o.Ainvc, k_horner_acc<T, KK, RR><<<grid_rows(o.Ainvc, k_horner_acc<T, KK, RR>), block_rows(o.Ainvc), 0, st>>>(
+                 WITH_KR(o.Ainvc, launch_pdl(st, grid_rows(o.Ainvc, k_horner_acc<T, KK, RR>), block_rows(o.Ainvc), 0, k_horner_acc<T, KK, RR>, 
                                      view(o.Ainvc), wk.t, wk.t, el + lv.n_f, T(0))));
         return;
     }
@@ -1334,11 +1352,11 @@ void f_smooth_again(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, c
     const int p = int(lv.alpha.size()) - 1;
     const long long fB = (long long)nf * VB;
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mf) + (long long)(nf + lv.n_c) * VB + 3 * fB, 2 * o.Mf.nnz + 2LL * nf,
-             WITH_KR(o.Mf, k_fresid<T, KK, RR><<<grid_rows(o.Mf, k_fresid<T, KK, RR>), block_rows(o.Mf), 0, st>>>(
+             WITH_KR(o.Mf, launch_pdl(st, grid_rows(o.Mf, k_fresid<T, KK, RR>), block_rows(o.Mf), 0, k_fresid<T, KK, RR>, 
                               view(o.Mf), rf, el, wk.t, wk.wa, T(lv.alpha[p]))));
     if (o.Ainv.n_rows) {    // assembled: e_f += Ahat_ff^-1 t
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB, 2 * o.Ainv.nnz + 2LL * nf,
-                 WITH_KR(o.Ainv, k_horner_acc<T, KK, RR><<<grid_rows(o.Ainv, k_horner_acc<T, KK, RR>), block_rows(o.Ainv), 0, st>>>(
+                 WITH_KR(o.Ainv, launch_pdl(st, grid_rows(o.Ainv, k_horner_acc<T, KK, RR>), block_rows(o.Ainv), 0, k_horner_acc<T, KK, RR>, 
                                     view(o.Ainv), wk.t, wk.t, el, T(0))));
         return;
     }
@@ -1360,16 +1378,16 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         S.cur_level = l;
         if (l > 0 && lv.n_c && S.smooth_type != AIRG_SMOOTH_F)   // restriction overwrites r_c in place
             LAUNCH_F(S, PK_RESTRICT, 2LL * lv.n_c * VB, 0,
-                     k_copy<T><<<grid_for(lv.n_c, TB), TB, 0, st>>>(lv.n_c, src + lv.off + lv.n_f,
+                     launch_pdl(st, grid_for(lv.n_c, TB), TB, 0, k_copy<T>, lv.n_c, src + lv.off + lv.n_f,
                                                                     wk.rcs + lv.rc_off));
         if (lv.n_c && Zb.val.n)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Zb) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Zb.nnz + lv.n_c,
-                   WITH_KR(Zb, k_restrict<T, KK, RR, bf16s><<<grid_rows(Zb, k_restrict<T, KK, RR, bf16s>), block_rows(Zb), 0, st>>>(
+                   WITH_KR(Zb, launch_pdl(st, grid_rows(Zb, k_restrict<T, KK, RR, bf16s>), block_rows(Zb), 0, k_restrict<T, KK, RR, bf16s>, 
                                    view(Zb), src + lv.off, src + lv.off + lv.n_f,
                                    wk.rwork + lv.off + lv.n_f)));
         else if (lv.n_c)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Z.nnz + lv.n_c,
-                   WITH_KR(Z, k_restrict<T, KK, RR><<<grid_rows(Z, k_restrict<T, KK, RR>), block_rows(Z), 0, st>>>(
+                   WITH_KR(Z, launch_pdl(st, grid_rows(Z, k_restrict<T, KK, RR>), block_rows(Z), 0, k_restrict<T, KK, RR>, 
                                   view(Z), src + lv.off, src + lv.off + lv.n_f,
                                   wk.rwork + lv.off + lv.n_f)));
     }
@@ -1421,18 +1439,18 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
             if (q.im == 0.0) {
                 if (last)
                     LAUNCH_F(S, PK_NEWTON, (i == 0 ? 2 : 3) * nB, 2LL * nco,
-                           k_newton_last<T><<<grid_for(nco, TB), TB, 0, st>>>(nco, rin, x, T(1.0 / q.re), i == 0));
+                           launch_pdl(st, grid_for(nco, TB), TB, 0, k_newton_last<T>, nco, rin, x, T(1.0 / q.re), i == 0));
                 else if (A.stream)
                     LAUNCH_F(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB, 2 * A.nnz + 4LL * nco,
                              coarse_stream_launch<T>(A, CS_REAL, rin, nullptr, rout, x, T(1.0 / q.re), T(0), i == 0,
                                                      serr, st));
                 else if (A.xs)
                     LAUNCH_F(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB, 2 * A.nnz + 4LL * nco,
-                           WITH_KR_XS(A, k_newton_real_xs<T, KK, RR><<<A.xs, XS_THREADS, xs_smem(A), st>>>(
+                           WITH_KR_XS(A, launch_pdl(st, A.xs, XS_THREADS, xs_smem(A), k_newton_real_xs<T, KK, RR>, 
                                                Av, rin, A.n_cols, rout, x, T(1.0 / q.re), i == 0)));
                 else
                     LAUNCH_F(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB, 2 * A.nnz + 4LL * nco,
-                           WITH_KR_COL(A, k_newton_real<T, KK, RR, C16><<<grid_rows(A, k_newton_real<T, KK, RR, C16>), block_rows(A), 0, st>>>(
+                           WITH_KR_COL(A, launch_pdl(st, grid_rows(A, k_newton_real<T, KK, RR, C16>), block_rows(A), 0, k_newton_real<T, KK, RR, C16>, 
                                           Av, rin, rout, x, T(1.0 / q.re), i == 0)));
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
@@ -1442,11 +1460,11 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
                                                      T(1.0 / mod2), i == 0, serr, st));
                 else if (A.xs)
                     LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, 2 * A.nnz + 4LL * nco,
-                           WITH_KR_XS(A, k_newton_pair1_xs<T, KK, RR><<<A.xs, XS_THREADS, xs_smem(A), st>>>(
+                           WITH_KR_XS(A, launch_pdl(st, A.xs, XS_THREADS, xs_smem(A), k_newton_pair1_xs<T, KK, RR>, 
                                                Av, rin, A.n_cols, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
                 else
                     LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, 2 * A.nnz + 4LL * nco,
-                           WITH_KR_COL(A, k_newton_pair1<T, KK, RR, C16><<<grid_rows(A, k_newton_pair1<T, KK, RR, C16>), block_rows(A), 0, st>>>(
+                           WITH_KR_COL(A, launch_pdl(st, grid_rows(A, k_newton_pair1<T, KK, RR, C16>), block_rows(A), 0, k_newton_pair1<T, KK, RR, C16>, 
                                           Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
                 if (!last && A.stream)
                     LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
@@ -1454,11 +1472,11 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
                                                      serr, st));
                 else if (!last && A.xs)
                     LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
-                           WITH_KR_XS(A, k_newton_pair2_xs<T, KK, RR><<<A.xs, XS_THREADS, xs_smem(A), st>>>(
+                           WITH_KR_XS(A, launch_pdl(st, A.xs, XS_THREADS, xs_smem(A), k_newton_pair2_xs<T, KK, RR>, 
                                                Av, rin, wk.ct, A.n_cols, rout, T(1.0 / mod2))));
                 else if (!last)
                     LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
-                           WITH_KR_COL(A, k_newton_pair2<T, KK, RR, C16><<<grid_rows(A, k_newton_pair2<T, KK, RR, C16>), block_rows(A), 0, st>>>(
+                           WITH_KR_COL(A, launch_pdl(st, grid_rows(A, k_newton_pair2<T, KK, RR, C16>), block_rows(A), 0, k_newton_pair2<T, KK, RR, C16>, 
                                           Av, rin, wk.ct, rout, T(1.0 / mod2))));
             }
             if (!last) { rin = rout; nb ^= 1; }
@@ -1992,11 +2010,11 @@ void precond_launch(Hierarchy& H, const double* v, double* z, cudaStream_t st)
     SolveData& S = *H.solve;
     long long n = S.n0;
     if (mixed_precision(H.opt)) {
-        LAUNCH(S, PK_LAYOUT, 12 * n, k_d2f<<<grid_for(n, TB), TB, 0, st>>>(n, v, S.vin32.p));
+        LAUNCH(S, PK_LAYOUT, 12 * n, launch_pdl(st, grid_for(n, TB), TB, 0, k_d2f, n, v, S.vin32.p));
         VWork<float> wk{S.rwork32.p, S.t32.p, S.wa32.p, S.wb32.p, nullptr, S.cr032.p, S.cr132.p, S.ct32.p,
                         S.rcs32.p};
         vcycle<float>(S, S.vin32.p, S.e32.p, wk, st);
-        LAUNCH(S, PK_LAYOUT, 12 * n, k_f2d<<<grid_for(n, TB), TB, 0, st>>>(n, S.e32.p, z));
+        LAUNCH(S, PK_LAYOUT, 12 * n, launch_pdl(st, grid_for(n, TB), TB, 0, k_f2d, n, S.e32.p, z));
         CK_LAUNCH();
     } else {
         VWork<double> wk{S.rwork.p, S.t.p, S.wa.p, S.wb.p, nullptr, S.cr0.p, S.cr1.p, S.ct.p, S.rcs.p};
