@@ -721,7 +721,9 @@ def run_gpu_pair(args):
         vdt = "f32" if wa["opts"].get("precision", 0) in (1, 2) else "f64"
         roof = roofline_entry(G, torch, h, b, x, rtol, flush, args.steps, sinfo["levels"], t_max / args.steps,
                               peak, peak_kind, vdt, {"value": "c3_fp64", "mixed": "c3_fp32",
-                                                     "mixed_bf16r": "c3_bf16"}[key])
+                                                     # bf16 R changes no coarse operator: the FP32
+                                                     # captures apply where the operator's bytes match
+                                                     "mixed_bf16r": "c3_fp32"}[key])
         x.zero_()
         _, info = G.airg_solve(h, b, x, rtol=rtol)
         res[key] = dict(value=world * n * args.steps / (t_max / 1e3), ms=t_max / args.steps,

@@ -45,12 +45,14 @@ constexpr int MAXK = 128;        // right-hand sides per batch (KW <= 4)
 // (acc = 0).  Every thread of the block reaches the barrier.
 template <class T, int KW, int PW, class V, class Pre, class Epi>
 __device__ __forceinline__ void bfor_rows(const SellView<T, V>& S, const T* __restrict__ x, int k, bool dot,
-                                          const Pre& pre, const Epi& epi)
+                                          const Pre& pre, const Epi& epi, int rev = 0)
 {
     using PV = decltype(pre(0, 0));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int part = warp % PW;
-    const int r = blockIdx.x * (BT / 32 / PW) + warp / PW;
+    // rev != 0: blocks take the rows in reverse order (serpentine chains)
+    const int bx = rev ? int(gridDim.x) - 1 - int(blockIdx.x) : int(blockIdx.x);
+    const int r = bx * (BT / 32 / PW) + warp / PW;
     const bool valid = r < S.n_rows;
     const bool lead = valid && part == 0;
     const PV pv = lead ? pre(r, lane) : PV{};
@@ -188,7 +190,7 @@ __global__ void kb_fresid(SellView<T> M, const T* __restrict__ rf, const T* __re
 
 template <class T, int KW, int PW>
 __global__ void kb_horner(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
-                          T* __restrict__ wout, T ak, int k)
+                          T* __restrict__ wout, T ak, int k, int rev)
 {
     bfor_rows<T, KW, PW>(A, win, k, true,
                          [&](int r, int lane) { return row_vals<T, KW>(t, nullptr, r, -1, lane, k); },
@@ -198,13 +200,13 @@ __global__ void kb_horner(SellView<T> A, const T* __restrict__ t, const T* __res
             int q = lane + 32 * j;
             if (q < k) wout[size_t(r) * k + q] = fma(ak, pv.a[j], a[j]);
         }
-    });
+    }, rev);
 }
 
 template <class T, int KW, int PW>
 __global__ void kb_horner_last(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
                                const T* __restrict__ ec, const int* __restrict__ W,
-                               T* __restrict__ ef, T a0, int k)
+                               T* __restrict__ ef, T a0, int k, int rev)
 {
     bfor_rows<T, KW, PW>(A, win, k, true,
                          [&](int r, int lane) { return row_vals<T, KW>(t, ec, r, W[r], lane, k); },
@@ -214,7 +216,7 @@ __global__ void kb_horner_last(SellView<T> A, const T* __restrict__ t, const T* 
             int q = lane + 32 * j;
             if (q < k) ef[size_t(r) * k + q] = pv.b[j] + fma(a0, pv.a[j], a[j]);
         }
-    });
+    }, rev);
 }
 
 // last Horner term of an in-place smoother: e += a_0 t + A win (C-point
@@ -222,7 +224,7 @@ __global__ void kb_horner_last(SellView<T> A, const T* __restrict__ t, const T* 
 // an assembled inverse)
 template <class T, int KW, int PW>
 __global__ void kb_horner_acc(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win, T* e, T a0,
-                              int k)
+                              int k, int rev)
 {
     bfor_rows<T, KW, PW>(A, win, k, true,
                          [&](int r, int lane) { return row_vals<T, KW>(t, e, r, r, lane, k); },
@@ -232,7 +234,7 @@ __global__ void kb_horner_acc(SellView<T> A, const T* __restrict__ t, const T* _
             int q = lane + 32 * j;
             if (q < k) e[size_t(r) * k + q] = pv.b[j] + fma(a0, pv.a[j], a[j]);
         }
-    });
+    }, rev);
 }
 
 // degree-0 in-place correction e += a_0 t, and a copy, over m values
@@ -264,7 +266,7 @@ __global__ void kb_smooth0(long long n, const T* __restrict__ t, const T* __rest
 // Newton steps of the coarse polynomial (Sec. 2.3) for k right-hand sides
 template <class T, int KW, int PW>
 __global__ void kb_newton_real(SellView<T> A, const T* __restrict__ rin, T* __restrict__ rout,
-                               T* __restrict__ x, T inv, int first, int last, int k)
+                               T* __restrict__ x, T inv, int first, int last, int k, int rev)
 {
     bfor_rows<T, KW, PW>(A, rin, k, !last,
                          [&](int r, int lane) { return row_vals<T, KW>(rin, first ? nullptr : x, r, r, lane, k); },
@@ -278,12 +280,12 @@ __global__ void kb_newton_real(SellView<T> A, const T* __restrict__ rin, T* __re
                 if (!last) rout[o] = pv.a[j] - a[j] * inv;
             }
         }
-    });
+    }, rev);
 }
 
 template <class T, int KW, int PW>
 __global__ void kb_newton_pair1(SellView<T> A, const T* __restrict__ rin, T* __restrict__ t,
-                                T* __restrict__ x, T two_a, T inv2, int first, int k)
+                                T* __restrict__ x, T two_a, T inv2, int first, int k, int rev)
 {
     bfor_rows<T, KW, PW>(A, rin, k, true,
                          [&](int r, int lane) { return row_vals<T, KW>(rin, first ? nullptr : x, r, r, lane, k); },
@@ -298,12 +300,12 @@ __global__ void kb_newton_pair1(SellView<T> A, const T* __restrict__ rin, T* __r
                 x[o] = fma(tt, inv2, pv.b[j]);
             }
         }
-    });
+    }, rev);
 }
 
 template <class T, int KW, int PW>
 __global__ void kb_newton_pair2(SellView<T> A, const T* __restrict__ rin, const T* __restrict__ t,
-                                T* __restrict__ rout, T inv2, int k)
+                                T* __restrict__ rout, T inv2, int k, int rev)
 {
     bfor_rows<T, KW, PW>(A, t, k, true,
                          [&](int r, int lane) { return row_vals<T, KW>(rin, nullptr, r, -1, lane, k); },
@@ -313,7 +315,7 @@ __global__ void kb_newton_pair2(SellView<T> A, const T* __restrict__ rin, const 
             int q = lane + 32 * j;
             if (q < k) rout[size_t(r) * k + q] = pv.a[j] - a[j] * inv2;
         }
-    });
+    }, rev);
 }
 
 __global__ void kb_d2f(long long m, const double* a, float* b)
@@ -587,7 +589,7 @@ void bf_smooth(SolveData& S, int l, int k, const T* v, T* e, const BWork<T>& wk,
         // assembled smoother: e_f = W e_c + Ahat^-1 t (last Horner kernel, a0 = 0)
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, (2 * o.Ainv.nnz + 3LL * nf) * kk,
                  WITH_KWPW(k, o.Ainv, kb_horner_last<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Ainv), wk.t, wk.t, ec,
-                                                                               lv.W.p, ef, T(0), k)));
+                                                                               lv.W.p, ef, T(0), k, 0)));
         return;
     }
     if (p == 0) {
@@ -602,12 +604,12 @@ void bf_smooth(SolveData& S, int l, int k, const T* v, T* e, const BWork<T>& wk,
     for (int kq = p - 1; kq >= 1; --kq) {
         LAUNCH_F(S, PK_HORNER, hB, (2 * o.Aff.nnz + 2LL * nf) * kk,
                WITH_KWPW(k, o.Aff, kb_horner<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Aff), wk.t, win, wout,
-                                                                        T(lv.alpha[kq]), k)));
+                                                                        T(lv.alpha[kq]), k, serpentine(p - 1 - kq))));
         std::swap(win, wout);
     }
     LAUNCH_F(S, PK_HORNER, hB + fB + 4LL * nf, (2 * o.Aff.nnz + 3LL * nf) * kk,
            WITH_KWPW(k, o.Aff, kb_horner_last<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Aff), wk.t, win, ec,
-                                                                         lv.W.p, ef, T(lv.alpha[0]), k)));
+                                                                         lv.W.p, ef, T(lv.alpha[0]), k, serpentine(p - 1))));
 }
 
 // e += q(A) t by Horner for k right-hand sides, w = a_p t already in wk.wa
@@ -629,12 +631,12 @@ void bhorner_into(SolveData& S, const Sell<T>& A, const std::vector<double>& al,
     for (int kq = p - 1; kq >= 1; --kq) {
         LAUNCH_F(S, PK_HORNER, hB, (2 * A.nnz + 2LL * n) * kk,
                  WITH_KWPW(k, A, kb_horner<T, KW, PW><<<grid_rows(n, PW), BT, 0, st>>>(view(A), wk.t, win, wout,
-                                                                                      T(al[kq]), k)));
+                                                                                      T(al[kq]), k, serpentine(p - 1 - kq))));
         std::swap(win, wout);
     }
     LAUNCH_F(S, PK_HORNER, hB + fB, (2 * A.nnz + 3LL * n) * kk,
              WITH_KWPW(k, A, kb_horner_acc<T, KW, PW><<<grid_rows(n, PW), BT, 0, st>>>(view(A), wk.t, win, e,
-                                                                                      T(al[0]), k)));
+                                                                                      T(al[0]), k, serpentine(p - 1))));
 }
 
 // C-point smooth of level l for k right-hand sides (Sec. 2):
@@ -660,7 +662,7 @@ void bc_smooth(SolveData& S, int l, int k, const T* v, T* e, const BWork<T>& wk,
     if (o.Ainvc.n_rows) {
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainvc) + 4 * cB, (2 * o.Ainvc.nnz + 2LL * nc) * kk,
                  WITH_KWPW(k, o.Ainvc, kb_horner_acc<T, KW, PW><<<grid_rows(nc, PW), BT, 0, st>>>(
-                                           view(o.Ainvc), wk.t, wk.t, ec, T(0), k)));
+                                           view(o.Ainvc), wk.t, wk.t, ec, T(0), k, 0)));
         return;
     }
     bhorner_into<T>(S, o.Acc, lv.alpha_c, wk, ec, nc, k, st);
@@ -687,7 +689,7 @@ void bf_smooth_again(SolveData& S, int l, int k, const T* v, T* e, const BWork<T
     if (o.Ainv.n_rows) {
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB, (2 * o.Ainv.nnz + 2LL * nf) * kk,
                  WITH_KWPW(k, o.Ainv, kb_horner_acc<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(
-                                          view(o.Ainv), wk.t, wk.t, el, T(0), k)));
+                                          view(o.Ainv), wk.t, wk.t, el, T(0), k, 0)));
         return;
     }
     bhorner_into<T>(S, o.Aff, lv.alpha, wk, el, nf, k, st);
@@ -735,6 +737,7 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         T* bufs[2] = {wk.cr0, wk.cr1};
         int nb = 0;
         size_t nr = S.roots.size();
+        int nsp = 0;   // SpMVs with the coarse operator so far (their direction alternates)
         for (size_t i = 0; i < nr; ++i) {
             bool last = i + 1 == nr;
             const Root& q = S.roots[i];
@@ -743,16 +746,18 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
                 LAUNCH_F(S, PK_NEWTON, (last ? 0 : mB + 2 * nB) + (i == 0 ? 2 : 3) * nB,
                          (last ? 2LL * nco : 2 * A.nnz + 4LL * nco) * kk,
                        WITH_KWPW(k, A, kb_newton_real<T, KW, PW><<<grid_rows(nco, PW), BT, 0, st>>>(
-                                      Av, rin, rout, x, T(1.0 / q.re), i == 0, last, k)));
+                                      Av, rin, rout, x, T(1.0 / q.re), i == 0, last, k, serpentine(nsp))));
+                nsp += 1;
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
                 LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, (2 * A.nnz + 4LL * nco) * kk,
                        WITH_KWPW(k, A, kb_newton_pair1<T, KW, PW><<<grid_rows(nco, PW), BT, 0, st>>>(
-                                      Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0, k)));
+                                      Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0, k, serpentine(nsp))));
                 if (!last)
                     LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, (2 * A.nnz + 2LL * nco) * kk,
                            WITH_KWPW(k, A, kb_newton_pair2<T, KW, PW><<<grid_rows(nco, PW), BT, 0, st>>>(
-                                          Av, rin, wk.ct, rout, T(1.0 / mod2), k)));
+                                          Av, rin, wk.ct, rout, T(1.0 / mod2), k, serpentine(nsp + 1))));
+                nsp += 2;
             }
             if (!last) { rin = rout; nb ^= 1; }
         }

@@ -7,10 +7,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstdio>
-#include <map>
-#include <mutex>
 #include <string>
-#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -129,74 +126,14 @@ inline double reorth_ratio()
 
 inline int grid_for(long long n, int block) { return int((n + block - 1) / block) > 0 ? int((n + block - 1) / block) : 1; }
 
-// ------------------------------------------- programmatic dependent launch --
-// A kernel launched by launch_pdl with the programmatic-serialisation
-// attribute may have its blocks scheduled while the previous kernel on the
-// stream is still running its last wave, so the launch and the block
-// start-up overlap that tail.  Such a kernel must call pdl_wait() before it
-// reads anything an earlier kernel wrote or writes anything an earlier
-// kernel reads; pdl_wait() returns once every preceding kernel on the
-// stream has completed and its writes are visible.  pdl_trigger() lets the
-// next kernel's blocks be scheduled as soon as every block of this one has
-// passed it.  Both are no-ops in a kernel launched without the attribute.
-//
-// The attribute is set only for grids larger than one wave of resident
-// blocks: there the next kernel's blocks fill the slots that the last wave
-// leaves idle.  A grid that fits on the GPU at once keeps every slot it
-// needs busy until it ends, and waiting blocks of the next kernel placed
-// beside it measured slower (the coarse steps of a 17k-row operator, 10.8
-// against 13.8 us).  AIRG_PDL=0 never sets it, AIRG_PDL=all always does;
-// the arithmetic is the same in every case.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-enum PdlMode { PDL_OFF = 0, PDL_MULTI_WAVE = 1, PDL_ALL = 2 };
-
-inline PdlMode pdl_mode()
-{
-    const char* e = getenv("AIRG_PDL");
-    if (!e) return PDL_MULTI_WAVE;
-    if (e[0] == '0') return PDL_OFF;
-    if (e[0] == 'a') return PDL_ALL;
-    return PDL_MULTI_WAVE;
-}
-
-// Blocks of `kernel` (block size, dynamic shared memory) that fit on the
-// GPU at once, looked up once per configuration.
-template <class F>
-int resident_blocks(F* kernel, int block, size_t smem)
-{
-    static std::mutex mu;
-    static std::map<std::tuple<const void*, int, size_t>, int> cache;
-    std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_tuple(reinterpret_cast<const void*>(kernel), block, smem);
-    auto it = cache.find(key);
-    if (it != cache.end()) return it->second;
-    int dev = 0, sms = 0, per = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, smem));
-    const int g = per * sms > 0 ? per * sms : 1;
-    cache[key] = g;
-    return g;
-}
-
+// ------------------------------------------------------------ launches --
+// kern<<<grid, block, smem, st>>>(args...), written as a call so that a
+// launch can sit inside the statement of a dispatch macro.
 template <class... KArgs, class... Args>
-inline void launch_pdl(cudaStream_t st, int grid, int block, size_t smem, void (*kern)(KArgs...), Args&&... args)
+inline void launch_kernel(cudaStream_t st, int grid, int block, size_t smem, void (*kern)(KArgs...),
+                          Args&&... args)
 {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(grid));
-    cfg.blockDim = dim3(unsigned(block));
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    const PdlMode m = pdl_mode();
-    const bool on = m == PDL_ALL || (m == PDL_MULTI_WAVE && grid > resident_blocks(kern, block, smem));
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = on ? 1 : 0;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    CK(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+    kern<<<unsigned(grid), unsigned(block), smem, st>>>(std::forward<Args>(args)...);
 }
 
 template <class T>

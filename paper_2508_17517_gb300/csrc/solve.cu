@@ -159,15 +159,11 @@ void add_col16(Sell<T>& S, cudaStream_t st)
 
 __global__ void k_d2f(long long n, const double* a, float* b)
 {
-    pdl_wait();
-    pdl_trigger();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
 }
 __global__ void k_f2d(long long n, const float* a, double* b)
 {
-    pdl_wait();
-    pdl_trigger();
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = (double)a[i];
 }
@@ -430,20 +426,21 @@ __device__ __forceinline__ void dot_slices(const SellView<T, V>& S, const T* __r
 // change the arithmetic.
 template <class T, int K, int R, bool C16 = false, class V, class Pre, class Epi>
 __device__ __forceinline__ void for_rows(const SellView<T, V>& S, const T* __restrict__ x, const Pre& pre,
-                                         const Epi& epi)
+                                         const Epi& epi, int rev = 0)
 {
     static_assert(!C16 || K > 1, "16-bit columns are read by the long-row path only");
     using PV = decltype(pre(0));
     const int lane = threadIdx.x & 31;
-    // launched by launch_pdl: wait for the previous kernel's results, then
-    // let the next kernel's blocks be scheduled into this one's tail
-    pdl_wait();
-    pdl_trigger();
     // A grid smaller than the operator's (a resident grid, Sell::persist)
     // strides over the slices; each row is computed the same way either way.
+    // rev != 0 takes the groups of slices in reverse order (block 0 the last
+    // group): a chain of steps over one operator that alternates the
+    // direction starts each step on the lines the previous one left in L2.
     if constexpr (K == 1) {
         const int nw = (gridDim.x * blockDim.x) >> 5;
-        for (int s0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * R; s0 < S.n_slices; s0 += nw * R) {
+        const int ngr = (S.n_slices + R - 1) / R;
+        for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ngr; w += nw) {
+            const int s0 = (rev ? ngr - 1 - w : w) * R;
             PV pv[R];
 #pragma unroll
             for (int q = 0; q < R; ++q) {
@@ -462,7 +459,8 @@ __device__ __forceinline__ void for_rows(const SellView<T, V>& S, const T* __res
         constexpr int SPB = wpb_for(K) / K;   // slices per block-group
         const int part = (threadIdx.x >> 5) % K;
         const int ngroups = (S.n_slices + SPB - 1) / SPB;
-        for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {   // uniform over the block
+        for (int g0 = blockIdx.x; g0 < ngroups; g0 += gridDim.x) {   // uniform over the block
+            const int g = rev ? ngroups - 1 - g0 : g0;
             const int slice = g * SPB + (threadIdx.x >> 5) / K;
             const int r = slice * 32 + lane;
             const bool lead = part == 0 && r < S.n_rows;
@@ -511,24 +509,24 @@ __global__ void k_fresid(SellView<T> M, const T* __restrict__ rf, const T* __res
 // Horner term: wout = a_k t + A_ff win
 template <class T, int K, int R>
 __global__ void k_horner(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
-                         T* __restrict__ wout, T ak)
+                         T* __restrict__ wout, T ak, int rev)
 {
     for_rows<T, K, R>(A, win, [&](int r) { return t[r]; },
-                      [&](int r, T d, T tr) { wout[r] = fma(ak, tr, d); });
+                      [&](int r, T d, T tr) { wout[r] = fma(ak, tr, d); }, rev);
 }
 
 // last Horner term and the correction: e_f = W e_c + (a_0 t + A_ff win)
 template <class T, int K, int R>
 __global__ void k_horner_last(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
                               const T* __restrict__ ec, const int* __restrict__ W,
-                              T* __restrict__ ef, T a0)
+                              T* __restrict__ ef, T a0, int rev)
 {
     for_rows<T, K, R>(A, win,
                       [&](int r) {
                           int wc = W[r];
                           return Pair<T>{t[r], wc >= 0 ? ec[wc] : T(0)};
                       },
-                      [&](int r, T d, Pair<T> q) { ef[r] = q.b + fma(a0, q.a, d); });
+                      [&](int r, T d, Pair<T> q) { ef[r] = q.b + fma(a0, q.a, d); }, rev);
 }
 
 // degree-0 smoother: e_f = W e_c + a_0 t
@@ -536,8 +534,6 @@ template <class T>
 __global__ void k_smooth0(int n, const T* __restrict__ t, const T* __restrict__ ec,
                           const int* __restrict__ W, T* __restrict__ ef, T a0)
 {
-    pdl_wait();
-    pdl_trigger();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     int wc = W[r];
@@ -547,18 +543,17 @@ __global__ void k_smooth0(int n, const T* __restrict__ t, const T* __restrict__ 
 // last Horner term of a smoother that corrects in place: e += a_0 t + A win
 // (the C-point smooth, and the second F-point smooth of FCF)
 template <class T, int K, int R>
-__global__ void k_horner_acc(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win, T* e, T a0)
+__global__ void k_horner_acc(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win, T* e, T a0,
+                             int rev)
 {
     for_rows<T, K, R>(A, win, [&](int r) { return Pair<T>{t[r], e[r]}; },
-                      [&](int r, T d, Pair<T> q) { e[r] = q.b + fma(a0, q.a, d); });
+                      [&](int r, T d, Pair<T> q) { e[r] = q.b + fma(a0, q.a, d); }, rev);
 }
 
 // degree-0 in-place correction: e += a_0 t
 template <class T>
 __global__ void k_acc0(int n, const T* __restrict__ t, T* __restrict__ e, T a0)
 {
-    pdl_wait();
-    pdl_trigger();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) e[r] = e[r] + a0 * t[r];
 }
@@ -566,8 +561,6 @@ __global__ void k_acc0(int n, const T* __restrict__ t, T* __restrict__ e, T a0)
 template <class T>
 __global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b)
 {
-    pdl_wait();
-    pdl_trigger();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < n) b[r] = a[r];
 }
@@ -576,21 +569,19 @@ __global__ void k_copy(int n, const T* __restrict__ a, T* __restrict__ b)
 // real root, not the last: x += r / theta, r' = r - A r / theta
 template <class T, int K, int R, bool C16 = false>
 __global__ void k_newton_real(SellView<T> A, const T* __restrict__ rin, T* __restrict__ rout,
-                              T* __restrict__ x, T inv_theta, int first)
+                              T* __restrict__ x, T inv_theta, int first, int rev)
 {
     for_rows<T, K, R, C16>(A, rin, [&](int r) { return Pair<T>{rin[r], first ? T(0) : x[r]}; },
                       [&](int r, T d, Pair<T> q) {
                           x[r] = fma(q.a, inv_theta, q.b);
                           rout[r] = q.a - d * inv_theta;
-                      });
+                      }, rev);
 }
 
 // last real root: x += r / theta (no residual update, no SpMV)
 template <class T>
 __global__ void k_newton_last(int n, const T* __restrict__ rin, T* __restrict__ x, T inv_theta, int first)
 {
-    pdl_wait();
-    pdl_trigger();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     x[r] = fma(rin[r], inv_theta, first ? T(0) : x[r]);
@@ -598,22 +589,22 @@ __global__ void k_newton_last(int n, const T* __restrict__ rin, T* __restrict__ 
 
 template <class T, int K, int R, bool C16 = false>
 __global__ void k_newton_pair1(SellView<T> A, const T* __restrict__ rin, T* __restrict__ t,
-                               T* __restrict__ x, T two_a, T inv_mod2, int first)
+                               T* __restrict__ x, T two_a, T inv_mod2, int first, int rev)
 {
     for_rows<T, K, R, C16>(A, rin, [&](int r) { return Pair<T>{rin[r], first ? T(0) : x[r]}; },
                       [&](int r, T d, Pair<T> q) {
                           T tt = two_a * q.a - d;
                           t[r] = tt;
                           x[r] = fma(tt, inv_mod2, q.b);
-                      });
+                      }, rev);
 }
 
 template <class T, int K, int R, bool C16 = false>
 __global__ void k_newton_pair2(SellView<T> A, const T* __restrict__ rin, const T* __restrict__ t,
-                               T* __restrict__ rout, T inv_mod2)
+                               T* __restrict__ rout, T inv_mod2, int rev)
 {
     for_rows<T, K, R, C16>(A, t, [&](int r) { return rin[r]; },
-                      [&](int r, T d, T ri) { rout[r] = ri - d * inv_mod2; });
+                      [&](int r, T d, T ri) { rout[r] = ri - d * inv_mod2; }, rev);
 }
 
 // ------------------------------------- coarse steps with x in shared memory --
@@ -631,8 +622,6 @@ template <class T, int K, int R, class V, class Pre, class Epi>
 __device__ __forceinline__ void for_rows_xs(const SellView<T, V>& S, const T* __restrict__ x, int n_x,
                                             const Pre& pre, const Epi& epi)
 {
-    pdl_wait();
-    pdl_trigger();
     extern __shared__ __align__(16) unsigned char xs_raw[];
     T* xs = reinterpret_cast<T*>(xs_raw);
     for (int i = threadIdx.x; i < n_x; i += XS_THREADS) xs[i] = x[i];
@@ -1232,11 +1221,11 @@ void f_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
         // assembled smoother (Eq. 8 matrix): t = r_f - M e_c, then
         // e_f = W e_c + Ahat^-1 t, the last Horner kernel with a0 = 0
         LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
-                 WITH_KR(o.M, launch_pdl(st, grid_rows(o.M, k_fresid<T, KK, RR>), block_rows(o.M), 0, k_fresid<T, KK, RR>, 
+                 WITH_KR(o.M, launch_kernel(st, grid_rows(o.M, k_fresid<T, KK, RR>), block_rows(o.M), 0, k_fresid<T, KK, RR>,
                                   view(o.M), rf, ec, wk.t, wk.wa, T(0))));
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, 2 * o.Ainv.nnz + 3LL * nf,
-                 WITH_KR(o.Ainv, launch_pdl(st, grid_rows(o.Ainv, k_horner_last<T, KK, RR>), block_rows(o.Ainv), 0, k_horner_last<T, KK, RR>, 
-                                     view(o.Ainv), wk.t, wk.t, ec, lv.W.p, ef, T(0))));
+                 WITH_KR(o.Ainv, launch_kernel(st, grid_rows(o.Ainv, k_horner_last<T, KK, RR>), block_rows(o.Ainv), 0, k_horner_last<T, KK, RR>,
+                                     view(o.Ainv), wk.t, wk.t, ec, lv.W.p, ef, T(0), 0)));
         return;
     }
     if (S.smooth_grid[pidx2] > 0 && p < 32) {
@@ -1264,25 +1253,26 @@ void f_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
         return;
     }
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
-           WITH_KR(o.M, launch_pdl(st, grid_rows(o.M, k_fresid<T, KK, RR>), block_rows(o.M), 0, k_fresid<T, KK, RR>, 
+           WITH_KR(o.M, launch_kernel(st, grid_rows(o.M, k_fresid<T, KK, RR>), block_rows(o.M), 0, k_fresid<T, KK, RR>,
                             view(o.M), rf, ec, wk.t, wk.wa, T(lv.alpha[p]))));
     if (p == 0) {
         LAUNCH_F(S, PK_HORNER, 3 * fB + 4LL * nf, 3LL * nf,
-               launch_pdl(st, g, TB, 0, k_smooth0<T>, nf, wk.t, ec, lv.W.p, ef, T(lv.alpha[0])));
+               launch_kernel(st, g, TB, 0, k_smooth0<T>, nf, wk.t, ec, lv.W.p, ef, T(lv.alpha[0])));
         return;
     }
     const long long hB = mat_bytes(o.Aff) + 3 * fB;
     T* win = wk.wa;
     T* wout = wk.wb;
+    // the p SpMVs with A_ff alternate their direction (serpentine order)
     for (int k = p - 1; k >= 1; --k) {
         LAUNCH_F(S, PK_HORNER, hB, 2 * o.Aff.nnz + 2LL * nf,
-               WITH_KR(o.Aff, launch_pdl(st, grid_rows(o.Aff, k_horner<T, KK, RR>), block_rows(o.Aff), 0, k_horner<T, KK, RR>, 
-                                  view(o.Aff), wk.t, win, wout, T(lv.alpha[k]))));
+               WITH_KR(o.Aff, launch_kernel(st, grid_rows(o.Aff, k_horner<T, KK, RR>), block_rows(o.Aff), 0, k_horner<T, KK, RR>,
+                                  view(o.Aff), wk.t, win, wout, T(lv.alpha[k]), serpentine(p - 1 - k))));
         std::swap(win, wout);
     }
     LAUNCH_F(S, PK_HORNER, hB + fB + 4LL * nf, 2 * o.Aff.nnz + 3LL * nf,
-           WITH_KR(o.Aff, launch_pdl(st, grid_rows(o.Aff, k_horner_last<T, KK, RR>), block_rows(o.Aff), 0, k_horner_last<T, KK, RR>, 
-                              view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0]))));
+           WITH_KR(o.Aff, launch_kernel(st, grid_rows(o.Aff, k_horner_last<T, KK, RR>), block_rows(o.Aff), 0, k_horner_last<T, KK, RR>,
+                              view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0]), serpentine(p - 1))));
 }
 
 // e += q(A) t by Horner, with w = a_p t already in wk.wa (written by the
@@ -1295,7 +1285,7 @@ void horner_into(SolveData& S, const Sell<T>& A, const std::vector<double>& al, 
     const int p = int(al.size()) - 1;
     const long long fB = (long long)n * VB;
     if (p == 0) {
-        LAUNCH_F(S, PK_HORNER, 3 * fB, 2LL * n, launch_pdl(st, grid_for(n, TB), TB, 0, k_acc0<T>, n, wk.t, e, T(al[0])));
+        LAUNCH_F(S, PK_HORNER, 3 * fB, 2LL * n, launch_kernel(st, grid_for(n, TB), TB, 0, k_acc0<T>, n, wk.t, e, T(al[0])));
         return;
     }
     const long long hB = mat_bytes(A) + 3 * fB;
@@ -1303,13 +1293,13 @@ void horner_into(SolveData& S, const Sell<T>& A, const std::vector<double>& al, 
     T* wout = wk.wb;
     for (int k = p - 1; k >= 1; --k) {
         LAUNCH_F(S, PK_HORNER, hB, 2 * A.nnz + 2LL * n,
-                 WITH_KR(A, launch_pdl(st, grid_rows(A, k_horner<T, KK, RR>), block_rows(A), 0, k_horner<T, KK, RR>, view(A), wk.t, win,
-                                                                                        wout, T(al[k]))));
+                 WITH_KR(A, launch_kernel(st, grid_rows(A, k_horner<T, KK, RR>), block_rows(A), 0, k_horner<T, KK, RR>, view(A), wk.t, win,
+                                       wout, T(al[k]), serpentine(p - 1 - k))));
         std::swap(win, wout);
     }
     LAUNCH_F(S, PK_HORNER, hB + fB, 2 * A.nnz + 3LL * n,
-             WITH_KR(A, launch_pdl(st, grid_rows(A, k_horner_acc<T, KK, RR>), block_rows(A), 0, k_horner_acc<T, KK, RR>, view(A), wk.t, win, e,
-                                                                                        T(al[0]))));
+             WITH_KR(A, launch_kernel(st, grid_rows(A, k_horner_acc<T, KK, RR>), block_rows(A), 0, k_horner_acc<T, KK, RR>, view(A), wk.t, win, e,
+                                   T(al[0]), serpentine(p - 1))));
 }
 
 // C-point smooth of level l (Sec. 2): t_c = r_c - [A_cf A_cc] e_l with the
@@ -1327,12 +1317,12 @@ void c_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
     const int p = int(lv.alpha_c.size()) - 1;
     const long long cB = (long long)nc * VB;
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mc) + (long long)(lv.n_f + nc) * VB + 3 * cB, 2 * o.Mc.nnz + 2LL * nc,
-             WITH_KR(o.Mc, launch_pdl(st, grid_rows(o.Mc, k_fresid<T, KK, RR>), block_rows(o.Mc), 0, k_fresid<T, KK, RR>, 
+             WITH_KR(o.Mc, launch_kernel(st, grid_rows(o.Mc, k_fresid<T, KK, RR>), block_rows(o.Mc), 0, k_fresid<T, KK, RR>,
                               view(o.Mc), rc, el, wk.t, wk.wa, T(lv.alpha_c[p]))));
     if (o.Ainvc.n_rows) {   // assembled: e_c += Ahat_cc^-1 t_c
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainvc) + 4 * cB, 2 * o.Ainvc.nnz + 2LL * nc,
-                 WITH_KR(o.Ainvc, launch_pdl(st, grid_rows(o.Ainvc, k_horner_acc<T, KK, RR>), block_rows(o.Ainvc), 0, k_horner_acc<T, KK, RR>, 
-                                     view(o.Ainvc), wk.t, wk.t, el + lv.n_f, T(0))));
+                 WITH_KR(o.Ainvc, launch_kernel(st, grid_rows(o.Ainvc, k_horner_acc<T, KK, RR>), block_rows(o.Ainvc), 0, k_horner_acc<T, KK, RR>,
+                                     view(o.Ainvc), wk.t, wk.t, el + lv.n_f, T(0), 0)));
         return;
     }
     horner_into<T>(S, o.Acc, lv.alpha_c, wk, el + lv.n_f, nc, st);
@@ -1352,12 +1342,12 @@ void f_smooth_again(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, c
     const int p = int(lv.alpha.size()) - 1;
     const long long fB = (long long)nf * VB;
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mf) + (long long)(nf + lv.n_c) * VB + 3 * fB, 2 * o.Mf.nnz + 2LL * nf,
-             WITH_KR(o.Mf, launch_pdl(st, grid_rows(o.Mf, k_fresid<T, KK, RR>), block_rows(o.Mf), 0, k_fresid<T, KK, RR>, 
+             WITH_KR(o.Mf, launch_kernel(st, grid_rows(o.Mf, k_fresid<T, KK, RR>), block_rows(o.Mf), 0, k_fresid<T, KK, RR>,
                               view(o.Mf), rf, el, wk.t, wk.wa, T(lv.alpha[p]))));
     if (o.Ainv.n_rows) {    // assembled: e_f += Ahat_ff^-1 t
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB, 2 * o.Ainv.nnz + 2LL * nf,
-                 WITH_KR(o.Ainv, launch_pdl(st, grid_rows(o.Ainv, k_horner_acc<T, KK, RR>), block_rows(o.Ainv), 0, k_horner_acc<T, KK, RR>, 
-                                    view(o.Ainv), wk.t, wk.t, el, T(0))));
+                 WITH_KR(o.Ainv, launch_kernel(st, grid_rows(o.Ainv, k_horner_acc<T, KK, RR>), block_rows(o.Ainv), 0, k_horner_acc<T, KK, RR>,
+                                    view(o.Ainv), wk.t, wk.t, el, T(0), 0)));
         return;
     }
     horner_into<T>(S, o.Aff, lv.alpha, wk, el, nf, st);
@@ -1378,16 +1368,16 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
         S.cur_level = l;
         if (l > 0 && lv.n_c && S.smooth_type != AIRG_SMOOTH_F)   // restriction overwrites r_c in place
             LAUNCH_F(S, PK_RESTRICT, 2LL * lv.n_c * VB, 0,
-                     launch_pdl(st, grid_for(lv.n_c, TB), TB, 0, k_copy<T>, lv.n_c, src + lv.off + lv.n_f,
+                     launch_kernel(st, grid_for(lv.n_c, TB), TB, 0, k_copy<T>, lv.n_c, src + lv.off + lv.n_f,
                                                                     wk.rcs + lv.rc_off));
         if (lv.n_c && Zb.val.n)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Zb) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Zb.nnz + lv.n_c,
-                   WITH_KR(Zb, launch_pdl(st, grid_rows(Zb, k_restrict<T, KK, RR, bf16s>), block_rows(Zb), 0, k_restrict<T, KK, RR, bf16s>, 
+                   WITH_KR(Zb, launch_kernel(st, grid_rows(Zb, k_restrict<T, KK, RR, bf16s>), block_rows(Zb), 0, k_restrict<T, KK, RR, bf16s>,
                                    view(Zb), src + lv.off, src + lv.off + lv.n_f,
                                    wk.rwork + lv.off + lv.n_f)));
         else if (lv.n_c)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Z.nnz + lv.n_c,
-                   WITH_KR(Z, launch_pdl(st, grid_rows(Z, k_restrict<T, KK, RR>), block_rows(Z), 0, k_restrict<T, KK, RR>, 
+                   WITH_KR(Z, launch_kernel(st, grid_rows(Z, k_restrict<T, KK, RR>), block_rows(Z), 0, k_restrict<T, KK, RR>,
                                   view(Z), src + lv.off, src + lv.off + lv.n_f,
                                   wk.rwork + lv.off + lv.n_f)));
     }
@@ -1431,6 +1421,7 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
                                                      S.bar.p, S.bar.p + 1, (int*)(S.bar.p + 2)))));
             goto coarse_done;
         }
+        int nsp = 0;   // SpMVs with the coarse operator so far (their direction alternates)
         for (size_t i = 0; i < nr; ++i) {
             bool last = i + 1 == nr;
             const Root& q = S.roots[i];
@@ -1439,19 +1430,20 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
             if (q.im == 0.0) {
                 if (last)
                     LAUNCH_F(S, PK_NEWTON, (i == 0 ? 2 : 3) * nB, 2LL * nco,
-                           launch_pdl(st, grid_for(nco, TB), TB, 0, k_newton_last<T>, nco, rin, x, T(1.0 / q.re), i == 0));
+                           launch_kernel(st, grid_for(nco, TB), TB, 0, k_newton_last<T>, nco, rin, x, T(1.0 / q.re), i == 0));
                 else if (A.stream)
                     LAUNCH_F(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB, 2 * A.nnz + 4LL * nco,
                              coarse_stream_launch<T>(A, CS_REAL, rin, nullptr, rout, x, T(1.0 / q.re), T(0), i == 0,
                                                      serr, st));
                 else if (A.xs)
                     LAUNCH_F(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB, 2 * A.nnz + 4LL * nco,
-                           WITH_KR_XS(A, launch_pdl(st, A.xs, XS_THREADS, xs_smem(A), k_newton_real_xs<T, KK, RR>, 
+                           WITH_KR_XS(A, launch_kernel(st, A.xs, XS_THREADS, xs_smem(A), k_newton_real_xs<T, KK, RR>,
                                                Av, rin, A.n_cols, rout, x, T(1.0 / q.re), i == 0)));
                 else
                     LAUNCH_F(S, PK_NEWTON, mB + 2 * nB + (i == 0 ? 2 : 3) * nB, 2 * A.nnz + 4LL * nco,
-                           WITH_KR_COL(A, launch_pdl(st, grid_rows(A, k_newton_real<T, KK, RR, C16>), block_rows(A), 0, k_newton_real<T, KK, RR, C16>, 
-                                          Av, rin, rout, x, T(1.0 / q.re), i == 0)));
+                           WITH_KR_COL(A, launch_kernel(st, grid_rows(A, k_newton_real<T, KK, RR, C16>), block_rows(A), 0, k_newton_real<T, KK, RR, C16>,
+                                          Av, rin, rout, x, T(1.0 / q.re), i == 0, serpentine(nsp))));
+                if (!last) nsp += 1;
             } else {
                 double mod2 = q.re * q.re + q.im * q.im;
                 if (A.stream)
@@ -1460,24 +1452,25 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
                                                      T(1.0 / mod2), i == 0, serr, st));
                 else if (A.xs)
                     LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, 2 * A.nnz + 4LL * nco,
-                           WITH_KR_XS(A, launch_pdl(st, A.xs, XS_THREADS, xs_smem(A), k_newton_pair1_xs<T, KK, RR>, 
+                           WITH_KR_XS(A, launch_kernel(st, A.xs, XS_THREADS, xs_smem(A), k_newton_pair1_xs<T, KK, RR>,
                                                Av, rin, A.n_cols, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
                 else
                     LAUNCH_F(S, PK_NEWTON, mB + (i == 0 ? 3 : 4) * nB, 2 * A.nnz + 4LL * nco,
-                           WITH_KR_COL(A, launch_pdl(st, grid_rows(A, k_newton_pair1<T, KK, RR, C16>), block_rows(A), 0, k_newton_pair1<T, KK, RR, C16>, 
-                                          Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0)));
+                           WITH_KR_COL(A, launch_kernel(st, grid_rows(A, k_newton_pair1<T, KK, RR, C16>), block_rows(A), 0, k_newton_pair1<T, KK, RR, C16>,
+                                          Av, rin, wk.ct, x, T(2.0 * q.re), T(1.0 / mod2), i == 0, serpentine(nsp))));
                 if (!last && A.stream)
                     LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
                              coarse_stream_launch<T>(A, CS_PAIR2, wk.ct, rin, rout, nullptr, T(0), T(1.0 / mod2), 0,
                                                      serr, st));
                 else if (!last && A.xs)
                     LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
-                           WITH_KR_XS(A, launch_pdl(st, A.xs, XS_THREADS, xs_smem(A), k_newton_pair2_xs<T, KK, RR>, 
+                           WITH_KR_XS(A, launch_kernel(st, A.xs, XS_THREADS, xs_smem(A), k_newton_pair2_xs<T, KK, RR>,
                                                Av, rin, wk.ct, A.n_cols, rout, T(1.0 / mod2))));
                 else if (!last)
                     LAUNCH_F(S, PK_NEWTON, mB + 3 * nB, 2 * A.nnz + 2LL * nco,
-                           WITH_KR_COL(A, launch_pdl(st, grid_rows(A, k_newton_pair2<T, KK, RR, C16>), block_rows(A), 0, k_newton_pair2<T, KK, RR, C16>, 
-                                          Av, rin, wk.ct, rout, T(1.0 / mod2))));
+                           WITH_KR_COL(A, launch_kernel(st, grid_rows(A, k_newton_pair2<T, KK, RR, C16>), block_rows(A), 0, k_newton_pair2<T, KK, RR, C16>,
+                                          Av, rin, wk.ct, rout, T(1.0 / mod2), serpentine(nsp + 1))));
+                nsp += last ? 1 : 2;
             }
             if (!last) { rin = rout; nb ^= 1; }
         }
@@ -2010,11 +2003,11 @@ void precond_launch(Hierarchy& H, const double* v, double* z, cudaStream_t st)
     SolveData& S = *H.solve;
     long long n = S.n0;
     if (mixed_precision(H.opt)) {
-        LAUNCH(S, PK_LAYOUT, 12 * n, launch_pdl(st, grid_for(n, TB), TB, 0, k_d2f, n, v, S.vin32.p));
+        LAUNCH(S, PK_LAYOUT, 12 * n, launch_kernel(st, grid_for(n, TB), TB, 0, k_d2f, n, v, S.vin32.p));
         VWork<float> wk{S.rwork32.p, S.t32.p, S.wa32.p, S.wb32.p, nullptr, S.cr032.p, S.cr132.p, S.ct32.p,
                         S.rcs32.p};
         vcycle<float>(S, S.vin32.p, S.e32.p, wk, st);
-        LAUNCH(S, PK_LAYOUT, 12 * n, launch_pdl(st, grid_for(n, TB), TB, 0, k_f2d, n, S.e32.p, z));
+        LAUNCH(S, PK_LAYOUT, 12 * n, launch_kernel(st, grid_for(n, TB), TB, 0, k_f2d, n, S.e32.p, z));
         CK_LAUNCH();
     } else {
         VWork<double> wk{S.rwork.p, S.t.p, S.wa.p, S.wb.p, nullptr, S.cr0.p, S.cr1.p, S.ct.p, S.rcs.p};

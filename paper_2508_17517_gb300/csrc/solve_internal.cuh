@@ -131,6 +131,17 @@ inline int choose_parts(long long nnz, int n_rows)
     return p;
 }
 
+// Direction of the i-th of a chain of SpMVs with one operator: even steps
+// forward, odd steps reversed (serpentine order), so that each step starts
+// on the end of the operator that the previous step read last and that is
+// most likely still in L2.  Each row is computed the same way in either
+// direction.  AIRG_SERPENTINE=0 keeps every step forward.
+inline int serpentine(int i)
+{
+    const char* e = getenv("AIRG_SERPENTINE");
+    return (e && e[0] == '0') ? 0 : (i & 1);
+}
+
 // warps per block for P warps per slice (blocks of at least 8 warps)
 __host__ __device__ constexpr int wpb_for(int P) { return P > 8 ? P : 8; }
 

@@ -80,3 +80,27 @@ def test_batched_host_buffers_and_richardson(outer):
         if q % 4 == 0:
             xo, _ = O.solve(Ho, po.A, bo, rtol=1e-10, outer="richardson" if outer else "fgmres")
             assert np.linalg.norm(X[q] - xo) / np.linalg.norm(xo) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_serpentine_order_never_changes_a_bit(prec, monkeypatch):
+    """The batched Horner and Newton chains alternate their traversal
+    direction; with AIRG_SERPENTINE=0 every step runs forward.  The k
+    solutions are equal bit for bit either way."""
+    w = workload("grid", (120, 101))
+    vx, vy = velocity(w["theta"])
+    k = 12
+    rng = np.random.default_rng(91 + prec)
+    po = O.advection_2d(w["nx"], w["ny"], vx, vy)
+    g = rng.uniform(0.0, 1.0, (k, po.inflow.size))
+    s = rng.standard_normal((k, po.A.n_rows))
+    pg = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
+    b = G.airg_assemble_rhs_advection2d(pg, torch.tensor(g, device="cuda"), torch.tensor(s, device="cuda"))
+    xs = []
+    for serp in ("0", "1"):
+        monkeypatch.setenv("AIRG_SERPENTINE", serp)
+        h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"], G.airg_options_default(**dict(w["opts"], precision=prec)))
+        x, info = G.airg_solve(h, b, rtol=1e-10)
+        assert info.converged
+        xs.append(x.cpu().numpy())
+    assert np.array_equal(xs[0], xs[1])
