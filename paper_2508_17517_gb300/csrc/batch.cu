@@ -582,12 +582,12 @@ void bf_smooth(SolveData& S, int l, int k, const T* v, T* e, const BWork<T>& wk,
     const int p = int(lv.alpha.size()) - 1;
     const long long fB = (long long)nf * VB * kk;
     S.cur_level = l;
-    LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB * kk + 3 * fB, (2 * o.M.nnz + 2LL * nf) * kk,
+    LAUNCH_F(S, PK_FRESID, mat_bytes32(o.M) + (long long)lv.n_c * VB * kk + 3 * fB, (2 * o.M.nnz + 2LL * nf) * kk,
            WITH_KWPW(k, o.M, kb_fresid<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.M), rf, ec, wk.t, wk.wa,
                                                                     T(lv.alpha[p]), k)));
     if (o.Ainv.n_rows) {
         // assembled smoother: e_f = W e_c + Ahat^-1 t (last Horner kernel, a0 = 0)
-        LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, (2 * o.Ainv.nnz + 3LL * nf) * kk,
+        LAUNCH_F(S, PK_HORNER, mat_bytes32(o.Ainv) + 4 * fB + 4LL * nf, (2 * o.Ainv.nnz + 3LL * nf) * kk,
                  WITH_KWPW(k, o.Ainv, kb_horner_last<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Ainv), wk.t, wk.t, ec,
                                                                                lv.W.p, ef, T(0), k, 0)));
         return;
@@ -598,7 +598,7 @@ void bf_smooth(SolveData& S, int l, int k, const T* v, T* e, const BWork<T>& wk,
                                                                             T(lv.alpha[0]), k));
         return;
     }
-    const long long hB = mat_bytes(o.Aff) + 3 * fB;
+    const long long hB = mat_bytes32(o.Aff) + 3 * fB;
     T* win = wk.wa;
     T* wout = wk.wb;
     for (int kq = p - 1; kq >= 1; --kq) {
@@ -625,7 +625,7 @@ void bhorner_into(SolveData& S, const Sell<T>& A, const std::vector<double>& al,
                  kb_acc0<T><<<grid_for((long long)n * k, BT), BT, 0, st>>>((long long)n * k, wk.t, e, T(al[0])));
         return;
     }
-    const long long hB = mat_bytes(A) + 3 * fB;
+    const long long hB = mat_bytes32(A) + 3 * fB;
     T* win = wk.wa;
     T* wout = wk.wb;
     for (int kq = p - 1; kq >= 1; --kq) {
@@ -655,12 +655,12 @@ void bc_smooth(SolveData& S, int l, int k, const T* v, T* e, const BWork<T>& wk,
     T* ec = el + size_t(lv.n_f) * k;
     const int p = int(lv.alpha_c.size()) - 1;
     const long long cB = (long long)nc * VB * kk;
-    LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mc) + (long long)(lv.n_f + nc) * VB * kk + 3 * cB,
+    LAUNCH_F(S, PK_FRESID, mat_bytes32(o.Mc) + (long long)(lv.n_f + nc) * VB * kk + 3 * cB,
              (2 * o.Mc.nnz + 2LL * nc) * kk,
              WITH_KWPW(k, o.Mc, kb_fresid<T, KW, PW><<<grid_rows(nc, PW), BT, 0, st>>>(view(o.Mc), rc, el, wk.t, wk.wa,
                                                                                    T(lv.alpha_c[p]), k)));
     if (o.Ainvc.n_rows) {
-        LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainvc) + 4 * cB, (2 * o.Ainvc.nnz + 2LL * nc) * kk,
+        LAUNCH_F(S, PK_HORNER, mat_bytes32(o.Ainvc) + 4 * cB, (2 * o.Ainvc.nnz + 2LL * nc) * kk,
                  WITH_KWPW(k, o.Ainvc, kb_horner_acc<T, KW, PW><<<grid_rows(nc, PW), BT, 0, st>>>(
                                            view(o.Ainvc), wk.t, wk.t, ec, T(0), k, 0)));
         return;
@@ -682,12 +682,12 @@ void bf_smooth_again(SolveData& S, int l, int k, const T* v, T* e, const BWork<T
     T* el = e + size_t(lv.off) * k;
     const int p = int(lv.alpha.size()) - 1;
     const long long fB = (long long)nf * VB * kk;
-    LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mf) + (long long)(nf + lv.n_c) * VB * kk + 3 * fB,
+    LAUNCH_F(S, PK_FRESID, mat_bytes32(o.Mf) + (long long)(nf + lv.n_c) * VB * kk + 3 * fB,
              (2 * o.Mf.nnz + 2LL * nf) * kk,
              WITH_KWPW(k, o.Mf, kb_fresid<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(view(o.Mf), rf, el, wk.t, wk.wa,
                                                                                    T(lv.alpha[p]), k)));
     if (o.Ainv.n_rows) {
-        LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB, (2 * o.Ainv.nnz + 2LL * nf) * kk,
+        LAUNCH_F(S, PK_HORNER, mat_bytes32(o.Ainv) + 4 * fB, (2 * o.Ainv.nnz + 2LL * nf) * kk,
                  WITH_KWPW(k, o.Ainv, kb_horner_acc<T, KW, PW><<<grid_rows(nf, PW), BT, 0, st>>>(
                                           view(o.Ainv), wk.t, wk.t, el, T(0), k, 0)));
         return;
@@ -713,13 +713,13 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
                      kb_copy<T><<<grid_for((long long)lv.n_c * k, BT), BT, 0, st>>>(
                          (long long)lv.n_c * k, src + size_t(lv.off + lv.n_f) * k, wk.rcs + size_t(lv.rc_off) * k));
         if (lv.n_c && Zb.val.n)
-            LAUNCH_F(S, PK_RESTRICT, mat_bytes(Zb) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
+            LAUNCH_F(S, PK_RESTRICT, mat_bytes32(Zb) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
                      (2 * Zb.nnz + lv.n_c) * kk,
                      WITH_KWPW(k, Zb, kb_restrict<T, KW, PW, bf16s><<<grid_rows(lv.n_c, PW), BT, 0, st>>>(
                                     view(Zb), src + size_t(lv.off) * k, src + size_t(lv.off + lv.n_f) * k,
                                     wk.rwork + size_t(lv.off + lv.n_f) * k, k)));
         else if (lv.n_c)
-            LAUNCH_F(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
+            LAUNCH_F(S, PK_RESTRICT, mat_bytes32(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB * kk,
                      (2 * Z.nnz + lv.n_c) * kk,
                    WITH_KWPW(k, Z, kb_restrict<T, KW, PW><<<grid_rows(lv.n_c, PW), BT, 0, st>>>(
                                   view(Z), src + size_t(lv.off) * k, src + size_t(lv.off + lv.n_f) * k,
@@ -731,7 +731,7 @@ void bvcycle(SolveData& S, int k, const T* v, T* e, const BWork<T>& wk, cudaStre
         const Sell<T>& A = bcoarse<T>(S);
         SellView<T> Av = view(A);
         const int nco = S.n_coarse;
-        const long long nB = (long long)nco * VB * kk, mB = mat_bytes(A);
+        const long long nB = (long long)nco * VB * kk, mB = mat_bytes32(A);
         S.cur_level = L;
         const T* rin = rc;
         T* bufs[2] = {wk.cr0, wk.cr1};
@@ -890,7 +890,7 @@ void solve_batched(Hierarchy& H, int k, const double* b, double* x, double rtol,
     const int m = B.m;
     const int g = grid_for(nk, BT);
     SellView<double> A = view(S.Atop);
-    const long long topB = mat_bytes(S.Atop) + 16 * nk;
+    const long long topB = mat_bytes32(S.Atop) + 16 * nk;
     LAUNCH(S, PK_LAYOUT, 20 * nk, kb_to_nested<<<grid_tiles(n, k), 256, 0, st>>>(n, k, S.pos0.p, b, B.bp.p));
     LAUNCH(S, PK_LAYOUT, 20 * nk, kb_to_nested<<<grid_tiles(n, k), 256, 0, st>>>(n, k, S.pos0.p, x, B.xp.p));
     std::vector<double> bn, rn, tol(k);

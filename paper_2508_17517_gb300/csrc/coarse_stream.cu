@@ -262,7 +262,7 @@ bool coarse_stream_ok(const Sell<T>& A)
     // the layout the stream kernel reproduces: 8 parts per slice, 16-bit
     // columns; the copies start at multiples of 32 entries, so every source
     // address is 64-byte aligned (cudaMalloc bases are 256-byte aligned)
-    return A.k == CS_PARTS && A.col16.n && A.n_slices > 0 && A.padded % 32 == 0;
+    return A.k == CS_PARTS && A.col16.n && !A.cbase.n && A.n_slices > 0 && A.padded % 32 == 0;
 }
 
 template <class T>

@@ -73,12 +73,12 @@ __global__ void k_sell_fill(int nrows, int nslices, const int* rp, const int* ci
     int s = r >> 5, lane = r & 31;
     int w = (sptr[s + 1] - sptr[s]) >> 5;
     int base = sptr[s] + lane;
-    if (r >= nrows) {
-        for (int k = 0; k < w; ++k) { col[base + k * 32] = 0; val[base + k * 32] = T(0); }
+    if (r >= nrows) {   // columns set by k_sell_pad
+        for (int k = 0; k < w; ++k) { col[base + k * 32] = -1; val[base + k * 32] = T(0); }
         return;
     }
     int i = src_row ? src_row[r] : r;
-    int k = 0, lastc = 0;
+    int k = 0, lastc = -1;   // a row without stored entries: columns set by k_sell_pad
     bool found = false;
     for (int j = rp[i]; j < rp[i + 1]; ++j) {
         int c = cmap ? cmap[ci[j]] : ci[j];
@@ -100,6 +100,26 @@ __global__ void k_sell_fill(int nrows, int nslices, const int* rp, const int* ci
         if (found) atomicAdd(ndiag, 1ULL);
         else diag[r] = T(0);
     }
+}
+
+// Padding of the rows that have no stored entry (and of the rows past the
+// end of the last slice): the slice's smallest stored column, so that every
+// padded entry gathers a valid element near the slice's others (its value
+// is 0).  One warp per slice, lane = row.
+__global__ void k_sell_pad(int nslices, const int* __restrict__ sptr, int* col)
+{
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (s >= nslices) return;
+    const int b = sptr[s] + lane, w = (sptr[s + 1] - sptr[s]) >> 5;
+    int m = 0x7fffffff;
+    for (int k = 0; k < w; ++k) {
+        const int c = col[b + 32 * k];
+        if (c >= 0) m = min(m, c);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (m == 0x7fffffff) m = 0;
+    for (int k = 0; k < w; ++k)
+        if (col[b + 32 * k] < 0) col[b + 32 * k] = m;
 }
 
 template <class T>
@@ -127,6 +147,7 @@ void build_sell(const DevCSR& A, const int* src_row, const int* cmap, int n_cols
         k_sell_fill<T><<<grid_for((long long)S.n_slices * 32, TB), TB, 0, st>>>(
             A.n_rows, S.n_slices, A.rp.p, A.ci.p, A.v.p, src_row, cmap, S.sptr.p, S.col.p, S.val.p,
             split_diag ? S.diag.p : nullptr, cnt.p);
+    if (S.n_slices) k_sell_pad<<<grid_for((long long)S.n_slices * 32, TB), TB, 0, st>>>(S.n_slices, S.sptr.p, S.col.p);
     CK_LAUNCH();
     unsigned long long nd = 0;
     d2h(&nd, cnt.p, 1, st);
@@ -143,18 +164,59 @@ __global__ void k_col16(long long n, const int* __restrict__ col, unsigned short
     if (i < n) col16[i] = (unsigned short)col[i];
 }
 
-// 16-bit copy of the column indices of a long-row operator with at most
-// 65536 columns (the coarsest operator): its single-vector row kernels then
-// read 2 instead of 4 bytes of index per entry, with the same values.
-// AIRG_COL16=0 keeps 32-bit indices (for comparison).
-template <class T>
-void add_col16(Sell<T>& S, cudaStream_t st)
+// Slice bases and 16-bit offsets: cbase[s] = smallest column of slice s,
+// col16 = col - cbase[s]; *span gets the largest offset.  One warp per slice.
+__global__ void k_col16_rel(int nslices, const int* __restrict__ sptr, const int* __restrict__ col,
+                            int* __restrict__ cbase, unsigned short* __restrict__ col16, int* span)
+{
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (s >= nslices) return;
+    const int b = sptr[s], e = sptr[s + 1];
+    int lo = 0x7fffffff, hi = 0;
+    for (int i = b + lane; i < e; i += 32) {
+        lo = min(lo, col[i]);
+        hi = max(hi, col[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lo == 0x7fffffff) lo = hi = 0;
+    if (lane == 0) {
+        cbase[s] = lo;
+        atomicMax(span, hi - lo);
+    }
+    if (hi - lo > 65535) return;   // the operator keeps 32-bit indices
+    for (int i = b + lane; i < e; i += 32) col16[i] = (unsigned short)(col[i] - lo);
+}
+
+// 16-bit copy of an operator's column indices: its single-vector row
+// kernels then read 2 instead of 4 bytes of index per entry, and find the
+// same column values (the index itself with at most 65536 columns, else the
+// offset from the slice's base, where every slice spans at most 65536
+// columns; otherwise the operator keeps 32-bit indices only).  AIRG_COL16=0
+// keeps 32-bit indices everywhere (for comparison).
+template <class T, class V>
+void add_col16(Sell<T, V>& S, cudaStream_t st)
 {
     const char* e = getenv("AIRG_COL16");
-    if ((e && e[0] == '0') || S.k < 2 || S.n_cols > 65536 || S.padded == 0) return;
+    if ((e && e[0] == '0') || S.padded == 0 || S.n_slices == 0) return;
     S.col16.alloc(size_t(S.padded));
-    k_col16<<<grid_for(S.padded, TB), TB, 0, st>>>(S.padded, S.col.p, S.col16.p);
+    if (S.n_cols <= 65536) {
+        k_col16<<<grid_for(S.padded, TB), TB, 0, st>>>(S.padded, S.col.p, S.col16.p);
+        CK_LAUNCH();
+        return;
+    }
+    S.cbase.alloc(size_t(S.n_slices));
+    DBuf<int> span(1);
+    CK(cudaMemsetAsync(span.p, 0, sizeof(int), st));
+    k_col16_rel<<<grid_for((long long)S.n_slices * 32, TB), TB, 0, st>>>(S.n_slices, S.sptr.p, S.col.p, S.cbase.p,
+                                                                        S.col16.p, span.p);
     CK_LAUNCH();
+    if (read1(span.p, st) > 65535) {
+        S.col16 = DBuf<unsigned short>();
+        S.cbase = DBuf<int>();
+    }
 }
 
 __global__ void k_d2f(long long n, const double* a, float* b)
@@ -278,17 +340,18 @@ __global__ void k_invert_perm(int n, const int* perm, int* inv)
 // so at most 3 issued slots per row carry no entry (predicated slots still
 // occupy the FP64 pipe, which is the scarce unit for FP64 on this part).
 template <bool C16>
-__device__ __forceinline__ int ldcol(const int* __restrict__ col, const unsigned short* __restrict__ col16, int i)
+__device__ __forceinline__ int ldcol(const int* __restrict__ col, const unsigned short* __restrict__ col16, int cb,
+                                     int i)
 {
-    if constexpr (C16) return int(__ldg(col16 + i));
+    if constexpr (C16) return cb + int(__ldg(col16 + i));
     else return __ldg(col + i);
 }
 
-// C16: column indices from the 16-bit copy (same values)
+// C16: column indices from the 16-bit copy, cb + col16 (the same values)
 template <class T, int U = 4, class V = T, bool C16 = false>
 __device__ __forceinline__ T strided_dot(const int* __restrict__ col, const unsigned short* __restrict__ col16,
-                                         const V* __restrict__ val, const T* __restrict__ x, int idx, int end,
-                                         int stride)
+                                         int cb, const V* __restrict__ val, const T* __restrict__ x, int idx,
+                                         int end, int stride)
 {
     static_assert(U % 4 == 0, "U must be a multiple of 4");
     T a[4] = {T(0), T(0), T(0), T(0)};
@@ -297,7 +360,7 @@ __device__ __forceinline__ T strided_dot(const int* __restrict__ col, const unsi
         T v[U], xv[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            c[u] = ldcol<C16>(col, col16, idx + u * stride);
+            c[u] = ldcol<C16>(col, col16, cb, idx + u * stride);
             v[u] = ldval<T>(val + idx + u * stride);
         }
 #pragma unroll
@@ -311,7 +374,7 @@ __device__ __forceinline__ T strided_dot(const int* __restrict__ col, const unsi
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const bool ok = idx + u * stride < end;
-            c[u] = ok ? ldcol<C16>(col, col16, idx + u * stride) : 0;
+            c[u] = ok ? ldcol<C16>(col, col16, cb, idx + u * stride) : 0;
             v[u] = ok ? ldval<T>(val + idx + u * stride) : T(0);
         }
 #pragma unroll
@@ -334,7 +397,8 @@ __device__ __forceinline__ T row_dot(const SellView<T, V>& S, int slice, int lan
     T acc = T(0);
     if (slice < S.n_slices) {
         int b = S.sptr[slice], w = (S.sptr[slice + 1] - b) >> 5;
-        acc = strided_dot<T, U, V, C16>(S.col, S.col16, S.val, x, b + lane + 32 * part, b + lane + 32 * w,
+        const int cb = C16 && S.cbase ? __ldg(S.cbase + slice) : 0;
+        acc = strided_dot<T, U, V, C16>(S.col, S.col16, cb, S.val, x, b + lane + 32 * part, b + lane + 32 * w,
                                         32 * P);
     }
     if (P > 1) {
@@ -360,17 +424,18 @@ __device__ __forceinline__ T row_dot(const SellView<T, V>& S, int slice, int lan
 // below runs, so the slices-per-warp choice never changes a result bit.
 // When every slice is at most 4 wide, all loads of the R rows are issued
 // (predicated) before their gathers, and all gathers before the sums.
-template <class T, int R, class V>
+template <class T, int R, class V, bool C16 = false>
 __device__ __forceinline__ void dot_slices(const SellView<T, V>& S, const T* __restrict__ x, int s0, int lane,
                                            T (&acc)[R])
 {
-    int b[R], w[R];
+    int b[R], w[R], cb[R];
     bool fits = true;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
         const int s = s0 + q;
         const bool ok = s < S.n_slices;
         const int p0 = ok ? __ldg(S.sptr + s) : 0, p1 = ok ? __ldg(S.sptr + s + 1) : 0;
+        cb[q] = C16 && ok && S.cbase ? __ldg(S.cbase + s) : 0;
         b[q] = p0 + lane;
         w[q] = (p1 - p0) >> 5;
         fits = fits && w[q] <= 4;
@@ -385,7 +450,7 @@ __device__ __forceinline__ void dot_slices(const SellView<T, V>& S, const T* __r
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const bool ok = u < w[q];
-                c[q][u] = ok ? __ldg(S.col + b[q] + 32 * u) : 0;
+                c[q][u] = ok ? ldcol<C16>(S.col, S.col16, cb[q], b[q] + 32 * u) : 0;
                 v[q][u] = ok ? ldval<T>(S.val + b[q] + 32 * u) : T(0);
             }
 #pragma unroll
@@ -406,7 +471,7 @@ __device__ __forceinline__ void dot_slices(const SellView<T, V>& S, const T* __r
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const bool ok = u0 + u < w[q];
-                    c[u] = ok ? __ldg(S.col + b[q] + 32 * (u0 + u)) : 0;
+                    c[u] = ok ? ldcol<C16>(S.col, S.col16, cb[q], b[q] + 32 * (u0 + u)) : 0;
                     v[u] = ok ? ldval<T>(S.val + b[q] + 32 * (u0 + u)) : T(0);
                 }
 #pragma unroll
@@ -428,7 +493,6 @@ template <class T, int K, int R, bool C16 = false, class V, class Pre, class Epi
 __device__ __forceinline__ void for_rows(const SellView<T, V>& S, const T* __restrict__ x, const Pre& pre,
                                          const Epi& epi, int rev = 0)
 {
-    static_assert(!C16 || K > 1, "16-bit columns are read by the long-row path only");
     using PV = decltype(pre(0));
     const int lane = threadIdx.x & 31;
     // A grid smaller than the operator's (a resident grid, Sell::persist)
@@ -448,7 +512,7 @@ __device__ __forceinline__ void for_rows(const SellView<T, V>& S, const T* __res
                 pv[q] = r < S.n_rows ? pre(r) : PV{};
             }
             T acc[R];
-            dot_slices<T, R, V>(S, x, s0, lane, acc);
+            dot_slices<T, R, V, C16>(S, x, s0, lane, acc);
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int r = (s0 + q) * 32 + lane;
@@ -485,20 +549,20 @@ __global__ void k_spmv(SellView<T, V> S, const T* __restrict__ x, T* __restrict_
 
 // restriction (R = [Z I] of Eq. 4): dst_c[k] = src_c[k] + (Z src_f)[k]; the
 // values of Z may be stored narrower than T (V)
-template <class T, int K, int R, class V = T>
+template <class T, int K, int R, class V = T, bool C16 = false>
 __global__ void k_restrict(SellView<T, V> Z, const T* __restrict__ src_f, const T* __restrict__ src_c,
                            T* __restrict__ dst_c)
 {
-    for_rows<T, K, R>(Z, src_f, [&](int r) { return src_c[r]; },
+    for_rows<T, K, R, C16>(Z, src_f, [&](int r) { return src_c[r]; },
                       [&](int r, T d, T sc) { dst_c[r] = sc + d; });
 }
 
 // F-point residual (Eq. 6): t = r_f - M e_c, and the first Horner term w = a_p t
-template <class T, int K, int R>
+template <class T, int K, int R, bool C16 = false>
 __global__ void k_fresid(SellView<T> M, const T* __restrict__ rf, const T* __restrict__ ec,
                          T* __restrict__ t, T* __restrict__ w, T ap)
 {
-    for_rows<T, K, R>(M, ec, [&](int r) { return rf[r]; },
+    for_rows<T, K, R, C16>(M, ec, [&](int r) { return rf[r]; },
                       [&](int r, T d, T f) {
                           T tt = f - d;
                           t[r] = tt;
@@ -507,21 +571,21 @@ __global__ void k_fresid(SellView<T> M, const T* __restrict__ rf, const T* __res
 }
 
 // Horner term: wout = a_k t + A_ff win
-template <class T, int K, int R>
+template <class T, int K, int R, bool C16 = false>
 __global__ void k_horner(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
                          T* __restrict__ wout, T ak, int rev)
 {
-    for_rows<T, K, R>(A, win, [&](int r) { return t[r]; },
+    for_rows<T, K, R, C16>(A, win, [&](int r) { return t[r]; },
                       [&](int r, T d, T tr) { wout[r] = fma(ak, tr, d); }, rev);
 }
 
 // last Horner term and the correction: e_f = W e_c + (a_0 t + A_ff win)
-template <class T, int K, int R>
+template <class T, int K, int R, bool C16 = false>
 __global__ void k_horner_last(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win,
                               const T* __restrict__ ec, const int* __restrict__ W,
                               T* __restrict__ ef, T a0, int rev)
 {
-    for_rows<T, K, R>(A, win,
+    for_rows<T, K, R, C16>(A, win,
                       [&](int r) {
                           int wc = W[r];
                           return Pair<T>{t[r], wc >= 0 ? ec[wc] : T(0)};
@@ -542,11 +606,11 @@ __global__ void k_smooth0(int n, const T* __restrict__ t, const T* __restrict__ 
 
 // last Horner term of a smoother that corrects in place: e += a_0 t + A win
 // (the C-point smooth, and the second F-point smooth of FCF)
-template <class T, int K, int R>
+template <class T, int K, int R, bool C16 = false>
 __global__ void k_horner_acc(SellView<T> A, const T* __restrict__ t, const T* __restrict__ win, T* e, T a0,
                              int rev)
 {
-    for_rows<T, K, R>(A, win, [&](int r) { return Pair<T>{t[r], e[r]}; },
+    for_rows<T, K, R, C16>(A, win, [&](int r) { return Pair<T>{t[r], e[r]}; },
                       [&](int r, T d, Pair<T> q) { e[r] = q.b + fma(a0, q.a, d); }, rev);
 }
 
@@ -772,17 +836,12 @@ inline int block_rows(const Sell<T, V>& S) { return bk(S.k); }
     } while (0)
 
 // WITH_KR with the compile-time flag C16 = whether S's row kernels read
-// its 16-bit column indices (long rows only).
+// its 16-bit column indices.
 #define WITH_KR_COL(S, ...)                                                     \
     do {                                                                        \
         if ((S).col16.n) {                                                      \
             constexpr bool C16 = true;                                          \
-            switch ((S).r) {                                                    \
-                case 4: { constexpr int RR = 4; WITH_K_LONG((S).k, __VA_ARGS__); } break;   \
-                case 8: { constexpr int RR = 8; WITH_K_LONG((S).k, __VA_ARGS__); } break;   \
-                case 16: { constexpr int RR = 16; WITH_K_LONG((S).k, __VA_ARGS__); } break; \
-                default: fail(AIRG_ERR_STATE, "bad loads-per-lane");            \
-            }                                                                   \
+            WITH_KR(S, __VA_ARGS__);                                            \
         } else {                                                                \
             constexpr bool C16 = false;                                         \
             WITH_KR(S, __VA_ARGS__);                                            \
@@ -941,7 +1000,7 @@ __device__ __forceinline__ T row_dot_rt(const SellView<T>& S, int slice, int lan
     T acc = T(0);
     if (slice < S.n_slices) {
         int b = S.sptr[slice], w = (S.sptr[slice + 1] - b) >> 5;
-        acc = strided_dot(S.col, S.col16, S.val, x, b + lane + 32 * part, b + lane + 32 * w, 32 * P);
+        acc = strided_dot(S.col, S.col16, 0, S.val, x, b + lane + 32 * part, b + lane + 32 * w, 32 * P);
     }
     if (P > 1) {
         const int warp = threadIdx.x >> 5;
@@ -1221,10 +1280,10 @@ void f_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
         // assembled smoother (Eq. 8 matrix): t = r_f - M e_c, then
         // e_f = W e_c + Ahat^-1 t, the last Horner kernel with a0 = 0
         LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
-                 WITH_KR(o.M, launch_kernel(st, grid_rows(o.M, k_fresid<T, KK, RR>), block_rows(o.M), 0, k_fresid<T, KK, RR>,
+                 WITH_KR_COL(o.M, launch_kernel(st, grid_rows(o.M, k_fresid<T, KK, RR, C16>), block_rows(o.M), 0, k_fresid<T, KK, RR, C16>,
                                   view(o.M), rf, ec, wk.t, wk.wa, T(0))));
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB + 4LL * nf, 2 * o.Ainv.nnz + 3LL * nf,
-                 WITH_KR(o.Ainv, launch_kernel(st, grid_rows(o.Ainv, k_horner_last<T, KK, RR>), block_rows(o.Ainv), 0, k_horner_last<T, KK, RR>,
+                 WITH_KR_COL(o.Ainv, launch_kernel(st, grid_rows(o.Ainv, k_horner_last<T, KK, RR, C16>), block_rows(o.Ainv), 0, k_horner_last<T, KK, RR, C16>,
                                      view(o.Ainv), wk.t, wk.t, ec, lv.W.p, ef, T(0), 0)));
         return;
     }
@@ -1253,7 +1312,7 @@ void f_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
         return;
     }
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB, 2 * o.M.nnz + 2LL * nf,
-           WITH_KR(o.M, launch_kernel(st, grid_rows(o.M, k_fresid<T, KK, RR>), block_rows(o.M), 0, k_fresid<T, KK, RR>,
+           WITH_KR_COL(o.M, launch_kernel(st, grid_rows(o.M, k_fresid<T, KK, RR, C16>), block_rows(o.M), 0, k_fresid<T, KK, RR, C16>,
                             view(o.M), rf, ec, wk.t, wk.wa, T(lv.alpha[p]))));
     if (p == 0) {
         LAUNCH_F(S, PK_HORNER, 3 * fB + 4LL * nf, 3LL * nf,
@@ -1266,12 +1325,12 @@ void f_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
     // the p SpMVs with A_ff alternate their direction (serpentine order)
     for (int k = p - 1; k >= 1; --k) {
         LAUNCH_F(S, PK_HORNER, hB, 2 * o.Aff.nnz + 2LL * nf,
-               WITH_KR(o.Aff, launch_kernel(st, grid_rows(o.Aff, k_horner<T, KK, RR>), block_rows(o.Aff), 0, k_horner<T, KK, RR>,
+               WITH_KR_COL(o.Aff, launch_kernel(st, grid_rows(o.Aff, k_horner<T, KK, RR, C16>), block_rows(o.Aff), 0, k_horner<T, KK, RR, C16>,
                                   view(o.Aff), wk.t, win, wout, T(lv.alpha[k]), serpentine(p - 1 - k))));
         std::swap(win, wout);
     }
     LAUNCH_F(S, PK_HORNER, hB + fB + 4LL * nf, 2 * o.Aff.nnz + 3LL * nf,
-           WITH_KR(o.Aff, launch_kernel(st, grid_rows(o.Aff, k_horner_last<T, KK, RR>), block_rows(o.Aff), 0, k_horner_last<T, KK, RR>,
+           WITH_KR_COL(o.Aff, launch_kernel(st, grid_rows(o.Aff, k_horner_last<T, KK, RR, C16>), block_rows(o.Aff), 0, k_horner_last<T, KK, RR, C16>,
                               view(o.Aff), wk.t, win, ec, lv.W.p, ef, T(lv.alpha[0]), serpentine(p - 1))));
 }
 
@@ -1293,12 +1352,12 @@ void horner_into(SolveData& S, const Sell<T>& A, const std::vector<double>& al, 
     T* wout = wk.wb;
     for (int k = p - 1; k >= 1; --k) {
         LAUNCH_F(S, PK_HORNER, hB, 2 * A.nnz + 2LL * n,
-                 WITH_KR(A, launch_kernel(st, grid_rows(A, k_horner<T, KK, RR>), block_rows(A), 0, k_horner<T, KK, RR>, view(A), wk.t, win,
+                 WITH_KR_COL(A, launch_kernel(st, grid_rows(A, k_horner<T, KK, RR, C16>), block_rows(A), 0, k_horner<T, KK, RR, C16>, view(A), wk.t, win,
                                        wout, T(al[k]), serpentine(p - 1 - k))));
         std::swap(win, wout);
     }
     LAUNCH_F(S, PK_HORNER, hB + fB, 2 * A.nnz + 3LL * n,
-             WITH_KR(A, launch_kernel(st, grid_rows(A, k_horner_acc<T, KK, RR>), block_rows(A), 0, k_horner_acc<T, KK, RR>, view(A), wk.t, win, e,
+             WITH_KR_COL(A, launch_kernel(st, grid_rows(A, k_horner_acc<T, KK, RR, C16>), block_rows(A), 0, k_horner_acc<T, KK, RR, C16>, view(A), wk.t, win, e,
                                    T(al[0]), serpentine(p - 1))));
 }
 
@@ -1317,11 +1376,11 @@ void c_smooth(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, cudaStr
     const int p = int(lv.alpha_c.size()) - 1;
     const long long cB = (long long)nc * VB;
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mc) + (long long)(lv.n_f + nc) * VB + 3 * cB, 2 * o.Mc.nnz + 2LL * nc,
-             WITH_KR(o.Mc, launch_kernel(st, grid_rows(o.Mc, k_fresid<T, KK, RR>), block_rows(o.Mc), 0, k_fresid<T, KK, RR>,
+             WITH_KR_COL(o.Mc, launch_kernel(st, grid_rows(o.Mc, k_fresid<T, KK, RR, C16>), block_rows(o.Mc), 0, k_fresid<T, KK, RR, C16>,
                               view(o.Mc), rc, el, wk.t, wk.wa, T(lv.alpha_c[p]))));
     if (o.Ainvc.n_rows) {   // assembled: e_c += Ahat_cc^-1 t_c
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainvc) + 4 * cB, 2 * o.Ainvc.nnz + 2LL * nc,
-                 WITH_KR(o.Ainvc, launch_kernel(st, grid_rows(o.Ainvc, k_horner_acc<T, KK, RR>), block_rows(o.Ainvc), 0, k_horner_acc<T, KK, RR>,
+                 WITH_KR_COL(o.Ainvc, launch_kernel(st, grid_rows(o.Ainvc, k_horner_acc<T, KK, RR, C16>), block_rows(o.Ainvc), 0, k_horner_acc<T, KK, RR, C16>,
                                      view(o.Ainvc), wk.t, wk.t, el + lv.n_f, T(0), 0)));
         return;
     }
@@ -1342,11 +1401,11 @@ void f_smooth_again(SolveData& S, int l, const T* v, T* e, const VWork<T>& wk, c
     const int p = int(lv.alpha.size()) - 1;
     const long long fB = (long long)nf * VB;
     LAUNCH_F(S, PK_FRESID, mat_bytes(o.Mf) + (long long)(nf + lv.n_c) * VB + 3 * fB, 2 * o.Mf.nnz + 2LL * nf,
-             WITH_KR(o.Mf, launch_kernel(st, grid_rows(o.Mf, k_fresid<T, KK, RR>), block_rows(o.Mf), 0, k_fresid<T, KK, RR>,
+             WITH_KR_COL(o.Mf, launch_kernel(st, grid_rows(o.Mf, k_fresid<T, KK, RR, C16>), block_rows(o.Mf), 0, k_fresid<T, KK, RR, C16>,
                               view(o.Mf), rf, el, wk.t, wk.wa, T(lv.alpha[p]))));
     if (o.Ainv.n_rows) {    // assembled: e_f += Ahat_ff^-1 t
         LAUNCH_F(S, PK_HORNER, mat_bytes(o.Ainv) + 4 * fB, 2 * o.Ainv.nnz + 2LL * nf,
-                 WITH_KR(o.Ainv, launch_kernel(st, grid_rows(o.Ainv, k_horner_acc<T, KK, RR>), block_rows(o.Ainv), 0, k_horner_acc<T, KK, RR>,
+                 WITH_KR_COL(o.Ainv, launch_kernel(st, grid_rows(o.Ainv, k_horner_acc<T, KK, RR, C16>), block_rows(o.Ainv), 0, k_horner_acc<T, KK, RR, C16>,
                                     view(o.Ainv), wk.t, wk.t, el, T(0), 0)));
         return;
     }
@@ -1372,12 +1431,12 @@ void vcycle(SolveData& S, const T* v, T* e, const VWork<T>& wk, cudaStream_t st)
                                                                     wk.rcs + lv.rc_off));
         if (lv.n_c && Zb.val.n)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Zb) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Zb.nnz + lv.n_c,
-                   WITH_KR(Zb, launch_kernel(st, grid_rows(Zb, k_restrict<T, KK, RR, bf16s>), block_rows(Zb), 0, k_restrict<T, KK, RR, bf16s>,
+                   WITH_KR_COL(Zb, launch_kernel(st, grid_rows(Zb, k_restrict<T, KK, RR, bf16s, C16>), block_rows(Zb), 0, k_restrict<T, KK, RR, bf16s, C16>,
                                    view(Zb), src + lv.off, src + lv.off + lv.n_f,
                                    wk.rwork + lv.off + lv.n_f)));
         else if (lv.n_c)
             LAUNCH_F(S, PK_RESTRICT, mat_bytes(Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB, 2 * Z.nnz + lv.n_c,
-                   WITH_KR(Z, launch_kernel(st, grid_rows(Z, k_restrict<T, KK, RR>), block_rows(Z), 0, k_restrict<T, KK, RR>,
+                   WITH_KR_COL(Z, launch_kernel(st, grid_rows(Z, k_restrict<T, KK, RR, T, C16>), block_rows(Z), 0, k_restrict<T, KK, RR, T, C16>,
                                   view(Z), src + lv.off, src + lv.off + lv.n_f,
                                   wk.rwork + lv.off + lv.n_f)));
     }
@@ -1495,7 +1554,8 @@ long long sell_bytes(const Sell<double>& S, int vbytes)
 {
     // values + column indices (none for a dense diagonal) + one read of the
     // gathered input + one write
-    return (S.nnz - S.ndiag) * (vbytes + (S.col16.n ? 2 : 4)) + S.ndiag * vbytes + 2LL * S.n_rows * vbytes;
+    return (S.nnz - S.ndiag) * (vbytes + (S.col16.n ? 2 : 4)) + S.ndiag * vbytes + 2LL * S.n_rows * vbytes +
+           4LL * (long long)S.cbase.n;
 }
 
 // Row-kernel variant of every operator, picked by timing y = S x: slices
@@ -1533,10 +1593,7 @@ float tune_rows(Sell<T, V>& A, const T* x, T* y, int forced_short, int forced_lo
         if ((forced && ci % 3) || (forced_p >= 0 && A.persist != forced_p)) continue;
         SellView<T, V> v = view(A);
         auto launch = [&]() {
-            if constexpr (std::is_same<T, V>::value)
-                WITH_KR_COL(A, k_spmv<T, KK, RR, V, C16><<<grid_rows(A, k_spmv<T, KK, RR, V, C16>), block_rows(A), 0, st>>>(v, x, y));
-            else
-                WITH_KR(A, k_spmv<T, KK, RR, V><<<grid_rows(A, k_spmv<T, KK, RR, V>), block_rows(A), 0, st>>>(v, x, y));
+            WITH_KR_COL(A, k_spmv<T, KK, RR, V, C16><<<grid_rows(A, k_spmv<T, KK, RR, V, C16>), block_rows(A), 0, st>>>(v, x, y));
         };
         launch();
         CK_LAUNCH();
@@ -1838,6 +1895,15 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
             if (sl->d.Mf.n_rows) copy_sell_f32(sl->d.Mf, sl->f.Mf, st);
             if (sl->d.Ainvc.n_rows) copy_sell_f32(sl->d.Ainvc, sl->f.Ainvc, st);
         }
+        // 16-bit column copies (the FP64 operators' set the V-cycle's byte count)
+        for (Sell<double>* X : {&sl->d.Z, &sl->d.M, &sl->d.Aff, &sl->d.Ainv, &sl->d.Mc, &sl->d.Acc, &sl->d.Mf,
+                                &sl->d.Ainvc})
+            add_col16(*X, st);
+        if (mixed_precision(H.opt)) {
+            SolveLevelT<float>& o = sl->f;
+            for (Sell<float>* X : {&o.Z, &o.M, &o.Aff, &o.Ainv, &o.Mc, &o.Acc, &o.Mf, &o.Ainvc}) add_col16(*X, st);
+            add_col16(o.Zb, st);
+        }
         int vb = mixed_precision(H.opt) ? 4 : 8;
         int p = int(lv.alpha.size()) - 1;
         bytes += (H.opt.precision == AIRG_MIXED_FP32_BF16R ? sell_bytes(sl->d.Z, vb) - 2LL * lv.Z.nnz
@@ -1911,6 +1977,7 @@ void build_solve_data(Hierarchy& H, cudaStream_t st)
         if (S->n0) k_rel<<<grid_for(S->n0, TB), TB, 0, st>>>(S->n0, S->pos0.p, 0, dummy.p, inv0.p);
         CK_LAUNCH();
         build_sell<double>(A0, inv0.p, S->pos0.p, S->n0, S->Atop, true, st);
+        add_col16(S->Atop, st);
         CK(cudaStreamSynchronize(st));
     }
     // slices per warp of the short-row operators, by timing
@@ -2093,7 +2160,7 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
     int its = 0;
     auto residual = [&]() {
         LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz,
-               WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop, k_spmv<double, KK, RR>), block_rows(S.Atop), 0, st>>>(A, S.xp.p, S.w.p)));
+               WITH_KR_COL(S.Atop, k_spmv<double, KK, RR, double, C16><<<grid_rows(S.Atop, k_spmv<double, KK, RR, double, C16>), block_rows(S.Atop), 0, st>>>(A, S.xp.p, S.w.p)));
         LAUNCH_F(S, PK_KRYLOV, 24 * n, n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
         CK_LAUNCH();
         return dev_norm(S, S.r.p, n, st);
@@ -2111,7 +2178,7 @@ void fgmres(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_info& 
             double* zj = S.Zs.p + size_t(j) * n;
             precond(H, vj, zj, st);
             LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz,
-                   WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop, k_spmv<double, KK, RR>), block_rows(S.Atop), 0, st>>>(A, zj, S.w.p)));
+                   WITH_KR_COL(S.Atop, k_spmv<double, KK, RR, double, C16><<<grid_rows(S.Atop, k_spmv<double, KK, RR, double, C16>), block_rows(S.Atop), 0, st>>>(A, zj, S.w.p)));
             // classical Gram-Schmidt; a second pass only when the first
             // one cancelled enough of ||w|| to cost orthogonality:
             // ||w'||^2 < reorth_ratio() ||w||^2
@@ -2186,7 +2253,7 @@ void richardson(Hierarchy& H, double rtol, double atol, int maxit, airg_solve_in
     double tol = std::max(rtol * bn, atol);
     auto residual = [&]() {
         LAUNCH_F(S, PK_TOPSPMV, topB, 2 * S.Atop.nnz,
-               WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop, k_spmv<double, KK, RR>), block_rows(S.Atop), 0, st>>>(A, S.xp.p, S.w.p)));
+               WITH_KR_COL(S.Atop, k_spmv<double, KK, RR, double, C16><<<grid_rows(S.Atop, k_spmv<double, KK, RR, double, C16>), block_rows(S.Atop), 0, st>>>(A, S.xp.p, S.w.p)));
         LAUNCH_F(S, PK_KRYLOV, 24 * n, n, k_sub2<<<g, TB, 0, st>>>(n, S.bp.p, S.w.p, S.r.p));
         CK_LAUNCH();
         return dev_norm(S, S.r.p, n, st);
@@ -2228,7 +2295,7 @@ void mp_top_spmv(Hierarchy& H, const double* x, double* y, cudaStream_t st)
     long long n = S.n0;
     SellView<double> A = view(S.Atop);
     LAUNCH_F(S, PK_TOPSPMV, mat_bytes(S.Atop) + 16 * n, 2 * S.Atop.nnz,
-           WITH_KR(S.Atop, k_spmv<double, KK, RR><<<grid_rows(S.Atop, k_spmv<double, KK, RR>), block_rows(S.Atop), 0, st>>>(A, x, y)));
+           WITH_KR_COL(S.Atop, k_spmv<double, KK, RR, double, C16><<<grid_rows(S.Atop, k_spmv<double, KK, RR, double, C16>), block_rows(S.Atop), 0, st>>>(A, x, y)));
 }
 
 void mp_multidot(Hierarchy& H, int m, const double* V, const double* w, double* out, int selfdot,

@@ -51,10 +51,12 @@ struct bf16s {
 };
 
 //
-// col16: the same column indices in 16 bits, kept for long-row operators
-// with at most 65536 columns (the coarsest operator): their single-vector
-// row kernels read 2 instead of 4 bytes of index per entry.  `col` stays
-// for the kernels that do not read col16.
+// col16: the same column indices in 16 bits, read by the single-vector row
+// kernels (2 instead of 4 bytes of index per entry): with at most 65536
+// columns the index itself (cbase empty), else its offset from the
+// slice's smallest column, cbase[s], where every slice of the operator
+// spans at most 65536 columns.  `col` stays for the kernels that do not
+// read col16 (batched, many-grid work list, staged coarse forms).
 template <class T, class V = T>
 struct Sell {
     int n_rows = 0, n_cols = 0, n_slices = 0, k = 1, r = 1;
@@ -65,6 +67,7 @@ struct Sell {
     DBuf<int> sptr;
     DBuf<int> col;
     DBuf<unsigned short> col16;
+    DBuf<int> cbase;
     DBuf<V> val;
     DBuf<T> diag;
 };
@@ -77,13 +80,14 @@ struct SellView {
     const V* __restrict__ val;
     const T* __restrict__ diag;   // nullptr: no diagonal split
     const unsigned short* __restrict__ col16;   // nullptr: none
+    const int* __restrict__ cbase;              // nullptr: col16 holds the columns themselves
 };
 
 template <class T, class V>
 SellView<T, V> view(const Sell<T, V>& s)
 {
     return SellView<T, V>{s.n_rows, s.n_slices, s.sptr.p, s.col.p, s.val.p, s.ndiag ? s.diag.p : nullptr,
-                          s.col16.n ? s.col16.p : nullptr};
+                          s.col16.n ? s.col16.p : nullptr, s.cbase.n ? s.cbase.p : nullptr};
 }
 
 // stored value -> arithmetic type
@@ -105,11 +109,18 @@ __device__ __forceinline__ double ldval<double, bf16s>(const bf16s* p)
 
 // algorithmic bytes of the stored entries: value + column index per entry
 // (2 bytes when the row kernels read col16, else 4), value only for a
-// diagonal held densely
+// diagonal held densely; plus the slice bases the row kernels then read
 template <class T, class V>
 long long mat_bytes(const Sell<T, V>& s)
 {
-    return (s.nnz - s.ndiag) * (long long)(sizeof(V) + (s.col16.n ? 2 : 4)) + s.ndiag * (long long)sizeof(T);
+    return (s.nnz - s.ndiag) * (long long)(sizeof(V) + (s.col16.n ? 2 : 4)) + s.ndiag * (long long)sizeof(T) +
+           4LL * (long long)s.cbase.n;
+}
+// the same for kernels that read the 32-bit columns (batched, work list)
+template <class T, class V>
+long long mat_bytes32(const Sell<T, V>& s)
+{
+    return (s.nnz - s.ndiag) * (long long)(sizeof(V) + 4) + s.ndiag * (long long)sizeof(T);
 }
 
 // Warps per slice from the mean row length: the smallest power of two that

@@ -650,7 +650,7 @@ void vcycle_ops(const SolveData& S, const T* v, T* e, T* rwork, T* t, T* wa, T* 
         o.in = src + lv.off;
         o.in2 = src + lv.off + lv.n_f;
         o.out = rwork + lv.off + lv.n_f;
-        o.bytes = mat_bytes(lops<T>(lv).Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB;
+        o.bytes = mat_bytes32(lops<T>(lv).Z) + (2LL * lv.n_c + lv.n_f + lv.n_c) * VB;
         out.push_back(o);
     }
     {
@@ -659,7 +659,7 @@ void vcycle_ops(const SolveData& S, const T* v, T* e, T* rwork, T* t, T* wa, T* 
         T* bufs[2] = {cr0, cr1};
         int nb = 0;
         const size_t nr = S.roots.size();
-        const long long nB = (long long)S.n_coarse * VB, mB = mat_bytes(Ac);
+        const long long nB = (long long)S.n_coarse * VB, mB = mat_bytes32(Ac);
         for (size_t i = 0; i < nr; ++i) {
             const bool last = i + 1 == nr;
             const Root& q = S.roots[i];
@@ -712,7 +712,7 @@ void vcycle_ops(const SolveData& S, const T* v, T* e, T* rwork, T* t, T* wa, T* 
         const int p = int(lv.alpha.size()) - 1;
         const long long fB = (long long)lv.n_f * VB;
         WOp fr = sell_op(W_FRESID, o.M, fp);
-        fr.bytes = mat_bytes(o.M) + (long long)lv.n_c * VB + 3 * fB;
+        fr.bytes = mat_bytes32(o.M) + (long long)lv.n_c * VB + 3 * fB;
         fr.in = ec;
         fr.in2 = rf;
         fr.out = t;
@@ -738,7 +738,7 @@ void vcycle_ops(const SolveData& S, const T* v, T* e, T* rwork, T* t, T* wa, T* 
             h.in2 = t;
             h.out = wout;
             h.a = double(T(lv.alpha[k]));
-            h.bytes = mat_bytes(o.Aff) + 3 * fB;
+            h.bytes = mat_bytes32(o.Aff) + 3 * fB;
             out.push_back(h);
             std::swap(win, wout);
         }
@@ -749,7 +749,7 @@ void vcycle_ops(const SolveData& S, const T* v, T* e, T* rwork, T* t, T* wa, T* 
         hl.W = lv.W.p;
         hl.out = ef;
         hl.a = double(T(lv.alpha[0]));
-        hl.bytes = mat_bytes(o.Aff) + 4 * fB + 4LL * lv.n_f;
+        hl.bytes = mat_bytes32(o.Aff) + 4 * fB + 4LL * lv.n_f;
         out.push_back(hl);
     }
 }
@@ -818,7 +818,7 @@ std::vector<WOp> problem_chain(const WlProblem& pr, int j)
         WOp sp = sell_op(W_SPMV, S.Atop, 0);
         sp.in = zj;
         sp.out = S.w.p;
-        sp.bytes = mat_bytes(S.Atop) + 16 * n;
+        sp.bytes = mat_bytes32(S.Atop) + 16 * n;
         ch.push_back(sp);
         const int unit = std::max<long long>(WL_VEC_UNIT, ((n + WL_MAX_DOT_TILES - 1) / WL_MAX_DOT_TILES + 255) / 256 * 256);
         WOp dot = vec_op(W_DOT, n, 0, unit);

@@ -368,20 +368,23 @@ def test_slices_per_warp_never_changes_a_bit(prec, monkeypatch):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_coarse_16bit_columns_never_change_a_bit(prec, monkeypatch):
-    """The coarsest operator's 16-bit column indices (long rows, at most
-    65536 columns) hold the same values as the 32-bit ones: solutions are
-    equal bit for bit with and without them, at every loads-per-lane
-    setting of the coarse kernels, and with the coarse steps streaming the
-    operator through shared memory by bulk copies."""
+def test_16bit_columns_never_change_a_bit(prec, monkeypatch):
+    """16-bit column indices (the index itself for the coarsest operator,
+    with at most 65536 columns; the offset from each slice's smallest column
+    for the level and top-level operators, whose 409,600 columns need the
+    slice bases) hold the same values as the 32-bit ones: solutions are
+    equal bit for bit with and without them, at every slices-per-warp and
+    loads-per-lane setting of the row kernels, and with the coarse steps
+    streaming the operator through shared memory by bulk copies."""
     w = workload("c2", n=640)
     vx, vy = velocity(w["theta"])
     pg = G.airg_problem_advection2d(w["nx"], w["ny"], vx, vy)
     b = G.airg_assemble_rhs_advection2d(pg, torch.tensor(w["g"][0], device="cuda"))
     xs, vbytes = [], []
-    for col16, u, stream in [("0", "4", "0"), ("1", "4", "0"), ("1", "8", "0"), ("1", "16", "0"),
-                             ("1", "4", "1")]:
+    for col16, r, u, stream in [("0", "1", "4", "0"), ("1", "1", "4", "0"), ("1", "2", "8", "0"),
+                                ("1", "4", "16", "0"), ("1", "1", "4", "1")]:
         monkeypatch.setenv("AIRG_COL16", col16)
+        monkeypatch.setenv("AIRG_ROWS_PER_WARP", r)
         monkeypatch.setenv("AIRG_LOADS_PER_LANE", u)
         monkeypatch.setenv("AIRG_COARSE_STREAM", stream)
         h = G.airg_setup(pg["rowptr"], pg["col"], pg["val"],
@@ -392,7 +395,7 @@ def test_coarse_16bit_columns_never_change_a_bit(prec, monkeypatch):
         x, si = G.airg_solve(h, b, rtol=1e-10)
         assert si.converged
         xs.append(x.cpu().numpy())
-    # the 16-bit path was taken: 2 index bytes fewer per coarse entry
+    # the 16-bit paths were taken: fewer index bytes per V-cycle
     assert vbytes[1] < vbytes[0] and vbytes[1] == vbytes[2] == vbytes[3] == vbytes[4]
     for x in xs[1:]:
         assert np.array_equal(xs[0], x)
