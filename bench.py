@@ -603,13 +603,30 @@ def e2e_timed(G, torch, h, b, rtol, flush, steps):
     return e2e_s
 
 
-def hierarchy_entry(sinfo):
-    return {"levels": sinfo["levels"], "coarse_rows": sinfo["n"][-1],
-            "cycle_complexity": sinfo["cycle_complexity"], "storage_complexity": sinfo["storage_complexity"],
-            "vcycle_algorithmic_bytes": sinfo["bytes_per_vcycle"],
-            "setup_ms": sinfo["setup_ms"],
-            "setup_breakdown_ms": {k: round(v, 2) for k, v in sinfo["setup_breakdown_ms"].items()},
-            "setup_exact_dots": sinfo["exact_dots"]}
+def row_kernel_choices(G, h):
+    """What the setup's per-operator timing picked, one short string per
+    operator the solve keeps: warps per slice (w), slices per warp or loads
+    in flight per lane (r), own or resident grid, index and value bytes per
+    entry ('+base': 16-bit offsets from each slice's smallest column)."""
+    out = {}
+    for lev, name, d in G.airg_row_kernel_choices(h):
+        out["L%d %s" % (lev, name)] = "%dw r%d %s i%d%s v%d, %d rows x %.1f" % (
+            d["warps_per_slice"], d["r"], "resident" if d["resident_grid"] else "own", d["index_bytes"],
+            "+base" if d["slice_bases"] else "", d["value_bytes"], d["n_rows"],
+            d["nnz"] / max(d["n_rows"], 1))
+    return out
+
+
+def hierarchy_entry(sinfo, G=None, h=None):
+    e = {"levels": sinfo["levels"], "coarse_rows": sinfo["n"][-1],
+         "cycle_complexity": sinfo["cycle_complexity"], "storage_complexity": sinfo["storage_complexity"],
+         "vcycle_algorithmic_bytes": sinfo["bytes_per_vcycle"],
+         "setup_ms": sinfo["setup_ms"],
+         "setup_breakdown_ms": {k: round(v, 2) for k, v in sinfo["setup_breakdown_ms"].items()},
+         "setup_exact_dots": sinfo["exact_dots"]}
+    if h is not None:
+        e["row_kernels"] = row_kernel_choices(G, h)
+    return e
 
 
 def run_gpu(args):
@@ -667,7 +684,7 @@ def run_gpu(args):
             "iterations_per_solve": statistics.median(its),
             # DOFs x V-cycles per second, the paper's per-V-cycle rate (Sec. 3.2)
             "dofs_per_s_per_vcycle": value * statistics.median(its),
-            "hierarchy": hierarchy_entry(sinfo),
+            "hierarchy": hierarchy_entry(sinfo, G, h),
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": launches, "wall_s_timed": wall_s,
         }
@@ -728,7 +745,7 @@ def run_gpu_pair(args):
         _, info = G.airg_solve(h, b, x, rtol=rtol)
         res[key] = dict(value=world * n * args.steps / (t_max / 1e3), ms=t_max / args.steps,
                         its=statistics.median(its), launches=launches, wall_s=wall_s, x=x.clone(),
-                        rel_residual=info.rel_residual, hier=hierarchy_entry(sinfo), roofline=roof,
+                        rel_residual=info.rel_residual, hier=hierarchy_entry(sinfo, G, h), roofline=roof,
                         e2e=world * n * args.steps / e2e_max)
         G.airg_free(h)
         del x

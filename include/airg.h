@@ -370,6 +370,56 @@ airg_status airg_profile_read_level(const airg_handle* h, int kind, int level, d
                                     int64_t* launches, int64_t* bytes, int64_t* flops);
 
 /*
+ * Storage and row-kernel variant of one solve-phase operator, as the setup
+ * laid it out (SELL-32: slices of 32 rows, padded to their longest row) and
+ * as its timing of y = S x picked the variant (the product of Sec. 3's
+ * solve-phase SpMVs is the same whichever variant runs).
+ */
+typedef struct {
+    int64_t n_rows, n_cols;
+    int64_t nnz;              /* stored entries, diagonal included            */
+    int64_t padded;           /* SELL slots of the off-diagonal entries,
+                                 padding included                             */
+    int32_t warps_per_slice;  /* 1: short rows, one warp per slice or more    */
+    int32_t r;                /* short rows: slices per warp (1, 2, 4); long
+                                 rows: loads in flight per lane (4, 8, 16)    */
+    int32_t resident_grid;    /* 1: the row kernels run on a grid of resident
+                                 blocks that stride over the slices           */
+    int32_t index_bytes;      /* column index bytes per entry that the
+                                 single-vector row kernels read: 2 or 4       */
+    int32_t slice_bases;      /* 1: those 16-bit indices are offsets from each
+                                 slice's smallest column                      */
+    int32_t value_bytes;      /* 8 FP64, 4 FP32, 2 bfloat16                   */
+    int32_t dense_diagonal;   /* 1: the diagonal is a dense vector, outside
+                                 the slices                                   */
+} airg_operator_layout;
+
+/* Operators of airg_operator_layout_info, in the precision the V-cycle runs
+ * in (bfloat16 values for the restrictor with AIRG_MIXED_FP32_BF16R):
+ * the top-level FP64 operator of the outer iteration (level 0); level l's
+ * restrictor block Z (Eq. 4), F-point residual operator M = A_fc + A_ff W
+ * (Eq. 6 with the one-point P), A_ff (Horner terms, Eq. 7), the assembled
+ * Ahat_ff^-1 of Eq. 8 (AIRG_SMOOTH_ASSEMBLED); the C rows [A_cf A_cc], A_cc,
+ * Ahat_cc^-1 and the F rows [A_ff A_fc] of C-point / FCF smoothing; and the
+ * coarsest operator (level = number of levels - 1, Sec. 2.3). */
+enum {
+    AIRG_OPERATOR_TOP = 0, AIRG_OPERATOR_Z = 1, AIRG_OPERATOR_M = 2, AIRG_OPERATOR_AFF = 3,
+    AIRG_OPERATOR_AINV = 4, AIRG_OPERATOR_C_ROWS = 5, AIRG_OPERATOR_ACC = 6,
+    AIRG_OPERATOR_AINV_CC = 7, AIRG_OPERATOR_F_ROWS = 8, AIRG_OPERATOR_COARSE = 9
+};
+
+/*
+ * Fills *out (a HOST struct) with the layout of operator `op` of level
+ * `level`.  An operator that the hierarchy does not keep (Ahat^-1 without
+ * the assembled smoother, the C-point operators without C-point smoothing)
+ * is reported with n_rows = 0 and AIRG_OK.  AIRG_ERR_ARG for a NULL handle
+ * or out, an `op` outside the enum, AIRG_OPERATOR_TOP on a level other than
+ * 0, AIRG_OPERATOR_COARSE on another level than the coarsest, or a level
+ * operator asked of the coarsest level or beyond it.
+ */
+airg_status airg_operator_layout_info(const airg_handle* h, int level, int op, airg_operator_layout* out);
+
+/*
  * Failure-detection check of the device-side waits: launches one block that
  * waits, through the same bounded wait as the grid barrier of the
  * persistent kernels, for an arrival that never comes.  The wait must give

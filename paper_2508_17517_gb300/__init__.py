@@ -39,7 +39,7 @@ EXPORTS = ["airg_options_default", "airg_problem_advection2d", "airg_assemble_rh
            "airg_profile", "airg_profile_read", "airg_profile_read_level", "airg_dot_exact_noalloc",
            "airg_rhs_adjoint_advection2d", "airg_setup_batch", "airg_solve_batch",
            "airg_batch_free", "airg_batch_setup_info", "airg_check_wait_timeout", "airg_profile_group",
-           "airg_batch_profile", "airg_batch_profile_read"]
+           "airg_batch_profile", "airg_batch_profile_read", "airg_operator_layout_info"]
 PROFILE_KINDS = ["restrict", "f_residual", "f_smoother", "coarse_newton", "top_spmv",
                  "krylov_vectors", "layout"]
 # airg_hierarchy_info.setup_phase_ms entries (AIRG_PHASE_* of the header)
@@ -81,6 +81,18 @@ class airg_hierarchy_info(ctypes.Structure):
                 ("n", ctypes.c_int64 * 64), ("n_f", ctypes.c_int64 * 64),
                 ("nnz_a", ctypes.c_int64 * 64), ("bytes_per_vcycle", ctypes.c_int64),
                 ("setup_phase_ms", ctypes.c_double * 16), ("exact_dots", ctypes.c_int64)]
+
+
+class airg_operator_layout(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("padded", ctypes.c_int64), ("warps_per_slice", ctypes.c_int32), ("r", ctypes.c_int32),
+                ("resident_grid", ctypes.c_int32), ("index_bytes", ctypes.c_int32),
+                ("slice_bases", ctypes.c_int32), ("value_bytes", ctypes.c_int32),
+                ("dense_diagonal", ctypes.c_int32)]
+
+
+# operators of airg_operator_layout_info (AIRG_OPERATOR_* of the header)
+OPERATORS = ["top", "Z", "M", "A_ff", "Ainv", "C_rows", "A_cc", "Ainv_cc", "F_rows", "coarse"]
 
 
 class AirgError(RuntimeError):
@@ -135,6 +147,7 @@ def lib():
                                   ctypes.POINTER(i64)],
             "airg_profile_read_level": [vp, ci, ci, ctypes.POINTER(f64), ctypes.POINTER(i64),
                                         ctypes.POINTER(i64), ctypes.POINTER(i64)],
+            "airg_operator_layout_info": [vp, ci, ci, ctypes.POINTER(airg_operator_layout)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -426,6 +439,31 @@ def airg_profile_read_level(handle, levels):
             if nl.value:
                 out[(name, lev)] = (ms.value, nl.value, nb.value, nf.value)
     return out
+
+
+def airg_operator_layout_info(handle, level, op):
+    """Layout and tuned row-kernel variant of operator `op` (an index or a
+    name of OPERATORS) of `level`, as a dict; n_rows 0 for an operator the
+    hierarchy does not keep."""
+    if isinstance(op, str):
+        op = OPERATORS.index(op)
+    out = airg_operator_layout()
+    _check(lib().airg_operator_layout_info(handle.ptr, int(level), int(op), ctypes.byref(out)))
+    return {name: getattr(out, name) for name, _ in airg_operator_layout._fields_}
+
+
+def airg_row_kernel_choices(handle):
+    """Every operator that the solve keeps, level by level:
+    [(level, name, layout dict)]."""
+    L = airg_setup_info(handle)["levels"] - 1
+    rows = [(0, "top", airg_operator_layout_info(handle, 0, "top"))]
+    for lev in range(L):
+        for name in OPERATORS[1:-1]:
+            d = airg_operator_layout_info(handle, lev, name)
+            if d["n_rows"]:
+                rows.append((lev, name, d))
+    rows.append((L, "coarse", airg_operator_layout_info(handle, L, "coarse")))
+    return rows
 
 
 def _dev_f64(t, name):

@@ -506,6 +506,15 @@ airg_status airg_profile_read_level(const airg_handle* h, int kind, int level, d
     });
 }
 
+airg_status airg_operator_layout_info(const airg_handle* h, int level, int op, airg_operator_layout* out)
+{
+    return guarded([&] {
+        if (!h || !h->H || !out) airg::fail(AIRG_ERR_ARG, "null handle or out");
+        if (!airg::operator_layout(*h->H, level, op, out))
+            airg::fail(AIRG_ERR_ARG, "no operator slot for this level and op");
+    });
+}
+
 airg_status airg_check_wait_timeout(int64_t spin_limit, void* stream)
 {
     bool gave_up = false;

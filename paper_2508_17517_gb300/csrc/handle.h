@@ -75,6 +75,9 @@ void build_solve_data(Hierarchy& H, cudaStream_t st);
 void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_device,
                   double rtol, double atol, int maxit, airg_solve_info* info, cudaStream_t st);
 void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info);
+// layout and tuned row-kernel variant of one solve-phase operator
+// (AIRG_OPERATOR_*); false for an op or level that names no operator slot
+bool operator_layout(const Hierarchy& H, int level, int op, airg_operator_layout* out);
 // on: time the solve kernels; kind >= 0 restricts the timing to the
 // launches of that kind on `level` (consecutive V-cycle launches of the
 // group share one event pair)

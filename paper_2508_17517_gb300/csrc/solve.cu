@@ -2430,6 +2430,66 @@ void solve_system(Hierarchy& H, int nrhs, const double* b, double* x, bool on_de
     if (!info.converged) fail(AIRG_ERR_NOT_CONVERGED, "the outer iteration did not reach the tolerance within maxit");
 }
 
+template <class T, class V>
+void describe_sell(const Sell<T, V>& A, airg_operator_layout* out)
+{
+    std::memset(out, 0, sizeof *out);
+    if (A.n_rows == 0) return;
+    out->n_rows = A.n_rows;
+    out->n_cols = A.n_cols;
+    out->nnz = A.nnz;
+    out->padded = A.padded;
+    out->warps_per_slice = A.k;
+    out->r = A.r;
+    out->resident_grid = A.persist;
+    out->index_bytes = A.col16.n ? 2 : 4;
+    out->slice_bases = A.cbase.n ? 1 : 0;
+    out->value_bytes = int(sizeof(V));
+    out->dense_diagonal = A.ndiag ? 1 : 0;
+}
+
+template <class T>
+bool level_layout(const SolveLevelT<T>& o, bool bf16r, int op, airg_operator_layout* out)
+{
+    switch (op) {
+        case AIRG_OPERATOR_Z:
+            if (bf16r) describe_sell(o.Zb, out);
+            else describe_sell(o.Z, out);
+            return true;
+        case AIRG_OPERATOR_M: describe_sell(o.M, out); return true;
+        case AIRG_OPERATOR_AFF: describe_sell(o.Aff, out); return true;
+        case AIRG_OPERATOR_AINV: describe_sell(o.Ainv, out); return true;
+        case AIRG_OPERATOR_C_ROWS: describe_sell(o.Mc, out); return true;
+        case AIRG_OPERATOR_ACC: describe_sell(o.Acc, out); return true;
+        case AIRG_OPERATOR_AINV_CC: describe_sell(o.Ainvc, out); return true;
+        case AIRG_OPERATOR_F_ROWS: describe_sell(o.Mf, out); return true;
+        default: return false;
+    }
+}
+
+bool operator_layout(const Hierarchy& H, int level, int op, airg_operator_layout* out)
+{
+    if (!H.solve) return false;
+    const SolveData& S = *H.solve;
+    const bool mixed = mixed_precision(H.opt);
+    const int L = int(S.lv.size());   // the coarsest level's index
+    if (op == AIRG_OPERATOR_TOP) {
+        if (level != 0) return false;
+        describe_sell(S.Atop, out);
+        return true;
+    }
+    if (op == AIRG_OPERATOR_COARSE) {
+        if (level != L) return false;
+        if (mixed) describe_sell(S.Ac32, out);
+        else describe_sell(S.Ac, out);
+        return true;
+    }
+    if (level < 0 || level >= L) return false;
+    const SolveLevel& lv = *S.lv[size_t(level)];
+    return mixed ? level_layout(lv.f, H.opt.precision == AIRG_MIXED_FP32_BF16R, op, out)
+                 : level_layout(lv.d, false, op, out);
+}
+
 void fill_setup_info(const Hierarchy& H, airg_hierarchy_info* info)
 {
     std::memset(info, 0, sizeof *info);

@@ -173,6 +173,8 @@ def test_host_argument_checks_need_no_gpu(L):
     assert L.airg_dot_exact(-1, fake, fake, ctypes.byref(d), None) == ARG
     assert L.airg_dot_exact(1 << 31, fake, fake, ctypes.byref(d), None) == ARG and "2^31" in err()
     assert L.airg_check_wait_timeout(0, None) == ARG
+    lay = G.airg_operator_layout()
+    assert L.airg_operator_layout_info(None, 0, 0, ctypes.byref(lay)) == ARG and "null handle" in err()
     L.airg_free(None)
     L.airg_batch_free(None)
 
@@ -196,6 +198,7 @@ def test_header_is_plain_c_and_links_from_c(L, tmp_path):
         "  o.poly_order = 99;\n"
         "  if (airg_setup(0, &o, 0, &h) != AIRG_ERR_ARG || h) return 2;\n"
         '  printf("%d %d %.2f %s\\n", o.ddc_its, o.coarse_poly_order, o.strong_threshold, airg_last_error());\n'
+        '  printf("%d %d\\n", (int)sizeof(airg_operator_layout), (int)sizeof(airg_hierarchy_info));\n'
         "  airg_free(h);\n"
         "  return 0;\n"
         "}\n")
@@ -208,3 +211,7 @@ def test_header_is_plain_c_and_links_from_c(L, tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stderr)
     assert r.stdout.split()[:3] == ["2", "100", "0.99"] and "poly_order" in r.stdout
+    # the binding's structs have the C layout's size
+    import ctypes
+    sizes = [int(v) for v in r.stdout.splitlines()[-1].split()]
+    assert sizes == [ctypes.sizeof(G.airg_operator_layout), ctypes.sizeof(G.airg_hierarchy_info)]
