@@ -116,3 +116,28 @@ def test_corner_solution_is_the_restriction_of_the_full_solution():
     uf = O.sweep_solve(pf.A, O.assemble_rhs(pf, w["g"][0], np.zeros(48 * 48)), O.sweep_order(pf))
     uc = O.sweep_solve(pc.A, O.assemble_rhs(pc, wc["g"][0], np.zeros(400)), O.sweep_order(pc))
     assert np.array_equal(uf.reshape(48, 48)[:20, :20].reshape(-1), uc)
+
+
+def test_row_kernel_choices_are_recorded_per_operator():
+    """The line's hierarchy.row_kernels: one entry per operator the solve
+    keeps, naming its level, warps per slice, r, grid form, index and value
+    bytes (16-bit offsets from slice bases marked '+base')."""
+    class FakeG:
+        @staticmethod
+        def airg_row_kernel_choices(h):
+            base = dict(n_cols=10, padded=64, dense_diagonal=1)
+            return [(0, "top", dict(base, n_rows=1000, nnz=3000, warps_per_slice=1, r=2, resident_grid=1,
+                                    index_bytes=4, slice_bases=0, value_bytes=8)),
+                    (0, "A_ff", dict(base, n_rows=400, nnz=560, warps_per_slice=1, r=4, resident_grid=0,
+                                     index_bytes=2, slice_bases=1, value_bytes=4)),
+                    (1, "coarse", dict(base, n_rows=50, nnz=5000, warps_per_slice=8, r=16, resident_grid=0,
+                                       index_bytes=2, slice_bases=0, value_bytes=4))]
+    rk = bench.row_kernel_choices(FakeG, None)
+    assert list(rk) == ["L0 top", "L0 A_ff", "L1 coarse"]
+    assert rk["L0 top"] == "1w r2 resident i4 v8, 1000 rows x 3.0"
+    assert rk["L0 A_ff"] == "1w r4 own i2+base v4, 400 rows x 1.4"
+    assert rk["L1 coarse"] == "8w r16 own i2 v4, 50 rows x 100.0"
+    sinfo = {"levels": 2, "n": [1000, 50], "cycle_complexity": 3.0, "storage_complexity": 2.0,
+             "bytes_per_vcycle": 1, "setup_ms": 1.0, "setup_breakdown_ms": {"rap": 0.5}, "exact_dots": 0}
+    assert "row_kernels" not in bench.hierarchy_entry(sinfo)
+    assert bench.hierarchy_entry(sinfo, FakeG, object())["row_kernels"] == rk
